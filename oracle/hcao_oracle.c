@@ -1,0 +1,1067 @@
+/*
+ * hcao_oracle.c -- TEST INFRASTRUCTURE, not the product.
+ *
+ * A plain, slow, single-threaded FP64 reference DSMC for the collision phase of
+ * the HCAO model ("A harmonically-coupled-anharmonic-oscillator approach for
+ * polyatomic chemistry modeling in DSMC").  It is loaded only by the tests, by
+ * the smoke check and by the CPU-baseline leg of the benchmark.  It shares no
+ * code with the CUDA library; both follow the same written readings of the
+ * paper, so that in FP64 every decision can be compared bit for bit.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (no FMA
+ * contraction, IEEE double everywhere).
+ *
+ * Parity status per function (pins live in tests/test_oracle_*.py):
+ *   philox            : pinned (published known-answer vectors)
+ *   levels            : pinned (Morse closed-form spacing, D_e truncation by
+ *                       brute force, harmonic spacing)
+ *   K5 table sampler  : pinned (enumerated LB target, chi^2; equals literal P8)
+ *   literal P8        : pinned (enumerated LB target, chi^2)
+ *   init P6/P7        : pinned (Boltzmann populations, chi^2)
+ *   feistel           : pinned (bijection, exhaustive)
+ *   NTC + VHS         : pinned (VHS closed-form collision frequency)
+ *   relax + scatter   : pinned (per-collision momentum/energy conservation,
+ *                       equilibrium Boltzmann populations, detailed balance)
+ *   dissociation      : pinned (single-step probability vs level-sum quadrature)
+ *   exchange          : pinned (single-step probability vs level-sum quadrature)
+ *   product split     : parity unpinned beyond conservation (reading A13)
+ */
+#include "hcao_oracle.h"
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* SI constants (CODATA 2018 exact values, k_B, h, c). */
+#define KB 1.380649e-23
+#define HPLANCK 6.62607015e-34
+#define CLIGHT 299792458.0
+#define PI_D 3.14159265358979323846
+
+/* Philox stream purposes (counter word 3 = purpose << 24 | block). */
+enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
+       PU_INIT = 7, PU_TEST = 8 };
+
+#define MAX_SPECIES 16
+#define MAX_REACTIONS 32
+#define MAX_RES 4096
+#define MAX_CHANNELS 80
+#define TABLE_PAD 17
+
+typedef struct {
+    ora_species_desc d;
+    int n_modes;
+    int is_bend[ORA_MAX_MODES];
+    int n_levels[ORA_MAX_MODES];
+    double E[ORA_MAX_MODES][ORA_MAX_LEVELS];
+    double ktheta[ORA_MAX_MODES];
+    double zpe;
+    /* K5 tables */
+    double base[ORA_MAX_MODES + 1];
+    double delta, inv_delta;
+    int MT;
+    double* H[ORA_MAX_MODES];
+} o_species;
+
+typedef struct {
+    double v[3];
+    int32_t sp;
+    uint8_t qn[ORA_MAX_MODES];
+} o_part;
+
+typedef struct {
+    int n, cap;
+    o_part* p;
+    double sgmax;
+} o_cell;
+
+typedef struct {
+    int n_cells;
+    double Vc, w, dt, T_sgmax;
+    uint64_t seed;
+    uint32_t step;
+    o_cell* cells;
+    uint64_t counters[8 + MAX_REACTIONS];
+} o_res;
+
+struct ora_ctx {
+    int M;
+    double span;
+    uint32_t reject_cap;
+    int n_species, n_reactions, n_res;
+    o_species sp[MAX_SPECIES];
+    ora_reaction_desc rx[MAX_REACTIONS];
+    double rx_zpesum[MAX_REACTIONS];
+    o_res* res[MAX_RES];
+    int amode; /* 0: a=0.75, 1: a=1, 2: a=0.5 ; -1 unset */
+    double omega;
+    int log_on;
+    ora_log_rec* log;
+    int64_t log_n, log_cap;
+    int error;
+    char msg[256];
+};
+
+static void set_err(ora_ctx* c, int code, const char* m) {
+    if (!c->error) c->error = code;
+    snprintf(c->msg, sizeof c->msg, "%s", m);
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11 "Parallel random numbers:
+   as easy as 1, 2, 3"): 10 rounds of two 32x32->64 multiplies with the
+   published multipliers and Weyl key increments. */
+void ora_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+typedef struct {
+    uint32_t key[2];
+    uint32_t c0, c1, c2, purpose;
+    uint32_t block;
+    int word;
+    uint32_t buf[4];
+} o_stream;
+
+static void st_init(o_stream* s, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                    uint32_t purpose) {
+    s->key[0] = (uint32_t)seed;
+    s->key[1] = (uint32_t)(seed >> 32);
+    s->c0 = c0; s->c1 = c1; s->c2 = c2; s->purpose = purpose;
+    s->block = 0; s->word = 4;
+}
+static uint32_t st_word(o_stream* s) {
+    if (s->word == 4) {
+        uint32_t ctr[4] = { s->c0, s->c1, s->c2, (s->purpose << 24) | (s->block & 0xFFFFFFu) };
+        ora_philox(ctr, s->key, s->buf);
+        s->block++;
+        s->word = 0;
+    }
+    return s->buf[s->word++];
+}
+/* uniform in [0,1): 27 bits of the first word, 26 of the second, times 2^-53 */
+static double st_u01(o_stream* s) {
+    uint32_t a = st_word(s) >> 5;
+    uint32_t b = st_word(s) >> 6;
+    uint64_t m = ((uint64_t)a << 26) | (uint64_t)b;
+    return (double)m * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------ */
+/* Feistel bijection on [0,N): balanced 4-round Feistel network on the
+   smallest even bit width covering N, cycle-walked into [0,N).  Round
+   function: MurmurHash3's 32-bit finaliser of (R xor round key). */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+uint32_t ora_feistel(uint32_t x, uint32_t N, const uint32_t key[4]) {
+    int b = 2;
+    while (((uint64_t)1 << b) < (uint64_t)N) b += 2;
+    int half = b / 2;
+    uint32_t mask = (uint32_t)(((uint64_t)1 << half) - 1);
+    do {
+        uint32_t L = x >> half, R = x & mask;
+        for (int r = 0; r < 4; ++r) {
+            uint32_t nL = R;
+            uint32_t nR = L ^ (fmix32(R ^ key[r]) & mask);
+            L = nL; R = nR;
+        }
+        x = (L << half) | R;
+    } while (x >= N);
+    return x;
+}
+
+/* ------------------------------------------------------------------ */
+/* LB weight (E_coll - sum E_j)^(xi_rel/2 - 1), xi_rel = 5 - 2 omega:
+   exponent 0.75, 1 or 0.5 for omega = 0.75, 0.5, 1 (written with sqrt). */
+static double pw(const ora_ctx* c, double x) {
+    if (c->amode == 0) { double s = sqrt(x); return s * sqrt(s); }
+    if (c->amode == 1) return x;
+    return sqrt(x);
+}
+/* g^(2 - 2 omega): sigma_T(g) g of the VHS model */
+static double gpow(const ora_ctx* c, double g) {
+    if (c->amode == 0) return sqrt(g);
+    if (c->amode == 1) return g;
+    return 1.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Levels.  Stretch: Eq. energy-AHO, E(i) = hc we (i+1/2) - hc wexe (i+1/2)^2,
+   kept while E(i) < De and E(i) increases (reading A2: we and wexe give the
+   levels, De truncates them).  Bend: (i+1/2) k Theta (harmonic, Theta form),
+   kept while i < 256 and E(i) < ZPE + table span. */
+static void build_levels(ora_ctx* c, o_species* s) {
+    const double hc = HPLANCK * CLIGHT;
+    int n = s->d.n_stretch + s->d.n_bend;
+    s->n_modes = n;
+    for (int j = 0; j < s->d.n_stretch; ++j) {
+        s->is_bend[j] = 0;
+        int L = 0;
+        double prev = -1.0;
+        for (int i = 0; i < ORA_MAX_LEVELS; ++i) {
+            double x = (double)i + 0.5;
+            double E = hc * s->d.we[j] * x - hc * s->d.wexe[j] * (x * x);
+            if (!(E < s->d.De[j])) break;
+            if (i > 0 && !(E > prev)) break;
+            s->E[j][L++] = E;
+            prev = E;
+        }
+        s->n_levels[j] = L;
+    }
+    double zpe_bend = 0.0;
+    for (int b = 0; b < s->d.n_bend; ++b) {
+        int j = s->d.n_stretch + b;
+        s->is_bend[j] = 1;
+        s->ktheta[j] = KB * s->d.theta[b];
+    }
+    /* ZPE: sum of ground levels in mode order */
+    double z = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double e0 = s->is_bend[j] ? 0.5 * s->ktheta[j] : s->E[j][0];
+        z = z + e0;
+    }
+    (void)zpe_bend;
+    s->zpe = z;
+    double top = z + c->span;
+    for (int j = 0; j < n; ++j) {
+        if (!s->is_bend[j]) continue;
+        int L = 0;
+        for (int i = 0; i < ORA_MAX_LEVELS; ++i) {
+            double E = ((double)i + 0.5) * s->ktheta[j];
+            if (!(E < top)) break;
+            s->E[j][L++] = E;
+        }
+        s->n_levels[j] = L;
+    }
+}
+
+/* K5 tables (reading A5).  H_k(g) bounds from above the LB weight sum of modes
+   k..n-1 at budget g; grid g_m = base_k + m * delta, base_k = sum_{j>=k} E_j(0).
+   H_{n-1}(g) = sum_i pw(g - E_{n-1,i});  H_k(g) = sum_i W_{k+1}(g - E_{k,i}),
+   W_k(E) = H_k[idx_k(E)], idx_k(E) = smallest grid index with g >= E. */
+static int64_t grid_idx(const o_species* s, int k, double E) {
+    if (!(E > s->base[k])) return 0;
+    double t = (E - s->base[k]) * s->inv_delta;
+    int64_t m = (int64_t)ceil(t);
+    if (m < 1) m = 1;
+    while (s->base[k] + (double)m * s->delta < E) m++;
+    return m;
+}
+static double W_tab(const o_species* s, int k, double E) {
+    int64_t m = grid_idx(s, k, E);
+    if (m == 0) return 0.0;
+    if (m > s->MT - 1) m = s->MT - 1; /* only reached by table entries never queried */
+    return s->H[k][m];
+}
+static int build_tables(ora_ctx* c, o_species* s) {
+    int n = s->n_modes;
+    if (n == 0) return 0;
+    s->base[n] = 0.0;
+    for (int k = n - 1; k >= 0; --k) s->base[k] = s->E[k][0] + s->base[k + 1];
+    s->delta = c->span / (double)c->M;
+    s->inv_delta = 1.0 / s->delta;
+    s->MT = c->M + TABLE_PAD;
+    for (int k = n - 1; k >= 0; --k) {
+        s->H[k] = (double*)malloc(sizeof(double) * (size_t)s->MT);
+        if (!s->H[k]) return -1;
+        for (int m = 0; m < s->MT; ++m) {
+            double g = s->base[k] + (double)m * s->delta;
+            double sum = 0.0;
+            for (int i = 0; i < s->n_levels[k]; ++i) {
+                if (!(s->E[k][i] < g)) break;
+                double x = g - s->E[k][i];
+                double w = (k == n - 1) ? pw(c, x) : W_tab(s, k + 1, x);
+                sum = sum + w;
+            }
+            s->H[k][m] = sum;
+        }
+    }
+    return 0;
+}
+
+static double evib(const o_species* s, const uint8_t* qn) {
+    double e = 0.0;
+    for (int j = 0; j < s->n_modes; ++j) e = e + s->E[j][qn[j]];
+    return e;
+}
+
+/* ------------------------------------------------------------------ */
+/* Samplers of the post-collision vibrational state at collision energy Ec.
+   Target (relaxation step of the HCAO model, the joint acceptance of all
+   modes): p(i) proportional to (Ec - sum_j E_j(i_j))^(xi_rel/2-1) over states
+   with sum_j E_j(i_j) < Ec.  Return: 0 new state, 1 table overflow (state
+   kept), 2 degenerate Ec (A6, state kept), -1 rejection cap (state kept). */
+enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
+
+/* K5: sequential draw through the H tables; a draw that runs past the end of a
+   mode's level list restarts the trial.  Accepted states follow the target
+   exactly (each trial's acceptance probability is pw(..)/H_0). */
+static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
+                        uint8_t* qn_out, uint64_t* trials) {
+    int n = s->n_modes;
+    if (n == 0) return S_OK;
+    int64_t m0 = grid_idx(s, 0, Ec);
+    if (m0 > c->M) return S_OVER;
+    if (m0 == 0 || !(s->H[0][m0] > 0.0)) return S_DEGEN;
+    uint8_t qn[ORA_MAX_MODES];
+    for (uint32_t trial = 0; trial < c->reject_cap; ++trial) {
+        if (trials) (*trials)++;
+        double E = Ec;
+        int ok = 1;
+        for (int k = 0; k < n; ++k) {
+            int64_t m = (k == 0) ? m0 : grid_idx(s, k, E);
+            double u = st_u01(st);
+            double t = u * s->H[k][m];
+            double cum = 0.0;
+            int sel = -1;
+            for (int i = 0; i < s->n_levels[k]; ++i) {
+                if (!(s->E[k][i] < E)) break;
+                double x = E - s->E[k][i];
+                double w = (k == n - 1) ? pw(c, x) : W_tab(s, k + 1, x);
+                cum = cum + w;
+                if (t < cum) { sel = i; break; }
+            }
+            if (sel < 0) { ok = 0; break; }
+            qn[k] = (uint8_t)sel;
+            E = E - s->E[k][sel];
+        }
+        if (ok) {
+            memcpy(qn_out, qn, (size_t)n);
+            return S_OK;
+        }
+    }
+    return S_CAP;
+}
+
+/* Literal P8 (distribution reference): each mode drawn uniformly below Ec
+   (bend: i_max = floor(Ec/(k Theta) - 1/2) + 1, i = floor(r i_max); stretch:
+   i_max = highest level below Ec, i = floor(r (i_max+1)), reading A4), then
+   all modes accepted jointly if r < pw(Ec - sum E)/pw(Ec - ZPE). */
+static int sample_literal(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
+                          uint8_t* qn_out, uint64_t* trials) {
+    int n = s->n_modes;
+    if (n == 0) return S_OK;
+    if (!(Ec > s->zpe)) return S_DEGEN;
+    double denom = pw(c, Ec - s->zpe);
+    uint8_t qn[ORA_MAX_MODES];
+    for (uint32_t trial = 0; trial < c->reject_cap; ++trial) {
+        if (trials) (*trials)++;
+        double Esum = 0.0;
+        int bad = 0;
+        for (int j = 0; j < n; ++j) {
+            double u = st_u01(st);
+            int i;
+            if (s->is_bend[j]) {
+                int imax = (int)floor(Ec / s->ktheta[j] - 0.5) + 1;
+                i = (int)floor(u * (double)imax);
+            } else {
+                int imax = 0;
+                for (int l = 0; l < s->n_levels[j]; ++l)
+                    if (s->E[j][l] < Ec) imax = l;
+                i = (int)floor(u * (double)(imax + 1));
+            }
+            if (i >= s->n_levels[j]) { bad = 1; i = 0; }
+            qn[j] = (uint8_t)i;
+            Esum = Esum + s->E[j][i];
+        }
+        double u = st_u01(st);
+        if (!bad && Esum < Ec && u < pw(c, Ec - Esum) / denom) {
+            memcpy(qn_out, qn, (size_t)n);
+            return S_OK;
+        }
+    }
+    return S_CAP;
+}
+
+/* Initial quantum numbers at T_vib (P6 bends, P7 stretches with reading A7:
+   i = floor(r (i_diss+1)), accepted if r < exp(-(E_i - E_0)/(k T_vib))).  A bend
+   draw beyond the level list is redrawn (Boltzmann over the finite set). */
+static int sample_init(ora_ctx* c, const o_species* s, double T, o_stream* st, uint8_t* qn) {
+    for (int j = 0; j < s->n_modes; ++j) {
+        int done = 0;
+        for (uint32_t t = 0; t < c->reject_cap && !done; ++t) {
+            if (s->is_bend[j]) {
+                double u = st_u01(st);
+                double x = floor(-log(u) * T / s->d.theta[j - s->d.n_stretch]);
+                if (x < (double)s->n_levels[j]) { qn[j] = (uint8_t)x; done = 1; }
+            } else {
+                double u1 = st_u01(st);
+                int i = (int)floor(u1 * (double)s->n_levels[j]);
+                double u2 = st_u01(st);
+                if (u2 < exp(-(s->E[j][i] - s->E[j][0]) / (KB * T))) { qn[j] = (uint8_t)i; done = 1; }
+            }
+        }
+        if (!done) return S_CAP;
+    }
+    return S_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* VHS pair constants (Bird's VHS model, cited for xi_rel = 5 - 2 omega):
+   sigma_T(g) g = C g^(2-2 omega),
+   C = pi d^2 (2 k T_ref / m_r)^(omega - 1/2) / Gamma(5/2 - omega),
+   d and T_ref the means of the two species'.  Mean over a Maxwellian at T:
+   <sigma_T g> = 2 d^2 sqrt(2 pi k T_ref / m_r) (T/T_ref)^(1-omega). */
+typedef struct { double mr, C, mt, fp, fq; } o_pair;
+static o_pair pair_consts(const ora_ctx* c, int a, int b) {
+    const ora_species_desc* A = &c->sp[a].d;
+    const ora_species_desc* B = &c->sp[b].d;
+    o_pair p;
+    p.mr = A->mass * B->mass / (A->mass + B->mass);
+    double d = 0.5 * (A->d_ref + B->d_ref);
+    double Tr = 0.5 * (A->T_ref + B->T_ref);
+    p.C = PI_D * d * d * pow(2.0 * KB * Tr / p.mr, c->omega - 0.5) / tgamma(2.5 - c->omega);
+    p.mt = A->mass + B->mass;
+    p.fp = B->mass / p.mt; /* velocity share of particle a in the relative motion */
+    p.fq = A->mass / p.mt;
+    return p;
+}
+double ora_mean_sigma_g(ora_ctx* c, int a, int b, double T) {
+    const ora_species_desc* A = &c->sp[a].d;
+    const ora_species_desc* B = &c->sp[b].d;
+    double mr = A->mass * B->mass / (A->mass + B->mass);
+    double d = 0.5 * (A->d_ref + B->d_ref);
+    double Tr = 0.5 * (A->T_ref + B->T_ref);
+    return 2.0 * d * d * sqrt(2.0 * PI_D * KB * Tr / mr) * pow(T / Tr, 1.0 - c->omega);
+}
+
+/* ------------------------------------------------------------------ */
+ora_ctx* ora_create(int table_points, double table_span_J, uint32_t reject_cap) {
+    ora_ctx* c = (ora_ctx*)calloc(1, sizeof(ora_ctx));
+    if (!c) return NULL;
+    c->M = table_points;
+    c->span = table_span_J;
+    c->reject_cap = reject_cap;
+    c->amode = -1;
+    return c;
+}
+void ora_destroy(ora_ctx* c) {
+    if (!c) return;
+    for (int i = 0; i < c->n_species; ++i)
+        for (int k = 0; k < ORA_MAX_MODES; ++k) free(c->sp[i].H[k]);
+    for (int r = 0; r < c->n_res; ++r) {
+        o_res* R = c->res[r];
+        for (int j = 0; j < R->n_cells; ++j) free(R->cells[j].p);
+        free(R->cells);
+        free(R);
+    }
+    free(c->log);
+    free(c);
+}
+const char* ora_last_error(ora_ctx* c) { return c->msg; }
+
+int ora_add_species(ora_ctx* c, const ora_species_desc* d) {
+    if (c->n_species >= MAX_SPECIES) return ORA_EINVAL;
+    if (d->n_stretch + d->n_bend > ORA_MAX_MODES) return ORA_EINVAL;
+    int am;
+    if (d->omega == 0.75) am = 0; else if (d->omega == 0.5) am = 1; else if (d->omega == 1.0) am = 2;
+    else return ORA_EINVAL;
+    if (c->amode >= 0 && c->amode != am) return ORA_EINVAL;
+    c->amode = am;
+    c->omega = d->omega;
+    o_species* s = &c->sp[c->n_species];
+    memset(s, 0, sizeof *s);
+    s->d = *d;
+    build_levels(c, s);
+    for (int j = 0; j < s->n_modes; ++j)
+        if (s->n_levels[j] < 1) return ORA_EINVAL;
+    if (build_tables(c, s)) return ORA_ENOMEM;
+    return c->n_species++;
+}
+
+int ora_add_reaction(ora_ctx* c, const ora_reaction_desc* r) {
+    if (c->n_reactions >= MAX_REACTIONS) return ORA_EINVAL;
+    int id = c->n_reactions;
+    c->rx[id] = *r;
+    if (r->type == ORA_DISS) {
+        /* Eq. Ecoll-diss: the ZPEs of A, B and C are subtracted */
+        c->rx_zpesum[id] = c->sp[r->reactants[0]].zpe + c->sp[r->products[0]].zpe +
+                           c->sp[r->products[1]].zpe;
+    } else {
+        c->rx_zpesum[id] = 0.0;
+    }
+    return c->n_reactions++;
+}
+
+int ora_add_reservoir(ora_ctx* c, int n_cells, double Vc, double w, double dt,
+                      uint64_t seed, double T_sgmax) {
+    if (c->n_res >= MAX_RES || n_cells < 1) return ORA_EINVAL;
+    o_res* R = (o_res*)calloc(1, sizeof(o_res));
+    R->n_cells = n_cells;
+    R->Vc = Vc; R->w = w; R->dt = dt; R->seed = seed; R->T_sgmax = T_sgmax;
+    R->cells = (o_cell*)calloc((size_t)n_cells, sizeof(o_cell));
+    c->res[c->n_res] = R;
+    return c->n_res++;
+}
+
+static void cell_push(o_cell* cl, const o_part* p) {
+    if (cl->n == cl->cap) {
+        cl->cap = cl->cap ? 2 * cl->cap : 16;
+        cl->p = (o_part*)realloc(cl->p, sizeof(o_part) * (size_t)cl->cap);
+    }
+    cl->p[cl->n++] = *p;
+}
+
+/* Load: particles go to their cells in input order (a stable counting sort by
+   cell).  (sigma g)_max starts at 2 <sigma_T g>(T_sgmax), the largest over the
+   species pairs present (reading A10). */
+int ora_load(ora_ctx* c, int res, int64_t n, const double* v, const uint8_t* qn,
+             const int32_t* species, const int32_t* cell) {
+    o_res* R = c->res[res];
+    int present[MAX_SPECIES] = {0};
+    for (int64_t i = 0; i < n; ++i) {
+        if (cell[i] < 0 || cell[i] >= R->n_cells) return ORA_EINVAL;
+        if (species[i] < 0 || species[i] >= c->n_species) return ORA_EINVAL;
+        o_part p;
+        memset(&p, 0, sizeof p);
+        p.v[0] = v[3 * i]; p.v[1] = v[3 * i + 1]; p.v[2] = v[3 * i + 2];
+        p.sp = species[i];
+        memcpy(p.qn, qn + 16 * i, 16);
+        cell_push(&R->cells[cell[i]], &p);
+        present[species[i]] = 1;
+    }
+    double mx = 0.0;
+    for (int a = 0; a < c->n_species; ++a)
+        for (int b = 0; b < c->n_species; ++b)
+            if (present[a] && present[b]) {
+                double m = ora_mean_sigma_g(c, a, b, R->T_sgmax);
+                if (m > mx) mx = m;
+            }
+    for (int j = 0; j < R->n_cells; ++j) R->cells[j].sgmax = 2.0 * mx;
+    return 0;
+}
+
+int ora_init_vibration(ora_ctx* c, int res, double T_vib) {
+    o_res* R = c->res[res];
+    for (int j = 0; j < R->n_cells; ++j) {
+        o_cell* cl = &R->cells[j];
+        for (int i = 0; i < cl->n; ++i) {
+            o_stream st;
+            st_init(&st, R->seed, 0xFFFFFFFFu, (uint32_t)j, (uint32_t)i, PU_INIT);
+            const o_species* s = &c->sp[cl->p[i].sp];
+            memset(cl->p[i].qn, 0, 16);
+            if (sample_init(c, s, T_vib, &st, cl->p[i].qn) != S_OK) {
+                set_err(c, ORA_EREJECT, "init: rejection cap");
+                return ORA_EREJECT;
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+static void iso_dir(o_stream* st, double d[3]) {
+    /* Marsaglia (1972): a point uniform in the unit disk mapped onto the sphere */
+    for (;;) {
+        double x1 = 2.0 * st_u01(st) - 1.0;
+        double x2 = 2.0 * st_u01(st) - 1.0;
+        double s = x1 * x1 + x2 * x2;
+        if (s < 1.0) {
+            double r = 2.0 * sqrt(1.0 - s);
+            d[0] = x1 * r; d[1] = x2 * r; d[2] = 1.0 - 2.0 * s;
+            return;
+        }
+    }
+}
+
+typedef struct { int rx, side, mode; double ex; } o_chan;
+
+/* sample a molecule's state; keeps it on overflow/degenerate/cap and counts */
+static void relax_one(ora_ctx* c, o_res* R, const o_species* s, double Ec, o_stream* st,
+                      uint8_t* qn) {
+    uint8_t nq[ORA_MAX_MODES];
+    memcpy(nq, qn, 16);
+    R->counters[2]++;
+    int r = sample_table(c, s, Ec, st, nq, &R->counters[3]);
+    if (r == S_OK) memcpy(qn, nq, (size_t)s->n_modes);
+    else if (r == S_OVER) R->counters[4]++;
+    else if (r == S_DEGEN) R->counters[5]++;
+    else set_err(c, ORA_EREJECT, "LB sampler: rejection cap");
+}
+
+/* Product state at budget Ec (reading A13): the same LB target as relaxation */
+static void product_state(ora_ctx* c, o_res* R, const o_species* s, double Ec, o_stream* st,
+                          uint8_t* qn) {
+    memset(qn, 0, 16);
+    if (s->n_modes == 0) return;
+    R->counters[2]++;
+    int r = sample_table(c, s, Ec, st, qn, &R->counters[3]);
+    if (r != S_OK) { memset(qn, 0, 16); set_err(c, ORA_EREJECT, "product sampler failed"); }
+}
+
+static double table_top(const o_species* s, const ora_ctx* c) {
+    if (s->n_modes == 0) return INFINITY;
+    return s->base[0] + (double)c->M * s->delta;
+}
+
+/* Dissociation A + M -> B + C + M (Sec. "Dissociation reactions"), energy kept
+   exactly with well-bottom formation energies (reading A13). Returns 1 if done. */
+static int do_diss(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* M, double EvibA,
+                   uint32_t cell, uint32_t rk, o_cell* cl, o_part* created, int* n_created) {
+    const ora_reaction_desc* r = &c->rx[rx];
+    const o_species* sA = &c->sp[A->sp];
+    const o_species* sM = &c->sp[M->sp];
+    const o_species* sB = &c->sp[r->products[0]];
+    const o_species* sC = &c->sp[r->products[1]];
+    double mA = sA->d.mass, mM = sM->d.mass, mB = sB->d.mass, mC = sC->d.mass;
+    double mBC = mB + mC;
+    double mt = mBC + mM;
+    double P[3], V[3];
+    for (int i = 0; i < 3; ++i) P[i] = mA * A->v[i] + mM * M->v[i];
+    for (int i = 0; i < 3; ++i) V[i] = P[i] / mt;
+    double vA2 = A->v[0] * A->v[0] + A->v[1] * A->v[1] + A->v[2] * A->v[2];
+    double vM2 = M->v[0] * M->v[0] + M->v[1] * M->v[1] + M->v[2] * M->v[2];
+    double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    double KEin = 0.5 * mA * vA2 + 0.5 * mM * vM2;
+    double KEcm = 0.5 * mt * V2;
+    double dEf = (sB->d.E_form + sC->d.E_form) - sA->d.E_form;
+    double Eav = KEin - KEcm + EvibA - dEf;
+    if (!(Eav - sB->zpe - sC->zpe > 0.0) || Eav - sC->zpe > table_top(sB, c) ||
+        Eav - sB->zpe > table_top(sC, c))
+        return 0;
+    o_stream sa, sb, ss;
+    st_init(&sa, R->seed, R->step, cell, rk, PU_LB_A);
+    st_init(&sb, R->seed, R->step, cell, rk, PU_LB_B);
+    st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
+    uint8_t qB[16], qC[16];
+    product_state(c, R, sB, Eav - sC->zpe, &sa, qB);
+    double EvB = evib(sB, qB);
+    product_state(c, R, sC, Eav - EvB, &sb, qC);
+    double EvC = evib(sC, qC);
+    double Etr = (Eav - EvB) - EvC;
+    double x;
+    for (;;) { /* Beta(3/2,3/2) by rejection under the constant 1/2 */
+        x = st_u01(&ss);
+        double y = st_u01(&ss);
+        if (y * y * 0.25 < x * (1.0 - x)) break;
+    }
+    double E1 = x * Etr;
+    double E2 = Etr - E1;
+    double mu1 = mB * mC / mBC;
+    double mu2 = mBC * mM / mt;
+    double g1 = sqrt(2.0 * E1 / mu1);
+    double g2 = sqrt(2.0 * E2 / mu2);
+    double d1[3], d2[3];
+    iso_dir(&ss, d1);
+    iso_dir(&ss, d2);
+    double fM = mM / mt, fBC = mBC / mt, fC = mC / mBC, fB = mB / mBC;
+    double VBC[3], vM[3], vB[3], vC[3];
+    for (int i = 0; i < 3; ++i) {
+        double G2 = g2 * d2[i];
+        VBC[i] = V[i] + fM * G2;
+        vM[i] = V[i] - fBC * G2;
+    }
+    for (int i = 0; i < 3; ++i) {
+        double G1 = g1 * d1[i];
+        vB[i] = VBC[i] + fC * G1;
+        vC[i] = VBC[i] - fB * G1;
+    }
+    A->sp = r->products[0];
+    memcpy(A->qn, qB, 16);
+    for (int i = 0; i < 3; ++i) { A->v[i] = vB[i]; M->v[i] = vM[i]; }
+    o_part nc;
+    memset(&nc, 0, sizeof nc);
+    nc.sp = r->products[1];
+    memcpy(nc.qn, qC, 16);
+    for (int i = 0; i < 3; ++i) nc.v[i] = vC[i];
+    created[(*n_created)++] = nc;
+    (void)cl;
+    return 1;
+}
+
+/* Exchange A + B -> C + D (Sec. "Exchange reactions"). Returns 1 if done. */
+static int do_exch(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* B, double EvA,
+                   double EvB, uint32_t cell, uint32_t rk) {
+    const ora_reaction_desc* r = &c->rx[rx];
+    const o_species* sA = &c->sp[A->sp];
+    const o_species* sB = &c->sp[B->sp];
+    const o_species* sC = &c->sp[r->products[0]];
+    const o_species* sD = &c->sp[r->products[1]];
+    double mA = sA->d.mass, mB = sB->d.mass, mC = sC->d.mass, mD = sD->d.mass;
+    double mt = mC + mD;
+    double P[3], V[3];
+    for (int i = 0; i < 3; ++i) P[i] = mA * A->v[i] + mB * B->v[i];
+    for (int i = 0; i < 3; ++i) V[i] = P[i] / mt;
+    double vA2 = A->v[0] * A->v[0] + A->v[1] * A->v[1] + A->v[2] * A->v[2];
+    double vB2 = B->v[0] * B->v[0] + B->v[1] * B->v[1] + B->v[2] * B->v[2];
+    double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    double KEin = 0.5 * mA * vA2 + 0.5 * mB * vB2;
+    double KEcm = 0.5 * mt * V2;
+    double dEf = (sC->d.E_form + sD->d.E_form) - (sA->d.E_form + sB->d.E_form);
+    double Eav = KEin - KEcm + EvA + EvB - dEf;
+    if (!(Eav - sC->zpe - sD->zpe > 0.0) || Eav - sD->zpe > table_top(sC, c) ||
+        Eav - sC->zpe > table_top(sD, c))
+        return 0;
+    o_stream sa, sb, ss;
+    st_init(&sa, R->seed, R->step, cell, rk, PU_LB_A);
+    st_init(&sb, R->seed, R->step, cell, rk, PU_LB_B);
+    st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
+    uint8_t qC[16], qD[16];
+    product_state(c, R, sC, Eav - sD->zpe, &sa, qC);
+    double EvC = evib(sC, qC);
+    product_state(c, R, sD, Eav - EvC, &sb, qD);
+    double EvD = evib(sD, qD);
+    double Etr = (Eav - EvC) - EvD;
+    double mu = mC * mD / mt;
+    double g = sqrt(2.0 * Etr / mu);
+    double d[3];
+    iso_dir(&ss, d);
+    double fC = mD / mt, fD = mC / mt;
+    for (int i = 0; i < 3; ++i) {
+        double G = g * d[i];
+        A->v[i] = V[i] + fC * G;
+        B->v[i] = V[i] - fD * G;
+    }
+    A->sp = r->products[0];
+    B->sp = r->products[1];
+    memcpy(A->qn, qC, 16);
+    memcpy(B->qn, qD, 16);
+    return 1;
+}
+
+static void log_push(ora_ctx* c, const ora_log_rec* r) {
+    if (!c->log_on) return;
+    if (c->log_n == c->log_cap) {
+        c->log_cap = c->log_cap ? 2 * c->log_cap : 4096;
+        c->log = (ora_log_rec*)realloc(c->log, sizeof(ora_log_rec) * (size_t)c->log_cap);
+    }
+    c->log[c->log_n++] = *r;
+}
+
+/* One candidate pair: VHS acceptance (NTC), then the QK reaction test, then
+   either the reaction or LB relaxation of molecule 1, then molecule 2, then
+   isotropic VHS scattering. */
+static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, uint32_t k,
+                         o_part* P, o_part* Q, uint32_t ip, uint32_t iq, double sgmax,
+                         double* seen, o_part* created, int* n_created) {
+    uint32_t rk = (round << 24) | k;
+    R->counters[0]++;
+    const o_species* sP = &c->sp[P->sp];
+    const o_species* sQ = &c->sp[Q->sp];
+    o_pair pc = pair_consts(c, P->sp, Q->sp);
+    double gx = P->v[0] - Q->v[0], gy = P->v[1] - Q->v[1], gz = P->v[2] - Q->v[2];
+    double g2 = gx * gx + gy * gy + gz * gz;
+    double g = sqrt(g2);
+    double sg = pc.C * gpow(c, g);
+    if (sg > *seen) *seen = sg;
+    o_stream sp;
+    st_init(&sp, R->seed, R->step, cell, rk, PU_PAIR);
+    double u_acc = st_u01(&sp);
+    double u_ster = st_u01(&sp);
+    double u_sel = st_u01(&sp);
+    double u_ch = st_u01(&sp);
+    ora_log_rec lr = { R->step, cell, rk, ip, iq, -1, 0 };
+    if (!(u_acc < sg / sgmax)) { log_push(c, &lr); return; }
+    R->counters[1]++;
+    double Etr = 0.5 * pc.mr * g2;
+    double EvP = evib(sP, P->qn);
+    double EvQ = evib(sQ, Q->qn);
+
+    /* QK reaction test: channel list in fixed order (reading A21) */
+    o_chan ch[MAX_CHANNELS];
+    int nch = 0;
+    for (int side = 0; side < 2; ++side) {
+        const o_part* A = side ? Q : P;
+        const o_species* sA = side ? sQ : sP;
+        double EvA = side ? EvQ : EvP;
+        for (int r = 0; r < c->n_reactions; ++r) {
+            const ora_reaction_desc* rx = &c->rx[r];
+            if (rx->type != ORA_DISS || rx->reactants[0] != A->sp) continue;
+            for (int j = 0; j < sA->d.n_stretch; ++j) {
+                if (!((rx->diss_mode_mask >> j) & 1u)) continue;
+                /* Eq. Ecoll-diss */
+                double Ecoll = Etr + EvA - c->rx_zpesum[r] + sA->E[j][0];
+                double Eex = Ecoll - sA->d.De[j];
+                if (Eex > 0.0 && nch < MAX_CHANNELS) {
+                    o_chan cc = { r, side, j, Eex };
+                    ch[nch++] = cc;
+                }
+            }
+        }
+    }
+    for (int r = 0; r < c->n_reactions; ++r) {
+        const ora_reaction_desc* rx = &c->rx[r];
+        if (rx->type != ORA_EXCH) continue;
+        int side;
+        if (P->sp == rx->reactants[0] && Q->sp == rx->reactants[1]) side = 0;
+        else if (Q->sp == rx->reactants[0] && P->sp == rx->reactants[1]) side = 1;
+        else continue;
+        if (!(u_ster < rx->steric)) continue;
+        const o_part* A = side ? Q : P;
+        const o_species* sA = side ? sQ : sP;
+        /* Eq. Ecoll-exch (reading A12: level energies include the ZPE) */
+        double s = 0.0;
+        if (rx->alpha_mode == ORA_ALPHA_ONE_RANDOM_STRETCH) {
+            int js = (int)floor(u_sel * (double)sA->d.n_stretch);
+            s = sA->E[js][A->qn[js]];
+        } else {
+            for (int j = 0; j < sA->n_modes; ++j) s = s + rx->alpha[j] * sA->E[j][A->qn[j]];
+        }
+        double Ecoll = Etr + s;
+        double Eex = Ecoll - rx->Ea;
+        if (Eex > 0.0 && nch < MAX_CHANNELS) {
+            o_chan cc = { r, side, 0, Eex };
+            ch[nch++] = cc;
+        }
+    }
+    if (nch > 0) {
+        int pick = 0;
+        if (nch > 1) { /* "Competing reactions": weighted by E_excess */
+            double tot = 0.0;
+            for (int i = 0; i < nch; ++i) tot = tot + ch[i].ex;
+            double t = u_ch * tot;
+            double pre = 0.0;
+            pick = nch - 1;
+            for (int i = 0; i < nch; ++i) {
+                pre = pre + ch[i].ex;
+                if (t < pre) { pick = i; break; }
+            }
+        }
+        const o_chan* cc = &ch[pick];
+        int done;
+        if (c->rx[cc->rx].type == ORA_DISS) {
+            o_part* A = cc->side ? Q : P;
+            o_part* M = cc->side ? P : Q;
+            done = do_diss(c, R, cc->rx, A, M, cc->side ? EvQ : EvP, cell, rk, NULL, created,
+                           n_created);
+            lr.aux = (uint32_t)cc->mode + (cc->side ? 16u : 0u);
+        } else {
+            o_part* A = cc->side ? Q : P;
+            o_part* B = cc->side ? P : Q;
+            done = do_exch(c, R, cc->rx, A, B, cc->side ? EvQ : EvP, cc->side ? EvP : EvQ,
+                           cell, rk);
+            lr.aux = (uint32_t)cc->side;
+        }
+        if (done) {
+            R->counters[8 + cc->rx]++;
+            lr.event = 1 + cc->rx;
+            log_push(c, &lr);
+            return;
+        }
+        R->counters[6]++;
+        lr.aux = 0;
+    }
+
+    /* relaxation (HCAO LB): molecule 1, then molecule 2 with the updated E_rel */
+    double E = Etr;
+    if (sP->n_modes > 0) {
+        o_stream s1;
+        st_init(&s1, R->seed, R->step, cell, rk, PU_LB_A);
+        double Ec = E + EvP;
+        relax_one(c, R, sP, Ec, &s1, P->qn);
+        E = Ec - evib(sP, P->qn);
+    }
+    if (sQ->n_modes > 0) {
+        o_stream s2;
+        st_init(&s2, R->seed, R->step, cell, rk, PU_LB_B);
+        double Ec = E + EvQ;
+        relax_one(c, R, sQ, Ec, &s2, Q->qn);
+        E = Ec - evib(sQ, Q->qn);
+    }
+    /* isotropic VHS scattering; centre-of-mass velocity kept */
+    o_stream ss;
+    st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
+    double gn = sqrt(2.0 * E / pc.mr);
+    double d[3];
+    iso_dir(&ss, d);
+    double mp = sP->d.mass, mq = sQ->d.mass;
+    double V[3];
+    for (int i = 0; i < 3; ++i) V[i] = (mp * P->v[i] + mq * Q->v[i]) / pc.mt;
+    for (int i = 0; i < 3; ++i) {
+        double G = gn * d[i];
+        P->v[i] = V[i] + pc.fp * G;
+        Q->v[i] = V[i] - pc.fq * G;
+    }
+    lr.event = 0;
+    log_push(c, &lr);
+}
+
+static int step_reservoir(ora_ctx* c, o_res* R) {
+    for (int ci = 0; ci < R->n_cells; ++ci) {
+        o_cell* cl = &R->cells[ci];
+        int N = cl->n;
+        if (N < 2) continue;
+        /* NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically */
+        double x = 0.5 * (double)N * (double)(N - 1) * R->w * cl->sgmax * R->dt / R->Vc;
+        double fl = floor(x);
+        int64_t nsel = (int64_t)fl;
+        o_stream sn;
+        st_init(&sn, R->seed, R->step, (uint32_t)ci, 0u, PU_NSEL);
+        if (st_u01(&sn) < x - fl) nsel++;
+        int64_t P = N / 2;
+        int64_t rounds = (nsel + P - 1) / P;
+        if (rounds > 255) { set_err(c, ORA_EINVAL, "more than 255 NTC rounds"); return ORA_EINVAL; }
+        double seen = 0.0;
+        o_part* created = (o_part*)malloc(sizeof(o_part) * (size_t)(nsel + 1));
+        int n_created = 0;
+        for (int64_t r = 0; r < rounds; ++r) {
+            o_stream sf;
+            st_init(&sf, R->seed, R->step, (uint32_t)ci, (uint32_t)r << 24, PU_FEISTEL);
+            uint32_t key[4];
+            for (int i = 0; i < 4; ++i) key[i] = st_word(&sf);
+            int64_t kmax = nsel - r * P;
+            if (kmax > P) kmax = P;
+            for (int64_t k = 0; k < kmax; ++k) {
+                uint32_t ip = ora_feistel((uint32_t)(2 * k), (uint32_t)N, key);
+                uint32_t iq = ora_feistel((uint32_t)(2 * k + 1), (uint32_t)N, key);
+                process_pair(c, R, (uint32_t)ci, (uint32_t)r, (uint32_t)k, &cl->p[ip], &cl->p[iq],
+                             ip, iq, cl->sgmax, &seen, created, &n_created);
+            }
+        }
+        for (int i = 0; i < n_created; ++i) cell_push(cl, &created[i]);
+        free(created);
+        if (seen > cl->sgmax) cl->sgmax = seen;
+    }
+    R->step++;
+    R->counters[7]++;
+    return 0;
+}
+
+int ora_step(ora_ctx* c, int n_steps) {
+    for (int s = 0; s < n_steps; ++s) {
+        c->log_n = 0; /* the log keeps the last step only */
+        for (int r = 0; r < c->n_res; ++r) {
+            int e = step_reservoir(c, c->res[r]);
+            if (e) return e;
+        }
+        if (c->error) return c->error;
+    }
+    return 0;
+}
+
+int ora_set_log(ora_ctx* c, int on) { c->log_on = on; c->log_n = 0; return 0; }
+int64_t ora_log_count(ora_ctx* c) { return c->log_n; }
+int ora_read_log(ora_ctx* c, ora_log_rec* out, int64_t max) {
+    int64_t n = c->log_n < max ? c->log_n : max;
+    memcpy(out, c->log, sizeof(ora_log_rec) * (size_t)n);
+    return 0;
+}
+
+int64_t ora_count(ora_ctx* c, int res) {
+    o_res* R = c->res[res];
+    int64_t n = 0;
+    for (int j = 0; j < R->n_cells; ++j) n += R->cells[j].n;
+    return n;
+}
+
+int ora_read_particles(ora_ctx* c, int res, double* v, uint8_t* qn, int32_t* species,
+                       int32_t* cell) {
+    o_res* R = c->res[res];
+    int64_t o = 0;
+    for (int j = 0; j < R->n_cells; ++j) {
+        o_cell* cl = &R->cells[j];
+        for (int i = 0; i < cl->n; ++i, ++o) {
+            for (int d = 0; d < 3; ++d) v[3 * o + d] = cl->p[i].v[d];
+            memcpy(qn + 16 * o, cl->p[i].qn, 16);
+            species[o] = cl->p[i].sp;
+            cell[o] = j;
+        }
+    }
+    return 0;
+}
+
+int ora_read_cell_sgmax(ora_ctx* c, int res, double* out) {
+    o_res* R = c->res[res];
+    for (int j = 0; j < R->n_cells; ++j) out[j] = R->cells[j].sgmax;
+    return 0;
+}
+
+int ora_read_counters(ora_ctx* c, int res, uint64_t* out, int max) {
+    o_res* R = c->res[res];
+    int n = 8 + c->n_reactions;
+    if (n > max) n = max;
+    memcpy(out, R->counters, sizeof(uint64_t) * (size_t)n);
+    return n;
+}
+
+int ora_n_levels(ora_ctx* c, int sp, int mode) { return c->sp[sp].n_levels[mode]; }
+double ora_level_energy(ora_ctx* c, int sp, int mode, int level) { return c->sp[sp].E[mode][level]; }
+double ora_table_value(ora_ctx* c, int sp, int k, int m) { return c->sp[sp].H[k][m]; }
+int ora_table_entries(ora_ctx* c, int sp) { return c->sp[sp].MT; }
+double ora_zpe(ora_ctx* c, int sp) { return c->sp[sp].zpe; }
+
+int ora_sample_lb(ora_ctx* c, int sp, double Ec, uint64_t seed, int64_t n, int method,
+                  uint8_t* out_qn, uint64_t* trials) {
+    const o_species* s = &c->sp[sp];
+    uint64_t tr = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        o_stream st;
+        st_init(&st, seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, PU_TEST);
+        uint8_t* q = out_qn + 16 * i;
+        memset(q, 0, 16);
+        int r = method == ORA_SAMPLER_LITERAL ? sample_literal(c, s, Ec, &st, q, &tr)
+                                              : sample_table(c, s, Ec, &st, q, &tr);
+        if (r != S_OK) return r == S_CAP ? ORA_EREJECT : ORA_EINVAL;
+    }
+    if (trials) *trials = tr;
+    return 0;
+}
+
+int ora_sample_init(ora_ctx* c, int sp, double T, uint64_t seed, int64_t n, uint8_t* out_qn) {
+    const o_species* s = &c->sp[sp];
+    for (int64_t i = 0; i < n; ++i) {
+        o_stream st;
+        st_init(&st, seed, (uint32_t)i, (uint32_t)(i >> 32), 1u, PU_TEST);
+        uint8_t* q = out_qn + 16 * i;
+        memset(q, 0, 16);
+        if (sample_init(c, s, T, &st, q) != S_OK) return ORA_EREJECT;
+    }
+    return 0;
+}
+
+/* P5: T_vib of species sp as the root of <E_vib>(T) = mean vibrational energy
+   above the ZPE (bends: harmonic closed form; stretches: Boltzmann sum over the
+   Morse levels), by bisection. */
+static double mean_evib_T(const o_species* s, double T) {
+    double e = 0.0;
+    for (int j = 0; j < s->n_modes; ++j) {
+        if (s->is_bend[j]) {
+            double th = s->d.theta[j - s->d.n_stretch];
+            e += KB * th / (exp(th / T) - 1.0);
+        } else {
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < s->n_levels[j]; ++i) {
+                double de = s->E[j][i] - s->E[j][0];
+                double b = exp(-de / (KB * T));
+                num += de * b;
+                den += b;
+            }
+            e += num / den;
+        }
+    }
+    return e;
+}
+double ora_tvib(ora_ctx* c, int res, int sp) {
+    o_res* R = c->res[res];
+    const o_species* s = &c->sp[sp];
+    double sum = 0.0;
+    int64_t n = 0;
+    for (int j = 0; j < R->n_cells; ++j)
+        for (int i = 0; i < R->cells[j].n; ++i)
+            if (R->cells[j].p[i].sp == sp) {
+                sum += evib(s, R->cells[j].p[i].qn) - s->zpe;
+                n++;
+            }
+    if (n == 0 || s->n_modes == 0) return 0.0;
+    double target = sum / (double)n;
+    if (!(target > 0.0)) return 0.0;
+    double lo = 1.0, hi = 1.0e6;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mean_evib_T(s, mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}

@@ -1,0 +1,116 @@
+/*
+ * hcao_oracle.h -- the oracle: a plain, slow, single-threaded FP64 CPU
+ * implementation of the DSMC collision phase with the HCAO vibrational model
+ * and QK-type chemistry of "A harmonically-coupled-anharmonic-oscillator
+ * approach for polyatomic chemistry modeling in DSMC".
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it. The product path (the CUDA
+ * library) shares no code, header, table or constant generator with it.
+ *
+ * Paper sections followed:
+ *   Eq. energy-SHO, the Theta form of the harmonic levels (Sec. "The polyatomic
+ *   HCAO model")                                   -> harmonic bend levels
+ *   Eq. energy-AHO                                  -> Morse stretch levels
+ *   Sec. "Implementation of the polyatomic HCAO model": initial bend and
+ *   stretch quantum numbers, Eq. accept-quant, the joint LB acceptance of all
+ *   modes (the relaxation step)                     -> ora_init_vibration, samplers
+ *   Sec. "Polyatomic QK reaction modeling", Eq. Ecoll-diss, Eq. Ecoll-exch,
+ *   "Competing reactions"                           -> reaction test / execution
+ *   Sec. "Verification": single reservoir cell, closed system, no rotation.
+ * Readings where the paper is silent are stated beside each function.
+ */
+#ifndef HCAO_ORACLE_H
+#define HCAO_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORA_MAX_MODES 16
+#define ORA_MAX_LEVELS 256
+
+enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ENOMEM = -2, ORA_EREJECT = -4, ORA_ELEVEL = -5 };
+enum { ORA_DISS = 1, ORA_EXCH = 2 };
+enum { ORA_ALPHA_PER_MODE = 0, ORA_ALPHA_ONE_RANDOM_STRETCH = 1 };
+enum { ORA_SAMPLER_TABLE = 0, ORA_SAMPLER_LITERAL = 1 };
+
+typedef struct {
+    double mass;     /* kg */
+    double d_ref;    /* m, VHS reference diameter */
+    double T_ref;    /* K */
+    double omega;    /* VHS viscosity index (0.5, 0.75 or 1.0) */
+    double E_form;   /* J, formation energy measured from the well bottom */
+    int n_stretch;   /* Morse local stretches, modes 0..n_stretch-1 */
+    double we[ORA_MAX_MODES];    /* m^-1 */
+    double wexe[ORA_MAX_MODES];  /* m^-1 (omega_e * chi_e) */
+    double De[ORA_MAX_MODES];    /* J, from the well bottom */
+    int n_bend;      /* harmonic bends, modes n_stretch..n_stretch+n_bend-1 */
+    double theta[ORA_MAX_MODES]; /* K */
+} ora_species_desc;
+
+typedef struct {
+    int type;             /* ORA_DISS: A + M -> B + C + M ; ORA_EXCH: A + B -> C + D */
+    int reactants[2];     /* DISS: {A, -1}; EXCH: {A, B} */
+    int products[2];      /* DISS: {B, C};  EXCH: {C, D} */
+    uint32_t diss_mode_mask; /* DISS: stretch modes of A whose breaking gives B + C */
+    double Ea;            /* EXCH: activation energy, J */
+    double steric;        /* EXCH: steric factor in [0,1] */
+    int alpha_mode;       /* EXCH: ORA_ALPHA_PER_MODE or ORA_ALPHA_ONE_RANDOM_STRETCH */
+    double alpha[ORA_MAX_MODES];
+} ora_reaction_desc;
+
+typedef struct {
+    uint32_t step, cell, round_k, p, q;
+    int32_t event;        /* -1: rejected candidate, 0: relaxed, 1+r: reaction r */
+    uint32_t aux;         /* DISS: broken stretch mode (+16 if partner q); EXCH: 0/1 A is p/q */
+} ora_log_rec;
+
+typedef struct ora_ctx ora_ctx;
+
+ora_ctx* ora_create(int table_points, double table_span_J, uint32_t reject_cap);
+void     ora_destroy(ora_ctx*);
+int      ora_add_species(ora_ctx*, const ora_species_desc*);
+int      ora_add_reaction(ora_ctx*, const ora_reaction_desc*);
+int      ora_add_reservoir(ora_ctx*, int n_cells, double cell_volume, double weight,
+                           double dt, uint64_t seed, double T_sgmax);
+int      ora_load(ora_ctx*, int res, int64_t n, const double* v, const uint8_t* qn,
+                  const int32_t* species, const int32_t* cell);
+int      ora_init_vibration(ora_ctx*, int res, double T_vib);
+int      ora_step(ora_ctx*, int n_steps);
+int      ora_set_log(ora_ctx*, int enable);
+int64_t  ora_log_count(ora_ctx*);
+int      ora_read_log(ora_ctx*, ora_log_rec* out, int64_t max);
+int64_t  ora_count(ora_ctx*, int res);
+int      ora_read_particles(ora_ctx*, int res, double* v, uint8_t* qn, int32_t* species,
+                            int32_t* cell);
+int      ora_read_cell_sgmax(ora_ctx*, int res, double* out);
+/* counters: [0] candidate pairs, [1] accepted collisions, [2] LB samples,
+   [3] LB trials, [4] table overflows, [5] degenerate (A6) samples,
+   [6] not-executed reactions, [7] steps, [8..8+n_reactions) reaction events */
+int      ora_read_counters(ora_ctx*, int res, uint64_t* out, int max);
+int      ora_n_levels(ora_ctx*, int sp, int mode);
+double   ora_level_energy(ora_ctx*, int sp, int mode, int level);
+double   ora_table_value(ora_ctx*, int sp, int k, int m);
+int      ora_table_entries(ora_ctx*, int sp);
+double   ora_zpe(ora_ctx*, int sp);
+/* draws n samples of the post-collision state of species sp at collision
+   energy Ec with the chosen sampler; a Philox stream keyed by seed */
+int      ora_sample_lb(ora_ctx*, int sp, double Ec, uint64_t seed, int64_t n, int method,
+                       uint8_t* out_qn, uint64_t* trials);
+/* draws n initial states of species sp at T_vib (P6/P7) */
+int      ora_sample_init(ora_ctx*, int sp, double T_vib, uint64_t seed, int64_t n,
+                         uint8_t* out_qn);
+/* Feistel permutation of [0,N) used for the disjoint NTC pairs */
+uint32_t ora_feistel(uint32_t x, uint32_t N, const uint32_t key[4]);
+void     ora_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* T_vib of one species in a reservoir by the zero-point search (P5) */
+double   ora_tvib(ora_ctx*, int res, int sp);
+double   ora_mean_sigma_g(ora_ctx*, int sp, int sq, double T);
+const char* ora_last_error(ora_ctx*);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

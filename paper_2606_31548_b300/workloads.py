@@ -1,0 +1,188 @@
+"""Seeded synthetic workloads: species presets and initial particle arrays.
+
+This module holds input data only -- species parameters, reservoir sizes and
+seeded generators of initial velocities, species and cell assignments.  It does
+none of the method's arithmetic (no level energies, no sampling of quantum
+numbers, no collision physics) and serves both the CUDA library and the
+oracle.  Unit conversions (cm^-1, eV, u) are the only computations.
+
+Species presets follow the synthetic workloads built on the paper's
+verification setups (Sec. "Verification": single reservoir cell of
+V = 4.64e-6 m^3, n = 1e23 m^-3 for the water case, 1e22 m^-3 per species for
+the CH4 + H exchange case), with the readings listed beside each preset.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional
+
+import numpy as np
+
+EV = 1.602176634e-19          # J
+AMU = 1.66053906660e-27       # kg
+CM1 = 100.0                   # cm^-1 -> m^-1
+C2_RAD = 1.438776877e-2       # m K, second radiation constant hc/k (cm^-1 -> K)
+KB = 1.380649e-23             # J/K (used only for Maxwellian input velocities)
+
+
+@dataclasses.dataclass
+class Species:
+    name: str
+    mass: float                     # kg
+    d_ref: float                    # m
+    T_ref: float = 273.0            # K
+    omega: float = 0.75
+    E_form: float = 0.0             # J, from the well bottom
+    we: List[float] = dataclasses.field(default_factory=list)     # m^-1 per stretch
+    wexe: List[float] = dataclasses.field(default_factory=list)   # m^-1 per stretch
+    De: List[float] = dataclasses.field(default_factory=list)     # J per stretch
+    theta: List[float] = dataclasses.field(default_factory=list)  # K per bend
+    coupling_m1: float = 0.0        # stretch-bend coupling, stored, unused (reading A1)
+
+    @property
+    def n_modes(self) -> int:
+        return len(self.we) + len(self.theta)
+
+
+@dataclasses.dataclass
+class Reaction:
+    type: str                       # "diss" or "exch"
+    reactants: List[int]
+    products: List[int]
+    diss_mode_mask: int = 0
+    Ea: float = 0.0
+    steric: float = 1.0
+    alpha_mode: str = "per_mode"    # or "one_random_stretch" (reading A18)
+    alpha: List[float] = dataclasses.field(default_factory=list)
+
+
+def triatomic() -> Species:
+    """Synthetic triatomic: 2 Morse stretches (we 3800, wexe 80 cm^-1, De 5.1 eV),
+    1 bend at 1600 cm^-1, coupling -50 cm^-1 (stored only), 18.015 u."""
+    return Species("triatomic", 18.015 * AMU, 4.0e-10,
+                   we=[3800 * CM1] * 2, wexe=[80 * CM1] * 2, De=[5.1 * EV] * 2,
+                   theta=[1600 * CM1 * C2_RAD], coupling_m1=-50 * CM1)
+
+
+def ch4_like() -> Species:
+    """CH4-like: 4 Morse C-H stretches (we 3100, wexe 60 cm^-1, De 4.5 eV) and
+    bends 3 x 1300 + 2 x 1550 cm^-1 (reading A3), 16.043 u."""
+    return Species("CH4", 16.043 * AMU, 4.0e-10,
+                   we=[3100 * CM1] * 4, wexe=[60 * CM1] * 4, De=[4.5 * EV] * 4,
+                   theta=[1300 * CM1 * C2_RAD] * 3 + [1550 * CM1 * C2_RAD] * 2)
+
+
+def ch3_like() -> Species:
+    """CH3 product: the paper's CH3 bends (872.1 K x1, 2016.2 K x2) with the C-H
+    stretch parameters of ch4_like; E_form = +4.5 eV so that breaking one C-H
+    bond of CH4 costs exactly its De (reading A13)."""
+    return Species("CH3", 15.035 * AMU, 4.0e-10, E_form=4.5 * EV,
+                   we=[3100 * CM1] * 3, wexe=[60 * CM1] * 3, De=[4.5 * EV] * 3,
+                   theta=[872.1, 2016.2, 2016.2])
+
+
+def h_atom() -> Species:
+    return Species("H", 1.008 * AMU, 2.5e-10)
+
+
+def h2() -> Species:
+    """H2 with the paper's Morse constants (we = 439524 m^-1, chi_e = 0.0287);
+    De = 4.7469 eV and E_form = -De (two H atoms bind)."""
+    we = 439524.0
+    De = 4.746866797 * EV
+    return Species("H2", 2.016 * AMU, 2.9e-10, E_form=-De, we=[we], wexe=[0.0287 * we], De=[De])
+
+
+def maxwellian(rng: np.random.Generator, n: int, mass: np.ndarray, T: float) -> np.ndarray:
+    """Velocities (n,3) from a Maxwellian at T: each component N(0, kT/m)."""
+    sig = np.sqrt(KB * T / mass)
+    return rng.standard_normal((n, 3)) * sig[:, None]
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    species: List[Species]
+    reactions: List[Reaction]
+    n_cells: int
+    cell_volume: float
+    weight: float
+    dt: float
+    T_tr0: float
+    T_vib0: float
+    seed: int
+    v: np.ndarray
+    species_idx: np.ndarray
+    cell: np.ndarray
+    steps: int
+
+    @property
+    def n(self) -> int:
+        return int(self.v.shape[0])
+
+    def qn0(self) -> np.ndarray:
+        return np.zeros((self.n, 16), dtype=np.uint8)
+
+
+def _build(name, species, reactions, n_cells, per_cell_counts, fractions, V_total, n_density,
+           dt, T_tr0, T_vib0, seed, steps, shuffle=True) -> Workload:
+    rng = np.random.default_rng(seed)
+    n = int(np.sum(per_cell_counts))
+    cell = np.repeat(np.arange(n_cells, dtype=np.int32), per_cell_counts)
+    sp = rng.choice(len(fractions), size=n, p=np.asarray(fractions) / np.sum(fractions)).astype(np.int32) \
+        if len(fractions) > 1 else np.zeros(n, dtype=np.int32)
+    if shuffle:
+        perm = rng.permutation(n)
+        cell = cell[perm]
+    mass = np.array([species[i].mass for i in range(len(species))])[sp]
+    v = maxwellian(rng, n, mass, T_tr0)
+    weight = n_density * V_total / n
+    return Workload(name, species, reactions, n_cells, V_total / n_cells, weight, dt, T_tr0, T_vib0,
+                    seed, np.ascontiguousarray(v, dtype=np.float64), sp.astype(np.int32),
+                    cell.astype(np.int32), steps)
+
+
+def relaxation_triatomic(n_particles: int = 20000, n_cells: int = 1, steps: int = 1000,
+                         seed: int = 0x48434131) -> Workload:
+    """0D adiabatic reservoir of the synthetic triatomic: T_tr0 = 10000 K,
+    T_vib0 = 300 K, no chemistry; n = 1e23 m^-3 in V = 4.64e-6 m^3;
+    dt = 2.0e-9 s (0.2 / nu(T_tr0) of the VHS closed form, reading A19)."""
+    counts = np.full(n_cells, n_particles // n_cells)
+    counts[: n_particles % n_cells] += 1
+    return _build("relaxation_triatomic", [triatomic()], [], n_cells, counts, [1.0], 4.64e-6,
+                  1e23, 2.0e-9, 10000.0, 300.0, seed, steps)
+
+
+def ch4_heat_bath(n_cells: int = 4096, per_cell: int = 500, steps: int = 500,
+                  seed: int = 0x48434132, T0: float = 15000.0, dissociation: bool = True) -> Workload:
+    """0D CH4-like heat bath at 15000 K (T_tr0 = T_vib0, reading A20),
+    dissociation CH4 + M -> CH3 + H + M on all four stretches; n = 1e23 m^-3 in
+    V = 4.64e-6 m^3 split into n_cells cells; dt = 1.7e-9 s (0.2 / nu(T0))."""
+    sp = [ch4_like(), ch3_like(), h_atom()]
+    rx = [Reaction("diss", [0], [1, 2], diss_mode_mask=0xF)] if dissociation else []
+    counts = np.full(n_cells, per_cell)
+    return _build("ch4_heat_bath", sp, rx, n_cells, counts, [1.0], 4.64e-6, 1e23, 1.7e-9,
+                  T0, T0, seed, steps)
+
+
+def ch4_h_exchange(n_cells: int = 16384, per_cell: int = 1200, steps: int = 2000,
+                   seed: int = 0x48434133, T0: float = 5000.0) -> Workload:
+    """CH4 + H -> CH3 + H2, 50/50 CH4/H, Ea = 1.03e-19 J, steric factor 1,
+    alpha = 1 on one stretch chosen per collision (reading A18); n = 1e22 m^-3
+    per species (2e22 total) in V = 4.64e-6 m^3; dt = 0.2/nu(T0) of the
+    mixture, tabulated for 2000..6000 K."""
+    dts = {2000.0: 8.2e-9, 3000.0: 7.4e-9, 4000.0: 6.9e-9, 5000.0: 6.5e-9, 6000.0: 6.2e-9}
+    dt = dts.get(float(T0), 6.5e-9)
+    sp = [ch4_like(), h_atom(), ch3_like(), h2()]
+    rx = [Reaction("exch", [0, 1], [2, 3], Ea=1.03e-19, steric=1.0, alpha_mode="one_random_stretch")]
+    counts = np.full(n_cells, per_cell)
+    return _build("ch4_h_exchange", sp, rx, n_cells, counts, [0.5, 0.5], 4.64e-6, 2e22, dt,
+                  T0, T0, seed, steps)
+
+
+def random_levels(rng: np.random.Generator, n: int, n_levels: List[int], n_modes: int) -> np.ndarray:
+    """Uniformly random valid quantum numbers for load-path tests (no physics)."""
+    q = np.zeros((n, 16), dtype=np.uint8)
+    for j in range(n_modes):
+        q[:, j] = rng.integers(0, n_levels[j], size=n)
+    return q
