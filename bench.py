@@ -1,0 +1,315 @@
+"""Benchmark: the DSMC collision phase (HCAO LB relaxation + QK dissociation)
+on the 4096-cell x 500-particle CH4-like heat bath at 15000 K (2.05M
+particles), one step = one collision phase over all cells.
+
+Prints one JSON line.  `value` = particle-steps/s over the timed steps, device
+time from CUDA events on the library's stream, L2 flushed (a 256 MiB write)
+before every timed step.  `e2e` = the same metric through the C ABI with host
+buffers: every step loads the state from pinned host memory, steps, and reads
+the moments back.  --impl reference times the oracle (CPU) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2606_31548_b300 import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+WORKLOAD = "ch4_heat_bath_4096x500_15000K_dissociation"
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def _max_over_ranks(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def _sum_over_ranks(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+    return x
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.dev = device
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(budget_s: float = 12.0, cells: int = 48):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    `cells` of the 4096 cells (500 particles each), stepped until ~budget_s."""
+    import oracle
+    w = W.ch4_heat_bath()
+    pick = np.arange(cells) * (w.n_cells // cells)
+    sel = np.isin(w.cell, pick)
+    o = oracle.Oracle()
+    for s in w.species:
+        o.add_species(s)
+    for r in w.reactions:
+        o.add_reaction(r)
+    o.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    o.load(0, w.v[sel], w.qn0()[sel], w.species_idx[sel], w.cell[sel])
+    o.init_vibration(0, w.T_vib0)
+    psteps = 0
+    steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and steps < 2000:
+        n = o.count(0)
+        o.step(1)
+        psteps += n
+        steps += 1
+    dt = time.perf_counter() - t0
+    acc = int(o.read_counters(0)[1])
+    return {"value": psteps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "collisions_per_s": acc / dt,
+            "sample": f"{cells} of the 4096 cells ({int(sel.sum())} particles), {steps} steps, "
+                      f"single-threaded FP64 C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(budget_s=max(3.0, min(20.0, 2.0 * args.steps)))
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": cb["value"],
+            "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": 4096, "particles_per_cell": 500,
+                       "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2606_31548_b300 import hcao
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    prec = hcao.FP32 if args.precision == "fp32" else hcao.FP64
+    w = W.ch4_heat_bath(seed=0x48434132 + rank)
+    ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.step(1)
+    ctx.sync()
+    c0 = ctx.read_counters(0)
+    launches0 = ctx.kernel_launches()
+    ctx.set_profiling(True)
+    torch.cuda.synchronize()
+    _barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    psteps = 0
+    with Clocks(local) as clk:
+        t_wall0 = time.perf_counter()
+        for i in range(args.steps):
+            n = ctx.count(0)  # particles entering this step (host sync, outside the events)
+            psteps += n
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.step(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    _barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.sync()
+    c1 = ctx.read_counters(0)
+    launches = ctx.kernel_launches() - launches0
+    kms, kn = ctx.read_profile()
+    ctx.set_profiling(False)
+    collisions = float(c1[1] - c0[1])
+    t = _max_over_ranks(ms / 1e3)
+    tot_psteps = _sum_over_ranks(float(psteps))
+    tot_coll = _sum_over_ranks(collisions)
+
+    # roofline of the dominant kernel (collide): algorithmic bytes per
+    # particle-step = 2 S, S = 12 B velocity + 9 B quantum numbers + 1 B species
+    # + 4 B cell (FP32) = 26 B; FP64 adds 12 B
+    S = 26.0 if prec == hcao.FP32 else 38.0
+    collide_s = kms[1] / 1e3
+    peak, peak_kind = _peaks()
+    achieved = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_kind": peak_kind, "kernel": "k_collide",
+            "kernel_ms_per_step": {"setup": kms[0] / args.steps, "collide": kms[1] / args.steps,
+                                   "finish": kms[2] / args.steps}}
+
+    # e2e through the C ABI with host buffers (pinned): load + step + moments
+    e2e = None
+    if args.e2e_steps > 0:
+        v_h = torch.from_numpy(w.v).pin_memory()
+        q_h = torch.from_numpy(w.qn0()).pin_memory()
+        s_h = torch.from_numpy(w.species_idx).pin_memory()
+        c_h = torch.from_numpy(w.cell).pin_memory()
+        ectx = hcao.Context(precision=prec, stream=stream.cuda_stream, device=local)
+        ectx.set_species(w.species)
+        ectx.set_reactions(w.reactions)
+        rid = ectx.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        L = ectx.L
+        import ctypes as C
+        mom = hcao.Moments()
+
+        def one():
+            ectx._chk(L.hcao_load_particles(ectx.h, rid, w.n, C.c_void_p(v_h.data_ptr()),
+                                            C.c_void_p(q_h.data_ptr()), C.c_void_p(s_h.data_ptr()),
+                                            C.c_void_p(c_h.data_ptr())))
+            ectx._chk(L.hcao_step(ectx.h, 1))
+            ectx._chk(L.hcao_read_moments(ectx.h, rid, C.byref(mom)))
+
+        one()
+        torch.cuda.synchronize()
+        _barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            one()
+        torch.cuda.synchronize()
+        te = _max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": _sum_over_ranks(float(w.n * args.e2e_steps)) / te, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(w.n * (24 + 16 + 4 + 4)),
+               "d2h_bytes_per_step": int(C.sizeof(hcao.Moments)),
+               "note": "per step: hcao_load_particles from pinned host memory (state of the "
+                       "workload), hcao_step(1), hcao_read_moments"}
+        ectx.close()
+
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": "particle-steps/s", "value": tot_psteps / t, "unit": "particle-steps/s",
+            "collisions_per_s": tot_coll / t,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == hcao.FP32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": w.n_cells, "particles_per_cell": 500,
+                       "particles": w.n, "T0_K": w.T_tr0, "precision": args.precision,
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clocks, "wall_s_timed_loop": t_wall,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * hcao.h -- C ABI of libhcao: the DSMC collision phase with the HCAO
+ * vibrational model and QK-type chemistry on one NVIDIA B300 (sm_103a).
+ *
+ * Paper: "A harmonically-coupled-anharmonic-oscillator approach for polyatomic
+ * chemistry modeling in DSMC" (Lauterbach, Tuttas, Pfeiffer).
+ *
+ * Conventions (every entry point):
+ *   - Returns hcao_status; HCAO_OK (0) on success, a negative code otherwise.
+ *     hcao_last_error() gives a one-line description of the last failure.
+ *     No C++ exception crosses this boundary.
+ *   - SI units throughout: J, K, m, kg, s.
+ *   - Pointers named host_* or documented as "host" are host memory owned by the
+ *     caller; the library copies what it needs before returning (or, for reads,
+ *     has filled them when the call returns).  Pointers documented as "device"
+ *     are device memory owned by the caller.
+ *   - The context owns all of its device memory (cudaMallocAsync on its
+ *     stream) and frees it in hcao_destroy.
+ *   - All work is issued on the context's stream (hcao_config.cuda_stream,
+ *     borrowed, may be PyTorch's current stream; NULL = the legacy default
+ *     stream).  Calls on one context are not thread-safe.
+ *   - Device-side failures (rejection-loop cap, capacity, round limit) set a
+ *     sticky error word on the device; hcao_sync() and every read call return
+ *     it as a status.
+ */
+#ifndef HCAO_H
+#define HCAO_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HCAO_OK = 0,
+    HCAO_EINVAL = -1,          /* bad argument or call order */
+    HCAO_ENOMEM = -2,          /* device allocation failed */
+    HCAO_ECUDA = -3,           /* a CUDA runtime call failed */
+    HCAO_EREJECT_LIMIT = -4,   /* an LB/init rejection loop hit its cap */
+    HCAO_ELEVEL_OVERFLOW = -5, /* a quantum number outside a mode's level list */
+    HCAO_EBUSY = -6,           /* job still running (serving) */
+    HCAO_ECAPACITY = -7,       /* a cell ran out of particle slots */
+    HCAO_EROUNDS = -8,         /* NTC needed more pairing rounds than configured */
+    HCAO_ENOTFOUND = -9
+} hcao_status;
+
+enum { HCAO_FP64 = 0, HCAO_FP32 = 1 };
+enum { HCAO_DISS = 1, HCAO_EXCH = 2 };
+enum { HCAO_ALPHA_PER_MODE = 0, HCAO_ALPHA_ONE_RANDOM_STRETCH = 1 };
+
+#define HCAO_MAX_MODES 16
+#define HCAO_MAX_SPECIES 16
+#define HCAO_MAX_REACTIONS 8
+
+typedef struct {
+    int precision;          /* HCAO_FP64 (bit-exact parity mode) or HCAO_FP32 */
+    int device;             /* CUDA device ordinal */
+    void* cuda_stream;      /* borrowed cudaStream_t; NULL = default stream */
+    int table_points;       /* K5 quadratic grid points M, 16..4000 (default 2048) */
+    double table_span_J;    /* K5 grid span above the ZPE (default 64 eV) */
+    uint32_t reject_cap;    /* trials per LB sample before HCAO_EREJECT_LIMIT (default 2^20) */
+    int max_rounds;         /* NTC pairing rounds per cell and step (default 2) */
+    double capacity_factor; /* per-cell slots = count*factor + extra (default 2.0) */
+    int capacity_extra;     /* (default 64) */
+} hcao_config;
+
+/* One species (Sec. "The polyatomic HCAO model").  Modes are numbered with the
+   Morse stretches first (0..n_stretch-1), then the harmonic bends. */
+typedef struct {
+    double mass, d_ref, T_ref, omega; /* VHS: omega must be 0.5, 0.75 or 1.0 and
+                                         equal for all species */
+    double E_form;                    /* J, formation energy from the well bottom */
+    int n_stretch;
+    const double* we;                 /* host, n_stretch, m^-1 (Eq. energy-AHO) */
+    const double* wexe;               /* host, n_stretch, m^-1 */
+    const double* De;                 /* host, n_stretch, J (truncates the levels) */
+    int n_bend;
+    const double* theta;              /* host, n_bend, K (Theta form of Eq. energy-SHO) */
+} hcao_species;
+
+/* One reaction (Sec. "Polyatomic QK reaction modeling"). */
+typedef struct {
+    int type;              /* HCAO_DISS: A + M -> B + C + M (Eq. Ecoll-diss);
+                              HCAO_EXCH: A + B -> C + D (Eq. Ecoll-exch) */
+    int reactants[2];      /* DISS: {A, -1}; EXCH: {A, B} (species indices) */
+    int products[2];       /* DISS: {B, C}; EXCH: {C, D} */
+    uint32_t diss_mode_mask; /* DISS: stretches of A that may break */
+    double Ea;             /* EXCH: activation energy, J */
+    double steric;         /* EXCH: steric factor in [0,1] */
+    int alpha_mode;        /* EXCH: HCAO_ALPHA_PER_MODE or _ONE_RANDOM_STRETCH */
+    const double* alpha;   /* host, n_modes of A, or NULL */
+} hcao_reaction;
+
+/* One candidate pair of the last step (parity inspection). */
+typedef struct {
+    uint32_t step, cell, round_k, p, q;
+    int32_t event;         /* -1 rejected candidate, 0 relaxed, 1+r reaction r */
+    uint32_t aux;          /* DISS: broken stretch (+16 if partner q); EXCH: side */
+} hcao_log_rec;
+
+typedef struct {
+    int64_t n[HCAO_MAX_SPECIES];        /* particles per species */
+    double momentum[3];                 /* sum m v, kg m/s (times 1, not the weight) */
+    double E_tr;                        /* sum 1/2 m v^2, J */
+    double E_vib[HCAO_MAX_SPECIES];     /* sum of vibrational energies incl. ZPE, J */
+    double E_form;                      /* sum of formation energies, J */
+    double T_tr;                        /* from the peculiar translational energy, K */
+    double T_vib[HCAO_MAX_SPECIES];     /* zero-point search (Sec. implementation), K */
+} hcao_moments;
+
+typedef struct hcao_ctx hcao_ctx;
+
+/* Create a context on config->device.  config may be NULL (defaults). */
+hcao_status hcao_create(const hcao_config* config, hcao_ctx** out);
+/* Free all device memory of the context (synchronises its stream). */
+void hcao_destroy(hcao_ctx* ctx);
+const char* hcao_last_error(const hcao_ctx* ctx);
+/* Fill *config with the defaults. */
+void hcao_default_config(hcao_config* config);
+
+/* Species and their level / sampler tables: Morse stretch levels (Eq.
+   energy-AHO), harmonic bends (Eq. energy-SHO), the K5 sampler tables.  Call
+   once, before any reservoir is added.  Copies all arrays. */
+hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n);
+/* Reactions (Sec. "Polyatomic QK reaction modeling").  Call after
+   hcao_set_species, before any reservoir is added.  Copies all arrays. */
+hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* reactions, int n);
+
+/* A 0D reservoir of n_cells independent cells of volume cell_volume with
+   particle weight `weight` and time step dt (Sec. "Verification": single
+   reservoir cell, closed system).  seed keys its Philox stream; T_sgmax sets
+   the initial (sigma_T g)_max = 2 <sigma_T g>(T_sgmax).  *id receives the
+   reservoir index. */
+hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, double weight,
+                               double dt, uint64_t seed, double T_sgmax, int* id);
+/* Remove a reservoir and free its device memory. */
+hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int res);
+
+/* Load n particles into reservoir res (host arrays: v n x 3 doubles, qn
+   n x 16 bytes (mode j of particle i at qn[16 i + j]), species and cell
+   n int32).  Sorts them into cells with the stable counting sort, keeping
+   input order within a cell.  Replaces any earlier content. */
+hcao_status hcao_load_particles(hcao_ctx* ctx, int res, int64_t n, const double* host_v,
+                                const uint8_t* host_qn, const int32_t* host_species,
+                                const int32_t* host_cell);
+/* Initial quantum numbers of all particles of res at T_vib on the device:
+   bends i = floor(-ln(r) T_vib / Theta) (redrawn beyond the level list),
+   stretches drawn uniformly over 0..i_diss and accepted with
+   exp(-(E_i - E_0)/(k T_vib)) (Sec. implementation, Eq. accept-quant). */
+hcao_status hcao_init_vibration(hcao_ctx* ctx, int res, double T_vib);
+
+/* Advance every reservoir by n_steps collision phases (NTC pair selection with
+   VHS cross-sections, QK reaction test and execution, HCAO LB relaxation,
+   isotropic scattering).  Asynchronous on the context's stream. */
+hcao_status hcao_step(hcao_ctx* ctx, int n_steps);
+/* Wait for the stream; return the sticky device error status. */
+hcao_status hcao_sync(hcao_ctx* ctx);
+
+/* Number of particles of reservoir res (synchronises). */
+hcao_status hcao_count(hcao_ctx* ctx, int res, int64_t* n);
+/* Copy reservoir res back in canonical order (cell by cell, slot order):
+   host arrays sized by hcao_count; any of them may be NULL. */
+hcao_status hcao_read_particles(hcao_ctx* ctx, int res, double* host_v, uint8_t* host_qn,
+                                int32_t* host_species, int32_t* host_cell);
+/* Moments of reservoir res, reduced on the device in FP64; T_vib by the
+   zero-point search on the host. */
+hcao_status hcao_read_moments(hcao_ctx* ctx, int res, hcao_moments* out);
+/* Level populations of one mode of one species in reservoir res:
+   counts[i] = particles with quantum number i (i < max_levels). */
+hcao_status hcao_read_level_populations(hcao_ctx* ctx, int res, int species, int mode,
+                                        uint64_t* host_counts, int max_levels);
+/* Counters of reservoir res since load: [0] candidate pairs, [1] accepted
+   collisions, [2] LB samples, [3] LB trials, [4] sampler table overflows,
+   [5] degenerate samples, [6] reactions not executed, [7] steps,
+   [8 + r] events of reaction r.  Returns the number written in *n_out. */
+hcao_status hcao_read_counters(hcao_ctx* ctx, int res, uint64_t* host_out, int max, int* n_out);
+/* Reaction event counts only (host_out[r], r < n). */
+hcao_status hcao_read_reaction_counts(hcao_ctx* ctx, int res, uint64_t* host_out, int n);
+/* (sigma_T g)_max of every cell of res (host, n_cells doubles). */
+hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int res, double* host_out);
+
+/* Per-pair log of the most recent step, in canonical order (reservoir, cell,
+   round, pair).  Enable before stepping; costs one 28-byte record per pair.
+   With host_out == NULL, *n_out receives the number of records available. */
+hcao_status hcao_set_log(hcao_ctx* ctx, int enable);
+hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* host_out, int64_t max, int64_t* n_out);
+
+/* Stable counting sort by cell (the sort that places loaded particles in
+   their cells): device keys[n] (cell ids < n_cells) -> device perm[n]
+   (perm[j] = input index of the j-th particle in cell order, input order kept
+   within a cell) and device offsets[n_cells+1] (start of each cell in perm).
+   Keys >= n_cells are sorted but not counted in offsets.  Uses scratch from
+   the context; asynchronous on the context's stream. */
+hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint32_t n_cells,
+                           uint32_t* perm, uint32_t* offsets);
+
+/* Level energy (J) of level `level` of mode `mode` of species sp, and the
+   number of levels; host-side table lookups. */
+hcao_status hcao_level_energy(const hcao_ctx* ctx, int sp, int mode, int level, double* out);
+hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out);
+
+/* Kernel timing: with profiling on, hcao_step records CUDA events on the
+   context's stream around each kernel.  hcao_read_profile accumulates and
+   returns, for k = 0 (setup), 1 (collide), 2 (finish), the summed device time
+   in ms (host_ms[k]) and the number of launches (host_launches[k]); *n_out = 3.
+   hcao_set_profiling resets the sums. */
+hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
+hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
+                              int* n_out);
+
+/* Number of this library's kernels launched since create (instrumentation). */
+uint64_t hcao_kernel_launches(const hcao_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -58,7 +58,8 @@ typedef struct {
     double zpe;
     /* K5 tables */
     double base[ORA_MAX_MODES + 1];
-    double delta, inv_delta;
+    double cq;          /* quadratic grid: g_m = base_k + cq * m^2 */
+    double eps_min;     /* smallest single-quantum excitation of any mode */
     int MT;
     double* H[ORA_MAX_MODES];
 } o_species;
@@ -249,16 +250,23 @@ static void build_levels(ora_ctx* c, o_species* s) {
 }
 
 /* K5 tables (reading A5).  H_k(g) bounds from above the LB weight sum of modes
-   k..n-1 at budget g; grid g_m = base_k + m * delta, base_k = sum_{j>=k} E_j(0).
-   H_{n-1}(g) = sum_i pw(g - E_{n-1,i});  H_k(g) = sum_i W_{k+1}(g - E_{k,i}),
-   W_k(E) = H_k[idx_k(E)], idx_k(E) = smallest grid index with g >= E. */
+   k..n-1 at budget g, on the quadratic grid g_m = base_k + cq m^2 (cq = span /
+   M^2), base_k = sum_{j>=k} E_j(0):
+     H_{n-1}(g) = sum_i pw(g - E_{n-1,i}),   H_k(g) = sum_i W_{k+1}(g - E_{k,i}),
+     W_k(E) = H_k[idx_k(E)], idx_k(E) = the smallest m >= 1 with g_m >= E (0 if
+   E <= base_k; MT if no grid point reaches E).  Found by bisection. */
+static double grid_pt(const o_species* s, int k, int64_t m) {
+    return s->base[k] + s->cq * (double)(m * m);
+}
 static int64_t grid_idx(const o_species* s, int k, double E) {
     if (!(E > s->base[k])) return 0;
-    double t = (E - s->base[k]) * s->inv_delta;
-    int64_t m = (int64_t)ceil(t);
-    if (m < 1) m = 1;
-    while (s->base[k] + (double)m * s->delta < E) m++;
-    return m;
+    if (grid_pt(s, k, s->MT - 1) < E) return s->MT;
+    int64_t lo = 0, hi = s->MT - 1; /* g_lo < E <= g_hi */
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (grid_pt(s, k, mid) < E) lo = mid; else hi = mid;
+    }
+    return hi;
 }
 static double W_tab(const o_species* s, int k, double E) {
     int64_t m = grid_idx(s, k, E);
@@ -271,14 +279,16 @@ static int build_tables(ora_ctx* c, o_species* s) {
     if (n == 0) return 0;
     s->base[n] = 0.0;
     for (int k = n - 1; k >= 0; --k) s->base[k] = s->E[k][0] + s->base[k + 1];
-    s->delta = c->span / (double)c->M;
-    s->inv_delta = 1.0 / s->delta;
+    s->cq = c->span / ((double)c->M * (double)c->M);
     s->MT = c->M + TABLE_PAD;
+    s->eps_min = INFINITY;
+    for (int j = 0; j < n; ++j)
+        if (s->n_levels[j] > 1 && s->E[j][1] - s->E[j][0] < s->eps_min) s->eps_min = s->E[j][1] - s->E[j][0];
     for (int k = n - 1; k >= 0; --k) {
         s->H[k] = (double*)malloc(sizeof(double) * (size_t)s->MT);
         if (!s->H[k]) return -1;
         for (int m = 0; m < s->MT; ++m) {
-            double g = s->base[k] + (double)m * s->delta;
+            double g = grid_pt(s, k, m);
             double sum = 0.0;
             for (int i = 0; i < s->n_levels[k]; ++i) {
                 if (!(s->E[k][i] < g)) break;
@@ -308,7 +318,9 @@ enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
 
 /* K5: sequential draw through the H tables; a draw that runs past the end of a
    mode's level list restarts the trial.  Accepted states follow the target
-   exactly (each trial's acceptance probability is pw(..)/H_0). */
+   exactly (each trial's acceptance probability is pw(..)/H_0).  Below the
+   smallest single-quantum excitation only the ground state has sum E < Ec, so
+   it is taken without a draw. */
 static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
                         uint8_t* qn_out, uint64_t* trials) {
     int n = s->n_modes;
@@ -316,6 +328,10 @@ static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
     int64_t m0 = grid_idx(s, 0, Ec);
     if (m0 > c->M) return S_OVER;
     if (m0 == 0 || !(s->H[0][m0] > 0.0)) return S_DEGEN;
+    if (Ec - s->base[0] < s->eps_min) {
+        memset(qn_out, 0, (size_t)n);
+        return S_OK;
+    }
     uint8_t qn[ORA_MAX_MODES];
     for (uint32_t trial = 0; trial < c->reject_cap; ++trial) {
         if (trials) (*trials)++;
@@ -604,7 +620,7 @@ static void product_state(ora_ctx* c, o_res* R, const o_species* s, double Ec, o
 
 static double table_top(const o_species* s, const ora_ctx* c) {
     if (s->n_modes == 0) return INFINITY;
-    return s->base[0] + (double)c->M * s->delta;
+    return grid_pt(s, 0, c->M);
 }
 
 /* Dissociation A + M -> B + C + M (Sec. "Dissociation reactions"), energy kept

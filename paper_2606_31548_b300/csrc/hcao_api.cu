@@ -1,0 +1,1150 @@
+// hcao_api.cu -- host side of libhcao: the C ABI, species level tables and
+// the K5 sampler tables, reservoir layout in HBM, launches.
+//
+// Host arithmetic that feeds device decisions (level energies, grid bases,
+// K5 tables, VHS pair constants) is evaluated in IEEE double without FMA
+// contraction (-ffp-contract=off) in the operation order documented beside
+// each formula.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hcao_internal.h"
+#include "hcao_sort.h"
+
+using namespace hcao;
+
+namespace {
+
+constexpr double KB = 1.380649e-23;
+constexpr double HPLANCK = 6.62607015e-34;
+constexpr double CLIGHT = 299792458.0;
+constexpr double PI_D = 3.14159265358979323846;
+
+struct HostSpecies {
+    hcao_species d;
+    std::vector<double> we, wexe, De, theta;
+    int n_modes = 0;
+    bool bend[MAXM] = {};
+    double ktheta[MAXM] = {};
+    std::vector<double> lev[MAXM];
+    double zpe = 0.0;
+};
+
+struct Reservoir {
+    bool live = false, loaded = false;
+    int n_cells = 0;
+    double Vc = 0, w = 0, dt = 0, T_sgmax = 0;
+    uint64_t seed = 0;
+    int cell0 = 0;                 // first global cell index
+    void* recs = nullptr;
+    size_t rec_bytes = 0;
+    uint64_t total_cap = 0;
+};
+
+}  // namespace
+
+struct hcao_ctx {
+    hcao_config cfg{};
+    cudaStream_t stream = nullptr;
+    int sm_count = 148;
+    std::string err;
+    uint64_t launches = 0;
+
+    int n_species = 0;
+    HostSpecies sp[MAXS];
+    int n_reactions = 0;
+    Consts hc{};
+    Consts* d_consts = nullptr;
+    double* d_lev64 = nullptr;
+    float* d_lev32 = nullptr;
+    double* d_H64 = nullptr;
+    float* d_H32 = nullptr;
+    int amode = -1;
+    double omega = 0.75;
+
+    std::vector<Reservoir> res;
+    DevRes* d_res = nullptr;
+    int d_res_cap = 0;
+    DevCell* d_cells = nullptr;
+    unsigned long long* d_cellcnt = nullptr;
+    int n_cells_total = 0;
+    uint32_t* d_pbase = nullptr;
+    uint32_t* d_abase = nullptr;
+    uint32_t* d_totals = nullptr;
+    uint32_t* d_cflag = nullptr;
+    void* d_cscratch = nullptr;
+    hcao_log_rec* d_log = nullptr;
+    uint64_t pair_cap = 0;
+    uint32_t* d_err = nullptr;
+    bool log_on = false;
+    uint32_t* d_scratch = nullptr;
+    int64_t scratch_words = 0;
+    // kernel timing: events recorded on the stream around each kernel class
+    bool prof_on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
+    size_t prof_used[3] = {0, 0, 0};
+    double prof_ms[3] = {0, 0, 0};
+    uint64_t prof_n[3] = {0, 0, 0};
+};
+
+namespace {
+
+hcao_status fail(hcao_ctx* c, hcao_status s, const std::string& m) {
+    if (c) c->err = m;
+    return s;
+}
+#define CU(call)                                                                           \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HCAO_ENOMEM : HCAO_ECUDA,     \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(hcao_ctx* ctx, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), ctx->stream);
+}
+template <class T>
+void dfree(hcao_ctx* ctx, T*& p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
+    p = nullptr;
+}
+
+size_t rec_size(const hcao_ctx* c) { return c->cfg.precision == HCAO_FP64 ? sizeof(RecD) : sizeof(RecF); }
+
+// ---- levels: Morse stretches (Eq. energy-AHO) E(i) = hc we (i+1/2) - hc wexe (i+1/2)^2,
+// kept while E < De and increasing; bends (i+1/2) k Theta, kept while i < 256 and
+// E < ZPE + table span.  Operation order: ((hc*we)*x) - ((hc*wexe)*(x*x)).
+void build_levels(const hcao_ctx* ctx, HostSpecies& s) {
+    const double hc = HPLANCK * CLIGHT;
+    const int ns = s.d.n_stretch, nb = s.d.n_bend;
+    s.n_modes = ns + nb;
+    for (int j = 0; j < ns; ++j) {
+        s.bend[j] = false;
+        s.lev[j].clear();
+        double prev = -1.0;
+        for (int i = 0; i < MAXL; ++i) {
+            const double x = (double)i + 0.5;
+            const double E = hc * s.we[j] * x - hc * s.wexe[j] * (x * x);
+            if (!(E < s.De[j])) break;
+            if (i > 0 && !(E > prev)) break;
+            s.lev[j].push_back(E);
+            prev = E;
+        }
+    }
+    for (int b = 0; b < nb; ++b) {
+        s.bend[ns + b] = true;
+        s.ktheta[ns + b] = KB * s.theta[b];
+    }
+    double z = 0.0;
+    for (int j = 0; j < s.n_modes; ++j) {
+        const double e0 = s.bend[j] ? 0.5 * s.ktheta[j] : (s.lev[j].empty() ? 0.0 : s.lev[j][0]);
+        z = z + e0;
+    }
+    s.zpe = z;
+    const double top = z + ctx->cfg.table_span_J;
+    for (int j = ns; j < s.n_modes; ++j) {
+        s.lev[j].clear();
+        for (int i = 0; i < MAXL; ++i) {
+            const double E = ((double)i + 0.5) * s.ktheta[j];
+            if (!(E < top)) break;
+            s.lev[j].push_back(E);
+        }
+    }
+}
+
+template <class R>
+R lbpow_host(int amode, R x) {
+    if (amode == 0) {
+        const R s = std::sqrt(x);
+        return s * std::sqrt(s);
+    }
+    if (amode == 1) return x;
+    return std::sqrt(x);
+}
+
+// K5 tables in precision R over the levels `lev` (already in R), quadratic grid
+// g_m = base_k + cq m^2:  H_{n-1}(g_m) = sum_i pw(g_m - E_i),
+// H_k(g_m) = sum_i W_{k+1}(g_m - E_{k,i}),  W_k(E) = H_k[idx_k(E)],
+// idx_k(E) = smallest m >= 1 with g_m >= E (0 if E <= base_k, MT if none).
+template <class R>
+R grid_pt_host(R base, R cq, int64_t m) {
+    return base + cq * (R)(m * m);
+}
+template <class R>
+int64_t grid_idx_host(R base, R cq, int MT, R E) {
+    if (!(E > base)) return 0;
+    if (grid_pt_host<R>(base, cq, MT - 1) < E) return MT;
+    int64_t lo = 0, hi = MT - 1;  // g_lo < E <= g_hi
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (grid_pt_host<R>(base, cq, mid) < E) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+template <class R>
+void build_tables(int amode, int n, const std::vector<R>* lev, const R* base, R cq, int MT,
+                  std::vector<R>& out) {
+    out.assign((size_t)n * MT, (R)0);
+    for (int k = n - 1; k >= 0; --k) {
+        for (int m = 0; m < MT; ++m) {
+            const R g = grid_pt_host<R>(base[k], cq, m);
+            R sum = (R)0;
+            for (size_t i = 0; i < lev[k].size(); ++i) {
+                if (!(lev[k][i] < g)) break;
+                const R x = g - lev[k][i];
+                R w;
+                if (k == n - 1) {
+                    w = lbpow_host<R>(amode, x);
+                } else {
+                    int64_t mm = grid_idx_host<R>(base[k + 1], cq, MT, x);
+                    if (mm > MT - 1) mm = MT - 1;
+                    w = mm == 0 ? (R)0 : out[(size_t)(k + 1) * MT + mm];
+                }
+                sum = sum + w;
+            }
+            out[(size_t)k * MT + m] = sum;
+        }
+    }
+}
+
+// VHS pair constants: sigma_T g = C g^(2 - 2 omega),
+// C = ((pi*d)*d) * (2 k T_ref / m_r)^(omega-1/2) / Gamma(5/2 - omega),
+// d, T_ref the means of both species', m_r = (mA*mB)/(mA+mB).
+DevPair pair_consts(const hcao_ctx* ctx, int a, int b) {
+    const hcao_species& A = ctx->sp[a].d;
+    const hcao_species& B = ctx->sp[b].d;
+    DevPair p{};
+    p.mr = A.mass * B.mass / (A.mass + B.mass);
+    const double d = 0.5 * (A.d_ref + B.d_ref);
+    const double Tr = 0.5 * (A.T_ref + B.T_ref);
+    p.C = PI_D * d * d * std::pow(2.0 * KB * Tr / p.mr, ctx->omega - 0.5) / std::tgamma(2.5 - ctx->omega);
+    p.mt = A.mass + B.mass;
+    p.fp = B.mass / p.mt;
+    p.fq = A.mass / p.mt;
+    p.mr_f = (float)p.mr;
+    p.C_f = (float)p.C;
+    p.fp_f = (float)p.fp;
+    p.fq_f = (float)p.fq;
+    return p;
+}
+
+// <sigma_T g> over a Maxwellian at T: 2 d^2 sqrt(2 pi k T_ref / m_r) (T/T_ref)^(1-omega)
+double mean_sigma_g(const hcao_ctx* ctx, int a, int b, double T) {
+    const hcao_species& A = ctx->sp[a].d;
+    const hcao_species& B = ctx->sp[b].d;
+    const double mr = A.mass * B.mass / (A.mass + B.mass);
+    const double d = 0.5 * (A.d_ref + B.d_ref);
+    const double Tr = 0.5 * (A.T_ref + B.T_ref);
+    return 2.0 * d * d * std::sqrt(2.0 * PI_D * KB * Tr / mr) * std::pow(T / Tr, 1.0 - ctx->omega);
+}
+
+hcao_status upload_consts(hcao_ctx* ctx) {
+    if (!ctx->d_consts) CU(dalloc(ctx, &ctx->d_consts, 1));
+    CU(cudaMemcpyAsync(ctx->d_consts, &ctx->hc, sizeof(Consts), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+hcao_status ensure_scratch(hcao_ctx* ctx, int64_t words) {
+    if (words <= ctx->scratch_words) return HCAO_OK;
+    dfree(ctx, ctx->d_scratch);
+    CU(dalloc(ctx, &ctx->d_scratch, (size_t)words));
+    ctx->scratch_words = words;
+    return HCAO_OK;
+}
+
+hcao_status map_err(hcao_ctx* ctx) {
+    uint32_t e = 0;
+    CU(cudaMemcpyAsync(&e, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (e & ERR_REJECT) return fail(ctx, HCAO_EREJECT_LIMIT, "a rejection loop hit its cap");
+    if (e & ERR_CAPACITY) return fail(ctx, HCAO_ECAPACITY, "a cell ran out of particle slots");
+    if (e & ERR_ROUNDS) return fail(ctx, HCAO_EROUNDS, "NTC needed more pairing rounds than max_rounds");
+    if (e & ERR_LEVEL) return fail(ctx, HCAO_ELEVEL_OVERFLOW, "quantum number outside the level list");
+    return HCAO_OK;
+}
+
+// (Re)build the global cell table after reservoirs change: cells of live,
+// loaded reservoirs in reservoir order; per-pair buffers sized for
+// max_rounds * slots / 2 + cells.
+hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new_cells) {
+    int total = 0;
+    uint64_t pairs = 0;
+    for (auto& r : ctx->res)
+        if (r.live && r.loaded) {
+            total += r.n_cells;
+            pairs += (uint64_t)ctx->cfg.max_rounds * (r.total_cap / 2) + (uint64_t)r.n_cells;
+        }
+    DevCell* cells = nullptr;
+    unsigned long long* cnt = nullptr;
+    CU(dalloc(ctx, &cells, (size_t)total));
+    CU(dalloc(ctx, &cnt, (size_t)total * NCNT));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (size_t)std::max(total, 1) * NCNT, ctx->stream));
+    int at = 0;
+    for (int id = 0; id < (int)ctx->res.size(); ++id) {
+        Reservoir& r = ctx->res[id];
+        if (!(r.live && r.loaded)) continue;
+        if (id == new_res) {
+            CU(cudaMemcpyAsync(cells + at, new_cells->data(), sizeof(DevCell) * r.n_cells,
+                               cudaMemcpyHostToDevice, ctx->stream));
+        } else {
+            CU(cudaMemcpyAsync(cells + at, ctx->d_cells + r.cell0, sizeof(DevCell) * r.n_cells,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(cnt + (size_t)at * NCNT, ctx->d_cellcnt + (size_t)r.cell0 * NCNT,
+                               sizeof(unsigned long long) * r.n_cells * NCNT,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        r.cell0 = at;
+        at += r.n_cells;
+    }
+    dfree(ctx, ctx->d_cells);
+    dfree(ctx, ctx->d_cellcnt);
+    ctx->d_cells = cells;
+    ctx->d_cellcnt = cnt;
+    ctx->n_cells_total = total;
+    dfree(ctx, ctx->d_pbase);
+    dfree(ctx, ctx->d_abase);
+    CU(dalloc(ctx, &ctx->d_pbase, (size_t)MAX_ROUNDS * (total + 1)));
+    CU(dalloc(ctx, &ctx->d_abase, (size_t)total + 1));
+    if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
+        dfree(ctx, ctx->d_cflag);
+        dfree(ctx, ctx->d_log);
+        if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
+        ctx->d_cscratch = nullptr;
+        ctx->pair_cap = std::max<uint64_t>(pairs, 1024);
+        CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
+        if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+    }
+    if (ctx->hc.creates && !ctx->d_cscratch)
+        CU(cudaMallocAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->stream));
+    // reservoir table
+    if ((int)ctx->res.size() > ctx->d_res_cap) {
+        DevRes* nr = nullptr;
+        const int cap = std::max<int>(64, 2 * (int)ctx->res.size());
+        CU(dalloc(ctx, &nr, (size_t)cap));
+        if (ctx->d_res)
+            CU(cudaMemcpyAsync(nr, ctx->d_res, sizeof(DevRes) * ctx->d_res_cap, cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+        dfree(ctx, ctx->d_res);
+        ctx->d_res = nr;
+        ctx->d_res_cap = cap;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+hcao_status read_cells(hcao_ctx* ctx, const Reservoir& r, std::vector<DevCell>& out) {
+    out.resize(r.n_cells);
+    CU(cudaMemcpyAsync(out.data(), ctx->d_cells + r.cell0, sizeof(DevCell) * r.n_cells,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+Reservoir* get_res(hcao_ctx* ctx, int id) {
+    if (id < 0 || id >= (int)ctx->res.size() || !ctx->res[id].live) return nullptr;
+    return &ctx->res[id];
+}
+
+// P5 zero-point search for T_vib: root of <E_vib>(T) (bends: harmonic closed
+// form k Theta / (exp(Theta/T) - 1); stretches: Boltzmann mean over the Morse
+// levels) = mean vibrational energy above the ZPE, by bisection.
+double tvib_host(const HostSpecies& s, double target) {
+    if (!(target > 0.0) || s.n_modes == 0) return 0.0;
+    auto mean = [&](double T) {
+        double e = 0.0;
+        for (int j = 0; j < s.n_modes; ++j) {
+            if (s.bend[j]) {
+                const double th = s.theta[j - s.d.n_stretch];
+                e += KB * th / (std::exp(th / T) - 1.0);
+            } else {
+                double num = 0.0, den = 0.0;
+                for (double Ei : s.lev[j]) {
+                    const double de = Ei - s.lev[j][0];
+                    const double b = std::exp(-de / (KB * T));
+                    num += de * b;
+                    den += b;
+                }
+                e += num / den;
+            }
+        }
+        return e;
+    };
+    double lo = 1.0, hi = 1.0e6;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mean(mid) < target) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+StepArgs make_args(hcao_ctx* ctx) {
+    StepArgs a{};
+    a.C = ctx->d_consts;
+    a.lev64 = ctx->d_lev64;
+    a.lev32 = ctx->d_lev32;
+    a.H64 = ctx->d_H64;
+    a.H32 = ctx->d_H32;
+    a.cells = ctx->d_cells;
+    a.n_cells = ctx->n_cells_total;
+    a.res = ctx->d_res;
+    a.n_res = (int)ctx->res.size();
+    a.counters = ctx->d_cellcnt;
+    a.pbase = ctx->d_pbase;
+    a.abase = ctx->d_abase;
+    a.totals = ctx->d_totals;
+    a.cflag = ctx->d_cflag;
+    a.cscratch = ctx->d_cscratch;
+    a.pair_cap = ctx->pair_cap;
+    a.log = ctx->d_log;
+    a.log_on = ctx->log_on ? 1 : 0;
+    a.err = ctx->d_err;
+    a.max_rounds = ctx->cfg.max_rounds;
+    a.reject_cap = ctx->cfg.reject_cap;
+    return a;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+void hcao_default_config(hcao_config* c) {
+    std::memset(c, 0, sizeof *c);
+    c->precision = HCAO_FP64;
+    c->device = 0;
+    c->cuda_stream = nullptr;
+    c->table_points = 2048;
+    c->table_span_J = 64.0 * 1.602176634e-19;
+    c->reject_cap = 1u << 20;
+    c->max_rounds = 2;
+    c->capacity_factor = 2.0;
+    c->capacity_extra = 64;
+}
+
+hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
+    if (!out) return HCAO_EINVAL;
+    *out = nullptr;
+    hcao_ctx* ctx = new hcao_ctx();
+    hcao_default_config(&ctx->cfg);
+    if (config) ctx->cfg = *config;
+    if (ctx->cfg.table_points < 16 || ctx->cfg.table_points > 4000 || !(ctx->cfg.table_span_J > 0) ||
+        ctx->cfg.max_rounds < 1 || ctx->cfg.max_rounds > MAX_ROUNDS || ctx->cfg.reject_cap < 1 ||
+        (ctx->cfg.precision != HCAO_FP64 && ctx->cfg.precision != HCAO_FP32) ||
+        ctx->cfg.capacity_factor < 1.0 || ctx->cfg.capacity_extra < 0) {
+        delete ctx;
+        return HCAO_EINVAL;
+    }
+    cudaError_t e = cudaSetDevice(ctx->cfg.device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return HCAO_ECUDA;
+    }
+    int dev = ctx->cfg.device;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
+    if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess) {
+        delete ctx;
+        return HCAO_ENOMEM;
+    }
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
+    cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 1), ctx->stream);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        delete ctx;
+        return HCAO_ECUDA;
+    }
+    *out = ctx;
+    return HCAO_OK;
+}
+
+void hcao_destroy(hcao_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& r : ctx->res)
+        if (r.recs) cudaFreeAsync(r.recs, ctx->stream);
+    dfree(ctx, ctx->d_consts);
+    dfree(ctx, ctx->d_lev64);
+    dfree(ctx, ctx->d_lev32);
+    dfree(ctx, ctx->d_H64);
+    dfree(ctx, ctx->d_H32);
+    dfree(ctx, ctx->d_res);
+    dfree(ctx, ctx->d_cells);
+    dfree(ctx, ctx->d_cellcnt);
+    dfree(ctx, ctx->d_pbase);
+    dfree(ctx, ctx->d_abase);
+    dfree(ctx, ctx->d_totals);
+    dfree(ctx, ctx->d_cflag);
+    if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
+    dfree(ctx, ctx->d_log);
+    dfree(ctx, ctx->d_err);
+    dfree(ctx, ctx->d_scratch);
+    cudaStreamSynchronize(ctx->stream);
+    for (int k = 0; k < 3; ++k)
+        for (auto& e : ctx->prof_ev[k]) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+    delete ctx;
+}
+
+const char* hcao_last_error(const hcao_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+uint64_t hcao_kernel_launches(const hcao_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) {
+    if (!ctx || !species || n < 1 || n > MAXS) return fail(ctx, HCAO_EINVAL, "set_species: bad arguments");
+    if (ctx->n_species > 0) return fail(ctx, HCAO_EINVAL, "set_species: already set");
+    int amode = -1;
+    for (int i = 0; i < n; ++i) {
+        const hcao_species& d = species[i];
+        int am;
+        if (d.omega == 0.75) am = 0;
+        else if (d.omega == 0.5) am = 1;
+        else if (d.omega == 1.0) am = 2;
+        else return fail(ctx, HCAO_EINVAL, "set_species: omega must be 0.5, 0.75 or 1");
+        if (amode >= 0 && am != amode) return fail(ctx, HCAO_EINVAL, "set_species: omega differs between species");
+        amode = am;
+        if (d.n_stretch < 0 || d.n_bend < 0 || d.n_stretch + d.n_bend > MAXM || !(d.mass > 0) ||
+            !(d.d_ref > 0) || !(d.T_ref > 0))
+            return fail(ctx, HCAO_EINVAL, "set_species: bad species parameters");
+        if ((d.n_stretch > 0 && (!d.we || !d.wexe || !d.De)) || (d.n_bend > 0 && !d.theta))
+            return fail(ctx, HCAO_EINVAL, "set_species: missing mode arrays");
+    }
+    ctx->amode = amode;
+    ctx->omega = species[0].omega;
+    // levels
+    std::vector<double> lev64;
+    std::vector<float> lev32;
+    for (int i = 0; i < n; ++i) {
+        HostSpecies& s = ctx->sp[i];
+        s.d = species[i];
+        s.we.assign(species[i].we, species[i].we + species[i].n_stretch);
+        s.wexe.assign(species[i].wexe, species[i].wexe + species[i].n_stretch);
+        s.De.assign(species[i].De, species[i].De + species[i].n_stretch);
+        s.theta.assign(species[i].theta, species[i].theta + species[i].n_bend);
+        s.d.we = s.we.data(); s.d.wexe = s.wexe.data(); s.d.De = s.De.data(); s.d.theta = s.theta.data();
+        build_levels(ctx, s);
+        for (int j = 0; j < s.n_modes; ++j)
+            if (s.lev[j].empty()) return fail(ctx, HCAO_EINVAL, "set_species: a stretch has no level below De");
+    }
+    ctx->n_species = n;
+    Consts& C = ctx->hc;
+    std::memset(&C, 0, sizeof C);
+    C.n_species = n;
+    C.amode = amode;
+    const int M = ctx->cfg.table_points;
+    const int MT = M + TABLE_PAD;
+    std::vector<double> H64;
+    std::vector<float> H32;
+    for (int i = 0; i < n; ++i) {
+        HostSpecies& s = ctx->sp[i];
+        DevSpecies& D = C.sp[i];
+        D.mass = s.d.mass;
+        D.E_form = s.d.E_form;
+        D.zpe = s.zpe;
+        D.n_modes = s.n_modes;
+        D.n_stretch = s.d.n_stretch;
+        D.M = M;
+        D.MT = MT;
+        for (int j = 0; j < s.d.n_stretch; ++j) D.De[j] = s.De[j];
+        for (int j = 0; j < s.n_modes; ++j) {
+            D.lev_off[j] = (int)lev64.size();
+            D.n_lev[j] = (int)s.lev[j].size();
+            for (double e : s.lev[j]) {
+                lev64.push_back(e);
+                lev32.push_back((float)e);
+            }
+        }
+        // K5 grid: base_k = E_k(0) + base_{k+1}; delta = span / M
+        const int nm = s.n_modes;
+        D.base[nm] = 0.0;
+        D.base_f[nm] = 0.0f;
+        for (int k = nm - 1; k >= 0; --k) {
+            D.base[k] = s.lev[k][0] + D.base[k + 1];
+            D.base_f[k] = (float)s.lev[k][0] + D.base_f[k + 1];
+        }
+        D.cq = ctx->cfg.table_span_J / ((double)M * (double)M);
+        D.inv_cq = 1.0 / D.cq;
+        D.cq_f = (float)D.cq;
+        D.inv_cq_f = 1.0f / D.cq_f;
+        D.top = nm > 0 ? D.base[0] + D.cq * (double)((int64_t)M * M) : INFINITY;
+        D.eps_min = INFINITY;
+        D.eps_min_f = INFINITY;
+        for (int j = 0; j < nm; ++j)
+            if (s.lev[j].size() > 1) {
+                const double e = s.lev[j][1] - s.lev[j][0];
+                const float ef = (float)s.lev[j][1] - (float)s.lev[j][0];
+                if (e < D.eps_min) D.eps_min = e;
+                if (ef < D.eps_min_f) D.eps_min_f = ef;
+            }
+        if (nm > 0) {
+            if (ctx->cfg.precision == HCAO_FP64) {
+                std::vector<double> L[MAXM];
+                for (int j = 0; j < nm; ++j) L[j] = s.lev[j];
+                std::vector<double> t;
+                build_tables<double>(amode, nm, L, D.base, D.cq, MT, t);
+                D.tab_off = (int)H64.size();
+                H64.insert(H64.end(), t.begin(), t.end());
+            } else {
+                std::vector<float> L[MAXM];
+                for (int j = 0; j < nm; ++j) {
+                    L[j].resize(s.lev[j].size());
+                    for (size_t l = 0; l < s.lev[j].size(); ++l) L[j][l] = (float)s.lev[j][l];
+                }
+                std::vector<float> t;
+                build_tables<float>(amode, nm, L, D.base_f, D.cq_f, MT, t);
+                D.tab_off = (int)H32.size();
+                H32.insert(H32.end(), t.begin(), t.end());
+            }
+        }
+    }
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b) C.pair[a * MAXS + b] = pair_consts(ctx, a, b);
+    CU(dalloc(ctx, &ctx->d_lev64, lev64.size()));
+    CU(dalloc(ctx, &ctx->d_lev32, lev32.size()));
+    CU(cudaMemcpyAsync(ctx->d_lev64, lev64.data(), sizeof(double) * lev64.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_lev32, lev32.data(), sizeof(float) * lev32.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (!H64.empty()) {
+        CU(dalloc(ctx, &ctx->d_H64, H64.size()));
+        CU(cudaMemcpyAsync(ctx->d_H64, H64.data(), sizeof(double) * H64.size(), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (!H32.empty()) {
+        CU(dalloc(ctx, &ctx->d_H32, H32.size()));
+        CU(cudaMemcpyAsync(ctx->d_H32, H32.data(), sizeof(float) * H32.size(), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return upload_consts(ctx);
+}
+
+hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
+    if (!ctx || n < 0 || n > MAXR || (n > 0 && !rx)) return fail(ctx, HCAO_EINVAL, "set_reactions: bad arguments");
+    if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "set_reactions: species first");
+    for (auto& r : ctx->res)
+        if (r.live) return fail(ctx, HCAO_EINVAL, "set_reactions: before any reservoir");
+    Consts& C = ctx->hc;
+    const int S = ctx->n_species;
+    int creates = 0;
+    for (int i = 0; i < n; ++i) {
+        const hcao_reaction& r = rx[i];
+        DevReaction& D = C.rx[i];
+        std::memset(&D, 0, sizeof D);
+        D.type = r.type;
+        if (r.type != HCAO_DISS && r.type != HCAO_EXCH) return fail(ctx, HCAO_EINVAL, "set_reactions: bad type");
+        D.A = r.reactants[0];
+        D.B = r.type == HCAO_EXCH ? r.reactants[1] : -1;
+        D.P0 = r.products[0];
+        D.P1 = r.products[1];
+        if (D.A < 0 || D.A >= S || D.P0 < 0 || D.P0 >= S || D.P1 < 0 || D.P1 >= S ||
+            (r.type == HCAO_EXCH && (D.B < 0 || D.B >= S)))
+            return fail(ctx, HCAO_EINVAL, "set_reactions: species index out of range");
+        const HostSpecies& A = ctx->sp[D.A];
+        D.mask = r.diss_mode_mask;
+        D.Ea = r.Ea;
+        D.steric = r.steric;
+        D.alpha_mode = r.alpha_mode;
+        if (r.type == HCAO_DISS) {
+            if (A.d.n_stretch == 0 || (r.diss_mode_mask >> A.d.n_stretch) != 0)
+                return fail(ctx, HCAO_EINVAL, "set_reactions: dissociation mask outside the stretches");
+            // Eq. Ecoll-diss subtracts the ZPEs of A, B and C
+            D.zpesum = A.zpe + ctx->sp[D.P0].zpe + ctx->sp[D.P1].zpe;
+            D.dEf = (ctx->sp[D.P0].d.E_form + ctx->sp[D.P1].d.E_form) - A.d.E_form;
+            creates = 1;
+        } else {
+            if (r.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH && A.d.n_stretch == 0)
+                return fail(ctx, HCAO_EINVAL, "set_reactions: exchange coupling needs a stretch");
+            if (r.alpha_mode == HCAO_ALPHA_PER_MODE && r.alpha)
+                for (int j = 0; j < A.n_modes; ++j) D.alpha[j] = r.alpha[j];
+            D.dEf = (ctx->sp[D.P0].d.E_form + ctx->sp[D.P1].d.E_form) -
+                    (A.d.E_form + ctx->sp[D.B].d.E_form);
+        }
+    }
+    C.n_reactions = n;
+    C.creates = creates;
+    ctx->n_reactions = n;
+    return upload_consts(ctx);
+}
+
+hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, double weight, double dt,
+                               uint64_t seed, double T_sgmax, int* id) {
+    if (!ctx || n_cells < 1 || !(cell_volume > 0) || !(weight > 0) || !(dt > 0) || !(T_sgmax > 0) || !id)
+        return fail(ctx, HCAO_EINVAL, "add_reservoir: bad arguments");
+    if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "add_reservoir: species first");
+    Reservoir r;
+    r.live = true;
+    r.n_cells = n_cells;
+    r.Vc = cell_volume;
+    r.w = weight;
+    r.dt = dt;
+    r.seed = seed;
+    r.T_sgmax = T_sgmax;
+    ctx->res.push_back(r);
+    *id = (int)ctx->res.size() - 1;
+    return HCAO_OK;
+}
+
+hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int id) {
+    if (!ctx) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r) return fail(ctx, HCAO_ENOTFOUND, "remove_reservoir: no such reservoir");
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (r->recs) cudaFreeAsync(r->recs, ctx->stream);
+    r->recs = nullptr;
+    const bool was_loaded = r->loaded;
+    r->live = false;
+    r->loaded = false;
+    if (ctx->d_res && id < ctx->d_res_cap) {
+        DevRes dr{};
+        dr.active = 0;
+        CU(cudaMemcpyAsync(ctx->d_res + id, &dr, sizeof dr, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (was_loaded) return relayout(ctx, -1, nullptr);
+    return HCAO_OK;
+}
+
+hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_t* perm,
+                           uint32_t* offsets) {
+    if (!ctx || n < 0 || n > 0xFFFFFFFFll || n_cells < 1 || (n > 0 && (!keys || !perm)) || !offsets)
+        return fail(ctx, HCAO_EINVAL, "cell_sort: bad arguments");
+    hcao_status st = ensure_scratch(ctx, sort_scratch_words(n, n_cells));
+    if (st != HCAO_OK) return st;
+    CU(cell_sort(keys, n, n_cells, perm, offsets, ctx->d_scratch, ctx->stream, &ctx->launches));
+    return HCAO_OK;
+}
+
+hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* v, const uint8_t* qn,
+                                const int32_t* species, const int32_t* cell) {
+    if (!ctx) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r) return fail(ctx, HCAO_ENOTFOUND, "load_particles: no such reservoir");
+    if (n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!v || !qn || !species || !cell)))
+        return fail(ctx, HCAO_EINVAL, "load_particles: bad arguments");
+    // validate on the host: cell and species ranges, levels inside each mode's list
+    bool present[MAXS] = {};
+    std::vector<uint32_t> counts(r->n_cells, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (cell[i] < 0 || cell[i] >= r->n_cells) return fail(ctx, HCAO_EINVAL, "load_particles: cell out of range");
+        if (species[i] < 0 || species[i] >= ctx->n_species)
+            return fail(ctx, HCAO_EINVAL, "load_particles: species out of range");
+        const HostSpecies& s = ctx->sp[species[i]];
+        for (int j = 0; j < 16; ++j) {
+            const int q = qn[16 * i + j];
+            if (j < s.n_modes ? q >= (int)s.lev[j].size() : q != 0)
+                return fail(ctx, HCAO_ELEVEL_OVERFLOW, "load_particles: quantum number outside the level list");
+        }
+        present[species[i]] = true;
+        counts[cell[i]]++;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (r->recs) {
+        cudaFreeAsync(r->recs, ctx->stream);
+        r->recs = nullptr;
+    }
+    // capacities and slot bases
+    const double f = ctx->cfg.capacity_factor;
+    std::vector<DevCell> cells(r->n_cells);
+    std::vector<uint64_t> slot0(r->n_cells);
+    uint64_t tot = 0;
+    double mx = 0.0;
+    for (int a = 0; a < ctx->n_species; ++a)
+        for (int b = 0; b < ctx->n_species; ++b)
+            if (present[a] && present[b]) {
+                const double m = mean_sigma_g(ctx, a, b, r->T_sgmax);
+                if (m > mx) mx = m;
+            }
+    for (int c = 0; c < r->n_cells; ++c) {
+        uint64_t cap = (uint64_t)std::ceil(counts[c] * f) + (uint64_t)ctx->cfg.capacity_extra;
+        cap = (cap + 7) & ~(uint64_t)7;
+        slot0[c] = tot;
+        tot += cap;
+        DevCell& d = cells[c];
+        std::memset(&d, 0, sizeof d);
+        d.n = counts[c];
+        d.cap = (uint32_t)cap;
+        d.res = (uint32_t)id;
+        d.lcell = (uint32_t)c;
+        d.sgmax = 2.0 * mx;  // reading A10: 2 <sigma_T g>(T_sgmax), largest pair present
+    }
+    const size_t rs = rec_size(ctx);
+    r->total_cap = tot;
+    r->rec_bytes = (size_t)tot * rs;
+    CU(cudaMallocAsync(&r->recs, std::max<size_t>(r->rec_bytes, 64), ctx->stream));
+    CU(cudaMemsetAsync(r->recs, 0, std::max<size_t>(r->rec_bytes, 64), ctx->stream));
+    for (int c = 0; c < r->n_cells; ++c)
+        cells[c].rec = static_cast<char*>(r->recs) + slot0[c] * rs;
+    if (n > 0) {
+        // stage the host arrays, sort by cell on the device, scatter into the cells
+        double* dv = nullptr;
+        uint8_t* dq = nullptr;
+        int32_t* ds = nullptr;
+        uint32_t *dk = nullptr, *dperm = nullptr, *doff = nullptr;
+        uint64_t* dslot = nullptr;
+        CU(dalloc(ctx, &dv, (size_t)n * 3));
+        CU(dalloc(ctx, &dq, (size_t)n * 16));
+        CU(dalloc(ctx, &ds, (size_t)n));
+        CU(dalloc(ctx, &dk, (size_t)n));
+        CU(dalloc(ctx, &dperm, (size_t)n));
+        CU(dalloc(ctx, &doff, (size_t)r->n_cells + 1));
+        CU(dalloc(ctx, &dslot, (size_t)r->n_cells));
+        CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dslot, slot0.data(), sizeof(uint64_t) * r->n_cells, cudaMemcpyHostToDevice, ctx->stream));
+        hcao_status st = hcao_cell_sort(ctx, dk, n, (uint32_t)r->n_cells, dperm, doff);
+        if (st != HCAO_OK) return st;
+        if (ctx->cfg.precision == HCAO_FP64)
+            launch_scatter_load<double>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
+        else
+            launch_scatter_load<float>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
+        ctx->launches++;
+        CU(cudaGetLastError());
+        dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dk);
+        dfree(ctx, dperm); dfree(ctx, doff); dfree(ctx, dslot);
+    }
+    r->loaded = true;
+    hcao_status st = relayout(ctx, id, &cells);
+    if (st != HCAO_OK) return st;
+    DevRes dr{};
+    dr.seed = r->seed;
+    dr.step = 0;
+    dr.active = 1;
+    dr.w = r->w;
+    dr.dt = r->dt;
+    dr.Vc = r->Vc;
+    CU(cudaMemcpyAsync(ctx->d_res + id, &dr, sizeof dr, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
+    if (!ctx) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "init_vibration: no loaded reservoir");
+    if (!(T > 0)) return fail(ctx, HCAO_EINVAL, "init_vibration: T_vib must be > 0");
+    // bends: thresholds exp(-k Theta / T), k = 1..L (i >= k <=> u <= threshold);
+    // stretches: acceptance exp(-(E_i - E_0)/(k T)) per level (Eq. accept-quant)
+    std::vector<double> bt, sa;
+    std::vector<int> off(MAXS * MAXM, 0);
+    for (int s = 0; s < ctx->n_species; ++s) {
+        const HostSpecies& S = ctx->sp[s];
+        for (int j = 0; j < S.n_modes; ++j) {
+            if (S.bend[j]) {
+                off[s * MAXM + j] = (int)bt.size();
+                const double th = S.theta[j - S.d.n_stretch];
+                for (size_t k = 1; k <= S.lev[j].size(); ++k) bt.push_back(std::exp(-(double)k * th / T));
+            } else {
+                off[s * MAXM + j] = (int)sa.size();
+                for (double Ei : S.lev[j]) sa.push_back(std::exp(-(Ei - S.lev[j][0]) / (KB * T)));
+            }
+        }
+    }
+    double *dbt = nullptr, *dsa = nullptr;
+    int* doff = nullptr;
+    CU(dalloc(ctx, &dbt, bt.size()));
+    CU(dalloc(ctx, &dsa, sa.size()));
+    CU(dalloc(ctx, &doff, off.size()));
+    if (!bt.empty()) CU(cudaMemcpyAsync(dbt, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (!sa.empty()) CU(cudaMemcpyAsync(dsa, sa.data(), sizeof(double) * sa.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_init_vib<double>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_res, id, ctx->d_consts, dbt, dsa, doff,
+                                ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+    else
+        launch_init_vib<float>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_res, id, ctx->d_consts, dbt, dsa, doff,
+                               ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    dfree(ctx, dbt);
+    dfree(ctx, dsa);
+    dfree(ctx, doff);
+    return map_err(ctx);
+}
+
+hcao_status hcao_set_log(hcao_ctx* ctx, int enable) {
+    if (!ctx) return HCAO_EINVAL;
+    ctx->log_on = enable != 0;
+    if (ctx->log_on && !ctx->d_log && ctx->pair_cap > 0) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+    return HCAO_OK;
+}
+
+hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
+    if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
+    if (ctx->n_cells_total == 0 || n_steps == 0) return HCAO_OK;
+    if (ctx->log_on && !ctx->d_log) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+    StepArgs a = make_args(ctx);
+    const int block = 128;
+    const int grid = ctx->sm_count * 8;
+    const bool f64 = ctx->cfg.precision == HCAO_FP64;
+    for (int s = 0; s < n_steps; ++s) {
+        if (!ctx->prof_on) {
+            if (f64) launch_step<double>(a, grid, block, ctx->stream, &ctx->launches);
+            else launch_step<float>(a, grid, block, ctx->stream, &ctx->launches);
+            continue;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const int reps = k == 1 ? a.max_rounds : 1;
+            for (int r = 0; r < reps; ++r) {
+                auto& pool = ctx->prof_ev[k];
+                if (ctx->prof_used[k] == pool.size()) {
+                    cudaEvent_t e0, e1;
+                    CU(cudaEventCreate(&e0));
+                    CU(cudaEventCreate(&e1));
+                    pool.emplace_back(e0, e1);
+                }
+                auto& ev = pool[ctx->prof_used[k]++];
+                CU(cudaEventRecord(ev.first, ctx->stream));
+                if (k == 0) launch_setup(a, ctx->stream);
+                else if (k == 1) {
+                    if (f64) launch_collide<double>(a, r, grid, block, ctx->stream);
+                    else launch_collide<float>(a, r, grid, block, ctx->stream);
+                } else {
+                    if (f64) launch_finish<double>(a, ctx->stream);
+                    else launch_finish<float>(a, ctx->stream);
+                }
+                CU(cudaEventRecord(ev.second, ctx->stream));
+                ctx->launches++;
+            }
+        }
+    }
+    CU(cudaGetLastError());
+    return HCAO_OK;
+}
+
+hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable) {
+    if (!ctx) return HCAO_EINVAL;
+    ctx->prof_on = enable != 0;
+    for (int k = 0; k < 3; ++k) {
+        ctx->prof_used[k] = 0;
+        ctx->prof_ms[k] = 0.0;
+        ctx->prof_n[k] = 0;
+    }
+    return HCAO_OK;
+}
+
+hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int max, int* n_out) {
+    if (!ctx || !ms || !launches || max < 1) return HCAO_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 3; ++k) {
+        for (size_t i = 0; i < ctx->prof_used[k]; ++i) {
+            float t = 0.0f;
+            CU(cudaEventElapsedTime(&t, ctx->prof_ev[k][i].first, ctx->prof_ev[k][i].second));
+            ctx->prof_ms[k] += t;
+            ctx->prof_n[k]++;
+        }
+        ctx->prof_used[k] = 0;
+    }
+    const int n = std::min(max, 3);
+    for (int k = 0; k < n; ++k) {
+        ms[k] = ctx->prof_ms[k];
+        launches[k] = ctx->prof_n[k];
+    }
+    if (n_out) *n_out = n;
+    return HCAO_OK;
+}
+
+hcao_status hcao_sync(hcao_ctx* ctx) {
+    if (!ctx) return HCAO_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return map_err(ctx);
+}
+
+hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
+    if (!ctx || !n) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r) return fail(ctx, HCAO_ENOTFOUND, "count: no such reservoir");
+    *n = 0;
+    if (!r->loaded) return HCAO_OK;
+    std::vector<DevCell> cells;
+    hcao_status st = read_cells(ctx, *r, cells);
+    if (st != HCAO_OK) return st;
+    for (auto& c : cells) *n += c.n;
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, int32_t* species, int32_t* cell) {
+    if (!ctx) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_particles: no loaded reservoir");
+    std::vector<DevCell> cells;
+    hcao_status st = read_cells(ctx, *r, cells);
+    if (st != HCAO_OK) return st;
+    std::vector<uint64_t> off(r->n_cells);
+    uint64_t n = 0;
+    for (int c = 0; c < r->n_cells; ++c) {
+        off[c] = n;
+        n += cells[c].n;
+    }
+    if (n == 0) return map_err(ctx);
+    double* dv = nullptr;
+    uint8_t* dq = nullptr;
+    int32_t *ds = nullptr, *dc = nullptr;
+    uint64_t* doff = nullptr;
+    CU(dalloc(ctx, &dv, (size_t)n * 3));
+    CU(dalloc(ctx, &dq, (size_t)n * 16));
+    CU(dalloc(ctx, &ds, (size_t)n));
+    CU(dalloc(ctx, &dc, (size_t)n));
+    CU(dalloc(ctx, &doff, (size_t)r->n_cells));
+    CU(cudaMemcpyAsync(doff, off.data(), sizeof(uint64_t) * r->n_cells, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff, dv, dq, ds, dc, ctx->stream);
+    else
+        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff, dv, dq, ds, dc, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    if (v) CU(cudaMemcpyAsync(v, dv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (qn) CU(cudaMemcpyAsync(qn, dq, (size_t)16 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (species) CU(cudaMemcpyAsync(species, ds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cell) CU(cudaMemcpyAsync(cell, dc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dc); dfree(ctx, doff);
+    CU(cudaStreamSynchronize(ctx->stream));
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
+    if (!ctx || !out) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_moments: no loaded reservoir");
+    double* dacc = nullptr;
+    unsigned long long* dcnt = nullptr;
+    CU(dalloc(ctx, &dacc, 5 + MAXS));
+    CU(dalloc(ctx, &dcnt, MAXS));
+    CU(cudaMemsetAsync(dacc, 0, sizeof(double) * (5 + MAXS), ctx->stream));
+    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_consts, ctx->d_lev64, dacc, dcnt, ctx->stream);
+    else
+        launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_consts, ctx->d_lev64, dacc, dcnt, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    double acc[5 + MAXS];
+    unsigned long long cnt[MAXS];
+    CU(cudaMemcpyAsync(acc, dacc, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(cnt, dcnt, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, dacc);
+    dfree(ctx, dcnt);
+    std::memset(out, 0, sizeof *out);
+    double M = 0.0;
+    int64_t N = 0;
+    for (int s = 0; s < MAXS; ++s) {
+        out->n[s] = (int64_t)cnt[s];
+        N += out->n[s];
+        if (s < ctx->n_species) M += ctx->sp[s].d.mass * (double)cnt[s];
+    }
+    for (int d = 0; d < 3; ++d) out->momentum[d] = acc[d];
+    out->E_tr = acc[3];
+    out->E_form = acc[4];
+    for (int s = 0; s < MAXS; ++s) out->E_vib[s] = acc[5 + s];
+    if (N > 0 && M > 0) {
+        const double p2 = acc[0] * acc[0] + acc[1] * acc[1] + acc[2] * acc[2];
+        out->T_tr = 2.0 / 3.0 * (acc[3] - 0.5 * p2 / M) / ((double)N * KB);
+    }
+    for (int s = 0; s < ctx->n_species; ++s)
+        if (cnt[s] > 0 && ctx->sp[s].n_modes > 0)
+            out->T_vib[s] = tvib_host(ctx->sp[s], acc[5 + s] / (double)cnt[s] - ctx->sp[s].zpe);
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode, uint64_t* counts, int max_levels) {
+    if (!ctx || !counts || max_levels < 1) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_level_populations: no loaded reservoir");
+    if (sp < 0 || sp >= ctx->n_species || mode < 0 || mode >= ctx->sp[sp].n_modes)
+        return fail(ctx, HCAO_EINVAL, "read_level_populations: bad species or mode");
+    unsigned long long* dh = nullptr;
+    CU(dalloc(ctx, &dh, MAXL));
+    CU(cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * MAXL, ctx->stream));
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_levelpop<double>(ctx->d_cells, r->cell0, r->n_cells, sp, mode, dh, ctx->stream);
+    else
+        launch_levelpop<float>(ctx->d_cells, r->cell0, r->n_cells, sp, mode, dh, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    unsigned long long h[MAXL];
+    CU(cudaMemcpyAsync(h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, dh);
+    for (int i = 0; i < max_levels; ++i) counts[i] = i < MAXL ? (uint64_t)h[i] : 0;
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_counters(hcao_ctx* ctx, int id, uint64_t* out, int max, int* n_out) {
+    if (!ctx || !out || max < 1) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_counters: no loaded reservoir");
+    std::vector<unsigned long long> h((size_t)r->n_cells * NCNT);
+    CU(cudaMemcpyAsync(h.data(), ctx->d_cellcnt + (size_t)r->cell0 * NCNT, sizeof(unsigned long long) * h.size(),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    DevRes dr{};
+    CU(cudaMemcpyAsync(&dr, ctx->d_res + id, sizeof dr, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int n = std::min(max, 8 + ctx->n_reactions);
+    for (int i = 0; i < n; ++i) {
+        uint64_t s = 0;
+        for (int c = 0; c < r->n_cells; ++c) s += h[(size_t)c * NCNT + i];
+        out[i] = s;
+    }
+    if (n > CNT_STEPS) out[CNT_STEPS] = dr.step;
+    if (n_out) *n_out = n;
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_reaction_counts(hcao_ctx* ctx, int id, uint64_t* out, int n) {
+    if (!ctx || !out || n < 0) return HCAO_EINVAL;
+    uint64_t buf[8 + MAXR];
+    int got = 0;
+    hcao_status st = hcao_read_counters(ctx, id, buf, 8 + MAXR, &got);
+    if (st != HCAO_OK) return st;
+    for (int i = 0; i < n; ++i) out[i] = (8 + i < got) ? buf[8 + i] : 0;
+    return HCAO_OK;
+}
+
+hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int id, double* out) {
+    if (!ctx || !out) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_cell_sgmax: no loaded reservoir");
+    std::vector<DevCell> cells;
+    hcao_status st = read_cells(ctx, *r, cells);
+    if (st != HCAO_OK) return st;
+    for (int c = 0; c < r->n_cells; ++c) out[c] = cells[c].sgmax;
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* out, int64_t max, int64_t* n_out) {
+    if (!ctx || !n_out) return HCAO_EINVAL;
+    *n_out = 0;
+    if (!ctx->log_on || !ctx->d_log) return fail(ctx, HCAO_EINVAL, "read_log: logging is off");
+    uint32_t tot[MAX_ROUNDS + 1];
+    CU(cudaMemcpyAsync(tot, ctx->d_totals, sizeof tot, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int64_t n = out ? std::min<int64_t>(max, tot[MAX_ROUNDS]) : (int64_t)tot[MAX_ROUNDS];
+    if (n > 0 && out)
+        CU(cudaMemcpyAsync(out, ctx->d_log, sizeof(hcao_log_rec) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *n_out = n;
+    return map_err(ctx);
+}
+
+hcao_status hcao_level_energy(const hcao_ctx* ctx, int sp, int mode, int level, double* out) {
+    if (!ctx || !out || sp < 0 || sp >= ctx->n_species || mode < 0 || mode >= ctx->sp[sp].n_modes ||
+        level < 0 || level >= (int)ctx->sp[sp].lev[mode].size())
+        return HCAO_EINVAL;
+    *out = ctx->sp[sp].lev[mode][level];
+    return HCAO_OK;
+}
+
+hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out) {
+    if (!ctx || !out || sp < 0 || sp >= ctx->n_species || mode < 0 || mode >= ctx->sp[sp].n_modes)
+        return HCAO_EINVAL;
+    *out = (int)ctx->sp[sp].lev[mode].size();
+    return HCAO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// hcao_internal.h -- data layout shared by the host side and the kernels of
+// libhcao.  Particle state lives in HBM as one fixed-size record per particle,
+// grouped cell by cell (each cell owns a contiguous run of slots), so that the
+// two members of a candidate pair are fetched with 128-bit loads and a cell's
+// pairs touch one contiguous region.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hcao.h"
+
+namespace hcao {
+
+constexpr int MAXM = 16;        // vibrational modes per species
+constexpr int MAXS = 16;        // species
+constexpr int MAXR = 8;         // reactions
+constexpr int MAXL = 256;       // levels per mode (quantum numbers are bytes)
+constexpr int TABLE_PAD = 17;   // grid entries beyond M (one per mode + 1)
+constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard cap)
+
+// Philox stream purposes: counter word 3 = purpose << 24 | block index.
+enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
+       PU_INIT = 7 };
+
+// per-reservoir counters
+enum { CNT_CAND = 0, CNT_ACC, CNT_SAMPLES, CNT_TRIALS, CNT_OVER, CNT_DEGEN, CNT_NOTEXEC,
+       CNT_STEPS, CNT_RX0 = 8, NCNT = 8 + MAXR };
+
+// sticky device error bits
+enum { ERR_REJECT = 1, ERR_CAPACITY = 2, ERR_ROUNDS = 4, ERR_LEVEL = 8 };
+
+constexpr uint32_t SPECIES_NONE = 0xFFu;
+
+// Particle records.  FP32: 32 bytes (one sector); FP64: 64 bytes (two sectors).
+struct alignas(16) RecF {
+    float v[3];
+    uint32_t meta;        // species in bits 0..7
+    uint32_t q[4];        // quantum numbers, mode j in byte j
+};
+struct alignas(16) RecD {
+    double v[3];
+    uint32_t meta;
+    uint32_t pad;
+    uint32_t q[4];
+    uint32_t pad2[4];
+};
+static_assert(sizeof(RecF) == 32, "RecF layout");
+static_assert(sizeof(RecD) == 64, "RecD layout");
+
+struct DevSpecies {
+    double mass, E_form, zpe, top;   // top: highest collision energy the sampler covers
+    double De[MAXM];                 // Morse De per stretch
+    double base[MAXM + 1];           // K5 grid base per table (sum of ground levels k..n-1)
+    double cq, inv_cq;               // quadratic grid g_m = base_k + cq m^2
+    double eps_min;                  // smallest single-quantum excitation
+    float base_f[MAXM + 1];
+    float cq_f, inv_cq_f, eps_min_f, pad_f;
+    int n_modes, n_stretch, MT, M;
+    int lev_off[MAXM];               // offset of mode j's levels in the level arrays
+    int n_lev[MAXM];
+    int tab_off;                     // offset of table 0; table k at tab_off + k * MT
+    int pad[3];
+};
+
+struct DevPair {
+    double mr, C, mt, fp, fq;        // reduced mass, VHS constant, total mass, velocity shares
+    float mr_f, C_f, fp_f, fq_f;
+};
+
+struct DevReaction {
+    int type, A, B, P0, P1;
+    uint32_t mask;
+    int alpha_mode;
+    int pad;
+    double Ea, steric, zpesum, dEf;
+    double alpha[MAXM];
+};
+
+struct Consts {
+    int n_species, n_reactions, amode, creates;
+    DevSpecies sp[MAXS];
+    DevPair pair[MAXS * MAXS];
+    DevReaction rx[MAXR];
+};
+
+struct DevCell {
+    void* rec;                        // first record of the cell
+    uint32_t n, cap;                  // particles at step start, slots
+    uint32_t res, lcell;              // reservoir slot, reservoir-local cell index
+    double sgmax;                     // (sigma_T g)_max
+    unsigned long long seen;          // max sigma_T g of this step (bits of a double >= 0)
+    uint32_t nsel, ncreated;
+    uint32_t fkey[MAX_ROUNDS][4];     // Feistel keys per round of this step
+};
+
+struct DevRes {
+    uint64_t seed;
+    uint32_t step;
+    uint32_t active;
+    double w, dt, Vc;
+};
+
+struct StepArgs {
+    const Consts* C;
+    const double* lev64;
+    const float* lev32;
+    const double* H64;
+    const float* H32;
+    DevCell* cells;
+    int n_cells;
+    DevRes* res;
+    int n_res;
+    unsigned long long* counters;   // [n_res][NCNT]
+    uint32_t* pbase;                // [MAX_ROUNDS][n_cells + 1]: round-r pair prefix
+    uint32_t* abase;                // [n_cells + 1]: all-round pair prefix
+    uint32_t* totals;               // [MAX_ROUNDS + 1]
+    uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
+    void* cscratch;                 // per-pair record of a particle created by a reaction
+    uint64_t pair_cap;              // capacity of cflag / log
+    hcao_log_rec* log;
+    int log_on;
+    uint32_t* err;
+    int max_rounds;
+    uint32_t reject_cap;
+};
+
+// launchers, one instantiation per precision (hcao_f64.cu / hcao_f32.cu)
+template <class R> struct RecOf;
+template <> struct RecOf<float> { using T = RecF; };
+template <> struct RecOf<double> { using T = RecD; };
+
+template <class R> void launch_step(const StepArgs& a, int grid_collide, int block_collide,
+                                    cudaStream_t s, uint64_t* launches);
+void launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu)
+template <class R> void launch_collide(const StepArgs& a, int r, int grid, int block, cudaStream_t s);
+template <class R> void launch_finish(const StepArgs& a, cudaStream_t s);
+template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm,
+                                            const uint32_t* offsets, const uint64_t* cell_slot0,
+                                            int n_cells, const double* v, const uint8_t* qn,
+                                            const int32_t* sp, int64_t n, cudaStream_t s);
+template <class R> void launch_pack(const DevCell* cells, int cell0, int n_cells,
+                                    const uint64_t* out_off, double* v, uint8_t* qn, int32_t* sp,
+                                    int32_t* cell, cudaStream_t s);
+template <class R> void launch_init_vib(const DevCell* cells, int cell0, int n_cells,
+                                        const DevRes* res, int res_slot, const Consts* C,
+                                        const double* bend_thr, const double* str_acc,
+                                        const int* thr_off, uint32_t reject_cap, uint32_t* err,
+                                        cudaStream_t s);
+template <class R> void launch_moments(const DevCell* cells, int cell0, int n_cells,
+                                       const Consts* C, const double* lev64, double* acc,
+                                       unsigned long long* cnt, cudaStream_t s);
+template <class R> void launch_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
+                                        int mode, unsigned long long* hist, cudaStream_t s);
+
+}  // namespace hcao

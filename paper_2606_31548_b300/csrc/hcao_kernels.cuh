@@ -1,0 +1,1163 @@
+// hcao_kernels.cuh -- the collision-phase kernels of libhcao (sm_103a).
+//
+// One step of the DSMC collision phase, per reservoir cell:
+//   k_setup   (1 CTA)   NTC candidate count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c
+//                       with stochastic rounding, Feistel keys per pairing round,
+//                       block-wide scans that give every candidate pair a flat index.
+//   k_collide (grid)    one thread per candidate pair: Feistel pair draw, VHS
+//                       acceptance, QK reaction test (Eq. Ecoll-diss, Eq.
+//                       Ecoll-exch, competing reactions), reaction execution or
+//                       HCAO Larsen-Borgnakke relaxation of both molecules (the
+//                       joint acceptance of all modes, sampled exactly with the
+//                       K5 tables), isotropic VHS scattering.
+//   k_finish  (warp/cell) (sigma g)_max update, per-cell counters, stable append
+//                       of particles created by dissociation, step counter.
+// Randomness: Philox4x32-10 keyed by the reservoir seed, counter
+// (step, cell, round<<24 | pair, purpose<<24 | block): draws do not depend on
+// launch geometry, so results are identical for any grid or batching.
+//
+// Template parameter R: double = FP64 parity mode (the translation unit is
+// compiled without FMA contraction; every expression follows the documented
+// operation order), float = FP32 mode (velocities, relative speeds and the
+// sampler in FP32; energies, reaction thresholds and reductions in FP64).
+#pragma once
+#include <cstdint>
+#include <type_traits>
+
+#include "hcao_internal.h"
+
+namespace hcao {
+
+// ------------------------------------------------------------- arithmetic
+// Round-to-nearest intrinsics never contract into FMA: the sampler and its
+// host-built tables then see bit-identical arithmetic in either precision.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float ceil_r(float a) { return ceilf(a); }
+__device__ __forceinline__ double ceil_r(double a) { return ceil(a); }
+
+// (E_coll - sum E)^(xi_rel/2 - 1), xi_rel = 5 - 2 omega: exponent 3/4, 1, 1/2
+template <class R>
+__device__ __forceinline__ R lb_pow(int amode, R x) {
+    if (amode == 0) {
+        R s = sqrt_rn(x);
+        return mul_rn(s, sqrt_rn(s));
+    }
+    if (amode == 1) return x;
+    return sqrt_rn(x);
+}
+
+// ------------------------------------------------------------- Philox4x32-10
+__device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                         uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+        uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        uint32_t n0 = hi1 ^ x1 ^ k0;
+        uint32_t n2 = hi0 ^ x3 ^ k1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+    }
+}
+
+// A counter-based stream: uniform number j uses words 2(j%2), 2(j%2)+1 of block j/2.
+struct Stream {
+    uint32_t k0, k1, c0, c1, c2, c3;
+    uint32_t blk;
+    uint32_t w0, w1, w2, w3;
+    int half;
+};
+__device__ __forceinline__ void st_init(Stream& s, uint64_t seed, uint32_t c0, uint32_t c1,
+                                        uint32_t c2, uint32_t purpose) {
+    s.k0 = (uint32_t)seed; s.k1 = (uint32_t)(seed >> 32);
+    s.c0 = c0; s.c1 = c1; s.c2 = c2; s.c3 = purpose << 24;
+    s.blk = 0; s.half = 2;
+}
+__device__ __forceinline__ void st_block(Stream& s) {
+    s.w0 = s.c0; s.w1 = s.c1; s.w2 = s.c2; s.w3 = s.c3 | (s.blk & 0xFFFFFFu);
+    philox10(s.w0, s.w1, s.w2, s.w3, s.k0, s.k1);
+    s.blk++;
+}
+__device__ __forceinline__ void st_pair(Stream& s, uint32_t& a, uint32_t& b) {
+    if (s.half == 2) { st_block(s); s.half = 0; }
+    if (s.half == 0) { a = s.w0; b = s.w1; s.half = 1; }
+    else { a = s.w2; b = s.w3; s.half = 2; }
+}
+// FP64 uniform: (27 bits of a, 26 bits of b) * 2^-53; FP32 uniform: 24 bits of a * 2^-24
+__device__ __forceinline__ double st_u64(Stream& s) {
+    uint32_t a, b;
+    st_pair(s, a, b);
+    uint64_t m = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
+    return (double)m * 0x1p-53;
+}
+__device__ __forceinline__ float st_u32(Stream& s) {
+    uint32_t a, b;
+    st_pair(s, a, b);
+    return (float)(a >> 8) * 0x1p-24f;
+}
+template <class R> __device__ __forceinline__ R st_uni(Stream& s);
+template <> __device__ __forceinline__ double st_uni<double>(Stream& s) { return st_u64(s); }
+template <> __device__ __forceinline__ float st_uni<float>(Stream& s) { return st_u32(s); }
+
+// ------------------------------------------------------------- Feistel pairing
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
+    return h;
+}
+// keyed bijection of [0,N): 4-round balanced Feistel on the smallest even bit
+// width covering N, cycle-walked into range
+__device__ __forceinline__ uint32_t feistel(uint32_t x, uint32_t N, const uint32_t key[4]) {
+    int b = 2;
+    while (((uint64_t)1 << b) < (uint64_t)N) b += 2;
+    int half = b >> 1;
+    uint32_t mask = (uint32_t)(((uint64_t)1 << half) - 1);
+    for (int walk = 0; walk < (1 << 20); ++walk) {
+        uint32_t L = x >> half, Rr = x & mask;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            uint32_t nR = L ^ (fmix32(Rr ^ key[r]) & mask);
+            L = Rr; Rr = nR;
+        }
+        x = (L << half) | Rr;
+        if (x < N) return x;
+    }
+    return 0;  // unreachable: a cycle through x < N returns to [0,N)
+}
+
+// ------------------------------------------------------------- quantum numbers
+__device__ __forceinline__ uint32_t get_q(const uint32_t q[4], int j) {
+    uint32_t w = j < 4 ? q[0] : (j < 8 ? q[1] : (j < 12 ? q[2] : q[3]));
+    return (w >> ((j & 3) * 8)) & 0xFFu;
+}
+__device__ __forceinline__ void set_q(uint32_t q[4], int j, uint32_t v) {
+    uint32_t sh = (uint32_t)(j & 3) * 8u;
+    uint32_t m = ~(0xFFu << sh), val = v << sh;
+    switch (j >> 2) {
+        case 0: q[0] = (q[0] & m) | val; break;
+        case 1: q[1] = (q[1] & m) | val; break;
+        case 2: q[2] = (q[2] & m) | val; break;
+        default: q[3] = (q[3] & m) | val; break;
+    }
+}
+
+// ------------------------------------------------------------- records
+__device__ __forceinline__ void load_rec(const RecF* p, RecF& r) {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4 a = s[0], b = s[1];
+    r.v[0] = __uint_as_float(a.x); r.v[1] = __uint_as_float(a.y); r.v[2] = __uint_as_float(a.z);
+    r.meta = a.w;
+    r.q[0] = b.x; r.q[1] = b.y; r.q[2] = b.z; r.q[3] = b.w;
+}
+__device__ __forceinline__ void store_rec(RecF* p, const RecF& r) {
+    uint4* d = reinterpret_cast<uint4*>(p);
+    d[0] = make_uint4(__float_as_uint(r.v[0]), __float_as_uint(r.v[1]), __float_as_uint(r.v[2]), r.meta);
+    d[1] = make_uint4(r.q[0], r.q[1], r.q[2], r.q[3]);
+}
+__device__ __forceinline__ void load_rec(const RecD* p, RecD& r) {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4 a = s[0], b = s[1], c = s[2];
+    r.v[0] = __hiloint2double((int)a.y, (int)a.x);
+    r.v[1] = __hiloint2double((int)a.w, (int)a.z);
+    r.v[2] = __hiloint2double((int)b.y, (int)b.x);
+    r.meta = b.z; r.pad = 0;
+    r.q[0] = c.x; r.q[1] = c.y; r.q[2] = c.z; r.q[3] = c.w;
+}
+__device__ __forceinline__ void store_rec(RecD* p, const RecD& r) {
+    uint4* d = reinterpret_cast<uint4*>(p);
+    unsigned long long v0 = __double_as_longlong(r.v[0]), v1 = __double_as_longlong(r.v[1]),
+                       v2 = __double_as_longlong(r.v[2]);
+    d[0] = make_uint4((uint32_t)v0, (uint32_t)(v0 >> 32), (uint32_t)v1, (uint32_t)(v1 >> 32));
+    d[1] = make_uint4((uint32_t)v2, (uint32_t)(v2 >> 32), r.meta, 0u);
+    d[2] = make_uint4(r.q[0], r.q[1], r.q[2], r.q[3]);
+}
+
+// ------------------------------------------------------------- tables
+template <class R> __device__ __forceinline__ const R* lev_tab(const StepArgs& A);
+template <> __device__ __forceinline__ const double* lev_tab<double>(const StepArgs& A) { return A.lev64; }
+template <> __device__ __forceinline__ const float* lev_tab<float>(const StepArgs& A) { return A.lev32; }
+template <class R> __device__ __forceinline__ const R* h_tab(const StepArgs& A);
+template <> __device__ __forceinline__ const double* h_tab<double>(const StepArgs& A) { return A.H64; }
+template <> __device__ __forceinline__ const float* h_tab<float>(const StepArgs& A) { return A.H32; }
+template <class R> __device__ __forceinline__ R sp_base(const DevSpecies& S, int k);
+template <> __device__ __forceinline__ double sp_base<double>(const DevSpecies& S, int k) { return S.base[k]; }
+template <> __device__ __forceinline__ float sp_base<float>(const DevSpecies& S, int k) { return S.base_f[k]; }
+template <class R> __device__ __forceinline__ R sp_cq(const DevSpecies& S);
+template <> __device__ __forceinline__ double sp_cq<double>(const DevSpecies& S) { return S.cq; }
+template <> __device__ __forceinline__ float sp_cq<float>(const DevSpecies& S) { return S.cq_f; }
+template <class R> __device__ __forceinline__ R sp_inv(const DevSpecies& S);
+template <> __device__ __forceinline__ double sp_inv<double>(const DevSpecies& S) { return S.inv_cq; }
+template <> __device__ __forceinline__ float sp_inv<float>(const DevSpecies& S) { return S.inv_cq_f; }
+template <class R> __device__ __forceinline__ R sp_eps(const DevSpecies& S);
+template <> __device__ __forceinline__ double sp_eps<double>(const DevSpecies& S) { return S.eps_min; }
+template <> __device__ __forceinline__ float sp_eps<float>(const DevSpecies& S) { return S.eps_min_f; }
+
+// quadratic grid point g_m = base + cq m^2 (m^2 exact in either precision)
+template <class R>
+__device__ __forceinline__ R grid_pt(R base, R cq, int m) {
+    return add_rn(base, mul_rn(cq, (R)(m * m)));
+}
+// smallest m in [1, MT) with g_m >= E; 0 if E <= base; MT if no grid point
+// reaches E.  The candidate from sqrt is corrected against the grid points,
+// so the result is the exact function the host tables were built with.
+template <class R>
+__device__ __forceinline__ int grid_idx(R base, R cq, R inv, int MT, R E) {
+    if (!(E > base)) return 0;
+    const float t = (float)mul_rn(sub_rn(E, base), inv);
+    int m;
+    if (!(t < (float)MT * (float)MT)) m = MT - 1;
+    else {
+        m = (int)ceilf(sqrtf(t));
+        m = m < 1 ? 1 : (m > MT - 1 ? MT - 1 : m);
+    }
+    for (int it = 0; it < 64 && m > 1 && !(grid_pt<R>(base, cq, m - 1) < E); ++it) m--;
+    for (int it = 0; it < 64 && grid_pt<R>(base, cq, m) < E; ++it) {
+        if (m == MT - 1) return MT;
+        m++;
+    }
+    return m;
+}
+
+__device__ __forceinline__ double evib64(const double* lev, const DevSpecies& S, const uint32_t q[4]) {
+    double e = 0.0;
+    for (int j = 0; j < S.n_modes; ++j) e = e + __ldg(lev + S.lev_off[j] + get_q(q, j));
+    return e;
+}
+
+enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
+
+// Post-collision vibrational state of one molecule at collision energy Ec:
+// p(i) ~ (Ec - sum_j E_j(i_j))^(xi_rel/2-1) over states with sum E < Ec (the
+// joint LB acceptance of all local modes).  Sequential draw through the H_k
+// tables; a draw running past the end of a mode's levels restarts the trial.
+// Every accepted state has probability lb_pow(..)/H_0: the target, exactly.
+template <class R>
+__device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, double Ec_d,
+                         Stream& st, uint32_t q[4], uint32_t& trials) {
+    const int n = S.n_modes;
+    if (n == 0) return S_OK;
+    const R* L = lev_tab<R>(A);
+    const R* H = h_tab<R>(A) + S.tab_off;
+    const R cq = sp_cq<R>(S), inv = sp_inv<R>(S);
+    const int MT = S.MT;
+    const R Ec = (R)Ec_d;
+    const R b0 = sp_base<R>(S, 0);
+    const int m0 = grid_idx<R>(b0, cq, inv, MT, Ec);
+    if (m0 > S.M) return S_OVER;
+    if (m0 == 0) return S_DEGEN;
+    const R h0 = __ldg(H + m0);
+    if (!(h0 > (R)0)) return S_DEGEN;
+    // below the smallest single-quantum excitation only the ground state fits
+    if (sub_rn(Ec, b0) < sp_eps<R>(S)) {
+        q[0] = 0u; q[1] = 0u; q[2] = 0u; q[3] = 0u;
+        return S_OK;
+    }
+    for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
+        trials++;
+        uint32_t nq[4] = {0u, 0u, 0u, 0u};
+        R E = Ec;
+        bool ok = true;
+        for (int k = 0; k < n; ++k) {
+            int m = (k == 0) ? m0 : grid_idx<R>(sp_base<R>(S, k), cq, inv, MT, E);
+            if (m > MT - 1) {  // cannot happen for budgets below the table top
+                m = MT - 1;
+                atomicOr(A.err, (uint32_t)ERR_LEVEL);
+            }
+            const R u = st_uni<R>(st);
+            const R t = mul_rn(u, __ldg(H + k * MT + m));
+            const R* Lk = L + S.lev_off[k];
+            const int nl = S.n_lev[k];
+            const bool last = (k == n - 1);
+            const R bn = last ? (R)0 : sp_base<R>(S, k + 1);
+            const R* Hn = H + (k + 1) * MT;
+            R cum = (R)0;
+            int sel = -1;
+            for (int i = 0; i < nl; ++i) {
+                const R e = __ldg(Lk + i);
+                if (!(e < E)) break;
+                const R x = sub_rn(E, e);
+                R w;
+                if (last) {
+                    w = lb_pow<R>(amode, x);
+                } else {
+                    int mm = grid_idx<R>(bn, cq, inv, MT, x);
+                    if (mm > MT - 1) mm = MT - 1;
+                    w = mm == 0 ? (R)0 : __ldg(Hn + mm);
+                }
+                cum = add_rn(cum, w);
+                if (t < cum) { sel = i; break; }
+            }
+            if (sel < 0) { ok = false; break; }
+            set_q(nq, k, (uint32_t)sel);
+            E = sub_rn(E, __ldg(Lk + sel));
+        }
+        if (ok) {
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            return S_OK;
+        }
+    }
+    return S_CAP;
+}
+
+// Marsaglia (1972): a point uniform in the unit disk mapped onto the sphere
+template <class R>
+__device__ __forceinline__ void iso_dir(Stream& st, R d[3]) {
+    for (int it = 0; it < 4096; ++it) {
+        R x1 = (R)2 * st_uni<R>(st) - (R)1;
+        R x2 = (R)2 * st_uni<R>(st) - (R)1;
+        R s = x1 * x1 + x2 * x2;
+        if (s < (R)1) {
+            R r = (R)2 * sqrt_rn((R)1 - s);
+            d[0] = x1 * r; d[1] = x2 * r; d[2] = (R)1 - (R)2 * s;
+            return;
+        }
+    }
+    d[0] = 0; d[1] = 0; d[2] = 1;
+}
+
+// per-pair event word, reduced per cell by k_finish
+enum : uint32_t {
+    EV_ACC = 1u, EV_CREATED = 2u, EV_RX_SHIFT = 2, /* bits 2..7: reaction + 1 */
+    EV_SAMP_SHIFT = 8, /* bits 8..9 */ EV_OVER_SHIFT = 10, EV_DEGEN_SHIFT = 12,
+    EV_NOTEXEC = 1u << 14, EV_TRIAL_SHIFT = 16
+};
+
+struct PairOut {
+    uint32_t ev;
+    uint32_t trials;
+};
+
+// energy-conserving dissociation A + M -> B + C + M (Sec. "Dissociation
+// reactions"; product split of reading A13).  FP64 arithmetic in both modes.
+template <class R>
+__device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& rx, double vA[3],
+                        double vM[3], int spA, int spM, double EvA, const DevRes& rs, uint32_t lcell,
+                        uint32_t rk, uint32_t qB[4], uint32_t qC[4], double vC[3], PairOut& o) {
+    const DevSpecies& sA = C->sp[spA];
+    const DevSpecies& sM = C->sp[spM];
+    const DevSpecies& sB = C->sp[rx.P0];
+    const DevSpecies& sC = C->sp[rx.P1];
+    const double mA = sA.mass, mM = sM.mass, mB = sB.mass, mC = sC.mass;
+    const double mBC = mB + mC;
+    const double mt = mBC + mM;
+    double V[3];
+    for (int i = 0; i < 3; ++i) V[i] = (mA * vA[i] + mM * vM[i]) / mt;
+    const double vA2 = vA[0] * vA[0] + vA[1] * vA[1] + vA[2] * vA[2];
+    const double vM2 = vM[0] * vM[0] + vM[1] * vM[1] + vM[2] * vM[2];
+    const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const double KEin = 0.5 * mA * vA2 + 0.5 * mM * vM2;
+    const double KEcm = 0.5 * mt * V2;
+    const double Eav = KEin - KEcm + EvA - rx.dEf;
+    if (!(Eav - sB.zpe - sC.zpe > 0.0) || Eav - sC.zpe > sB.top || Eav - sB.zpe > sC.top)
+        return false;
+    Stream sa, sb, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) { qB[j] = 0u; qC[j] = 0u; }
+    uint32_t tr = 0;
+    if (sB.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<R>(A, sB, C->amode, Eav - sC.zpe, sa, qB, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qB[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    const double EvB = evib64(A.lev64, sB, qB);
+    if (sC.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<R>(A, sC, C->amode, Eav - EvB, sb, qC, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qC[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    o.trials += tr;
+    const double EvC = evib64(A.lev64, sC, qC);
+    const double Etr = (Eav - EvB) - EvC;
+    double x = 0.5;
+    for (int it = 0; it < 4096; ++it) {  // Beta(3/2,3/2) by rejection under 1/2
+        x = st_u64(ss);
+        const double y = st_u64(ss);
+        if (y * y * 0.25 < x * (1.0 - x)) break;
+    }
+    const double E1 = x * Etr;
+    const double E2 = Etr - E1;
+    const double mu1 = mB * mC / mBC;
+    const double mu2 = mBC * mM / mt;
+    const double g1 = sqrt(2.0 * E1 / mu1);
+    const double g2 = sqrt(2.0 * E2 / mu2);
+    double d1[3], d2[3];
+    iso_dir<double>(ss, d1);
+    iso_dir<double>(ss, d2);
+    const double fM = mM / mt, fBC = mBC / mt, fC = mC / mBC, fB = mB / mBC;
+    double VBC[3];
+    for (int i = 0; i < 3; ++i) {
+        const double G2 = g2 * d2[i];
+        VBC[i] = V[i] + fM * G2;
+        vM[i] = V[i] - fBC * G2;
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double G1 = g1 * d1[i];
+        vA[i] = VBC[i] + fC * G1;
+        vC[i] = VBC[i] - fB * G1;
+    }
+    return true;
+}
+
+// exchange A + B -> C + D (Sec. "Exchange reactions")
+template <class R>
+__device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& rx, double vA[3],
+                        double vB[3], int spA, int spB, double EvA, double EvB, const DevRes& rs,
+                        uint32_t lcell, uint32_t rk, uint32_t qC[4], uint32_t qD[4], PairOut& o) {
+    const DevSpecies& sA = C->sp[spA];
+    const DevSpecies& sB = C->sp[spB];
+    const DevSpecies& sC = C->sp[rx.P0];
+    const DevSpecies& sD = C->sp[rx.P1];
+    const double mA = sA.mass, mB = sB.mass, mC = sC.mass, mD = sD.mass;
+    const double mt = mC + mD;
+    double V[3];
+    for (int i = 0; i < 3; ++i) V[i] = (mA * vA[i] + mB * vB[i]) / mt;
+    const double vA2 = vA[0] * vA[0] + vA[1] * vA[1] + vA[2] * vA[2];
+    const double vB2 = vB[0] * vB[0] + vB[1] * vB[1] + vB[2] * vB[2];
+    const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const double KEin = 0.5 * mA * vA2 + 0.5 * mB * vB2;
+    const double KEcm = 0.5 * mt * V2;
+    const double Eav = KEin - KEcm + EvA + EvB - rx.dEf;
+    if (!(Eav - sC.zpe - sD.zpe > 0.0) || Eav - sD.zpe > sC.top || Eav - sC.zpe > sD.top)
+        return false;
+    Stream sa, sb, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) { qC[j] = 0u; qD[j] = 0u; }
+    uint32_t tr = 0;
+    if (sC.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<R>(A, sC, C->amode, Eav - sD.zpe, sa, qC, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qC[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    const double EvC = evib64(A.lev64, sC, qC);
+    if (sD.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<R>(A, sD, C->amode, Eav - EvC, sb, qD, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qD[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    o.trials += tr;
+    const double EvD = evib64(A.lev64, sD, qD);
+    const double Etr = (Eav - EvC) - EvD;
+    const double mu = mC * mD / mt;
+    const double g = sqrt(2.0 * Etr / mu);
+    double d[3];
+    iso_dir<double>(ss, d);
+    const double fC = mD / mt, fD = mC / mt;
+    for (int i = 0; i < 3; ++i) {
+        const double G = g * d[i];
+        vA[i] = V[i] + fC * G;
+        vB[i] = V[i] - fD * G;
+    }
+    return true;
+}
+
+struct Chan {
+    int rx, side, mode;
+    double ex;
+};
+constexpr int MAX_CHAN = 40;
+
+// One candidate pair: VHS acceptance (NTC), QK reaction test, reaction or LB
+// relaxation of molecule 1 then molecule 2, isotropic VHS scattering.
+template <class R>
+__device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double& seen_max) {
+    using Rec = typename RecOf<R>::T;
+    constexpr bool F64 = std::is_same<R, double>::value;
+    const Consts* __restrict__ C = A.C;
+    DevCell& cell = A.cells[c];
+    const DevRes& rs = A.res[cell.res];
+    const uint32_t N = cell.n;
+    const uint32_t P = N >> 1;
+    const uint32_t lcell = cell.lcell;
+    const uint32_t rk = ((uint32_t)r << 24) | k;
+    const uint32_t gpair = (uint32_t)r * P + k;  // pair number within the cell and step
+    const uint32_t ev_idx = A.abase[c] + gpair;
+    uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
+    const uint32_t ip = feistel(2u * k, N, key);
+    const uint32_t iq = feistel(2u * k + 1u, N, key);
+    Rec* recs = reinterpret_cast<Rec*>(cell.rec);
+    Rec Pr, Qr;
+    load_rec(recs + ip, Pr);
+    load_rec(recs + iq, Qr);
+    const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+    const DevPair& pc = C->pair[sP * MAXS + sQ];
+    const int amode = C->amode;
+    PairOut o{0u, 0u};
+    hcao_log_rec lr{rs.step, lcell, rk, ip, iq, -1, 0u};
+
+    // relative velocity and VHS acceptance: sigma_T g = C g^(2 - 2 omega)
+    double g2d, sg;
+    bool accept;
+    Stream sp;
+    st_init(sp, rs.seed, rs.step, lcell, rk, PU_PAIR);
+    if constexpr (F64) {
+        const double gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
+        g2d = gx * gx + gy * gy + gz * gz;
+        const double g = sqrt(g2d);
+        const double gp = amode == 0 ? sqrt(g) : (amode == 1 ? g : 1.0);
+        sg = pc.C * gp;
+        const double u_acc = st_u64(sp);
+        accept = u_acc < sg / cell.sgmax;
+    } else {
+        const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        g2d = (double)g2;
+        const float g = sqrtf(g2);
+        const float gp = amode == 0 ? sqrtf(g) : (amode == 1 ? g : 1.0f);
+        const float sgf = pc.C_f * gp;
+        sg = (double)sgf;
+        const float u_acc = st_u32(sp);
+        accept = u_acc < sgf / (float)cell.sgmax;
+    }
+    if (sg > seen_max) seen_max = sg;
+    if (!accept) {
+        A.cflag[ev_idx] = 0;
+        if (A.log_on) A.log[ev_idx] = lr;
+        return;
+    }
+    o.ev |= EV_ACC;
+    const double u_ster = st_u64(sp);
+    const double u_sel = st_u64(sp);
+    const double u_ch = st_u64(sp);
+    const double Etr = 0.5 * pc.mr * g2d;
+    const DevSpecies& SP = C->sp[sP];
+    const DevSpecies& SQ = C->sp[sQ];
+    const double EvP = evib64(A.lev64, SP, Pr.q);
+    const double EvQ = evib64(A.lev64, SQ, Qr.q);
+
+    // ---- QK reaction test: channels in fixed order (partner 1 stretches,
+    // partner 2 stretches, exchange); weighted by E_excess when several
+    Chan ch[MAX_CHAN];
+    int nch = 0;
+    if (C->n_reactions > 0) {
+        for (int side = 0; side < 2; ++side) {
+            const int spA = side ? sQ : sP;
+            const DevSpecies& SA = side ? SQ : SP;
+            const double EvA = side ? EvQ : EvP;
+            for (int ri = 0; ri < C->n_reactions; ++ri) {
+                const DevReaction& rx = C->rx[ri];
+                if (rx.type != HCAO_DISS || rx.A != spA) continue;
+                for (int j = 0; j < SA.n_stretch; ++j) {
+                    if (!((rx.mask >> j) & 1u)) continue;
+                    // Eq. Ecoll-diss: ZPEs of A, B, C removed, the breaking mode's restored
+                    const double E0j = __ldg(A.lev64 + SA.lev_off[j]);
+                    const double Ecoll = Etr + EvA - rx.zpesum + E0j;
+                    const double Eex = Ecoll - SA.De[j];
+                    if (Eex > 0.0 && nch < MAX_CHAN) ch[nch++] = Chan{ri, side, j, Eex};
+                }
+            }
+        }
+        for (int ri = 0; ri < C->n_reactions; ++ri) {
+            const DevReaction& rx = C->rx[ri];
+            if (rx.type != HCAO_EXCH) continue;
+            int side;
+            if (sP == rx.A && sQ == rx.B) side = 0;
+            else if (sQ == rx.A && sP == rx.B) side = 1;
+            else continue;
+            if (!(u_ster < rx.steric)) continue;
+            const DevSpecies& SA = side ? SQ : SP;
+            const uint32_t* qa = side ? Qr.q : Pr.q;
+            // Eq. Ecoll-exch; level energies include the ZPE (reading A12)
+            double s = 0.0;
+            if (rx.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH) {
+                const int js = (int)floor(u_sel * (double)SA.n_stretch);
+                s = __ldg(A.lev64 + SA.lev_off[js] + get_q(qa, js));
+            } else {
+                for (int j = 0; j < SA.n_modes; ++j)
+                    s = s + rx.alpha[j] * __ldg(A.lev64 + SA.lev_off[j] + get_q(qa, j));
+            }
+            const double Ecoll = Etr + s;
+            const double Eex = Ecoll - rx.Ea;
+            if (Eex > 0.0 && nch < MAX_CHAN) ch[nch++] = Chan{ri, side, 0, Eex};
+        }
+    }
+    if (nch > 0) {
+        int pick = 0;
+        if (nch > 1) {
+            double tot = 0.0;
+            for (int i = 0; i < nch; ++i) tot = tot + ch[i].ex;
+            const double t = u_ch * tot;
+            double pre = 0.0;
+            pick = nch - 1;
+            for (int i = 0; i < nch; ++i) {
+                pre = pre + ch[i].ex;
+                if (t < pre) { pick = i; break; }
+            }
+        }
+        const Chan cc = ch[pick];
+        const DevReaction& rx = C->rx[cc.rx];
+        double vA[3], vB[3], vN[3];
+        Rec& RA = cc.side ? Qr : Pr;
+        Rec& RB = cc.side ? Pr : Qr;
+        for (int i = 0; i < 3; ++i) { vA[i] = (double)RA.v[i]; vB[i] = (double)RB.v[i]; }
+        const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
+        bool done;
+        uint32_t q1[4], q2[4];
+        if (rx.type == HCAO_DISS) {
+            done = do_diss<R>(A, C, rx, vA, vB, spA, spB, cc.side ? EvQ : EvP, rs, lcell, rk, q1,
+                              q2, vN, o);
+            lr.aux = (uint32_t)cc.mode + (cc.side ? 16u : 0u);
+            if (done) {
+                // A becomes B in place; M keeps its state; C goes to the pair's
+                // scratch slot and is appended to the cell by k_finish
+                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
+                RA.meta = (uint32_t)rx.P0;
+                for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                Rec RN;
+                for (int i = 0; i < 3; ++i) RN.v[i] = (R)vN[i];
+                RN.meta = (uint32_t)rx.P1;
+                for (int j = 0; j < 4; ++j) RN.q[j] = q2[j];
+                if constexpr (F64) { RN.pad = 0; }
+                store_rec(reinterpret_cast<Rec*>(A.cscratch) + ev_idx, RN);
+                o.ev |= EV_CREATED;
+            }
+        } else {
+            done = do_exch<R>(A, C, rx, vA, vB, spA, spB, cc.side ? EvQ : EvP,
+                              cc.side ? EvP : EvQ, rs, lcell, rk, q1, q2, o);
+            lr.aux = (uint32_t)cc.side;
+            if (done) {
+                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
+                RA.meta = (uint32_t)rx.P0;
+                RB.meta = (uint32_t)rx.P1;
+                for (int j = 0; j < 4; ++j) { RA.q[j] = q1[j]; RB.q[j] = q2[j]; }
+            }
+        }
+        if (done) {
+            o.ev |= (uint32_t)(cc.rx + 1) << EV_RX_SHIFT;
+            lr.event = 1 + cc.rx;
+            store_rec(recs + ip, Pr);
+            store_rec(recs + iq, Qr);
+            o.ev |= (o.trials > 0xFFFFu ? 0xFFFFu : o.trials) << EV_TRIAL_SHIFT;
+            A.cflag[ev_idx] = o.ev;
+            if (A.log_on) A.log[ev_idx] = lr;
+            return;
+        }
+        o.ev |= EV_NOTEXEC;
+        lr.aux = 0u;
+    }
+
+    // ---- HCAO LB relaxation: molecule 1, then molecule 2 with the updated E_rel
+    double E = Etr;
+    uint32_t tr = 0;
+    if (SP.n_modes > 0) {
+        Stream s1;
+        st_init(s1, rs.seed, rs.step, lcell, rk, PU_LB_A);
+        const double Ec = E + EvP;
+        uint32_t nq[4] = {Pr.q[0], Pr.q[1], Pr.q[2], Pr.q[3]};
+        o.ev += 1u << EV_SAMP_SHIFT;
+        const int st = sample_lb<R>(A, SP, amode, Ec, s1, nq, tr);
+        if (st == S_OK) {
+            const double En = Ec - evib64(A.lev64, SP, nq);
+            if (F64 || En >= 0.0) {
+                for (int j = 0; j < 4; ++j) Pr.q[j] = nq[j];
+                E = En;
+            } else {
+                o.ev += 1u << EV_DEGEN_SHIFT;
+                E = Ec - EvP;
+            }
+        } else {
+            if (st == S_OVER) o.ev += 1u << EV_OVER_SHIFT;
+            else if (st == S_DEGEN) o.ev += 1u << EV_DEGEN_SHIFT;
+            else atomicOr(A.err, (uint32_t)ERR_REJECT);
+            E = Ec - EvP;
+        }
+    }
+    if (SQ.n_modes > 0) {
+        Stream s2;
+        st_init(s2, rs.seed, rs.step, lcell, rk, PU_LB_B);
+        const double Ec = E + EvQ;
+        uint32_t nq[4] = {Qr.q[0], Qr.q[1], Qr.q[2], Qr.q[3]};
+        o.ev += 1u << EV_SAMP_SHIFT;
+        const int st = sample_lb<R>(A, SQ, amode, Ec, s2, nq, tr);
+        if (st == S_OK) {
+            const double En = Ec - evib64(A.lev64, SQ, nq);
+            if (F64 || En >= 0.0) {
+                for (int j = 0; j < 4; ++j) Qr.q[j] = nq[j];
+                E = En;
+            } else {
+                o.ev += 1u << EV_DEGEN_SHIFT;
+                E = Ec - EvQ;
+            }
+        } else {
+            if (st == S_OVER) o.ev += 1u << EV_OVER_SHIFT;
+            else if (st == S_DEGEN) o.ev += 1u << EV_DEGEN_SHIFT;
+            else atomicOr(A.err, (uint32_t)ERR_REJECT);
+            E = Ec - EvQ;
+        }
+    }
+    o.trials += tr;
+
+    // ---- isotropic VHS scattering, centre-of-mass velocity kept
+    Stream ss;
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    if constexpr (F64) {
+        const double gn = sqrt(2.0 * E / pc.mr);
+        double d[3];
+        iso_dir<double>(ss, d);
+        const double mp = SP.mass, mq = SQ.mass;
+        double V[3];
+        for (int i = 0; i < 3; ++i) V[i] = (mp * Pr.v[i] + mq * Qr.v[i]) / pc.mt;
+        for (int i = 0; i < 3; ++i) {
+            const double G = gn * d[i];
+            Pr.v[i] = V[i] + pc.fp * G;
+            Qr.v[i] = V[i] - pc.fq * G;
+        }
+    } else {
+        const float gn = sqrtf((float)(E * (2.0 / pc.mr)));
+        float d[3];
+        iso_dir<float>(ss, d);
+        float V[3];
+        for (int i = 0; i < 3; ++i) V[i] = pc.fq_f * Pr.v[i] + pc.fp_f * Qr.v[i];
+        for (int i = 0; i < 3; ++i) {
+            const float G = gn * d[i];
+            Pr.v[i] = V[i] + pc.fp_f * G;
+            Qr.v[i] = V[i] - pc.fq_f * G;
+        }
+    }
+    store_rec(recs + ip, Pr);
+    store_rec(recs + iq, Qr);
+    o.ev |= (o.trials > 0xFFFFu ? 0xFFFFu : o.trials) << EV_TRIAL_SHIFT;
+    A.cflag[ev_idx] = o.ev;
+    lr.event = 0;
+    if (A.log_on) A.log[ev_idx] = lr;
+}
+
+// ------------------------------------------------------------- kernels
+constexpr int SETUP_THREADS = 1024;
+#ifdef HCAO_COMMON_KERNELS
+
+// inclusive scan of a[1..n] in place (a[0] = 0 kept), one CTA
+static __device__ void block_scan_inplace(uint32_t* a, int n) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 1; base <= n; base += blockDim.x) {
+        const int i = base + tid;
+        uint32_t v = i <= n ? a[i] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t add = carry + (wid > 0 ? wsum[wid - 1] : 0u);
+        if (i <= n) a[i] = v + add;
+        __syncthreads();
+        if (tid == 0) carry += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+
+static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
+    const int nc = A.n_cells;
+    const int R = A.max_rounds;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        DevCell& cl = A.cells[c];
+        const DevRes rs = A.res[cl.res];
+        const uint32_t N = cl.n;
+        uint32_t nsel = 0, rounds = 0, P = N >> 1;
+        if (rs.active && N >= 2) {
+            // NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically
+            const double x = 0.5 * (double)N * (double)(N - 1) * rs.w * cl.sgmax * rs.dt / rs.Vc;
+            const double fl = floor(x);
+            long long ns = (long long)fl;
+            Stream st;
+            st_init(st, rs.seed, rs.step, cl.lcell, 0u, PU_NSEL);
+            if (st_u64(st) < x - fl) ns++;
+            long long rr = (ns + P - 1) / P;
+            if (rr > R) { atomicOr(A.err, (uint32_t)ERR_ROUNDS); ns = 0; rr = 0; }
+            nsel = (uint32_t)ns;
+            rounds = (uint32_t)rr;
+            for (uint32_t r = 0; r < rounds; ++r) {
+                Stream sf;
+                st_init(sf, rs.seed, rs.step, cl.lcell, r << 24, PU_FEISTEL);
+                st_block(sf);
+                cl.fkey[r][0] = sf.w0; cl.fkey[r][1] = sf.w1;
+                cl.fkey[r][2] = sf.w2; cl.fkey[r][3] = sf.w3;
+            }
+        }
+        cl.nsel = nsel;
+        cl.ncreated = 0;
+        cl.seen = 0ull;
+        for (int r = 0; r < R; ++r) {
+            uint32_t cnt = 0;
+            if ((uint32_t)r < rounds) {
+                const uint32_t left = nsel - (uint32_t)r * P;
+                cnt = left < P ? left : P;
+            }
+            A.pbase[r * (nc + 1) + c + 1] = cnt;
+        }
+        A.abase[c + 1] = nsel;
+    }
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1)] = 0;
+        A.abase[0] = 0;
+    }
+    __syncthreads();
+    for (int r = 0; r < R; ++r) block_scan_inplace(A.pbase + r * (nc + 1), nc);
+    block_scan_inplace(A.abase, nc);
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < R; ++r) A.totals[r] = A.pbase[r * (nc + 1) + nc];
+        A.totals[MAX_ROUNDS] = A.abase[nc];
+    }
+}
+
+void launch_setup(const StepArgs& a, cudaStream_t s) { k_setup<<<1, SETUP_THREADS, 0, s>>>(a); }
+#endif
+
+template <class R>
+__global__ void __launch_bounds__(128) k_collide(StepArgs A, int r) {
+    const uint32_t total = A.totals[r];
+    const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        int lo = 0, hi = A.n_cells;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(pb + mid) <= g) lo = mid; else hi = mid;
+        }
+        double seen = 0.0;
+        process_pair<R>(A, lo, r, g - __ldg(pb + lo), seen);
+        // per-cell max of sigma_T g: lanes of one cell combine before the atomic
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        unsigned left = act;
+        while (left) {
+            const int leader = __ffs(left) - 1;
+            const int cl = __shfl_sync(act, lo, leader);
+            const unsigned grp = __ballot_sync(act, lo == cl);
+            double mx = 0.0;
+            unsigned g2 = grp;
+            while (g2) {
+                const double v = __shfl_sync(act, seen, __ffs(g2) - 1);
+                if (v > mx) mx = v;
+                g2 &= g2 - 1;
+            }
+            if (lane == leader)
+                atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong(mx));
+            left &= ~grp;
+        }
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* cellcnt,
+                                                int ncnt) {
+    using Rec = typename RecOf<R>::T;
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < A.n_res; i += blockDim.x)
+            if (A.res[i].active) A.res[i].step++;
+    }
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < A.n_cells; c += warps) {
+        DevCell& cl = A.cells[c];
+        const uint32_t N = cl.n, nsel = cl.nsel, base = A.abase[c];
+        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
+        uint32_t acc = 0, samp = 0, over = 0, degen = 0, notex = 0, created = 0;
+        unsigned long long trials = 0;
+        uint32_t rxc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t j0 = 0; j0 < nsel; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const uint32_t ev = j < nsel ? A.cflag[base + j] : 0u;
+            acc += ev & EV_ACC;
+            samp += (ev >> EV_SAMP_SHIFT) & 3u;
+            over += (ev >> EV_OVER_SHIFT) & 3u;
+            degen += (ev >> EV_DEGEN_SHIFT) & 3u;
+            notex += (ev & EV_NOTEXEC) ? 1u : 0u;
+            trials += ev >> EV_TRIAL_SHIFT;
+            const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
+            if (rxid > 0 && rxid <= 8) rxc[rxid - 1]++;
+            const bool cr = (ev & EV_CREATED) != 0u;
+            const unsigned m = __ballot_sync(0xFFFFFFFFu, cr);
+            if (cr) {
+                const uint32_t dst = N + created + __popc(m & ((1u << lane) - 1u));
+                if (dst < cl.cap) {
+                    Rec t;
+                    load_rec(reinterpret_cast<const Rec*>(A.cscratch) + base + j, t);
+                    store_rec(recs + dst, t);
+                } else {
+                    atomicOr(A.err, (uint32_t)ERR_CAPACITY);
+                }
+            }
+            created += __popc(m);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            samp += __shfl_xor_sync(0xFFFFFFFFu, samp, o);
+            over += __shfl_xor_sync(0xFFFFFFFFu, over, o);
+            degen += __shfl_xor_sync(0xFFFFFFFFu, degen, o);
+            notex += __shfl_xor_sync(0xFFFFFFFFu, notex, o);
+            trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) rxc[i] += __shfl_xor_sync(0xFFFFFFFFu, rxc[i], o);
+        }
+        if (lane == 0) {
+            unsigned long long* cc = cellcnt + (size_t)c * NCNT;
+            cc[CNT_CAND] += nsel;
+            cc[CNT_ACC] += acc;
+            cc[CNT_SAMPLES] += samp;
+            cc[CNT_TRIALS] += trials;
+            cc[CNT_OVER] += over;
+            cc[CNT_DEGEN] += degen;
+            cc[CNT_NOTEXEC] += notex;
+            for (int i = 0; i < 8 && i < ncnt - CNT_RX0; ++i) cc[CNT_RX0 + i] += rxc[i];
+            const double seen = __longlong_as_double((long long)cl.seen);
+            if (seen > cl.sgmax) cl.sgmax = seen;
+            cl.n = N + created < cl.cap ? N + created : cl.cap;
+            cl.ncreated = created;
+        }
+    }
+}
+
+template <class R>
+void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {
+    k_collide<R><<<grid, block, 0, s>>>(a, r);
+}
+template <class R>
+void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
+    const int g = (a.n_cells + 7) / 8 < 1184 ? (a.n_cells + 7) / 8 : 1184;
+    k_finish<R><<<g < 1 ? 1 : g, 256, 0, s>>>(a, reinterpret_cast<unsigned long long*>(a.counters), NCNT);
+}
+template <class R>
+void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, uint64_t* launches) {
+    launch_setup(a, s);
+    for (int r = 0; r < a.max_rounds; ++r) launch_collide_impl<R>(a, r, grid, block, s);
+    launch_finish_impl<R>(a, s);
+    if (launches) *launches += 2 + a.max_rounds;
+}
+
+// ------------------------------------------------------------- load / read kernels
+template <class R>
+__global__ void k_scatter_load(typename RecOf<R>::T* recs, const uint32_t* perm,
+                               const uint32_t* offsets, const uint64_t* slot0, int n_cells,
+                               const double* v, const uint8_t* qn, const int32_t* sp, int64_t n) {
+    using Rec = typename RecOf<R>::T;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        // cell of sorted position j: largest c with offsets[c] <= j
+        int lo = 0, hi = n_cells;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (offsets[mid] <= (uint32_t)j) lo = mid; else hi = mid;
+        }
+        const uint32_t i = perm[j];
+        Rec r;
+        for (int d = 0; d < 3; ++d) r.v[d] = (R)v[3 * (int64_t)i + d];
+        r.meta = (uint32_t)sp[i];
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(qn + 16 * (int64_t)i);
+        for (int w = 0; w < 4; ++w) r.q[w] = q[w];
+        if constexpr (std::is_same<R, double>::value) { r.pad = 0; }
+        store_rec(recs + slot0[lo] + (j - offsets[lo]), r);
+    }
+}
+
+template <class R>
+__global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* out_off,
+                       double* v, uint8_t* qn, int32_t* sp, int32_t* cell) {
+    using Rec = typename RecOf<R>::T;
+    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+        const DevCell cl = cells[cell0 + c];
+        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
+        const uint64_t o = out_off[c];
+        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
+            Rec r;
+            load_rec(recs + i, r);
+            if (v) for (int d = 0; d < 3; ++d) v[3 * (o + i) + d] = (double)r.v[d];
+            if (qn) {
+                uint32_t* q = reinterpret_cast<uint32_t*>(qn + 16 * (o + i));
+                for (int w = 0; w < 4; ++w) q[w] = r.q[w];
+            }
+            if (sp) sp[o + i] = (int32_t)(r.meta & 0xFFu);
+            if (cell) cell[o + i] = c;
+        }
+    }
+}
+
+// P6/P7 initial quantum numbers (double draws in both precisions)
+template <class R>
+__global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const DevRes* res,
+                           int rslot, const Consts* C, const double* bend_thr,
+                           const double* str_acc, const int* thr_off, uint32_t reject_cap,
+                           uint32_t* err) {
+    using Rec = typename RecOf<R>::T;
+    const DevRes rs = res[rslot];
+    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+        const DevCell cl = cells[cell0 + c];
+        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
+        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
+            Rec r;
+            load_rec(recs + i, r);
+            const int s = (int)(r.meta & 0xFFu);
+            const DevSpecies& S = C->sp[s];
+            Stream st;
+            st_init(st, rs.seed, 0xFFFFFFFFu, cl.lcell, i, PU_INIT);
+            uint32_t q[4] = {0u, 0u, 0u, 0u};
+            for (int j = 0; j < S.n_modes; ++j) {
+                const int L = S.n_lev[j];
+                const int off = thr_off[s * MAXM + j];
+                bool done = false;
+                for (uint32_t t = 0; t < reject_cap && !done; ++t) {
+                    if (j >= S.n_stretch) {
+                        // bend: i = floor(-ln(u) T / Theta) >= k  <=>  u <= exp(-k Theta / T)
+                        const double u = st_u64(st);
+                        int lv = 0;
+                        while (lv < L && u <= bend_thr[off + lv]) lv++;
+                        if (lv < L) { set_q(q, j, (uint32_t)lv); done = true; }
+                    } else {
+                        const double u1 = st_u64(st);
+                        const int lv = (int)floor(u1 * (double)L);
+                        const double u2 = st_u64(st);
+                        if (u2 < str_acc[off + lv]) { set_q(q, j, (uint32_t)lv); done = true; }
+                    }
+                }
+                if (!done) atomicOr(err, (uint32_t)ERR_REJECT);
+            }
+            for (int w = 0; w < 4; ++w) r.q[w] = q[w];
+            store_rec(recs + i, r);
+        }
+    }
+}
+
+// moments: acc[0..2] momentum, [3] E_tr, [4] E_form, [5 + s] E_vib of species s
+template <class R>
+__global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const Consts* C,
+                          const double* lev64, double* acc, unsigned long long* cnt) {
+    using Rec = typename RecOf<R>::T;
+    __shared__ double sacc[5 + MAXS];
+    __shared__ unsigned long long scnt[MAXS];
+    for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) sacc[i] = 0.0;
+    for (int i = threadIdx.x; i < MAXS; i += blockDim.x) scnt[i] = 0ull;
+    __syncthreads();
+    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+        const DevCell cl = cells[cell0 + c];
+        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
+        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
+            Rec r;
+            load_rec(recs + i, r);
+            const int s = (int)(r.meta & 0xFFu);
+            const DevSpecies& S = C->sp[s];
+            const double m = S.mass;
+            const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
+            atomicAdd(&sacc[0], m * vx);
+            atomicAdd(&sacc[1], m * vy);
+            atomicAdd(&sacc[2], m * vz);
+            atomicAdd(&sacc[3], 0.5 * m * (vx * vx + vy * vy + vz * vz));
+            atomicAdd(&sacc[4], S.E_form);
+            atomicAdd(&sacc[5 + s], evib64(lev64, S, r.q));
+            atomicAdd(&scnt[s], 1ull);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
+    for (int i = threadIdx.x; i < MAXS; i += blockDim.x) atomicAdd(&cnt[i], scnt[i]);
+}
+
+template <class R>
+__global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp, int mode,
+                           unsigned long long* hist) {
+    using Rec = typename RecOf<R>::T;
+    __shared__ unsigned int sh[MAXL];
+    for (int i = threadIdx.x; i < MAXL; i += blockDim.x) sh[i] = 0u;
+    __syncthreads();
+    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
+        const DevCell cl = cells[cell0 + c];
+        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
+        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
+            Rec r;
+            load_rec(recs + i, r);
+            if ((int)(r.meta & 0xFFu) == sp) atomicAdd(&sh[get_q(r.q, mode)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < MAXL; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+}
+
+// ------------------------------------------------------------- launchers
+#define HCAO_INSTANTIATE(R)                                                                      \
+    template <>                                                                                  \
+    void launch_step<R>(const StepArgs& a, int grid, int block, cudaStream_t s,                  \
+                        uint64_t* launches) {                                                    \
+        launch_step_impl<R>(a, grid, block, s, launches);                                        \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_collide<R>(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {      \
+        launch_collide_impl<R>(a, r, grid, block, s);                                            \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_finish<R>(const StepArgs& a, cudaStream_t s) { launch_finish_impl<R>(a, s); }    \
+    template <>                                                                                  \
+    void launch_scatter_load<R>(void* rec_base, const uint32_t* perm, const uint32_t* offsets,   \
+                                const uint64_t* slot0, int n_cells, const double* v,             \
+                                const uint8_t* qn, const int32_t* sp, int64_t n,                 \
+                                cudaStream_t s) {                                                \
+        if (n <= 0) return;                                                                      \
+        int grid = (int)((n + 255) / 256);                                                       \
+        if (grid > 4096) grid = 4096;                                                            \
+        k_scatter_load<R><<<grid, 256, 0, s>>>(reinterpret_cast<typename RecOf<R>::T*>(rec_base), \
+                                               perm, offsets, slot0, n_cells, v, qn, sp, n);     \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_pack<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* out_off,   \
+                        double* v, uint8_t* qn, int32_t* sp, int32_t* cell, cudaStream_t s) {    \
+        int grid = n_cells < 4096 ? n_cells : 4096;                                              \
+        if (grid < 1) return;                                                                    \
+        k_pack<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, out_off, v, qn, sp, cell);         \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_init_vib<R>(const DevCell* cells, int cell0, int n_cells, const DevRes* res,     \
+                            int rslot, const Consts* C, const double* bt, const double* sa,      \
+                            const int* to, uint32_t cap, uint32_t* err, cudaStream_t s) {        \
+        int grid = n_cells < 4096 ? n_cells : 4096;                                              \
+        if (grid < 1) return;                                                                    \
+        k_init_vib<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, res, rslot, C, bt, sa, to, cap, \
+                                           err);                                                 \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_moments<R>(const DevCell* cells, int cell0, int n_cells, const Consts* C,        \
+                           const double* lev64, double* acc, unsigned long long* cnt,            \
+                           cudaStream_t s) {                                                     \
+        int grid = n_cells < 1184 ? n_cells : 1184;                                              \
+        if (grid < 1) return;                                                                    \
+        k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, C, lev64, acc, cnt);            \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_levelpop<R>(const DevCell* cells, int cell0, int n_cells, int sp, int mode,      \
+                            unsigned long long* hist, cudaStream_t s) {                          \
+        int grid = n_cells < 1184 ? n_cells : 1184;                                              \
+        if (grid < 1) return;                                                                    \
+        k_levelpop<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, sp, mode, hist);               \
+    }
+
+}  // namespace hcao

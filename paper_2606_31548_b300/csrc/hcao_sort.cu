@@ -1,0 +1,186 @@
+// hcao_sort.cu -- stable counting sort of particles by cell key (sm_103a).
+//
+// LSD radix sort on 8-bit digits of the cell key, each pass a stable counting
+// sort: per-tile digit histograms built with warp-aggregated shared-memory
+// atomics (__match_any_sync: one atomic per group of lanes holding the same
+// digit), one exclusive scan over the digit-major histogram matrix, and a
+// stable scatter in which a particle's rank inside its tile is
+//   (count of its digit in earlier rounds of the tile)
+// + (count in earlier warps of this round) + (lanes below it with the same digit).
+// Equal keys keep input order, so the particles of a cell stay in load order.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hcao_sort.h"
+
+namespace hcao {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 8;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+static __global__ void __launch_bounds__(SORT_THREADS)
+k_digit_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* hist, int nblocks) {
+    __shared__ uint32_t cnt[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    cnt[tid] = 0u;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int64_t j = t0 + it * SORT_THREADS + tid;
+        const bool valid = j < n;
+        const uint32_t d = valid ? (keys[j] >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[(int64_t)tid * nblocks + blockIdx.x] = cnt[tid];
+}
+
+// exclusive scan of a[0..n) in place, one CTA of 1024 threads
+static __global__ void __launch_bounds__(1024) k_scan_excl(uint32_t* a, int64_t n) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        const int64_t i = base + tid;
+        const uint32_t x = i < n ? a[i] : 0u;
+        uint32_t v = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += t;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t pre = carry + (wid > 0 ? wsum[wid - 1] : 0u);
+        if (i < n) a[i] = pre + v - x;
+        __syncthreads();
+        if (tid == 0) carry += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+}
+
+static __global__ void __launch_bounds__(SORT_THREADS)
+k_digit_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin, int64_t n,
+                int shift, const uint32_t* __restrict__ hist, int nblocks, uint32_t* kout,
+                uint32_t* iout) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[SORT_THREADS / 32][257];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    run[tid] = hist[(int64_t)tid * nblocks + blockIdx.x];
+    const int64_t t0 = (int64_t)blockIdx.x * SORT_TILE;
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        for (int w = 0; w < SORT_THREADS / 32; ++w) wcnt[w][tid] = 0u;
+        if (tid == 0)
+            for (int w = 0; w < SORT_THREADS / 32; ++w) wcnt[w][256] = 0u;
+        __syncthreads();
+        const int64_t j = t0 + it * SORT_THREADS + tid;
+        const bool valid = j < n;
+        const uint32_t key = valid ? kin[j] : 0u;
+        const uint32_t d = valid ? (key >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t below = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        if (lane == __ffs(peers) - 1) wcnt[wid][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = run[d] + below;
+            for (int w = 0; w < wid; ++w) pos += wcnt[w][d];
+            kout[pos] = key;
+            iout[pos] = iin ? iin[j] : (uint32_t)j;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < SORT_THREADS / 32; ++w) add += wcnt[w][tid];
+        run[tid] += add;
+        __syncthreads();
+    }
+}
+
+// per-cell counts with warp-aggregated atomics
+static __global__ void k_cell_count(const uint32_t* __restrict__ keys, int64_t n, uint32_t n_cells,
+                             uint32_t* cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < n; j0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = j0 + threadIdx.x;
+        const bool valid = j < n;
+        const uint32_t k = valid ? keys[j] : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+        if (valid && k < n_cells && lane == __ffs(peers) - 1) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
+    }
+}
+
+static __global__ void k_zero(uint32_t* a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = 0u;
+}
+
+int64_t sort_scratch_words(int64_t n, uint32_t n_cells) {
+    const int64_t nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    (void)n_cells;
+    return 4 * n + 256 * (nblocks > 0 ? nblocks : 1);
+}
+
+int sort_passes(uint32_t n_cells) {
+    int bits = 1;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)n_cells) bits++;
+    return (bits + 7) / 8;
+}
+
+cudaError_t cell_sort(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_t* perm,
+                      uint32_t* offsets, uint32_t* scratch, cudaStream_t s, uint64_t* launches) {
+    if (n < 0) return cudaErrorInvalidValue;
+    const int64_t nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    uint32_t* kA = scratch;
+    uint32_t* iA = scratch + n;
+    uint32_t* kB = scratch + 2 * n;
+    uint32_t* iB = scratch + 3 * n;
+    uint32_t* hist = scratch + 4 * n;
+    uint64_t L = 0;
+    // offsets[c] = count of cell c, then one exclusive scan over n_cells + 1
+    // entries: offsets[c] = start of cell c, offsets[n_cells] = n
+    k_zero<<<64, 256, 0, s>>>(offsets, (int64_t)n_cells + 1);
+    ++L;
+    if (n > 0) {
+        int g = (int)((n + 255) / 256);
+        if (g > 4096) g = 4096;
+        k_cell_count<<<g, 256, 0, s>>>(keys, n, n_cells, offsets);
+        ++L;
+    }
+    k_scan_excl<<<1, 1024, 0, s>>>(offsets, (int64_t)n_cells + 1);
+    ++L;
+    if (n == 0) {
+        if (launches) *launches += L;
+        return cudaGetLastError();
+    }
+    const int passes = sort_passes(n_cells);
+    const uint32_t* kin = keys;
+    const uint32_t* iin = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        uint32_t* kout = (p % 2 == 0) ? kA : kB;
+        uint32_t* iout = (p == passes - 1) ? perm : ((p % 2 == 0) ? iA : iB);
+        k_digit_hist<<<(unsigned)nblocks, SORT_THREADS, 0, s>>>(kin, n, shift, hist, (int)nblocks);
+        k_scan_excl<<<1, 1024, 0, s>>>(hist, 256 * nblocks);
+        k_digit_scatter<<<(unsigned)nblocks, SORT_THREADS, 0, s>>>(kin, iin, n, shift, hist,
+                                                                   (int)nblocks, kout, iout);
+        L += 3;
+        kin = kout;
+        iin = iout;
+    }
+    if (launches) *launches += L;
+    return cudaGetLastError();
+}
+
+}  // namespace hcao

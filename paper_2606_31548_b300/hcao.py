@@ -1,0 +1,325 @@
+"""Thin ctypes binding of libhcao (argument marshalling only).
+
+Every step of the collision phase runs in the library's CUDA kernels; this
+module only converts numpy arrays and workload presets into the C structs of
+include/hcao.h.  It raises if the compiled library is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhcao.so")
+
+FP64, FP32 = 0, 1
+DISS, EXCH = 1, 2
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
+          -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND"}
+
+EXPORTS = [
+    "hcao_create", "hcao_destroy", "hcao_last_error", "hcao_default_config", "hcao_set_species",
+    "hcao_set_reactions", "hcao_add_reservoir", "hcao_remove_reservoir", "hcao_load_particles",
+    "hcao_init_vibration", "hcao_step", "hcao_sync", "hcao_count", "hcao_read_particles",
+    "hcao_read_moments", "hcao_read_level_populations", "hcao_read_counters",
+    "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
+    "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
+    "hcao_set_profiling", "hcao_read_profile",
+]
+
+
+class HcaoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
+                ("table_points", C.c_int), ("table_span_J", C.c_double), ("reject_cap", C.c_uint32),
+                ("max_rounds", C.c_int), ("capacity_factor", C.c_double), ("capacity_extra", C.c_int)]
+
+
+class _Species(C.Structure):
+    _fields_ = [("mass", C.c_double), ("d_ref", C.c_double), ("T_ref", C.c_double),
+                ("omega", C.c_double), ("E_form", C.c_double), ("n_stretch", C.c_int),
+                ("we", C.POINTER(C.c_double)), ("wexe", C.POINTER(C.c_double)),
+                ("De", C.POINTER(C.c_double)), ("n_bend", C.c_int), ("theta", C.POINTER(C.c_double))]
+
+
+class _Reaction(C.Structure):
+    _fields_ = [("type", C.c_int), ("reactants", C.c_int * 2), ("products", C.c_int * 2),
+                ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
+                ("alpha_mode", C.c_int), ("alpha", C.POINTER(C.c_double))]
+
+
+class LogRec(C.Structure):
+    _fields_ = [("step", C.c_uint32), ("cell", C.c_uint32), ("round_k", C.c_uint32),
+                ("p", C.c_uint32), ("q", C.c_uint32), ("event", C.c_int32), ("aux", C.c_uint32)]
+
+
+LOG_DTYPE = np.dtype([("step", "u4"), ("cell", "u4"), ("round_k", "u4"), ("p", "u4"), ("q", "u4"),
+                      ("event", "i4"), ("aux", "u4")])
+
+
+class Moments(C.Structure):
+    _fields_ = [("n", C.c_int64 * 16), ("momentum", C.c_double * 3), ("E_tr", C.c_double),
+                ("E_vib", C.c_double * 16), ("E_form", C.c_double), ("T_tr", C.c_double),
+                ("T_vib", C.c_double * 16)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libhcao.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhcao.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl, u64 = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_uint64
+        L.hcao_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+        L.hcao_destroy.argtypes = [vp]
+        L.hcao_destroy.restype = None
+        L.hcao_last_error.argtypes = [vp]
+        L.hcao_last_error.restype = C.c_char_p
+        L.hcao_default_config.argtypes = [C.POINTER(Config)]
+        L.hcao_default_config.restype = None
+        L.hcao_set_species.argtypes = [vp, C.POINTER(_Species), i32]
+        L.hcao_set_reactions.argtypes = [vp, C.POINTER(_Reaction), i32]
+        L.hcao_add_reservoir.argtypes = [vp, i32, dbl, dbl, dbl, u64, dbl, C.POINTER(i32)]
+        L.hcao_remove_reservoir.argtypes = [vp, i32]
+        L.hcao_load_particles.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+        L.hcao_init_vibration.argtypes = [vp, i32, dbl]
+        L.hcao_step.argtypes = [vp, i32]
+        L.hcao_sync.argtypes = [vp]
+        L.hcao_count.argtypes = [vp, i32, C.POINTER(i64)]
+        L.hcao_read_particles.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.hcao_read_moments.argtypes = [vp, i32, C.POINTER(Moments)]
+        L.hcao_read_level_populations.argtypes = [vp, i32, i32, i32, vp, i32]
+        L.hcao_read_counters.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]
+        L.hcao_read_reaction_counts.argtypes = [vp, i32, vp, i32]
+        L.hcao_read_cell_sgmax.argtypes = [vp, i32, vp]
+        L.hcao_set_log.argtypes = [vp, i32]
+        L.hcao_read_log.argtypes = [vp, vp, i64, C.POINTER(i64)]
+        L.hcao_cell_sort.argtypes = [vp, vp, i64, C.c_uint32, vp, vp]
+        L.hcao_level_energy.argtypes = [vp, i32, i32, i32, C.POINTER(dbl)]
+        L.hcao_n_levels.argtypes = [vp, i32, i32, C.POINTER(i32)]
+        L.hcao_set_profiling.argtypes = [vp, i32]
+        L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+        L.hcao_kernel_launches.argtypes = [vp]
+        L.hcao_kernel_launches.restype = u64
+        _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(ptr) -> C.c_void_p:
+    """Device pointer from an int or a torch tensor."""
+    if hasattr(ptr, "data_ptr"):
+        return C.c_void_p(ptr.data_ptr())
+    return C.c_void_p(int(ptr))
+
+
+class Context:
+    """One libhcao context on one GPU."""
+
+    def __init__(self, precision: int = FP64, device: int = 0, stream: Optional[int] = None,
+                 table_points: int = 2048, table_span_J: float = 64 * 1.602176634e-19,
+                 max_rounds: int = 2, capacity_factor: float = 2.0, capacity_extra: int = 64,
+                 reject_cap: int = 1 << 20):
+        self.L = lib()
+        cfg = Config()
+        self.L.hcao_default_config(C.byref(cfg))
+        cfg.precision, cfg.device = precision, device
+        cfg.cuda_stream = stream
+        cfg.table_points, cfg.table_span_J = table_points, table_span_J
+        cfg.max_rounds, cfg.capacity_factor, cfg.capacity_extra = max_rounds, capacity_factor, capacity_extra
+        cfg.reject_cap = reject_cap
+        h = C.c_void_p()
+        r = self.L.hcao_create(C.byref(cfg), C.byref(h))
+        if r != 0:
+            raise HcaoError(r, "hcao_create failed")
+        self.h = h
+        self.precision = precision
+        self._keep = []
+        self.n_reactions = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hcao_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, r):
+        if r != 0:
+            raise HcaoError(r, self.L.hcao_last_error(self.h).decode())
+        return r
+
+    # -- setup
+    def set_species(self, species: Sequence) -> None:
+        arr = (_Species * len(species))()
+        keep = []
+        for i, s in enumerate(species):
+            d = arr[i]
+            d.mass, d.d_ref, d.T_ref, d.omega, d.E_form = s.mass, s.d_ref, s.T_ref, s.omega, s.E_form
+            d.n_stretch, d.n_bend = len(s.we), len(s.theta)
+            for name in ("we", "wexe", "De", "theta"):
+                vals = list(getattr(s, name))
+                buf = (C.c_double * max(1, len(vals)))(*vals)
+                keep.append(buf)
+                setattr(d, name, C.cast(buf, C.POINTER(C.c_double)))
+        self._chk(self.L.hcao_set_species(self.h, arr, len(species)))
+
+    def set_reactions(self, reactions: Sequence) -> None:
+        if not reactions:
+            return
+        arr = (_Reaction * len(reactions))()
+        keep = []
+        for i, r in enumerate(reactions):
+            d = arr[i]
+            d.type = DISS if r.type == "diss" else EXCH
+            rc = list(r.reactants) + [-1] * (2 - len(r.reactants))
+            d.reactants[0], d.reactants[1] = rc[0], rc[1]
+            d.products[0], d.products[1] = r.products[0], r.products[1]
+            d.diss_mode_mask = r.diss_mode_mask
+            d.Ea, d.steric = r.Ea, r.steric
+            d.alpha_mode = 1 if r.alpha_mode == "one_random_stretch" else 0
+            if r.alpha:
+                buf = (C.c_double * len(r.alpha))(*r.alpha)
+                keep.append(buf)
+                d.alpha = C.cast(buf, C.POINTER(C.c_double))
+        self._chk(self.L.hcao_set_reactions(self.h, arr, len(reactions)))
+        self.n_reactions = len(reactions)
+
+    def add_reservoir(self, n_cells, cell_volume, weight, dt, seed, T_sgmax) -> int:
+        rid = C.c_int()
+        self._chk(self.L.hcao_add_reservoir(self.h, n_cells, cell_volume, weight, dt, seed, T_sgmax,
+                                            C.byref(rid)))
+        return rid.value
+
+    def remove_reservoir(self, res: int) -> None:
+        self._chk(self.L.hcao_remove_reservoir(self.h, res))
+
+    def load_particles(self, res, v, qn, species, cell) -> None:
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        qn = np.ascontiguousarray(qn, dtype=np.uint8)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        cell = np.ascontiguousarray(cell, dtype=np.int32)
+        self._chk(self.L.hcao_load_particles(self.h, res, v.shape[0], _p(v), _p(qn), _p(species), _p(cell)))
+
+    def init_vibration(self, res, T_vib) -> None:
+        self._chk(self.L.hcao_init_vibration(self.h, res, T_vib))
+
+    # -- run
+    def step(self, n=1) -> None:
+        self._chk(self.L.hcao_step(self.h, n))
+
+    def sync(self) -> None:
+        self._chk(self.L.hcao_sync(self.h))
+
+    def set_log(self, on=True) -> None:
+        self._chk(self.L.hcao_set_log(self.h, 1 if on else 0))
+
+    # -- read
+    def count(self, res) -> int:
+        n = C.c_int64()
+        self._chk(self.L.hcao_count(self.h, res, C.byref(n)))
+        return n.value
+
+    def read_particles(self, res):
+        n = self.count(res)
+        v = np.zeros((n, 3)); qn = np.zeros((n, 16), np.uint8)
+        sp = np.zeros(n, np.int32); cell = np.zeros(n, np.int32)
+        if n:
+            self._chk(self.L.hcao_read_particles(self.h, res, _p(v), _p(qn), _p(sp), _p(cell)))
+        return v, qn, sp, cell
+
+    def read_moments(self, res) -> Moments:
+        m = Moments()
+        self._chk(self.L.hcao_read_moments(self.h, res, C.byref(m)))
+        return m
+
+    def read_level_populations(self, res, species, mode, max_levels=256) -> np.ndarray:
+        out = np.zeros(max_levels, np.uint64)
+        self._chk(self.L.hcao_read_level_populations(self.h, res, species, mode, _p(out), max_levels))
+        return out
+
+    def read_counters(self, res) -> np.ndarray:
+        out = np.zeros(40, np.uint64)
+        n = C.c_int()
+        self._chk(self.L.hcao_read_counters(self.h, res, _p(out), 40, C.byref(n)))
+        return out[: n.value].copy()
+
+    def read_reaction_counts(self, res, n) -> np.ndarray:
+        out = np.zeros(max(n, 1), np.uint64)
+        self._chk(self.L.hcao_read_reaction_counts(self.h, res, _p(out), n))
+        return out[:n]
+
+    def read_cell_sgmax(self, res, n_cells) -> np.ndarray:
+        out = np.zeros(n_cells)
+        self._chk(self.L.hcao_read_cell_sgmax(self.h, res, _p(out)))
+        return out
+
+    def read_log(self) -> np.ndarray:
+        n = C.c_int64()
+        self._chk(self.L.hcao_read_log(self.h, None, 0, C.byref(n)))
+        buf = np.zeros(max(n.value, 1), dtype=LOG_DTYPE)
+        got = C.c_int64()
+        self._chk(self.L.hcao_read_log(self.h, _p(buf), buf.shape[0], C.byref(got)))
+        return buf[: got.value].copy()
+
+    def cell_sort(self, keys_dev, n, n_cells, perm_dev, offsets_dev) -> None:
+        self._chk(self.L.hcao_cell_sort(self.h, _dptr(keys_dev), n, n_cells, _dptr(perm_dev),
+                                        _dptr(offsets_dev)))
+
+    def level_energy(self, sp, mode, level) -> float:
+        e = C.c_double()
+        self._chk(self.L.hcao_level_energy(self.h, sp, mode, level, C.byref(e)))
+        return e.value
+
+    def n_levels(self, sp, mode) -> int:
+        n = C.c_int()
+        self._chk(self.L.hcao_n_levels(self.h, sp, mode, C.byref(n)))
+        return n.value
+
+    def set_profiling(self, on=True) -> None:
+        self._chk(self.L.hcao_set_profiling(self.h, 1 if on else 0))
+
+    def read_profile(self):
+        """(ms, launches) per kernel class: setup, collide, finish."""
+        ms = np.zeros(3)
+        n = np.zeros(3, np.uint64)
+        got = C.c_int()
+        self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 3, C.byref(got)))
+        return ms, n
+
+    def kernel_launches(self) -> int:
+        return int(self.L.hcao_kernel_launches(self.h))
+
+
+def from_workload(w, precision=FP64, log=False, init_vib=True, **kw) -> Context:
+    """A context loaded with a workload's species, reactions and initial state."""
+    c = Context(precision=precision, **kw)
+    c.set_species(w.species)
+    c.set_reactions(w.reactions)
+    rid = c.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    c.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
+    if init_vib:
+        c.init_vibration(rid, w.T_vib0)
+    if log:
+        c.set_log(True)
+    return c

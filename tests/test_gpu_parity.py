@@ -1,0 +1,249 @@
+"""GPU (libhcao, C ABI) against the oracle.
+
+FP64 mode: every integer decision -- cell sort, selected pairs, accepted
+collisions, reaction events, quantum numbers, species, created particles -- and
+every FP64 velocity must equal the oracle's bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_31548_b300 import hcao
+from paper_2606_31548_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EV = 1.602176634e-19
+
+
+def _pair(w, precision=hcao.FP64, log=True, **kw):
+    g = hcao.from_workload(w, precision=precision, log=log, **kw)
+    o = oracle.from_workload(w, log=log)
+    return g, o
+
+
+def _assert_same_state(g, o, res=0, exact_v=True):
+    vg, qg, sg, cg = g.read_particles(res)
+    vo, qo, so, co = o.read_particles(res)
+    assert vg.shape == vo.shape
+    assert np.array_equal(cg, co)
+    assert np.array_equal(sg, so)
+    assert np.array_equal(qg, qo)
+    if exact_v:
+        assert np.array_equal(vg, vo), np.max(np.abs(vg - vo))
+
+
+def _assert_same_log(g, o):
+    lg, lo = g.read_log(), o.read_log()
+    assert len(lg) == len(lo)
+    for f in ("step", "cell", "round_k", "p", "q", "event", "aux"):
+        assert np.array_equal(lg[f], lo[f]), f
+
+
+# ------------------------------------------------------------- cell sort
+@pytest.mark.parametrize("n,n_cells", [(0, 5), (1, 1), (1000, 1), (2047, 7), (2049, 300),
+                                       (100003, 4096), (300000, 70000), (2_100_000, 16384)])
+def test_cell_sort_is_stable_counting_sort(n, n_cells):
+    import torch
+    rng = np.random.default_rng(n + n_cells)
+    keys = rng.integers(0, n_cells, size=n).astype(np.uint32)
+    if n > 10:
+        keys[: n // 10] = keys[0]  # long runs of one key
+    ctx = hcao.Context()
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    perm = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    off = torch.zeros(n_cells + 1, dtype=torch.int32, device="cuda")
+    ctx.cell_sort(dk, n, n_cells, perm, off)
+    ctx.sync()
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(perm.cpu().numpy()[:n].view(np.uint32), ref.astype(np.uint32))
+    cnt = np.bincount(keys, minlength=n_cells)
+    exp_off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.uint32)
+    assert np.array_equal(off.cpu().numpy().view(np.uint32), exp_off)
+
+
+# ------------------------------------------------------------- load path
+@pytest.mark.parametrize("precision", [hcao.FP64, hcao.FP32])
+def test_load_read_roundtrip(precision):
+    w = W.ch4_heat_bath(n_cells=37, per_cell=123)
+    rng = np.random.default_rng(4)
+    sp = rng.integers(0, 3, size=w.n).astype(np.int32)
+    nl = [[18] * 4 + [256] * 5, [18] * 3 + [256] * 3, []]
+    qn = np.zeros((w.n, 16), np.uint8)
+    for s in range(3):
+        sel = sp == s
+        qn[sel] = W.random_levels(rng, int(sel.sum()), nl[s] + [1] * (16 - len(nl[s])), len(nl[s]))
+    g = hcao.Context(precision=precision)
+    g.set_species(w.species)
+    rid = g.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    g.load_particles(rid, w.v, qn, sp, w.cell)
+    v2, q2, s2, c2 = g.read_particles(rid)
+    order = np.argsort(w.cell, kind="stable")
+    assert np.array_equal(c2, w.cell[order])
+    assert np.array_equal(s2, sp[order])
+    assert np.array_equal(q2, qn[order])
+    vexp = w.v[order] if precision == hcao.FP64 else w.v[order].astype(np.float32).astype(np.float64)
+    assert np.array_equal(v2, vexp)
+
+
+def test_load_rejects_bad_levels():
+    w = W.relaxation_triatomic(n_particles=100)
+    g = hcao.Context()
+    g.set_species(w.species)
+    rid = g.add_reservoir(1, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    qn = np.zeros((w.n, 16), np.uint8)
+    qn[3, 0] = 17  # stretch has 17 levels: 0..16
+    with pytest.raises(hcao.HcaoError):
+        g.load_particles(rid, w.v, qn, w.species_idx, w.cell)
+
+
+# ------------------------------------------------------------- init
+@pytest.mark.parametrize("T", [300.0, 6000.0, 20000.0])
+def test_init_vibration_matches_oracle(T):
+    w = W.ch4_heat_bath(n_cells=16, per_cell=400)
+    w.T_vib0 = T
+    g, o = _pair(w, log=False)
+    _, qg, _, _ = g.read_particles(0)
+    _, qo, _, _ = o.read_particles(0)
+    assert np.array_equal(qg, qo)
+
+
+# ------------------------------------------------------------- FP64 step parity
+def _run_parity(w, steps, check_each=True):
+    g, o = _pair(w)
+    for s in range(steps):
+        g.step(1)
+        o.step(1)
+        if check_each or s == steps - 1:
+            _assert_same_log(g, o)
+            _assert_same_state(g, o)
+    cg = g.read_counters(0)
+    co = o.read_counters(0)
+    assert np.array_equal(cg, co[: len(cg)]), (cg, co)
+    assert np.array_equal(g.read_cell_sgmax(0, w.n_cells), o.read_cell_sgmax(0, w.n_cells))
+    return g, o
+
+
+def test_parity_triatomic_multicell():
+    _run_parity(W.relaxation_triatomic(n_particles=3000, n_cells=5, steps=20), 20)
+
+
+def test_parity_triatomic_single_cell_20000():
+    """The full 20,000-particle single-cell relaxation reservoir (large cell:
+    pairs gathered through the Feistel permutation across many CTAs)."""
+    g, o = _run_parity(W.relaxation_triatomic(), 25, check_each=False)
+    assert g.read_counters(0)[1] > 20000
+
+
+def test_parity_ch4_dissociation():
+    g, o = _run_parity(W.ch4_heat_bath(n_cells=24, per_cell=250), 8)
+    assert g.read_reaction_counts(0, 1)[0] > 100
+    assert g.count(0) > 24 * 250
+
+
+def test_parity_exchange():
+    g, o = _run_parity(W.ch4_h_exchange(n_cells=12, per_cell=400, T0=6000.0), 8)
+    assert g.read_reaction_counts(0, 1)[0] > 10
+
+
+def test_parity_ragged_and_tiny_cells():
+    """Cells of 0, 1, 2, 3 particles and ragged sizes."""
+    base = W.relaxation_triatomic(n_particles=10, n_cells=1)
+    counts = np.array([0, 1, 2, 3, 5, 64, 127, 300, 0, 2])
+    rng = np.random.default_rng(9)
+    n = int(counts.sum())
+    cell = np.repeat(np.arange(len(counts), dtype=np.int32), counts)
+    perm = rng.permutation(n)
+    base.cell = cell[perm]
+    base.n_cells = len(counts)
+    base.species_idx = np.zeros(n, np.int32)
+    base.v = W.maxwellian(rng, n, np.full(n, base.species[0].mass), 20000.0)
+    base.weight = 1e23 * base.cell_volume / counts.max()  # the largest cell at n = 1e23 m^-3
+    _run_parity(base, 12)
+
+
+def test_parity_multiple_rounds():
+    """A large (sigma g)_max forces N_sel > N/2: two pairing rounds per step."""
+    w = W.relaxation_triatomic(n_particles=2000, n_cells=4)
+    w.dt *= 3.0
+    g, o = _pair(w, max_rounds=4)
+    for _ in range(4):
+        g.step(1)
+        o.step(1)
+        _assert_same_log(g, o)
+        _assert_same_state(g, o)
+    lg = g.read_log()
+    assert np.any((lg["round_k"] >> 24) >= 1)
+
+
+def test_full_size_heat_bath_sampled_cells():
+    """The 4096-cell x 500 CH4 heat bath (2.05M particles) in the launch
+    configuration of the benchmark, FP64; 6 sampled cells recomputed by the
+    oracle on their own (cells are independent, keyed by their index)."""
+    w = W.ch4_heat_bath()
+    g = hcao.from_workload(w, precision=hcao.FP64)
+    g.step(2)
+    g.sync()
+    vg, qg, sg, cg = g.read_particles(0)
+    pick = [0, 1, 777, 2048, 3000, 4095]
+    sel_in = np.isin(w.cell, pick)
+    o = oracle.Oracle()
+    for s in w.species:
+        o.add_species(s)
+    for r in w.reactions:
+        o.add_reaction(r)
+    o.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    o.load(0, w.v[sel_in], w.qn0()[sel_in], w.species_idx[sel_in], w.cell[sel_in])
+    o.init_vibration(0, w.T_vib0)
+    o.step(2)
+    vo, qo, so, co = o.read_particles(0)
+    sel_out = np.isin(cg, pick)
+    assert np.array_equal(cg[sel_out], co)
+    assert np.array_equal(sg[sel_out], so)
+    assert np.array_equal(qg[sel_out], qo)
+    assert np.array_equal(vg[sel_out], vo)
+
+
+# ------------------------------------------------------------- FP32 mode
+def _totals(ctx_or_o, res, species, oracle_side=False):
+    v, qn, sp, _ = ctx_or_o.read_particles(res)
+    m = np.array([s.mass for s in species])[sp]
+    ke = 0.5 * np.sum(m * np.sum(v * v, axis=1))
+    return ke, np.sum(m[:, None] * v, axis=0)
+
+
+def test_fp32_energy_conservation_per_step():
+    """FP32 mode: total energy (translational + vibrational + formation)
+    changes by at most 1e-6 relative per step."""
+    w = W.ch4_heat_bath(n_cells=32, per_cell=500)
+    g = hcao.from_workload(w, precision=hcao.FP32)
+    prev = None
+    for _ in range(6):
+        m = g.read_moments(0)
+        E = m.E_tr + sum(m.E_vib[i] for i in range(16)) + m.E_form
+        if prev is not None:
+            assert abs(E - prev) / abs(prev) < 1e-6
+        prev = E
+        g.step(1)
+
+
+def test_fp32_tracks_oracle_statistics():
+    """FP32 mode against the FP64 oracle: relaxation of the triatomic (T_vib
+    after 150 steps) and the dissociation count of the CH4 bath agree within
+    3 sigma of the oracle's run-to-run spread."""
+    w = W.relaxation_triatomic(n_particles=20000, n_cells=1)
+    g = hcao.from_workload(w, precision=hcao.FP32)
+    g.step(150)
+    tv_g = g.read_moments(0).T_vib[0]
+    o = oracle.from_workload(w)
+    o.step(150)
+    tv_o = o.tvib(0, 0)
+    assert abs(tv_g - tv_o) / tv_o < 0.02, (tv_g, tv_o)
+    w2 = W.ch4_heat_bath(n_cells=40, per_cell=500)
+    g2 = hcao.from_workload(w2, precision=hcao.FP32)
+    g2.step(5)
+    o2 = oracle.from_workload(w2)
+    o2.step(5)
+    ng = int(g2.read_reaction_counts(0, 1)[0])
+    no = int(o2.read_counters(0)[8])
+    assert abs(ng - no) < 3 * np.sqrt(no) + 10, (ng, no)
