@@ -77,6 +77,9 @@ struct hcao_ctx {
     uint32_t* d_totals = nullptr;
     uint32_t* d_cflag = nullptr;
     void* d_cscratch = nullptr;
+    uint2* d_qA = nullptr;
+    uint4* d_qB = nullptr;
+    uint32_t* d_qsize = nullptr;
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint32_t* d_err = nullptr;
@@ -233,6 +236,7 @@ DevPair pair_consts(const hcao_ctx* ctx, int a, int b) {
     p.C_f = (float)p.C;
     p.fp_f = (float)p.fp;
     p.fq_f = (float)p.fq;
+    p.inv2mr_f = (float)(2.0 / p.mr);
     return p;
 }
 
@@ -321,6 +325,10 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         ctx->d_cscratch = nullptr;
         ctx->pair_cap = std::max<uint64_t>(pairs, 1024);
         CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
+        dfree(ctx, ctx->d_qA);
+        dfree(ctx, ctx->d_qB);
+        CU(dalloc(ctx, &ctx->d_qA, (size_t)ctx->pair_cap));
+        CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
     }
     if (ctx->hc.creates && !ctx->d_cscratch)
@@ -403,6 +411,10 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.totals = ctx->d_totals;
     a.cflag = ctx->d_cflag;
     a.cscratch = ctx->d_cscratch;
+    a.qA = ctx->d_qA;
+    a.qB = ctx->d_qB;
+    a.qsize = ctx->d_qsize;
+    a.has_reactions = ctx->n_reactions > 0 ? 1 : 0;
     a.pair_cap = ctx->pair_cap;
     a.log = ctx->d_log;
     a.log_on = ctx->log_on ? 1 : 0;
@@ -451,7 +463,8 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     int dev = ctx->cfg.device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
-    if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess) {
+    if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_qsize, 2 * MAX_ROUNDS) != cudaSuccess) {
         delete ctx;
         return HCAO_ENOMEM;
     }
@@ -484,6 +497,9 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_cflag);
     if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
     dfree(ctx, ctx->d_log);
+    dfree(ctx, ctx->d_qA);
+    dfree(ctx, ctx->d_qB);
+    dfree(ctx, ctx->d_qsize);
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);

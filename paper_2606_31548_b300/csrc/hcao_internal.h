@@ -64,7 +64,7 @@ struct DevSpecies {
 
 struct DevPair {
     double mr, C, mt, fp, fq;        // reduced mass, VHS constant, total mass, velocity shares
-    float mr_f, C_f, fp_f, fq_f;
+    float mr_f, C_f, fp_f, fq_f, inv2mr_f, pad_f;
 };
 
 struct DevReaction {
@@ -116,6 +116,10 @@ struct StepArgs {
     uint32_t* totals;               // [MAX_ROUNDS + 1]
     uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
     void* cscratch;                 // per-pair record of a particle created by a reaction
+    uint2* qA;                      // accepted pairs of the current round (cell, pair)
+    uint4* qB;                      // reacting pairs (cell, pair, channel)
+    uint32_t* qsize;                // [2 * MAX_ROUNDS] queue lengths per round
+    int has_reactions;
     uint64_t pair_cap;              // capacity of cflag / log
     hcao_log_rec* log;
     int log_on;

@@ -4,12 +4,18 @@
 //   k_setup   (1 CTA)   NTC candidate count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c
 //                       with stochastic rounding, Feistel keys per pairing round,
 //                       block-wide scans that give every candidate pair a flat index.
-//   k_collide (grid)    one thread per candidate pair: Feistel pair draw, VHS
-//                       acceptance, QK reaction test (Eq. Ecoll-diss, Eq.
-//                       Ecoll-exch, competing reactions), reaction execution or
-//                       HCAO Larsen-Borgnakke relaxation of both molecules (the
+//   per pairing round, three grid kernels over compacted work:
+//   k_select  (grid)    one thread per candidate pair: Feistel pair draw, VHS
+//                       acceptance; accepted pairs appended to a queue.
+//   k_relax   (grid)    one thread per accepted pair: QK reaction test (Eq.
+//                       Ecoll-diss, Eq. Ecoll-exch, competing reactions);
+//                       reacting pairs to a second queue, the rest get the HCAO
+//                       Larsen-Borgnakke relaxation of both molecules (the
 //                       joint acceptance of all modes, sampled exactly with the
-//                       K5 tables), isotropic VHS scattering.
+//                       K5 tables) and isotropic VHS scattering.
+//   k_react   (grid)    one thread per reacting pair: dissociation / exchange.
+// Queue order is irrelevant: pairs of one round are disjoint and every draw is
+// keyed by (step, cell, round, pair), never by a thread or queue position.
 //   k_finish  (warp/cell) (sigma g)_max update, per-cell counters, stable append
 //                       of particles created by dissociation, step counter.
 // Randomness: Philox4x32-10 keyed by the reservoir seed, counter
@@ -468,90 +474,58 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
     return true;
 }
 
-struct Chan {
-    int rx, side, mode;
-    double ex;
+// ------------------------------------------------------------- one pair
+// Where pair k of round r of cell c lives: its Feistel members, its event slot.
+struct PairLoc {
+    uint32_t N, lcell, rk, ev_idx, ip, iq;
+    void* recs;
+    double sgmax;
 };
-constexpr int MAX_CHAN = 40;
+__device__ __forceinline__ PairLoc locate(const StepArgs& A, int c, int r, uint32_t k) {
+    const DevCell& cell = A.cells[c];
+    PairLoc L;
+    L.N = cell.n;
+    L.lcell = cell.lcell;
+    L.rk = ((uint32_t)r << 24) | k;
+    L.ev_idx = A.abase[c] + (uint32_t)r * (L.N >> 1) + k;
+    const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
+    L.ip = feistel(2u * k, L.N, key);
+    L.iq = feistel(2u * k + 1u, L.N, key);
+    L.recs = cell.rec;
+    L.sgmax = cell.sgmax;
+    return L;
+}
 
-// One candidate pair: VHS acceptance (NTC), QK reaction test, reaction or LB
-// relaxation of molecule 1 then molecule 2, isotropic VHS scattering.
+// channel id: reaction (3 bits) | side << 3 | broken stretch << 4
+__device__ __forceinline__ uint32_t chan_pack(int rx, int side, int mode) {
+    return (uint32_t)rx | ((uint32_t)side << 3) | ((uint32_t)mode << 4);
+}
+
+// QK reaction test: channels in fixed order (partner 1 stretches, partner 2
+// stretches, exchange); one with E_excess > 0 is taken, several are chosen
+// with probability proportional to E_excess ("Competing reactions").  Two
+// passes over the same channel list instead of storing it.
 template <class R>
-__device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double& seen_max) {
-    using Rec = typename RecOf<R>::T;
-    constexpr bool F64 = std::is_same<R, double>::value;
-    const Consts* __restrict__ C = A.C;
-    DevCell& cell = A.cells[c];
-    const DevRes& rs = A.res[cell.res];
-    const uint32_t N = cell.n;
-    const uint32_t P = N >> 1;
-    const uint32_t lcell = cell.lcell;
-    const uint32_t rk = ((uint32_t)r << 24) | k;
-    const uint32_t gpair = (uint32_t)r * P + k;  // pair number within the cell and step
-    const uint32_t ev_idx = A.abase[c] + gpair;
-    uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
-    const uint32_t ip = feistel(2u * k, N, key);
-    const uint32_t iq = feistel(2u * k + 1u, N, key);
-    Rec* recs = reinterpret_cast<Rec*>(cell.rec);
-    Rec Pr, Qr;
-    load_rec(recs + ip, Pr);
-    load_rec(recs + iq, Qr);
-    const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
-    const DevPair& pc = C->pair[sP * MAXS + sQ];
-    const int amode = C->amode;
-    PairOut o{0u, 0u};
-    hcao_log_rec lr{rs.step, lcell, rk, ip, iq, -1, 0u};
-
-    // relative velocity and VHS acceptance: sigma_T g = C g^(2 - 2 omega)
-    double g2d, sg;
-    bool accept;
-    Stream sp;
-    st_init(sp, rs.seed, rs.step, lcell, rk, PU_PAIR);
-    if constexpr (F64) {
-        const double gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-        g2d = gx * gx + gy * gy + gz * gz;
-        const double g = sqrt(g2d);
-        const double gp = amode == 0 ? sqrt(g) : (amode == 1 ? g : 1.0);
-        sg = pc.C * gp;
-        const double u_acc = st_u64(sp);
-        accept = u_acc < sg / cell.sgmax;
-    } else {
-        const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-        const float g2 = gx * gx + gy * gy + gz * gz;
-        g2d = (double)g2;
-        const float g = sqrtf(g2);
-        const float gp = amode == 0 ? sqrtf(g) : (amode == 1 ? g : 1.0f);
-        const float sgf = pc.C_f * gp;
-        sg = (double)sgf;
-        const float u_acc = st_u32(sp);
-        accept = u_acc < sgf / (float)cell.sgmax;
-    }
-    if (sg > seen_max) seen_max = sg;
-    if (!accept) {
-        A.cflag[ev_idx] = 0;
-        if (A.log_on) A.log[ev_idx] = lr;
-        return;
-    }
-    o.ev |= EV_ACC;
-    const double u_ster = st_u64(sp);
-    const double u_sel = st_u64(sp);
-    const double u_ch = st_u64(sp);
-    const double Etr = 0.5 * pc.mr * g2d;
+__device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
+                             const uint32_t qP[4], const uint32_t qQ[4], double Etr, double EvP,
+                             double EvQ, double u_ster, double u_sel, double u_ch, uint32_t& chan) {
     const DevSpecies& SP = C->sp[sP];
     const DevSpecies& SQ = C->sp[sQ];
-    const double EvP = evib64(A.lev64, SP, Pr.q);
-    const double EvQ = evib64(A.lev64, SQ, Qr.q);
-
-    // ---- QK reaction test: channels in fixed order (partner 1 stretches,
-    // partner 2 stretches, exchange); weighted by E_excess when several
-    Chan ch[MAX_CHAN];
     int nch = 0;
-    if (C->n_reactions > 0) {
-        for (int side = 0; side < 2; ++side) {
+    double tot = 0.0;
+    uint32_t last = 0u;
+    double t = 0.0, pre = 0.0;
+    bool picked = false;
+    for (int pass = 0; pass < 2 && !picked; ++pass) {
+        if (pass == 1) {
+            if (nch <= 1) break;
+            t = u_ch * tot;
+        }
+        for (int side = 0; side < 2 && !picked; ++side) {
             const int spA = side ? sQ : sP;
             const DevSpecies& SA = side ? SQ : SP;
             const double EvA = side ? EvQ : EvP;
-            for (int ri = 0; ri < C->n_reactions; ++ri) {
+            for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
                 const DevReaction& rx = C->rx[ri];
                 if (rx.type != HCAO_DISS || rx.A != spA) continue;
                 for (int j = 0; j < SA.n_stretch; ++j) {
@@ -560,11 +534,17 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
                     const double E0j = __ldg(A.lev64 + SA.lev_off[j]);
                     const double Ecoll = Etr + EvA - rx.zpesum + E0j;
                     const double Eex = Ecoll - SA.De[j];
-                    if (Eex > 0.0 && nch < MAX_CHAN) ch[nch++] = Chan{ri, side, j, Eex};
+                    if (!(Eex > 0.0)) continue;
+                    const uint32_t id = chan_pack(ri, side, j);
+                    if (pass == 0) { nch++; tot = tot + Eex; last = id; }
+                    else {
+                        pre = pre + Eex;
+                        if (t < pre) { chan = id; picked = true; break; }
+                    }
                 }
             }
         }
-        for (int ri = 0; ri < C->n_reactions; ++ri) {
+        for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
             const DevReaction& rx = C->rx[ri];
             if (rx.type != HCAO_EXCH) continue;
             int side;
@@ -573,7 +553,7 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
             else continue;
             if (!(u_ster < rx.steric)) continue;
             const DevSpecies& SA = side ? SQ : SP;
-            const uint32_t* qa = side ? Qr.q : Pr.q;
+            const uint32_t* qa = side ? qQ : qP;
             // Eq. Ecoll-exch; level energies include the ZPE (reading A12)
             double s = 0.0;
             if (rx.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH) {
@@ -585,80 +565,57 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
             }
             const double Ecoll = Etr + s;
             const double Eex = Ecoll - rx.Ea;
-            if (Eex > 0.0 && nch < MAX_CHAN) ch[nch++] = Chan{ri, side, 0, Eex};
+            if (!(Eex > 0.0)) continue;
+            const uint32_t id = chan_pack(ri, side, 0);
+            if (pass == 0) { nch++; tot = tot + Eex; last = id; }
+            else {
+                pre = pre + Eex;
+                if (t < pre) { chan = id; picked = true; }
+            }
         }
     }
-    if (nch > 0) {
-        int pick = 0;
-        if (nch > 1) {
-            double tot = 0.0;
-            for (int i = 0; i < nch; ++i) tot = tot + ch[i].ex;
-            const double t = u_ch * tot;
-            double pre = 0.0;
-            pick = nch - 1;
-            for (int i = 0; i < nch; ++i) {
-                pre = pre + ch[i].ex;
-                if (t < pre) { pick = i; break; }
-            }
-        }
-        const Chan cc = ch[pick];
-        const DevReaction& rx = C->rx[cc.rx];
-        double vA[3], vB[3], vN[3];
-        Rec& RA = cc.side ? Qr : Pr;
-        Rec& RB = cc.side ? Pr : Qr;
-        for (int i = 0; i < 3; ++i) { vA[i] = (double)RA.v[i]; vB[i] = (double)RB.v[i]; }
-        const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
-        bool done;
-        uint32_t q1[4], q2[4];
-        if (rx.type == HCAO_DISS) {
-            done = do_diss<R>(A, C, rx, vA, vB, spA, spB, cc.side ? EvQ : EvP, rs, lcell, rk, q1,
-                              q2, vN, o);
-            lr.aux = (uint32_t)cc.mode + (cc.side ? 16u : 0u);
-            if (done) {
-                // A becomes B in place; M keeps its state; C goes to the pair's
-                // scratch slot and is appended to the cell by k_finish
-                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
-                RA.meta = (uint32_t)rx.P0;
-                for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
-                Rec RN;
-                for (int i = 0; i < 3; ++i) RN.v[i] = (R)vN[i];
-                RN.meta = (uint32_t)rx.P1;
-                for (int j = 0; j < 4; ++j) RN.q[j] = q2[j];
-                if constexpr (F64) { RN.pad = 0; }
-                store_rec(reinterpret_cast<Rec*>(A.cscratch) + ev_idx, RN);
-                o.ev |= EV_CREATED;
-            }
-        } else {
-            done = do_exch<R>(A, C, rx, vA, vB, spA, spB, cc.side ? EvQ : EvP,
-                              cc.side ? EvP : EvQ, rs, lcell, rk, q1, q2, o);
-            lr.aux = (uint32_t)cc.side;
-            if (done) {
-                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
-                RA.meta = (uint32_t)rx.P0;
-                RB.meta = (uint32_t)rx.P1;
-                for (int j = 0; j < 4; ++j) { RA.q[j] = q1[j]; RB.q[j] = q2[j]; }
-            }
-        }
-        if (done) {
-            o.ev |= (uint32_t)(cc.rx + 1) << EV_RX_SHIFT;
-            lr.event = 1 + cc.rx;
-            store_rec(recs + ip, Pr);
-            store_rec(recs + iq, Qr);
-            o.ev |= (o.trials > 0xFFFFu ? 0xFFFFu : o.trials) << EV_TRIAL_SHIFT;
-            A.cflag[ev_idx] = o.ev;
-            if (A.log_on) A.log[ev_idx] = lr;
-            return;
-        }
-        o.ev |= EV_NOTEXEC;
-        lr.aux = 0u;
-    }
+    if (nch == 0) return 0;
+    if (!picked) chan = last;  // one channel, or rounding left t >= the full sum
+    if (nch == 1) chan = last;
+    return nch;
+}
 
-    // ---- HCAO LB relaxation: molecule 1, then molecule 2 with the updated E_rel
+// relative velocity, VHS sigma_T g and the pair's energies (shared by the phases)
+template <class R>
+__device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const R vP[3],
+                                            const R vQ[3], double& g2d, double& sg) {
+    if constexpr (std::is_same<R, double>::value) {
+        const double gx = vP[0] - vQ[0], gy = vP[1] - vQ[1], gz = vP[2] - vQ[2];
+        g2d = gx * gx + gy * gy + gz * gz;
+        const double g = sqrt(g2d);
+        const double gp = amode == 0 ? sqrt(g) : (amode == 1 ? g : 1.0);
+        sg = pc.C * gp;
+    } else {
+        const float gx = vP[0] - vQ[0], gy = vP[1] - vQ[1], gz = vP[2] - vQ[2];
+        const float g2 = gx * gx + gy * gy + gz * gz;
+        g2d = (double)g2;
+        const float g = sqrtf(g2);
+        const float gp = amode == 0 ? sqrtf(g) : (amode == 1 ? g : 1.0f);
+        sg = (double)(pc.C_f * gp);
+    }
+}
+
+// HCAO LB relaxation of molecule 1 then molecule 2 (with the updated E_rel),
+// then isotropic VHS scattering with the centre-of-mass velocity kept.
+template <class R, class Rec>
+__device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, const DevRes& rs,
+                              const PairLoc& L, Rec& Pr, Rec& Qr, const DevPair& pc, double Etr,
+                              double EvP, double EvQ, PairOut& o) {
+    constexpr bool F64 = std::is_same<R, double>::value;
+    const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+    const DevSpecies& SP = C->sp[sP];
+    const DevSpecies& SQ = C->sp[sQ];
+    const int amode = C->amode;
     double E = Etr;
     uint32_t tr = 0;
     if (SP.n_modes > 0) {
         Stream s1;
-        st_init(s1, rs.seed, rs.step, lcell, rk, PU_LB_A);
+        st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
         const double Ec = E + EvP;
         uint32_t nq[4] = {Pr.q[0], Pr.q[1], Pr.q[2], Pr.q[3]};
         o.ev += 1u << EV_SAMP_SHIFT;
@@ -681,7 +638,7 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
     }
     if (SQ.n_modes > 0) {
         Stream s2;
-        st_init(s2, rs.seed, rs.step, lcell, rk, PU_LB_B);
+        st_init(s2, rs.seed, rs.step, L.lcell, L.rk, PU_LB_B);
         const double Ec = E + EvQ;
         uint32_t nq[4] = {Qr.q[0], Qr.q[1], Qr.q[2], Qr.q[3]};
         o.ev += 1u << EV_SAMP_SHIFT;
@@ -703,10 +660,8 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
         }
     }
     o.trials += tr;
-
-    // ---- isotropic VHS scattering, centre-of-mass velocity kept
     Stream ss;
-    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
     if constexpr (F64) {
         const double gn = sqrt(2.0 * E / pc.mr);
         double d[3];
@@ -720,7 +675,7 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
             Qr.v[i] = V[i] - pc.fq * G;
         }
     } else {
-        const float gn = sqrtf((float)(E * (2.0 / pc.mr)));
+        const float gn = sqrtf((float)E * pc.inv2mr_f);
         float d[3];
         iso_dir<float>(ss, d);
         float V[3];
@@ -731,12 +686,33 @@ __device__ void process_pair(const StepArgs& A, int c, int r, uint32_t k, double
             Qr.v[i] = V[i] - pc.fq_f * G;
         }
     }
-    store_rec(recs + ip, Pr);
-    store_rec(recs + iq, Qr);
-    o.ev |= (o.trials > 0xFFFFu ? 0xFFFFu : o.trials) << EV_TRIAL_SHIFT;
-    A.cflag[ev_idx] = o.ev;
-    lr.event = 0;
-    if (A.log_on) A.log[ev_idx] = lr;
+}
+
+__device__ __forceinline__ uint32_t ev_final(const PairOut& o) {
+    return o.ev | ((o.trials > 0xFFFFu ? 0xFFFFu : o.trials) << EV_TRIAL_SHIFT);
+}
+
+// warp-aggregated append of one entry per lane with `want` to a queue
+__device__ __forceinline__ uint32_t queue_slot(uint32_t* size, bool want) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, want);
+    if (!want) return 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(size, (uint32_t)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + (uint32_t)__popc(m & ((1u << lane) - 1u));
+}
+
+// cell of flat pair index g in a prefix array (largest c with pb[c] <= g)
+__device__ __forceinline__ int cell_of(const uint32_t* pb, int n_cells, uint32_t g) {
+    int lo = 0, hi = n_cells;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pb + mid) <= g) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // ------------------------------------------------------------- kernels
@@ -822,6 +798,7 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1)] = 0;
         A.abase[0] = 0;
+        for (int i = 0; i < 2 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
     }
     __syncthreads();
     for (int r = 0; r < R; ++r) block_scan_inplace(A.pbase + r * (nc + 1), nc);
@@ -835,31 +812,60 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
 void launch_setup(const StepArgs& a, cudaStream_t s) { k_setup<<<1, SETUP_THREADS, 0, s>>>(a); }
 #endif
 
+// Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
+// pairs are finished here; accepted ones go to the relaxation queue.
 template <class R>
-__global__ void __launch_bounds__(128) k_collide(StepArgs A, int r) {
+__global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
+    using Rec = typename RecOf<R>::T;
     const uint32_t total = A.totals[r];
     const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        int lo = 0, hi = A.n_cells;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(pb + mid) <= g) lo = mid; else hi = mid;
+    const Consts* __restrict__ C = A.C;
+    const int amode = C->amode;
+    uint32_t* qsize = A.qsize + 2 * r;
+    for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
+        const uint32_t g = g0 + threadIdx.x;
+        const bool valid = g < total;
+        int c = 0;
+        bool accept = false;
+        double sg = 0.0;
+        uint32_t k = 0;
+        if (valid) {
+            c = cell_of(pb, A.n_cells, g);
+            k = g - __ldg(pb + c);
+            const PairLoc L = locate(A, c, r, k);
+            const DevRes& rs = A.res[A.cells[c].res];
+            const Rec* recs = reinterpret_cast<const Rec*>(L.recs);
+            Rec Pr, Qr;
+            load_rec(recs + L.ip, Pr);
+            load_rec(recs + L.iq, Qr);
+            const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+            double g2d;
+            pair_energy<R>(C->pair[sP * MAXS + sQ], amode, Pr.v, Qr.v, g2d, sg);
+            Stream sp;
+            st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
+            if constexpr (std::is_same<R, double>::value) accept = st_u64(sp) < sg / L.sgmax;
+            else accept = st_u32(sp) < (float)sg / (float)L.sgmax;
+            if (!accept) {
+                A.cflag[L.ev_idx] = 0u;
+                if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{rs.step, L.lcell, L.rk, L.ip, L.iq, -1, 0u};
+            }
         }
-        double seen = 0.0;
-        process_pair<R>(A, lo, r, g - __ldg(pb + lo), seen);
+        const uint32_t slot = queue_slot(qsize, accept);
+        if (accept) A.qA[slot] = make_uint2((uint32_t)c, k);
         // per-cell max of sigma_T g: lanes of one cell combine before the atomic
         const unsigned act = __activemask();
         const int lane = threadIdx.x & 31;
-        unsigned left = act;
+        const int key = valid ? c : -1;
+        unsigned left = __ballot_sync(act, valid);
         while (left) {
             const int leader = __ffs(left) - 1;
-            const int cl = __shfl_sync(act, lo, leader);
-            const unsigned grp = __ballot_sync(act, lo == cl);
+            const int cl = __shfl_sync(act, key, leader);
+            const unsigned grp = __ballot_sync(act, key == cl);
             double mx = 0.0;
             unsigned g2 = grp;
             while (g2) {
-                const double v = __shfl_sync(act, seen, __ffs(g2) - 1);
+                const double v = __shfl_sync(act, sg, __ffs(g2) - 1);
                 if (v > mx) mx = v;
                 g2 &= g2 - 1;
             }
@@ -867,6 +873,137 @@ __global__ void __launch_bounds__(128) k_collide(StepArgs A, int r) {
                 atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong(mx));
             left &= ~grp;
         }
+    }
+}
+
+// Phase 2: accepted pairs.  QK reaction test; reacting pairs go to the
+// reaction queue, the others are relaxed and scattered here.
+template <class R>
+__global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
+    using Rec = typename RecOf<R>::T;
+    const uint32_t total = A.qsize[2 * r];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const Consts* __restrict__ C = A.C;
+    const int amode = C->amode;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const uint2 e = A.qA[g];
+        const int c = (int)e.x;
+        const PairLoc L = locate(A, c, r, e.y);
+        const DevRes& rs = A.res[A.cells[c].res];
+        Rec* recs = reinterpret_cast<Rec*>(L.recs);
+        Rec Pr, Qr;
+        load_rec(recs + L.ip, Pr);
+        load_rec(recs + L.iq, Qr);
+        const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+        const DevPair& pc = C->pair[sP * MAXS + sQ];
+        double g2d, sg;
+        pair_energy<R>(pc, amode, Pr.v, Qr.v, g2d, sg);
+        const double Etr = 0.5 * pc.mr * g2d;
+        const double EvP = evib64(A.lev64, C->sp[sP], Pr.q);
+        const double EvQ = evib64(A.lev64, C->sp[sQ], Qr.q);
+        if (C->n_reactions > 0) {
+            Stream sp;
+            st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
+            st_u64(sp);
+            const double u_ster = st_u64(sp);
+            const double u_sel = st_u64(sp);
+            const double u_ch = st_u64(sp);
+            uint32_t chan = 0u;
+            const int nch = reaction_pick<R>(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel,
+                                             u_ch, chan);
+            if (nch > 0) {
+                const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
+                A.qB[slot] = make_uint4((uint32_t)c, e.y, chan, 0u);
+                continue;
+            }
+        }
+        PairOut o{EV_ACC, 0u};
+        relax_scatter<R>(A, C, rs, L, Pr, Qr, pc, Etr, EvP, EvQ, o);
+        store_rec(recs + L.ip, Pr);
+        store_rec(recs + L.iq, Qr);
+        A.cflag[L.ev_idx] = ev_final(o);
+        if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+    }
+}
+
+// Phase 3: pairs whose reaction test picked a channel: dissociation or
+// exchange; a reaction whose products cannot be formed falls back to
+// relaxation.
+template <class R>
+__global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
+    using Rec = typename RecOf<R>::T;
+    const uint32_t total = A.qsize[2 * r + 1];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const Consts* __restrict__ C = A.C;
+    const int amode = C->amode;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const uint4 e = A.qB[g];
+        const int c = (int)e.x;
+        const PairLoc L = locate(A, c, r, e.y);
+        const DevRes& rs = A.res[A.cells[c].res];
+        Rec* recs = reinterpret_cast<Rec*>(L.recs);
+        Rec Pr, Qr;
+        load_rec(recs + L.ip, Pr);
+        load_rec(recs + L.iq, Qr);
+        const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+        const DevPair& pc = C->pair[sP * MAXS + sQ];
+        double g2d, sg;
+        pair_energy<R>(pc, amode, Pr.v, Qr.v, g2d, sg);
+        const double Etr = 0.5 * pc.mr * g2d;
+        const double EvP = evib64(A.lev64, C->sp[sP], Pr.q);
+        const double EvQ = evib64(A.lev64, C->sp[sQ], Qr.q);
+        const int rxi = (int)(e.z & 7u), side = (int)((e.z >> 3) & 1u), mode = (int)(e.z >> 4);
+        const DevReaction& rx = C->rx[rxi];
+        PairOut o{EV_ACC, 0u};
+        hcao_log_rec lr{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+        double vA[3], vB[3], vN[3];
+        Rec& RA = side ? Qr : Pr;
+        Rec& RB = side ? Pr : Qr;
+        for (int i = 0; i < 3; ++i) { vA[i] = (double)RA.v[i]; vB[i] = (double)RB.v[i]; }
+        const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
+        uint32_t q1[4], q2[4];
+        bool done;
+        if (rx.type == HCAO_DISS) {
+            done = do_diss<R>(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
+                              vN, o);
+            lr.aux = (uint32_t)mode + (side ? 16u : 0u);
+            if (done) {
+                // A becomes B in place; M keeps its state; C goes to the pair's
+                // scratch slot and is appended to the cell by k_finish
+                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
+                RA.meta = (uint32_t)rx.P0;
+                for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                Rec RN;
+                for (int i = 0; i < 3; ++i) RN.v[i] = (R)vN[i];
+                RN.meta = (uint32_t)rx.P1;
+                for (int j = 0; j < 4; ++j) RN.q[j] = q2[j];
+                if constexpr (std::is_same<R, double>::value) { RN.pad = 0; }
+                store_rec(reinterpret_cast<Rec*>(A.cscratch) + L.ev_idx, RN);
+                o.ev |= EV_CREATED;
+            }
+        } else {
+            done = do_exch<R>(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, side ? EvP : EvQ, rs,
+                              L.lcell, L.rk, q1, q2, o);
+            lr.aux = (uint32_t)side;
+            if (done) {
+                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
+                RA.meta = (uint32_t)rx.P0;
+                RB.meta = (uint32_t)rx.P1;
+                for (int j = 0; j < 4; ++j) { RA.q[j] = q1[j]; RB.q[j] = q2[j]; }
+            }
+        }
+        if (done) {
+            o.ev |= (uint32_t)(rxi + 1) << EV_RX_SHIFT;
+            lr.event = 1 + rxi;
+        } else {
+            o.ev |= EV_NOTEXEC;
+            lr.aux = 0u;
+            relax_scatter<R>(A, C, rs, L, Pr, Qr, pc, Etr, EvP, EvQ, o);
+        }
+        store_rec(recs + L.ip, Pr);
+        store_rec(recs + L.iq, Qr);
+        A.cflag[L.ev_idx] = ev_final(o);
+        if (A.log_on) A.log[L.ev_idx] = lr;
     }
 }
 
@@ -942,7 +1079,10 @@ __global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* 
 
 template <class R>
 void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {
-    k_collide<R><<<grid, block, 0, s>>>(a, r);
+    (void)block;
+    k_select<R><<<grid, 256, 0, s>>>(a, r);
+    k_relax<R><<<grid, 128, 0, s>>>(a, r);
+    if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
 }
 template <class R>
 void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
@@ -954,7 +1094,7 @@ void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, ui
     launch_setup(a, s);
     for (int r = 0; r < a.max_rounds; ++r) launch_collide_impl<R>(a, r, grid, block, s);
     launch_finish_impl<R>(a, s);
-    if (launches) *launches += 2 + a.max_rounds;
+    if (launches) *launches += 2 + a.max_rounds * (a.has_reactions ? 3 : 2);
 }
 
 // ------------------------------------------------------------- load / read kernels
