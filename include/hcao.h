@@ -194,6 +194,17 @@ hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* host_out, int64_t max, in
 hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint32_t n_cells,
                            uint32_t* perm, uint32_t* offsets);
 
+/* The relaxation step's sampler alone (diagnostics, distribution tests):
+   n independent post-collision vibrational states of species sp at collision
+   energy Ec (J), drawn with the sampler of hcao_step in the context's
+   precision (the joint LB acceptance of all modes, Sec. implementation of the
+   HCAO model).  Sample i uses the Philox stream keyed by seed with counter
+   (i, i >> 32, 0, 8 << 24 | block).  host_qn: n x 16 bytes; *host_trials
+   (may be NULL) receives the total number of trials.  HCAO_EINVAL if Ec is
+   outside the sampler's tables or sp has no vibrational modes. */
+hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int64_t n,
+                           uint8_t* host_qn, uint64_t* host_trials);
+
 /* Level energy (J) of level `level` of mode `mode` of species sp, and the
    number of levels; host-side table lookups. */
 hcao_status hcao_level_energy(const hcao_ctx* ctx, int sp, int mode, int level, double* out);

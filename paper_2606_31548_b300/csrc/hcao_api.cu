@@ -218,6 +218,57 @@ void build_tables(int amode, int n, const std::vector<R>* lev, const R* base, R 
     }
 }
 
+// FP32 tables on the buckets idx(E) = ceil(sqrt((E - base) * inv)) (IEEE
+// float, as on the device).  Entry m is evaluated at the bucket's upper edge
+// G_m, the largest float whose index is <= m (bisection over the ordered bit
+// patterns of positive floats), so every budget in the bucket is bounded.
+int idx_f32(float base, float inv, int MT, float E) {
+    if (!(E > base)) return 0;
+    const float c = std::ceil(std::sqrt((E - base) * inv));
+    if (!(c <= (float)(MT - 1))) return MT;
+    return (int)c;
+}
+float bucket_top_f32(float base, float inv, int MT, int m) {
+    if (m <= 0) return base;
+    uint32_t lo, hi;
+    float fb = base, fmax = 3.4028234663852886e38f;
+    std::memcpy(&lo, &fb, 4);
+    std::memcpy(&hi, &fmax, 4);
+    while (hi - lo > 1) {  // idx(lo) <= m < idx(hi)
+        const uint32_t mid = lo + (hi - lo) / 2;
+        float f;
+        std::memcpy(&f, &mid, 4);
+        if (idx_f32(base, inv, MT, f) <= m) lo = mid; else hi = mid;
+    }
+    float r;
+    std::memcpy(&r, &lo, 4);
+    return r;
+}
+void build_tables_f32(int amode, int n, const std::vector<float>* lev, const float* base, float inv, int MT,
+                      std::vector<float>& out) {
+    out.assign((size_t)n * MT, 0.0f);
+    for (int k = n - 1; k >= 0; --k) {
+        for (int m = 0; m < MT; ++m) {
+            const float g = bucket_top_f32(base[k], inv, MT, m);
+            float sum = 0.0f;
+            for (size_t i = 0; i < lev[k].size(); ++i) {
+                if (!(lev[k][i] < g)) break;
+                const float x = g - lev[k][i];
+                float w;
+                if (k == n - 1) {
+                    w = lbpow_host<float>(amode, x);
+                } else {
+                    int mm = idx_f32(base[k + 1], inv, MT, x);
+                    if (mm > MT - 1) mm = MT - 1;
+                    w = mm == 0 ? 0.0f : out[(size_t)(k + 1) * MT + mm];
+                }
+                sum = sum + w;
+            }
+            out[(size_t)k * MT + m] = sum;
+        }
+    }
+}
+
 // VHS pair constants: sigma_T g = C g^(2 - 2 omega),
 // C = ((pi*d)*d) * (2 k T_ref / m_r)^(omega-1/2) / Gamma(5/2 - omega),
 // d, T_ref the means of both species', m_r = (mA*mB)/(mA+mB).
@@ -616,9 +667,10 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
                     for (size_t l = 0; l < s.lev[j].size(); ++l) L[j][l] = (float)s.lev[j][l];
                 }
                 std::vector<float> t;
-                build_tables<float>(amode, nm, L, D.base_f, D.cq_f, MT, t);
+                build_tables_f32(amode, nm, L, D.base_f, D.inv_cq_f, MT, t);
                 D.tab_off = (int)H32.size();
                 H32.insert(H32.end(), t.begin(), t.end());
+                D.top = (double)bucket_top_f32(D.base_f[0], D.inv_cq_f, MT, M);
             }
         }
     }
@@ -880,6 +932,40 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
     dfree(ctx, dbt);
     dfree(ctx, dsa);
     dfree(ctx, doff);
+    return map_err(ctx);
+}
+
+hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int64_t n, uint8_t* host_qn,
+                           uint64_t* host_trials) {
+    if (!ctx || n < 0 || (n > 0 && !host_qn)) return HCAO_EINVAL;
+    if (sp < 0 || sp >= ctx->n_species || ctx->sp[sp].n_modes == 0)
+        return fail(ctx, HCAO_EINVAL, "sample_lb: species without vibrational modes");
+    uint8_t* dq = nullptr;
+    unsigned long long* dt = nullptr;
+    int* dst = nullptr;
+    CU(dalloc(ctx, &dq, (size_t)std::max<int64_t>(n, 1) * 16));
+    CU(dalloc(ctx, &dt, 1));
+    CU(dalloc(ctx, &dst, 1));
+    CU(cudaMemsetAsync(dt, 0, sizeof(unsigned long long), ctx->stream));
+    CU(cudaMemsetAsync(dst, 0, sizeof(int), ctx->stream));
+    StepArgs a = make_args(ctx);
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_sample_diag<double>(a, sp, Ec, seed, n, dq, dt, dst, ctx->stream);
+    else
+        launch_sample_diag<float>(a, sp, Ec, seed, n, dq, dt, dst, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    unsigned long long tr = 0;
+    int status = 0;
+    if (n > 0) CU(cudaMemcpyAsync(host_qn, dq, (size_t)n * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&tr, dt, sizeof tr, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&status, dst, sizeof status, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, dq);
+    dfree(ctx, dt);
+    dfree(ctx, dst);
+    if (host_trials) *host_trials = tr;
+    if (status != 0) return fail(ctx, HCAO_EINVAL, "sample_lb: collision energy outside the tables");
     return map_err(ctx);
 }
 

@@ -153,6 +153,9 @@ template <class R> void launch_init_vib(const DevCell* cells, int cell0, int n_c
 template <class R> void launch_moments(const DevCell* cells, int cell0, int n_cells,
                                        const Consts* C, const double* lev64, double* acc,
                                        unsigned long long* cnt, cudaStream_t s);
+template <class R> void launch_sample_diag(const StepArgs& a, int sp, double Ec, uint64_t seed,
+                                           int64_t n, uint8_t* out, unsigned long long* trials,
+                                           int* status, cudaStream_t s);
 template <class R> void launch_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
                                         int mode, unsigned long long* hist, cudaStream_t s);
 

@@ -230,6 +230,19 @@ __device__ __forceinline__ int grid_idx(R base, R cq, R inv, int MT, R E) {
     return m;
 }
 
+// FP32 buckets: idx(E) = ceil(sqrt((E - base) * inv)) in IEEE float (0 if E <=
+// base, MT if above the last bucket).  The host builds the FP32 tables at each
+// bucket's upper edge (the largest float with that index), so the same exact
+// bound holds without comparing against grid points.
+template <>
+__device__ __forceinline__ int grid_idx<float>(float base, float cq, float inv, int MT, float E) {
+    (void)cq;
+    if (!(E > base)) return 0;
+    const float c = ceilf(__fsqrt_rn(__fmul_rn(__fsub_rn(E, base), inv)));
+    if (!(c <= (float)(MT - 1))) return MT;
+    return (int)c;
+}
+
 __device__ __forceinline__ double evib64(const double* lev, const DevSpecies& S, const uint32_t q[4]) {
     double e = 0.0;
     for (int j = 0; j < S.n_modes; ++j) e = e + __ldg(lev + S.lev_off[j] + get_q(q, j));
@@ -600,6 +613,127 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
     }
 }
 
+// FP32 LB relaxation of up to two molecules as one flattened loop: every
+// iteration is one level step of the K5 draw, whatever molecule, mode or trial
+// a lane is in, so the lanes of a warp stay converged.  Draws, tables and the
+// target are those of sample_lb<float>; bookkeeping of the relative energy in
+// FP64.  sp < 0 or a species without modes skips that molecule.  Returns the
+// relative energy left for scattering.
+static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict__ C, int spA, uint32_t* qA,
+                             double EvA, Stream stA, int spB, uint32_t* qB, double EvB, Stream stB,
+                             double Erel, PairOut& o) {
+    const float* __restrict__ Lv = A.lev32;
+    const float* __restrict__ Hb = A.H32;
+    const int amode = C->amode;
+    int mol = 0;
+    bool starting = true;
+    // molecule state
+    const DevSpecies* S = nullptr;
+    uint32_t* q = nullptr;
+    double Ecd = 0.0, Evold = 0.0;
+    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
+    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0;
+    const float* Hm = nullptr;   // table 0 of the species
+    const float* Lk = nullptr;   // levels of mode k
+    const float* Hn = nullptr;   // table k + 1
+    bool last = false;
+    uint32_t nq[4] = {0u, 0u, 0u, 0u};
+    uint32_t trials = 0, trials_all = 0;
+    Stream st = stA;
+    for (int guard = 0; mol < 2 && guard < (1 << 26); ++guard) {
+        if (starting) {
+            const int sp = mol ? spB : spA;
+            if (sp < 0 || C->sp[sp].n_modes == 0) { mol++; continue; }
+            S = &C->sp[sp];
+            q = mol ? qB : qA;
+            Evold = mol ? EvB : EvA;
+            st = mol ? stB : stA;
+            Ecd = Erel + Evold;
+            n = S->n_modes;
+            MT = S->MT;
+            inv = S->inv_cq_f;
+            Hm = Hb + S->tab_off;
+            o.ev += 1u << EV_SAMP_SHIFT;
+            Ec = (float)Ecd;
+            m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
+            starting = false;
+            if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; Erel = Ecd - Evold; mol++; starting = true; continue; }
+            if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) {
+                o.ev += 1u << EV_DEGEN_SHIFT; Erel = Ecd - Evold; mol++; starting = true; continue;
+            }
+            trials = 0;
+            nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+            if (__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f) {  // only the ground state fits
+                k = n;
+            } else {
+                k = 0;
+                i = -1;  // start mode 0 below
+            }
+            E = Ec;
+        }
+        if (k < n && i < 0) {  // start mode k of the current trial
+            if (k == 0) trials++;
+            const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+            t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
+            cum = 0.f;
+            i = 0;
+            Lk = Lv + S->lev_off[k];
+            nl = S->n_lev[k];
+            last = k == n - 1;
+            if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
+        }
+        if (k < n) {  // one level step
+            const float e = i < nl ? __ldg(Lk + i) : 0.f;
+            if (i < nl && e < E) {
+                const float x = __fsub_rn(E, e);
+                float w;
+                if (last) {
+                    w = lb_pow<float>(amode, x);
+                } else {
+                    const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
+                    w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
+                }
+                cum = __fadd_rn(cum, w);
+                if (t < cum) {
+                    set_q(nq, k, (uint32_t)i);
+                    E = __fsub_rn(E, e);
+                    k++;
+                    i = -1;
+                } else {
+                    i++;
+                }
+            } else if (trials >= A.reject_cap) {  // give up: keep the old state
+                atomicOr(A.err, (uint32_t)ERR_REJECT);
+                trials_all += trials;
+                Erel = Ecd - Evold;
+                mol++;
+                starting = true;
+                continue;
+            } else {  // the draw ran past the levels: restart the trial
+                k = 0;
+                i = -1;
+                E = Ec;
+                nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+            }
+            if (k < n) continue;
+        }
+        // molecule done: FP64 bookkeeping of the relative energy
+        trials_all += trials;
+        const double En = Ecd - evib64(A.lev64, *S, nq);
+        if (En >= 0.0) {
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            Erel = En;
+        } else {
+            o.ev += 1u << EV_DEGEN_SHIFT;
+            Erel = Ecd - Evold;
+        }
+        mol++;
+        starting = true;
+    }
+    o.trials += trials_all;
+    return Erel;
+}
+
 // HCAO LB relaxation of molecule 1 then molecule 2 (with the updated E_rel),
 // then isotropic VHS scattering with the centre-of-mass velocity kept.
 template <class R, class Rec>
@@ -613,6 +747,12 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
     const int amode = C->amode;
     double E = Etr;
     uint32_t tr = 0;
+    if constexpr (!F64) {
+        Stream s1, s2;
+        st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
+        st_init(s2, rs.seed, rs.step, L.lcell, L.rk, PU_LB_B);
+        E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
+    } else {
     if (SP.n_modes > 0) {
         Stream s1;
         st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
@@ -660,6 +800,7 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
         }
     }
     o.trials += tr;
+    }
     Stream ss;
     st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
     if constexpr (F64) {
@@ -1097,6 +1238,39 @@ void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, ui
     if (launches) *launches += 2 + a.max_rounds * (a.has_reactions ? 3 : 2);
 }
 
+// ------------------------------------------------------------- sampler diagnostics
+// n independent post-collision states of species sp at collision energy Ec,
+// sample i on the Philox stream (seed; i, i >> 32, 0; purpose 8).  FP64: the
+// sequential K5 sampler of the collision kernels; FP32: the flattened one.
+template <class R>
+__global__ void k_sample_diag(StepArgs A, int sp, double Ec, uint64_t seed, int64_t n, uint8_t* out,
+                              unsigned long long* trials, int* status) {
+    const Consts* __restrict__ C = A.C;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Stream st;
+        st_init(st, seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, 8u);
+        uint32_t q[4] = {0u, 0u, 0u, 0u};
+        PairOut o{0u, 0u};
+        int rc = S_OK;
+        if constexpr (std::is_same<R, double>::value) {
+            uint32_t tr = 0;
+            rc = sample_lb<double>(A, C->sp[sp], C->amode, Ec, st, q, tr);
+            o.trials = tr;
+        } else {
+            // the relative energy plus the ground state's energy is Ec
+            const double Ev0 = evib64(A.lev64, C->sp[sp], q);
+            relax_flat(A, C, sp, q, Ev0, st, -1, nullptr, 0.0, st, Ec - Ev0, o);
+            if ((o.ev >> EV_OVER_SHIFT) & 3u) rc = S_OVER;
+            if ((o.ev >> EV_DEGEN_SHIFT) & 3u) rc = S_DEGEN;
+        }
+        uint32_t* d = reinterpret_cast<uint32_t*>(out + 16 * i);
+        for (int w = 0; w < 4; ++w) d[w] = q[w];
+        atomicAdd(trials, (unsigned long long)o.trials);
+        if (rc != S_OK) atomicExch(status, rc);
+    }
+}
+
 // ------------------------------------------------------------- load / read kernels
 template <class R>
 __global__ void k_scatter_load(typename RecOf<R>::T* recs, const uint32_t* perm,
@@ -1291,6 +1465,15 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
         int grid = n_cells < 1184 ? n_cells : 1184;                                              \
         if (grid < 1) return;                                                                    \
         k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, C, lev64, acc, cnt);            \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_sample_diag<R>(const StepArgs& a, int sp, double Ec, uint64_t seed, int64_t n,   \
+                               uint8_t* out, unsigned long long* trials, int* status,            \
+                               cudaStream_t s) {                                                 \
+        int grid = (int)((n + 127) / 128);                                                       \
+        if (grid > 4096) grid = 4096;                                                            \
+        if (grid < 1) return;                                                                    \
+        k_sample_diag<R><<<grid, 128, 0, s>>>(a, sp, Ec, seed, n, out, trials, status);         \
     }                                                                                            \
     template <>                                                                                  \
     void launch_levelpop<R>(const DevCell* cells, int cell0, int n_cells, int sp, int mode,      \

@@ -28,7 +28,7 @@ EXPORTS = [
     "hcao_read_moments", "hcao_read_level_populations", "hcao_read_counters",
     "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
-    "hcao_set_profiling", "hcao_read_profile",
+    "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb",
 ]
 
 
@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
         L.hcao_cell_sort.argtypes = [vp, vp, i64, C.c_uint32, vp, vp]
         L.hcao_level_energy.argtypes = [vp, i32, i32, i32, C.POINTER(dbl)]
         L.hcao_n_levels.argtypes = [vp, i32, i32, C.POINTER(i32)]
+        L.hcao_sample_lb.argtypes = [vp, i32, dbl, u64, i64, vp, C.POINTER(u64)]
         L.hcao_set_profiling.argtypes = [vp, i32]
         L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
@@ -295,6 +296,13 @@ class Context:
         n = C.c_int()
         self._chk(self.L.hcao_n_levels(self.h, sp, mode, C.byref(n)))
         return n.value
+
+    def sample_lb(self, sp, Ec, seed, n):
+        """n post-collision states of species sp at collision energy Ec (device sampler)."""
+        out = np.zeros((n, 16), np.uint8)
+        tr = C.c_uint64(0)
+        self._chk(self.L.hcao_sample_lb(self.h, sp, Ec, seed, n, _p(out), C.byref(tr)))
+        return out, int(tr.value)
 
     def set_profiling(self, on=True) -> None:
         self._chk(self.L.hcao_set_profiling(self.h, 1 if on else 0))
