@@ -41,7 +41,8 @@ typedef enum {
     HCAO_EBUSY = -6,           /* job still running (serving) */
     HCAO_ECAPACITY = -7,       /* a cell ran out of particle slots */
     HCAO_EROUNDS = -8,         /* NTC needed more pairing rounds than configured */
-    HCAO_ENOTFOUND = -9
+    HCAO_ENOTFOUND = -9,
+    HCAO_ENONFINITE = -10      /* a non-finite velocity or (sigma_T g)_max was met */
 } hcao_status;
 
 enum { HCAO_FP64 = 0, HCAO_FP32 = 1 };

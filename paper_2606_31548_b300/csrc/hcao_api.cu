@@ -61,6 +61,7 @@ struct hcao_ctx {
     Consts* d_consts = nullptr;
     double* d_lev64 = nullptr;
     float* d_lev32 = nullptr;
+    long long* d_levfix = nullptr;
     double* d_H64 = nullptr;
     float* d_H32 = nullptr;
     int amode = -1;
@@ -119,6 +120,10 @@ void dfree(hcao_ctx* ctx, T*& p) {
     if (p) cudaFreeAsync(p, ctx->stream);
     p = nullptr;
 }
+
+// FP32-mode energy bookkeeping unit: 2^-100 J (int64 range +-7e-12 J,
+// resolution 8e-31 J)
+long long to_fix(double E) { return std::llround(std::ldexp(E, 100)); }
 
 size_t rec_size(const hcao_ctx* c) { return c->cfg.precision == HCAO_FP64 ? sizeof(RecD) : sizeof(RecF); }
 
@@ -324,6 +329,7 @@ hcao_status map_err(hcao_ctx* ctx) {
     if (e & ERR_CAPACITY) return fail(ctx, HCAO_ECAPACITY, "a cell ran out of particle slots");
     if (e & ERR_ROUNDS) return fail(ctx, HCAO_EROUNDS, "NTC needed more pairing rounds than max_rounds");
     if (e & ERR_LEVEL) return fail(ctx, HCAO_ELEVEL_OVERFLOW, "quantum number outside the level list");
+    if (e & ERR_NONFINITE) return fail(ctx, HCAO_ENONFINITE, "non-finite velocity or (sigma g)_max");
     return HCAO_OK;
 }
 
@@ -450,6 +456,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.C = ctx->d_consts;
     a.lev64 = ctx->d_lev64;
     a.lev32 = ctx->d_lev32;
+    a.levfix = ctx->d_levfix;
     a.H64 = ctx->d_H64;
     a.H32 = ctx->d_H32;
     a.cells = ctx->d_cells;
@@ -537,6 +544,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_consts);
     dfree(ctx, ctx->d_lev64);
     dfree(ctx, ctx->d_lev32);
+    dfree(ctx, ctx->d_levfix);
     dfree(ctx, ctx->d_H64);
     dfree(ctx, ctx->d_H32);
     dfree(ctx, ctx->d_res);
@@ -590,6 +598,7 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     // levels
     std::vector<double> lev64;
     std::vector<float> lev32;
+    std::vector<long long> levfix;
     for (int i = 0; i < n; ++i) {
         HostSpecies& s = ctx->sp[i];
         s.d = species[i];
@@ -615,19 +624,24 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
         HostSpecies& s = ctx->sp[i];
         DevSpecies& D = C.sp[i];
         D.mass = s.d.mass;
+        D.mass_f = (float)s.d.mass;
         D.E_form = s.d.E_form;
         D.zpe = s.zpe;
         D.n_modes = s.n_modes;
         D.n_stretch = s.d.n_stretch;
         D.M = M;
         D.MT = MT;
-        for (int j = 0; j < s.d.n_stretch; ++j) D.De[j] = s.De[j];
+        for (int j = 0; j < s.d.n_stretch; ++j) {
+            D.De[j] = s.De[j];
+            D.De_fix[j] = to_fix(s.De[j]);
+        }
         for (int j = 0; j < s.n_modes; ++j) {
             D.lev_off[j] = (int)lev64.size();
             D.n_lev[j] = (int)s.lev[j].size();
             for (double e : s.lev[j]) {
                 lev64.push_back(e);
                 lev32.push_back((float)e);
+                levfix.push_back(to_fix(e));
             }
         }
         // K5 grid: base_k = E_k(0) + base_{k+1}; delta = span / M
@@ -674,10 +688,20 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
             }
         }
     }
+    for (int i = 0; i < n; ++i) {
+        DevSpecies& D = C.sp[i];
+        long long z = 0;  // ZPE in fixed point: the exact sum of the ground levels
+        for (int j = 0; j < D.n_modes; ++j) z += levfix[D.lev_off[j]];
+        D.zpe_fix = z;
+        D.top_fix = std::isfinite(D.top) ? to_fix(D.top) : (long long)0x7FFFFFFFFFFFFFFFll;
+    }
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b) C.pair[a * MAXS + b] = pair_consts(ctx, a, b);
     CU(dalloc(ctx, &ctx->d_lev64, lev64.size()));
     CU(dalloc(ctx, &ctx->d_lev32, lev32.size()));
+    CU(dalloc(ctx, &ctx->d_levfix, levfix.size()));
+    CU(cudaMemcpyAsync(ctx->d_levfix, levfix.data(), sizeof(long long) * levfix.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
     CU(cudaMemcpyAsync(ctx->d_lev64, lev64.data(), sizeof(double) * lev64.size(), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->d_lev32, lev32.data(), sizeof(float) * lev32.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (!H64.empty()) {
@@ -723,6 +747,7 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
             // Eq. Ecoll-diss subtracts the ZPEs of A, B and C
             D.zpesum = A.zpe + ctx->sp[D.P0].zpe + ctx->sp[D.P1].zpe;
             D.dEf = (ctx->sp[D.P0].d.E_form + ctx->sp[D.P1].d.E_form) - A.d.E_form;
+            D.zpesum_fix = C.sp[D.A].zpe_fix + C.sp[D.P0].zpe_fix + C.sp[D.P1].zpe_fix;
             creates = 1;
         } else {
             if (r.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH && A.d.n_stretch == 0)
@@ -732,6 +757,8 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
             D.dEf = (ctx->sp[D.P0].d.E_form + ctx->sp[D.P1].d.E_form) -
                     (A.d.E_form + ctx->sp[D.B].d.E_form);
         }
+        D.dEf_fix = to_fix(D.dEf);
+        D.Ea_fix = to_fix(D.Ea);
     }
     C.n_reactions = n;
     C.creates = creates;

@@ -27,7 +27,7 @@ enum { CNT_CAND = 0, CNT_ACC, CNT_SAMPLES, CNT_TRIALS, CNT_OVER, CNT_DEGEN, CNT_
        CNT_STEPS, CNT_RX0 = 8, NCNT = 8 + MAXR };
 
 // sticky device error bits
-enum { ERR_REJECT = 1, ERR_CAPACITY = 2, ERR_ROUNDS = 4, ERR_LEVEL = 8 };
+enum { ERR_REJECT = 1, ERR_CAPACITY = 2, ERR_ROUNDS = 4, ERR_LEVEL = 8, ERR_NONFINITE = 16 };
 
 constexpr uint32_t SPECIES_NONE = 0xFFu;
 
@@ -59,7 +59,11 @@ struct DevSpecies {
     int lev_off[MAXM];               // offset of mode j's levels in the level arrays
     int n_lev[MAXM];
     int tab_off;                     // offset of table 0; table k at tab_off + k * MT
-    int pad[3];
+    float mass_f;
+    int pad[2];
+    // FP32-mode bookkeeping in int64 fixed point (1 unit = 2^-100 J)
+    long long zpe_fix, top_fix;
+    long long De_fix[MAXM];
 };
 
 struct DevPair {
@@ -74,6 +78,7 @@ struct DevReaction {
     int pad;
     double Ea, steric, zpesum, dEf;
     double alpha[MAXM];
+    long long Ea_fix, zpesum_fix, dEf_fix;   // FP32 mode (2^-100 J units)
 };
 
 struct Consts {
@@ -104,6 +109,7 @@ struct StepArgs {
     const Consts* C;
     const double* lev64;
     const float* lev32;
+    const long long* levfix;        // level energies in 2^-100 J units (FP32-mode bookkeeping)
     const double* H64;
     const float* H32;
     DevCell* cells;

@@ -249,6 +249,17 @@ __device__ __forceinline__ double evib64(const double* lev, const DevSpecies& S,
     return e;
 }
 
+// FP32-mode energy bookkeeping: int64 fixed point, 1 unit = 2^-100 J.  A
+// float energy converts exactly (a power-of-two scale); sums are exact.
+__device__ __forceinline__ long long f2fix(float x) { return __float2ll_rn(__fmul_rn(x, 0x1p100f)); }
+__device__ __forceinline__ float fix2f(long long a) { return __fmul_rn(__ll2float_rn(a), 0x1p-100f); }
+__device__ __forceinline__ double fix2d(long long a) { return __ll2double_rn(a) * 0x1p-100; }
+__device__ __forceinline__ long long evib_fix(const long long* lf, const DevSpecies& S, const uint32_t q[4]) {
+    long long e = 0;
+    for (int j = 0; j < S.n_modes; ++j) e += __ldg(lf + S.lev_off[j] + get_q(q, j));
+    return e;
+}
+
 enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
 
 // Post-collision vibrational state of one molecule at collision energy Ec:
@@ -616,26 +627,26 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
 // FP32 LB relaxation of up to two molecules as one flattened loop: every
 // iteration is one level step of the K5 draw, whatever molecule, mode or trial
 // a lane is in, so the lanes of a warp stay converged.  Draws, tables and the
-// target are those of sample_lb<float>; bookkeeping of the relative energy in
-// FP64.  sp < 0 or a species without modes skips that molecule.  Returns the
-// relative energy left for scattering.
-static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict__ C, int spA, uint32_t* qA,
-                             double EvA, Stream stA, int spB, uint32_t* qB, double EvB, Stream stB,
-                             double Erel, PairOut& o) {
+// target are those of sample_lb<float>; the relative energy is kept in int64
+// fixed point (exact sums).  sp < 0 or a species without modes skips that
+// molecule.  Returns the relative energy left for scattering.
+static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C,
+                                                       int spA, uint32_t (&qA)[4], long long EvA,
+                                                       Stream stA, int spB, uint32_t (&qB)[4],
+                                                       long long EvB, Stream stB, long long Erel,
+                                                       PairOut& o) {
     const float* __restrict__ Lv = A.lev32;
     const float* __restrict__ Hb = A.H32;
     const int amode = C->amode;
     int mol = 0;
     bool starting = true;
-    // molecule state
     const DevSpecies* S = nullptr;
-    uint32_t* q = nullptr;
-    double Ecd = 0.0, Evold = 0.0;
+    long long Ecd = 0, Evold = 0;
     float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
     int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0;
-    const float* Hm = nullptr;   // table 0 of the species
-    const float* Lk = nullptr;   // levels of mode k
-    const float* Hn = nullptr;   // table k + 1
+    const float* Hm = nullptr;
+    const float* Lk = nullptr;
+    const float* Hn = nullptr;
     bool last = false;
     uint32_t nq[4] = {0u, 0u, 0u, 0u};
     uint32_t trials = 0, trials_all = 0;
@@ -645,7 +656,6 @@ static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict_
             const int sp = mol ? spB : spA;
             if (sp < 0 || C->sp[sp].n_modes == 0) { mol++; continue; }
             S = &C->sp[sp];
-            q = mol ? qB : qA;
             Evold = mol ? EvB : EvA;
             st = mol ? stB : stA;
             Ecd = Erel + Evold;
@@ -654,7 +664,7 @@ static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict_
             inv = S->inv_cq_f;
             Hm = Hb + S->tab_off;
             o.ev += 1u << EV_SAMP_SHIFT;
-            Ec = (float)Ecd;
+            Ec = fix2f(Ecd);
             m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
             starting = false;
             if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; Erel = Ecd - Evold; mol++; starting = true; continue; }
@@ -667,7 +677,7 @@ static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict_
                 k = n;
             } else {
                 k = 0;
-                i = -1;  // start mode 0 below
+                i = -1;
             }
             E = Ec;
         }
@@ -717,11 +727,12 @@ static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict_
             }
             if (k < n) continue;
         }
-        // molecule done: FP64 bookkeeping of the relative energy
+        // molecule done: the new relative energy, exact in fixed point
         trials_all += trials;
-        const double En = Ecd - evib64(A.lev64, *S, nq);
-        if (En >= 0.0) {
-            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+        const long long En = Ecd - evib_fix(A.levfix, *S, nq);
+        if (En >= 0) {
+            if (mol == 0) { qA[0] = nq[0]; qA[1] = nq[1]; qA[2] = nq[2]; qA[3] = nq[3]; }
+            else { qB[0] = nq[0]; qB[1] = nq[1]; qB[2] = nq[2]; qB[3] = nq[3]; }
             Erel = En;
         } else {
             o.ev += 1u << EV_DEGEN_SHIFT;
@@ -732,6 +743,218 @@ static __device__ double relax_flat(const StepArgs& A, const Consts* __restrict_
     }
     o.trials += trials_all;
     return Erel;
+}
+
+// FP32 mode: QK reaction test in fixed point (exact thresholds), the same
+// channel order and E_excess-weighted choice as reaction_pick.
+static __device__ int reaction_pick_fix(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
+                                 const uint32_t qP[4], const uint32_t qQ[4], long long Etr,
+                                 long long EvP, long long EvQ, float u_ster, float u_sel, float u_ch,
+                                 uint32_t& chan) {
+    const DevSpecies& SP = C->sp[sP];
+    const DevSpecies& SQ = C->sp[sQ];
+    int nch = 0;
+    long long tot = 0;
+    uint32_t last = 0u;
+    double t = 0.0;
+    long long pre = 0;
+    bool picked = false;
+    for (int pass = 0; pass < 2 && !picked; ++pass) {
+        if (pass == 1) {
+            if (nch <= 1) break;
+            t = (double)u_ch * (double)tot;
+        }
+        for (int side = 0; side < 2 && !picked; ++side) {
+            const int spA = side ? sQ : sP;
+            const DevSpecies& SA = side ? SQ : SP;
+            const long long EvA = side ? EvQ : EvP;
+            for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
+                const DevReaction& rx = C->rx[ri];
+                if (rx.type != HCAO_DISS || rx.A != spA) continue;
+                const long long base = Etr + EvA - rx.zpesum_fix;
+                for (int j = 0; j < SA.n_stretch; ++j) {
+                    if (!((rx.mask >> j) & 1u)) continue;
+                    const long long Eex = base + __ldg(A.levfix + SA.lev_off[j]) - SA.De_fix[j];
+                    if (Eex <= 0) continue;
+                    const uint32_t id = chan_pack(ri, side, j);
+                    if (pass == 0) { nch++; tot += Eex; last = id; }
+                    else {
+                        pre += Eex;
+                        if (t < (double)pre) { chan = id; picked = true; break; }
+                    }
+                }
+            }
+        }
+        for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
+            const DevReaction& rx = C->rx[ri];
+            if (rx.type != HCAO_EXCH) continue;
+            int side;
+            if (sP == rx.A && sQ == rx.B) side = 0;
+            else if (sQ == rx.A && sP == rx.B) side = 1;
+            else continue;
+            if (!(u_ster < (float)rx.steric)) continue;
+            const DevSpecies& SA = side ? SQ : SP;
+            const uint32_t* qa = side ? qQ : qP;
+            long long s = 0;
+            if (rx.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH) {
+                const int js = min((int)(u_sel * (float)SA.n_stretch), SA.n_stretch - 1);
+                s = __ldg(A.levfix + SA.lev_off[js] + get_q(qa, js));
+            } else {
+                double sd = 0.0;
+                for (int j = 0; j < SA.n_modes; ++j)
+                    sd = sd + rx.alpha[j] * (double)__ldg(A.levfix + SA.lev_off[j] + get_q(qa, j));
+                s = __double2ll_rn(sd);
+            }
+            const long long Eex = Etr + s - rx.Ea_fix;
+            if (Eex <= 0) continue;
+            const uint32_t id = chan_pack(ri, side, 0);
+            if (pass == 0) { nch++; tot += Eex; last = id; }
+            else {
+                pre += Eex;
+                if (t < (double)pre) { chan = id; picked = true; }
+            }
+        }
+    }
+    if (nch == 0) return 0;
+    if (!picked || nch == 1) chan = last;
+    return nch;
+}
+
+// FP32 mode, dissociation A + M -> B + C + M: float kinematics, fixed-point
+// energies (the same product split as do_diss, reading A13).
+static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
+                            float vA[3], float vM[3], int spA, int spM, long long EvA, const DevRes& rs,
+                            uint32_t lcell, uint32_t rk, uint32_t qB[4], uint32_t qC[4], float vC[3],
+                            PairOut& o) {
+    const DevSpecies& sA = C->sp[spA];
+    const DevSpecies& sM = C->sp[spM];
+    const DevSpecies& sB = C->sp[rx.P0];
+    const DevSpecies& sC = C->sp[rx.P1];
+    // masses ~1e-26 kg: a product of two underflows FP32, so reduced masses
+    // come from the host-built pair table and only ratios are formed here
+    const float mA = sA.mass_f, mM = sM.mass_f, mB = sB.mass_f, mC = sC.mass_f;
+    const float mAM = mA + mM, mBC = mB + mC, mt = mBC + mM;
+    float V[3], g[3];
+    for (int i = 0; i < 3; ++i) {
+        V[i] = (mA * vA[i] + mM * vM[i]) / mAM;
+        g[i] = vA[i] - vM[i];
+    }
+    const float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const long long Ein = f2fix(0.5f * C->pair[spA * MAXS + spM].mr_f * g2);
+    const long long Eav = Ein + EvA - rx.dEf_fix;
+    if (!(Eav - sB.zpe_fix - sC.zpe_fix > 0) || Eav - sC.zpe_fix > sB.top_fix ||
+        Eav - sB.zpe_fix > sC.top_fix)
+        return false;
+    Stream sa, sb, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) { qB[j] = 0u; qC[j] = 0u; }
+    uint32_t tr = 0;
+    if (sB.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<float>(A, sB, C->amode, fix2d(Eav - sC.zpe_fix), sa, qB, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qB[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    const long long EvB = evib_fix(A.levfix, sB, qB);
+    if (sC.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<float>(A, sC, C->amode, fix2d(Eav - EvB), sb, qC, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qC[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    o.trials += tr;
+    const long long EvC = evib_fix(A.levfix, sC, qC);
+    long long Etr = Eav - EvB - EvC;
+    if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
+    float x = 0.5f;
+    for (int it = 0; it < 4096; ++it) {  // Beta(3/2,3/2) by rejection under 1/2
+        x = st_u32(ss);
+        const float y = st_u32(ss);
+        if (y * y * 0.25f < x * (1.0f - x)) break;
+    }
+    const float Et = fix2f(Etr);
+    const float E1 = x * Et;
+    const float E2 = Et - E1;
+    const float mu1 = C->pair[rx.P0 * MAXS + rx.P1].mr_f;
+    const float mu2 = mBC * (mM / mt);
+    const float g1 = sqrtf(2.0f * E1 / mu1);
+    const float g2n = sqrtf(2.0f * E2 / mu2);
+    float d1[3], d2[3];
+    iso_dir<float>(ss, d1);
+    iso_dir<float>(ss, d2);
+    const float fM = mM / mt, fBC = mBC / mt, fC = mC / mBC, fB = mB / mBC;
+    for (int i = 0; i < 3; ++i) {
+        const float G2 = g2n * d2[i];
+        const float VBC = V[i] + fM * G2;
+        vM[i] = V[i] - fBC * G2;
+        const float G1 = g1 * d1[i];
+        vA[i] = VBC + fC * G1;
+        vC[i] = VBC - fB * G1;
+    }
+    return true;
+}
+
+// FP32 mode, exchange A + B -> C + D: float kinematics, fixed-point energies
+static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
+                            float vA[3], float vB[3], int spA, int spB, long long EvA, long long EvB,
+                            const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t qC[4],
+                            uint32_t qD[4], PairOut& o) {
+    const DevSpecies& sA = C->sp[spA];
+    const DevSpecies& sB = C->sp[spB];
+    const DevSpecies& sC = C->sp[rx.P0];
+    const DevSpecies& sD = C->sp[rx.P1];
+    const float mA = sA.mass_f, mB = sB.mass_f, mC = sC.mass_f, mD = sD.mass_f;
+    const float mAB = mA + mB, mt = mC + mD;
+    float V[3], g[3];
+    for (int i = 0; i < 3; ++i) {
+        V[i] = (mA * vA[i] + mB * vB[i]) / mAB;
+        g[i] = vA[i] - vB[i];
+    }
+    const float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const long long Ein = f2fix(0.5f * C->pair[spA * MAXS + spB].mr_f * g2);
+    const long long Eav = Ein + EvA + EvB - rx.dEf_fix;
+    if (!(Eav - sC.zpe_fix - sD.zpe_fix > 0) || Eav - sD.zpe_fix > sC.top_fix ||
+        Eav - sC.zpe_fix > sD.top_fix)
+        return false;
+    Stream sa, sb, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) { qC[j] = 0u; qD[j] = 0u; }
+    uint32_t tr = 0;
+    if (sC.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<float>(A, sC, C->amode, fix2d(Eav - sD.zpe_fix), sa, qC, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qC[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    const long long EvC = evib_fix(A.levfix, sC, qC);
+    if (sD.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<float>(A, sD, C->amode, fix2d(Eav - EvC), sb, qD, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qD[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    o.trials += tr;
+    const long long EvD = evib_fix(A.levfix, sD, qD);
+    long long Etr = Eav - EvC - EvD;
+    if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
+    const float gn = sqrtf(2.0f * fix2f(Etr) / C->pair[rx.P0 * MAXS + rx.P1].mr_f);
+    float d[3];
+    iso_dir<float>(ss, d);
+    const float fC = mD / mt, fD = mC / mt;
+    for (int i = 0; i < 3; ++i) {
+        const float G = gn * d[i];
+        vA[i] = V[i] + fC * G;
+        vB[i] = V[i] - fD * G;
+    }
+    return true;
 }
 
 // HCAO LB relaxation of molecule 1 then molecule 2 (with the updated E_rel),
@@ -748,10 +971,7 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
     double E = Etr;
     uint32_t tr = 0;
     if constexpr (!F64) {
-        Stream s1, s2;
-        st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
-        st_init(s2, rs.seed, rs.step, L.lcell, L.rk, PU_LB_B);
-        E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
+        // FP32 mode goes through relax_scatter_fix
     } else {
     if (SP.n_modes > 0) {
         Stream s1;
@@ -826,6 +1046,31 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
             Pr.v[i] = V[i] + pc.fp_f * G;
             Qr.v[i] = V[i] - pc.fq_f * G;
         }
+    }
+}
+
+// FP32 mode: relaxation (flattened sampler, fixed-point bookkeeping) and
+// isotropic scattering with the centre-of-mass velocity kept.
+__device__ __forceinline__ void relax_scatter_fix(const StepArgs& A, const Consts* __restrict__ C,
+                                                  const DevRes& rs, const PairLoc& L, RecF& Pr,
+                                                  RecF& Qr, const DevPair& pc, long long Etr,
+                                                  long long EvP, long long EvQ, PairOut& o) {
+    const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+    Stream s1, s2;
+    st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
+    st_init(s2, rs.seed, rs.step, L.lcell, L.rk, PU_LB_B);
+    const long long E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
+    Stream ss;
+    st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
+    const float gn = sqrtf(fix2f(E) * pc.inv2mr_f);
+    float d[3];
+    iso_dir<float>(ss, d);
+    float V[3];
+    for (int i = 0; i < 3; ++i) V[i] = pc.fq_f * Pr.v[i] + pc.fp_f * Qr.v[i];
+    for (int i = 0; i < 3; ++i) {
+        const float G = gn * d[i];
+        Pr.v[i] = V[i] + pc.fp_f * G;
+        Qr.v[i] = V[i] - pc.fq_f * G;
     }
 }
 
@@ -906,13 +1151,18 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
         if (rs.active && N >= 2) {
             // NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically
             const double x = 0.5 * (double)N * (double)(N - 1) * rs.w * cl.sgmax * rs.dt / rs.Vc;
-            const double fl = floor(x);
-            long long ns = (long long)fl;
-            Stream st;
-            st_init(st, rs.seed, rs.step, cl.lcell, 0u, PU_NSEL);
-            if (st_u64(st) < x - fl) ns++;
-            long long rr = (ns + P - 1) / P;
-            if (rr > R) { atomicOr(A.err, (uint32_t)ERR_ROUNDS); ns = 0; rr = 0; }
+            long long ns = 0, rr = 0;
+            if (x >= 0.0 && x < 4.0e9) {
+                const double fl = floor(x);
+                ns = (long long)fl;
+                Stream st;
+                st_init(st, rs.seed, rs.step, cl.lcell, 0u, PU_NSEL);
+                if (st_u64(st) < x - fl) ns++;
+                rr = (ns + P - 1) / P;
+                if (rr > R) { atomicOr(A.err, (uint32_t)ERR_ROUNDS); ns = 0; rr = 0; }
+            } else {  // a non-finite or absurd (sigma g)_max: no pairs, report
+                atomicOr(A.err, (uint32_t)ERR_NONFINITE);
+            }
             nsel = (uint32_t)ns;
             rounds = (uint32_t)rr;
             for (uint32_t r = 0; r < rounds; ++r) {
@@ -983,6 +1233,10 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
             const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
             double g2d;
             pair_energy<R>(C->pair[sP * MAXS + sQ], amode, Pr.v, Qr.v, g2d, sg);
+            if (!(sg <= 1.0e300)) {  // non-finite velocities: report, keep (sigma g)_max
+                atomicOr(A.err, (uint32_t)ERR_NONFINITE);
+                sg = 0.0;
+            }
             Stream sp;
             st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
             if constexpr (std::is_same<R, double>::value) accept = st_u64(sp) < sg / L.sgmax;
@@ -1037,6 +1291,34 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
         load_rec(recs + L.iq, Qr);
         const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
         const DevPair& pc = C->pair[sP * MAXS + sQ];
+        if constexpr (!std::is_same<R, double>::value) {
+            // FP32 mode: fixed-point energies, no FP64 arithmetic
+            const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
+            const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+            const long long EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
+            const long long EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
+            if (C->n_reactions > 0) {
+                Stream sp;
+                st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
+                st_u32(sp);
+                const float u_ster = st_u32(sp);
+                const float u_sel = st_u32(sp);
+                const float u_ch = st_u32(sp);
+                uint32_t chan = 0u;
+                if (reaction_pick_fix(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan) > 0) {
+                    const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
+                    A.qB[slot] = make_uint4((uint32_t)c, e.y, chan, 0u);
+                    continue;
+                }
+            }
+            PairOut o{EV_ACC, 0u};
+            relax_scatter_fix(A, C, rs, L, Pr, Qr, pc, Etr, EvP, EvQ, o);
+            store_rec(recs + L.ip, Pr);
+            store_rec(recs + L.iq, Qr);
+            A.cflag[L.ev_idx] = ev_final(o);
+            if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+            continue;
+        }
         double g2d, sg;
         pair_energy<R>(pc, amode, Pr.v, Qr.v, g2d, sg);
         const double Etr = 0.5 * pc.mr * g2d;
@@ -1088,12 +1370,67 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
         load_rec(recs + L.iq, Qr);
         const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
         const DevPair& pc = C->pair[sP * MAXS + sQ];
+        const int rxi = (int)(e.z & 7u), side = (int)((e.z >> 3) & 1u), mode = (int)(e.z >> 4);
+        if constexpr (!std::is_same<R, double>::value) {
+            const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
+            const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+            const long long EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
+            const long long EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
+            const DevReaction& rx = C->rx[rxi];
+            PairOut o{EV_ACC, 0u};
+            hcao_log_rec lr{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+            float vA[3], vB[3], vN[3];
+            RecF& RA = side ? Qr : Pr;
+            RecF& RB = side ? Pr : Qr;
+            for (int i = 0; i < 3; ++i) { vA[i] = RA.v[i]; vB[i] = RB.v[i]; }
+            const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
+            uint32_t q1[4], q2[4];
+            bool done;
+            if (rx.type == HCAO_DISS) {
+                done = do_diss_fix(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
+                                   vN, o);
+                lr.aux = (uint32_t)mode + (side ? 16u : 0u);
+                if (done) {
+                    for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; RB.v[i] = vB[i]; }
+                    RA.meta = (uint32_t)rx.P0;
+                    for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                    RecF RN;
+                    for (int i = 0; i < 3; ++i) RN.v[i] = vN[i];
+                    RN.meta = (uint32_t)rx.P1;
+                    for (int j = 0; j < 4; ++j) RN.q[j] = q2[j];
+                    store_rec(reinterpret_cast<RecF*>(A.cscratch) + L.ev_idx, RN);
+                    o.ev |= EV_CREATED;
+                }
+            } else {
+                done = do_exch_fix(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, side ? EvP : EvQ, rs,
+                                   L.lcell, L.rk, q1, q2, o);
+                lr.aux = (uint32_t)side;
+                if (done) {
+                    for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; RB.v[i] = vB[i]; }
+                    RA.meta = (uint32_t)rx.P0;
+                    RB.meta = (uint32_t)rx.P1;
+                    for (int j = 0; j < 4; ++j) { RA.q[j] = q1[j]; RB.q[j] = q2[j]; }
+                }
+            }
+            if (done) {
+                o.ev |= (uint32_t)(rxi + 1) << EV_RX_SHIFT;
+                lr.event = 1 + rxi;
+            } else {
+                o.ev |= EV_NOTEXEC;
+                lr.aux = 0u;
+                relax_scatter_fix(A, C, rs, L, Pr, Qr, pc, Etr, EvP, EvQ, o);
+            }
+            store_rec(recs + L.ip, Pr);
+            store_rec(recs + L.iq, Qr);
+            A.cflag[L.ev_idx] = ev_final(o);
+            if (A.log_on) A.log[L.ev_idx] = lr;
+            continue;
+        }
         double g2d, sg;
         pair_energy<R>(pc, amode, Pr.v, Qr.v, g2d, sg);
         const double Etr = 0.5 * pc.mr * g2d;
         const double EvP = evib64(A.lev64, C->sp[sP], Pr.q);
         const double EvQ = evib64(A.lev64, C->sp[sQ], Qr.q);
-        const int rxi = (int)(e.z & 7u), side = (int)((e.z >> 3) & 1u), mode = (int)(e.z >> 4);
         const DevReaction& rx = C->rx[rxi];
         PairOut o{EV_ACC, 0u};
         hcao_log_rec lr{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
@@ -1259,8 +1596,9 @@ __global__ void k_sample_diag(StepArgs A, int sp, double Ec, uint64_t seed, int6
             o.trials = tr;
         } else {
             // the relative energy plus the ground state's energy is Ec
-            const double Ev0 = evib64(A.lev64, C->sp[sp], q);
-            relax_flat(A, C, sp, q, Ev0, st, -1, nullptr, 0.0, st, Ec - Ev0, o);
+            const long long Ev0 = evib_fix(A.levfix, C->sp[sp], q);
+            uint32_t qdummy[4] = {0u, 0u, 0u, 0u};
+            relax_flat(A, C, sp, q, Ev0, st, -1, qdummy, 0, st, __double2ll_rn(Ec * 0x1p100) - Ev0, o);
             if ((o.ev >> EV_OVER_SHIFT) & 3u) rc = S_OVER;
             if ((o.ev >> EV_DEGEN_SHIFT) & 3u) rc = S_DEGEN;
         }

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libhcao.so")
 FP64, FP32 = 0, 1
 DISS, EXCH = 1, 2
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
-          -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND"}
+          -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND",
+          -10: "ENONFINITE"}
 
 EXPORTS = [
     "hcao_create", "hcao_destroy", "hcao_last_error", "hcao_default_config", "hcao_set_species",
