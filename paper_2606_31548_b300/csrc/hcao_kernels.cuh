@@ -624,22 +624,27 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
     }
 }
 
-// FP32 LB relaxation of up to two molecules as one flattened loop: every
-// iteration is one level step of the K5 draw, whatever molecule, mode or trial
-// a lane is in, so the lanes of a warp stay converged.  Draws, tables and the
-// target are those of sample_lb<float>; the relative energy is kept in int64
-// fixed point (exact sums).  sp < 0 or a species without modes skips that
-// molecule.  Returns the relative energy left for scattering.
+// FP32 LB relaxation of up to two molecules, scheduled for SIMT efficiency.
+// Each lane runs the K5 draw as a state machine whose common step is one
+// level of one mode.  The rarer transitions -- starting a molecule, starting a
+// mode (with its Philox draw), finishing a molecule -- are batched: lanes that
+// need one wait while the others keep stepping, and once at least half of the
+// live lanes wait they all make their transitions together.  Draws, tables
+// and the target are those of sample_lb<float>; the relative energy is kept
+// in int64 fixed point.  sp < 0 or a species without modes skips a molecule.
+// Returns the relative energy left for scattering.
 static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C,
                                                        int spA, uint32_t (&qA)[4], long long EvA,
                                                        Stream stA, int spB, uint32_t (&qB)[4],
                                                        long long EvB, Stream stB, long long Erel,
                                                        PairOut& o) {
+    enum { P_NONE = 0, P_START_MOL, P_START_MODE, P_DONE_MOL };
     const float* __restrict__ Lv = A.lev32;
     const float* __restrict__ Hb = A.H32;
     const int amode = C->amode;
-    int mol = 0;
-    bool starting = true;
+    const unsigned act = __activemask();
+    int mol = 0, pend = P_START_MOL;
+    bool alive = true, failed = false;
     const DevSpecies* S = nullptr;
     long long Ecd = 0, Evold = 0;
     float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
@@ -651,95 +656,110 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
     uint32_t nq[4] = {0u, 0u, 0u, 0u};
     uint32_t trials = 0, trials_all = 0;
     Stream st = stA;
-    for (int guard = 0; mol < 2 && guard < (1 << 26); ++guard) {
-        if (starting) {
-            const int sp = mol ? spB : spA;
-            if (sp < 0 || C->sp[sp].n_modes == 0) { mol++; continue; }
-            S = &C->sp[sp];
-            Evold = mol ? EvB : EvA;
-            st = mol ? stB : stA;
-            Ecd = Erel + Evold;
-            n = S->n_modes;
-            MT = S->MT;
-            inv = S->inv_cq_f;
-            Hm = Hb + S->tab_off;
-            o.ev += 1u << EV_SAMP_SHIFT;
-            Ec = fix2f(Ecd);
-            m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
-            starting = false;
-            if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; Erel = Ecd - Evold; mol++; starting = true; continue; }
-            if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) {
-                o.ev += 1u << EV_DEGEN_SHIFT; Erel = Ecd - Evold; mol++; starting = true; continue;
-            }
-            trials = 0;
-            nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-            if (__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f) {  // only the ground state fits
-                k = n;
-            } else {
-                k = 0;
-                i = -1;
-            }
-            E = Ec;
-        }
-        if (k < n && i < 0) {  // start mode k of the current trial
-            if (k == 0) trials++;
-            const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
-            t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
-            cum = 0.f;
-            i = 0;
-            Lk = Lv + S->lev_off[k];
-            nl = S->n_lev[k];
-            last = k == n - 1;
-            if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
-        }
-        if (k < n) {  // one level step
-            const float e = i < nl ? __ldg(Lk + i) : 0.f;
-            if (i < nl && e < E) {
-                const float x = __fsub_rn(E, e);
-                float w;
-                if (last) {
-                    w = lb_pow<float>(amode, x);
-                } else {
-                    const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
-                    w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
-                }
-                cum = __fadd_rn(cum, w);
-                if (t < cum) {
-                    set_q(nq, k, (uint32_t)i);
-                    E = __fsub_rn(E, e);
-                    k++;
-                    i = -1;
-                } else {
-                    i++;
-                }
-            } else if (trials >= A.reject_cap) {  // give up: keep the old state
-                atomicOr(A.err, (uint32_t)ERR_REJECT);
+    for (int guard = 0; guard < (1 << 24); ++guard) {
+        // ---- transitions of every waiting lane
+        for (int tg = 0; alive && pend != P_NONE && tg < 64; ++tg) {
+            if (pend == P_DONE_MOL) {
                 trials_all += trials;
-                Erel = Ecd - Evold;
+                if (failed) {
+                    Erel = Ecd - Evold;
+                } else {
+                    const long long En = Ecd - evib_fix(A.levfix, *S, nq);
+                    if (En >= 0) {
+                        if (mol == 0) { qA[0] = nq[0]; qA[1] = nq[1]; qA[2] = nq[2]; qA[3] = nq[3]; }
+                        else { qB[0] = nq[0]; qB[1] = nq[1]; qB[2] = nq[2]; qB[3] = nq[3]; }
+                        Erel = En;
+                    } else {
+                        o.ev += 1u << EV_DEGEN_SHIFT;
+                        Erel = Ecd - Evold;
+                    }
+                }
                 mol++;
-                starting = true;
-                continue;
-            } else {  // the draw ran past the levels: restart the trial
-                k = 0;
-                i = -1;
-                E = Ec;
+                pend = P_START_MOL;
+                if (mol >= 2) alive = false;
+            } else if (pend == P_START_MOL) {
+                const int sp = mol ? spB : spA;
+                if (sp < 0 || C->sp[sp].n_modes == 0) {
+                    mol++;
+                    if (mol >= 2) alive = false;
+                    continue;
+                }
+                S = &C->sp[sp];
+                Evold = mol ? EvB : EvA;
+                st = mol ? stB : stA;
+                Ecd = Erel + Evold;
+                n = S->n_modes;
+                MT = S->MT;
+                inv = S->inv_cq_f;
+                Hm = Hb + S->tab_off;
+                o.ev += 1u << EV_SAMP_SHIFT;
+                Ec = fix2f(Ecd);
+                m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
+                trials = 0;
+                failed = false;
                 nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+                pend = P_DONE_MOL;
+                if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
+                else if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
+                else if (!(__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f)) {  // else: ground state only
+                    k = 0;
+                    pend = P_START_MODE;
+                }
+            } else {  // P_START_MODE
+                if (k == 0) {  // a new trial
+                    if (trials >= A.reject_cap) {
+                        atomicOr(A.err, (uint32_t)ERR_REJECT);
+                        failed = true;
+                        pend = P_DONE_MOL;
+                        continue;
+                    }
+                    trials++;
+                    E = Ec;
+                    nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+                }
+                const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+                t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
+                cum = 0.f;
+                i = 0;
+                Lk = Lv + S->lev_off[k];
+                nl = S->n_lev[k];
+                last = k == n - 1;
+                if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
+                pend = P_NONE;
             }
-            if (k < n) continue;
         }
-        // molecule done: the new relative energy, exact in fixed point
-        trials_all += trials;
-        const long long En = Ecd - evib_fix(A.levfix, *S, nq);
-        if (En >= 0) {
-            if (mol == 0) { qA[0] = nq[0]; qA[1] = nq[1]; qA[2] = nq[2]; qA[3] = nq[3]; }
-            else { qB[0] = nq[0]; qB[1] = nq[1]; qB[2] = nq[2]; qB[3] = nq[3]; }
-            Erel = En;
-        } else {
-            o.ev += 1u << EV_DEGEN_SHIFT;
-            Erel = Ecd - Evold;
+        if (!__any_sync(act, alive)) break;
+        // ---- level steps until at least half of the live lanes wait
+        for (int sg = 0; sg < (1 << 20); ++sg) {
+            if (alive && pend == P_NONE) {
+                const float e = i < nl ? __ldg(Lk + i) : 0.f;
+                if (i < nl && e < E) {
+                    const float x = __fsub_rn(E, e);
+                    float w;
+                    if (last) {
+                        w = lb_pow<float>(amode, x);
+                    } else {
+                        const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
+                        w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
+                    }
+                    cum = __fadd_rn(cum, w);
+                    if (t < cum) {
+                        set_q(nq, k, (uint32_t)i);
+                        E = __fsub_rn(E, e);
+                        k++;
+                        pend = k < n ? P_START_MODE : P_DONE_MOL;
+                    } else {
+                        i++;
+                    }
+                } else {  // the draw ran past the levels: restart the trial
+                    k = 0;
+                    pend = P_START_MODE;
+                }
+            }
+            const unsigned live = __ballot_sync(act, alive);
+            const unsigned wait = __ballot_sync(act, alive && pend != P_NONE);
+            if (2 * __popc(wait) >= __popc(live)) break;
         }
-        mol++;
-        starting = true;
     }
     o.trials += trials_all;
     return Erel;
@@ -824,8 +844,8 @@ static __device__ int reaction_pick_fix(const StepArgs& A, const Consts* __restr
 // energies (the same product split as do_diss, reading A13).
 static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
                             float vA[3], float vM[3], int spA, int spM, long long EvA, const DevRes& rs,
-                            uint32_t lcell, uint32_t rk, uint32_t qB[4], uint32_t qC[4], float vC[3],
-                            PairOut& o) {
+                            uint32_t lcell, uint32_t rk, uint32_t (&qB)[4], uint32_t (&qC)[4],
+                            float vC[3], PairOut& o) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sM = C->sp[spM];
     const DevSpecies& sB = C->sp[rx.P0];
@@ -850,25 +870,10 @@ static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__
     st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) { qB[j] = 0u; qC[j] = 0u; }
-    uint32_t tr = 0;
-    if (sB.n_modes > 0) {
-        o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<float>(A, sB, C->amode, fix2d(Eav - sC.zpe_fix), sa, qB, tr) != S_OK) {
-            for (int j = 0; j < 4; ++j) qB[j] = 0u;
-            atomicOr(A.err, (uint32_t)ERR_REJECT);
-        }
-    }
-    const long long EvB = evib_fix(A.levfix, sB, qB);
-    if (sC.n_modes > 0) {
-        o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<float>(A, sC, C->amode, fix2d(Eav - EvB), sb, qC, tr) != S_OK) {
-            for (int j = 0; j < 4; ++j) qC[j] = 0u;
-            atomicOr(A.err, (uint32_t)ERR_REJECT);
-        }
-    }
-    o.trials += tr;
-    const long long EvC = evib_fix(A.levfix, sC, qC);
-    long long Etr = Eav - EvB - EvC;
+    // products start in their ground states: B is drawn at Eav - ZPE_C, then C
+    // at Eav - E_vib,B; what is left is translational
+    long long Etr = relax_flat(A, C, rx.P0, qB, sB.zpe_fix, sa, rx.P1, qC, sC.zpe_fix, sb,
+                               Eav - sB.zpe_fix - sC.zpe_fix, o);
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
     float x = 0.5f;
     for (int it = 0; it < 4096; ++it) {  // Beta(3/2,3/2) by rejection under 1/2
@@ -901,8 +906,8 @@ static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__
 // FP32 mode, exchange A + B -> C + D: float kinematics, fixed-point energies
 static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
                             float vA[3], float vB[3], int spA, int spB, long long EvA, long long EvB,
-                            const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t qC[4],
-                            uint32_t qD[4], PairOut& o) {
+                            const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t (&qC)[4],
+                            uint32_t (&qD)[4], PairOut& o) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sB = C->sp[spB];
     const DevSpecies& sC = C->sp[rx.P0];
@@ -925,25 +930,8 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) { qC[j] = 0u; qD[j] = 0u; }
-    uint32_t tr = 0;
-    if (sC.n_modes > 0) {
-        o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<float>(A, sC, C->amode, fix2d(Eav - sD.zpe_fix), sa, qC, tr) != S_OK) {
-            for (int j = 0; j < 4; ++j) qC[j] = 0u;
-            atomicOr(A.err, (uint32_t)ERR_REJECT);
-        }
-    }
-    const long long EvC = evib_fix(A.levfix, sC, qC);
-    if (sD.n_modes > 0) {
-        o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<float>(A, sD, C->amode, fix2d(Eav - EvC), sb, qD, tr) != S_OK) {
-            for (int j = 0; j < 4; ++j) qD[j] = 0u;
-            atomicOr(A.err, (uint32_t)ERR_REJECT);
-        }
-    }
-    o.trials += tr;
-    const long long EvD = evib_fix(A.levfix, sD, qD);
-    long long Etr = Eav - EvC - EvD;
+    long long Etr = relax_flat(A, C, rx.P0, qC, sC.zpe_fix, sa, rx.P1, qD, sD.zpe_fix, sb,
+                               Eav - sC.zpe_fix - sD.zpe_fix, o);
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
     const float gn = sqrtf(2.0f * fix2f(Etr) / C->pair[rx.P0 * MAXS + rx.P1].mr_f);
     float d[3];
