@@ -238,14 +238,17 @@ def main():
     # particle-step = 2 S, S = 12 B velocity + 9 B quantum numbers + 1 B species
     # + 4 B cell (FP32) = 26 B; FP64 adds 12 B
     S = 26.0 if prec == hcao.FP32 else 38.0
-    collide_s = kms[1] / 1e3
+    names = hcao.Context.PROFILE_KERNELS
+    per_step = {k: kms[i] / args.steps for i, k in enumerate(names)}
+    dom = max(("select", "relax", "react"), key=lambda k: per_step[k])
+    collide_s = (kms[1] + kms[2] + kms[3]) / 1e3
     peak, peak_kind = _peaks()
     achieved = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_kind": peak_kind, "kernel": "k_collide",
-            "kernel_ms_per_step": {"setup": kms[0] / args.steps, "collide": kms[1] / args.steps,
-                                   "finish": kms[2] / args.steps}}
+            "peak_kind": peak_kind, "kernel": "collide phase (k_select+k_relax+k_react)",
+            "dominant_kernel": "k_" + dom, "kernel_ms_per_step": per_step,
+            "kernel_launches": {k: int(kn[i]) for i, k in enumerate(names)}}
 
     # e2e through the C ABI with host buffers (pinned): load + step + moments
     e2e = None

@@ -213,9 +213,9 @@ hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out);
 
 /* Kernel timing: with profiling on, hcao_step records CUDA events on the
    context's stream around each kernel.  hcao_read_profile accumulates and
-   returns, for k = 0 (setup), 1 (collide), 2 (finish), the summed device time
-   in ms (host_ms[k]) and the number of launches (host_launches[k]); *n_out = 3.
-   hcao_set_profiling resets the sums. */
+   returns, for k = 0 (setup), 1 (select), 2 (relax), 3 (react), 4 (finish),
+   the summed device time in ms (host_ms[k]) and the number of launches
+   (host_launches[k]); *n_out = 5.  hcao_set_profiling resets the sums. */
 hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
                               int* n_out);

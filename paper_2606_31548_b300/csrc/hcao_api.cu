@@ -89,10 +89,11 @@ struct hcao_ctx {
     int64_t scratch_words = 0;
     // kernel timing: events recorded on the stream around each kernel class
     bool prof_on = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
-    size_t prof_used[3] = {0, 0, 0};
-    double prof_ms[3] = {0, 0, 0};
-    uint64_t prof_n[3] = {0, 0, 0};
+    static constexpr int NPROF = 5;  // setup, select, relax, react, finish
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[NPROF];
+    size_t prof_used[NPROF] = {};
+    double prof_ms[NPROF] = {};
+    uint64_t prof_n[NPROF] = {};
 };
 
 namespace {
@@ -562,7 +563,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < hcao_ctx::NPROF; ++k)
         for (auto& e : ctx->prof_ev[k]) {
             cudaEventDestroy(e.first);
             cudaEventDestroy(e.second);
@@ -1017,29 +1018,37 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             else launch_step<float>(a, grid, block, ctx->stream, &ctx->launches);
             continue;
         }
-        for (int k = 0; k < 3; ++k) {
-            const int reps = k == 1 ? a.max_rounds : 1;
-            for (int r = 0; r < reps; ++r) {
-                auto& pool = ctx->prof_ev[k];
-                if (ctx->prof_used[k] == pool.size()) {
-                    cudaEvent_t e0, e1;
-                    CU(cudaEventCreate(&e0));
-                    CU(cudaEventCreate(&e1));
-                    pool.emplace_back(e0, e1);
-                }
-                auto& ev = pool[ctx->prof_used[k]++];
-                CU(cudaEventRecord(ev.first, ctx->stream));
-                if (k == 0) launch_setup(a, ctx->stream);
-                else if (k == 1) {
-                    if (f64) launch_collide<double>(a, r, grid, block, ctx->stream);
-                    else launch_collide<float>(a, r, grid, block, ctx->stream);
-                } else {
-                    if (f64) launch_finish<double>(a, ctx->stream);
-                    else launch_finish<float>(a, ctx->stream);
-                }
-                CU(cudaEventRecord(ev.second, ctx->stream));
-                ctx->launches++;
+        // setup, then per round select / relax / react, then finish
+        int seq[2 + 3 * MAX_ROUNDS][2];
+        int ns = 0;
+        seq[ns][0] = 0; seq[ns++][1] = 0;
+        for (int r = 0; r < a.max_rounds; ++r)
+            for (int ph = 0; ph < 3; ++ph) {
+                if (ph == 2 && !a.has_reactions) continue;
+                seq[ns][0] = 1 + ph; seq[ns++][1] = r;
             }
+        seq[ns][0] = 4; seq[ns++][1] = 0;
+        for (int q = 0; q < ns; ++q) {
+            const int k = seq[q][0], r = seq[q][1];
+            auto& pool = ctx->prof_ev[k];
+            if (ctx->prof_used[k] == pool.size()) {
+                cudaEvent_t e0, e1;
+                CU(cudaEventCreate(&e0));
+                CU(cudaEventCreate(&e1));
+                pool.emplace_back(e0, e1);
+            }
+            auto& ev = pool[ctx->prof_used[k]++];
+            CU(cudaEventRecord(ev.first, ctx->stream));
+            if (k == 0) launch_setup(a, ctx->stream);
+            else if (k == 4) {
+                if (f64) launch_finish<double>(a, ctx->stream);
+                else launch_finish<float>(a, ctx->stream);
+            } else {
+                if (f64) launch_phase<double>(a, r, k - 1, grid, ctx->stream);
+                else launch_phase<float>(a, r, k - 1, grid, ctx->stream);
+            }
+            CU(cudaEventRecord(ev.second, ctx->stream));
+            ctx->launches++;
         }
     }
     CU(cudaGetLastError());
@@ -1049,7 +1058,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
 hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable) {
     if (!ctx) return HCAO_EINVAL;
     ctx->prof_on = enable != 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < hcao_ctx::NPROF; ++k) {
         ctx->prof_used[k] = 0;
         ctx->prof_ms[k] = 0.0;
         ctx->prof_n[k] = 0;
@@ -1060,7 +1069,7 @@ hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable) {
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int max, int* n_out) {
     if (!ctx || !ms || !launches || max < 1) return HCAO_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < hcao_ctx::NPROF; ++k) {
         for (size_t i = 0; i < ctx->prof_used[k]; ++i) {
             float t = 0.0f;
             CU(cudaEventElapsedTime(&t, ctx->prof_ev[k][i].first, ctx->prof_ev[k][i].second));
@@ -1069,7 +1078,7 @@ hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int
         }
         ctx->prof_used[k] = 0;
     }
-    const int n = std::min(max, 3);
+    const int n = std::min(max, hcao_ctx::NPROF);
     for (int k = 0; k < n; ++k) {
         ms[k] = ctx->prof_ms[k];
         launches[k] = ctx->prof_n[k];

@@ -143,6 +143,8 @@ template <class R> void launch_step(const StepArgs& a, int grid_collide, int blo
                                     cudaStream_t s, uint64_t* launches);
 void launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu)
 template <class R> void launch_collide(const StepArgs& a, int r, int grid, int block, cudaStream_t s);
+// phase k of round r: 0 select, 1 relax, 2 react (for per-kernel timing)
+template <class R> void launch_phase(const StepArgs& a, int r, int phase, int grid, cudaStream_t s);
 template <class R> void launch_finish(const StepArgs& a, cudaStream_t s);
 template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm,
                                             const uint32_t* offsets, const uint64_t* cell_slot0,

@@ -1551,6 +1551,12 @@ void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStre
     if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
 }
 template <class R>
+void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream_t s) {
+    if (phase == 0) k_select<R><<<grid, 256, 0, s>>>(a, r);
+    else if (phase == 1) k_relax<R><<<grid, 128, 0, s>>>(a, r);
+    else if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
+}
+template <class R>
 void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
     const int g = (a.n_cells + 7) / 8 < 1184 ? (a.n_cells + 7) / 8 : 1184;
     k_finish<R><<<g < 1 ? 1 : g, 256, 0, s>>>(a, reinterpret_cast<unsigned long long*>(a.counters), NCNT);
@@ -1757,6 +1763,10 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
     }                                                                                            \
     template <>                                                                                  \
     void launch_finish<R>(const StepArgs& a, cudaStream_t s) { launch_finish_impl<R>(a, s); }    \
+    template <>                                                                                  \
+    void launch_phase<R>(const StepArgs& a, int r, int phase, int grid, cudaStream_t s) {        \
+        launch_phase_impl<R>(a, r, phase, grid, s);                                              \
+    }                                                                                            \
     template <>                                                                                  \
     void launch_scatter_load<R>(void* rec_base, const uint32_t* perm, const uint32_t* offsets,   \
                                 const uint64_t* slot0, int n_cells, const double* v,             \

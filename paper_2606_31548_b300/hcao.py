@@ -308,12 +308,14 @@ class Context:
     def set_profiling(self, on=True) -> None:
         self._chk(self.L.hcao_set_profiling(self.h, 1 if on else 0))
 
+    PROFILE_KERNELS = ("setup", "select", "relax", "react", "finish")
+
     def read_profile(self):
-        """(ms, launches) per kernel class: setup, collide, finish."""
-        ms = np.zeros(3)
-        n = np.zeros(3, np.uint64)
+        """(ms, launches) per kernel: setup, select, relax, react, finish."""
+        ms = np.zeros(5)
+        n = np.zeros(5, np.uint64)
         got = C.c_int()
-        self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 3, C.byref(got)))
+        self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 5, C.byref(got)))
         return ms, n
 
     def kernel_launches(self) -> int:
