@@ -523,7 +523,7 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_qsize, 2 * MAX_ROUNDS) != cudaSuccess) {
+        dalloc(ctx, &ctx->d_qsize, 3 * MAX_ROUNDS) != cudaSuccess) {
         delete ctx;
         return HCAO_ENOMEM;
     }

@@ -124,7 +124,8 @@ struct StepArgs {
     void* cscratch;                 // per-pair record of a particle created by a reaction
     uint2* qA;                      // accepted pairs of the current round (cell, pair)
     uint4* qB;                      // reacting pairs (cell, pair, channel)
-    uint32_t* qsize;                // [2 * MAX_ROUNDS] queue lengths per round
+    uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax and react queue
+                                    // lengths, then the relax queue's fetch heads
     int has_reactions;
     uint64_t pair_cap;              // capacity of cflag / log
     hcao_log_rec* log;

@@ -1177,7 +1177,7 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1)] = 0;
         A.abase[0] = 0;
-        for (int i = 0; i < 2 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
+        for (int i = 0; i < 3 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
     }
     __syncthreads();
     for (int r = 0; r < R; ++r) block_scan_inplace(A.pbase + r * (nc + 1), nc);
@@ -1334,6 +1334,227 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
         store_rec(recs + L.iq, Qr);
         A.cflag[L.ev_idx] = ev_final(o);
         if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{rs.step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+    }
+}
+
+// FP32 phase 2 as a persistent state machine.  Each lane takes an accepted
+// pair from the queue, runs its reaction test (reacting pairs go to the
+// reaction queue), relaxes both molecules with the K5 draw one level step per
+// iteration, scatters, stores, and takes the next pair.  Lanes that need a
+// transition (fetching or finishing a pair, starting a molecule or a mode)
+// wait while the others step; once at least half of the live lanes wait,
+// all of them make their transitions together.  Same draws, tables and
+// target as relax_flat.
+template <class R>
+__global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
+    static_assert(std::is_same<R, float>::value, "FP32 mode only");
+    enum { P_NONE = 0, P_FETCH, P_PAIR, P_START_MOL, P_START_MODE, P_DONE_MOL, P_SCATTER };
+    const Consts* __restrict__ C = A.C;
+    const float* __restrict__ Lv = A.lev32;
+    const float* __restrict__ Hb = A.H32;
+    const int amode = C->amode;
+    const uint32_t total = A.qsize[2 * r];
+    uint32_t* head = A.qsize + 2 * MAX_ROUNDS + r;
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    // pair state
+    bool alive = true;
+    int pend = P_FETCH;
+    uint32_t qi = 0;
+    int cidx = 0;
+    PairLoc L;
+    uint64_t seed = 0;
+    uint32_t step = 0;
+    RecF Pr, Qr;
+    int sP = 0, sQ = 0;
+    long long EvP = 0, EvQ = 0, Erel = 0;
+    PairOut o{0u, 0u};
+    // molecule state
+    int mol = 0;
+    bool failed = false;
+    const DevSpecies* S = nullptr;
+    long long Ecd = 0, Evold = 0;
+    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
+    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0;
+    const float* Hm = nullptr;
+    const float* Lk = nullptr;
+    const float* Hn = nullptr;
+    bool last = false;
+    uint32_t nq[4] = {0u, 0u, 0u, 0u};
+    uint32_t trials = 0;
+    Stream st;
+    st_init(st, 0, 0, 0, 0, 0);
+    for (int guard = 0; guard < (1 << 26); ++guard) {
+        // ---- fetch: one atomic per warp for every lane that needs a pair
+        const bool need = alive && pend == P_FETCH;
+        const unsigned fm = __ballot_sync(act, need);
+        if (fm) {
+            const int leader = __ffs(fm) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(fm));
+            base = __shfl_sync(act, base, leader);
+            if (need) {
+                qi = base + (uint32_t)__popc(fm & ((1u << lane) - 1u));
+                if (qi < total) pend = P_PAIR;
+                else alive = false;
+            }
+        }
+        // ---- transitions of every waiting lane (not fetching)
+        for (int tg = 0; alive && pend != P_NONE && pend != P_FETCH && tg < 64; ++tg) {
+            if (pend == P_PAIR) {
+                const uint2 e = A.qA[qi];
+                cidx = (int)e.x;
+                L = locate(A, cidx, r, e.y);
+                const DevRes& rs = A.res[A.cells[cidx].res];
+                seed = rs.seed;
+                step = rs.step;
+                const RecF* recs = reinterpret_cast<const RecF*>(L.recs);
+                load_rec(recs + L.ip, Pr);
+                load_rec(recs + L.iq, Qr);
+                sP = (int)(Pr.meta & 0xFFu);
+                sQ = (int)(Qr.meta & 0xFFu);
+                const DevPair& pc = C->pair[sP * MAXS + sQ];
+                const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
+                const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+                EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
+                EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
+                if (C->n_reactions > 0) {
+                    Stream sp;
+                    st_init(sp, seed, step, L.lcell, L.rk, PU_PAIR);
+                    st_u32(sp);
+                    const float u_ster = st_u32(sp);
+                    const float u_sel = st_u32(sp);
+                    const float u_ch = st_u32(sp);
+                    uint32_t chan = 0u;
+                    if (reaction_pick_fix(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel, u_ch,
+                                          chan) > 0) {
+                        const uint32_t slot = atomicAdd(A.qsize + 2 * r + 1, 1u);
+                        A.qB[slot] = make_uint4((uint32_t)cidx, e.y, chan, 0u);
+                        pend = P_FETCH;
+                        continue;
+                    }
+                }
+                o.ev = EV_ACC;
+                o.trials = 0u;
+                Erel = Etr;
+                mol = 0;
+                pend = P_START_MOL;
+            } else if (pend == P_START_MOL) {
+                if (mol >= 2) { pend = P_SCATTER; continue; }
+                const int sp = mol ? sQ : sP;
+                if (C->sp[sp].n_modes == 0) { mol++; continue; }
+                S = &C->sp[sp];
+                Evold = mol ? EvQ : EvP;
+                st_init(st, seed, step, L.lcell, L.rk, mol ? PU_LB_B : PU_LB_A);
+                Ecd = Erel + Evold;
+                n = S->n_modes;
+                MT = S->MT;
+                inv = S->inv_cq_f;
+                Hm = Hb + S->tab_off;
+                o.ev += 1u << EV_SAMP_SHIFT;
+                Ec = fix2f(Ecd);
+                m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
+                trials = 0;
+                failed = false;
+                nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+                pend = P_DONE_MOL;
+                if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
+                else if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
+                else if (!(__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f)) {  // else: ground state only
+                    k = 0;
+                    pend = P_START_MODE;
+                }
+            } else if (pend == P_START_MODE) {
+                if (k == 0) {  // a new trial
+                    if (trials >= A.reject_cap) {
+                        atomicOr(A.err, (uint32_t)ERR_REJECT);
+                        failed = true;
+                        pend = P_DONE_MOL;
+                        continue;
+                    }
+                    trials++;
+                    E = Ec;
+                    nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+                }
+                const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+                t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
+                cum = 0.f;
+                i = 0;
+                Lk = Lv + S->lev_off[k];
+                nl = S->n_lev[k];
+                last = k == n - 1;
+                if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
+                pend = P_NONE;
+            } else if (pend == P_DONE_MOL) {
+                o.trials += trials;
+                if (failed) {
+                    Erel = Ecd - Evold;
+                } else {
+                    const long long En = Ecd - evib_fix(A.levfix, *S, nq);
+                    if (En >= 0) {
+                        if (mol == 0) { Pr.q[0] = nq[0]; Pr.q[1] = nq[1]; Pr.q[2] = nq[2]; Pr.q[3] = nq[3]; }
+                        else { Qr.q[0] = nq[0]; Qr.q[1] = nq[1]; Qr.q[2] = nq[2]; Qr.q[3] = nq[3]; }
+                        Erel = En;
+                    } else {
+                        o.ev += 1u << EV_DEGEN_SHIFT;
+                        Erel = Ecd - Evold;
+                    }
+                }
+                mol++;
+                pend = P_START_MOL;
+            } else {  // P_SCATTER: isotropic, centre-of-mass velocity kept
+                const DevPair& pc = C->pair[sP * MAXS + sQ];
+                Stream ss;
+                st_init(ss, seed, step, L.lcell, L.rk, PU_SCAT);
+                const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
+                float d[3];
+                iso_dir<float>(ss, d);
+                for (int c3 = 0; c3 < 3; ++c3) {
+                    const float V = pc.fq_f * Pr.v[c3] + pc.fp_f * Qr.v[c3];
+                    const float G = gn * d[c3];
+                    Pr.v[c3] = V + pc.fp_f * G;
+                    Qr.v[c3] = V - pc.fq_f * G;
+                }
+                RecF* recs = reinterpret_cast<RecF*>(L.recs);
+                store_rec(recs + L.ip, Pr);
+                store_rec(recs + L.iq, Qr);
+                A.cflag[L.ev_idx] = ev_final(o);
+                if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+                pend = P_FETCH;
+            }
+        }
+        if (!__any_sync(act, alive)) break;
+        // ---- level steps until at least half of the live lanes wait
+        for (int sg = 0; sg < (1 << 20); ++sg) {
+            if (alive && pend == P_NONE) {
+                const float e = i < nl ? __ldg(Lk + i) : 0.f;
+                if (i < nl && e < E) {
+                    const float x = __fsub_rn(E, e);
+                    float w;
+                    if (last) {
+                        w = lb_pow<float>(amode, x);
+                    } else {
+                        const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
+                        w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
+                    }
+                    cum = __fadd_rn(cum, w);
+                    if (t < cum) {
+                        set_q(nq, k, (uint32_t)i);
+                        E = __fsub_rn(E, e);
+                        k++;
+                        pend = k < n ? P_START_MODE : P_DONE_MOL;
+                    } else {
+                        i++;
+                    }
+                } else {  // the draw ran past the levels: restart the trial
+                    k = 0;
+                    pend = P_START_MODE;
+                }
+            }
+            const unsigned live = __ballot_sync(act, alive);
+            const unsigned wait = __ballot_sync(act, alive && pend != P_NONE);
+            if (2 * __popc(wait) >= __popc(live)) break;
+        }
     }
 }
 
@@ -1544,17 +1765,19 @@ __global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* 
 }
 
 template <class R>
-void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {
-    (void)block;
-    k_select<R><<<grid, 256, 0, s>>>(a, r);
-    k_relax<R><<<grid, 128, 0, s>>>(a, r);
-    if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
-}
-template <class R>
 void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream_t s) {
     if (phase == 0) k_select<R><<<grid, 256, 0, s>>>(a, r);
-    else if (phase == 1) k_relax<R><<<grid, 128, 0, s>>>(a, r);
-    else if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
+    else if (phase == 1) {
+        if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<grid, 128, 0, s>>>(a, r);
+        else k_relax<R><<<grid, 128, 0, s>>>(a, r);
+    } else if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
+}
+template <class R>
+void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {
+    (void)block;
+    launch_phase_impl<R>(a, r, 0, grid, s);
+    launch_phase_impl<R>(a, r, 1, grid, s);
+    launch_phase_impl<R>(a, r, 2, grid, s);
 }
 template <class R>
 void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
