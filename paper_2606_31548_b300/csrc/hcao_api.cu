@@ -78,7 +78,7 @@ struct hcao_ctx {
     uint32_t* d_totals = nullptr;
     uint32_t* d_cflag = nullptr;
     void* d_cscratch = nullptr;
-    uint2* d_qA = nullptr;
+    uint4* d_qA = nullptr;
     uint4* d_qB = nullptr;
     uint32_t* d_qsize = nullptr;
     hcao_log_rec* d_log = nullptr;

@@ -122,7 +122,7 @@ struct StepArgs {
     uint32_t* totals;               // [MAX_ROUNDS + 1]
     uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
     void* cscratch;                 // per-pair record of a particle created by a reaction
-    uint2* qA;                      // accepted pairs of the current round (cell, pair)
+    uint4* qA;                      // accepted pairs of the current round (cell, pair, ip, iq)
     uint4* qB;                      // reacting pairs (cell, pair, channel)
     uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax and react queue
                                     // lengths, then the relax queue's fetch heads

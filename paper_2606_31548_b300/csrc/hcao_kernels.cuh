@@ -520,6 +520,22 @@ __device__ __forceinline__ PairLoc locate(const StepArgs& A, int c, int r, uint3
     return L;
 }
 
+// the same as locate() with the Feistel members already known
+__device__ __forceinline__ PairLoc locate_known(const StepArgs& A, int c, int r, uint32_t k, uint32_t ip,
+                                                uint32_t iq) {
+    const DevCell& cell = A.cells[c];
+    PairLoc L;
+    L.N = cell.n;
+    L.lcell = cell.lcell;
+    L.rk = ((uint32_t)r << 24) | k;
+    L.ev_idx = A.abase[c] + (uint32_t)r * (L.N >> 1) + k;
+    L.ip = ip;
+    L.iq = iq;
+    L.recs = cell.rec;
+    L.sgmax = cell.sgmax;
+    return L;
+}
+
 // channel id: reaction (3 bits) | side << 3 | broken stretch << 4
 __device__ __forceinline__ uint32_t chan_pack(int rx, int side, int mode) {
     return (uint32_t)rx | ((uint32_t)side << 3) | ((uint32_t)mode << 4);
@@ -1206,13 +1222,15 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
         const uint32_t g = g0 + threadIdx.x;
         const bool valid = g < total;
         int c = 0;
-        bool accept = false;
+        bool accept = false, react = false;
         double sg = 0.0;
-        uint32_t k = 0;
+        uint32_t k = 0, ip = 0, iq = 0, chan = 0;
         if (valid) {
             c = cell_of(pb, A.n_cells, g);
             k = g - __ldg(pb + c);
             const PairLoc L = locate(A, c, r, k);
+            ip = L.ip;
+            iq = L.iq;
             const DevRes& rs = A.res[A.cells[c].res];
             const Rec* recs = reinterpret_cast<const Rec*>(L.recs);
             Rec Pr, Qr;
@@ -1227,15 +1245,32 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
             }
             Stream sp;
             st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
-            if constexpr (std::is_same<R, double>::value) accept = st_u64(sp) < sg / L.sgmax;
-            else accept = st_u32(sp) < (float)sg / (float)L.sgmax;
+            if constexpr (std::is_same<R, double>::value) {
+                accept = st_u64(sp) < sg / L.sgmax;
+            } else {
+                accept = st_u32(sp) < (float)sg / (float)L.sgmax;
+                if (accept && C->n_reactions > 0) {
+                    // FP32 mode: the QK reaction test here, in fixed point
+                    const DevPair& pc = C->pair[sP * MAXS + sQ];
+                    const long long Etr = f2fix(0.5f * pc.mr_f * (float)g2d);
+                    const long long EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
+                    const long long EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
+                    const float u_ster = st_u32(sp);
+                    const float u_sel = st_u32(sp);
+                    const float u_ch = st_u32(sp);
+                    react = reaction_pick_fix(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel,
+                                              u_ch, chan) > 0;
+                }
+            }
             if (!accept) {
                 A.cflag[L.ev_idx] = 0u;
                 if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{rs.step, L.lcell, L.rk, L.ip, L.iq, -1, 0u};
             }
         }
-        const uint32_t slot = queue_slot(qsize, accept);
-        if (accept) A.qA[slot] = make_uint2((uint32_t)c, k);
+        const uint32_t slot = queue_slot(qsize, accept && !react);
+        if (accept && !react) A.qA[slot] = make_uint4((uint32_t)c, k, ip, iq);
+        const uint32_t rslot = queue_slot(qsize + 1, react);
+        if (react) A.qB[rslot] = make_uint4((uint32_t)c, k, chan, 0u);
         // per-cell max of sigma_T g: lanes of one cell combine before the atomic
         const unsigned act = __activemask();
         const int lane = threadIdx.x & 31;
@@ -1269,9 +1304,9 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
     const Consts* __restrict__ C = A.C;
     const int amode = C->amode;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const uint2 e = A.qA[g];
+        const uint4 e = A.qA[g];
         const int c = (int)e.x;
-        const PairLoc L = locate(A, c, r, e.y);
+        const PairLoc L = locate_known(A, c, r, e.y, e.z, e.w);
         const DevRes& rs = A.res[A.cells[c].res];
         Rec* recs = reinterpret_cast<Rec*>(L.recs);
         Rec Pr, Qr;
@@ -1348,7 +1383,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
 template <class R>
 __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
-    enum { P_NONE = 0, P_FETCH, P_PAIR, P_START_MOL, P_START_MODE, P_DONE_MOL, P_SCATTER };
+    enum { P_NONE = 0, P_START_MODE, P_FETCH, P_PAIR, P_START_MOL, P_DONE_MOL, P_SCATTER };
     const Consts* __restrict__ C = A.C;
     const float* __restrict__ Lv = A.lev32;
     const float* __restrict__ Hb = A.H32;
@@ -1357,11 +1392,9 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     uint32_t* head = A.qsize + 2 * MAX_ROUNDS + r;
     const unsigned act = __activemask();
     const int lane = threadIdx.x & 31;
-    // pair state
     bool alive = true;
     int pend = P_FETCH;
     uint32_t qi = 0;
-    int cidx = 0;
     PairLoc L;
     uint64_t seed = 0;
     uint32_t step = 0;
@@ -1369,7 +1402,6 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     int sP = 0, sQ = 0;
     long long EvP = 0, EvQ = 0, Erel = 0;
     PairOut o{0u, 0u};
-    // molecule state
     int mol = 0;
     bool failed = false;
     const DevSpecies* S = nullptr;
@@ -1384,27 +1416,14 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     uint32_t trials = 0;
     Stream st;
     st_init(st, 0, 0, 0, 0, 0);
-    for (int guard = 0; guard < (1 << 26); ++guard) {
-        // ---- fetch: one atomic per warp for every lane that needs a pair
-        const bool need = alive && pend == P_FETCH;
-        const unsigned fm = __ballot_sync(act, need);
-        if (fm) {
-            const int leader = __ffs(fm) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(fm));
-            base = __shfl_sync(act, base, leader);
-            if (need) {
-                qi = base + (uint32_t)__popc(fm & ((1u << lane) - 1u));
-                if (qi < total) pend = P_PAIR;
-                else alive = false;
-            }
-        }
-        // ---- transitions of every waiting lane (not fetching)
-        for (int tg = 0; alive && pend != P_NONE && pend != P_FETCH && tg < 64; ++tg) {
+
+    // heavy transitions of one lane until it steps, needs a pair, or is done
+    auto heavy = [&]() {
+        for (int tg = 0; alive && pend >= P_PAIR && tg < 64; ++tg) {
             if (pend == P_PAIR) {
-                const uint2 e = A.qA[qi];
-                cidx = (int)e.x;
-                L = locate(A, cidx, r, e.y);
+                const uint4 e = A.qA[qi];
+                const int cidx = (int)e.x;
+                L = locate_known(A, cidx, r, e.y, e.z, e.w);
                 const DevRes& rs = A.res[A.cells[cidx].res];
                 seed = rs.seed;
                 step = rs.step;
@@ -1415,28 +1434,11 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 sQ = (int)(Qr.meta & 0xFFu);
                 const DevPair& pc = C->pair[sP * MAXS + sQ];
                 const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-                const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+                Erel = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
                 EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
                 EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
-                if (C->n_reactions > 0) {
-                    Stream sp;
-                    st_init(sp, seed, step, L.lcell, L.rk, PU_PAIR);
-                    st_u32(sp);
-                    const float u_ster = st_u32(sp);
-                    const float u_sel = st_u32(sp);
-                    const float u_ch = st_u32(sp);
-                    uint32_t chan = 0u;
-                    if (reaction_pick_fix(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel, u_ch,
-                                          chan) > 0) {
-                        const uint32_t slot = atomicAdd(A.qsize + 2 * r + 1, 1u);
-                        A.qB[slot] = make_uint4((uint32_t)cidx, e.y, chan, 0u);
-                        pend = P_FETCH;
-                        continue;
-                    }
-                }
                 o.ev = EV_ACC;
                 o.trials = 0u;
-                Erel = Etr;
                 mol = 0;
                 pend = P_START_MOL;
             } else if (pend == P_START_MOL) {
@@ -1464,27 +1466,6 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                     k = 0;
                     pend = P_START_MODE;
                 }
-            } else if (pend == P_START_MODE) {
-                if (k == 0) {  // a new trial
-                    if (trials >= A.reject_cap) {
-                        atomicOr(A.err, (uint32_t)ERR_REJECT);
-                        failed = true;
-                        pend = P_DONE_MOL;
-                        continue;
-                    }
-                    trials++;
-                    E = Ec;
-                    nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-                }
-                const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
-                t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
-                cum = 0.f;
-                i = 0;
-                Lk = Lv + S->lev_off[k];
-                nl = S->n_lev[k];
-                last = k == n - 1;
-                if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
-                pend = P_NONE;
             } else if (pend == P_DONE_MOL) {
                 o.trials += trials;
                 if (failed) {
@@ -1523,9 +1504,53 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 pend = P_FETCH;
             }
         }
-        if (!__any_sync(act, alive)) break;
-        // ---- level steps until at least half of the live lanes wait
-        for (int sg = 0; sg < (1 << 20); ++sg) {
+    };
+    // one warp-aggregated atomic for every lane that needs a pair
+    auto fetch = [&]() {
+        const bool need = alive && pend == P_FETCH;
+        const unsigned fm = __ballot_sync(act, need);
+        if (fm) {
+            const int leader = __ffs(fm) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(fm));
+            base = __shfl_sync(act, base, leader);
+            if (need) {
+                qi = base + (uint32_t)__popc(fm & ((1u << lane) - 1u));
+                if (qi < total) pend = P_PAIR;
+                else alive = false;
+            }
+        }
+    };
+    auto start_mode = [&]() {
+        if (k == 0) {  // a new trial
+            if (trials >= A.reject_cap) {
+                atomicOr(A.err, (uint32_t)ERR_REJECT);
+                failed = true;
+                pend = P_DONE_MOL;
+                return;
+            }
+            trials++;
+            E = Ec;
+            nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+        }
+        const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+        t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
+        cum = 0.f;
+        i = 0;
+        Lk = Lv + S->lev_off[k];
+        nl = S->n_lev[k];
+        last = k == n - 1;
+        if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
+        pend = P_NONE;
+    };
+
+    for (int guard = 0; guard < (1 << 28); ++guard) {
+        const unsigned live = __ballot_sync(act, alive);
+        if (!live) break;
+        const unsigned stepping = __ballot_sync(act, alive && pend == P_NONE);
+        const int nlive = __popc(live), nstep = __popc(stepping);
+        if (2 * nstep >= nlive) {
+            // ---- one level step of the K5 draw
             if (alive && pend == P_NONE) {
                 const float e = i < nl ? __ldg(Lk + i) : 0.f;
                 if (i < nl && e < E) {
@@ -1551,10 +1576,21 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                     pend = P_START_MODE;
                 }
             }
-            const unsigned live = __ballot_sync(act, alive);
-            const unsigned wait = __ballot_sync(act, alive && pend != P_NONE);
-            if (2 * __popc(wait) >= __popc(live)) break;
+            continue;
         }
+        // ---- too few lanes stepping: cheap mode starts now, heavy transitions
+        // once at least a quarter of the live lanes need one (or nothing else can run)
+        const unsigned cheap = __ballot_sync(act, alive && pend == P_START_MODE);
+        const unsigned heavyset = live & ~stepping & ~cheap;
+        const bool do_heavy = 4 * __popc(heavyset) >= nlive || (stepping | cheap) == 0u;
+        if (do_heavy) {
+            if (alive && pend >= P_PAIR) heavy();
+            fetch();
+            if (alive && pend >= P_PAIR) heavy();
+        }
+        if (alive && pend == P_START_MODE) start_mode();
+        if (do_heavy && alive && pend >= P_PAIR) heavy();
+        if (alive && pend == P_START_MODE) start_mode();
     }
 }
 
