@@ -224,17 +224,21 @@ void build_tables(int amode, int n, const std::vector<R>* lev, const R* base, R 
     }
 }
 
-// FP32 tables on the buckets idx(E) = ceil(sqrt((E - base) * inv)) (IEEE
-// float, as on the device).  Entry m is evaluated at the bucket's upper edge
-// G_m, the largest float whose index is <= m (bisection over the ordered bit
-// patterns of positive floats), so every budget in the bucket is bounded.
-int idx_f32(float base, float inv, int MT, float E) {
+// FP32 tables on geometric buckets read off the float bit pattern of
+// x = E - base: idx = (bits(x) >> shift) - j0, at least 1 (0 if E <= base, MT
+// past the last bucket), as on the device.  Entry m is evaluated at the
+// bucket's upper edge G_m, the largest float whose index is <= m (bisection
+// over the ordered bit patterns of positive floats), so every budget in the
+// bucket is bounded.
+int idx_f32(float base, int shift, int j0, int MT, float E) {
     if (!(E > base)) return 0;
-    const float c = std::ceil(std::sqrt((E - base) * inv));
-    if (!(c <= (float)(MT - 1))) return MT;
-    return (int)c;
+    const float x = E - base;
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    const int j = (int)(b >> shift) - j0;
+    return j < 1 ? 1 : (j > MT - 1 ? MT : j);
 }
-float bucket_top_f32(float base, float inv, int MT, int m) {
+float bucket_top_f32(float base, int shift, int j0, int MT, int m) {
     if (m <= 0) return base;
     uint32_t lo, hi;
     float fb = base, fmax = 3.4028234663852886e38f;
@@ -244,18 +248,18 @@ float bucket_top_f32(float base, float inv, int MT, int m) {
         const uint32_t mid = lo + (hi - lo) / 2;
         float f;
         std::memcpy(&f, &mid, 4);
-        if (idx_f32(base, inv, MT, f) <= m) lo = mid; else hi = mid;
+        if (idx_f32(base, shift, j0, MT, f) <= m) lo = mid; else hi = mid;
     }
     float r;
     std::memcpy(&r, &lo, 4);
     return r;
 }
-void build_tables_f32(int amode, int n, const std::vector<float>* lev, const float* base, float inv, int MT,
-                      std::vector<float>& out) {
+void build_tables_f32(int amode, int n, const std::vector<float>* lev, const float* base, int shift, int j0,
+                      int MT, std::vector<float>& out) {
     out.assign((size_t)n * MT, 0.0f);
     for (int k = n - 1; k >= 0; --k) {
         for (int m = 0; m < MT; ++m) {
-            const float g = bucket_top_f32(base[k], inv, MT, m);
+            const float g = bucket_top_f32(base[k], shift, j0, MT, m);
             float sum = 0.0f;
             for (size_t i = 0; i < lev[k].size(); ++i) {
                 if (!(lev[k][i] < g)) break;
@@ -264,7 +268,7 @@ void build_tables_f32(int amode, int n, const std::vector<float>* lev, const flo
                 if (k == n - 1) {
                     w = lbpow_host<float>(amode, x);
                 } else {
-                    int mm = idx_f32(base[k + 1], inv, MT, x);
+                    int mm = idx_f32(base[k + 1], shift, j0, MT, x);
                     if (mm > MT - 1) mm = MT - 1;
                     w = mm == 0 ? 0.0f : out[(size_t)(k + 1) * MT + mm];
                 }
@@ -681,11 +685,17 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
                     L[j].resize(s.lev[j].size());
                     for (size_t l = 0; l < s.lev[j].size(); ++l) L[j][l] = (float)s.lev[j][l];
                 }
+                // 7 mantissa bits per octave (buckets ~0.8% wide); x = span maps to M
+                D.gshift = 23 - 7;
+                const float span = (float)ctx->cfg.table_span_J;
+                uint32_t sb;
+                std::memcpy(&sb, &span, 4);
+                D.gj0 = (int)(sb >> D.gshift) - M;
                 std::vector<float> t;
-                build_tables_f32(amode, nm, L, D.base_f, D.inv_cq_f, MT, t);
+                build_tables_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t);
                 D.tab_off = (int)H32.size();
                 H32.insert(H32.end(), t.begin(), t.end());
-                D.top = (double)bucket_top_f32(D.base_f[0], D.inv_cq_f, MT, M);
+                D.top = (double)bucket_top_f32(D.base_f[0], D.gshift, D.gj0, MT, M);
             }
         }
     }

@@ -55,6 +55,7 @@ struct DevSpecies {
     double eps_min;                  // smallest single-quantum excitation
     float base_f[MAXM + 1];
     float cq_f, inv_cq_f, eps_min_f, pad_f;
+    int gshift, gj0;                 // FP32 buckets: (bits(E - base) >> gshift) - gj0
     int n_modes, n_stretch, MT, M;
     int lev_off[MAXM];               // offset of mode j's levels in the level arrays
     int n_lev[MAXM];
@@ -95,6 +96,8 @@ struct DevCell {
     double sgmax;                     // (sigma_T g)_max
     unsigned long long seen;          // max sigma_T g of this step (bits of a double >= 0)
     uint32_t nsel, ncreated;
+    float sgmax_f;                    // FP32 copy of sgmax for the step
+    uint32_t pad_c;
     uint32_t fkey[MAX_ROUNDS][4];     // Feistel keys per round of this step
 };
 

@@ -234,13 +234,24 @@ __device__ __forceinline__ int grid_idx(R base, R cq, R inv, int MT, R E) {
 // base, MT if above the last bucket).  The host builds the FP32 tables at each
 // bucket's upper edge (the largest float with that index), so the same exact
 // bound holds without comparing against grid points.
-template <>
-__device__ __forceinline__ int grid_idx<float>(float base, float cq, float inv, int MT, float E) {
-    (void)cq;
+// FP32 buckets: a geometric grid read off the float bit pattern of x = E - base:
+// idx = (bits(x) >> shift) - j0, at least 1 (0 if E <= base, MT past the last
+// bucket).  Monotone in E and exactly reproducible with integer operations; the
+// host builds the FP32 tables at each bucket's upper edge.
+__device__ __forceinline__ int grid_idx_f32(float base, int shift, int j0, int MT, float E) {
     if (!(E > base)) return 0;
-    const float c = ceilf(__fsqrt_rn(__fmul_rn(__fsub_rn(E, base), inv)));
-    if (!(c <= (float)(MT - 1))) return MT;
-    return (int)c;
+    const int j = (int)(__float_as_uint(__fsub_rn(E, base)) >> shift) - j0;
+    return j < 1 ? 1 : (j > MT - 1 ? MT : j);
+}
+
+// grid index of table k of species S in precision R (FP64: quadratic grid
+// with exact correction; FP32: bit-pattern buckets)
+template <class R> __device__ __forceinline__ int gidx(const DevSpecies& S, int k, R E);
+template <> __device__ __forceinline__ int gidx<double>(const DevSpecies& S, int k, double E) {
+    return grid_idx<double>(S.base[k], S.cq, S.inv_cq, S.MT, E);
+}
+template <> __device__ __forceinline__ int gidx<float>(const DevSpecies& S, int k, float E) {
+    return grid_idx_f32(S.base_f[k], S.gshift, S.gj0, S.MT, E);
 }
 
 __device__ __forceinline__ double evib64(const double* lev, const DevSpecies& S, const uint32_t q[4]) {
@@ -278,7 +289,7 @@ __device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, doub
     const int MT = S.MT;
     const R Ec = (R)Ec_d;
     const R b0 = sp_base<R>(S, 0);
-    const int m0 = grid_idx<R>(b0, cq, inv, MT, Ec);
+    const int m0 = gidx<R>(S, 0, Ec);
     if (m0 > S.M) return S_OVER;
     if (m0 == 0) return S_DEGEN;
     const R h0 = __ldg(H + m0);
@@ -294,7 +305,7 @@ __device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, doub
         R E = Ec;
         bool ok = true;
         for (int k = 0; k < n; ++k) {
-            int m = (k == 0) ? m0 : grid_idx<R>(sp_base<R>(S, k), cq, inv, MT, E);
+            int m = (k == 0) ? m0 : gidx<R>(S, k, E);
             if (m > MT - 1) {  // cannot happen for budgets below the table top
                 m = MT - 1;
                 atomicOr(A.err, (uint32_t)ERR_LEVEL);
@@ -316,7 +327,7 @@ __device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, doub
                 if (last) {
                     w = lb_pow<R>(amode, x);
                 } else {
-                    int mm = grid_idx<R>(bn, cq, inv, MT, x);
+                    int mm = gidx<R>(S, k + 1, x);
                     if (mm > MT - 1) mm = MT - 1;
                     w = mm == 0 ? (R)0 : __ldg(Hn + mm);
                 }
@@ -663,8 +674,8 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
     bool alive = true, failed = false;
     const DevSpecies* S = nullptr;
     long long Ecd = 0, Evold = 0;
-    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
-    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0;
+    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f;
+    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0, gsh = 0, gj0 = 0;
     const float* Hm = nullptr;
     const float* Lk = nullptr;
     const float* Hn = nullptr;
@@ -706,11 +717,12 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
                 Ecd = Erel + Evold;
                 n = S->n_modes;
                 MT = S->MT;
-                inv = S->inv_cq_f;
+                gsh = S->gshift;
+                gj0 = S->gj0;
                 Hm = Hb + S->tab_off;
                 o.ev += 1u << EV_SAMP_SHIFT;
                 Ec = fix2f(Ecd);
-                m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
+                m0 = grid_idx_f32(S->base_f[0], S->gshift, S->gj0, MT, Ec);
                 trials = 0;
                 failed = false;
                 nq[0] = nq[1] = nq[2] = nq[3] = 0u;
@@ -733,7 +745,7 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
                     E = Ec;
                     nq[0] = nq[1] = nq[2] = nq[3] = 0u;
                 }
-                const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+                const int m = k == 0 ? m0 : min(grid_idx_f32(S->base_f[k], S->gshift, S->gj0, MT, E), MT - 1);
                 t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
                 cum = 0.f;
                 i = 0;
@@ -755,7 +767,7 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
                     if (last) {
                         w = lb_pow<float>(amode, x);
                     } else {
-                        const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
+                        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
                         w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
                     }
                     cum = __fadd_rn(cum, w);
@@ -1180,6 +1192,7 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
         cl.nsel = nsel;
         cl.ncreated = 0;
         cl.seen = 0ull;
+        cl.sgmax_f = (float)cl.sgmax;
         for (int r = 0; r < R; ++r) {
             uint32_t cnt = 0;
             if ((uint32_t)r < rounds) {
@@ -1218,6 +1231,83 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
     const Consts* __restrict__ C = A.C;
     const int amode = C->amode;
     uint32_t* qsize = A.qsize + 2 * r;
+    if constexpr (std::is_same<R, float>::value) {
+        // FP32 mode: no FP64 arithmetic; the second half of a record (the
+        // quantum numbers) is read only for accepted pairs when reactions exist
+        for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
+            const uint32_t g = g0 + threadIdx.x;
+            const bool valid = g < total;
+            int c = 0;
+            bool accept = false, react = false;
+            float sgf = 0.f;
+            uint32_t k = 0, ip = 0, iq = 0, chan = 0;
+            if (valid) {
+                c = cell_of(pb, A.n_cells, g);
+                k = g - __ldg(pb + c);
+                const DevCell& cell = A.cells[c];
+                const uint32_t N = cell.n;
+                const uint32_t rk = ((uint32_t)r << 24) | k;
+                const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
+                ip = feistel(2u * k, N, key);
+                iq = feistel(2u * k + 1u, N, key);
+                const uint4* recs = reinterpret_cast<const uint4*>(cell.rec);
+                const uint4 a = recs[2 * ip], b = recs[2 * iq];
+                const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
+                const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
+                const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
+                const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
+                const float g2 = gx * gx + gy * gy + gz * gz;
+                const DevPair& pc = C->pair[sP * MAXS + sQ];
+                const float gr = sqrtf(g2);
+                sgf = pc.C_f * (amode == 0 ? sqrtf(gr) : (amode == 1 ? gr : 1.0f));
+                if (!(sgf <= 3.0e38f)) {
+                    atomicOr(A.err, (uint32_t)ERR_NONFINITE);
+                    sgf = 0.f;
+                }
+                const DevRes& rs = A.res[cell.res];
+                Stream sp;
+                st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
+                accept = st_u32(sp) < sgf / cell.sgmax_f;
+                const uint32_t ev_idx = A.abase[c] + (uint32_t)r * (N >> 1) + k;
+                if (accept && C->n_reactions > 0) {
+                    const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
+                    const uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w};
+                    const uint32_t qQ[4] = {qb.x, qb.y, qb.z, qb.w};
+                    const long long Etr = f2fix(0.5f * pc.mr_f * g2);
+                    const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
+                    const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
+                    const float u_ster = st_u32(sp);
+                    const float u_sel = st_u32(sp);
+                    const float u_ch = st_u32(sp);
+                    react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch,
+                                              chan) > 0;
+                }
+                if (!accept) {
+                    A.cflag[ev_idx] = 0u;
+                    if (A.log_on) A.log[ev_idx] = hcao_log_rec{rs.step, cell.lcell, rk, ip, iq, -1, 0u};
+                }
+            }
+            const uint32_t slot = queue_slot(qsize, accept && !react);
+            if (accept && !react) A.qA[slot] = make_uint4((uint32_t)c, k, ip, iq);
+            const uint32_t rslot = queue_slot(qsize + 1, react);
+            if (react) A.qB[rslot] = make_uint4((uint32_t)c, k, chan, 0u);
+            // per-cell max of sigma_T g: lanes of one cell combine before the atomic
+            const unsigned act = __activemask();
+            const int lane = threadIdx.x & 31;
+            const int key = valid ? c : -1;
+            unsigned left = __ballot_sync(act, valid);
+            while (left) {
+                const int leader = __ffs(left) - 1;
+                const int cl = __shfl_sync(act, key, leader);
+                const unsigned grp = __ballot_sync(act, key == cl);
+                float mx = key == cl ? sgf : 0.f;
+                for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(act, mx, o));
+                if (lane == leader)
+                    atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong((double)mx));
+                left &= ~grp;
+            }
+        }
+    } else {
     for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
         const uint32_t g = g0 + threadIdx.x;
         const bool valid = g < total;
@@ -1291,6 +1381,7 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                 atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong(mx));
             left &= ~grp;
         }
+    }
     }
 }
 
@@ -1406,8 +1497,8 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     bool failed = false;
     const DevSpecies* S = nullptr;
     long long Ecd = 0, Evold = 0;
-    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, inv = 0.f;
-    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0;
+    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f;
+    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0, gsh = 0, gj0 = 0;
     const float* Hm = nullptr;
     const float* Lk = nullptr;
     const float* Hn = nullptr;
@@ -1451,11 +1542,12 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 Ecd = Erel + Evold;
                 n = S->n_modes;
                 MT = S->MT;
-                inv = S->inv_cq_f;
+                gsh = S->gshift;
+                gj0 = S->gj0;
                 Hm = Hb + S->tab_off;
                 o.ev += 1u << EV_SAMP_SHIFT;
                 Ec = fix2f(Ecd);
-                m0 = grid_idx<float>(S->base_f[0], 0.f, inv, MT, Ec);
+                m0 = grid_idx_f32(S->base_f[0], S->gshift, S->gj0, MT, Ec);
                 trials = 0;
                 failed = false;
                 nq[0] = nq[1] = nq[2] = nq[3] = 0u;
@@ -1533,7 +1625,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
             E = Ec;
             nq[0] = nq[1] = nq[2] = nq[3] = 0u;
         }
-        const int m = k == 0 ? m0 : min(grid_idx<float>(S->base_f[k], 0.f, inv, MT, E), MT - 1);
+        const int m = k == 0 ? m0 : min(grid_idx_f32(S->base_f[k], S->gshift, S->gj0, MT, E), MT - 1);
         t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
         cum = 0.f;
         i = 0;
@@ -1559,7 +1651,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                     if (last) {
                         w = lb_pow<float>(amode, x);
                     } else {
-                        const int mm = grid_idx<float>(bn, 0.f, inv, MT, x);
+                        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
                         w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
                     }
                     cum = __fadd_rn(cum, w);
