@@ -1486,75 +1486,102 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     bool alive = true;
     int pend = P_FETCH;
     uint32_t qi = 0;
-    PairLoc L;
+    // pair: cell records, members, event slot and Philox counter words
+    uint4* recs = nullptr;
+    uint32_t ip = 0, iq = 0, ev_idx = 0, lcell = 0, rk = 0, step = 0;
     uint64_t seed = 0;
-    uint32_t step = 0;
-    RecF Pr, Qr;
     int sP = 0, sQ = 0;
     long long EvP = 0, EvQ = 0, Erel = 0;
     PairOut o{0u, 0u};
-    int mol = 0;
+    // molecule
+    int mol = 0, sp = 0;
     bool failed = false;
-    const DevSpecies* S = nullptr;
     long long Ecd = 0, Evold = 0;
-    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f;
+    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, b0 = 0.f;
     int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0, gsh = 0, gj0 = 0;
-    const float* Hm = nullptr;
-    const float* Lk = nullptr;
-    const float* Hn = nullptr;
+    int hm = 0, lk = 0, hn = 0;  // offsets of table 0, levels of mode k, table k + 1
     bool last = false;
     uint32_t nq[4] = {0u, 0u, 0u, 0u};
     uint32_t trials = 0;
-    Stream st;
-    st_init(st, 0, 0, 0, 0, 0);
+    // the molecule's Philox stream: block index, and the unused second word
+    // of the last block (uniform j uses word 0 of block j/2 if j is even, word 2
+    // if odd; an FP32 uniform takes the top 24 bits)
+    uint32_t sblk = 0, spur = 0, sword = 0;
+    bool shave = false;
 
-    // heavy transitions of one lane until it steps, needs a pair, or is done
+    auto uniform = [&]() -> float {
+        uint32_t w;
+        if (shave) {
+            w = sword;
+            shave = false;
+        } else {
+            uint32_t x0 = step, x1 = lcell, x2 = rk, x3 = (spur << 24) | (sblk & 0xFFFFFFu);
+            philox10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
+            sblk++;
+            w = x0;
+            sword = x2;
+            shave = true;
+        }
+        return (float)(w >> 8) * 0x1p-24f;
+    };
+
     auto heavy = [&]() {
         for (int tg = 0; alive && pend >= P_PAIR && tg < 64; ++tg) {
             if (pend == P_PAIR) {
                 const uint4 e = A.qA[qi];
                 const int cidx = (int)e.x;
-                L = locate_known(A, cidx, r, e.y, e.z, e.w);
-                const DevRes& rs = A.res[A.cells[cidx].res];
+                const DevCell& cell = A.cells[cidx];
+                const DevRes& rs = A.res[cell.res];
                 seed = rs.seed;
                 step = rs.step;
-                const RecF* recs = reinterpret_cast<const RecF*>(L.recs);
-                load_rec(recs + L.ip, Pr);
-                load_rec(recs + L.iq, Qr);
-                sP = (int)(Pr.meta & 0xFFu);
-                sQ = (int)(Qr.meta & 0xFFu);
-                const DevPair& pc = C->pair[sP * MAXS + sQ];
-                const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-                Erel = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
-                EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
-                EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
+                lcell = cell.lcell;
+                rk = ((uint32_t)r << 24) | e.y;
+                ev_idx = A.abase[cidx] + (uint32_t)r * (cell.n >> 1) + e.y;
+                ip = e.z;
+                iq = e.w;
+                recs = reinterpret_cast<uint4*>(cell.rec);
+                const uint4 a = recs[2 * ip], b = recs[2 * iq];
+                const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
+                sP = (int)(a.w & 0xFFu);
+                sQ = (int)(b.w & 0xFFu);
+                const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
+                const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
+                const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
+                Erel = f2fix(0.5f * C->pair[sP * MAXS + sQ].mr_f * (gx * gx + gy * gy + gz * gz));
+                const uint32_t q0[4] = {qa.x, qa.y, qa.z, qa.w};
+                const uint32_t q1[4] = {qb.x, qb.y, qb.z, qb.w};
+                EvP = evib_fix(A.levfix, C->sp[sP], q0);
+                EvQ = evib_fix(A.levfix, C->sp[sQ], q1);
                 o.ev = EV_ACC;
                 o.trials = 0u;
                 mol = 0;
                 pend = P_START_MOL;
             } else if (pend == P_START_MOL) {
                 if (mol >= 2) { pend = P_SCATTER; continue; }
-                const int sp = mol ? sQ : sP;
-                if (C->sp[sp].n_modes == 0) { mol++; continue; }
-                S = &C->sp[sp];
+                sp = mol ? sQ : sP;
+                const DevSpecies& S = C->sp[sp];
+                if (S.n_modes == 0) { mol++; continue; }
                 Evold = mol ? EvQ : EvP;
-                st_init(st, seed, step, L.lcell, L.rk, mol ? PU_LB_B : PU_LB_A);
+                spur = mol ? PU_LB_B : PU_LB_A;
+                sblk = 0;
+                shave = false;
                 Ecd = Erel + Evold;
-                n = S->n_modes;
-                MT = S->MT;
-                gsh = S->gshift;
-                gj0 = S->gj0;
-                Hm = Hb + S->tab_off;
+                n = S.n_modes;
+                MT = S.MT;
+                gsh = S.gshift;
+                gj0 = S.gj0;
+                hm = S.tab_off;
+                b0 = S.base_f[0];
                 o.ev += 1u << EV_SAMP_SHIFT;
                 Ec = fix2f(Ecd);
-                m0 = grid_idx_f32(S->base_f[0], S->gshift, S->gj0, MT, Ec);
+                m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
                 trials = 0;
                 failed = false;
                 nq[0] = nq[1] = nq[2] = nq[3] = 0u;
                 pend = P_DONE_MOL;
-                if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
-                else if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
-                else if (!(__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f)) {  // else: ground state only
+                if (m0 > S.M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
+                else if (m0 == 0 || !(__ldg(Hb + hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
+                else if (!(__fsub_rn(Ec, b0) < S.eps_min_f)) {  // else: ground state only
                     k = 0;
                     pend = P_START_MODE;
                 }
@@ -1563,10 +1590,9 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 if (failed) {
                     Erel = Ecd - Evold;
                 } else {
-                    const long long En = Ecd - evib_fix(A.levfix, *S, nq);
+                    const long long En = Ecd - evib_fix(A.levfix, C->sp[sp], nq);
                     if (En >= 0) {
-                        if (mol == 0) { Pr.q[0] = nq[0]; Pr.q[1] = nq[1]; Pr.q[2] = nq[2]; Pr.q[3] = nq[3]; }
-                        else { Qr.q[0] = nq[0]; Qr.q[1] = nq[1]; Qr.q[2] = nq[2]; Qr.q[3] = nq[3]; }
+                        recs[2 * (mol ? iq : ip) + 1] = make_uint4(nq[0], nq[1], nq[2], nq[3]);
                         Erel = En;
                     } else {
                         o.ev += 1u << EV_DEGEN_SHIFT;
@@ -1578,21 +1604,24 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
             } else {  // P_SCATTER: isotropic, centre-of-mass velocity kept
                 const DevPair& pc = C->pair[sP * MAXS + sQ];
                 Stream ss;
-                st_init(ss, seed, step, L.lcell, L.rk, PU_SCAT);
+                st_init(ss, seed, step, lcell, rk, PU_SCAT);
                 const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
                 float d[3];
                 iso_dir<float>(ss, d);
+                const uint4 a = recs[2 * ip], b = recs[2 * iq];
+                const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+                const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
+                float na[3], nb[3];
                 for (int c3 = 0; c3 < 3; ++c3) {
-                    const float V = pc.fq_f * Pr.v[c3] + pc.fp_f * Qr.v[c3];
+                    const float V = pc.fq_f * va[c3] + pc.fp_f * vb[c3];
                     const float G = gn * d[c3];
-                    Pr.v[c3] = V + pc.fp_f * G;
-                    Qr.v[c3] = V - pc.fq_f * G;
+                    na[c3] = V + pc.fp_f * G;
+                    nb[c3] = V - pc.fq_f * G;
                 }
-                RecF* recs = reinterpret_cast<RecF*>(L.recs);
-                store_rec(recs + L.ip, Pr);
-                store_rec(recs + L.iq, Qr);
-                A.cflag[L.ev_idx] = ev_final(o);
-                if (A.log_on) A.log[L.ev_idx] = hcao_log_rec{step, L.lcell, L.rk, L.ip, L.iq, 0, 0u};
+                recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
+                recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
+                A.cflag[ev_idx] = ev_final(o);
+                if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
                 pend = P_FETCH;
             }
         }
@@ -1614,6 +1643,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         }
     };
     auto start_mode = [&]() {
+        const DevSpecies& S = C->sp[sp];
         if (k == 0) {  // a new trial
             if (trials >= A.reject_cap) {
                 atomicOr(A.err, (uint32_t)ERR_REJECT);
@@ -1625,15 +1655,24 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
             E = Ec;
             nq[0] = nq[1] = nq[2] = nq[3] = 0u;
         }
-        const int m = k == 0 ? m0 : min(grid_idx_f32(S->base_f[k], S->gshift, S->gj0, MT, E), MT - 1);
-        t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
+        const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
+        t = __fmul_rn(uniform(), __ldg(Hb + hm + k * MT + m));
         cum = 0.f;
         i = 0;
-        Lk = Lv + S->lev_off[k];
-        nl = S->n_lev[k];
+        lk = S.lev_off[k];
+        nl = S.n_lev[k];
         last = k == n - 1;
-        if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
+        if (!last) { hn = hm + (k + 1) * MT; bn = S.base_f[k + 1]; }
         pend = P_NONE;
+    };
+    // weight of one level (0 past the mode's list or at/above the budget)
+    auto weight = [&](int ii, float& e) -> float {
+        e = ii < nl ? __ldg(Lv + lk + ii) : 3.0e38f;
+        if (!(e < E)) return -1.0f;
+        const float x = __fsub_rn(E, e);
+        if (last) return lb_pow<float>(amode, x);
+        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
+        return mm == 0 ? 0.f : __ldg(Hb + hn + min(mm, MT - 1));
     };
 
     for (int guard = 0; guard < (1 << 28); ++guard) {
@@ -1642,28 +1681,32 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         const unsigned stepping = __ballot_sync(act, alive && pend == P_NONE);
         const int nlive = __popc(live), nstep = __popc(stepping);
         if (2 * nstep >= nlive) {
-            // ---- one level step of the K5 draw
+            // ---- two level steps of the K5 draw (the second load chain
+            // overlaps the first; the selection is that of a sequential scan)
             if (alive && pend == P_NONE) {
-                const float e = i < nl ? __ldg(Lk + i) : 0.f;
-                if (i < nl && e < E) {
-                    const float x = __fsub_rn(E, e);
-                    float w;
-                    if (last) {
-                        w = lb_pow<float>(amode, x);
-                    } else {
-                        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
-                        w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
+                float e0, e1;
+                const float w0 = weight(i, e0);
+                const float w1 = weight(i + 1, e1);
+                int sel = -1;
+                bool exhausted = false;
+                if (w0 < 0.f) {
+                    exhausted = true;
+                } else {
+                    cum = __fadd_rn(cum, w0);
+                    if (t < cum) sel = i;
+                    else if (w1 < 0.f) exhausted = true;
+                    else {
+                        cum = __fadd_rn(cum, w1);
+                        if (t < cum) sel = i + 1;
+                        else i += 2;
                     }
-                    cum = __fadd_rn(cum, w);
-                    if (t < cum) {
-                        set_q(nq, k, (uint32_t)i);
-                        E = __fsub_rn(E, e);
-                        k++;
-                        pend = k < n ? P_START_MODE : P_DONE_MOL;
-                    } else {
-                        i++;
-                    }
-                } else {  // the draw ran past the levels: restart the trial
+                }
+                if (sel >= 0) {
+                    set_q(nq, k, (uint32_t)sel);
+                    E = __fsub_rn(E, sel == i ? e0 : e1);
+                    k++;
+                    pend = k < n ? P_START_MODE : P_DONE_MOL;
+                } else if (exhausted) {  // the draw ran past the levels: restart the trial
                     k = 0;
                     pend = P_START_MODE;
                 }
