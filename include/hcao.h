@@ -206,6 +206,27 @@ hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint3
 hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int64_t n,
                            uint8_t* host_qn, uint64_t* host_trials);
 
+/* The stable cell sort of hcao_cell_sort for callers that cannot allocate
+   device memory: code that must not call cudaMalloc once it is running, such
+   as a host application whose own pool allocator owns the device memory, or
+   a latency-bound loop that cannot take the device-wide synchronisation a
+   cudaMalloc/cudaFree may cause.  Same arguments and results as
+   hcao_cell_sort (device keys, perm and offsets; see there), on cuda_stream
+   (NULL = the legacy default stream); no context is needed.
+   - It allocates nothing: its scratch is one file-scope device array sized
+     for HCAO_NOALLOC_SORT_MAX_KEYS keys (about 8.7 MB), which every GPU that
+     loads the library holds until the process exits.
+   - The first call on a device looks up that array's device address (with
+     the device current); make that first call before any stream capture.
+   - n > HCAO_NOALLOC_SORT_MAX_KEYS returns HCAO_EINVAL; a failed CUDA call
+     returns HCAO_ECUDA.
+   - All calls share the one array: calls that may overlap on the GPU (other
+     streams, other host threads) race and must be serialised by the caller.
+   The paper has no counterpart of this entry point. */
+#define HCAO_NOALLOC_SORT_MAX_KEYS (1 << 19)
+hcao_status hcao_cell_sort_noalloc(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_t* perm,
+                                   uint32_t* offsets, void* cuda_stream);
+
 /* Level energy (J) of level `level` of mode `mode` of species sp, and the
    number of levels; host-side table lookups. */
 hcao_status hcao_level_energy(const hcao_ctx* ctx, int sp, int mode, int level, double* out);

@@ -9,15 +9,17 @@
 // + (count in earlier warps of this round) + (lanes below it with the same digit).
 // Equal keys keep input order, so the particles of a cell stay in load order.
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
+#include "../../include/hcao.h"
 #include "hcao_sort.h"
 
 namespace hcao {
 
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+static_assert(SORT_TILE == SORT_THREADS * SORT_ITEMS, "tile size");
 
 static __global__ void __launch_bounds__(SORT_THREADS)
 k_digit_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* hist, int nblocks) {
@@ -184,3 +186,51 @@ cudaError_t cell_sort(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_
 }
 
 }  // namespace hcao
+
+// ---------------------------------------------------------------------------
+// The same sort for callers that cannot allocate device memory.  Its scratch
+// (radix ping-pong buffers and per-tile digit histograms) lives in one
+// file-scope device array sized for HCAO_NOALLOC_SORT_MAX_KEYS keys; every
+// GPU that loads this library holds that array until the process exits.
+namespace {
+constexpr int64_t kNoAllocTiles = (HCAO_NOALLOC_SORT_MAX_KEYS + hcao::SORT_TILE - 1) / hcao::SORT_TILE;
+constexpr int64_t kNoAllocWords = 4 * (int64_t)HCAO_NOALLOC_SORT_MAX_KEYS + 256 * kNoAllocTiles;
+__device__ __align__(256) uint32_t g_noalloc_sort_scratch[kNoAllocWords];
+
+// Host-side device addresses of the array, one per device, looked up once with
+// that device current (in host code the array's name is only a stand-in).
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kMaxDevices] = {};
+
+cudaError_t noalloc_scratch(uint32_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+extern "C" hcao_status hcao_cell_sort_noalloc(const uint32_t* keys, int64_t n, uint32_t n_cells,
+                                              uint32_t* perm, uint32_t* offsets, void* cuda_stream) {
+    if (n < 0 || n > HCAO_NOALLOC_SORT_MAX_KEYS || n_cells < 1 || (n > 0 && (!keys || !perm)) || !offsets)
+        return HCAO_EINVAL;
+    uint32_t* scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return HCAO_ECUDA;
+    // every buffer the kernels read is written earlier in the same call (the
+    // offsets are zeroed first, each histogram is written before its scan), so
+    // what an earlier call left in the array does not matter
+    const cudaError_t e = hcao::cell_sort(keys, n, n_cells, perm, offsets, scratch,
+                                          static_cast<cudaStream_t>(cuda_stream), nullptr);
+    return e == cudaSuccess ? HCAO_OK : HCAO_ECUDA;
+}
+

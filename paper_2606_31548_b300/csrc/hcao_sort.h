@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 namespace hcao {
+constexpr int SORT_TILE = 256 * 8;  // keys per CTA tile
 // scratch words (uint32) cell_sort needs for n keys
 int64_t sort_scratch_words(int64_t n, uint32_t n_cells);
 int sort_passes(uint32_t n_cells);

@@ -29,8 +29,9 @@ EXPORTS = [
     "hcao_read_moments", "hcao_read_level_populations", "hcao_read_counters",
     "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
-    "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb",
+    "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
 ]
+NOALLOC_SORT_MAX_KEYS = 1 << 19
 
 
 class HcaoError(RuntimeError):
@@ -112,6 +113,7 @@ def lib() -> C.CDLL:
         L.hcao_level_energy.argtypes = [vp, i32, i32, i32, C.POINTER(dbl)]
         L.hcao_n_levels.argtypes = [vp, i32, i32, C.POINTER(i32)]
         L.hcao_sample_lb.argtypes = [vp, i32, dbl, u64, i64, vp, C.POINTER(u64)]
+        L.hcao_cell_sort_noalloc.argtypes = [vp, i64, C.c_uint32, vp, vp, vp]
         L.hcao_set_profiling.argtypes = [vp, i32]
         L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
@@ -320,6 +322,15 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.hcao_kernel_launches(self.h))
+
+
+def cell_sort_noalloc(keys_dev, n, n_cells, perm_dev, offsets_dev, stream=None) -> None:
+    """hcao_cell_sort_noalloc: the stable cell sort without any device
+    allocation (scratch in a fixed device array, n <= NOALLOC_SORT_MAX_KEYS)."""
+    r = lib().hcao_cell_sort_noalloc(_dptr(keys_dev), n, n_cells, _dptr(perm_dev), _dptr(offsets_dev),
+                                     None if stream is None else C.c_void_p(int(stream)))
+    if r != 0:
+        raise HcaoError(r, "hcao_cell_sort_noalloc failed")
 
 
 def from_workload(w, precision=FP64, log=False, init_vib=True, **kw) -> Context:
