@@ -27,15 +27,47 @@ from paper_2606_31548_b300 import workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 WORKLOAD = "ch4_heat_bath_4096x500_15000K_dissociation"
+KERNEL_SRC = os.path.join(ROOT, "paper_2606_31548_b300", "csrc", "hcao_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffic.json")
+
+# Algorithmic lane-operations of the relaxation kernel per unit of K5 work (the
+# least integer/FP32 lane operations each unit needs):
+#   level evaluation: 2 loads, subtract, bucket index (bit cast, shift, subtract,
+#     2 clamps), table offset, accumulate, compare, loop = 12
+#   mode draw: half a Philox4x32-10 block (10 rounds x 8 ops / 2) + 8 = 48
+#   molecule sample: vibrational energy of up to 9 modes twice + setup = 60
+#   pair: members, two record loads, relative energy, isotropic direction,
+#     scattering, two record stores, event word = 160
+OPS_PER_UNIT = (12, 48, 60, 160)
+SMS, LANES_PER_SM = 148, 128
 
 
 def _peaks():
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2032.0)), "measured"
     except Exception:
-        return 6400.0, "fallback"
+        return 6400.0, 2032.0, "fallback"
+
+
+def _kernel_hash():
+    import hashlib
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_per_launch():
+    """DRAM bytes per launch of the relaxation kernel from the committed ncu
+    summary, or None if the kernel source changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        if t.get("kernel_src_sha256_16") != _kernel_hash():
+            return None
+        return t
+    except Exception:
+        return None
 
 
 def _dist():
@@ -71,9 +103,10 @@ def _sum_over_ranks(x: float) -> float:
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 50 ms) around the timed region; only samples
+    whose timestamps fall inside it are kept."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -81,17 +114,32 @@ class Clocks:
         self.dev = device
         self.p = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 15
+            while time.time() < deadline:  # wait for the first sample
+                time.sleep(0.05)
+                if os.path.getsize(self.path) > 0:
+                    break
         except Exception:
             self.p = None
         return self
+
+    def start(self):
+        import datetime
+        self.t0 = datetime.datetime.now()
+
+    def stop(self):
+        import datetime
+        self.t1 = datetime.datetime.now()
+        time.sleep(0.12)
 
     def __exit__(self, *a):
         if self.p:
@@ -103,24 +151,30 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        import datetime
         if not self.p:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, n_all = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            n_all += 1
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                mhz, mxx = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            if self.t0 and self.t1 and not (self.t0 <= ts <= self.t1):
+                continue
+            sm.append(mhz)
+            mx = mxx
+            for n, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples_in_timed_region": len(sm), "samples_total": n_all}
 
 
 def cpu_baseline(budget_s: float = 12.0, cells: int = 48):
@@ -175,7 +229,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -204,6 +258,7 @@ def main():
         ctx.step(1)
     ctx.sync()
     c0 = ctx.read_counters(0)
+    work0 = ctx.read_work()
     launches0 = ctx.kernel_launches()
     ctx.set_profiling(True)
     torch.cuda.synchronize()
@@ -212,6 +267,7 @@ def main():
           for _ in range(args.steps)]
     psteps = 0
     with Clocks(local) as clk:
+        clk.start()
         t_wall0 = time.perf_counter()
         for i in range(args.steps):
             n = ctx.count(0)  # particles entering this step (host sync, outside the events)
@@ -222,10 +278,12 @@ def main():
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
+        clk.stop()
     _barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ctx.sync()
     c1 = ctx.read_counters(0)
+    work = (ctx.read_work() - work0).astype(np.float64)
     launches = ctx.kernel_launches() - launches0
     kms, kn = ctx.read_profile()
     ctx.set_profiling(False)
@@ -234,21 +292,35 @@ def main():
     tot_psteps = _sum_over_ranks(float(psteps))
     tot_coll = _sum_over_ranks(collisions)
 
-    # roofline of the dominant kernel (collide): algorithmic bytes per
-    # particle-step = 2 S, S = 12 B velocity + 9 B quantum numbers + 1 B species
-    # + 4 B cell (FP32) = 26 B; FP64 adds 12 B
-    S = 26.0 if prec == hcao.FP32 else 38.0
+    # roofline of the dominant kernel, the relaxation kernel: it is bound by
+    # plain ALU work (the K5 draws), so achieved = algorithmic lane-operations
+    # (counted K5 work x OPS_PER_UNIT) / its CUDA-event time, against the lane
+    # peak 148 SMs x 128 lanes x the maximum SM clock.  The HBM view (SURVEY's
+    # 2 S bytes per particle-step, S = 26 B FP32 / 38 B FP64) is kept beside it.
     names = hcao.Context.PROFILE_KERNELS
     per_step = {k: kms[i] / args.steps for i, k in enumerate(names)}
-    dom = max(("select", "relax", "react"), key=lambda k: per_step[k])
+    hbm_peak, sm_mhz_max, peak_kind = _peaks()
+    relax_s = kms[2] / 1e3
+    lane_ops = float(np.dot(work, OPS_PER_UNIT))
+    alu_peak = SMS * LANES_PER_SM * sm_mhz_max * 1e6 / 1e9  # Glane-op/s
+    alu_ach = lane_ops / relax_s / 1e9 if relax_s > 0 and lane_ops > 0 else None
+    S = 26.0 if prec == hcao.FP32 else 38.0
     collide_s = (kms[1] + kms[2] + kms[3]) / 1e3
-    peak, peak_kind = _peaks()
-    achieved = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_kind": peak_kind, "kernel": "collide phase (k_select+k_relax+k_react)",
-            "dominant_kernel": "k_" + dom, "kernel_ms_per_step": per_step,
-            "kernel_launches": {k: int(kn[i]) for i, k in enumerate(names)}}
+    hbm_ach = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
+    tr = _traffic_per_launch()
+    roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Glane-op/s",
+            "frac": (alu_ach / alu_peak) if alu_ach else None,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "peak_kind": f"derived: {SMS} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz ({peak_kind} clock)",
+            "kernel": "k_relax_fast" if prec == hcao.FP32 else "k_relax",
+            "work_per_step": {"level_evals": work[0] / args.steps, "mode_draws": work[1] / args.steps,
+                              "samples": work[2] / args.steps, "pairs": work[3] / args.steps},
+            "ops_per_unit": list(OPS_PER_UNIT),
+            "kernel_ms_per_step": per_step,
+            "kernel_launches": {k: int(kn[i]) for i, k in enumerate(names)},
+            "hbm_view": {"achieved_GBps": hbm_ach, "peak_GBps": hbm_peak,
+                         "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
+                         "bytes_per_particle_step": 2 * S, "time": "collide phase"}}
 
     # e2e through the C ABI with host buffers (pinned): load + step + moments
     e2e = None

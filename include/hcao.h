@@ -241,6 +241,12 @@ hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
                               int* n_out);
 
+/* Algorithmic work of the FP32 relaxation kernel since create: host_out[0]
+   LB level evaluations (one weight of one level of one mode), [1] mode draws
+   (one Philox uniform each), [2] molecule samples, [3] relaxed pairs; *n_out
+   = 4.  Zero in FP64 mode.  (Instrumentation for the ALU roofline.) */
+hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* host_out, int max, int* n_out);
+
 /* Number of this library's kernels launched since create (instrumentation). */
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx);
 

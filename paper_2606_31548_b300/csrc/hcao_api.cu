@@ -81,6 +81,7 @@ struct hcao_ctx {
     uint4* d_qA = nullptr;
     uint4* d_qB = nullptr;
     uint32_t* d_qsize = nullptr;
+    unsigned long long* d_work = nullptr;
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint32_t* d_err = nullptr;
@@ -478,6 +479,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.qB = ctx->d_qB;
     a.qsize = ctx->d_qsize;
     a.has_reactions = ctx->n_reactions > 0 ? 1 : 0;
+    a.work = ctx->d_work;
     a.pair_cap = ctx->pair_cap;
     a.log = ctx->d_log;
     a.log_on = ctx->log_on ? 1 : 0;
@@ -527,12 +529,13 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_qsize, 3 * MAX_ROUNDS) != cudaSuccess) {
+        dalloc(ctx, &ctx->d_qsize, 3 * MAX_ROUNDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
         delete ctx;
         return HCAO_ENOMEM;
     }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
     cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 1), ctx->stream);
+    cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long) * 4, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         delete ctx;
         return HCAO_ECUDA;
@@ -564,6 +567,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_qA);
     dfree(ctx, ctx->d_qB);
     dfree(ctx, ctx->d_qsize);
+    dfree(ctx, ctx->d_work);
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
@@ -1093,6 +1097,17 @@ hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int
         ms[k] = ctx->prof_ms[k];
         launches[k] = ctx->prof_n[k];
     }
+    if (n_out) *n_out = n;
+    return HCAO_OK;
+}
+
+hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* out, int max, int* n_out) {
+    if (!ctx || !out || max < 1) return HCAO_EINVAL;
+    unsigned long long w[4];
+    CU(cudaMemcpyAsync(w, ctx->d_work, sizeof w, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int n = std::min(max, 4);
+    for (int i = 0; i < n; ++i) out[i] = w[i];
     if (n_out) *n_out = n;
     return HCAO_OK;
 }

@@ -130,6 +130,7 @@ struct StepArgs {
     uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax and react queue
                                     // lengths, then the relax queue's fetch heads
     int has_reactions;
+    unsigned long long* work;       // [4] K5 level evaluations, mode starts, molecule samples, pairs
     uint64_t pair_cap;              // capacity of cflag / log
     hcao_log_rec* log;
     int log_on;

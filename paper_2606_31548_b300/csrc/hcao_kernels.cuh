@@ -1508,6 +1508,8 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     // if odd; an FP32 uniform takes the top 24 bits)
     uint32_t sblk = 0, spur = 0, sword = 0;
     bool shave = false;
+    // algorithmic work of this lane (level evaluations, mode starts, samples, pairs)
+    uint32_t w_lev = 0, w_mode = 0, w_samp = 0, w_pair = 0;
 
     auto uniform = [&]() -> float {
         uint32_t w;
@@ -1555,6 +1557,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 o.ev = EV_ACC;
                 o.trials = 0u;
                 mol = 0;
+                w_pair++;
                 pend = P_START_MOL;
             } else if (pend == P_START_MOL) {
                 if (mol >= 2) { pend = P_SCATTER; continue; }
@@ -1573,6 +1576,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 hm = S.tab_off;
                 b0 = S.base_f[0];
                 o.ev += 1u << EV_SAMP_SHIFT;
+                w_samp++;
                 Ec = fix2f(Ecd);
                 m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
                 trials = 0;
@@ -1657,6 +1661,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         }
         const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
         t = __fmul_rn(uniform(), __ldg(Hb + hm + k * MT + m));
+        w_mode++;
         cum = 0.f;
         i = 0;
         lk = S.lev_off[k];
@@ -1693,10 +1698,12 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                     exhausted = true;
                 } else {
                     cum = __fadd_rn(cum, w0);
+                    w_lev++;
                     if (t < cum) sel = i;
                     else if (w1 < 0.f) exhausted = true;
                     else {
                         cum = __fadd_rn(cum, w1);
+                        w_lev++;
                         if (t < cum) sel = i + 1;
                         else i += 2;
                     }
@@ -1726,6 +1733,20 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         if (alive && pend == P_START_MODE) start_mode();
         if (do_heavy && alive && pend >= P_PAIR) heavy();
         if (alive && pend == P_START_MODE) start_mode();
+    }
+    // work counters: one atomic per warp and counter
+    unsigned long long wl = w_lev, wm = w_mode, ws = w_samp, wp = w_pair;
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        wl += __shfl_xor_sync(act, wl, o2);
+        wm += __shfl_xor_sync(act, wm, o2);
+        ws += __shfl_xor_sync(act, ws, o2);
+        wp += __shfl_xor_sync(act, wp, o2);
+    }
+    if (lane == 0 && A.work) {
+        atomicAdd(A.work + 0, wl);
+        atomicAdd(A.work + 1, wm);
+        atomicAdd(A.work + 2, ws);
+        atomicAdd(A.work + 3, wp);
     }
 }
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
+    "hcao_read_work",
 ]
 NOALLOC_SORT_MAX_KEYS = 1 << 19
 
@@ -114,6 +115,7 @@ def lib() -> C.CDLL:
         L.hcao_n_levels.argtypes = [vp, i32, i32, C.POINTER(i32)]
         L.hcao_sample_lb.argtypes = [vp, i32, dbl, u64, i64, vp, C.POINTER(u64)]
         L.hcao_cell_sort_noalloc.argtypes = [vp, i64, C.c_uint32, vp, vp, vp]
+        L.hcao_read_work.argtypes = [vp, vp, i32, C.POINTER(i32)]
         L.hcao_set_profiling.argtypes = [vp, i32]
         L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
@@ -319,6 +321,13 @@ class Context:
         got = C.c_int()
         self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 5, C.byref(got)))
         return ms, n
+
+    def read_work(self) -> np.ndarray:
+        """[level evaluations, mode draws, molecule samples, relaxed pairs] (FP32 relax kernel)."""
+        out = np.zeros(4, np.uint64)
+        n = C.c_int()
+        self._chk(self.L.hcao_read_work(self.h, _p(out), 4, C.byref(n)))
+        return out
 
     def kernel_launches(self) -> int:
         return int(self.L.hcao_kernel_launches(self.h))
