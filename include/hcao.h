@@ -152,7 +152,9 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int res, double T_vib);
 
 /* Advance every reservoir by n_steps collision phases (NTC pair selection with
    VHS cross-sections, QK reaction test and execution, HCAO LB relaxation,
-   isotropic scattering).  Asynchronous on the context's stream. */
+   isotropic scattering).  Asynchronous on the context's stream.  For
+   n_steps >= 2 (profiling off) one step is captured once as a CUDA graph on a
+   private stream and launched n_steps times on the context's stream. */
 hcao_status hcao_step(hcao_ctx* ctx, int n_steps);
 /* Wait for the stream; return the sticky device error status. */
 hcao_status hcao_sync(hcao_ctx* ctx);
@@ -240,6 +242,14 @@ hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out);
 hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
                               int* n_out);
+
+/* Launch-shape autotuner: steps the reservoirs by 7 x steps_per_candidate
+   steps while timing candidate grid sizes of the pair-acceptance and
+   relaxation kernels (CUDA events), then keeps the fastest.  The simulation
+   advances normally: results do not depend on launch shapes (every draw is
+   keyed by step, cell and pair).  chosen (may be NULL) receives the two grid
+   sizes. */
+hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen);
 
 /* Algorithmic work of the FP32 relaxation kernel since create: host_out[0]
    LB level evaluations (one weight of one level of one mode), [1] mode draws

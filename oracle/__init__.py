@@ -263,3 +263,21 @@ def from_workload(w, table_points=2048, table_span_J=64 * 1.602176634e-19, log=F
         o.init_vibration(res, w.T_vib0)
     o.set_log(log)
     return o
+
+
+def from_batched(bw, table_points=2048, table_span_J=64 * 1.602176634e-19, log=False,
+                 only=None) -> Oracle:
+    """Oracle holding the reservoirs of a batched workload (all, or the indices in `only`)."""
+    o = Oracle(table_points, table_span_J)
+    for s in bw.species:
+        o.add_species(s)
+    for r in bw.reactions:
+        o.add_reaction(r)
+    for i, w in enumerate(bw.reservoirs):
+        if only is not None and i not in only:
+            continue
+        res = o.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        o.load(res, w.v, w.qn0(), w.species_idx, w.cell)
+        o.init_vibration(res, w.T_vib0)
+    o.set_log(log)
+    return o

@@ -82,6 +82,14 @@ struct hcao_ctx {
     uint4* d_qB = nullptr;
     uint32_t* d_qsize = nullptr;
     unsigned long long* d_work = nullptr;
+    // launch shapes (autotuned; results do not depend on them)
+    int grid_select = 0, grid_relax = 0, grid_react = 0;
+    // CUDA graph of one step, captured on a private stream, re-captured when
+    // the kernel arguments change
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    StepArgs graph_args{};
+    bool use_graph = true;
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint32_t* d_err = nullptr;
@@ -480,6 +488,9 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.qsize = ctx->d_qsize;
     a.has_reactions = ctx->n_reactions > 0 ? 1 : 0;
     a.work = ctx->d_work;
+    a.grid_select = ctx->grid_select;
+    a.grid_relax = ctx->grid_relax;
+    a.grid_react = ctx->grid_react;
     a.pair_cap = ctx->pair_cap;
     a.log = ctx->d_log;
     a.log_on = ctx->log_on ? 1 : 0;
@@ -571,6 +582,8 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (int k = 0; k < hcao_ctx::NPROF; ++k)
         for (auto& e : ctx->prof_ev[k]) {
             cudaEventDestroy(e.first);
@@ -1026,6 +1039,30 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
     const int block = 128;
     const int grid = ctx->sm_count * 8;
     const bool f64 = ctx->cfg.precision == HCAO_FP64;
+    if (!ctx->prof_on && ctx->use_graph && n_steps >= 2) {
+        // one step as a CUDA graph, launched n_steps times on the caller's stream
+        if (!ctx->graph || std::memcmp(&a, &ctx->graph_args, sizeof a) != 0) {
+            if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+            if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            uint64_t dummy = 0;
+            if (f64) launch_step<double>(a, grid, block, ctx->cap_stream, &dummy);
+            else launch_step<float>(a, grid, block, ctx->cap_stream, &dummy);
+            CU(cudaStreamEndCapture(ctx->cap_stream, &g));
+            cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+            cudaGraphDestroy(g);
+            CU(e);
+            ctx->graph_args = a;
+        }
+        const uint64_t per_step = 2 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2);
+        for (int s = 0; s < n_steps; ++s) {
+            CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+            ctx->launches += per_step;
+        }
+        return HCAO_OK;
+    }
     for (int s = 0; s < n_steps; ++s) {
         if (!ctx->prof_on) {
             if (f64) launch_step<double>(a, grid, block, ctx->stream, &ctx->launches);
@@ -1099,6 +1136,44 @@ hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int
     }
     if (n_out) *n_out = n;
     return HCAO_OK;
+}
+
+hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen) {
+    if (!ctx || steps_per_candidate < 1) return HCAO_EINVAL;
+    if (ctx->n_cells_total == 0) return HCAO_OK;
+    const int sm = ctx->sm_count;
+    const int sel_cand[4] = {2 * sm, 4 * sm, 8 * sm, 16 * sm};
+    const int rel_cand[3] = {4 * sm, 5 * sm, 8 * sm};
+    const bool was_prof = ctx->prof_on;
+    ctx->prof_on = true;
+    auto time_phase = [&](int k) -> double {  // mean ms of profile class k over the candidate's steps
+        for (int j = 0; j < hcao_ctx::NPROF; ++j) { ctx->prof_used[j] = 0; ctx->prof_ms[j] = 0; ctx->prof_n[j] = 0; }
+        if (hcao_step(ctx, steps_per_candidate) != HCAO_OK) return 1e30;
+        double ms[hcao_ctx::NPROF];
+        uint64_t n[hcao_ctx::NPROF];
+        int got = 0;
+        if (hcao_read_profile(ctx, ms, n, hcao_ctx::NPROF, &got) != HCAO_OK) return 1e30;
+        return ms[k];
+    };
+    double best = 1e30;
+    int bs = ctx->grid_select, br = ctx->grid_relax;
+    for (int c : sel_cand) {
+        ctx->grid_select = c;
+        const double t = time_phase(1);
+        if (t < best) { best = t; bs = c; }
+    }
+    ctx->grid_select = bs;
+    best = 1e30;
+    for (int c : rel_cand) {
+        ctx->grid_relax = c;
+        const double t = time_phase(2);
+        if (t < best) { best = t; br = c; }
+    }
+    ctx->grid_relax = br;
+    ctx->prof_on = was_prof;
+    for (int j = 0; j < hcao_ctx::NPROF; ++j) { ctx->prof_used[j] = 0; ctx->prof_ms[j] = 0; ctx->prof_n[j] = 0; }
+    if (chosen) { chosen[0] = bs; chosen[1] = br; }
+    return map_err(ctx);
 }
 
 hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* out, int max, int* n_out) {

@@ -131,6 +131,7 @@ struct StepArgs {
                                     // lengths, then the relax queue's fetch heads
     int has_reactions;
     unsigned long long* work;       // [4] K5 level evaluations, mode starts, molecule samples, pairs
+    int grid_select, grid_relax, grid_react;  // launch shapes (host-side; results do not depend on them)
     uint64_t pair_cap;              // capacity of cflag / log
     hcao_log_rec* log;
     int log_on;

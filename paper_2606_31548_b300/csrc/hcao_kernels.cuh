@@ -1958,11 +1958,14 @@ __global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* 
 
 template <class R>
 void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream_t s) {
-    if (phase == 0) k_select<R><<<grid, 256, 0, s>>>(a, r);
+    const int gs = a.grid_select > 0 ? a.grid_select : grid;
+    const int gr = a.grid_relax > 0 ? a.grid_relax : grid;
+    const int gx = a.grid_react > 0 ? a.grid_react : grid;
+    if (phase == 0) k_select<R><<<gs, 256, 0, s>>>(a, r);
     else if (phase == 1) {
-        if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<grid, 128, 0, s>>>(a, r);
-        else k_relax<R><<<grid, 128, 0, s>>>(a, r);
-    } else if (a.has_reactions) k_react<R><<<grid, 128, 0, s>>>(a, r);
+        if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<gr, 128, 0, s>>>(a, r);
+        else k_relax<R><<<gr, 128, 0, s>>>(a, r);
+    } else if (a.has_reactions) k_react<R><<<gx, 128, 0, s>>>(a, r);
 }
 template <class R>
 void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStream_t s) {

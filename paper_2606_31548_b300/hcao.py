@@ -30,7 +30,7 @@ EXPORTS = [
     "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
-    "hcao_read_work",
+    "hcao_read_work", "hcao_autotune",
 ]
 NOALLOC_SORT_MAX_KEYS = 1 << 19
 
@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
         L.hcao_sample_lb.argtypes = [vp, i32, dbl, u64, i64, vp, C.POINTER(u64)]
         L.hcao_cell_sort_noalloc.argtypes = [vp, i64, C.c_uint32, vp, vp, vp]
         L.hcao_read_work.argtypes = [vp, vp, i32, C.POINTER(i32)]
+        L.hcao_autotune.argtypes = [vp, i32, vp]
         L.hcao_set_profiling.argtypes = [vp, i32]
         L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
@@ -322,6 +323,12 @@ class Context:
         self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 5, C.byref(got)))
         return ms, n
 
+    def autotune(self, steps_per_candidate=1):
+        """Pick launch shapes by timing candidates on live steps; returns (select grid, relax grid)."""
+        out = np.zeros(2, np.int32)
+        self._chk(self.L.hcao_autotune(self.h, steps_per_candidate, _p(out)))
+        return int(out[0]), int(out[1])
+
     def read_work(self) -> np.ndarray:
         """[level evaluations, mode draws, molecule samples, relaxed pairs] (FP32 relax kernel)."""
         out = np.zeros(4, np.uint64)
@@ -331,6 +338,19 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.hcao_kernel_launches(self.h))
+
+
+def from_batched(bw, precision=FP64, init_vib=True, **kw) -> Context:
+    """A context holding every reservoir of a batched workload (reservoir i = id i)."""
+    c = Context(precision=precision, **kw)
+    c.set_species(bw.species)
+    c.set_reactions(bw.reactions)
+    for w in bw.reservoirs:
+        rid = c.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        c.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
+        if init_vib:
+            c.init_vibration(rid, w.T_vib0)
+    return c
 
 
 def cell_sort_noalloc(keys_dev, n, n_cells, perm_dev, offsets_dev, stream=None) -> None:

@@ -186,3 +186,50 @@ def random_levels(rng: np.random.Generator, n: int, n_levels: List[int], n_modes
     for j in range(n_modes):
         q[:, j] = rng.integers(0, n_levels[j], size=n)
     return q
+
+
+def vhs_collision_frequency(sp: Species, n_density: float, T: float) -> float:
+    """Mean collision frequency of a simple VHS gas, nu = 4 d^2 n sqrt(pi k T_ref / m)
+    (T/T_ref)^(1-omega) (Bird's VHS closed form), used only to choose a time step
+    dt = 0.2 / nu(T0) for a workload."""
+    import math
+    return 4.0 * sp.d_ref ** 2 * n_density * math.sqrt(math.pi * KB * sp.T_ref / sp.mass) * \
+        (T / sp.T_ref) ** (1.0 - sp.omega)
+
+
+@dataclasses.dataclass
+class BatchedWorkload:
+    """Many independent single-cell 0D reservoirs sharing one species table."""
+    name: str
+    species: List[Species]
+    reactions: List[Reaction]
+    reservoirs: List[Workload]
+    steps: int
+
+    @property
+    def n(self) -> int:
+        return int(sum(r.n for r in self.reservoirs))
+
+
+def batched_reservoirs(n_res: int = 256, n_min: int = 10_000, n_max: int = 2_000_000,
+                       T_min: float = 5000.0, T_max: float = 30000.0, steps: int = 1000,
+                       seed: int = 0x48434134) -> BatchedWorkload:
+    """Independent 0D reservoirs (one cell of V = 4.64e-6 m^3, n = 1e23 m^-3):
+    particle counts log-uniform in [n_min, n_max], T uniform in [T_min, T_max]
+    (T_tr0 = T_vib0), species the synthetic triatomic or the CH4-like
+    pentatomic with probability 1/2 each, no chemistry, dt = 0.2 / nu(T0)."""
+    rng = np.random.default_rng(seed)
+    species = [triatomic(), ch4_like()]
+    out = []
+    for i in range(n_res):
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        T = float(rng.uniform(T_min, T_max))
+        s = int(rng.integers(0, 2))
+        dt = 0.2 / vhs_collision_frequency(species[s], 1e23, T)
+        r = _build(f"reservoir{i}", species, [], 1, np.array([n]), [1.0], 4.64e-6, 1e23, dt, T, T,
+                   seed + 1 + i, steps, shuffle=False)
+        r.species_idx[:] = s
+        mass = np.full(n, species[s].mass)
+        r.v = np.ascontiguousarray(maxwellian(np.random.default_rng(seed + 100000 + i), n, mass, T))
+        out.append(r)
+    return BatchedWorkload("batched_reservoirs", species, [], out, steps)
