@@ -360,9 +360,10 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         }
     DevCell* cells = nullptr;
     unsigned long long* cnt = nullptr;
-    CU(dalloc(ctx, &cells, (size_t)total));
-    CU(dalloc(ctx, &cnt, (size_t)total * NCNT));
-    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (size_t)std::max(total, 1) * NCNT, ctx->stream));
+    const size_t cells_alloc = (size_t)std::max(total, 1);
+    CU(dalloc(ctx, &cells, cells_alloc));
+    CU(dalloc(ctx, &cnt, cells_alloc * NCNT));
+    CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * cells_alloc * NCNT, ctx->stream));
     int at = 0;
     for (int id = 0; id < (int)ctx->res.size(); ++id) {
         Reservoir& r = ctx->res[id];
@@ -394,7 +395,7 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         dfree(ctx, ctx->d_log);
         if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
         ctx->d_cscratch = nullptr;
-        ctx->pair_cap = std::max<uint64_t>(pairs, 1024);
+        ctx->pair_cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
         CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
         dfree(ctx, ctx->d_qA);
         dfree(ctx, ctx->d_qB);
@@ -425,6 +426,25 @@ hcao_status read_cells(hcao_ctx* ctx, const Reservoir& r, std::vector<DevCell>& 
     CU(cudaMemcpyAsync(out.data(), ctx->d_cells + r.cell0, sizeof(DevCell) * r.n_cells,
                        cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+// off[c] = first particle of cell c in canonical order, off[n_cells] = total,
+// uploaded to a fresh device buffer the caller frees
+hcao_status particle_prefix(hcao_ctx* ctx, const Reservoir& r, uint64_t** d_off, uint64_t* total) {
+    std::vector<DevCell> cells;
+    hcao_status st = read_cells(ctx, r, cells);
+    if (st != HCAO_OK) return st;
+    std::vector<uint64_t> off((size_t)r.n_cells + 1);
+    uint64_t n = 0;
+    for (int c = 0; c < r.n_cells; ++c) {
+        off[c] = n;
+        n += cells[c].n;
+    }
+    off[r.n_cells] = n;
+    CU(dalloc(ctx, d_off, off.size()));
+    CU(cudaMemcpyAsync(*d_off, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+    *total = n;
     return HCAO_OK;
 }
 
@@ -976,17 +996,22 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
     if (!bt.empty()) CU(cudaMemcpyAsync(dbt, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (!sa.empty()) CU(cudaMemcpyAsync(dsa, sa.data(), sizeof(double) * sa.size(), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+    uint64_t* dpo = nullptr;
+    uint64_t total = 0;
+    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_init_vib<double>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_res, id, ctx->d_consts, dbt, dsa, doff,
-                                ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+        launch_init_vib<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_res, id, ctx->d_consts, dbt,
+                                dsa, doff, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
     else
-        launch_init_vib<float>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_res, id, ctx->d_consts, dbt, dsa, doff,
-                               ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+        launch_init_vib<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_res, id, ctx->d_consts, dbt,
+                               dsa, doff, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     dfree(ctx, dbt);
     dfree(ctx, dsa);
     dfree(ctx, doff);
+    dfree(ctx, dpo);
     return map_err(ctx);
 }
 
@@ -1213,12 +1238,13 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
     std::vector<DevCell> cells;
     hcao_status st = read_cells(ctx, *r, cells);
     if (st != HCAO_OK) return st;
-    std::vector<uint64_t> off(r->n_cells);
+    std::vector<uint64_t> off((size_t)r->n_cells + 1);
     uint64_t n = 0;
     for (int c = 0; c < r->n_cells; ++c) {
         off[c] = n;
         n += cells[c].n;
     }
+    off[r->n_cells] = n;
     if (n == 0) return map_err(ctx);
     double* dv = nullptr;
     uint8_t* dq = nullptr;
@@ -1228,12 +1254,12 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
     CU(dalloc(ctx, &dq, (size_t)n * 16));
     CU(dalloc(ctx, &ds, (size_t)n));
     CU(dalloc(ctx, &dc, (size_t)n));
-    CU(dalloc(ctx, &doff, (size_t)r->n_cells));
-    CU(cudaMemcpyAsync(doff, off.data(), sizeof(uint64_t) * r->n_cells, cudaMemcpyHostToDevice, ctx->stream));
+    CU(dalloc(ctx, &doff, (size_t)r->n_cells + 1));
+    CU(cudaMemcpyAsync(doff, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff, dv, dq, ds, dc, ctx->stream);
+        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff, n, dv, dq, ds, dc, ctx->stream);
     else
-        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff, dv, dq, ds, dc, ctx->stream);
+        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff, n, dv, dq, ds, dc, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     if (v) CU(cudaMemcpyAsync(v, dv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1255,10 +1281,16 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     CU(dalloc(ctx, &dcnt, MAXS));
     CU(cudaMemsetAsync(dacc, 0, sizeof(double) * (5 + MAXS), ctx->stream));
     CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
+    uint64_t* dpo = nullptr;
+    uint64_t total = 0;
+    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_consts, ctx->d_lev64, dacc, dcnt, ctx->stream);
+        launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_consts, ctx->d_lev64, dacc,
+                               dcnt, ctx->stream);
     else
-        launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, ctx->d_consts, ctx->d_lev64, dacc, dcnt, ctx->stream);
+        launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_consts, ctx->d_lev64, dacc,
+                              dcnt, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     double acc[5 + MAXS];
@@ -1268,6 +1300,7 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     CU(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, dacc);
     dfree(ctx, dcnt);
+    dfree(ctx, dpo);
     std::memset(out, 0, sizeof *out);
     double M = 0.0;
     int64_t N = 0;
@@ -1299,16 +1332,21 @@ hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode,
     unsigned long long* dh = nullptr;
     CU(dalloc(ctx, &dh, MAXL));
     CU(cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * MAXL, ctx->stream));
+    uint64_t* dpo = nullptr;
+    uint64_t total = 0;
+    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_levelpop<double>(ctx->d_cells, r->cell0, r->n_cells, sp, mode, dh, ctx->stream);
+        launch_levelpop<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, sp, mode, dh, ctx->stream);
     else
-        launch_levelpop<float>(ctx->d_cells, r->cell0, r->n_cells, sp, mode, dh, ctx->stream);
+        launch_levelpop<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, sp, mode, dh, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     unsigned long long h[MAXL];
     CU(cudaMemcpyAsync(h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, dh);
+    dfree(ctx, dpo);
     for (int i = 0; i < max_levels; ++i) counts[i] = i < MAXL ? (uint64_t)h[i] : 0;
     return map_err(ctx);
 }

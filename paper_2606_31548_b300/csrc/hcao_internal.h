@@ -156,21 +156,23 @@ template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm
                                             const uint32_t* offsets, const uint64_t* cell_slot0,
                                             int n_cells, const double* v, const uint8_t* qn,
                                             const int32_t* sp, int64_t n, cudaStream_t s);
-template <class R> void launch_pack(const DevCell* cells, int cell0, int n_cells,
-                                    const uint64_t* out_off, double* v, uint8_t* qn, int32_t* sp,
+template <class R> void launch_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                                    uint64_t total, double* v, uint8_t* qn, int32_t* sp,
                                     int32_t* cell, cudaStream_t s);
 template <class R> void launch_init_vib(const DevCell* cells, int cell0, int n_cells,
-                                        const DevRes* res, int res_slot, const Consts* C,
-                                        const double* bend_thr, const double* str_acc,
-                                        const int* thr_off, uint32_t reject_cap, uint32_t* err,
-                                        cudaStream_t s);
+                                        const uint64_t* off, uint64_t total, const DevRes* res,
+                                        int res_slot, const Consts* C, const double* bend_thr,
+                                        const double* str_acc, const int* thr_off,
+                                        uint32_t reject_cap, uint32_t* err, cudaStream_t s);
 template <class R> void launch_moments(const DevCell* cells, int cell0, int n_cells,
-                                       const Consts* C, const double* lev64, double* acc,
-                                       unsigned long long* cnt, cudaStream_t s);
+                                       const uint64_t* off, uint64_t total, const Consts* C,
+                                       const double* lev64, double* acc, unsigned long long* cnt,
+                                       cudaStream_t s);
 template <class R> void launch_sample_diag(const StepArgs& a, int sp, double Ec, uint64_t seed,
                                            int64_t n, uint8_t* out, unsigned long long* trials,
                                            int* status, cudaStream_t s);
-template <class R> void launch_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
-                                        int mode, unsigned long long* hist, cudaStream_t s);
+template <class R> void launch_levelpop(const DevCell* cells, int cell0, int n_cells,
+                                        const uint64_t* off, uint64_t total, int sp, int mode,
+                                        unsigned long long* hist, cudaStream_t s);
 
 }  // namespace hcao

@@ -2046,101 +2046,114 @@ __global__ void k_scatter_load(typename RecOf<R>::T* recs, const uint32_t* perm,
     }
 }
 
+// Readout and initialisation kernels run flat over a reservoir's particles
+// (off[c] = first particle of cell c in canonical order, off[n_cells] = total),
+// so one very large cell spreads over the whole GPU.
+__device__ __forceinline__ int cell_of64(const uint64_t* off, int n_cells, uint64_t j) {
+    int lo = 0, hi = n_cells;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 template <class R>
-__global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* out_off,
+__global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
                        double* v, uint8_t* qn, int32_t* sp, int32_t* cell) {
     using Rec = typename RecOf<R>::T;
-    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
-        const DevCell cl = cells[cell0 + c];
-        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
-        const uint64_t o = out_off[c];
-        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
-            Rec r;
-            load_rec(recs + i, r);
-            if (v) for (int d = 0; d < 3; ++d) v[3 * (o + i) + d] = (double)r.v[d];
-            if (qn) {
-                uint32_t* q = reinterpret_cast<uint32_t*>(qn + 16 * (o + i));
-                for (int w = 0; w < 4; ++w) q[w] = r.q[w];
-            }
-            if (sp) sp[o + i] = (int32_t)(r.meta & 0xFFu);
-            if (cell) cell[o + i] = c;
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        const Rec* recs = reinterpret_cast<const Rec*>(cells[cell0 + c].rec);
+        Rec r;
+        load_rec(recs + (j - off[c]), r);
+        if (v) for (int d = 0; d < 3; ++d) v[3 * j + d] = (double)r.v[d];
+        if (qn) {
+            uint32_t* q = reinterpret_cast<uint32_t*>(qn + 16 * j);
+            for (int w = 0; w < 4; ++w) q[w] = r.q[w];
         }
+        if (sp) sp[j] = (int32_t)(r.meta & 0xFFu);
+        if (cell) cell[j] = c;
     }
 }
 
 // P6/P7 initial quantum numbers (double draws in both precisions)
 template <class R>
-__global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const DevRes* res,
-                           int rslot, const Consts* C, const double* bend_thr,
+__global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                           const DevRes* res, int rslot, const Consts* C, const double* bend_thr,
                            const double* str_acc, const int* thr_off, uint32_t reject_cap,
                            uint32_t* err) {
     using Rec = typename RecOf<R>::T;
     const DevRes rs = res[rslot];
-    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
-        const DevCell cl = cells[cell0 + c];
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        const uint32_t i = (uint32_t)(j - off[c]);
+        const DevCell& cl = cells[cell0 + c];
         Rec* recs = reinterpret_cast<Rec*>(cl.rec);
-        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
-            Rec r;
-            load_rec(recs + i, r);
-            const int s = (int)(r.meta & 0xFFu);
-            const DevSpecies& S = C->sp[s];
-            Stream st;
-            st_init(st, rs.seed, 0xFFFFFFFFu, cl.lcell, i, PU_INIT);
-            uint32_t q[4] = {0u, 0u, 0u, 0u};
-            for (int j = 0; j < S.n_modes; ++j) {
-                const int L = S.n_lev[j];
-                const int off = thr_off[s * MAXM + j];
-                bool done = false;
-                for (uint32_t t = 0; t < reject_cap && !done; ++t) {
-                    if (j >= S.n_stretch) {
-                        // bend: i = floor(-ln(u) T / Theta) >= k  <=>  u <= exp(-k Theta / T)
-                        const double u = st_u64(st);
-                        int lv = 0;
-                        while (lv < L && u <= bend_thr[off + lv]) lv++;
-                        if (lv < L) { set_q(q, j, (uint32_t)lv); done = true; }
-                    } else {
-                        const double u1 = st_u64(st);
-                        const int lv = (int)floor(u1 * (double)L);
-                        const double u2 = st_u64(st);
-                        if (u2 < str_acc[off + lv]) { set_q(q, j, (uint32_t)lv); done = true; }
-                    }
+        Rec r;
+        load_rec(recs + i, r);
+        const int s = (int)(r.meta & 0xFFu);
+        const DevSpecies& S = C->sp[s];
+        Stream st;
+        st_init(st, rs.seed, 0xFFFFFFFFu, cl.lcell, i, PU_INIT);
+        uint32_t q[4] = {0u, 0u, 0u, 0u};
+        for (int m = 0; m < S.n_modes; ++m) {
+            const int L = S.n_lev[m];
+            const int to = thr_off[s * MAXM + m];
+            bool done = false;
+            for (uint32_t t = 0; t < reject_cap && !done; ++t) {
+                if (m >= S.n_stretch) {
+                    // bend: i = floor(-ln(u) T / Theta) >= k  <=>  u <= exp(-k Theta / T)
+                    const double u = st_u64(st);
+                    int lv = 0;
+                    while (lv < L && u <= bend_thr[to + lv]) lv++;
+                    if (lv < L) { set_q(q, m, (uint32_t)lv); done = true; }
+                } else {
+                    const double u1 = st_u64(st);
+                    const int lv = (int)floor(u1 * (double)L);
+                    const double u2 = st_u64(st);
+                    if (u2 < str_acc[to + lv]) { set_q(q, m, (uint32_t)lv); done = true; }
                 }
-                if (!done) atomicOr(err, (uint32_t)ERR_REJECT);
             }
-            for (int w = 0; w < 4; ++w) r.q[w] = q[w];
-            store_rec(recs + i, r);
+            if (!done) atomicOr(err, (uint32_t)ERR_REJECT);
         }
+        for (int w = 0; w < 4; ++w) r.q[w] = q[w];
+        store_rec(recs + i, r);
     }
 }
 
 // moments: acc[0..2] momentum, [3] E_tr, [4] E_form, [5 + s] E_vib of species s
 template <class R>
-__global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const Consts* C,
-                          const double* lev64, double* acc, unsigned long long* cnt) {
+__global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                          const Consts* C, const double* lev64, double* acc, unsigned long long* cnt) {
     using Rec = typename RecOf<R>::T;
     __shared__ double sacc[5 + MAXS];
     __shared__ unsigned long long scnt[MAXS];
     for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) sacc[i] = 0.0;
     for (int i = threadIdx.x; i < MAXS; i += blockDim.x) scnt[i] = 0ull;
     __syncthreads();
-    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
-        const DevCell cl = cells[cell0 + c];
-        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
-        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
-            Rec r;
-            load_rec(recs + i, r);
-            const int s = (int)(r.meta & 0xFFu);
-            const DevSpecies& S = C->sp[s];
-            const double m = S.mass;
-            const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
-            atomicAdd(&sacc[0], m * vx);
-            atomicAdd(&sacc[1], m * vy);
-            atomicAdd(&sacc[2], m * vz);
-            atomicAdd(&sacc[3], 0.5 * m * (vx * vx + vy * vy + vz * vz));
-            atomicAdd(&sacc[4], S.E_form);
-            atomicAdd(&sacc[5 + s], evib64(lev64, S, r.q));
-            atomicAdd(&scnt[s], 1ull);
-        }
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        const Rec* recs = reinterpret_cast<const Rec*>(cells[cell0 + c].rec);
+        Rec r;
+        load_rec(recs + (j - off[c]), r);
+        const int s = (int)(r.meta & 0xFFu);
+        const DevSpecies& S = C->sp[s];
+        const double m = S.mass;
+        const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
+        atomicAdd(&sacc[0], m * vx);
+        atomicAdd(&sacc[1], m * vy);
+        atomicAdd(&sacc[2], m * vz);
+        atomicAdd(&sacc[3], 0.5 * m * (vx * vx + vy * vy + vz * vz));
+        atomicAdd(&sacc[4], S.E_form);
+        atomicAdd(&sacc[5 + s], evib64(lev64, S, r.q));
+        atomicAdd(&scnt[s], 1ull);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
@@ -2148,20 +2161,20 @@ __global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const Co
 }
 
 template <class R>
-__global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp, int mode,
-                           unsigned long long* hist) {
+__global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, const uint64_t* off, int sp,
+                           int mode, unsigned long long* hist) {
     using Rec = typename RecOf<R>::T;
     __shared__ unsigned int sh[MAXL];
     for (int i = threadIdx.x; i < MAXL; i += blockDim.x) sh[i] = 0u;
     __syncthreads();
-    for (int c = blockIdx.x; c < n_cells; c += gridDim.x) {
-        const DevCell cl = cells[cell0 + c];
-        const Rec* recs = reinterpret_cast<const Rec*>(cl.rec);
-        for (uint32_t i = threadIdx.x; i < cl.n; i += blockDim.x) {
-            Rec r;
-            load_rec(recs + i, r);
-            if ((int)(r.meta & 0xFFu) == sp) atomicAdd(&sh[get_q(r.q, mode)], 1u);
-        }
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        const Rec* recs = reinterpret_cast<const Rec*>(cells[cell0 + c].rec);
+        Rec r;
+        load_rec(recs + (j - off[c]), r);
+        if ((int)(r.meta & 0xFFu) == sp) atomicAdd(&sh[get_q(r.q, mode)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < MAXL; i += blockDim.x)
@@ -2197,28 +2210,30 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
                                                perm, offsets, slot0, n_cells, v, qn, sp, n);     \
     }                                                                                            \
     template <>                                                                                  \
-    void launch_pack<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* out_off,   \
-                        double* v, uint8_t* qn, int32_t* sp, int32_t* cell, cudaStream_t s) {    \
-        int grid = n_cells < 4096 ? n_cells : 4096;                                              \
-        if (grid < 1) return;                                                                    \
-        k_pack<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, out_off, v, qn, sp, cell);         \
+    void launch_pack<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,       \
+                        uint64_t total, double* v, uint8_t* qn, int32_t* sp, int32_t* cell,      \
+                        cudaStream_t s) {                                                        \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);                \
+        k_pack<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, v, qn, sp, cell);             \
     }                                                                                            \
     template <>                                                                                  \
-    void launch_init_vib<R>(const DevCell* cells, int cell0, int n_cells, const DevRes* res,     \
-                            int rslot, const Consts* C, const double* bt, const double* sa,      \
-                            const int* to, uint32_t cap, uint32_t* err, cudaStream_t s) {        \
-        int grid = n_cells < 4096 ? n_cells : 4096;                                              \
-        if (grid < 1) return;                                                                    \
-        k_init_vib<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, res, rslot, C, bt, sa, to, cap, \
-                                           err);                                                 \
+    void launch_init_vib<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,   \
+                            uint64_t total, const DevRes* res, int rslot, const Consts* C,       \
+                            const double* bt, const double* sa, const int* to, uint32_t cap,     \
+                            uint32_t* err, cudaStream_t s) {                                     \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);                \
+        k_init_vib<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, res, rslot, C, bt, sa, to, \
+                                           cap, err);                                            \
     }                                                                                            \
     template <>                                                                                  \
-    void launch_moments<R>(const DevCell* cells, int cell0, int n_cells, const Consts* C,        \
-                           const double* lev64, double* acc, unsigned long long* cnt,            \
-                           cudaStream_t s) {                                                     \
-        int grid = n_cells < 1184 ? n_cells : 1184;                                              \
-        if (grid < 1) return;                                                                    \
-        k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, C, lev64, acc, cnt);            \
+    void launch_moments<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,    \
+                           uint64_t total, const Consts* C, const double* lev64, double* acc,    \
+                           unsigned long long* cnt, cudaStream_t s) {                            \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 1184 ? total / 256 + 1 : 1184);                \
+        k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, C, lev64, acc, cnt);       \
     }                                                                                            \
     template <>                                                                                  \
     void launch_sample_diag<R>(const StepArgs& a, int sp, double Ec, uint64_t seed, int64_t n,   \
@@ -2230,11 +2245,12 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, int sp,
         k_sample_diag<R><<<grid, 128, 0, s>>>(a, sp, Ec, seed, n, out, trials, status);         \
     }                                                                                            \
     template <>                                                                                  \
-    void launch_levelpop<R>(const DevCell* cells, int cell0, int n_cells, int sp, int mode,      \
-                            unsigned long long* hist, cudaStream_t s) {                          \
-        int grid = n_cells < 1184 ? n_cells : 1184;                                              \
-        if (grid < 1) return;                                                                    \
-        k_levelpop<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, sp, mode, hist);               \
+    void launch_levelpop<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,   \
+                            uint64_t total, int sp, int mode, unsigned long long* hist,          \
+                            cudaStream_t s) {                                                    \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 1184 ? total / 256 + 1 : 1184);                \
+        k_levelpop<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, sp, mode, hist);          \
     }
 
 }  // namespace hcao

@@ -65,3 +65,24 @@ def test_autotune_does_not_change_results():
         vb, qb, _, _ = _state(b, i)
         assert np.array_equal(qa, qb) and np.array_equal(va, vb)
     assert chosen[0] > 0 and chosen[1] > 0
+
+
+def test_remove_all_then_add_again():
+    """Reservoirs come and go (the serving pattern): removing the last one and
+    adding another keeps the context usable and the results unchanged."""
+    bw = _small_batch(n_res=3, steps=4)
+    p = hcao.Context(precision=hcao.FP32)
+    p.set_species(bw.species)
+    results = []
+    for w in bw.reservoirs:
+        rid = p.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        p.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
+        p.init_vibration(rid, w.T_vib0)
+        p.step(bw.steps)
+        results.append(p.read_particles(rid))
+        p.remove_reservoir(rid)
+    g = hcao.from_batched(bw, precision=hcao.FP32)
+    g.step(bw.steps)
+    for i, (v, q, s, c) in enumerate(results):
+        v2, q2, s2, c2 = g.read_particles(i)
+        assert np.array_equal(q, q2) and np.array_equal(v, v2)
