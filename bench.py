@@ -213,7 +213,7 @@ def run_batched(hcao, torch, prec, stream, n_res: int, steps: int):
     10k-2M, T uniform 5000-30000 K, triatomic or CH4-like): all in one context
     and one CUDA-graph launch per step (launch shapes autotuned during the
     first steps), against the plain per-job loop (one reservoir at a time in
-    the same context, one launch sequence per step).  A job = load + init +
+    the same context, one CUDA-graph launch per step).  A job = load + init +
     `steps` collision phases + moments read back; results are identical either
     way (tests/test_gpu_batched.py)."""
     bw = W.batched_reservoirs(n_res=n_res, steps=steps)
@@ -250,8 +250,7 @@ def run_batched(hcao, torch, prec, stream, n_res: int, steps: int):
         p.init_vibration(rid, w.T_vib0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(steps):
-            p.step(1)
+        p.step(steps)  # one CUDA-graph launch per step
         b.record(stream)
         p.sync()
         dev_p += a.elapsed_time(b) / 1e3
@@ -267,6 +266,81 @@ def run_batched(hcao, torch, prec, stream, n_res: int, steps: int):
             "batched_load_s": t_load, "autotuned_grids": chosen,
             "note": "jobs/s include load, init, stepping and the moments read back; the "
                     "device rates time the stepping only"}
+
+
+def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool):
+    """Serving: Poisson-arriving reservoir jobs (rate 1/s, sizes log-uniform
+    10k-4M particles, 200-2000 steps, relaxation / heat-bath / CH4-CH3-H
+    equilibrium kinds) submitted to the library's continuous-batching engine
+    at their arrival times, against the plain loop: one job at a time, first
+    come first served (load, init, step(n) as one CUDA-graph launch per step,
+    moments read back).  Latency = completion - arrival."""
+    sw = W.served_jobs(n_jobs=n_jobs, rate=rate, recombination=recombination)
+    jobs = sw.jobs
+
+    def stats(lat):
+        lat = np.sort(np.asarray(lat))
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+    ctx = hcao.Context(precision=prec, stream=stream.cuda_stream)
+    ctx.set_species(sw.species)
+    ctx.set_reactions(sw.reactions)
+    ctx.serve_start()
+    t0 = time.monotonic()
+    ids = []
+    for j in jobs:
+        d = t0 + j.arrival - time.monotonic()
+        if d > 0:
+            time.sleep(d)
+        ids.append(ctx.serve_submit(j.workload, j.steps))
+    res = {}
+    while len(res) < len(ids):
+        for jid in ids:
+            if jid not in res:
+                r = ctx.serve_poll(jid)
+                if r is not None:
+                    res[jid] = r
+        time.sleep(0.001)
+    _, _, _, iters = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    lat_s = [res[jid].t_done - (t0 + j.arrival) for jid, j in zip(ids, jobs)]
+    span_s = max(res[jid].t_done for jid in ids) - t0
+    queue_s = [res[jid].t_admit - res[jid].t_submit for jid in ids]
+
+    p = hcao.Context(precision=prec, stream=stream.cuda_stream)
+    p.set_species(sw.species)
+    p.set_reactions(sw.reactions)
+    t0 = time.monotonic()
+    lat_p = []
+    for j in jobs:
+        d = t0 + j.arrival - time.monotonic()
+        if d > 0:
+            time.sleep(d)
+        w = j.workload
+        rid = p.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        p.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
+        p.init_vibration(rid, w.T_vib0)
+        p.step(j.steps)
+        p.read_moments(rid)
+        p.remove_reservoir(rid)
+        lat_p.append(time.monotonic() - (t0 + j.arrival))
+    span_p = time.monotonic() - t0
+    p.close()
+    return {"workload": f"{n_jobs} jobs, Poisson arrivals at {rate:g}/s, "
+                        f"{sum(j.workload.n for j in jobs)} particles, {sw.particle_steps:.3e} particle-steps",
+            "kinds": {k: sum(1 for j in jobs if j.kind == k) for k in ("relax", "bath", "equil")},
+            "recombination": recombination,
+            "served_jobs_per_s": n_jobs / span_s, "plain_jobs_per_s": n_jobs / span_p,
+            "jobs_speedup": span_p / span_s,
+            "served_latency": stats(lat_s), "plain_latency": stats(lat_p),
+            "served_queue_wait": stats(queue_s),
+            "served_particle_steps_per_s": sw.particle_steps / span_s,
+            "plain_particle_steps_per_s": sw.particle_steps / span_p,
+            "engine_iterations": int(iters),
+            "note": "jobs/s over the span from the first arrival to the last completion; the "
+                    "plain loop serves the same arrivals first come first served"}
 
 
 def run_reference(args):
@@ -298,6 +372,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--batched-res", type=int, default=256, help="reservoirs of the batched run (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=12)
+    ap.add_argument("--served-jobs", type=int, default=48, help="jobs of the served run (0: skip)")
+    ap.add_argument("--served-rate", type=float, default=50.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -426,6 +502,9 @@ def main():
     if args.batched_res > 0 and ws == 1:
         ctx.close()
         batched = run_batched(hcao, torch, prec, stream, args.batched_res, args.batched_steps)
+    served = None
+    if args.served_jobs > 0 and ws == 1:
+        served = run_served(hcao, prec, stream, args.served_jobs, args.served_rate, recombination=False)
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
@@ -443,7 +522,7 @@ def main():
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched,
+            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served,
         }
         print(json.dumps(line))
     if ws > 1:

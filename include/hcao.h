@@ -257,6 +257,58 @@ hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen);
    = 4.  Zero in FP64 mode.  (Instrumentation for the ALU roofline.) */
 hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* host_out, int max, int* n_out);
 
+/* ---------------------------------------------------------------- serving
+   Continuous batching of 0D reservoir jobs (no counterpart in the paper: the
+   serving form of the collision phase).  hcao_serve_start starts an engine
+   thread on a context that has species/reactions but no reservoir.  Jobs
+   submitted from any thread are admitted, between engine iterations, while
+   their estimated HBM (particle slots, per-pair buffers, staging) fits the
+   budget and fewer than max_active are resident.  A job larger than the
+   budget runs alone.  Every iteration advances all resident jobs together by
+   K steps, K the fewest steps any of them still needs (<= max_batch_steps).
+   Finished jobs are read back and their memory freed.  Each job's results
+   equal those of the same reservoir stepped alone: its draws are keyed by its
+   own seed, cells and step count.  While serving, only the serve_* functions
+   may be called on the context. */
+typedef struct {
+    int n_cells;
+    double cell_volume, weight, dt;  /* as hcao_add_reservoir */
+    uint64_t seed;
+    double T_sgmax;
+    int64_t n;                       /* particles; host arrays as hcao_load_particles */
+    const double* v;
+    const uint8_t* qn;               /* NULL = all ground state */
+    const int32_t* species;
+    const int32_t* cell;
+    double T_vib;                    /* > 0: initial quantum numbers drawn at T_vib */
+    int n_steps;
+} hcao_job;
+
+typedef struct {
+    int status;                      /* hcao_status of the job */
+    int steps;
+    int64_t n_particles;             /* at the end */
+    hcao_moments moments;            /* at the end */
+    uint64_t counters[8 + HCAO_MAX_REACTIONS];  /* as hcao_read_counters */
+    double t_submit, t_admit, t_done;           /* CLOCK_MONOTONIC, s */
+} hcao_job_result;
+
+/* hbm_budget_bytes <= 0: 80% of the free device memory; max_active <= 0: 256;
+   max_batch_steps <= 0: 8.  HCAO_EBUSY if already serving. */
+hcao_status hcao_serve_start(hcao_ctx* ctx, int64_t hbm_budget_bytes, int max_active,
+                             int max_batch_steps);
+/* Copies the job's host arrays; *job_id identifies it.  Thread-safe. */
+hcao_status hcao_serve_submit(hcao_ctx* ctx, const hcao_job* job, uint64_t* job_id);
+/* HCAO_EBUSY while queued or running; otherwise fills *out, releases the job
+   and returns its status (HCAO_ENOTFOUND for an unknown or released id).
+   Thread-safe. */
+hcao_status hcao_serve_poll(hcao_ctx* ctx, uint64_t job_id, hcao_job_result* out);
+/* Finishes the queued and resident jobs, then stops the engine thread. */
+hcao_status hcao_serve_stop(hcao_ctx* ctx);
+/* Queue length, resident jobs, budgeted bytes in use, engine iterations. */
+hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, int64_t* used_bytes,
+                             uint64_t* iterations);
+
 /* Number of this library's kernels launched since create (instrumentation). */
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx);
 

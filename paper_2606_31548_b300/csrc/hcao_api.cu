@@ -6,10 +6,18 @@
 // contraction (-ffp-contract=off) in the operation order documented beside
 // each formula.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <ctime>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hcao_internal.h"
@@ -44,6 +52,26 @@ struct Reservoir {
     size_t rec_bytes = 0;
     uint64_t total_cap = 0;
 };
+
+// one served job: its copied inputs, state and result
+struct Job {
+    uint64_t id = 0;
+    hcao_job spec{};
+    std::vector<double> v;
+    std::vector<uint8_t> qn;
+    std::vector<int32_t> sp, cell;
+    int res = -1;          // reservoir while resident
+    int steps_left = 0;
+    int64_t est_bytes = 0;
+    int state = 0;         // 0 queued, 1 resident, 2 done, 3 failed
+    hcao_job_result result{};
+};
+
+double now_s() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
 
 }  // namespace
 
@@ -90,6 +118,19 @@ struct hcao_ctx {
     cudaGraphExec_t graph = nullptr;
     StepArgs graph_args{};
     bool use_graph = true;
+    // serving engine: thread-safe queue in, results out; the engine thread is
+    // the only caller of the context's other functions while it runs
+    std::mutex serve_mu;
+    std::condition_variable serve_cv;
+    std::deque<std::shared_ptr<Job>> serve_queue;
+    std::vector<std::shared_ptr<Job>> serve_active;
+    std::map<uint64_t, std::shared_ptr<Job>> serve_jobs;
+    std::thread serve_thread;
+    bool serve_running = false, serve_stop = false;
+    uint64_t serve_next_id = 1;
+    int64_t serve_budget = 0, serve_used = 0;
+    int serve_max_active = 256, serve_max_batch_steps = 64;
+    uint64_t serve_iterations = 0;
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint32_t* d_err = nullptr;
@@ -111,6 +152,14 @@ hcao_status fail(hcao_ctx* c, hcao_status s, const std::string& m) {
     if (c) c->err = m;
     return s;
 }
+
+// set on the serving engine thread: while a context serves, its state-changing
+// entry points are refused on every other thread
+thread_local bool tl_serve_engine = false;
+#define SERVE_GUARD(ctx)                                                  \
+    do {                                                                  \
+        if ((ctx) && (ctx)->serve_running && !tl_serve_engine) return HCAO_EBUSY; \
+    } while (0)
 #define CU(call)                                                                           \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -577,6 +626,7 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
 
 void hcao_destroy(hcao_ctx* ctx) {
     if (!ctx) return;
+    hcao_serve_stop(ctx);
     cudaStreamSynchronize(ctx->stream);
     for (auto& r : ctx->res)
         if (r.recs) cudaFreeAsync(r.recs, ctx->stream);
@@ -816,6 +866,7 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
 
 hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, double weight, double dt,
                                uint64_t seed, double T_sgmax, int* id) {
+    SERVE_GUARD(ctx);
     if (!ctx || n_cells < 1 || !(cell_volume > 0) || !(weight > 0) || !(dt > 0) || !(T_sgmax > 0) || !id)
         return fail(ctx, HCAO_EINVAL, "add_reservoir: bad arguments");
     if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "add_reservoir: species first");
@@ -833,6 +884,7 @@ hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, d
 }
 
 hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int id) {
+    SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "remove_reservoir: no such reservoir");
@@ -863,6 +915,7 @@ hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint3
 
 hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* v, const uint8_t* qn,
                                 const int32_t* species, const int32_t* cell) {
+    SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "load_particles: no such reservoir");
@@ -967,6 +1020,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
 }
 
 hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
+    SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "init_vibration: no loaded reservoir");
@@ -1057,6 +1111,7 @@ hcao_status hcao_set_log(hcao_ctx* ctx, int enable) {
 }
 
 hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
+    SERVE_GUARD(ctx);
     if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
     if (ctx->n_cells_total == 0 || n_steps == 0) return HCAO_OK;
     if (ctx->log_on && !ctx->d_log) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
@@ -1423,4 +1478,204 @@ hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out) {
     return HCAO_OK;
 }
 
+
 }  // extern "C"
+
+// ===================================================================== serving
+// Continuous batching: queued jobs are admitted between engine iterations as
+// the HBM budget and the resident-job limit allow; every iteration advances
+// all resident jobs together by K steps (one graph launch per step), K the
+// fewest steps any resident job still needs (capped); finished jobs are read
+// back and their reservoirs freed.
+
+static int64_t job_bytes(const hcao_ctx* ctx, const hcao_job& j) {
+    const double f = ctx->cfg.capacity_factor;
+    const int64_t cap = (int64_t)std::ceil((double)j.n * f) + (int64_t)ctx->cfg.capacity_extra * j.n_cells +
+                        8 * (int64_t)j.n_cells;
+    const int64_t rec = ctx->cfg.precision == HCAO_FP64 ? 64 : 32;
+    const int64_t pair = (int64_t)ctx->cfg.max_rounds * (cap / 2 + j.n_cells) * (4 + 16 + 16 + rec);
+    return cap * rec + pair + (int64_t)j.n_cells * (int64_t)(sizeof(DevCell) + 8 * NCNT) +
+           j.n * 48;  // staging of the host arrays during the load
+}
+
+static void serve_fail(hcao_ctx* ctx, const std::shared_ptr<Job>& jb, int status) {
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    jb->state = 3;
+    jb->result.status = status;
+    jb->result.t_done = now_s();
+}
+
+static void serve_loop(hcao_ctx* ctx) {
+    tl_serve_engine = true;
+    for (;;) {
+        // ---- admission
+        std::vector<std::shared_ptr<Job>> admit;
+        {
+            std::unique_lock<std::mutex> lock(ctx->serve_mu);
+            if (ctx->serve_active.empty() && ctx->serve_queue.empty()) {
+                if (ctx->serve_stop) return;
+                ctx->serve_cv.wait_for(lock, std::chrono::milliseconds(20));
+                continue;
+            }
+            while (!ctx->serve_queue.empty() && (int)ctx->serve_active.size() + (int)admit.size() < ctx->serve_max_active) {
+                auto& jb = ctx->serve_queue.front();
+                if (ctx->serve_used + jb->est_bytes > ctx->serve_budget && !(ctx->serve_active.empty() && admit.empty()))
+                    break;  // wait for memory (a job larger than the budget runs alone)
+                ctx->serve_used += jb->est_bytes;
+                admit.push_back(jb);
+                ctx->serve_queue.pop_front();
+            }
+        }
+        for (auto& jb : admit) {
+            const hcao_job& j = jb->spec;
+            int rid = -1;
+            hcao_status st = hcao_add_reservoir(ctx, j.n_cells, j.cell_volume, j.weight, j.dt, j.seed, j.T_sgmax, &rid);
+            if (st == HCAO_OK)
+                st = hcao_load_particles(ctx, rid, j.n, jb->v.data(), jb->qn.data(), jb->sp.data(), jb->cell.data());
+            if (st == HCAO_OK && j.T_vib > 0) st = hcao_init_vibration(ctx, rid, j.T_vib);
+            if (st != HCAO_OK) {
+                if (rid >= 0) hcao_remove_reservoir(ctx, rid);
+                {
+                    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+                    ctx->serve_used -= jb->est_bytes;
+                }
+                serve_fail(ctx, jb, st);
+                continue;
+            }
+            jb->v.clear(); jb->v.shrink_to_fit();
+            jb->qn.clear(); jb->qn.shrink_to_fit();
+            jb->sp.clear(); jb->sp.shrink_to_fit();
+            jb->cell.clear(); jb->cell.shrink_to_fit();
+            jb->res = rid;
+            jb->steps_left = j.n_steps;
+            std::lock_guard<std::mutex> lock(ctx->serve_mu);
+            jb->state = 1;
+            jb->result.t_admit = now_s();
+            ctx->serve_active.push_back(jb);
+        }
+        if (ctx->serve_active.empty()) continue;
+        // ---- one engine iteration: every resident job advances K steps
+        int K = ctx->serve_max_batch_steps;
+        for (auto& jb : ctx->serve_active) K = std::min(K, jb->steps_left);
+        if (K > 0) {
+            hcao_status st = hcao_step(ctx, K);
+            if (st == HCAO_OK) st = hcao_sync(ctx);
+            if (st != HCAO_OK) {  // a device error fails every resident job
+                for (auto& jb : ctx->serve_active) {
+                    hcao_remove_reservoir(ctx, jb->res);
+                    serve_fail(ctx, jb, st);
+                }
+                std::lock_guard<std::mutex> lock(ctx->serve_mu);
+                for (auto& jb : ctx->serve_active) ctx->serve_used -= jb->est_bytes;
+                ctx->serve_active.clear();
+                continue;
+            }
+            for (auto& jb : ctx->serve_active) jb->steps_left -= K;
+            ctx->serve_iterations++;
+        }
+        // ---- retirement
+        std::vector<std::shared_ptr<Job>> keep;
+        for (auto& jb : ctx->serve_active) {
+            if (jb->steps_left > 0) { keep.push_back(jb); continue; }
+            hcao_job_result r = jb->result;
+            hcao_status st = hcao_read_moments(ctx, jb->res, &r.moments);
+            int got = 0;
+            if (st == HCAO_OK) st = hcao_read_counters(ctx, jb->res, r.counters, 8 + MAXR, &got);
+            if (st == HCAO_OK) st = hcao_count(ctx, jb->res, &r.n_particles);
+            hcao_remove_reservoir(ctx, jb->res);
+            std::lock_guard<std::mutex> lock(ctx->serve_mu);
+            ctx->serve_used -= jb->est_bytes;
+            r.status = st;
+            r.steps = jb->spec.n_steps;
+            r.t_done = now_s();
+            jb->result = r;
+            jb->state = st == HCAO_OK ? 2 : 3;
+        }
+        ctx->serve_active.swap(keep);
+    }
+}
+
+extern "C" {
+
+hcao_status hcao_serve_start(hcao_ctx* ctx, int64_t hbm_budget_bytes, int max_active, int max_batch_steps) {
+    if (!ctx || max_active < 0 || max_batch_steps < 0) return HCAO_EINVAL;
+    if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "serve_start: species first");
+    if (ctx->serve_running) return fail(ctx, HCAO_EBUSY, "serve_start: already serving");
+    for (auto& r : ctx->res)
+        if (r.live) return fail(ctx, HCAO_EINVAL, "serve_start: the context must hold no reservoir");
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    ctx->serve_budget = hbm_budget_bytes > 0 ? hbm_budget_bytes : (int64_t)(0.8 * (double)free_b);
+    ctx->serve_max_active = max_active > 0 ? max_active : 256;
+    ctx->serve_max_batch_steps = max_batch_steps > 0 ? max_batch_steps : 8;
+    ctx->serve_used = 0;
+    ctx->serve_stop = false;
+    ctx->serve_running = true;
+    ctx->serve_thread = std::thread(serve_loop, ctx);
+    return HCAO_OK;
+}
+
+hcao_status hcao_serve_submit(hcao_ctx* ctx, const hcao_job* job, uint64_t* job_id) {
+    if (!ctx || !job || !job_id || job->n < 0 || job->n_cells < 1 || job->n_steps < 0 ||
+        (job->n > 0 && (!job->v || !job->species || !job->cell)))
+        return HCAO_EINVAL;
+    if (!ctx->serve_running) return HCAO_EINVAL;
+    auto jb = std::make_shared<Job>();
+    jb->result.t_submit = now_s();
+    jb->spec = *job;
+    const size_t n = (size_t)job->n;
+    jb->v.assign(job->v, job->v + 3 * n);
+    if (job->qn) jb->qn.assign(job->qn, job->qn + 16 * n);
+    else jb->qn.assign(16 * n, 0);
+    jb->sp.assign(job->species, job->species + n);
+    jb->cell.assign(job->cell, job->cell + n);
+    jb->spec.v = nullptr; jb->spec.qn = nullptr; jb->spec.species = nullptr; jb->spec.cell = nullptr;
+    jb->est_bytes = job_bytes(ctx, *job);
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    jb->id = ctx->serve_next_id++;
+    ctx->serve_jobs[jb->id] = jb;
+    ctx->serve_queue.push_back(jb);
+    ctx->serve_cv.notify_one();
+    *job_id = jb->id;
+    return HCAO_OK;
+}
+
+hcao_status hcao_serve_poll(hcao_ctx* ctx, uint64_t job_id, hcao_job_result* out) {
+    if (!ctx || !out) return HCAO_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    auto it = ctx->serve_jobs.find(job_id);
+    if (it == ctx->serve_jobs.end()) return HCAO_ENOTFOUND;
+    const auto& jb = it->second;
+    if (jb->state < 2) return HCAO_EBUSY;
+    *out = jb->result;
+    const hcao_status st = (hcao_status)jb->result.status;
+    ctx->serve_jobs.erase(it);
+    return st;
+}
+
+hcao_status hcao_serve_stop(hcao_ctx* ctx) {
+    if (!ctx) return HCAO_EINVAL;
+    if (!ctx->serve_running) return HCAO_OK;
+    {
+        std::lock_guard<std::mutex> lock(ctx->serve_mu);
+        ctx->serve_stop = true;
+        ctx->serve_cv.notify_all();
+    }
+    ctx->serve_thread.join();
+    ctx->serve_running = false;
+    return HCAO_OK;
+}
+
+hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, int64_t* used_bytes,
+                             uint64_t* iterations) {
+    if (!ctx) return HCAO_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    if (queued) *queued = (int64_t)ctx->serve_queue.size();
+    if (active) *active = (int64_t)ctx->serve_active.size();
+    if (used_bytes) *used_bytes = ctx->serve_used;
+    if (iterations) *iterations = ctx->serve_iterations;
+    return HCAO_OK;
+}
+
+}  // extern "C"
+

@@ -30,7 +30,8 @@ EXPORTS = [
     "hcao_read_reaction_counts", "hcao_read_cell_sgmax", "hcao_set_log", "hcao_read_log",
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
-    "hcao_read_work", "hcao_autotune",
+    "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
+    "hcao_serve_stop", "hcao_serve_stats",
 ]
 NOALLOC_SORT_MAX_KEYS = 1 << 19
 
@@ -73,6 +74,19 @@ class Moments(C.Structure):
     _fields_ = [("n", C.c_int64 * 16), ("momentum", C.c_double * 3), ("E_tr", C.c_double),
                 ("E_vib", C.c_double * 16), ("E_form", C.c_double), ("T_tr", C.c_double),
                 ("T_vib", C.c_double * 16)]
+
+
+class Job(C.Structure):
+    _fields_ = [("n_cells", C.c_int), ("cell_volume", C.c_double), ("weight", C.c_double),
+                ("dt", C.c_double), ("seed", C.c_uint64), ("T_sgmax", C.c_double), ("n", C.c_int64),
+                ("v", C.c_void_p), ("qn", C.c_void_p), ("species", C.c_void_p), ("cell", C.c_void_p),
+                ("T_vib", C.c_double), ("n_steps", C.c_int)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps", C.c_int), ("n_particles", C.c_int64),
+                ("moments", Moments), ("counters", C.c_uint64 * 16), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
 
 
 _lib = None
@@ -119,6 +133,11 @@ def lib() -> C.CDLL:
         L.hcao_autotune.argtypes = [vp, i32, vp]
         L.hcao_set_profiling.argtypes = [vp, i32]
         L.hcao_read_profile.argtypes = [vp, vp, vp, i32, C.POINTER(i32)]
+        L.hcao_serve_start.argtypes = [vp, i64, i32, i32]
+        L.hcao_serve_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(u64)]
+        L.hcao_serve_poll.argtypes = [vp, u64, C.POINTER(JobResult)]
+        L.hcao_serve_stop.argtypes = [vp]
+        L.hcao_serve_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(u64)]
         L.hcao_kernel_launches.argtypes = [vp]
         L.hcao_kernel_launches.restype = u64
         _lib = L
@@ -338,6 +357,44 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.hcao_kernel_launches(self.h))
+
+    # -- serving (continuous batching of reservoir jobs)
+    def serve_start(self, hbm_budget_bytes=0, max_active=0, max_batch_steps=0) -> None:
+        self._chk(self.L.hcao_serve_start(self.h, int(hbm_budget_bytes), max_active, max_batch_steps))
+
+    def serve_submit(self, w, n_steps, T_vib=None) -> int:
+        """Queue a reservoir job built from a workload; returns its id.  The
+        host arrays are copied by the library before this returns."""
+        v = np.ascontiguousarray(w.v, dtype=np.float64)
+        qn = np.ascontiguousarray(w.qn0(), dtype=np.uint8)
+        sp = np.ascontiguousarray(w.species_idx, dtype=np.int32)
+        cell = np.ascontiguousarray(w.cell, dtype=np.int32)
+        j = Job(n_cells=w.n_cells, cell_volume=w.cell_volume, weight=w.weight, dt=w.dt, seed=w.seed,
+                T_sgmax=w.T_tr0, n=v.shape[0], v=_p(v), qn=_p(qn), species=_p(sp), cell=_p(cell),
+                T_vib=w.T_vib0 if T_vib is None else T_vib, n_steps=n_steps)
+        jid = C.c_uint64()
+        self._chk(self.L.hcao_serve_submit(self.h, C.byref(j), C.byref(jid)))
+        return jid.value
+
+    def serve_poll(self, job_id):
+        """None while the job is queued or running, else its JobResult
+        (raises on a failed job)."""
+        r = JobResult()
+        st = self.L.hcao_serve_poll(self.h, job_id, C.byref(r))
+        if st == -6:
+            return None
+        if st != 0:
+            raise HcaoError(st, f"serving job {job_id} failed")
+        return r
+
+    def serve_stop(self) -> None:
+        self._chk(self.L.hcao_serve_stop(self.h))
+
+    def serve_stats(self):
+        """(queued, resident, budgeted bytes in use, engine iterations)."""
+        q, a, b, it = C.c_int64(), C.c_int64(), C.c_int64(), C.c_uint64()
+        self._chk(self.L.hcao_serve_stats(self.h, C.byref(q), C.byref(a), C.byref(b), C.byref(it)))
+        return q.value, a.value, b.value, it.value
 
 
 def from_batched(bw, precision=FP64, init_vib=True, **kw) -> Context:

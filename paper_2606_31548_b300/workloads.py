@@ -233,3 +233,70 @@ def batched_reservoirs(n_res: int = 256, n_min: int = 10_000, n_max: int = 2_000
         r.v = np.ascontiguousarray(maxwellian(np.random.default_rng(seed + 100000 + i), n, mass, T))
         out.append(r)
     return BatchedWorkload("batched_reservoirs", species, [], out, steps)
+
+
+@dataclasses.dataclass
+class ServedJob:
+    arrival: float       # s after the first arrival
+    kind: str
+    workload: Workload
+    steps: int
+
+
+@dataclasses.dataclass
+class ServedWorkload:
+    """Poisson-arriving single-cell reservoir jobs sharing one species and
+    reaction table (the serving engine's input)."""
+    name: str
+    species: List[Species]
+    reactions: List[Reaction]
+    jobs: List[ServedJob]
+
+    @property
+    def particle_steps(self) -> int:
+        return int(sum(j.workload.n * j.steps for j in self.jobs))
+
+
+def served_jobs(n_jobs: int = 48, rate: float = 50.0, n_min: int = 10_000, n_max: int = 4_000_000,
+                steps_min: int = 200, steps_max: int = 2000, recombination: bool = False,
+                seed: int = 0x48434135) -> ServedWorkload:
+    """Reservoir jobs arriving as a Poisson process of the given rate (1/s):
+    particle counts log-uniform in [n_min, n_max], step counts uniform in
+    [steps_min, steps_max], one cell of V = 4.64e-6 m^3 each.  Species table
+    [triatomic, CH4-like, CH3-like, H]; reactions CH4 + M -> CH3 + H + M
+    (+ its recombination if asked).  Job kinds, 1/3 each:
+      relax  -- triatomic, n = 1e23 m^-3, T_tr0 uniform 5000-30000 K, T_vib0 = 300 K;
+      bath   -- CH4-like heat bath, n = 1e23 m^-3, T_tr0 = T_vib0 uniform 6000-10000 K;
+      equil  -- CH4 : CH3 : H = 1 : 1 : 1 at n = 1e23 m^-3 each, T_tr0 = T_vib0 = 4000 K.
+    dt = 0.2 / nu(T0) of the job's first species at the job's total density."""
+    rng = np.random.default_rng(seed)
+    species = [triatomic(), ch4_like(), ch3_like(), h_atom()]
+    rx = [Reaction("diss", [1], [2, 3], diss_mode_mask=0xF)]
+    if recombination:
+        rx.append(Reaction("recomb", [2, 3], [1, -1]))
+    t = 0.0
+    jobs = []
+    for i in range(n_jobs):
+        if i:
+            t += float(rng.exponential(1.0 / rate))
+        n = int(round(np.exp(rng.uniform(np.log(n_min), np.log(n_max)))))
+        steps = int(rng.integers(steps_min, steps_max + 1))
+        kind = ("relax", "bath", "equil")[int(rng.integers(0, 3))]
+        js = seed + 1 + i
+        if kind == "relax":
+            T = float(rng.uniform(5000.0, 30000.0))
+            dt = 0.2 / vhs_collision_frequency(species[0], 1e23, T)
+            w = _build(f"job{i}", species, rx, 1, np.array([n]), [1.0], 4.64e-6, 1e23, dt, T, 300.0,
+                       js, steps, shuffle=False)
+        elif kind == "bath":
+            T = float(rng.uniform(6000.0, 10000.0))
+            dt = 0.2 / vhs_collision_frequency(species[1], 1e23, T)
+            w = _build(f"job{i}", species, rx, 1, np.array([n]), [0.0, 1.0], 4.64e-6, 1e23, dt, T, T,
+                       js, steps, shuffle=False)
+        else:
+            T = 4000.0
+            dt = 0.2 / vhs_collision_frequency(species[1], 3e23, T)
+            w = _build(f"job{i}", species, rx, 1, np.array([n]), [0.0, 1.0, 1.0, 1.0], 4.64e-6, 3e23,
+                       dt, T, T, js, steps, shuffle=False)
+        jobs.append(ServedJob(t, kind, w, steps))
+    return ServedWorkload("served_jobs", species, rx, jobs)
