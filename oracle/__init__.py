@@ -94,6 +94,15 @@ def lib():
         L.ora_tvib.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.ora_mean_sigma_g.restype = C.c_double
         L.ora_mean_sigma_g.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double]
+        for name, args in (("ora_diss_prob", [C.c_void_p, C.c_int, C.c_double]),
+                           ("ora_keq", [C.c_void_p, C.c_int, C.c_double]),
+                           ("ora_rec_rate_node", [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+                           ("ora_rec_rate", [C.c_void_p, C.c_int, C.c_int, C.c_double]),
+                           ("ora_cell_temperature", [C.c_void_p, C.c_int, C.c_int]),
+                           ("ora_rec_node_T", [C.c_int]),
+                           ("ora_gamma_q", [C.c_double, C.c_double])):
+            getattr(L, name).restype = C.c_double
+            getattr(L, name).argtypes = args
         L.ora_last_error.restype = C.c_char_p
         L.ora_last_error.argtypes = [C.c_void_p]
     return _lib
@@ -154,7 +163,7 @@ class Oracle:
 
     def add_reaction(self, r) -> int:
         d = _Reaction()
-        d.type = 1 if r.type == "diss" else 2
+        d.type = {"diss": 1, "exch": 2, "recomb": 3}[r.type]
         rc = list(r.reactants) + [-1] * (2 - len(r.reactants))
         d.reactants[0], d.reactants[1] = rc[0], rc[1]
         d.products[0], d.products[1] = r.products[0], r.products[1]
@@ -247,6 +256,36 @@ class Oracle:
 
     def mean_sigma_g(self, a, b, T) -> float:
         return float(self.L.ora_mean_sigma_g(self.ctx, a, b, T))
+
+    # -- recombination (reading A14)
+    def diss_prob(self, rx, T) -> float:
+        """Thermal dissociation probability per collision of recombination rx's molecule."""
+        return float(self.L.ora_diss_prob(self.ctx, rx, T))
+
+    def keq(self, rx, T) -> float:
+        """Equilibrium constant n_B n_C / n_A (m^-3) of recombination rx."""
+        return float(self.L.ora_keq(self.ctx, rx, T))
+
+    def rec_rate(self, rx, spM, T) -> float:
+        """Tabulated k_r (m^6/s), interpolated at T."""
+        return float(self.L.ora_rec_rate(self.ctx, rx, spM, T))
+
+    def rec_rate_node(self, rx, spM, i) -> float:
+        return float(self.L.ora_rec_rate_node(self.ctx, rx, spM, i))
+
+    def cell_temperature(self, res, cell) -> float:
+        return float(self.L.ora_cell_temperature(self.ctx, res, cell))
+
+
+REC_NODES = 225
+
+
+def rec_node_T(i: int) -> float:
+    return float(lib().ora_rec_node_T(i))
+
+
+def gamma_q(a: float, x: float) -> float:
+    return float(lib().ora_gamma_q(a, x))
 
 
 def from_workload(w, table_points=2048, table_span_J=64 * 1.602176634e-19, log=False,

@@ -40,7 +40,7 @@
 
 /* Philox stream purposes (counter word 3 = purpose << 24 | block). */
 enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7, PU_TEST = 8 };
+       PU_INIT = 7, PU_TEST = 8, PU_REC = 9 };
 
 #define MAX_SPECIES 16
 #define MAX_REACTIONS 32
@@ -101,6 +101,10 @@ struct ora_ctx {
     int64_t log_n, log_cap;
     int error;
     char msg[256];
+    /* recombination: thermal dissociation probability of A at the rate-table
+       nodes, computed when first needed */
+    double rec_P[MAX_REACTIONS][ORA_REC_NODES];
+    unsigned char rec_P_done[MAX_REACTIONS][ORA_REC_NODES];
 };
 
 static void set_err(ora_ctx* c, int code, const char* m) {
@@ -455,6 +459,176 @@ double ora_mean_sigma_g(ora_ctx* c, int a, int b, double T) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Recombination B + C + M -> A + M (Sec. "Recombination reactions").
+   The rate coefficient is k_r = k_f / K_eq.  k_f is the forward (dissociation)
+   rate of the paper's expression, P times the VHS collision-rate coefficient
+   of A and M; P is the thermal average, over every vibrational level
+   combination of A, of the probability that the collision-weighted VHS
+   translational energy exceeds what the state lacks of the dissociation
+   threshold (Eq. recomb-correct), with Gamma_inc the regularised upper
+   incomplete gamma Q(5/2 - omega, .) (reading A16).  Readings (A14):
+     - the threshold is the one the QK test applies, D = min over the
+       breaking stretches j of (D_e,j + ZPE_A + ZPE_B + ZPE_C - E_j(0)), so
+       that k_f is the rate the simulated dissociation produces;
+     - the collision-rate factor is <sigma_T g>_{A,M}(T) for every M (no 1/2
+       for M = A: either partner of an A-A pair may dissociate);
+     - K_eq = n_B n_C / n_A from translational and HCAO vibrational
+       partition sums (level sums over the tabulated levels, no rotation);
+     - k_r is tabulated at T_i = 500 K * 2^(i/32) and interpolated linearly
+       in T (clamped at the ends). */
+
+double ora_rec_node_T(int i) { return 500.0 * pow(2.0, (double)i / 32.0); }
+
+/* Q(a, x) = Gamma(a, x) / Gamma(a): for x < a + 1 as 1 - P(a, x) with the
+   power series of P (Abramowitz & Stegun 6.5.29), otherwise the Legendre
+   continued fraction of Q (A&S 6.5.31) evaluated by the modified Lentz
+   method. */
+double ora_gamma_q(double a, double x) {
+    if (!(x > 0.0)) return 1.0;
+    double lpre = a * log(x) - x - lgamma(a);
+    if (x < a + 1.0) {
+        double term = 1.0 / a, sum = term, an = a;
+        for (int n = 1; n < 10000; ++n) {
+            an += 1.0;
+            term *= x / an;
+            sum += term;
+            if (fabs(term) < fabs(sum) * 1e-17) break;
+        }
+        return 1.0 - sum * exp(lpre);
+    }
+    const double tiny = 1e-300;
+    double b = x + 1.0 - a;
+    double C = 1.0 / tiny, D = 1.0 / b, h = D;
+    for (int i = 1; i < 10000; ++i) {
+        double an = -(double)i * ((double)i - a);
+        b += 2.0;
+        D = an * D + b;
+        if (fabs(D) < tiny) D = tiny;
+        C = b + an / C;
+        if (fabs(C) < tiny) C = tiny;
+        D = 1.0 / D;
+        double del = D * C;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-17) break;
+    }
+    return exp(lpre) * h;
+}
+
+/* The recombination's molecule A and its QK dissociation threshold. */
+static double rec_threshold(const ora_ctx* c, int rx) {
+    const ora_reaction_desc* r = &c->rx[rx];
+    const o_species* sA = &c->sp[r->products[0]];
+    double D = INFINITY;
+    for (int j = 0; j < sA->d.n_stretch; ++j) {
+        if (!((r->diss_mode_mask >> j) & 1u)) continue;
+        double Dj = (sA->d.De[j] + c->rx_zpesum[rx]) - sA->E[j][0];
+        if (Dj < D) D = Dj;
+    }
+    return D;
+}
+
+/* Sum over the level combinations of modes k..n-1 given the excitation X of
+   modes 0..k-1 (excitations x = E - E(0), so the ground state has X = 0):
+   states below the threshold Dx contribute exp(-X/kT) Q(a, (Dx - X)/kT);
+   every completion at or above it contributes exp(-X/kT), and once X >= Dx
+   those completions are summed at once as exp(-X/kT) times the partition
+   sums of the remaining modes (zr[k]); within a mode the levels increase,
+   so the first level that reaches Dx starts a suffix summed by zs. */
+typedef struct {
+    const o_species* s;
+    double kT, a, Dx;
+    double zr[ORA_MAX_MODES + 1];        /* prod_{j >= k} sum_i exp(-x_ji / kT) */
+    double zs[ORA_MAX_MODES][ORA_MAX_LEVELS + 1];  /* suffix sums per mode */
+} o_penum;
+
+static double penum(const o_penum* pe, int k, double X) {
+    const o_species* s = pe->s;
+    if (k == s->n_modes) return exp(-X / pe->kT) * ora_gamma_q(pe->a, (pe->Dx - X) / pe->kT);
+    double sum = 0.0;
+    for (int i = 0; i < s->n_levels[k]; ++i) {
+        double Xi = X + (s->E[k][i] - s->E[k][0]);
+        if (!(Xi < pe->Dx)) {
+            sum += exp(-X / pe->kT) * pe->zs[k][i] * pe->zr[k + 1];
+            break;
+        }
+        sum += penum(pe, k + 1, Xi);
+    }
+    return sum;
+}
+
+double ora_diss_prob(ora_ctx* c, int rx, double T) {
+    const o_species* s = &c->sp[c->rx[rx].products[0]];
+    o_penum* pe = (o_penum*)malloc(sizeof(o_penum));
+    pe->s = s;
+    pe->kT = KB * T;
+    pe->a = 2.5 - c->omega;
+    pe->Dx = rec_threshold(c, rx) - s->zpe;
+    int n = s->n_modes;
+    pe->zr[n] = 1.0;
+    for (int k = n - 1; k >= 0; --k) {
+        double acc = 0.0;
+        pe->zs[k][s->n_levels[k]] = 0.0;
+        for (int i = s->n_levels[k] - 1; i >= 0; --i) {
+            acc += exp(-(s->E[k][i] - s->E[k][0]) / pe->kT);
+            pe->zs[k][i] = acc;
+        }
+        pe->zr[k] = pe->zr[k + 1] * acc;
+    }
+    double P = penum(pe, 0, 0.0) / pe->zr[0];
+    free(pe);
+    return P;
+}
+
+/* vibrational partition sum with energies measured from the ground state */
+static double zvib_x(const o_species* s, double T) {
+    double z = 1.0;
+    for (int j = 0; j < s->n_modes; ++j) {
+        double m = 0.0;
+        for (int i = 0; i < s->n_levels[j]; ++i) m += exp(-(s->E[j][i] - s->E[j][0]) / (KB * T));
+        z *= m;
+    }
+    return z;
+}
+
+double ora_keq(ora_ctx* c, int rx, double T) {
+    const ora_reaction_desc* r = &c->rx[rx];
+    const o_species* sA = &c->sp[r->products[0]];
+    const o_species* sB = &c->sp[r->reactants[0]];
+    const o_species* sC = &c->sp[r->reactants[1]];
+    /* translational partition functions per unit volume, (2 pi m k T / h^2)^(3/2) */
+    double f = 2.0 * PI_D * KB * T / (HPLANCK * HPLANCK);
+    double qtr = pow(f * sB->d.mass, 1.5) * pow(f * sC->d.mass, 1.5) / pow(f * sA->d.mass, 1.5);
+    /* ground-state energies from the well bottoms, formation energies included */
+    double dE0 = (sB->d.E_form + sB->zpe + sC->d.E_form + sC->zpe) - (sA->d.E_form + sA->zpe);
+    return qtr * (zvib_x(sB, T) * zvib_x(sC, T) / zvib_x(sA, T)) * exp(-dE0 / (KB * T));
+}
+
+double ora_rec_rate_node(ora_ctx* c, int rx, int spM, int i) {
+    double T = ora_rec_node_T(i);
+    if (!c->rec_P_done[rx][i]) {
+        c->rec_P[rx][i] = ora_diss_prob(c, rx, T);
+        c->rec_P_done[rx][i] = 1;
+    }
+    double kf = c->rec_P[rx][i] * ora_mean_sigma_g(c, c->rx[rx].products[0], spM, T);
+    return kf / ora_keq(c, rx, T);
+}
+
+double ora_rec_rate(ora_ctx* c, int rx, int spM, double T) {
+    const int last = ORA_REC_NODES - 1;
+    if (!(T > ora_rec_node_T(0))) return ora_rec_rate_node(c, rx, spM, 0);
+    if (!(T < ora_rec_node_T(last))) return ora_rec_rate_node(c, rx, spM, last);
+    int lo = 0, hi = last; /* T_lo <= T < T_hi */
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (ora_rec_node_T(mid) <= T) lo = mid; else hi = mid;
+    }
+    double T0 = ora_rec_node_T(lo), T1 = ora_rec_node_T(hi);
+    double f = (T - T0) / (T1 - T0);
+    double k0 = ora_rec_rate_node(c, rx, spM, lo), k1 = ora_rec_rate_node(c, rx, spM, hi);
+    return k0 + f * (k1 - k0);
+}
+
+/* ------------------------------------------------------------------ */
 ora_ctx* ora_create(int table_points, double table_span_J, uint32_t reject_cap) {
     ora_ctx* c = (ora_ctx*)calloc(1, sizeof(ora_ctx));
     if (!c) return NULL;
@@ -506,6 +680,14 @@ int ora_add_reaction(ora_ctx* c, const ora_reaction_desc* r) {
         /* Eq. Ecoll-diss: the ZPEs of A, B and C are subtracted */
         c->rx_zpesum[id] = c->sp[r->reactants[0]].zpe + c->sp[r->products[0]].zpe +
                            c->sp[r->products[1]].zpe;
+    } else if (r->type == ORA_RECOMB) {
+        /* the reverse dissociation A + M -> B + C + M sets the threshold of P */
+        int A = r->products[0], B = r->reactants[0], Cc = r->reactants[1];
+        if (A < 0 || A >= c->n_species || B < 0 || B >= c->n_species || Cc < 0 ||
+            Cc >= c->n_species || c->sp[A].d.n_stretch == 0 ||
+            (r->diss_mode_mask & ((1u << c->sp[A].d.n_stretch) - 1u)) == 0u)
+            return ORA_EINVAL;
+        c->rx_zpesum[id] = c->sp[A].zpe + c->sp[B].zpe + c->sp[Cc].zpe;
     } else {
         c->rx_zpesum[id] = 0.0;
     }
@@ -748,6 +930,85 @@ static int do_exch(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* B, double Ev
     return 1;
 }
 
+/* Recombination B + C + M -> A + M (Sec. "Recombination reactions").  B takes
+   A's species; C is removed; the third body M keeps its species and levels.
+   The energy available to A's vibration and the A-M relative motion is the
+   translational energy of B, C and M in their centre-of-mass frame plus the
+   vibrational energies of B and C plus the released formation energy; A's
+   levels are drawn with the LB target at that budget (as for reaction
+   products, reading A13) and the rest goes to A-M relative motion in a
+   uniformly random direction, total momentum kept.  Returns 1 if done. */
+static int do_recomb(ora_ctx* c, o_res* R, int rx, o_part* B, o_part* Cp, o_part* M,
+                     double EvB, double EvC, uint32_t cell, uint32_t rk) {
+    const ora_reaction_desc* r = &c->rx[rx];
+    const o_species* sA = &c->sp[r->products[0]];
+    const o_species* sB = &c->sp[B->sp];
+    const o_species* sC = &c->sp[Cp->sp];
+    const o_species* sM = &c->sp[M->sp];
+    double mA = sA->d.mass, mB = sB->d.mass, mC = sC->d.mass, mM = sM->d.mass;
+    double mt = mA + mM;
+    double P[3], V[3];
+    for (int i = 0; i < 3; ++i) P[i] = (mB * B->v[i] + mC * Cp->v[i]) + mM * M->v[i];
+    for (int i = 0; i < 3; ++i) V[i] = P[i] / mt;
+    double vB2 = B->v[0] * B->v[0] + B->v[1] * B->v[1] + B->v[2] * B->v[2];
+    double vC2 = Cp->v[0] * Cp->v[0] + Cp->v[1] * Cp->v[1] + Cp->v[2] * Cp->v[2];
+    double vM2 = M->v[0] * M->v[0] + M->v[1] * M->v[1] + M->v[2] * M->v[2];
+    double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    double KEin = (0.5 * mB * vB2 + 0.5 * mC * vC2) + 0.5 * mM * vM2;
+    double KEcm = 0.5 * mt * V2;
+    double dEf = sA->d.E_form - (sB->d.E_form + sC->d.E_form);
+    double Eav = KEin - KEcm + EvB + EvC - dEf;
+    if (!(Eav - sA->zpe > 0.0) || Eav > table_top(sA, c)) return 0;
+    o_stream sa, ss;
+    st_init(&sa, R->seed, R->step, cell, rk, PU_LB_A);
+    st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
+    uint8_t qA[16];
+    product_state(c, R, sA, Eav, &sa, qA);
+    double Etr = Eav - evib(sA, qA);
+    double mu = mA * mM / mt;
+    double g = sqrt(2.0 * Etr / mu);
+    double d[3];
+    iso_dir(&ss, d);
+    double fA = mM / mt, fM = mA / mt;
+    for (int i = 0; i < 3; ++i) {
+        double G = g * d[i];
+        B->v[i] = V[i] + fA * G;
+        M->v[i] = V[i] - fM * G;
+    }
+    B->sp = r->products[0];
+    memcpy(B->qn, qA, 16);
+    Cp->sp = -1;
+    return 1;
+}
+
+/* Translational temperature of a cell at the start of a step: the kinetic
+   energy in the cell's centre-of-mass frame, 3/2 N k T.  The per-particle
+   energies, momenta and masses are summed as integers (units 2^-96 J,
+   2^-104 kg m/s, 2^-120 kg) so that the sums do not depend on their order. */
+static double cell_temperature(const ora_ctx* c, const o_cell* cl) {
+    int64_t E = 0, px = 0, py = 0, pz = 0, Ms = 0;
+    int N = cl->n;
+    if (N < 2) return 0.0;
+    for (int i = 0; i < N; ++i) {
+        const o_part* p = &cl->p[i];
+        double m = c->sp[p->sp].d.mass;
+        double e = 0.5 * m * (p->v[0] * p->v[0] + p->v[1] * p->v[1] + p->v[2] * p->v[2]);
+        E += llrint(ldexp(e, 96));
+        px += llrint(ldexp(m * p->v[0], 104));
+        py += llrint(ldexp(m * p->v[1], 104));
+        pz += llrint(ldexp(m * p->v[2], 104));
+        Ms += llrint(ldexp(m, 120));
+    }
+    double Ek = ldexp((double)E, -96);
+    double P2 = ((double)px * (double)px + (double)py * (double)py) + (double)pz * (double)pz;
+    double Ecm = ldexp(0.5 * (P2 / (double)Ms), -88);
+    return (2.0 * (Ek - Ecm)) / (3.0 * (double)N * KB);
+}
+
+double ora_cell_temperature(ora_ctx* c, int res, int cell) {
+    return cell_temperature(c, &c->res[res]->cells[cell]);
+}
+
 static void log_push(ora_ctx* c, const ora_log_rec* r) {
     if (!c->log_on) return;
     if (c->log_n == c->log_cap) {
@@ -760,11 +1021,24 @@ static void log_push(ora_ctx* c, const ora_log_rec* r) {
 /* One candidate pair: VHS acceptance (NTC), then the QK reaction test, then
    either the reaction or LB relaxation of molecule 1, then molecule 2, then
    isotropic VHS scattering. */
+typedef struct {
+    o_cell* cl;
+    uint32_t N;        /* particles at the start of the step */
+    int64_t kmax;      /* pairs of this round */
+    const uint32_t* key;
+    double T;          /* cell temperature at the start of the step */
+} o_round;
+
 static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, uint32_t k,
                          o_part* P, o_part* Q, uint32_t ip, uint32_t iq, double sgmax,
-                         double* seen, o_part* created, int* n_created) {
+                         double* seen, o_part* created, int* n_created, const o_round* rd) {
     uint32_t rk = (round << 24) | k;
     R->counters[0]++;
+    if (P->sp < 0 || Q->sp < 0) { /* a member removed earlier in this step */
+        ora_log_rec lr0 = { R->step, cell, rk, ip, iq, -1, 0 };
+        log_push(c, &lr0);
+        return;
+    }
     const o_species* sP = &c->sp[P->sp];
     const o_species* sQ = &c->sp[Q->sp];
     o_pair pc = pair_consts(c, P->sp, Q->sp);
@@ -785,6 +1059,43 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
     double Etr = 0.5 * pc.mr * g2;
     double EvP = evib(sP, P->qn);
     double EvQ = evib(sQ, Q->qn);
+
+    /* Recombination (reading A14), tested before the QK channels: the pair
+       (B, C) recombines with probability k_r(T_cell) n / (sigma_T g), n the
+       number density of third bodies ((N - 2) w / V_c); k_r is that of the
+       third body M, the particle at position 2 kmax + k of this round's
+       permutation (a particle in no pair of the round, uniform over them); no
+       third body, no recombination.  One recombination per pair type. */
+    for (int r = 0; r < c->n_reactions; ++r) {
+        const ora_reaction_desc* rx = &c->rx[r];
+        if (rx->type != ORA_RECOMB) continue;
+        int side;
+        if (P->sp == rx->reactants[0] && Q->sp == rx->reactants[1]) side = 0;
+        else if (Q->sp == rx->reactants[0] && P->sp == rx->reactants[1]) side = 1;
+        else continue;
+        int64_t m = 2 * rd->kmax + (int64_t)k;
+        if (m >= (int64_t)rd->N) break;
+        uint32_t iM = ora_feistel((uint32_t)m, rd->N, rd->key);
+        o_part* M = &rd->cl->p[iM];
+        if (M->sp < 0) break;
+        double kr = ora_rec_rate(c, r, M->sp, rd->T);
+        double n3 = ((double)(rd->N - 2) * R->w) / R->Vc;
+        double prec = (kr * n3) / sg;
+        o_stream sr;
+        st_init(&sr, R->seed, R->step, cell, rk, PU_REC);
+        if (!(st_u01(&sr) < prec)) break;
+        o_part* B = side ? Q : P;
+        o_part* Cp = side ? P : Q;
+        if (do_recomb(c, R, r, B, Cp, M, side ? EvQ : EvP, side ? EvP : EvQ, cell, rk)) {
+            R->counters[8 + r]++;
+            lr.event = 1 + r;
+            lr.aux = (uint32_t)side + 2u * iM;
+            log_push(c, &lr);
+            return;
+        }
+        R->counters[6]++; /* not executed: the pair relaxes */
+        goto relax;
+    }
 
     /* QK reaction test: channel list in fixed order (reading A21) */
     o_chan ch[MAX_CHANNELS];
@@ -872,6 +1183,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
     }
 
     /* relaxation (HCAO LB): molecule 1, then molecule 2 with the updated E_rel */
+relax:;
     double E = Etr;
     if (sP->n_modes > 0) {
         o_stream s1;
@@ -923,6 +1235,9 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
         double seen = 0.0;
         o_part* created = (o_part*)malloc(sizeof(o_part) * (size_t)(nsel + 1));
         int n_created = 0;
+        int has_rec = 0;
+        for (int r = 0; r < c->n_reactions; ++r) has_rec |= c->rx[r].type == ORA_RECOMB;
+        double Tcell = has_rec ? cell_temperature(c, cl) : 0.0;
         for (int64_t r = 0; r < rounds; ++r) {
             o_stream sf;
             st_init(&sf, R->seed, R->step, (uint32_t)ci, (uint32_t)r << 24, PU_FEISTEL);
@@ -930,15 +1245,31 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
             for (int i = 0; i < 4; ++i) key[i] = st_word(&sf);
             int64_t kmax = nsel - r * P;
             if (kmax > P) kmax = P;
+            o_round rd = { cl, (uint32_t)N, kmax, key, Tcell };
             for (int64_t k = 0; k < kmax; ++k) {
                 uint32_t ip = ora_feistel((uint32_t)(2 * k), (uint32_t)N, key);
                 uint32_t iq = ora_feistel((uint32_t)(2 * k + 1), (uint32_t)N, key);
                 process_pair(c, R, (uint32_t)ci, (uint32_t)r, (uint32_t)k, &cl->p[ip], &cl->p[iq],
-                             ip, iq, cl->sgmax, &seen, created, &n_created);
+                             ip, iq, cl->sgmax, &seen, created, &n_created, &rd);
             }
         }
         for (int i = 0; i < n_created; ++i) cell_push(cl, &created[i]);
         free(created);
+        /* removed particles (recombination): with d removed among the n
+           records, the surviving records at positions >= n - d move, in
+           increasing position order, into the removed positions below n - d,
+           taken in increasing order; the cell keeps n - d records */
+        int d = 0;
+        for (int i = 0; i < cl->n; ++i) d += cl->p[i].sp < 0;
+        if (d > 0) {
+            int t0 = cl->n - d, h = 0;
+            for (int t = t0; t < cl->n; ++t) {
+                if (cl->p[t].sp < 0) continue;
+                while (cl->p[h].sp >= 0) h++;
+                cl->p[h++] = cl->p[t];
+            }
+            cl->n = t0;
+        }
         if (seen > cl->sgmax) cl->sgmax = seen;
     }
     R->step++;

@@ -32,7 +32,7 @@ extern "C" {
 #define ORA_MAX_LEVELS 256
 
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_ENOMEM = -2, ORA_EREJECT = -4, ORA_ELEVEL = -5 };
-enum { ORA_DISS = 1, ORA_EXCH = 2 };
+enum { ORA_DISS = 1, ORA_EXCH = 2, ORA_RECOMB = 3 };
 enum { ORA_ALPHA_PER_MODE = 0, ORA_ALPHA_ONE_RANDOM_STRETCH = 1 };
 enum { ORA_SAMPLER_TABLE = 0, ORA_SAMPLER_LITERAL = 1 };
 
@@ -51,10 +51,11 @@ typedef struct {
 } ora_species_desc;
 
 typedef struct {
-    int type;             /* ORA_DISS: A + M -> B + C + M ; ORA_EXCH: A + B -> C + D */
-    int reactants[2];     /* DISS: {A, -1}; EXCH: {A, B} */
-    int products[2];      /* DISS: {B, C};  EXCH: {C, D} */
-    uint32_t diss_mode_mask; /* DISS: stretch modes of A whose breaking gives B + C */
+    int type;             /* ORA_DISS: A + M -> B + C + M ; ORA_EXCH: A + B -> C + D ;
+                             ORA_RECOMB: B + C + M -> A + M */
+    int reactants[2];     /* DISS: {A, -1}; EXCH: {A, B}; RECOMB: {B, C} */
+    int products[2];      /* DISS: {B, C};  EXCH: {C, D}; RECOMB: {A, -1} */
+    uint32_t diss_mode_mask; /* DISS / RECOMB: stretch modes of A whose breaking gives B + C */
     double Ea;            /* EXCH: activation energy, J */
     double steric;        /* EXCH: steric factor in [0,1] */
     int alpha_mode;       /* EXCH: ORA_ALPHA_PER_MODE or ORA_ALPHA_ONE_RANDOM_STRETCH */
@@ -64,7 +65,8 @@ typedef struct {
 typedef struct {
     uint32_t step, cell, round_k, p, q;
     int32_t event;        /* -1: rejected candidate, 0: relaxed, 1+r: reaction r */
-    uint32_t aux;         /* DISS: broken stretch mode (+16 if partner q); EXCH: 0/1 A is p/q */
+    uint32_t aux;         /* DISS: broken stretch mode (+16 if partner q); EXCH: 0/1 A is p/q;
+                             RECOMB: 0/1 B is p/q, plus 2 x the third body's index in the cell */
 } ora_log_rec;
 
 typedef struct ora_ctx ora_ctx;
@@ -108,6 +110,20 @@ void     ora_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4
 /* T_vib of one species in a reservoir by the zero-point search (P5) */
 double   ora_tvib(ora_ctx*, int res, int sp);
 double   ora_mean_sigma_g(ora_ctx*, int sp, int sq, double T);
+/* Recombination rates (reading A14).  Nodes T_i = 500 K * 2^(i/32), i < ORA_REC_NODES. */
+#define ORA_REC_NODES 225
+double   ora_rec_node_T(int i);
+/* Regularised upper incomplete gamma Q(a, x) (x <= 0 gives 1) */
+double   ora_gamma_q(double a, double x);
+/* thermal dissociation probability per collision of recombination rx's molecule A at T */
+double   ora_diss_prob(ora_ctx*, int rx, double T);
+/* equilibrium constant n_B n_C / n_A (m^-3) of recombination rx at T */
+double   ora_keq(ora_ctx*, int rx, double T);
+/* k_r (m^6/s) of recombination rx with a third body of species spM at node i / at T */
+double   ora_rec_rate_node(ora_ctx*, int rx, int spM, int i);
+double   ora_rec_rate(ora_ctx*, int rx, int spM, double T);
+/* translational temperature of one cell as the collision step computes it */
+double   ora_cell_temperature(ora_ctx*, int res, int cell);
 const char* ora_last_error(ora_ctx*);
 
 #ifdef __cplusplus
