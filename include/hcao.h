@@ -46,7 +46,7 @@ typedef enum {
 } hcao_status;
 
 enum { HCAO_FP64 = 0, HCAO_FP32 = 1 };
-enum { HCAO_DISS = 1, HCAO_EXCH = 2 };
+enum { HCAO_DISS = 1, HCAO_EXCH = 2, HCAO_RECOMB = 3 };
 enum { HCAO_ALPHA_PER_MODE = 0, HCAO_ALPHA_ONE_RANDOM_STRETCH = 1 };
 
 #define HCAO_MAX_MODES 16
@@ -79,13 +79,33 @@ typedef struct {
     const double* theta;              /* host, n_bend, K (Theta form of Eq. energy-SHO) */
 } hcao_species;
 
-/* One reaction (Sec. "Polyatomic QK reaction modeling"). */
+/* One reaction (Sec. "Polyatomic QK reaction modeling").
+   HCAO_RECOMB (Sec. "Recombination reactions"): a colliding (B, C) pair forms
+   A with a third body M with probability k_r(T_cell) n / (sigma_T g), n the
+   third-body number density of the cell and k_r = k_f / K_eq: k_f is P times
+   the VHS collision-rate coefficient of A and M, P the exact thermal average
+   of Eq. recomb-correct over A's level combinations with the QK threshold of
+   the reverse dissociation (the stretches in diss_mode_mask), and K_eq the
+   equilibrium constant from translational and vibrational partition sums.
+   k_r is tabulated per third-body species at T_i = 500 K * 2^(i/32),
+   i = 0..224, and interpolated linearly in T (clamped at the ends); the
+   tables are built on the host by hcao_set_reactions.  M is the particle at
+   position 2 kmax + k of the round's pairing permutation (kmax pairs in the
+   round, k the pair): a particle in no pair of the round; there is none when
+   that position is past the cell's end.  C is removed at the end of the step
+   (the survivors at the end of the cell fill the freed slots in increasing
+   order).  At most HCAO_MAX_REMOVALS_PER_CELL removals per cell and step
+   (HCAO_ECAPACITY beyond). */
+#define HCAO_MAX_REMOVALS_PER_CELL 4096
+#define HCAO_REC_NODES 225
 typedef struct {
     int type;              /* HCAO_DISS: A + M -> B + C + M (Eq. Ecoll-diss);
-                              HCAO_EXCH: A + B -> C + D (Eq. Ecoll-exch) */
-    int reactants[2];      /* DISS: {A, -1}; EXCH: {A, B} (species indices) */
-    int products[2];       /* DISS: {B, C}; EXCH: {C, D} */
-    uint32_t diss_mode_mask; /* DISS: stretches of A that may break */
+                              HCAO_EXCH: A + B -> C + D (Eq. Ecoll-exch);
+                              HCAO_RECOMB: B + C + M -> A + M */
+    int reactants[2];      /* DISS: {A, -1}; EXCH: {A, B}; RECOMB: {B, C} (species indices) */
+    int products[2];       /* DISS: {B, C}; EXCH: {C, D}; RECOMB: {A, -1} */
+    uint32_t diss_mode_mask; /* DISS: stretches of A that may break; RECOMB: those of
+                                the reverse dissociation (sets P's threshold) */
     double Ea;             /* EXCH: activation energy, J */
     double steric;         /* EXCH: steric factor in [0,1] */
     int alpha_mode;        /* EXCH: HCAO_ALPHA_PER_MODE or _ONE_RANDOM_STRETCH */
@@ -96,7 +116,8 @@ typedef struct {
 typedef struct {
     uint32_t step, cell, round_k, p, q;
     int32_t event;         /* -1 rejected candidate, 0 relaxed, 1+r reaction r */
-    uint32_t aux;          /* DISS: broken stretch (+16 if partner q); EXCH: side */
+    uint32_t aux;          /* DISS: broken stretch (+16 if partner q); EXCH: side;
+                              RECOMB: side (B is p: 0, q: 1) + 2 x the third body's index */
 } hcao_log_rec;
 
 typedef struct {
@@ -308,6 +329,11 @@ hcao_status hcao_serve_stop(hcao_ctx* ctx);
 /* Queue length, resident jobs, budgeted bytes in use, engine iterations. */
 hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, int64_t* used_bytes,
                              uint64_t* iterations);
+
+/* The tabulated recombination rate coefficient k_r (m^6/s) of reaction
+   `reaction` (an HCAO_RECOMB) with a third body of species spM at temperature
+   T, interpolated as the collision step does (host copy of the device table). */
+hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, double* out);
 
 /* Number of this library's kernels launched since create (instrumentation). */
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx);

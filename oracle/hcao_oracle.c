@@ -1064,8 +1064,9 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
        (B, C) recombines with probability k_r(T_cell) n / (sigma_T g), n the
        number density of third bodies ((N - 2) w / V_c); k_r is that of the
        third body M, the particle at position 2 kmax + k of this round's
-       permutation (a particle in no pair of the round, uniform over them); no
-       third body, no recombination.  One recombination per pair type. */
+       permutation (a particle in no pair of the round, uniform over them;
+       rounds hold at most N/3 pairs when a recombination exists, so every
+       pair has one when N >= 3).  One recombination per pair type. */
     for (int r = 0; r < c->n_reactions; ++r) {
         const ora_reaction_desc* rx = &c->rx[r];
         if (rx->type != ORA_RECOMB) continue;
@@ -1229,14 +1230,16 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
         o_stream sn;
         st_init(&sn, R->seed, R->step, (uint32_t)ci, 0u, PU_NSEL);
         if (st_u01(&sn) < x - fl) nsel++;
-        int64_t P = N / 2;
+        int has_rec = 0;
+        for (int r = 0; r < c->n_reactions; ++r) has_rec |= c->rx[r].type == ORA_RECOMB;
+        /* pairs per round: N/2, or N/3 with a recombination reaction, so that
+           every pair of a round has a third body in no pair of the round */
+        int64_t P = (has_rec && N >= 3) ? N / 3 : N / 2;
         int64_t rounds = (nsel + P - 1) / P;
         if (rounds > 255) { set_err(c, ORA_EINVAL, "more than 255 NTC rounds"); return ORA_EINVAL; }
         double seen = 0.0;
         o_part* created = (o_part*)malloc(sizeof(o_part) * (size_t)(nsel + 1));
         int n_created = 0;
-        int has_rec = 0;
-        for (int r = 0; r < c->n_reactions; ++r) has_rec |= c->rx[r].type == ORA_RECOMB;
         double Tcell = has_rec ? cell_temperature(c, cl) : 0.0;
         for (int64_t r = 0; r < rounds; ++r) {
             o_stream sf;

@@ -22,8 +22,9 @@ UNITS = {
     "hcao_f32.cu": [],
     "hcao_sort.cu": [],
     "hcao_api.cu": [],
+    "hcao_rates.cu": [],
 }
-HEADERS = ["hcao_internal.h", "hcao_kernels.cuh", "hcao_sort.h"]
+HEADERS = ["hcao_internal.h", "hcao_kernels.cuh", "hcao_sort.h", "hcao_rates.h"]
 
 
 def _nvcc() -> str:

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "hcao_internal.h"
+#include "hcao_rates.h"
 #include "hcao_sort.h"
 
 using namespace hcao;
@@ -110,6 +111,15 @@ struct hcao_ctx {
     uint4* d_qB = nullptr;
     uint32_t* d_qsize = nullptr;
     unsigned long long* d_work = nullptr;
+    // recombination: rate tables (host copy + device), per-cell sums, particle prefix
+    int n_recomb = 0;
+    std::vector<double> h_krec, h_Tnode;
+    double* d_krec = nullptr;
+    double* d_Tnode = nullptr;
+    long long* d_csum = nullptr;
+    uint32_t* d_nbase = nullptr;
+    uint32_t* d_chbase = nullptr;
+    uint32_t* d_chcnt = nullptr;
     // launch shapes (autotuned; results do not depend on them)
     int grid_select = 0, grid_relax = 0, grid_react = 0;
     // CUDA graph of one step, captured on a private stream, re-captured when
@@ -437,8 +447,14 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
     ctx->n_cells_total = total;
     dfree(ctx, ctx->d_pbase);
     dfree(ctx, ctx->d_abase);
+    dfree(ctx, ctx->d_nbase);
+    dfree(ctx, ctx->d_csum);
+    dfree(ctx, ctx->d_chbase);
+    CU(dalloc(ctx, &ctx->d_chbase, (size_t)total + 1));
     CU(dalloc(ctx, &ctx->d_pbase, (size_t)MAX_ROUNDS * (total + 1)));
     CU(dalloc(ctx, &ctx->d_abase, (size_t)total + 1));
+    CU(dalloc(ctx, &ctx->d_nbase, (size_t)total + 1));
+    CU(dalloc(ctx, &ctx->d_csum, (size_t)5 * cells_alloc));
     if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
         dfree(ctx, ctx->d_cflag);
         dfree(ctx, ctx->d_log);
@@ -452,6 +468,9 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
     }
+    // chunk counters: at most pairs / FINISH_CHUNK + one partial chunk per cell
+    dfree(ctx, ctx->d_chcnt);
+    CU(dalloc(ctx, &ctx->d_chcnt, (size_t)(ctx->pair_cap / FINISH_CHUNK) + (size_t)total + 1));
     if (ctx->hc.creates && !ctx->d_cscratch)
         CU(cudaMallocAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->stream));
     // reservoir table
@@ -534,6 +553,70 @@ double tvib_host(const HostSpecies& s, double target) {
     return 0.5 * (lo + hi);
 }
 
+// Rate tables of the recombination reactions (Sec. "Recombination
+// reactions", reading A14): at every node T_i and for every third-body
+// species M, k_r = P_A(T) <sigma_T g>_{A,M}(T) / K_eq(T), with P_A the exact
+// thermal dissociation probability of the product A (threshold of the reverse
+// QK dissociation: min over the masked stretches of De_j + ZPE_A + ZPE_B +
+// ZPE_C - E_j(0)) and K_eq = n_B n_C / n_A from translational and vibrational
+// partition sums with the formation energies.  Nodes are independent: they are
+// computed on host threads.
+hcao_status build_recomb_tables(hcao_ctx* ctx) {
+    const Consts& C = ctx->hc;
+    const int S = ctx->n_species;
+    ctx->h_Tnode.resize(REC_NODES);
+    for (int i = 0; i < REC_NODES; ++i) ctx->h_Tnode[i] = rec_node_T(i);
+    ctx->h_krec.assign((size_t)ctx->n_recomb * MAXS * REC_NODES, 0.0);
+    const double a = 2.5 - ctx->omega;
+    std::vector<int> rxs;
+    for (int i = 0; i < C.n_reactions; ++i)
+        if (C.rx[i].type == HCAO_RECOMB) rxs.push_back(i);
+    auto levels = [&](int sp) {
+        std::vector<std::vector<double>> l;
+        for (int j = 0; j < ctx->sp[sp].n_modes; ++j) l.push_back(ctx->sp[sp].lev[j]);
+        return l;
+    };
+    auto work = [&](int node) {
+        const double T = ctx->h_Tnode[node];
+        for (int ri : rxs) {
+            const DevReaction& D = C.rx[ri];
+            const HostSpecies& sA = ctx->sp[D.P0];
+            const HostSpecies& sB = ctx->sp[D.A];
+            const HostSpecies& sC = ctx->sp[D.B];
+            double Dthr = INFINITY;
+            for (int j = 0; j < sA.d.n_stretch; ++j)
+                if ((D.mask >> j) & 1u) Dthr = std::min(Dthr, (sA.De[j] + D.zpesum) - sA.lev[j][0]);
+            const double P = thermal_diss_prob(levels(D.P0), Dthr, a, T);
+            const double f = 2.0 * PI_D * KB * T / (HPLANCK * HPLANCK);
+            const double qtr = std::pow(f * sB.d.mass, 1.5) * std::pow(f * sC.d.mass, 1.5) /
+                               std::pow(f * sA.d.mass, 1.5);
+            const double dE0 = (sB.d.E_form + sB.zpe + sC.d.E_form + sC.zpe) - (sA.d.E_form + sA.zpe);
+            const double keq = qtr * (zvib_excited(levels(D.A), T) * zvib_excited(levels(D.B), T) /
+                                      zvib_excited(levels(D.P0), T)) * std::exp(-dE0 / (KB * T));
+            for (int m = 0; m < S; ++m)
+                ctx->h_krec[((size_t)D.rslot * MAXS + m) * REC_NODES + node] =
+                    P * mean_sigma_g(ctx, D.P0, m, T) / keq;
+        }
+    };
+    const int nth = std::max(1, std::min<int>(32, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t)
+        th.emplace_back([&, t] {
+            for (int node = t; node < REC_NODES; node += nth) work(node);
+        });
+    for (auto& x : th) x.join();
+    dfree(ctx, ctx->d_krec);
+    dfree(ctx, ctx->d_Tnode);
+    CU(dalloc(ctx, &ctx->d_krec, ctx->h_krec.size()));
+    CU(dalloc(ctx, &ctx->d_Tnode, ctx->h_Tnode.size()));
+    CU(cudaMemcpyAsync(ctx->d_krec, ctx->h_krec.data(), sizeof(double) * ctx->h_krec.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->d_Tnode, ctx->h_Tnode.data(), sizeof(double) * ctx->h_Tnode.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
 StepArgs make_args(hcao_ctx* ctx) {
     StepArgs a{};
     a.C = ctx->d_consts;
@@ -556,6 +639,14 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.qB = ctx->d_qB;
     a.qsize = ctx->d_qsize;
     a.has_reactions = ctx->n_reactions > 0 ? 1 : 0;
+    a.has_recomb = ctx->n_recomb > 0 ? 1 : 0;
+    a.creates = ctx->hc.creates;
+    a.krec = ctx->d_krec;
+    a.Tnode = ctx->d_Tnode;
+    a.csum = ctx->d_csum;
+    a.nbase = ctx->d_nbase;
+    a.chbase = ctx->d_chbase;
+    a.chcnt = ctx->d_chcnt;
     a.work = ctx->d_work;
     a.grid_select = ctx->grid_select;
     a.grid_relax = ctx->grid_relax;
@@ -608,13 +699,13 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     int dev = ctx->cfg.device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
-    if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 1) != cudaSuccess ||
+    if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 2) != cudaSuccess ||
         dalloc(ctx, &ctx->d_qsize, 3 * MAX_ROUNDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
         delete ctx;
         return HCAO_ENOMEM;
     }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
-    cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 1), ctx->stream);
+    cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 2), ctx->stream);
     cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long) * 4, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         delete ctx;
@@ -649,6 +740,12 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_qB);
     dfree(ctx, ctx->d_qsize);
     dfree(ctx, ctx->d_work);
+    dfree(ctx, ctx->d_krec);
+    dfree(ctx, ctx->d_Tnode);
+    dfree(ctx, ctx->d_csum);
+    dfree(ctx, ctx->d_nbase);
+    dfree(ctx, ctx->d_chbase);
+    dfree(ctx, ctx->d_chcnt);
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
@@ -663,6 +760,26 @@ void hcao_destroy(hcao_ctx* ctx) {
 }
 
 const char* hcao_last_error(const hcao_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, double* out) {
+    if (!ctx || !out || reaction < 0 || reaction >= ctx->n_reactions || spM < 0 || spM >= ctx->n_species)
+        return fail(ctx, HCAO_EINVAL, "recomb_rate: bad arguments");
+    const DevReaction& D = ctx->hc.rx[reaction];
+    if (D.type != HCAO_RECOMB) return fail(ctx, HCAO_EINVAL, "recomb_rate: not a recombination");
+    const double* Tn = ctx->h_Tnode.data();
+    const double* k = ctx->h_krec.data() + ((size_t)D.rslot * MAXS + spM) * REC_NODES;
+    const int last = REC_NODES - 1;
+    if (!(T > Tn[0])) { *out = k[0]; return HCAO_OK; }
+    if (!(T < Tn[last])) { *out = k[last]; return HCAO_OK; }
+    int lo = 0, hi = last;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (Tn[mid] <= T) lo = mid; else hi = mid;
+    }
+    const double f = (T - Tn[lo]) / (Tn[hi] - Tn[lo]);
+    *out = k[lo] + f * (k[hi] - k[lo]);
+    return HCAO_OK;
+}
 
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -820,13 +937,42 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         if (r.live) return fail(ctx, HCAO_EINVAL, "set_reactions: before any reservoir");
     Consts& C = ctx->hc;
     const int S = ctx->n_species;
-    int creates = 0;
+    int creates = 0, n_rec = 0;
+    for (int i = 0; i < MAXS * MAXS; ++i) C.rec_pair[i] = -1;
     for (int i = 0; i < n; ++i) {
         const hcao_reaction& r = rx[i];
         DevReaction& D = C.rx[i];
         std::memset(&D, 0, sizeof D);
         D.type = r.type;
-        if (r.type != HCAO_DISS && r.type != HCAO_EXCH) return fail(ctx, HCAO_EINVAL, "set_reactions: bad type");
+        if (r.type != HCAO_DISS && r.type != HCAO_EXCH && r.type != HCAO_RECOMB)
+            return fail(ctx, HCAO_EINVAL, "set_reactions: bad type");
+        if (r.type == HCAO_RECOMB) {
+            // B + C + M -> A + M: stored as A := B, B := C, P0 := A
+            D.A = r.reactants[0];
+            D.B = r.reactants[1];
+            D.P0 = r.products[0];
+            D.P1 = -1;
+            if (D.A < 0 || D.A >= S || D.B < 0 || D.B >= S || D.P0 < 0 || D.P0 >= S)
+                return fail(ctx, HCAO_EINVAL, "set_reactions: species index out of range");
+            const HostSpecies& P = ctx->sp[D.P0];
+            if (P.d.n_stretch == 0 || r.diss_mode_mask == 0u || (r.diss_mode_mask >> P.d.n_stretch) != 0)
+                return fail(ctx, HCAO_EINVAL, "set_reactions: recombination mask outside the product's stretches");
+            for (int o = 0; o < 2; ++o) {
+                const int a = o ? D.B : D.A, b = o ? D.A : D.B;
+                if (C.rec_pair[a * MAXS + b] >= 0)
+                    return fail(ctx, HCAO_EINVAL, "set_reactions: two recombinations of one species pair");
+            }
+            D.mask = r.diss_mode_mask;
+            // the reverse dissociation's threshold terms (Eq. Ecoll-diss) and the released energy
+            D.zpesum = P.zpe + ctx->sp[D.A].zpe + ctx->sp[D.B].zpe;
+            D.dEf = P.d.E_form - (ctx->sp[D.A].d.E_form + ctx->sp[D.B].d.E_form);
+            D.dEf_fix = to_fix(D.dEf);
+            D.rslot = n_rec++;
+            C.rec_pair[D.A * MAXS + D.B] = i;               // side 0: P is B
+            if (D.B != D.A) C.rec_pair[D.B * MAXS + D.A] = i | (1 << 3);
+            creates = 1;  // removed positions use the per-pair scratch slots
+            continue;
+        }
         D.A = r.reactants[0];
         D.B = r.type == HCAO_EXCH ? r.reactants[1] : -1;
         D.P0 = r.products[0];
@@ -860,7 +1006,13 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
     }
     C.n_reactions = n;
     C.creates = creates;
+    C.has_recomb = n_rec > 0 ? 1 : 0;
     ctx->n_reactions = n;
+    ctx->n_recomb = n_rec;
+    if (n_rec > 0) {
+        hcao_status st = build_recomb_tables(ctx);
+        if (st != HCAO_OK) return st;
+    }
     return upload_consts(ctx);
 }
 
@@ -1136,7 +1288,8 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             CU(e);
             ctx->graph_args = a;
         }
-        const uint64_t per_step = 2 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2);
+        const uint64_t per_step = 3 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2) +
+                                  (a.has_recomb ? 2 : 0) + (ctx->hc.creates ? 1 : 0);
         for (int s = 0; s < n_steps; ++s) {
             CU(cudaGraphLaunch(ctx->graph, ctx->stream));
             ctx->launches += per_step;
@@ -1170,10 +1323,22 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             }
             auto& ev = pool[ctx->prof_used[k]++];
             CU(cudaEventRecord(ev.first, ctx->stream));
-            if (k == 0) launch_setup(a, ctx->stream);
-            else if (k == 4) {
+            if (k == 0) {
+                launch_setup(a, ctx->stream);
+                if (a.has_recomb) {
+                    if (f64) launch_cellstats<double>(a, ctx->stream);
+                    else launch_cellstats<float>(a, ctx->stream);
+                    ctx->launches++;
+                }
+            } else if (k == 4) {
                 if (f64) launch_finish<double>(a, ctx->stream);
                 else launch_finish<float>(a, ctx->stream);
+                ctx->launches += ctx->hc.creates ? 2 : 1;
+                if (a.has_recomb) {
+                    if (f64) launch_compact<double>(a, ctx->stream);
+                    else launch_compact<float>(a, ctx->stream);
+                    ctx->launches++;
+                }
             } else {
                 if (f64) launch_phase<double>(a, r, k - 1, grid, ctx->stream);
                 else launch_phase<float>(a, r, k - 1, grid, ctx->stream);
@@ -1452,7 +1617,7 @@ hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* out, int64_t max, int64_t
     if (!ctx || !n_out) return HCAO_EINVAL;
     *n_out = 0;
     if (!ctx->log_on || !ctx->d_log) return fail(ctx, HCAO_EINVAL, "read_log: logging is off");
-    uint32_t tot[MAX_ROUNDS + 1];
+    uint32_t tot[MAX_ROUNDS + 2];
     CU(cudaMemcpyAsync(tot, ctx->d_totals, sizeof tot, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     const int64_t n = out ? std::min<int64_t>(max, tot[MAX_ROUNDS]) : (int64_t)tot[MAX_ROUNDS];

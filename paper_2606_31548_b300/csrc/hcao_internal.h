@@ -17,10 +17,13 @@ constexpr int MAXR = 8;         // reactions
 constexpr int MAXL = 256;       // levels per mode (quantum numbers are bytes)
 constexpr int TABLE_PAD = 17;   // grid entries beyond M (one per mode + 1)
 constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard cap)
+constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)
+constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
+constexpr int FINISH_CHUNK = 2048;  // pair slots per work item of the end-of-step kernels
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7 };
+       PU_INIT = 7, PU_REC = 9 };
 
 // per-reservoir counters
 enum { CNT_CAND = 0, CNT_ACC, CNT_SAMPLES, CNT_TRIALS, CNT_OVER, CNT_DEGEN, CNT_NOTEXEC,
@@ -72,11 +75,12 @@ struct DevPair {
     float mr_f, C_f, fp_f, fq_f, inv2mr_f, pad_f;
 };
 
+// DISS: A + M -> P0 + P1; EXCH: A + B -> P0 + P1; RECOMB: A + B (+ M) -> P0
 struct DevReaction {
     int type, A, B, P0, P1;
     uint32_t mask;
     int alpha_mode;
-    int pad;
+    int rslot;                       // RECOMB: slot of its rate table
     double Ea, steric, zpesum, dEf;
     double alpha[MAXM];
     long long Ea_fix, zpesum_fix, dEf_fix;   // FP32 mode (2^-100 J units)
@@ -84,6 +88,8 @@ struct DevReaction {
 
 struct Consts {
     int n_species, n_reactions, amode, creates;
+    int has_recomb, pad_c[3];
+    int rec_pair[MAXS * MAXS];       // species pair -> recombination | side << 3, or -1
     DevSpecies sp[MAXS];
     DevPair pair[MAXS * MAXS];
     DevReaction rx[MAXR];
@@ -97,7 +103,7 @@ struct DevCell {
     unsigned long long seen;          // max sigma_T g of this step (bits of a double >= 0)
     uint32_t nsel, ncreated;
     float sgmax_f;                    // FP32 copy of sgmax for the step
-    uint32_t pad_c;
+    uint32_t nremoved;                // particles removed this step (recombination)
     uint32_t fkey[MAX_ROUNDS][4];     // Feistel keys per round of this step
 };
 
@@ -122,7 +128,9 @@ struct StepArgs {
     unsigned long long* counters;   // [n_res][NCNT]
     uint32_t* pbase;                // [MAX_ROUNDS][n_cells + 1]: round-r pair prefix
     uint32_t* abase;                // [n_cells + 1]: all-round pair prefix
-    uint32_t* totals;               // [MAX_ROUNDS + 1]
+    uint32_t* totals;               // [MAX_ROUNDS + 2]: pairs per round, all pairs, chunks
+    uint32_t* chbase;               // [n_cells + 1]: prefix of FINISH_CHUNK chunks of each cell's pairs
+    uint32_t* chcnt;                // [chunks]: particles created in each chunk
     uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
     void* cscratch;                 // per-pair record of a particle created by a reaction
     uint4* qA;                      // accepted pairs of the current round (cell, pair, ip, iq)
@@ -130,6 +138,12 @@ struct StepArgs {
     uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax and react queue
                                     // lengths, then the relax queue's fetch heads
     int has_reactions;
+    int has_recomb;
+    int creates;                    // a reaction creates particles or removes them (scratch slots)
+    const double* krec;             // [slot][MAXS][REC_NODES] recombination k_r at the nodes
+    const double* Tnode;            // [REC_NODES]
+    long long* csum;                // [n_cells][5] integer sums: E (2^-96 J), p (2^-104), m (2^-120)
+    uint32_t* nbase;                // [n_cells + 1]: particle prefix at step start
     unsigned long long* work;       // [4] K5 level evaluations, mode starts, molecule samples, pairs
     int grid_select, grid_relax, grid_react;  // launch shapes (host-side; results do not depend on them)
     uint64_t pair_cap;              // capacity of cflag / log
@@ -152,6 +166,9 @@ template <class R> void launch_collide(const StepArgs& a, int r, int grid, int b
 // phase k of round r: 0 select, 1 relax, 2 react (for per-kernel timing)
 template <class R> void launch_phase(const StepArgs& a, int r, int phase, int grid, cudaStream_t s);
 template <class R> void launch_finish(const StepArgs& a, cudaStream_t s);
+// recombination: per-cell temperature sums before the rounds, removals after
+template <class R> void launch_cellstats(const StepArgs& a, cudaStream_t s);
+template <class R> void launch_compact(const StepArgs& a, cudaStream_t s);
 template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm,
                                             const uint32_t* offsets, const uint64_t* cell_slot0,
                                             int n_cells, const double* v, const uint8_t* qn,

@@ -366,7 +366,7 @@ __device__ __forceinline__ void iso_dir(Stream& st, R d[3]) {
 enum : uint32_t {
     EV_ACC = 1u, EV_CREATED = 2u, EV_RX_SHIFT = 2, /* bits 2..7: reaction + 1 */
     EV_SAMP_SHIFT = 8, /* bits 8..9 */ EV_OVER_SHIFT = 10, EV_DEGEN_SHIFT = 12,
-    EV_NOTEXEC = 1u << 14, EV_TRIAL_SHIFT = 16
+    EV_NOTEXEC = 1u << 14, EV_REMOVED = 1u << 15, EV_TRIAL_SHIFT = 16
 };
 
 struct PairOut {
@@ -509,7 +509,67 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
     return true;
 }
 
+// recombination B + C + M -> A + M (Sec. "Recombination reactions"): B takes
+// A's species, C is removed, M keeps its species and levels.  The budget of
+// A's vibration and the A-M relative motion is the B, C, M translational
+// energy in their centre-of-mass frame, the vibrational energies of B and C
+// and the released formation energy; A's levels follow the LB target at that
+// budget, the rest goes to A-M relative motion in a uniform direction.
+template <class R>
+__device__ bool do_recomb(const StepArgs& A, const Consts* C, const DevReaction& rx, double vB[3],
+                          double vC[3], double vM[3], int spB, int spC, int spM, double EvB, double EvC,
+                          const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t qA[4], PairOut& o) {
+    const DevSpecies& sA = C->sp[rx.P0];
+    const DevSpecies& sB = C->sp[spB];
+    const DevSpecies& sC = C->sp[spC];
+    const DevSpecies& sM = C->sp[spM];
+    const double mA = sA.mass, mB = sB.mass, mC = sC.mass, mM = sM.mass;
+    const double mt = mA + mM;
+    double V[3];
+    for (int i = 0; i < 3; ++i) V[i] = ((mB * vB[i] + mC * vC[i]) + mM * vM[i]) / mt;
+    const double vB2 = vB[0] * vB[0] + vB[1] * vB[1] + vB[2] * vB[2];
+    const double vC2 = vC[0] * vC[0] + vC[1] * vC[1] + vC[2] * vC[2];
+    const double vM2 = vM[0] * vM[0] + vM[1] * vM[1] + vM[2] * vM[2];
+    const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+    const double KEin = (0.5 * mB * vB2 + 0.5 * mC * vC2) + 0.5 * mM * vM2;
+    const double KEcm = 0.5 * mt * V2;
+    const double Eav = KEin - KEcm + EvB + EvC - rx.dEf;
+    if (!(Eav - sA.zpe > 0.0) || Eav > sA.top) return false;
+    Stream sa, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) qA[j] = 0u;
+    uint32_t tr = 0;
+    if (sA.n_modes > 0) {
+        o.ev += 1u << EV_SAMP_SHIFT;
+        if (sample_lb<R>(A, sA, C->amode, Eav, sa, qA, tr) != S_OK) {
+            for (int j = 0; j < 4; ++j) qA[j] = 0u;
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    o.trials += tr;
+    const double Etr = Eav - evib64(A.lev64, sA, qA);
+    const double mu = mA * mM / mt;
+    const double g = sqrt(2.0 * Etr / mu);
+    double d[3];
+    iso_dir<double>(ss, d);
+    const double fA = mM / mt, fM = mA / mt;
+    for (int i = 0; i < 3; ++i) {
+        const double G = g * d[i];
+        vB[i] = V[i] + fA * G;
+        vM[i] = V[i] - fM * G;
+    }
+    return true;
+}
+
 // ------------------------------------------------------------- one pair
+// Pairs per NTC round: N/2, or N/3 when a recombination reaction exists, so
+// that every pair of a round has a particle in no pair of the round (its
+// third body, reading A14) at position 2 kmax + k of the permutation.
+__device__ __forceinline__ uint32_t round_pairs(uint32_t N, int has_recomb) {
+    return (has_recomb && N >= 3u) ? N / 3u : N >> 1;
+}
+
 // Where pair k of round r of cell c lives: its Feistel members, its event slot.
 struct PairLoc {
     uint32_t N, lcell, rk, ev_idx, ip, iq;
@@ -522,7 +582,7 @@ __device__ __forceinline__ PairLoc locate(const StepArgs& A, int c, int r, uint3
     L.N = cell.n;
     L.lcell = cell.lcell;
     L.rk = ((uint32_t)r << 24) | k;
-    L.ev_idx = A.abase[c] + (uint32_t)r * (L.N >> 1) + k;
+    L.ev_idx = A.abase[c] + (uint32_t)r * round_pairs(L.N, A.has_recomb) + k;
     const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
     L.ip = feistel(2u * k, L.N, key);
     L.iq = feistel(2u * k + 1u, L.N, key);
@@ -539,7 +599,7 @@ __device__ __forceinline__ PairLoc locate_known(const StepArgs& A, int c, int r,
     L.N = cell.n;
     L.lcell = cell.lcell;
     L.rk = ((uint32_t)r << 24) | k;
-    L.ev_idx = A.abase[c] + (uint32_t)r * (L.N >> 1) + k;
+    L.ev_idx = A.abase[c] + (uint32_t)r * round_pairs(L.N, A.has_recomb) + k;
     L.ip = ip;
     L.iq = iq;
     L.recs = cell.rec;
@@ -973,6 +1033,116 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     return true;
 }
 
+// FP32 mode, recombination B + C + M -> A + M: float kinematics, fixed-point
+// energies (the three bodies' energies in their centre-of-mass frame are
+// converted one by one; no product of two masses is formed)
+static __device__ bool do_recomb_fix(const StepArgs& A, const Consts* __restrict__ C,
+                                     const DevReaction& rx, float vB[3], float vC[3], float vM[3],
+                                     int spB, int spC, int spM, long long EvB, long long EvC,
+                                     const DevRes& rs, uint32_t lcell, uint32_t rk,
+                                     uint32_t (&qA)[4], PairOut& o) {
+    const DevSpecies& sA = C->sp[rx.P0];
+    const float mB = C->sp[spB].mass_f, mC = C->sp[spC].mass_f, mM = C->sp[spM].mass_f;
+    const float m3 = (mB + mC) + mM;
+    float V[3];
+    for (int i = 0; i < 3; ++i) V[i] = ((mB / m3) * vB[i] + (mC / m3) * vC[i]) + (mM / m3) * vM[i];
+    float eB = 0.f, eC = 0.f, eM = 0.f;
+    for (int i = 0; i < 3; ++i) {
+        const float b = vB[i] - V[i], c = vC[i] - V[i], m = vM[i] - V[i];
+        eB += b * b;
+        eC += c * c;
+        eM += m * m;
+    }
+    const long long Ein = f2fix(0.5f * mB * eB) + f2fix(0.5f * mC * eC) + f2fix(0.5f * mM * eM);
+    const long long Eav = Ein + EvB + EvC - rx.dEf_fix;
+    if (!(Eav - sA.zpe_fix > 0) || Eav > sA.top_fix) return false;
+    Stream sa, sb, ss;
+    st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
+    st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
+    st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
+    for (int j = 0; j < 4; ++j) qA[j] = 0u;
+    uint32_t qn[4] = {0u, 0u, 0u, 0u};
+    long long Etr = relax_flat(A, C, rx.P0, qA, sA.zpe_fix, sa, -1, qn, 0, sb, Eav - sA.zpe_fix, o);
+    if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
+    const DevPair& pam = C->pair[rx.P0 * MAXS + spM];
+    const float gn = sqrtf(fix2f(Etr) * pam.inv2mr_f);
+    float d[3];
+    iso_dir<float>(ss, d);
+    for (int i = 0; i < 3; ++i) {
+        const float G = gn * d[i];
+        vB[i] = V[i] + pam.fp_f * G;
+        vM[i] = V[i] - pam.fq_f * G;
+    }
+    return true;
+}
+
+// recombination: cell temperature at the step start from the integer sums
+// (units 2^-96 J, 2^-104 kg m/s, 2^-120 kg): kinetic energy in the cell's
+// centre-of-mass frame = 3/2 N k T
+__device__ __forceinline__ double cell_temperature(const StepArgs& A, int c, uint32_t N) {
+    if (N < 2u) return 0.0;
+    const long long* s = A.csum + 5 * (size_t)c;
+    const double Ek = (double)s[0] * 0x1p-96;
+    const double px = (double)s[1], py = (double)s[2], pz = (double)s[3];
+    const double P2 = (px * px + py * py) + pz * pz;
+    const double Ecm = (0.5 * (P2 / (double)s[4])) * 0x1p-88;
+    return (2.0 * (Ek - Ecm)) / (3.0 * (double)N * 1.380649e-23);
+}
+
+// k_r of rate-table slot `slot` with a third body of species sM at T: linear
+// in T between the nodes T_i = 500 K * 2^(i/32), clamped at the ends
+__device__ __forceinline__ double rec_rate(const StepArgs& A, int slot, int sM, double T) {
+    const double* Tn = A.Tnode;
+    const double* k = A.krec + ((size_t)slot * MAXS + sM) * REC_NODES;
+    const int last = REC_NODES - 1;
+    if (!(T > __ldg(Tn))) return __ldg(k);
+    if (!(T < __ldg(Tn + last))) return __ldg(k + last);
+    int lo = 0, hi = last;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(Tn + mid) <= T) lo = mid; else hi = mid;
+    }
+    const double T0 = __ldg(Tn + lo), T1 = __ldg(Tn + hi);
+    const double f = (T - T0) / (T1 - T0);
+    const double k0 = __ldg(k + lo), k1 = __ldg(k + hi);
+    return k0 + f * (k1 - k0);
+}
+
+// Recombination test of an accepted pair (reading A14), before the QK
+// channels: a (B, C) pair recombines with probability k_r(T_cell) n / (sigma_T g),
+// n = (N - 2) w / V_c, k_r that of the third body M = the particle at position
+// 2 kmax + k of the round's permutation (in no pair of this round); no third
+// body (past the cell's end, or removed earlier this step), no recombination.
+template <class R>
+__device__ bool recomb_test(const StepArgs& A, const Consts* __restrict__ C, int c, int r, uint32_t k,
+                            int sP, int sQ, double sg, uint32_t& chan, uint32_t& iM) {
+    using Rec = typename RecOf<R>::T;
+    const int code = C->rec_pair[sP * MAXS + sQ];
+    if (code < 0) return false;
+    const DevCell& cell = A.cells[c];
+    const uint32_t N = cell.n;
+    const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
+    const uint64_t m = 2ull * (uint64_t)(__ldg(pb + c + 1) - __ldg(pb + c)) + k;
+    if (m >= N) return false;
+    const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
+    iM = feistel((uint32_t)m, N, key);
+    const Rec* recs = reinterpret_cast<const Rec*>(cell.rec);
+    const uint32_t meta = reinterpret_cast<const uint32_t*>(recs + iM)[std::is_same<R, double>::value ? 6 : 3];
+    const int sM = (int)(meta & 0xFFu);
+    if (sM >= MAXS) return false;
+    const int ri = code & 7;
+    const double kr = rec_rate(A, C->rx[ri].rslot, sM, cell_temperature(A, c, N));
+    const DevRes& rs = A.res[cell.res];
+    const double n3 = ((double)(N - 2u) * rs.w) / rs.Vc;
+    const double prec = (kr * n3) / sg;
+    Stream st;
+    st_init(st, rs.seed, rs.step, cell.lcell, ((uint32_t)r << 24) | k, PU_REC);
+    const double u = std::is_same<R, double>::value ? st_u64(st) : (double)st_u32(st);
+    if (!(u < prec)) return false;
+    chan = chan_pack(ri, (code >> 3) & 1, 0);
+    return true;
+}
+
 // HCAO LB relaxation of molecule 1 then molecule 2 (with the updated E_rel),
 // then isotropic VHS scattering with the centre-of-mass velocity kept.
 template <class R, class Rec>
@@ -1163,7 +1333,7 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
         DevCell& cl = A.cells[c];
         const DevRes rs = A.res[cl.res];
         const uint32_t N = cl.n;
-        uint32_t nsel = 0, rounds = 0, P = N >> 1;
+        uint32_t nsel = 0, rounds = 0, P = round_pairs(N, A.has_recomb);
         if (rs.active && N >= 2) {
             // NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically
             const double x = 0.5 * (double)N * (double)(N - 1) * rs.w * cl.sgmax * rs.dt / rs.Vc;
@@ -1202,18 +1372,29 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
             A.pbase[r * (nc + 1) + c + 1] = cnt;
         }
         A.abase[c + 1] = nsel;
+        A.chbase[c + 1] = (nsel + (uint32_t)FINISH_CHUNK - 1u) / (uint32_t)FINISH_CHUNK;
+        cl.nremoved = 0u;
+        if (A.has_recomb) {
+            A.nbase[c + 1] = N;
+            for (int q = 0; q < 5; ++q) A.csum[5 * (size_t)c + q] = 0ll;
+        }
     }
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1)] = 0;
         A.abase[0] = 0;
+        A.chbase[0] = 0;
+        if (A.has_recomb) A.nbase[0] = 0;
         for (int i = 0; i < 3 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
     }
     __syncthreads();
     for (int r = 0; r < R; ++r) block_scan_inplace(A.pbase + r * (nc + 1), nc);
     block_scan_inplace(A.abase, nc);
+    block_scan_inplace(A.chbase, nc);
+    if (A.has_recomb) block_scan_inplace(A.nbase, nc);
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) A.totals[r] = A.pbase[r * (nc + 1) + nc];
         A.totals[MAX_ROUNDS] = A.abase[nc];
+        A.totals[MAX_ROUNDS + 1] = A.chbase[nc];
     }
 }
 
@@ -1240,7 +1421,7 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
             int c = 0;
             bool accept = false, react = false;
             float sgf = 0.f;
-            uint32_t k = 0, ip = 0, iq = 0, chan = 0;
+            uint32_t k = 0, ip = 0, iq = 0, chan = 0, mpos = 0;
             if (valid) {
                 c = cell_of(pb, A.n_cells, g);
                 k = g - __ldg(pb + c);
@@ -1253,6 +1434,10 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                 const uint4* recs = reinterpret_cast<const uint4*>(cell.rec);
                 const uint4 a = recs[2 * ip], b = recs[2 * iq];
                 const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
+                const DevRes& rs = A.res[cell.res];
+                const uint32_t ev_idx = A.abase[c] + (uint32_t)r * round_pairs(N, A.has_recomb) + k;
+                // a member removed earlier in this step (recombination): no collision
+                if (sP < MAXS && sQ < MAXS) {
                 const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
                 const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
                 const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
@@ -1264,12 +1449,13 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                     atomicOr(A.err, (uint32_t)ERR_NONFINITE);
                     sgf = 0.f;
                 }
-                const DevRes& rs = A.res[cell.res];
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
                 accept = st_u32(sp) < sgf / cell.sgmax_f;
-                const uint32_t ev_idx = A.abase[c] + (uint32_t)r * (N >> 1) + k;
                 if (accept && C->n_reactions > 0) {
+                    if (C->has_recomb && recomb_test<float>(A, C, c, r, k, sP, sQ, (double)sgf, chan, mpos)) {
+                        react = true;
+                    } else {
                     const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
                     const uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w};
                     const uint32_t qQ[4] = {qb.x, qb.y, qb.z, qb.w};
@@ -1281,6 +1467,8 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                     const float u_ch = st_u32(sp);
                     react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch,
                                               chan) > 0;
+                    }
+                }
                 }
                 if (!accept) {
                     A.cflag[ev_idx] = 0u;
@@ -1290,7 +1478,7 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
             const uint32_t slot = queue_slot(qsize, accept && !react);
             if (accept && !react) A.qA[slot] = make_uint4((uint32_t)c, k, ip, iq);
             const uint32_t rslot = queue_slot(qsize + 1, react);
-            if (react) A.qB[rslot] = make_uint4((uint32_t)c, k, chan, 0u);
+            if (react) A.qB[rslot] = make_uint4((uint32_t)c, k, chan, mpos);
             // per-cell max of sigma_T g: lanes of one cell combine before the atomic
             const unsigned act = __activemask();
             const int lane = threadIdx.x & 31;
@@ -1327,6 +1515,8 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
             load_rec(recs + L.ip, Pr);
             load_rec(recs + L.iq, Qr);
             const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+            // a member removed earlier in this step (recombination): no collision
+            if (sP < MAXS && sQ < MAXS) {
             double g2d;
             pair_energy<R>(C->pair[sP * MAXS + sQ], amode, Pr.v, Qr.v, g2d, sg);
             if (!(sg <= 1.0e300)) {  // non-finite velocities: report, keep (sigma g)_max
@@ -1351,6 +1541,7 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                     react = reaction_pick_fix(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel,
                                               u_ch, chan) > 0;
                 }
+            }
             }
             if (!accept) {
                 A.cflag[L.ev_idx] = 0u;
@@ -1439,6 +1630,12 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
         const double EvP = evib64(A.lev64, C->sp[sP], Pr.q);
         const double EvQ = evib64(A.lev64, C->sp[sQ], Qr.q);
         if (C->n_reactions > 0) {
+            uint32_t rchan = 0u, mpos = 0u;
+            if (C->has_recomb && recomb_test<R>(A, C, c, r, e.y, sP, sQ, sg, rchan, mpos)) {
+                const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
+                A.qB[slot] = make_uint4((uint32_t)c, e.y, rchan, mpos);
+                continue;
+            }
             Stream sp;
             st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
             st_u64(sp);
@@ -1538,7 +1735,7 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
                 step = rs.step;
                 lcell = cell.lcell;
                 rk = ((uint32_t)r << 24) | e.y;
-                ev_idx = A.abase[cidx] + (uint32_t)r * (cell.n >> 1) + e.y;
+                ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
                 ip = e.z;
                 iq = e.w;
                 recs = reinterpret_cast<uint4*>(cell.rec);
@@ -1787,7 +1984,26 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
             const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
             uint32_t q1[4], q2[4];
             bool done;
-            if (rx.type == HCAO_DISS) {
+            if (rx.type == HCAO_RECOMB) {
+                // RA is B, RB is C; the third body's position came with the queue entry
+                const uint32_t iM = e.w;
+                RecF Mr;
+                load_rec(recs + iM, Mr);
+                float vM[3] = {Mr.v[0], Mr.v[1], Mr.v[2]};
+                done = do_recomb_fix(A, C, rx, vA, vB, vM, spA, spB, (int)(Mr.meta & 0xFFu),
+                                     side ? EvQ : EvP, side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o);
+                lr.aux = (uint32_t)side + 2u * iM;
+                if (done) {
+                    for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; Mr.v[i] = vM[i]; }
+                    RA.meta = (uint32_t)rx.P0;
+                    for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                    RB.meta = SPECIES_NONE;
+                    store_rec(recs + iM, Mr);
+                    reinterpret_cast<uint32_t*>(reinterpret_cast<RecF*>(A.cscratch) + L.ev_idx)[0] =
+                        side ? L.ip : L.iq;
+                    o.ev |= EV_REMOVED;
+                }
+            } else if (rx.type == HCAO_DISS) {
                 done = do_diss_fix(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
                                    vN, o);
                 lr.aux = (uint32_t)mode + (side ? 16u : 0u);
@@ -1842,7 +2058,26 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
         const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
         uint32_t q1[4], q2[4];
         bool done;
-        if (rx.type == HCAO_DISS) {
+        if (rx.type == HCAO_RECOMB) {
+            // RA is B, RB is C; the third body's position came with the queue entry
+            const uint32_t iM = e.w;
+            Rec Mr;
+            load_rec(recs + iM, Mr);
+            double vM[3] = {(double)Mr.v[0], (double)Mr.v[1], (double)Mr.v[2]};
+            done = do_recomb<R>(A, C, rx, vA, vB, vM, spA, spB, (int)(Mr.meta & 0xFFu), side ? EvQ : EvP,
+                                side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o);
+            lr.aux = (uint32_t)side + 2u * iM;
+            if (done) {
+                for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; Mr.v[i] = (R)vM[i]; }
+                RA.meta = (uint32_t)rx.P0;
+                for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                RB.meta = SPECIES_NONE;
+                store_rec(recs + iM, Mr);
+                reinterpret_cast<uint32_t*>(reinterpret_cast<Rec*>(A.cscratch) + L.ev_idx)[0] =
+                    side ? L.ip : L.iq;
+                o.ev |= EV_REMOVED;
+            }
+        } else if (rx.type == HCAO_DISS) {
             done = do_diss<R>(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
                               vN, o);
             lr.aux = (uint32_t)mode + (side ? 16u : 0u);
@@ -1886,38 +2121,126 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
     }
 }
 
+// End of step, in three kernels so that a cell of any size is spread over
+// many CTAs.  The pair slots of each cell are cut into FINISH_CHUNK-slot
+// chunks (prefix chbase, built by k_setup).
+// k_finish_count: per chunk, the event words reduced into the cell's
+// counters, and the number of particles the chunk's reactions created.
 template <class R>
-__global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* cellcnt,
-                                                int ncnt) {
-    using Rec = typename RecOf<R>::T;
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < A.n_res; i += blockDim.x)
-            if (A.res[i].active) A.res[i].step++;
-    }
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < A.n_cells; c += warps) {
+__global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
+    constexpr int NV = 7 + 8;  // acc samp over degen notexec removed created, 8 reactions
+    __shared__ unsigned long long red[8][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nch = A.totals[MAX_ROUNDS + 1];
+    unsigned long long* cellcnt = reinterpret_cast<unsigned long long*>(A.counters);
+    for (uint32_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int c = cell_of(A.chbase, A.n_cells, ch);
         DevCell& cl = A.cells[c];
-        const uint32_t N = cl.n, nsel = cl.nsel, base = A.abase[c];
-        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
-        uint32_t acc = 0, samp = 0, over = 0, degen = 0, notex = 0, created = 0;
+        const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
+        const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
+        const uint32_t base = A.abase[c];
+        unsigned long long v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = 0ull;
         unsigned long long trials = 0;
-        uint32_t rxc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t j0 = 0; j0 < nsel; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            const uint32_t ev = j < nsel ? A.cflag[base + j] : 0u;
-            acc += ev & EV_ACC;
-            samp += (ev >> EV_SAMP_SHIFT) & 3u;
-            over += (ev >> EV_OVER_SHIFT) & 3u;
-            degen += (ev >> EV_DEGEN_SHIFT) & 3u;
-            notex += (ev & EV_NOTEXEC) ? 1u : 0u;
+        for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const uint32_t ev = A.cflag[base + j];
+            v[0] += ev & EV_ACC;
+            v[1] += (ev >> EV_SAMP_SHIFT) & 3u;
+            v[2] += (ev >> EV_OVER_SHIFT) & 3u;
+            v[3] += (ev >> EV_DEGEN_SHIFT) & 3u;
+            v[4] += (ev & EV_NOTEXEC) ? 1u : 0u;
+            v[5] += (ev & EV_REMOVED) ? 1u : 0u;
+            v[6] += (ev & EV_CREATED) ? 1u : 0u;
             trials += ev >> EV_TRIAL_SHIFT;
             const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
-            if (rxid > 0 && rxid <= 8) rxc[rxid - 1]++;
-            const bool cr = (ev & EV_CREATED) != 0u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[7 + i] += rxid == (uint32_t)(i + 1) ? 1u : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            unsigned long long x = v[q];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+            if (lane == 0) red[wid][q] = x;
+        }
+        for (int o = 16; o > 0; o >>= 1) trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
+        __shared__ unsigned long long tred[8];
+        if (lane == 0) tred[wid] = trials;
+        __syncthreads();
+        if (threadIdx.x < NV + 1) {
+            unsigned long long x = 0;
+            const int nw = (int)(blockDim.x >> 5);
+            if (threadIdx.x < NV)
+                for (int w = 0; w < nw; ++w) x += red[w][threadIdx.x];
+            else
+                for (int w = 0; w < nw; ++w) x += tred[w];
+            unsigned long long* cc = cellcnt + (size_t)c * NCNT;
+            switch (threadIdx.x) {
+                case 0: if (x) atomicAdd(cc + CNT_ACC, x); break;
+                case 1: if (x) atomicAdd(cc + CNT_SAMPLES, x); break;
+                case 2: if (x) atomicAdd(cc + CNT_OVER, x); break;
+                case 3: if (x) atomicAdd(cc + CNT_DEGEN, x); break;
+                case 4: if (x) atomicAdd(cc + CNT_NOTEXEC, x); break;
+                case 5: if (x) atomicAdd(&cl.nremoved, (uint32_t)x); break;
+                case 6:
+                    A.chcnt[ch] = (uint32_t)x;
+                    if (x) atomicAdd(&cl.ncreated, (uint32_t)x);
+                    break;
+                case NV: if (x) atomicAdd(cc + CNT_TRIALS, x); break;
+                default:
+                    if (x && threadIdx.x - 7 < NCNT - CNT_RX0) atomicAdd(cc + CNT_RX0 + (threadIdx.x - 7), x);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// k_finish_append: particles created by dissociation, appended after the
+// cell's step-start particles in pair order (a block-wide scan per chunk on
+// top of the created counts of the cell's earlier chunks).
+template <class R>
+__global__ void __launch_bounds__(256) k_finish_append(StepArgs A) {
+    using Rec = typename RecOf<R>::T;
+    __shared__ uint32_t wsum[8];
+    __shared__ uint32_t sbefore;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nch = A.totals[MAX_ROUNDS + 1];
+    for (uint32_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        if (A.chcnt[ch] == 0u) continue;  // uniform over the CTA
+        const int c = cell_of(A.chbase, A.n_cells, ch);
+        const DevCell& cl = A.cells[c];
+        const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
+        const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
+        const uint32_t base = A.abase[c];
+        // created in the cell's earlier chunks
+        uint32_t b = 0;
+        for (uint32_t q = A.chbase[c] + threadIdx.x; q < ch; q += blockDim.x) b += A.chcnt[q];
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        if (lane == 0) wsum[wid] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+            sbefore = t;
+        }
+        __syncthreads();
+        uint32_t run = sbefore;
+        const uint32_t N = cl.n;
+        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
+        for (uint32_t t0 = j0; t0 < j1; t0 += blockDim.x) {
+            const uint32_t j = t0 + threadIdx.x;
+            const bool cr = j < j1 && (A.cflag[base + j] & EV_CREATED) != 0u;
             const unsigned m = __ballot_sync(0xFFFFFFFFu, cr);
+            __syncthreads();
+            if (lane == 0) wsum[wid] = (uint32_t)__popc(m);
+            __syncthreads();
+            uint32_t off = 0, tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (w < wid) off += wsum[w];
+                tot += wsum[w];
+            }
             if (cr) {
-                const uint32_t dst = N + created + __popc(m & ((1u << lane) - 1u));
+                const uint32_t dst = N + run + off + (uint32_t)__popc(m & ((1u << lane) - 1u));
                 if (dst < cl.cap) {
                     Rec t;
                     load_rec(reinterpret_cast<const Rec*>(A.cscratch) + base + j, t);
@@ -1926,32 +2249,189 @@ __global__ void __launch_bounds__(256) k_finish(StepArgs A, unsigned long long* 
                     atomicOr(A.err, (uint32_t)ERR_CAPACITY);
                 }
             }
-            created += __popc(m);
+            run += tot;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            samp += __shfl_xor_sync(0xFFFFFFFFu, samp, o);
-            over += __shfl_xor_sync(0xFFFFFFFFu, over, o);
-            degen += __shfl_xor_sync(0xFFFFFFFFu, degen, o);
-            notex += __shfl_xor_sync(0xFFFFFFFFu, notex, o);
-            trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
+        __syncthreads();
+    }
+}
+
+// k_cellupd: per cell, candidate count, (sigma g)_max update and the new
+// particle count; per reservoir, the step counter.
+static __global__ void __launch_bounds__(256) k_cellupd(StepArgs A) {
+    unsigned long long* cellcnt = reinterpret_cast<unsigned long long*>(A.counters);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < A.n_res; i += blockDim.x)
+            if (A.res[i].active) A.res[i].step++;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < A.n_cells; c += gridDim.x * blockDim.x) {
+        DevCell& cl = A.cells[c];
+        cellcnt[(size_t)c * NCNT + CNT_CAND] += cl.nsel;
+        const double seen = __longlong_as_double((long long)cl.seen);
+        if (seen > cl.sgmax) cl.sgmax = seen;
+        const uint32_t n = cl.n + cl.ncreated;
+        cl.n = n < cl.cap ? n : cl.cap;
+    }
+}
+
+// Recombination, before the rounds: per-cell integer sums of the kinetic
+// energy (2^-96 J), momentum (2^-104 kg m/s) and mass (2^-120 kg) of the
+// particles present at the step start, for the cell temperature.  Flat over
+// particles in chunks; a chunk inside one cell reduces over the CTA, lanes of
+// one cell otherwise combine per warp before the atomics.
+template <class R>
+__global__ void __launch_bounds__(256) k_cellstats(StepArgs A) {
+    using Rec = typename RecOf<R>::T;
+    constexpr uint32_t CH = 4096;
+    __shared__ long long red[8][5];
+    const uint32_t total = A.nbase[A.n_cells];
+    const Consts* __restrict__ C = A.C;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (uint32_t b0 = blockIdx.x * CH; b0 < total; b0 += gridDim.x * CH) {
+        const uint32_t end = min(b0 + CH, total);
+        const int c_lo = cell_of(A.nbase, A.n_cells, b0);
+        const int c_hi = cell_of(A.nbase, A.n_cells, end - 1);
+        long long acc[5] = {0ll, 0ll, 0ll, 0ll, 0ll};
+        for (uint32_t j0 = b0; j0 < end; j0 += blockDim.x) {
+            const uint32_t j = j0 + threadIdx.x;
+            const bool valid = j < end;
+            int c = c_lo;
+            long long v5[5] = {0ll, 0ll, 0ll, 0ll, 0ll};
+            if (valid) {
+                if (c_lo != c_hi) c = cell_of(A.nbase, A.n_cells, j);
+                const Rec* recs = reinterpret_cast<const Rec*>(A.cells[c].rec);
+                Rec rr;
+                load_rec(recs + (j - __ldg(A.nbase + c)), rr);
+                const DevSpecies& S = C->sp[min(rr.meta & 0xFFu, (uint32_t)(MAXS - 1))];
+                if constexpr (std::is_same<R, double>::value) {
+                    const double m = S.mass;
+                    const double e = 0.5 * m * (rr.v[0] * rr.v[0] + rr.v[1] * rr.v[1] + rr.v[2] * rr.v[2]);
+                    v5[0] = __double2ll_rn(e * 0x1p96);
+                    v5[1] = __double2ll_rn((m * rr.v[0]) * 0x1p104);
+                    v5[2] = __double2ll_rn((m * rr.v[1]) * 0x1p104);
+                    v5[3] = __double2ll_rn((m * rr.v[2]) * 0x1p104);
+                    v5[4] = __double2ll_rn(m * 0x1p120);
+                } else {
+                    const float m = S.mass_f;
+                    const float e = 0.5f * m * (rr.v[0] * rr.v[0] + rr.v[1] * rr.v[1] + rr.v[2] * rr.v[2]);
+                    v5[0] = __float2ll_rn(e * 0x1p96f);
+                    v5[1] = __float2ll_rn((m * rr.v[0]) * 0x1p104f);
+                    v5[2] = __float2ll_rn((m * rr.v[1]) * 0x1p104f);
+                    v5[3] = __float2ll_rn((m * rr.v[2]) * 0x1p104f);
+                    v5[4] = __float2ll_rn(m * 0x1p120f);
+                }
+            }
+            if (c_lo == c_hi) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) rxc[i] += __shfl_xor_sync(0xFFFFFFFFu, rxc[i], o);
+                for (int q = 0; q < 5; ++q) acc[q] += v5[q];
+                continue;
+            }
+            // several cells in the chunk: lanes of one cell combine, then one atomic each
+            const unsigned act = __activemask();
+            const int key = valid ? c : -1;
+            unsigned left = __ballot_sync(act, valid);
+            while (left) {
+                const int leader = __ffs(left) - 1;
+                const int cl = __shfl_sync(act, key, leader);
+                const unsigned grp = __ballot_sync(act, key == cl);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    long long x = key == cl ? v5[q] : 0ll;
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(act, x, o);
+                    if (lane == leader)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(A.csum + 5 * (size_t)cl + q),
+                                  (unsigned long long)x);
+                }
+                left &= ~grp;
+            }
         }
-        if (lane == 0) {
-            unsigned long long* cc = cellcnt + (size_t)c * NCNT;
-            cc[CNT_CAND] += nsel;
-            cc[CNT_ACC] += acc;
-            cc[CNT_SAMPLES] += samp;
-            cc[CNT_TRIALS] += trials;
-            cc[CNT_OVER] += over;
-            cc[CNT_DEGEN] += degen;
-            cc[CNT_NOTEXEC] += notex;
-            for (int i = 0; i < 8 && i < ncnt - CNT_RX0; ++i) cc[CNT_RX0 + i] += rxc[i];
-            const double seen = __longlong_as_double((long long)cl.seen);
-            if (seen > cl.sgmax) cl.sgmax = seen;
-            cl.n = N + created < cl.cap ? N + created : cl.cap;
-            cl.ncreated = created;
+        if (c_lo == c_hi) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                long long x = acc[q];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+                if (lane == 0) red[wid][q] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x < 5) {
+                long long x = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][threadIdx.x];
+                atomicAdd(reinterpret_cast<unsigned long long*>(A.csum + 5 * (size_t)c_lo + threadIdx.x),
+                          (unsigned long long)x);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Recombination, after k_finish: remove the particles marked removed.  With
+// d removed among a cell's n records, the surviving records at positions
+// >= n - d move, in increasing position order, into the removed positions
+// below n - d, taken in increasing order.  One CTA per cell with removals:
+// the removed positions (kept in the pairs' scratch slots) are gathered and
+// sorted in shared memory.
+template <class R>
+__global__ void __launch_bounds__(256) k_compact(StepArgs A) {
+    using Rec = typename RecOf<R>::T;
+    __shared__ uint32_t pos[MAX_REMOVALS];
+    __shared__ uint32_t cnt;
+    for (int c = blockIdx.x; c < A.n_cells; c += gridDim.x) {
+        DevCell& cl = A.cells[c];
+        const uint32_t d = cl.nremoved;
+        if (d == 0u) continue;
+        __syncthreads();
+        if (d > (uint32_t)MAX_REMOVALS) {
+            if (threadIdx.x == 0) atomicOr(A.err, (uint32_t)ERR_CAPACITY);
+            continue;
+        }
+        const uint32_t nsel = cl.nsel, base = A.abase[c];
+        if (threadIdx.x == 0) cnt = 0u;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < nsel; j += blockDim.x)
+            if (A.cflag[base + j] & EV_REMOVED) {
+                const uint32_t slot = atomicAdd(&cnt, 1u);
+                if (slot < (uint32_t)MAX_REMOVALS)
+                    pos[slot] = reinterpret_cast<const uint32_t*>(reinterpret_cast<const Rec*>(A.cscratch) +
+                                                                  base + j)[0];
+            }
+        __syncthreads();
+        uint32_t P = 1;
+        while (P < d) P <<= 1;
+        for (uint32_t i = d + threadIdx.x; i < P; i += blockDim.x) pos[i] = 0xFFFFFFFFu;
+        __syncthreads();
+        // bitonic sort of pos[0, P)
+        for (uint32_t kk = 2; kk <= P; kk <<= 1)
+            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    const uint32_t l = i ^ jj;
+                    if (l > i) {
+                        const uint32_t a = pos[i], b = pos[l];
+                        const bool up = (i & kk) == 0;
+                        if ((a > b) == up) { pos[i] = b; pos[l] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        const uint32_t n = cl.n, t0 = n - d;
+        // holes: removed positions below t0 (the first h0 sorted entries)
+        uint32_t lo = 0, hi = d;
+        while (lo < hi) { const uint32_t mid = (lo + hi) >> 1; if (pos[mid] < t0) lo = mid + 1; else hi = mid; }
+        const uint32_t h0 = lo;
+        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
+        for (uint32_t i = threadIdx.x; i < d; i += blockDim.x) {
+            const uint32_t t = t0 + i;
+            uint32_t a = 0, b = d;  // removed positions < t
+            while (a < b) { const uint32_t mid = (a + b) >> 1; if (pos[mid] < t) a = mid + 1; else b = mid; }
+            if (a < d && pos[a] == t) continue;
+            const uint32_t rank = i - (a - h0);
+            if (rank < h0) {
+                Rec tmp;
+                load_rec(recs + t, tmp);
+                store_rec(recs + pos[rank], tmp);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cl.n = t0;
+            cl.nremoved = 0u;
         }
     }
 }
@@ -1976,15 +2456,30 @@ void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStre
 }
 template <class R>
 void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
-    const int g = (a.n_cells + 7) / 8 < 1184 ? (a.n_cells + 7) / 8 : 1184;
-    k_finish<R><<<g < 1 ? 1 : g, 256, 0, s>>>(a, reinterpret_cast<unsigned long long*>(a.counters), NCNT);
+    k_finish_count<R><<<1184, 256, 0, s>>>(a);
+    if (a.creates) k_finish_append<R><<<1184, 256, 0, s>>>(a);
+    const int g = (a.n_cells + 255) / 256 < 148 ? (a.n_cells + 255) / 256 : 148;
+    k_cellupd<<<g < 1 ? 1 : g, 256, 0, s>>>(a);
+}
+template <class R>
+void launch_cellstats_impl(const StepArgs& a, cudaStream_t s) {
+    if (a.has_recomb) k_cellstats<R><<<1184, 256, 0, s>>>(a);
+}
+template <class R>
+void launch_compact_impl(const StepArgs& a, cudaStream_t s) {
+    if (!a.has_recomb) return;
+    const int g = a.n_cells < 1184 ? a.n_cells : 1184;
+    k_compact<R><<<g < 1 ? 1 : g, 256, 0, s>>>(a);
 }
 template <class R>
 void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, uint64_t* launches) {
     launch_setup(a, s);
+    launch_cellstats_impl<R>(a, s);
     for (int r = 0; r < a.max_rounds; ++r) launch_collide_impl<R>(a, r, grid, block, s);
     launch_finish_impl<R>(a, s);
-    if (launches) *launches += 2 + a.max_rounds * (a.has_reactions ? 3 : 2);
+    launch_compact_impl<R>(a, s);
+    if (launches)
+        *launches += 3 + a.max_rounds * (a.has_reactions ? 3 : 2) + (a.has_recomb ? 2 : 0) + (a.creates ? 1 : 0);
 }
 
 // ------------------------------------------------------------- sampler diagnostics
@@ -2097,6 +2592,7 @@ __global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const u
         Rec r;
         load_rec(recs + i, r);
         const int s = (int)(r.meta & 0xFFu);
+        if (s >= MAXS) continue;  // a removed particle left by a failed compaction (error reported)
         const DevSpecies& S = C->sp[s];
         Stream st;
         st_init(st, rs.seed, 0xFFFFFFFFu, cl.lcell, i, PU_INIT);
@@ -2144,6 +2640,7 @@ __global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const ui
         Rec r;
         load_rec(recs + (j - off[c]), r);
         const int s = (int)(r.meta & 0xFFu);
+        if (s >= MAXS) continue;  // a removed particle left by a failed compaction (error reported)
         const DevSpecies& S = C->sp[s];
         const double m = S.mass;
         const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
@@ -2194,6 +2691,10 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, const u
     }                                                                                            \
     template <>                                                                                  \
     void launch_finish<R>(const StepArgs& a, cudaStream_t s) { launch_finish_impl<R>(a, s); }    \
+    template <>                                                                                  \
+    void launch_cellstats<R>(const StepArgs& a, cudaStream_t s) { launch_cellstats_impl<R>(a, s); } \
+    template <>                                                                                  \
+    void launch_compact<R>(const StepArgs& a, cudaStream_t s) { launch_compact_impl<R>(a, s); }  \
     template <>                                                                                  \
     void launch_phase<R>(const StepArgs& a, int r, int phase, int grid, cudaStream_t s) {        \
         launch_phase_impl<R>(a, r, phase, grid, s);                                              \

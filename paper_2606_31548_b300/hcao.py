@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhcao.so")
 
 FP64, FP32 = 0, 1
-DISS, EXCH = 1, 2
+DISS, EXCH, RECOMB = 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
           -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND",
           -10: "ENONFINITE"}
@@ -31,8 +31,10 @@ EXPORTS = [
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
-    "hcao_serve_stop", "hcao_serve_stats",
+    "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate",
 ]
+REC_NODES = 225
+MAX_REMOVALS_PER_CELL = 4096
 NOALLOC_SORT_MAX_KEYS = 1 << 19
 
 
@@ -138,6 +140,7 @@ def lib() -> C.CDLL:
         L.hcao_serve_poll.argtypes = [vp, u64, C.POINTER(JobResult)]
         L.hcao_serve_stop.argtypes = [vp]
         L.hcao_serve_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(u64)]
+        L.hcao_recomb_rate.argtypes = [vp, i32, i32, dbl, C.POINTER(dbl)]
         L.hcao_kernel_launches.argtypes = [vp]
         L.hcao_kernel_launches.restype = u64
         _lib = L
@@ -217,7 +220,7 @@ class Context:
         keep = []
         for i, r in enumerate(reactions):
             d = arr[i]
-            d.type = DISS if r.type == "diss" else EXCH
+            d.type = {"diss": DISS, "exch": EXCH, "recomb": RECOMB}[r.type]
             rc = list(r.reactants) + [-1] * (2 - len(r.reactants))
             d.reactants[0], d.reactants[1] = rc[0], rc[1]
             d.products[0], d.products[1] = r.products[0], r.products[1]
@@ -357,6 +360,12 @@ class Context:
 
     def kernel_launches(self) -> int:
         return int(self.L.hcao_kernel_launches(self.h))
+
+    def recomb_rate(self, reaction, spM, T) -> float:
+        """The tabulated k_r (m^6/s) of a recombination with third-body species spM at T."""
+        out = C.c_double()
+        self._chk(self.L.hcao_recomb_rate(self.h, reaction, spM, T, C.byref(out)))
+        return out.value
 
     # -- serving (continuous batching of reservoir jobs)
     def serve_start(self, hbm_budget_bytes=0, max_active=0, max_batch_steps=0) -> None:

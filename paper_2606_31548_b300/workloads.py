@@ -180,6 +180,23 @@ def ch4_h_exchange(n_cells: int = 16384, per_cell: int = 1200, steps: int = 2000
                   T0, T0, seed, steps)
 
 
+def ch4_recombination(n_cells: int = 8, per_cell: int = 2000, steps: int = 500,
+                      seed: int = 0x48434136, T0: float = 4000.0, n_density: float = 3e23,
+                      fractions=(1.0, 1.0, 1.0), recombination: bool = True) -> Workload:
+    """CH4 + M <-> CH3 + H + M (the paper's methane dissociation-recombination
+    case, Sec. "Verification"): CH4 : CH3 : H in the given proportions at total
+    number density n_density, T_tr0 = T_vib0 = T0, dissociation on all four
+    C-H stretches and its recombination; dt = 0.2 / nu(T0) of CH4 at that
+    density."""
+    sp = [ch4_like(), ch3_like(), h_atom()]
+    rx = [Reaction("diss", [0], [1, 2], diss_mode_mask=0xF)]
+    if recombination:
+        rx.append(Reaction("recomb", [1, 2], [0, -1], diss_mode_mask=0xF))
+    dt = 0.2 / vhs_collision_frequency(sp[0], n_density, T0)
+    return _build("ch4_recombination", sp, rx, n_cells, np.full(n_cells, per_cell), list(fractions),
+                  4.64e-6, n_density, dt, T0, T0, seed, steps)
+
+
 def random_levels(rng: np.random.Generator, n: int, n_levels: List[int], n_modes: int) -> np.ndarray:
     """Uniformly random valid quantum numbers for load-path tests (no physics)."""
     q = np.zeros((n, 16), dtype=np.uint8)

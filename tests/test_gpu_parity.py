@@ -141,6 +141,14 @@ def test_parity_ch4_dissociation():
     assert g.count(0) > 24 * 250
 
 
+def test_parity_dissociation_single_large_cell():
+    """One 20,000-particle cell at 15000 K: the end-of-step kernels spread the
+    cell's pair slots over several chunks; created particles still follow in
+    pair order."""
+    g, o = _run_parity(W.ch4_heat_bath(n_cells=1, per_cell=20000), 3)
+    assert g.read_reaction_counts(0, 1)[0] > 50
+
+
 def test_parity_exchange():
     g, o = _run_parity(W.ch4_h_exchange(n_cells=12, per_cell=400, T0=6000.0), 8)
     assert g.read_reaction_counts(0, 1)[0] > 10
