@@ -208,6 +208,34 @@ def cpu_baseline(budget_s: float = 12.0, cells: int = 48):
                       f"single-threaded FP64 C oracle, {dt:.1f} s"}
 
 
+def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> dict:
+    """Device throughput of one more configuration: `warmup` untimed steps,
+    then `steps` steps timed one by one with CUDA events (L2 flushed before
+    each); particle-steps counted from the particles entering each step."""
+    ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream)
+    for _ in range(warmup):
+        ctx.step(1)
+    ctx.sync()
+    c0 = ctx.read_counters(0)
+    ms, ps = 0.0, 0
+    for _ in range(steps):
+        ps += ctx.count(0)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.step(1)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    c1 = ctx.read_counters(0)
+    ctx.close()
+    t = ms / 1e3
+    return {"workload": w.name, "particles": int(w.n), "cells": int(w.n_cells), "T0_K": w.T_tr0,
+            "precision": "fp64" if prec == hcao.FP64 else "fp32", "steps": steps, "warmup": warmup,
+            "particle_steps_per_s": ps / t, "collisions_per_s": float(c1[1] - c0[1]) / t,
+            "reactions_per_s": float(sum(c1[8:]) - sum(c0[8:])) / t, "ms_per_step": 1e3 * t / steps}
+
+
 def run_batched(hcao, torch, prec, stream, n_res: int, steps: int):
     """Many independent single-cell reservoirs (particle counts log-uniform
     10k-2M, T uniform 5000-30000 K, triatomic or CH4-like): all in one context
@@ -373,6 +401,7 @@ def main():
     ap.add_argument("--batched-res", type=int, default=256, help="reservoirs of the batched run (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=12)
     ap.add_argument("--served-jobs", type=int, default=48, help="jobs of the served run (0: skip)")
+    ap.add_argument("--other-configs", type=int, default=1, help="measure the triatomic and exchange configs too")
     ap.add_argument("--served-rate", type=float, default=50.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -502,9 +531,19 @@ def main():
     if args.batched_res > 0 and ws == 1:
         ctx.close()
         batched = run_batched(hcao, torch, prec, stream, args.batched_res, args.batched_steps)
+    others = None
+    if args.other_configs and ws == 1:
+        flush2 = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        others = {
+            "triatomic_relaxation_20000x1_fp64": run_config(
+                hcao, torch, stream, W.relaxation_triatomic(), hcao.FP64, 50, 5, flush2),
+            "ch4_h_exchange_16384x1200_4000K_fp32": run_config(
+                hcao, torch, stream, W.ch4_h_exchange(T0=4000.0), hcao.FP32, 10, 3, flush2),
+        }
+        del flush2
     served = None
     if args.served_jobs > 0 and ws == 1:
-        served = run_served(hcao, prec, stream, args.served_jobs, args.served_rate, recombination=False)
+        served = run_served(hcao, prec, stream, args.served_jobs, args.served_rate, recombination=True)
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline()
@@ -522,7 +561,7 @@ def main():
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served,
+            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served, "other_configs": others,
         }
         print(json.dumps(line))
     if ws > 1:

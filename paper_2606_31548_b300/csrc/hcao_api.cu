@@ -1073,26 +1073,59 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "load_particles: no such reservoir");
     if (n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!v || !qn || !species || !cell)))
         return fail(ctx, HCAO_EINVAL, "load_particles: bad arguments");
-    // validate on the host: cell and species ranges, levels inside each mode's list
-    bool present[MAXS] = {};
-    std::vector<uint32_t> counts(r->n_cells, 0);
-    for (int64_t i = 0; i < n; ++i) {
-        if (cell[i] < 0 || cell[i] >= r->n_cells) return fail(ctx, HCAO_EINVAL, "load_particles: cell out of range");
-        if (species[i] < 0 || species[i] >= ctx->n_species)
-            return fail(ctx, HCAO_EINVAL, "load_particles: species out of range");
-        const HostSpecies& s = ctx->sp[species[i]];
-        for (int j = 0; j < 16; ++j) {
-            const int q = qn[16 * i + j];
-            if (j < s.n_modes ? q >= (int)s.lev[j].size() : q != 0)
-                return fail(ctx, HCAO_ELEVEL_OVERFLOW, "load_particles: quantum number outside the level list");
-        }
-        present[species[i]] = true;
-        counts[cell[i]]++;
-    }
     CU(cudaStreamSynchronize(ctx->stream));
     if (r->recs) {
         cudaFreeAsync(r->recs, ctx->stream);
         r->recs = nullptr;
+    }
+    // stage the host arrays; validate and count on the device (a sort by cell
+    // gives the per-cell counts); host work stays O(cells)
+    double* dv = nullptr;
+    uint8_t* dq = nullptr;
+    int32_t* ds = nullptr;
+    uint32_t *dk = nullptr, *dperm = nullptr, *doff = nullptr, *dflags = nullptr;
+    uint64_t* dslot = nullptr;
+    auto release = [&]() {
+        dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dk);
+        dfree(ctx, dperm); dfree(ctx, doff); dfree(ctx, dslot); dfree(ctx, dflags);
+    };
+    std::vector<uint32_t> off((size_t)r->n_cells + 1, 0u);
+    uint32_t flags[2] = {0u, 0u};
+    if (n > 0) {
+        CU(dalloc(ctx, &dv, (size_t)n * 3));
+        CU(dalloc(ctx, &dq, (size_t)n * 16));
+        CU(dalloc(ctx, &ds, (size_t)n));
+        CU(dalloc(ctx, &dk, (size_t)n));
+        CU(dalloc(ctx, &dperm, (size_t)n));
+        CU(dalloc(ctx, &doff, (size_t)r->n_cells + 1));
+        CU(dalloc(ctx, &dslot, (size_t)r->n_cells));
+        CU(dalloc(ctx, &dflags, 2));
+        CU(cudaMemsetAsync(dflags, 0, 2 * sizeof(uint32_t), ctx->stream));
+        CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        launch_validate_load(ctx->d_consts, r->n_cells, reinterpret_cast<const int32_t*>(dk), ds, dq, n, dflags,
+                             ctx->stream);
+        ctx->launches++;
+        CU(cudaMemcpyAsync(flags, dflags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (flags[0] & (LOAD_BAD_CELL | LOAD_BAD_SPECIES)) {
+            release();
+            return fail(ctx, HCAO_EINVAL, (flags[0] & LOAD_BAD_CELL) ? "load_particles: cell out of range"
+                                                                     : "load_particles: species out of range");
+        }
+        if (flags[0] & LOAD_BAD_LEVEL) {
+            release();
+            return fail(ctx, HCAO_ELEVEL_OVERFLOW, "load_particles: quantum number outside the level list");
+        }
+        hcao_status st = hcao_cell_sort(ctx, dk, n, (uint32_t)r->n_cells, dperm, doff);
+        if (st != HCAO_OK) {
+            release();
+            return st;
+        }
+        CU(cudaMemcpyAsync(off.data(), doff, sizeof(uint32_t) * off.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
     }
     // capacities and slot bases
     const double f = ctx->cfg.capacity_factor;
@@ -1102,18 +1135,19 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     double mx = 0.0;
     for (int a = 0; a < ctx->n_species; ++a)
         for (int b = 0; b < ctx->n_species; ++b)
-            if (present[a] && present[b]) {
+            if (((flags[1] >> a) & 1u) && ((flags[1] >> b) & 1u)) {
                 const double m = mean_sigma_g(ctx, a, b, r->T_sgmax);
                 if (m > mx) mx = m;
             }
     for (int c = 0; c < r->n_cells; ++c) {
-        uint64_t cap = (uint64_t)std::ceil(counts[c] * f) + (uint64_t)ctx->cfg.capacity_extra;
+        const uint32_t count = off[c + 1] - off[c];
+        uint64_t cap = (uint64_t)std::ceil(count * f) + (uint64_t)ctx->cfg.capacity_extra;
         cap = (cap + 7) & ~(uint64_t)7;
         slot0[c] = tot;
         tot += cap;
         DevCell& d = cells[c];
         std::memset(&d, 0, sizeof d);
-        d.n = counts[c];
+        d.n = count;
         d.cap = (uint32_t)cap;
         d.res = (uint32_t)id;
         d.lcell = (uint32_t)c;
@@ -1127,34 +1161,15 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     for (int c = 0; c < r->n_cells; ++c)
         cells[c].rec = static_cast<char*>(r->recs) + slot0[c] * rs;
     if (n > 0) {
-        // stage the host arrays, sort by cell on the device, scatter into the cells
-        double* dv = nullptr;
-        uint8_t* dq = nullptr;
-        int32_t* ds = nullptr;
-        uint32_t *dk = nullptr, *dperm = nullptr, *doff = nullptr;
-        uint64_t* dslot = nullptr;
-        CU(dalloc(ctx, &dv, (size_t)n * 3));
-        CU(dalloc(ctx, &dq, (size_t)n * 16));
-        CU(dalloc(ctx, &ds, (size_t)n));
-        CU(dalloc(ctx, &dk, (size_t)n));
-        CU(dalloc(ctx, &dperm, (size_t)n));
-        CU(dalloc(ctx, &doff, (size_t)r->n_cells + 1));
-        CU(dalloc(ctx, &dslot, (size_t)r->n_cells));
-        CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        // scatter the staged particles into their cells' slots in sorted order
         CU(cudaMemcpyAsync(dslot, slot0.data(), sizeof(uint64_t) * r->n_cells, cudaMemcpyHostToDevice, ctx->stream));
-        hcao_status st = hcao_cell_sort(ctx, dk, n, (uint32_t)r->n_cells, dperm, doff);
-        if (st != HCAO_OK) return st;
         if (ctx->cfg.precision == HCAO_FP64)
             launch_scatter_load<double>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
         else
             launch_scatter_load<float>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
         ctx->launches++;
         CU(cudaGetLastError());
-        dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dk);
-        dfree(ctx, dperm); dfree(ctx, doff); dfree(ctx, dslot);
+        release();
     }
     r->loaded = true;
     hcao_status st = relayout(ctx, id, &cells);

@@ -19,7 +19,7 @@ constexpr int TABLE_PAD = 17;   // grid entries beyond M (one per mode + 1)
 constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard cap)
 constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)
 constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
-constexpr int FINISH_CHUNK = 2048;  // pair slots per work item of the end-of-step kernels
+constexpr int FINISH_CHUNK = 1024;  // pair slots per warp of the end-of-step kernels
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
@@ -28,6 +28,9 @@ enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SC
 // per-reservoir counters
 enum { CNT_CAND = 0, CNT_ACC, CNT_SAMPLES, CNT_TRIALS, CNT_OVER, CNT_DEGEN, CNT_NOTEXEC,
        CNT_STEPS, CNT_RX0 = 8, NCNT = 8 + MAXR };
+
+// load-path validation bits
+enum { LOAD_BAD_CELL = 1, LOAD_BAD_SPECIES = 2, LOAD_BAD_LEVEL = 4 };
 
 // sticky device error bits
 enum { ERR_REJECT = 1, ERR_CAPACITY = 2, ERR_ROUNDS = 4, ERR_LEVEL = 8, ERR_NONFINITE = 16 };
@@ -162,6 +165,8 @@ template <> struct RecOf<double> { using T = RecD; };
 template <class R> void launch_step(const StepArgs& a, int grid_collide, int block_collide,
                                     cudaStream_t s, uint64_t* launches);
 void launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu)
+void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, const int32_t* sp,
+                          const uint8_t* qn, int64_t n, uint32_t* flags, cudaStream_t s);
 template <class R> void launch_collide(const StepArgs& a, int r, int grid, int block, cudaStream_t s);
 // phase k of round r: 0 select, 1 relax, 2 react (for per-kernel timing)
 template <class R> void launch_phase(const StepArgs& a, int r, int phase, int grid, cudaStream_t s);

@@ -1399,6 +1399,45 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
 }
 
 void launch_setup(const StepArgs& a, cudaStream_t s) { k_setup<<<1, SETUP_THREADS, 0, s>>>(a); }
+
+// Load-path validation of staged host arrays: cell and species in range,
+// every quantum number inside its mode's level list (0 beyond the species'
+// modes).  flags[0] collects LOAD_BAD_* bits, flags[1] the species present.
+static __global__ void __launch_bounds__(256) k_validate_load(const Consts* C, int n_cells, const int32_t* cell,
+                                                              const int32_t* sp, const uint8_t* qn, int64_t n,
+                                                              uint32_t* flags) {
+    uint32_t bad = 0u, present = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cell[i], s = sp[i];
+        if (c < 0 || c >= n_cells) bad |= LOAD_BAD_CELL;
+        if (s < 0 || s >= C->n_species) {
+            bad |= LOAD_BAD_SPECIES;
+            continue;
+        }
+        present |= 1u << s;
+        const uint4 q4 = reinterpret_cast<const uint4*>(qn)[i];
+        const uint32_t q[4] = {q4.x, q4.y, q4.z, q4.w};
+        const DevSpecies& S = C->sp[s];
+        for (int j = 0; j < MAXM; ++j) {
+            const uint32_t v = get_q(q, j);
+            if (j < S.n_modes ? v >= (uint32_t)S.n_lev[j] : v != 0u) bad |= LOAD_BAD_LEVEL;
+        }
+    }
+    bad = __reduce_or_sync(0xFFFFFFFFu, bad);
+    present = __reduce_or_sync(0xFFFFFFFFu, present);
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicOr(flags, bad);
+        if (present) atomicOr(flags + 1, present);
+    }
+}
+
+void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, const int32_t* sp, const uint8_t* qn,
+                          int64_t n, uint32_t* flags, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t g = (n + 255) / 256;
+    if (g > 2368) g = 2368;
+    k_validate_load<<<(int)g, 256, 0, s>>>(C, n_cells, cell, sp, qn, n, flags);
+}
 #endif
 
 // Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
@@ -2122,125 +2161,100 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
 }
 
 // End of step, in three kernels so that a cell of any size is spread over
-// many CTAs.  The pair slots of each cell are cut into FINISH_CHUNK-slot
-// chunks (prefix chbase, built by k_setup).
+// many warps.  The pair slots of each cell are cut into FINISH_CHUNK-slot
+// chunks (prefix chbase, built by k_setup); one warp takes one chunk, so a
+// cell of 500 particles costs one warp and a cell of 4M about a thousand.
 // k_finish_count: per chunk, the event words reduced into the cell's
 // counters, and the number of particles the chunk's reactions created.
 template <class R>
 __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
-    constexpr int NV = 7 + 8;  // acc samp over degen notexec removed created, 8 reactions
-    __shared__ unsigned long long red[8][NV];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t nch = A.totals[MAX_ROUNDS + 1];
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long* cellcnt = reinterpret_cast<unsigned long long*>(A.counters);
-    for (uint32_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
         const int c = cell_of(A.chbase, A.n_cells, ch);
         DevCell& cl = A.cells[c];
         const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
         const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
         const uint32_t base = A.abase[c];
-        unsigned long long v[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = 0ull;
+        uint32_t acc = 0, samp = 0, over = 0, degen = 0, notex = 0, removed = 0, created = 0;
+        uint32_t rxc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         unsigned long long trials = 0;
-        for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        for (uint32_t j = j0 + lane; j < j1; j += 32) {
             const uint32_t ev = A.cflag[base + j];
-            v[0] += ev & EV_ACC;
-            v[1] += (ev >> EV_SAMP_SHIFT) & 3u;
-            v[2] += (ev >> EV_OVER_SHIFT) & 3u;
-            v[3] += (ev >> EV_DEGEN_SHIFT) & 3u;
-            v[4] += (ev & EV_NOTEXEC) ? 1u : 0u;
-            v[5] += (ev & EV_REMOVED) ? 1u : 0u;
-            v[6] += (ev & EV_CREATED) ? 1u : 0u;
+            acc += ev & EV_ACC;
+            samp += (ev >> EV_SAMP_SHIFT) & 3u;
+            over += (ev >> EV_OVER_SHIFT) & 3u;
+            degen += (ev >> EV_DEGEN_SHIFT) & 3u;
+            notex += (ev & EV_NOTEXEC) ? 1u : 0u;
+            removed += (ev & EV_REMOVED) ? 1u : 0u;
+            created += (ev & EV_CREATED) ? 1u : 0u;
             trials += ev >> EV_TRIAL_SHIFT;
             const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
+            if (rxid > 0 && rxid <= 8) rxc[rxid - 1]++;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+            samp += __shfl_xor_sync(0xFFFFFFFFu, samp, o);
+            over += __shfl_xor_sync(0xFFFFFFFFu, over, o);
+            degen += __shfl_xor_sync(0xFFFFFFFFu, degen, o);
+            notex += __shfl_xor_sync(0xFFFFFFFFu, notex, o);
+            removed += __shfl_xor_sync(0xFFFFFFFFu, removed, o);
+            created += __shfl_xor_sync(0xFFFFFFFFu, created, o);
+            trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[7 + i] += rxid == (uint32_t)(i + 1) ? 1u : 0u;
+            for (int i = 0; i < 8; ++i) rxc[i] += __shfl_xor_sync(0xFFFFFFFFu, rxc[i], o);
         }
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            unsigned long long x = v[q];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-            if (lane == 0) red[wid][q] = x;
+        unsigned long long* cc = cellcnt + (size_t)c * NCNT;
+        // one lane per counter; a cell of one chunk needs no atomics, but its
+        // counters may also receive other chunks' atomics, so all use them
+        switch (lane) {
+            case 0: if (acc) atomicAdd(cc + CNT_ACC, (unsigned long long)acc); break;
+            case 1: if (samp) atomicAdd(cc + CNT_SAMPLES, (unsigned long long)samp); break;
+            case 2: if (over) atomicAdd(cc + CNT_OVER, (unsigned long long)over); break;
+            case 3: if (degen) atomicAdd(cc + CNT_DEGEN, (unsigned long long)degen); break;
+            case 4: if (notex) atomicAdd(cc + CNT_NOTEXEC, (unsigned long long)notex); break;
+            case 5: if (removed) atomicAdd(&cl.nremoved, removed); break;
+            case 6:
+                A.chcnt[ch] = created;
+                if (created) atomicAdd(&cl.ncreated, created);
+                break;
+            case 7: if (trials) atomicAdd(cc + CNT_TRIALS, trials); break;
+            default:
+                if (lane < 16 && rxc[lane - 8] && lane - 8 < NCNT - CNT_RX0)
+                    atomicAdd(cc + CNT_RX0 + (lane - 8), (unsigned long long)rxc[lane - 8]);
         }
-        for (int o = 16; o > 0; o >>= 1) trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
-        __shared__ unsigned long long tred[8];
-        if (lane == 0) tred[wid] = trials;
-        __syncthreads();
-        if (threadIdx.x < NV + 1) {
-            unsigned long long x = 0;
-            const int nw = (int)(blockDim.x >> 5);
-            if (threadIdx.x < NV)
-                for (int w = 0; w < nw; ++w) x += red[w][threadIdx.x];
-            else
-                for (int w = 0; w < nw; ++w) x += tred[w];
-            unsigned long long* cc = cellcnt + (size_t)c * NCNT;
-            switch (threadIdx.x) {
-                case 0: if (x) atomicAdd(cc + CNT_ACC, x); break;
-                case 1: if (x) atomicAdd(cc + CNT_SAMPLES, x); break;
-                case 2: if (x) atomicAdd(cc + CNT_OVER, x); break;
-                case 3: if (x) atomicAdd(cc + CNT_DEGEN, x); break;
-                case 4: if (x) atomicAdd(cc + CNT_NOTEXEC, x); break;
-                case 5: if (x) atomicAdd(&cl.nremoved, (uint32_t)x); break;
-                case 6:
-                    A.chcnt[ch] = (uint32_t)x;
-                    if (x) atomicAdd(&cl.ncreated, (uint32_t)x);
-                    break;
-                case NV: if (x) atomicAdd(cc + CNT_TRIALS, x); break;
-                default:
-                    if (x && threadIdx.x - 7 < NCNT - CNT_RX0) atomicAdd(cc + CNT_RX0 + (threadIdx.x - 7), x);
-            }
-        }
-        __syncthreads();
     }
 }
 
 // k_finish_append: particles created by dissociation, appended after the
-// cell's step-start particles in pair order (a block-wide scan per chunk on
-// top of the created counts of the cell's earlier chunks).
+// cell's step-start particles in pair order: a warp scan per chunk on top of
+// the created counts of the cell's earlier chunks.
 template <class R>
 __global__ void __launch_bounds__(256) k_finish_append(StepArgs A) {
     using Rec = typename RecOf<R>::T;
-    __shared__ uint32_t wsum[8];
-    __shared__ uint32_t sbefore;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const uint32_t nch = A.totals[MAX_ROUNDS + 1];
-    for (uint32_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-        if (A.chcnt[ch] == 0u) continue;  // uniform over the CTA
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
+        if (A.chcnt[ch] == 0u) continue;  // uniform over the warp
         const int c = cell_of(A.chbase, A.n_cells, ch);
         const DevCell& cl = A.cells[c];
         const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
         const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
         const uint32_t base = A.abase[c];
-        // created in the cell's earlier chunks
-        uint32_t b = 0;
-        for (uint32_t q = A.chbase[c] + threadIdx.x; q < ch; q += blockDim.x) b += A.chcnt[q];
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-        if (lane == 0) wsum[wid] = b;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t t = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-            sbefore = t;
-        }
-        __syncthreads();
-        uint32_t run = sbefore;
+        uint32_t run = 0;  // created in the cell's earlier chunks
+        for (uint32_t q = A.chbase[c] + lane; q < ch; q += 32) run += A.chcnt[q];
+        for (int o = 16; o > 0; o >>= 1) run += __shfl_xor_sync(0xFFFFFFFFu, run, o);
         const uint32_t N = cl.n;
         Rec* recs = reinterpret_cast<Rec*>(cl.rec);
-        for (uint32_t t0 = j0; t0 < j1; t0 += blockDim.x) {
-            const uint32_t j = t0 + threadIdx.x;
+        for (uint32_t t0 = j0; t0 < j1; t0 += 32) {
+            const uint32_t j = t0 + lane;
             const bool cr = j < j1 && (A.cflag[base + j] & EV_CREATED) != 0u;
             const unsigned m = __ballot_sync(0xFFFFFFFFu, cr);
-            __syncthreads();
-            if (lane == 0) wsum[wid] = (uint32_t)__popc(m);
-            __syncthreads();
-            uint32_t off = 0, tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                if (w < wid) off += wsum[w];
-                tot += wsum[w];
-            }
             if (cr) {
-                const uint32_t dst = N + run + off + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                const uint32_t dst = N + run + (uint32_t)__popc(m & ((1u << lane) - 1u));
                 if (dst < cl.cap) {
                     Rec t;
                     load_rec(reinterpret_cast<const Rec*>(A.cscratch) + base + j, t);
@@ -2249,9 +2263,8 @@ __global__ void __launch_bounds__(256) k_finish_append(StepArgs A) {
                     atomicOr(A.err, (uint32_t)ERR_CAPACITY);
                 }
             }
-            run += tot;
+            run += (uint32_t)__popc(m);
         }
-        __syncthreads();
     }
 }
 
@@ -2457,7 +2470,7 @@ void launch_collide_impl(const StepArgs& a, int r, int grid, int block, cudaStre
 template <class R>
 void launch_finish_impl(const StepArgs& a, cudaStream_t s) {
     k_finish_count<R><<<1184, 256, 0, s>>>(a);
-    if (a.creates) k_finish_append<R><<<1184, 256, 0, s>>>(a);
+    if (a.creates) k_finish_append<R><<<592, 256, 0, s>>>(a);
     const int g = (a.n_cells + 255) / 256 < 148 ? (a.n_cells + 255) / 256 : 148;
     k_cellupd<<<g < 1 ? 1 : g, 256, 0, s>>>(a);
 }

@@ -290,7 +290,7 @@ def served_jobs(n_jobs: int = 48, rate: float = 50.0, n_min: int = 10_000, n_max
     species = [triatomic(), ch4_like(), ch3_like(), h_atom()]
     rx = [Reaction("diss", [1], [2, 3], diss_mode_mask=0xF)]
     if recombination:
-        rx.append(Reaction("recomb", [2, 3], [1, -1]))
+        rx.append(Reaction("recomb", [2, 3], [1, -1], diss_mode_mask=0xF))
     t = 0.0
     jobs = []
     for i in range(n_jobs):
