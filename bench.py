@@ -311,7 +311,9 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
         return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "mean_s": float(lat.mean()), "max_s": float(lat.max())}
 
-    ctx = hcao.Context(precision=prec, stream=stream.cuda_stream)
+    # recombination rounds hold N/3 pairs (a third body per pair): twice the
+    # default rounds for the hottest relaxation jobs' (sigma g)_max
+    ctx = hcao.Context(precision=prec, stream=stream.cuda_stream, max_rounds=4)
     ctx.set_species(sw.species)
     ctx.set_reactions(sw.reactions)
     ctx.serve_start()
@@ -337,7 +339,7 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
     span_s = max(res[jid].t_done for jid in ids) - t0
     queue_s = [res[jid].t_admit - res[jid].t_submit for jid in ids]
 
-    p = hcao.Context(precision=prec, stream=stream.cuda_stream)
+    p = hcao.Context(precision=prec, stream=stream.cuda_stream, max_rounds=4)
     p.set_species(sw.species)
     p.set_reactions(sw.reactions)
     t0 = time.monotonic()

@@ -95,7 +95,10 @@ typedef struct {
    that position is past the cell's end.  C is removed at the end of the step
    (the survivors at the end of the cell fill the freed slots in increasing
    order).  At most HCAO_MAX_REMOVALS_PER_CELL removals per cell and step
-   (HCAO_ECAPACITY beyond). */
+   (HCAO_ECAPACITY beyond).  While a recombination reaction is set, a pairing
+   round holds at most N/3 pairs (every pair needs a third body), so a cell
+   needs about 1.5 times the rounds: raise hcao_config.max_rounds
+   accordingly (HCAO_EROUNDS otherwise). */
 #define HCAO_MAX_REMOVALS_PER_CELL 4096
 #define HCAO_REC_NODES 225
 typedef struct {
@@ -173,9 +176,10 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int res, double T_vib);
 
 /* Advance every reservoir by n_steps collision phases (NTC pair selection with
    VHS cross-sections, QK reaction test and execution, HCAO LB relaxation,
-   isotropic scattering).  Asynchronous on the context's stream.  For
-   n_steps >= 2 (profiling off) one step is captured once as a CUDA graph on a
-   private stream and launched n_steps times on the context's stream. */
+   isotropic scattering).  Asynchronous on the context's stream.  With
+   profiling off, one step is captured as a CUDA graph on a private stream
+   (again whenever the kernel arguments change, e.g. after a reservoir is
+   added) and launched n_steps times on the context's stream. */
 hcao_status hcao_step(hcao_ctx* ctx, int n_steps);
 /* Wait for the stream; return the sticky device error status. */
 hcao_status hcao_sync(hcao_ctx* ctx);
@@ -290,7 +294,8 @@ hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* host_out, int max, int* n_ou
    Finished jobs are read back and their memory freed.  Each job's results
    equal those of the same reservoir stepped alone: its draws are keyed by its
    own seed, cells and step count.  While serving, only the serve_* functions
-   may be called on the context. */
+   may be called on the context.  A device error during an iteration fails
+   every job resident in it; the engine then clears the error and continues. */
 typedef struct {
     int n_cells;
     double cell_volume, weight, dt;  /* as hcao_add_reservoir */

@@ -1286,7 +1286,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
     const int block = 128;
     const int grid = ctx->sm_count * 8;
     const bool f64 = ctx->cfg.precision == HCAO_FP64;
-    if (!ctx->prof_on && ctx->use_graph && n_steps >= 2) {
+    if (!ctx->prof_on && ctx->use_graph) {
         // one step as a CUDA graph, launched n_steps times on the caller's stream
         if (!ctx->graph || std::memcmp(&a, &ctx->graph_args, sizeof a) != 0) {
             if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -1745,6 +1745,9 @@ static void serve_loop(hcao_ctx* ctx) {
                     hcao_remove_reservoir(ctx, jb->res);
                     serve_fail(ctx, jb, st);
                 }
+                // the error word is sticky: clear it for the jobs that follow
+                cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
+                cudaStreamSynchronize(ctx->stream);
                 std::lock_guard<std::mutex> lock(ctx->serve_mu);
                 for (auto& jb : ctx->serve_active) ctx->serve_used -= jb->est_bytes;
                 ctx->serve_active.clear();
