@@ -34,11 +34,11 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffi
 # least integer/FP32 lane operations each unit needs):
 #   level evaluation: 2 loads, subtract, bucket index (bit cast, shift, subtract,
 #     2 clamps), table offset, accumulate, compare, loop = 12
-#   mode draw: half a Philox4x32-10 block (10 rounds x 8 ops / 2) + 8 = 48
+#   mode draw: a quarter of a Philox4x32-10 block (10 rounds x 8 ops / 4) + 8 = 28
 #   molecule sample: vibrational energy of up to 9 modes twice + setup = 60
 #   pair: members, two record loads, relative energy, isotropic direction,
 #     scattering, two record stores, event word = 160
-OPS_PER_UNIT = (12, 48, 60, 160)
+OPS_PER_UNIT = (12, 28, 60, 160)
 SMS, LANES_PER_SM = 148, 128
 
 

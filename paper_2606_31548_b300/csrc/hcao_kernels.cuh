@@ -73,18 +73,20 @@ __device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x
     }
 }
 
-// A counter-based stream: uniform number j uses words 2(j%2), 2(j%2)+1 of block j/2.
+// A counter-based stream of Philox blocks, consumed word by word: an FP64
+// uniform takes words (0,1) then (2,3) of a block, an FP32 uniform one word
+// (0, 1, 2, 3 in turn).  A stream is read at one precision only.
 struct Stream {
     uint32_t k0, k1, c0, c1, c2, c3;
     uint32_t blk;
     uint32_t w0, w1, w2, w3;
-    int half;
+    int pos;  // next unread word; 4 = block used up
 };
 __device__ __forceinline__ void st_init(Stream& s, uint64_t seed, uint32_t c0, uint32_t c1,
                                         uint32_t c2, uint32_t purpose) {
     s.k0 = (uint32_t)seed; s.k1 = (uint32_t)(seed >> 32);
     s.c0 = c0; s.c1 = c1; s.c2 = c2; s.c3 = purpose << 24;
-    s.blk = 0; s.half = 2;
+    s.blk = 0; s.pos = 4;
 }
 __device__ __forceinline__ void st_block(Stream& s) {
     s.w0 = s.c0; s.w1 = s.c1; s.w2 = s.c2; s.w3 = s.c3 | (s.blk & 0xFFFFFFu);
@@ -92,11 +94,12 @@ __device__ __forceinline__ void st_block(Stream& s) {
     s.blk++;
 }
 __device__ __forceinline__ void st_pair(Stream& s, uint32_t& a, uint32_t& b) {
-    if (s.half == 2) { st_block(s); s.half = 0; }
-    if (s.half == 0) { a = s.w0; b = s.w1; s.half = 1; }
-    else { a = s.w2; b = s.w3; s.half = 2; }
+    if (s.pos > 2) { st_block(s); s.pos = 0; }
+    if (s.pos == 0) { a = s.w0; b = s.w1; }
+    else { a = s.w2; b = s.w3; }
+    s.pos += 2;
 }
-// FP64 uniform: (27 bits of a, 26 bits of b) * 2^-53; FP32 uniform: 24 bits of a * 2^-24
+// FP64 uniform: (27 bits of a, 26 bits of b) * 2^-53; FP32 uniform: 24 bits of one word * 2^-24
 __device__ __forceinline__ double st_u64(Stream& s) {
     uint32_t a, b;
     st_pair(s, a, b);
@@ -104,9 +107,10 @@ __device__ __forceinline__ double st_u64(Stream& s) {
     return (double)m * 0x1p-53;
 }
 __device__ __forceinline__ float st_u32(Stream& s) {
-    uint32_t a, b;
-    st_pair(s, a, b);
-    return (float)(a >> 8) * 0x1p-24f;
+    if (s.pos > 3) { st_block(s); s.pos = 0; }
+    const uint32_t w = s.pos == 0 ? s.w0 : (s.pos == 1 ? s.w1 : (s.pos == 2 ? s.w2 : s.w3));
+    s.pos++;
+    return (float)(w >> 8) * 0x1p-24f;
 }
 template <class R> __device__ __forceinline__ R st_uni(Stream& s);
 template <> __device__ __forceinline__ double st_uni<double>(Stream& s) { return st_u64(s); }
@@ -1708,7 +1712,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
 // all of them make their transitions together.  Same draws, tables and
 // target as relax_flat.
 template <class R>
-__global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
+__global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     enum { P_NONE = 0, P_START_MODE, P_FETCH, P_PAIR, P_START_MOL, P_DONE_MOL, P_SCATTER };
     const Consts* __restrict__ C = A.C;
@@ -1739,132 +1743,135 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     bool last = false;
     uint32_t nq[4] = {0u, 0u, 0u, 0u};
     uint32_t trials = 0;
-    // the molecule's Philox stream: block index, and the unused second word
-    // of the last block (uniform j uses word 0 of block j/2 if j is even, word 2
-    // if odd; an FP32 uniform takes the top 24 bits)
-    uint32_t sblk = 0, spur = 0, sword = 0;
-    bool shave = false;
+    // the molecule's Philox stream: block index and the unread words of the
+    // last block (uniform j uses word j%4 of block j/4, its top 24 bits, as
+    // st_u32)
+    uint32_t sblk = 0, spur = 0, sw1 = 0, sw2 = 0, sw3 = 0;
+    int sleft = 0;  // words of the last block still unread (1..3 taken in order)
     // algorithmic work of this lane (level evaluations, mode starts, samples, pairs)
     uint32_t w_lev = 0, w_mode = 0, w_samp = 0, w_pair = 0;
 
     auto uniform = [&]() -> float {
         uint32_t w;
-        if (shave) {
-            w = sword;
-            shave = false;
+        if (sleft > 0) {
+            w = sleft == 3 ? sw1 : (sleft == 2 ? sw2 : sw3);
+            sleft--;
         } else {
             uint32_t x0 = step, x1 = lcell, x2 = rk, x3 = (spur << 24) | (sblk & 0xFFFFFFu);
             philox10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
             sblk++;
             w = x0;
-            sword = x2;
-            shave = true;
+            sw1 = x1;
+            sw2 = x2;
+            sw3 = x3;
+            sleft = 3;
         }
         return (float)(w >> 8) * 0x1p-24f;
     };
 
-    auto heavy = [&]() {
-        for (int tg = 0; alive && pend >= P_PAIR && tg < 64; ++tg) {
-            if (pend == P_PAIR) {
-                const uint4 e = A.qA[qi];
-                const int cidx = (int)e.x;
-                const DevCell& cell = A.cells[cidx];
-                const DevRes& rs = A.res[cell.res];
-                seed = rs.seed;
-                step = rs.step;
-                lcell = cell.lcell;
-                rk = ((uint32_t)r << 24) | e.y;
-                ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
-                ip = e.z;
-                iq = e.w;
-                recs = reinterpret_cast<uint4*>(cell.rec);
-                const uint4 a = recs[2 * ip], b = recs[2 * iq];
-                const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
-                sP = (int)(a.w & 0xFFu);
-                sQ = (int)(b.w & 0xFFu);
-                const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
-                const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
-                const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
-                Erel = f2fix(0.5f * C->pair[sP * MAXS + sQ].mr_f * (gx * gx + gy * gy + gz * gz));
-                const uint32_t q0[4] = {qa.x, qa.y, qa.z, qa.w};
-                const uint32_t q1[4] = {qb.x, qb.y, qb.z, qb.w};
-                EvP = evib_fix(A.levfix, C->sp[sP], q0);
-                EvQ = evib_fix(A.levfix, C->sp[sQ], q1);
-                o.ev = EV_ACC;
-                o.trials = 0u;
-                mol = 0;
-                w_pair++;
-                pend = P_START_MOL;
-            } else if (pend == P_START_MOL) {
-                if (mol >= 2) { pend = P_SCATTER; continue; }
-                sp = mol ? sQ : sP;
-                const DevSpecies& S = C->sp[sp];
-                if (S.n_modes == 0) { mol++; continue; }
-                Evold = mol ? EvQ : EvP;
-                spur = mol ? PU_LB_B : PU_LB_A;
-                sblk = 0;
-                shave = false;
-                Ecd = Erel + Evold;
-                n = S.n_modes;
-                MT = S.MT;
-                gsh = S.gshift;
-                gj0 = S.gj0;
-                hm = S.tab_off;
-                b0 = S.base_f[0];
-                o.ev += 1u << EV_SAMP_SHIFT;
-                w_samp++;
-                Ec = fix2f(Ecd);
-                m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
-                trials = 0;
-                failed = false;
-                nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-                pend = P_DONE_MOL;
-                if (m0 > S.M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
-                else if (m0 == 0 || !(__ldg(Hb + hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
-                else if (!(__fsub_rn(Ec, b0) < S.eps_min_f)) {  // else: ground state only
-                    k = 0;
-                    pend = P_START_MODE;
-                }
-            } else if (pend == P_DONE_MOL) {
-                o.trials += trials;
-                if (failed) {
-                    Erel = Ecd - Evold;
-                } else {
-                    const long long En = Ecd - evib_fix(A.levfix, C->sp[sp], nq);
-                    if (En >= 0) {
-                        recs[2 * (mol ? iq : ip) + 1] = make_uint4(nq[0], nq[1], nq[2], nq[3]);
-                        Erel = En;
-                    } else {
-                        o.ev += 1u << EV_DEGEN_SHIFT;
-                        Erel = Ecd - Evold;
-                    }
-                }
-                mol++;
-                pend = P_START_MOL;
-            } else {  // P_SCATTER: isotropic, centre-of-mass velocity kept
-                const DevPair& pc = C->pair[sP * MAXS + sQ];
-                Stream ss;
-                st_init(ss, seed, step, lcell, rk, PU_SCAT);
-                const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
-                float d[3];
-                iso_dir<float>(ss, d);
-                const uint4 a = recs[2 * ip], b = recs[2 * iq];
-                const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
-                const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
-                float na[3], nb[3];
-                for (int c3 = 0; c3 < 3; ++c3) {
-                    const float V = pc.fq_f * va[c3] + pc.fp_f * vb[c3];
-                    const float G = gn * d[c3];
-                    na[c3] = V + pc.fp_f * G;
-                    nb[c3] = V - pc.fq_f * G;
-                }
-                recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
-                recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
-                A.cflag[ev_idx] = ev_final(o);
-                if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
-                pend = P_FETCH;
+    // heavy transitions, one lambda per state; a heavy pass runs them as a
+    // fixed pipeline so that lanes in the same state execute each body together
+    auto do_pair = [&]() {
+        const uint4 e = A.qA[qi];
+        const int cidx = (int)e.x;
+        const DevCell& cell = A.cells[cidx];
+        const DevRes& rs = A.res[cell.res];
+        seed = rs.seed;
+        step = rs.step;
+        lcell = cell.lcell;
+        rk = ((uint32_t)r << 24) | e.y;
+        ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
+        ip = e.z;
+        iq = e.w;
+        recs = reinterpret_cast<uint4*>(cell.rec);
+        const uint4 a = recs[2 * ip], b = recs[2 * iq];
+        const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
+        sP = (int)(a.w & 0xFFu);
+        sQ = (int)(b.w & 0xFFu);
+        const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
+        const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
+        const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
+        Erel = f2fix(0.5f * C->pair[sP * MAXS + sQ].mr_f * (gx * gx + gy * gy + gz * gz));
+        const uint32_t q0[4] = {qa.x, qa.y, qa.z, qa.w};
+        const uint32_t q1[4] = {qb.x, qb.y, qb.z, qb.w};
+        EvP = evib_fix(A.levfix, C->sp[sP], q0);
+        EvQ = evib_fix(A.levfix, C->sp[sQ], q1);
+        o.ev = EV_ACC;
+        o.trials = 0u;
+        mol = 0;
+        w_pair++;
+        pend = P_START_MOL;
+    };
+    auto do_start_mol = [&]() {
+        while (mol < 2 && C->sp[mol ? sQ : sP].n_modes == 0) mol++;  // atoms: nothing to draw
+        if (mol >= 2) { pend = P_SCATTER; return; }
+        sp = mol ? sQ : sP;
+        const DevSpecies& S = C->sp[sp];
+        Evold = mol ? EvQ : EvP;
+        spur = mol ? PU_LB_B : PU_LB_A;
+        sblk = 0;
+        sleft = 0;
+        Ecd = Erel + Evold;
+        n = S.n_modes;
+        MT = S.MT;
+        gsh = S.gshift;
+        gj0 = S.gj0;
+        hm = S.tab_off;
+        b0 = S.base_f[0];
+        o.ev += 1u << EV_SAMP_SHIFT;
+        w_samp++;
+        Ec = fix2f(Ecd);
+        m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
+        trials = 0;
+        failed = false;
+        nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+        pend = P_DONE_MOL;
+        if (m0 > S.M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
+        else if (m0 == 0 || !(__ldg(Hb + hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
+        else if (!(__fsub_rn(Ec, b0) < S.eps_min_f)) {  // else: ground state only
+            k = 0;
+            pend = P_START_MODE;
+        }
+    };
+    auto do_done_mol = [&]() {
+        o.trials += trials;
+        if (failed) {
+            Erel = Ecd - Evold;
+        } else {
+            const long long En = Ecd - evib_fix(A.levfix, C->sp[sp], nq);
+            if (En >= 0) {
+                recs[2 * (mol ? iq : ip) + 1] = make_uint4(nq[0], nq[1], nq[2], nq[3]);
+                Erel = En;
+            } else {
+                o.ev += 1u << EV_DEGEN_SHIFT;
+                Erel = Ecd - Evold;
             }
         }
+        mol++;
+        pend = P_START_MOL;
+    };
+    auto do_scatter = [&]() {  // isotropic, centre-of-mass velocity kept
+        const DevPair& pc = C->pair[sP * MAXS + sQ];
+        Stream ss;
+        st_init(ss, seed, step, lcell, rk, PU_SCAT);
+        const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
+        float d[3];
+        iso_dir<float>(ss, d);
+        const uint4 a = recs[2 * ip], b = recs[2 * iq];
+        const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+        const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
+        float na[3], nb[3];
+        for (int c3 = 0; c3 < 3; ++c3) {
+            const float V = pc.fq_f * va[c3] + pc.fp_f * vb[c3];
+            const float G = gn * d[c3];
+            na[c3] = V + pc.fp_f * G;
+            nb[c3] = V - pc.fq_f * G;
+        }
+        recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
+        recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
+        A.cflag[ev_idx] = ev_final(o);
+        if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
+        pend = P_FETCH;
     };
     // one warp-aggregated atomic for every lane that needs a pair
     auto fetch = [&]() {
@@ -1962,12 +1969,19 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         const unsigned heavyset = live & ~stepping & ~cheap;
         const bool do_heavy = 4 * __popc(heavyset) >= nlive || (stepping | cheap) == 0u;
         if (do_heavy) {
-            if (alive && pend >= P_PAIR) heavy();
+            // a molecule finished: the next one starts, or the pair scatters, a
+            // new pair is fetched and its first molecule starts
+            if (alive && pend == P_DONE_MOL) do_done_mol();
+            if (alive && pend == P_START_MOL) do_start_mol();
+            if (alive && pend == P_DONE_MOL) do_done_mol();   // ground-state / failed molecule
+            if (alive && pend == P_START_MOL) do_start_mol();
+            if (alive && pend == P_SCATTER) do_scatter();
             fetch();
-            if (alive && pend >= P_PAIR) heavy();
+            if (alive && pend == P_PAIR) do_pair();
+            if (alive && pend == P_START_MOL) do_start_mol();
+            if (alive && pend == P_DONE_MOL) do_done_mol();
+            if (alive && pend == P_START_MOL) do_start_mol();
         }
-        if (alive && pend == P_START_MODE) start_mode();
-        if (do_heavy && alive && pend >= P_PAIR) heavy();
         if (alive && pend == P_START_MODE) start_mode();
     }
     // work counters: one atomic per warp and counter
