@@ -102,6 +102,17 @@ def _sum_over_ranks(x: float) -> float:
     return x
 
 
+def replica_workload(rank: int, **kw):
+    """The heat bath each rank steps: the same recipe with a seed of its own
+    (ranks are independent replicas; no data-path collective)."""
+    return W.ch4_heat_bath(seed=0x48434132 + rank, **kw)
+
+
+def aggregate(units: float, seconds: float):
+    """Whole-job figures: units summed over ranks, time the slowest rank's."""
+    return _sum_over_ranks(units), _max_over_ranks(seconds)
+
+
 class Clocks:
     """nvidia-smi sampling (every 50 ms) around the timed region; only samples
     whose timestamps fall inside it are kept."""
@@ -420,7 +431,7 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     prec = hcao.FP32 if args.precision == "fp32" else hcao.FP64
-    w = W.ch4_heat_bath(seed=0x48434132 + rank)
+    w = replica_workload(rank)
     ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -458,8 +469,7 @@ def main():
     kms, kn = ctx.read_profile()
     ctx.set_profiling(False)
     collisions = float(c1[1] - c0[1])
-    t = _max_over_ranks(ms / 1e3)
-    tot_psteps = _sum_over_ranks(float(psteps))
+    tot_psteps, t = aggregate(float(psteps), ms / 1e3)
     tot_coll = _sum_over_ranks(collisions)
 
     # roofline of the dominant kernel, the relaxation kernel: it is bound by

@@ -59,6 +59,16 @@ __device__ __forceinline__ R lb_pow(int amode, R x) {
     return sqrt_rn(x);
 }
 
+// The same weight for the FP32 kernels with approximate reciprocal square
+// roots (x > 0): its ~1e-7 relative difference from the host-built FP32
+// tables only moves a draw whose uniform lies that close to a level boundary.
+__device__ __forceinline__ float lb_pow_fast(int amode, float x) {
+    if (amode == 1) return x;
+    const float s = x * rsqrtf(x);  // sqrt(x)
+    if (amode == 2) return s;
+    return s * (s * rsqrtf(s));     // x^(3/4)
+}
+
 // ------------------------------------------------------------- Philox4x32-10
 __device__ __forceinline__ void philox10(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
                                          uint32_t k0, uint32_t k1) {
@@ -351,6 +361,7 @@ __device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, doub
 }
 
 // Marsaglia (1972): a point uniform in the unit disk mapped onto the sphere
+// (FP32: approximate square root, the direction's norm is 1 to ~1e-7)
 template <class R>
 __device__ __forceinline__ void iso_dir(Stream& st, R d[3]) {
     for (int it = 0; it < 4096; ++it) {
@@ -358,7 +369,10 @@ __device__ __forceinline__ void iso_dir(Stream& st, R d[3]) {
         R x2 = (R)2 * st_uni<R>(st) - (R)1;
         R s = x1 * x1 + x2 * x2;
         if (s < (R)1) {
-            R r = (R)2 * sqrt_rn((R)1 - s);
+            const R om = (R)1 - s;
+            R r;
+            if constexpr (std::is_same<R, float>::value) r = 2.0f * (om * rsqrtf(om));
+            else r = (R)2 * sqrt_rn(om);
             d[0] = x1 * r; d[1] = x2 * r; d[2] = (R)1 - (R)2 * s;
             return;
         }
@@ -829,7 +843,7 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
                     const float x = __fsub_rn(E, e);
                     float w;
                     if (last) {
-                        w = lb_pow<float>(amode, x);
+                        w = lb_pow_fast(amode, x);
                     } else {
                         const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
                         w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
@@ -1742,6 +1756,8 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
     int hm = 0, lk = 0, hn = 0;  // offsets of table 0, levels of mode k, table k + 1
     bool last = false;
     uint32_t nq[4] = {0u, 0u, 0u, 0u};
+    long long Esel = 0;   // fixed-point energy of the levels drawn so far in this trial
+    bool drawn = false;   // the molecule went through the mode draws
     uint32_t trials = 0;
     // the molecule's Philox stream: block index and the unread words of the
     // last block (uniform j uses word j%4 of block j/4, its top 24 bits, as
@@ -1832,13 +1848,14 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
             k = 0;
             pend = P_START_MODE;
         }
+        drawn = pend == P_START_MODE;
     };
     auto do_done_mol = [&]() {
         o.trials += trials;
         if (failed) {
             Erel = Ecd - Evold;
         } else {
-            const long long En = Ecd - evib_fix(A.levfix, C->sp[sp], nq);
+            const long long En = Ecd - (drawn ? Esel : evib_fix(A.levfix, C->sp[sp], nq));
             if (En >= 0) {
                 recs[2 * (mol ? iq : ip) + 1] = make_uint4(nq[0], nq[1], nq[2], nq[3]);
                 Erel = En;
@@ -1900,6 +1917,7 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
             }
             trials++;
             E = Ec;
+            Esel = 0;
             nq[0] = nq[1] = nq[2] = nq[3] = 0u;
         }
         const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
@@ -1918,7 +1936,7 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
         e = ii < nl ? __ldg(Lv + lk + ii) : 3.0e38f;
         if (!(e < E)) return -1.0f;
         const float x = __fsub_rn(E, e);
-        if (last) return lb_pow<float>(amode, x);
+        if (last) return lb_pow_fast(amode, x);
         const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
         return mm == 0 ? 0.f : __ldg(Hb + hn + min(mm, MT - 1));
     };
@@ -1954,6 +1972,7 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
                 if (sel >= 0) {
                     set_q(nq, k, (uint32_t)sel);
                     E = __fsub_rn(E, sel == i ? e0 : e1);
+                    Esel += __ldg(A.levfix + lk + sel);
                     k++;
                     pend = k < n ? P_START_MODE : P_DONE_MOL;
                 } else if (exhausted) {  // the draw ran past the levels: restart the trial
