@@ -32,13 +32,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffi
 
 # Algorithmic lane-operations of the relaxation kernel per unit of K5 work (the
 # least integer/FP32 lane operations each unit needs):
-#   level evaluation: 2 loads, subtract, bucket index (bit cast, shift, subtract,
-#     2 clamps), table offset, accumulate, compare, loop = 12
-#   mode draw: a quarter of a Philox4x32-10 block (10 rounds x 8 ops / 4) + 8 = 28
+#   level evaluation (the acceptance weight at the budget): 2 loads, subtract,
+#     bucket index (bit cast, shift, subtract, 2 clamps), table offset, compare = 12
+#   mode draw: two quarters of a Philox4x32-10 block (2 x 10 rounds x 8 ops / 4)
+#     + alias entry (multiply, shift, 2 loads, compare, select) + 8 = 54
 #   molecule sample: vibrational energy of up to 9 modes twice + setup = 60
 #   pair: members, two record loads, relative energy, isotropic direction,
 #     scattering, two record stores, event word = 160
-OPS_PER_UNIT = (12, 28, 60, 160)
+OPS_PER_UNIT = (12, 54, 60, 160)
 SMS, LANES_PER_SM = 148, 128
 
 

@@ -93,6 +93,9 @@ struct hcao_ctx {
     long long* d_levfix = nullptr;
     double* d_H64 = nullptr;
     float* d_H32 = nullptr;
+    uint2* d_arow = nullptr;
+    float2* d_aw = nullptr;
+    uint8_t* d_ai = nullptr;
     int amode = -1;
     double omega = 0.75;
 
@@ -343,6 +346,68 @@ void build_tables_f32(int amode, int n, const std::vector<float>* lev, const flo
                 sum = sum + w;
             }
             out[(size_t)k * MT + m] = sum;
+        }
+    }
+}
+
+// FP32 alias proposals of the K5 draw.  For table entry (mode k, bucket m),
+// the levels i of mode k below the bucket's upper edge G_m with their weights
+// w_i(G_m) (the summands of H_k[m]) as a Walker/Vose alias table.  Drawing i
+// from it with probability w_i(G_m)/H_k[m] and accepting with probability
+// w_i(E)/w_i(G_m) (E <= G_m, weights increase with the budget) takes level i
+// with probability w_i(E)/H_k[idx(E)] and rejects with the rest: the K5 mode
+// draw exactly, in constant work instead of a scan of the levels.
+void build_alias_f32(int amode, int n, const std::vector<float>* lev, const float* base, int shift, int j0,
+                     int MT, const std::vector<float>& H, std::vector<uint2>& rows, std::vector<float2>& aw,
+                     std::vector<uint8_t>& ai) {
+    rows.assign((size_t)n * MT, make_uint2(0u, 0u));
+    std::vector<double> w, q;
+    std::vector<int> small, large, alias;
+    for (int k = 0; k < n; ++k) {
+        for (int m = 0; m < MT; ++m) {
+            const float g = bucket_top_f32(base[k], shift, j0, MT, m);
+            w.clear();
+            for (size_t i = 0; i < lev[k].size() && i < 256; ++i) {
+                if (!(lev[k][i] < g)) break;
+                const float x = g - lev[k][i];
+                float wi;
+                if (k == n - 1) {
+                    wi = lbpow_host<float>(amode, x);
+                } else {
+                    int mm = idx_f32(base[k + 1], shift, j0, MT, x);
+                    if (mm > MT - 1) mm = MT - 1;
+                    wi = mm == 0 ? 0.0f : H[(size_t)(k + 1) * MT + mm];
+                }
+                w.push_back(wi);
+            }
+            double tot = 0.0;
+            for (double x : w) tot += x;
+            const int L = tot > 0.0 ? (int)w.size() : 0;
+            rows[(size_t)k * MT + m] = make_uint2((uint32_t)aw.size(), (uint32_t)L);
+            if (L == 0) continue;
+            // Vose: scaled probabilities L w_i / W, split into small and large
+            q.assign(L, 0.0);
+            alias.assign(L, 0);
+            small.clear();
+            large.clear();
+            for (int i = 0; i < L; ++i) {
+                q[i] = w[i] * L / tot;
+                alias[i] = i;
+                (q[i] < 1.0 ? small : large).push_back(i);
+            }
+            while (!small.empty() && !large.empty()) {
+                const int a = small.back(), b = large.back();
+                small.pop_back();
+                alias[a] = b;
+                q[b] = (q[b] + q[a]) - 1.0;
+                if (q[b] < 1.0) { large.pop_back(); small.push_back(b); }
+            }
+            for (int i : large) q[i] = 1.0;
+            for (int i : small) q[i] = 1.0;  // rounding leftovers
+            for (int i = 0; i < L; ++i) {
+                aw.push_back(make_float2((float)q[i], (float)w[i]));
+                ai.push_back((uint8_t)alias[i]);
+            }
         }
     }
 }
@@ -625,6 +690,9 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.levfix = ctx->d_levfix;
     a.H64 = ctx->d_H64;
     a.H32 = ctx->d_H32;
+    a.arow = ctx->d_arow;
+    a.aw = ctx->d_aw;
+    a.ai = ctx->d_ai;
     a.cells = ctx->d_cells;
     a.n_cells = ctx->n_cells_total;
     a.res = ctx->d_res;
@@ -727,6 +795,9 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_levfix);
     dfree(ctx, ctx->d_H64);
     dfree(ctx, ctx->d_H32);
+    dfree(ctx, ctx->d_arow);
+    dfree(ctx, ctx->d_aw);
+    dfree(ctx, ctx->d_ai);
     dfree(ctx, ctx->d_res);
     dfree(ctx, ctx->d_cells);
     dfree(ctx, ctx->d_cellcnt);
@@ -829,6 +900,9 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     const int MT = M + TABLE_PAD;
     std::vector<double> H64;
     std::vector<float> H32;
+    std::vector<uint2> arow;
+    std::vector<float2> aw;
+    std::vector<uint8_t> ai;
     for (int i = 0; i < n; ++i) {
         HostSpecies& s = ctx->sp[i];
         DevSpecies& D = C.sp[i];
@@ -897,8 +971,11 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
                 D.gj0 = (int)(sb >> D.gshift) - M;
                 std::vector<float> t;
                 build_tables_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t);
+                std::vector<uint2> rows;
+                build_alias_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t, rows, aw, ai);
                 D.tab_off = (int)H32.size();
                 H32.insert(H32.end(), t.begin(), t.end());
+                arow.insert(arow.end(), rows.begin(), rows.end());
                 D.top = (double)bucket_top_f32(D.base_f[0], D.gshift, D.gj0, MT, M);
             }
         }
@@ -924,8 +1001,20 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
         CU(cudaMemcpyAsync(ctx->d_H64, H64.data(), sizeof(double) * H64.size(), cudaMemcpyHostToDevice, ctx->stream));
     }
     if (!H32.empty()) {
+        dfree(ctx, ctx->d_H32);
+        dfree(ctx, ctx->d_arow);
+        dfree(ctx, ctx->d_aw);
+        dfree(ctx, ctx->d_ai);
         CU(dalloc(ctx, &ctx->d_H32, H32.size()));
         CU(cudaMemcpyAsync(ctx->d_H32, H32.data(), sizeof(float) * H32.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CU(dalloc(ctx, &ctx->d_arow, arow.size()));
+        CU(cudaMemcpyAsync(ctx->d_arow, arow.data(), sizeof(uint2) * arow.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CU(dalloc(ctx, &ctx->d_aw, std::max<size_t>(aw.size(), 1)));
+        CU(dalloc(ctx, &ctx->d_ai, std::max<size_t>(ai.size(), 1)));
+        if (!aw.empty()) {
+            CU(cudaMemcpyAsync(ctx->d_aw, aw.data(), sizeof(float2) * aw.size(), cudaMemcpyHostToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(ctx->d_ai, ai.data(), ai.size(), cudaMemcpyHostToDevice, ctx->stream));
+        }
     }
     return upload_consts(ctx);
 }

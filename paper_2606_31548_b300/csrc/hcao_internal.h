@@ -124,6 +124,9 @@ struct StepArgs {
     const long long* levfix;        // level energies in 2^-100 J units (FP32-mode bookkeeping)
     const double* H64;
     const float* H32;
+    const uint2* arow;              // FP32 alias proposals, parallel to H32: (first entry, entries)
+    const float2* aw;               // per entry: alias threshold, weight of the entry's level
+    const uint8_t* ai;              // per entry: alias level
     DevCell* cells;
     int n_cells;
     DevRes* res;

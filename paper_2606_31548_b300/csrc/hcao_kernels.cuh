@@ -122,6 +122,13 @@ __device__ __forceinline__ float st_u32(Stream& s) {
     s.pos++;
     return (float)(w >> 8) * 0x1p-24f;
 }
+// the top 24 bits of the next word (the bits behind st_u32)
+__device__ __forceinline__ uint32_t st_bits24(Stream& s) {
+    if (s.pos > 3) { st_block(s); s.pos = 0; }
+    const uint32_t w = s.pos == 0 ? s.w0 : (s.pos == 1 ? s.w1 : (s.pos == 2 ? s.w2 : s.w3));
+    s.pos++;
+    return w >> 8;
+}
 template <class R> __device__ __forceinline__ R st_uni(Stream& s);
 template <> __device__ __forceinline__ double st_uni<double>(Stream& s) { return st_u64(s); }
 template <> __device__ __forceinline__ float st_uni<float>(Stream& s) { return st_u32(s); }
@@ -729,145 +736,121 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
     }
 }
 
-// FP32 LB relaxation of up to two molecules, scheduled for SIMT efficiency.
-// Each lane runs the K5 draw as a state machine whose common step is one
-// level of one mode.  The rarer transitions -- starting a molecule, starting a
-// mode (with its Philox draw), finishing a molecule -- are batched: lanes that
-// need one wait while the others keep stepping, and once at least half of the
-// live lanes wait they all make their transitions together.  Draws, tables
-// and the target are those of sample_lb<float>; the relative energy is kept
-// in int64 fixed point.  sp < 0 or a species without modes skips a molecule.
-// Returns the relative energy left for scattering.
-static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C,
-                                                       int spA, uint32_t (&qA)[4], long long EvA,
-                                                       Stream stA, int spB, uint32_t (&qB)[4],
-                                                       long long EvB, Stream stB, long long Erel,
-                                                       PairOut& o) {
-    enum { P_NONE = 0, P_START_MOL, P_START_MODE, P_DONE_MOL };
+// FP32 K5 draw of one molecule's levels at collision energy Ec (float, from
+// the fixed-point Ecd) with the alias proposals: per mode k, a level i is
+// proposed from the alias table of the bucket holding the budget E (weights
+// w_i at the bucket's upper edge) and accepted with probability
+// w_i(E)/w_i(edge); a rejection restarts the trial.  That is the K5 mode
+// draw (level i with probability w_i(E)/H_k[idx(E)], restart otherwise) in
+// constant work per mode.  Returns S_OK with the levels in q and their
+// fixed-point energy in Esel, S_OVER, S_DEGEN or S_CAP.  Counts mode draws
+// and level evaluations (one per draw).
+static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode, float Ec,
+                                       Stream& st, uint32_t (&q)[4], long long& Esel, uint32_t& trials,
+                                       uint32_t& wlev, uint32_t& wmode) {
     const float* __restrict__ Lv = A.lev32;
-    const float* __restrict__ Hb = A.H32;
-    const int amode = C->amode;
-    const unsigned act = __activemask();
-    int mol = 0, pend = P_START_MOL;
-    bool alive = true, failed = false;
-    const DevSpecies* S = nullptr;
-    long long Ecd = 0, Evold = 0;
-    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f;
-    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0, gsh = 0, gj0 = 0;
-    const float* Hm = nullptr;
-    const float* Lk = nullptr;
-    const float* Hn = nullptr;
-    bool last = false;
-    uint32_t nq[4] = {0u, 0u, 0u, 0u};
-    uint32_t trials = 0, trials_all = 0;
-    Stream st = stA;
-    for (int guard = 0; guard < (1 << 24); ++guard) {
-        // ---- transitions of every waiting lane
-        for (int tg = 0; alive && pend != P_NONE && tg < 64; ++tg) {
-            if (pend == P_DONE_MOL) {
-                trials_all += trials;
-                if (failed) {
-                    Erel = Ecd - Evold;
+    const float* __restrict__ H = A.H32 + S.tab_off;
+    const uint2* __restrict__ rows = A.arow + S.tab_off;
+    const int n = S.n_modes, MT = S.MT, gsh = S.gshift, gj0 = S.gj0;
+    q[0] = q[1] = q[2] = q[3] = 0u;
+    Esel = S.zpe_fix;
+    if (n == 0) return S_OK;
+    const float b0 = S.base_f[0];
+    const int m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
+    if (m0 > S.M) return S_OVER;
+    if (m0 == 0 || !(__ldg(H + m0) > 0.f)) return S_DEGEN;
+    if (__fsub_rn(Ec, b0) < S.eps_min_f) return S_OK;  // only the ground state fits
+    for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
+        trials++;
+        uint32_t nq[4] = {0u, 0u, 0u, 0u};
+        long long es = 0;
+        float E = Ec;
+        bool ok = true;
+        for (int k = 0; k < n; ++k) {
+            const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
+            const uint2 row = __ldg(rows + k * MT + m);
+            wmode++;
+            if (row.y == 0u) { ok = false; break; }
+            // proposal: 24 random bits give the entry (integer part of r L) and the coin
+            const uint32_t rbits = st_bits24(st);
+            const uint64_t rl = (uint64_t)rbits * row.y;
+            const uint32_t j = (uint32_t)(rl >> 24);
+            const float coin = (float)(uint32_t)(rl & 0xFFFFFFu) * 0x1p-24f;
+            const float2 awj = __ldg(A.aw + row.x + j);
+            uint32_t i = j;
+            float wg = awj.y;
+            if (!(coin < awj.x)) {
+                i = __ldg(A.ai + row.x + j);
+                wg = __ldg(A.aw + row.x + i).y;
+            }
+            // acceptance at the actual budget
+            const float e = __ldg(Lv + S.lev_off[k] + i);
+            float wE = 0.f;
+            if (e < E) {
+                const float x = __fsub_rn(E, e);
+                if (k == n - 1) {
+                    wE = lb_pow_fast(amode, x);
                 } else {
-                    const long long En = Ecd - evib_fix(A.levfix, *S, nq);
-                    if (En >= 0) {
-                        if (mol == 0) { qA[0] = nq[0]; qA[1] = nq[1]; qA[2] = nq[2]; qA[3] = nq[3]; }
-                        else { qB[0] = nq[0]; qB[1] = nq[1]; qB[2] = nq[2]; qB[3] = nq[3]; }
-                        Erel = En;
-                    } else {
-                        o.ev += 1u << EV_DEGEN_SHIFT;
-                        Erel = Ecd - Evold;
-                    }
+                    const int mm = grid_idx_f32(S.base_f[k + 1], gsh, gj0, MT, x);
+                    wE = mm == 0 ? 0.f : __ldg(H + (k + 1) * MT + min(mm, MT - 1));
                 }
-                mol++;
-                pend = P_START_MOL;
-                if (mol >= 2) alive = false;
-            } else if (pend == P_START_MOL) {
-                const int sp = mol ? spB : spA;
-                if (sp < 0 || C->sp[sp].n_modes == 0) {
-                    mol++;
-                    if (mol >= 2) alive = false;
-                    continue;
-                }
-                S = &C->sp[sp];
-                Evold = mol ? EvB : EvA;
-                st = mol ? stB : stA;
-                Ecd = Erel + Evold;
-                n = S->n_modes;
-                MT = S->MT;
-                gsh = S->gshift;
-                gj0 = S->gj0;
-                Hm = Hb + S->tab_off;
-                o.ev += 1u << EV_SAMP_SHIFT;
-                Ec = fix2f(Ecd);
-                m0 = grid_idx_f32(S->base_f[0], S->gshift, S->gj0, MT, Ec);
-                trials = 0;
-                failed = false;
-                nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-                pend = P_DONE_MOL;
-                if (m0 > S->M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
-                else if (m0 == 0 || !(__ldg(Hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
-                else if (!(__fsub_rn(Ec, S->base_f[0]) < S->eps_min_f)) {  // else: ground state only
-                    k = 0;
-                    pend = P_START_MODE;
-                }
-            } else {  // P_START_MODE
-                if (k == 0) {  // a new trial
-                    if (trials >= A.reject_cap) {
-                        atomicOr(A.err, (uint32_t)ERR_REJECT);
-                        failed = true;
-                        pend = P_DONE_MOL;
-                        continue;
-                    }
-                    trials++;
-                    E = Ec;
-                    nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-                }
-                const int m = k == 0 ? m0 : min(grid_idx_f32(S->base_f[k], S->gshift, S->gj0, MT, E), MT - 1);
-                t = __fmul_rn(st_u32(st), __ldg(Hm + k * MT + m));
-                cum = 0.f;
-                i = 0;
-                Lk = Lv + S->lev_off[k];
-                nl = S->n_lev[k];
-                last = k == n - 1;
-                if (!last) { Hn = Hm + (k + 1) * MT; bn = S->base_f[k + 1]; }
-                pend = P_NONE;
             }
+            wlev++;
+            if (!(st_u32(st) * wg < wE)) { ok = false; break; }
+            set_q(nq, k, i);
+            E = __fsub_rn(E, e);
+            es += __ldg(A.levfix + S.lev_off[k] + i);
         }
-        if (!__any_sync(act, alive)) break;
-        // ---- level steps until at least half of the live lanes wait
-        for (int sg = 0; sg < (1 << 20); ++sg) {
-            if (alive && pend == P_NONE) {
-                const float e = i < nl ? __ldg(Lk + i) : 0.f;
-                if (i < nl && e < E) {
-                    const float x = __fsub_rn(E, e);
-                    float w;
-                    if (last) {
-                        w = lb_pow_fast(amode, x);
-                    } else {
-                        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
-                        w = mm == 0 ? 0.f : __ldg(Hn + min(mm, MT - 1));
-                    }
-                    cum = __fadd_rn(cum, w);
-                    if (t < cum) {
-                        set_q(nq, k, (uint32_t)i);
-                        E = __fsub_rn(E, e);
-                        k++;
-                        pend = k < n ? P_START_MODE : P_DONE_MOL;
-                    } else {
-                        i++;
-                    }
-                } else {  // the draw ran past the levels: restart the trial
-                    k = 0;
-                    pend = P_START_MODE;
-                }
-            }
-            const unsigned live = __ballot_sync(act, alive);
-            const unsigned wait = __ballot_sync(act, alive && pend != P_NONE);
-            if (2 * __popc(wait) >= __popc(live)) break;
+        if (ok) {
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            Esel = es;
+            return S_OK;
         }
     }
-    o.trials += trials_all;
+    return S_CAP;
+}
+
+// FP32 LB relaxation of up to two molecules (molecule 1, then molecule 2
+// with the updated relative energy, in int64 fixed point); sp < 0 or a
+// species without modes skips a molecule.  Returns the relative energy left
+// for scattering.
+static __device__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C, int spA,
+                                       uint32_t (&qA)[4], long long EvA, Stream stA, int spB,
+                                       uint32_t (&qB)[4], long long EvB, Stream stB, long long Erel,
+                                       PairOut& o, uint32_t* work = nullptr) {
+    uint32_t wl = 0, wm = 0;
+    for (int mol = 0; mol < 2; ++mol) {
+        const int sp = mol ? spB : spA;
+        if (sp < 0 || C->sp[sp].n_modes == 0) continue;
+        const DevSpecies& S = C->sp[sp];
+        const long long Evold = mol ? EvB : EvA;
+        const long long Ecd = Erel + Evold;
+        Stream& st = mol ? stB : stA;
+        o.ev += 1u << EV_SAMP_SHIFT;
+        uint32_t nq[4];
+        long long Esel;
+        uint32_t tr = 0;
+        const int rc = sample_alias_f32(A, S, C->amode, fix2f(Ecd), st, nq, Esel, tr, wl, wm);
+        o.trials += tr;
+        Erel = Ecd - Evold;  // the state is kept unless a new one is drawn
+        if (rc == S_OK) {
+            const long long En = Ecd - Esel;
+            if (En >= 0) {
+                uint32_t (&qd)[4] = mol ? qB : qA;
+                qd[0] = nq[0]; qd[1] = nq[1]; qd[2] = nq[2]; qd[3] = nq[3];
+                Erel = En;
+            } else {
+                o.ev += 1u << EV_DEGEN_SHIFT;
+            }
+        } else if (rc == S_OVER) {
+            o.ev += 1u << EV_OVER_SHIFT;
+        } else if (rc == S_DEGEN) {
+            o.ev += 1u << EV_DEGEN_SHIFT;
+        } else {
+            atomicOr(A.err, (uint32_t)ERR_REJECT);
+        }
+    }
+    if (work) { work[0] += wl; work[1] += wm; }
     return Erel;
 }
 
@@ -1717,166 +1700,50 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
     }
 }
 
-// FP32 phase 2 as a persistent state machine.  Each lane takes an accepted
-// pair from the queue, runs its reaction test (reacting pairs go to the
-// reaction queue), relaxes both molecules with the K5 draw one level step per
-// iteration, scatters, stores, and takes the next pair.  Lanes that need a
-// transition (fetching or finishing a pair, starting a molecule or a mode)
-// wait while the others step; once at least half of the live lanes wait,
-// all of them make their transitions together.  Same draws, tables and
-// target as relax_flat.
+// FP32 phase 2: one thread per accepted pair (grid-stride over the queue).
+// Molecule 1 then molecule 2 with the alias K5 draw (relative energy in int64
+// fixed point), isotropic scattering with the centre-of-mass velocity kept.
 template <class R>
-__global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
+__global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
-    enum { P_NONE = 0, P_START_MODE, P_FETCH, P_PAIR, P_START_MOL, P_DONE_MOL, P_SCATTER };
     const Consts* __restrict__ C = A.C;
-    const float* __restrict__ Lv = A.lev32;
-    const float* __restrict__ Hb = A.H32;
-    const int amode = C->amode;
     const uint32_t total = A.qsize[2 * r];
-    uint32_t* head = A.qsize + 2 * MAX_ROUNDS + r;
-    const unsigned act = __activemask();
-    const int lane = threadIdx.x & 31;
-    bool alive = true;
-    int pend = P_FETCH;
-    uint32_t qi = 0;
-    // pair: cell records, members, event slot and Philox counter words
-    uint4* recs = nullptr;
-    uint32_t ip = 0, iq = 0, ev_idx = 0, lcell = 0, rk = 0, step = 0;
-    uint64_t seed = 0;
-    int sP = 0, sQ = 0;
-    long long EvP = 0, EvQ = 0, Erel = 0;
-    PairOut o{0u, 0u};
-    // molecule
-    int mol = 0, sp = 0;
-    bool failed = false;
-    long long Ecd = 0, Evold = 0;
-    float Ec = 0.f, E = 0.f, t = 0.f, cum = 0.f, bn = 0.f, b0 = 0.f;
-    int n = 0, k = 0, i = 0, nl = 0, m0 = 0, MT = 0, gsh = 0, gj0 = 0;
-    int hm = 0, lk = 0, hn = 0;  // offsets of table 0, levels of mode k, table k + 1
-    bool last = false;
-    uint32_t nq[4] = {0u, 0u, 0u, 0u};
-    long long Esel = 0;   // fixed-point energy of the levels drawn so far in this trial
-    bool drawn = false;   // the molecule went through the mode draws
-    uint32_t trials = 0;
-    // the molecule's Philox stream: block index and the unread words of the
-    // last block (uniform j uses word j%4 of block j/4, its top 24 bits, as
-    // st_u32)
-    uint32_t sblk = 0, spur = 0, sw1 = 0, sw2 = 0, sw3 = 0;
-    int sleft = 0;  // words of the last block still unread (1..3 taken in order)
-    // algorithmic work of this lane (level evaluations, mode starts, samples, pairs)
-    uint32_t w_lev = 0, w_mode = 0, w_samp = 0, w_pair = 0;
-
-    auto uniform = [&]() -> float {
-        uint32_t w;
-        if (sleft > 0) {
-            w = sleft == 3 ? sw1 : (sleft == 2 ? sw2 : sw3);
-            sleft--;
-        } else {
-            uint32_t x0 = step, x1 = lcell, x2 = rk, x3 = (spur << 24) | (sblk & 0xFFFFFFu);
-            philox10(x0, x1, x2, x3, (uint32_t)seed, (uint32_t)(seed >> 32));
-            sblk++;
-            w = x0;
-            sw1 = x1;
-            sw2 = x2;
-            sw3 = x3;
-            sleft = 3;
-        }
-        return (float)(w >> 8) * 0x1p-24f;
-    };
-
-    // heavy transitions, one lambda per state; a heavy pass runs them as a
-    // fixed pipeline so that lanes in the same state execute each body together
-    auto do_pair = [&]() {
-        const uint4 e = A.qA[qi];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t w[2] = {0u, 0u};
+    uint32_t w_samp = 0, w_pair = 0;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const uint4 e = A.qA[g];
         const int cidx = (int)e.x;
         const DevCell& cell = A.cells[cidx];
         const DevRes& rs = A.res[cell.res];
-        seed = rs.seed;
-        step = rs.step;
-        lcell = cell.lcell;
-        rk = ((uint32_t)r << 24) | e.y;
-        ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
-        ip = e.z;
-        iq = e.w;
-        recs = reinterpret_cast<uint4*>(cell.rec);
+        const uint32_t step = rs.step, lcell = cell.lcell;
+        const uint32_t rk = ((uint32_t)r << 24) | e.y;
+        const uint32_t ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
+        const uint32_t ip = e.z, iq = e.w;
+        uint4* recs = reinterpret_cast<uint4*>(cell.rec);
         const uint4 a = recs[2 * ip], b = recs[2 * iq];
         const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
-        sP = (int)(a.w & 0xFFu);
-        sQ = (int)(b.w & 0xFFu);
-        const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
-        const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
-        const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
-        Erel = f2fix(0.5f * C->pair[sP * MAXS + sQ].mr_f * (gx * gx + gy * gy + gz * gz));
-        const uint32_t q0[4] = {qa.x, qa.y, qa.z, qa.w};
-        const uint32_t q1[4] = {qb.x, qb.y, qb.z, qb.w};
-        EvP = evib_fix(A.levfix, C->sp[sP], q0);
-        EvQ = evib_fix(A.levfix, C->sp[sQ], q1);
-        o.ev = EV_ACC;
-        o.trials = 0u;
-        mol = 0;
-        w_pair++;
-        pend = P_START_MOL;
-    };
-    auto do_start_mol = [&]() {
-        while (mol < 2 && C->sp[mol ? sQ : sP].n_modes == 0) mol++;  // atoms: nothing to draw
-        if (mol >= 2) { pend = P_SCATTER; return; }
-        sp = mol ? sQ : sP;
-        const DevSpecies& S = C->sp[sp];
-        Evold = mol ? EvQ : EvP;
-        spur = mol ? PU_LB_B : PU_LB_A;
-        sblk = 0;
-        sleft = 0;
-        Ecd = Erel + Evold;
-        n = S.n_modes;
-        MT = S.MT;
-        gsh = S.gshift;
-        gj0 = S.gj0;
-        hm = S.tab_off;
-        b0 = S.base_f[0];
-        o.ev += 1u << EV_SAMP_SHIFT;
-        w_samp++;
-        Ec = fix2f(Ecd);
-        m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
-        trials = 0;
-        failed = false;
-        nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-        pend = P_DONE_MOL;
-        if (m0 > S.M) { o.ev += 1u << EV_OVER_SHIFT; failed = true; }
-        else if (m0 == 0 || !(__ldg(Hb + hm + m0) > 0.f)) { o.ev += 1u << EV_DEGEN_SHIFT; failed = true; }
-        else if (!(__fsub_rn(Ec, b0) < S.eps_min_f)) {  // else: ground state only
-            k = 0;
-            pend = P_START_MODE;
-        }
-        drawn = pend == P_START_MODE;
-    };
-    auto do_done_mol = [&]() {
-        o.trials += trials;
-        if (failed) {
-            Erel = Ecd - Evold;
-        } else {
-            const long long En = Ecd - (drawn ? Esel : evib_fix(A.levfix, C->sp[sp], nq));
-            if (En >= 0) {
-                recs[2 * (mol ? iq : ip) + 1] = make_uint4(nq[0], nq[1], nq[2], nq[3]);
-                Erel = En;
-            } else {
-                o.ev += 1u << EV_DEGEN_SHIFT;
-                Erel = Ecd - Evold;
-            }
-        }
-        mol++;
-        pend = P_START_MOL;
-    };
-    auto do_scatter = [&]() {  // isotropic, centre-of-mass velocity kept
+        const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
         const DevPair& pc = C->pair[sP * MAXS + sQ];
+        const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+        const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
+        const float gx = va[0] - vb[0], gy = va[1] - vb[1], gz = va[2] - vb[2];
+        const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+        uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
+        const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
+        const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
+        PairOut o{EV_ACC, 0u};
+        Stream s1, s2;
+        st_init(s1, rs.seed, step, lcell, rk, PU_LB_A);
+        st_init(s2, rs.seed, step, lcell, rk, PU_LB_B);
+        const long long Erel = relax_flat(A, C, sP, qP, EvP, s1, sQ, qQ, EvQ, s2, Etr, o, w);
+        w_samp += (C->sp[sP].n_modes > 0) + (C->sp[sQ].n_modes > 0);
+        w_pair++;
         Stream ss;
-        st_init(ss, seed, step, lcell, rk, PU_SCAT);
+        st_init(ss, rs.seed, step, lcell, rk, PU_SCAT);
         const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
         float d[3];
         iso_dir<float>(ss, d);
-        const uint4 a = recs[2 * ip], b = recs[2 * iq];
-        const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
-        const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
         float na[3], nb[3];
         for (int c3 = 0; c3 < 3; ++c3) {
             const float V = pc.fq_f * va[c3] + pc.fp_f * vb[c3];
@@ -1886,132 +1753,21 @@ __global__ void __launch_bounds__(128, 5) k_relax_fast(StepArgs A, int r) {
         }
         recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
         recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
+        recs[2 * ip + 1] = make_uint4(qP[0], qP[1], qP[2], qP[3]);
+        recs[2 * iq + 1] = make_uint4(qQ[0], qQ[1], qQ[2], qQ[3]);
         A.cflag[ev_idx] = ev_final(o);
         if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
-        pend = P_FETCH;
-    };
-    // one warp-aggregated atomic for every lane that needs a pair
-    auto fetch = [&]() {
-        const bool need = alive && pend == P_FETCH;
-        const unsigned fm = __ballot_sync(act, need);
-        if (fm) {
-            const int leader = __ffs(fm) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(head, (uint32_t)__popc(fm));
-            base = __shfl_sync(act, base, leader);
-            if (need) {
-                qi = base + (uint32_t)__popc(fm & ((1u << lane) - 1u));
-                if (qi < total) pend = P_PAIR;
-                else alive = false;
-            }
-        }
-    };
-    auto start_mode = [&]() {
-        const DevSpecies& S = C->sp[sp];
-        if (k == 0) {  // a new trial
-            if (trials >= A.reject_cap) {
-                atomicOr(A.err, (uint32_t)ERR_REJECT);
-                failed = true;
-                pend = P_DONE_MOL;
-                return;
-            }
-            trials++;
-            E = Ec;
-            Esel = 0;
-            nq[0] = nq[1] = nq[2] = nq[3] = 0u;
-        }
-        const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
-        t = __fmul_rn(uniform(), __ldg(Hb + hm + k * MT + m));
-        w_mode++;
-        cum = 0.f;
-        i = 0;
-        lk = S.lev_off[k];
-        nl = S.n_lev[k];
-        last = k == n - 1;
-        if (!last) { hn = hm + (k + 1) * MT; bn = S.base_f[k + 1]; }
-        pend = P_NONE;
-    };
-    // weight of one level (0 past the mode's list or at/above the budget)
-    auto weight = [&](int ii, float& e) -> float {
-        e = ii < nl ? __ldg(Lv + lk + ii) : 3.0e38f;
-        if (!(e < E)) return -1.0f;
-        const float x = __fsub_rn(E, e);
-        if (last) return lb_pow_fast(amode, x);
-        const int mm = grid_idx_f32(bn, gsh, gj0, MT, x);
-        return mm == 0 ? 0.f : __ldg(Hb + hn + min(mm, MT - 1));
-    };
-
-    for (int guard = 0; guard < (1 << 28); ++guard) {
-        const unsigned live = __ballot_sync(act, alive);
-        if (!live) break;
-        const unsigned stepping = __ballot_sync(act, alive && pend == P_NONE);
-        const int nlive = __popc(live), nstep = __popc(stepping);
-        if (2 * nstep >= nlive) {
-            // ---- two level steps of the K5 draw (the second load chain
-            // overlaps the first; the selection is that of a sequential scan)
-            if (alive && pend == P_NONE) {
-                float e0, e1;
-                const float w0 = weight(i, e0);
-                const float w1 = weight(i + 1, e1);
-                int sel = -1;
-                bool exhausted = false;
-                if (w0 < 0.f) {
-                    exhausted = true;
-                } else {
-                    cum = __fadd_rn(cum, w0);
-                    w_lev++;
-                    if (t < cum) sel = i;
-                    else if (w1 < 0.f) exhausted = true;
-                    else {
-                        cum = __fadd_rn(cum, w1);
-                        w_lev++;
-                        if (t < cum) sel = i + 1;
-                        else i += 2;
-                    }
-                }
-                if (sel >= 0) {
-                    set_q(nq, k, (uint32_t)sel);
-                    E = __fsub_rn(E, sel == i ? e0 : e1);
-                    Esel += __ldg(A.levfix + lk + sel);
-                    k++;
-                    pend = k < n ? P_START_MODE : P_DONE_MOL;
-                } else if (exhausted) {  // the draw ran past the levels: restart the trial
-                    k = 0;
-                    pend = P_START_MODE;
-                }
-            }
-            continue;
-        }
-        // ---- too few lanes stepping: cheap mode starts now, heavy transitions
-        // once at least a quarter of the live lanes need one (or nothing else can run)
-        const unsigned cheap = __ballot_sync(act, alive && pend == P_START_MODE);
-        const unsigned heavyset = live & ~stepping & ~cheap;
-        const bool do_heavy = 4 * __popc(heavyset) >= nlive || (stepping | cheap) == 0u;
-        if (do_heavy) {
-            // a molecule finished: the next one starts, or the pair scatters, a
-            // new pair is fetched and its first molecule starts
-            if (alive && pend == P_DONE_MOL) do_done_mol();
-            if (alive && pend == P_START_MOL) do_start_mol();
-            if (alive && pend == P_DONE_MOL) do_done_mol();   // ground-state / failed molecule
-            if (alive && pend == P_START_MOL) do_start_mol();
-            if (alive && pend == P_SCATTER) do_scatter();
-            fetch();
-            if (alive && pend == P_PAIR) do_pair();
-            if (alive && pend == P_START_MOL) do_start_mol();
-            if (alive && pend == P_DONE_MOL) do_done_mol();
-            if (alive && pend == P_START_MOL) do_start_mol();
-        }
-        if (alive && pend == P_START_MODE) start_mode();
     }
     // work counters: one atomic per warp and counter
-    unsigned long long wl = w_lev, wm = w_mode, ws = w_samp, wp = w_pair;
+    const unsigned act = __activemask();
+    unsigned long long wl = w[0], wm = w[1], ws = w_samp, wp = w_pair;
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
         wl += __shfl_xor_sync(act, wl, o2);
         wm += __shfl_xor_sync(act, wm, o2);
         ws += __shfl_xor_sync(act, ws, o2);
         wp += __shfl_xor_sync(act, wp, o2);
     }
-    if (lane == 0 && A.work) {
+    if ((threadIdx.x & 31) == 0 && A.work) {
         atomicAdd(A.work + 0, wl);
         atomicAdd(A.work + 1, wm);
         atomicAdd(A.work + 2, ws);
