@@ -1492,23 +1492,6 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
                 accept = st_u32(sp) < sgf / cell.sgmax_f;
-                if (accept && C->n_reactions > 0) {
-                    if (C->has_recomb && recomb_test<float>(A, C, c, r, k, sP, sQ, (double)sgf, chan, mpos)) {
-                        react = true;
-                    } else {
-                    const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
-                    const uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w};
-                    const uint32_t qQ[4] = {qb.x, qb.y, qb.z, qb.w};
-                    const long long Etr = f2fix(0.5f * pc.mr_f * g2);
-                    const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
-                    const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
-                    const float u_ster = st_u32(sp);
-                    const float u_sel = st_u32(sp);
-                    const float u_ch = st_u32(sp);
-                    react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch,
-                                              chan) > 0;
-                    }
-                }
                 }
                 if (!accept) {
                     A.cflag[ev_idx] = 0u;
@@ -1704,7 +1687,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
 // Molecule 1 then molecule 2 with the alias K5 draw (relative energy in int64
 // fixed point), isotropic scattering with the centre-of-mass velocity kept.
 template <class R>
-__global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
+__global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
     const uint32_t total = A.qsize[2 * r];
@@ -1732,6 +1715,30 @@ __global__ void __launch_bounds__(128) k_relax_fast(StepArgs A, int r) {
         uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
         const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
         const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
+        // reaction tests (recombination, then the QK channels in fixed point);
+        // a reacting pair goes to the reaction queue instead
+        bool react = false;
+        uint32_t chan = 0u, mpos = 0u;
+        if (C->n_reactions > 0) {
+            const float gr = sqrtf(gx * gx + gy * gy + gz * gz);
+            const float sgf = pc.C_f * (C->amode == 0 ? sqrtf(gr) : (C->amode == 1 ? gr : 1.0f));
+            if (C->has_recomb && recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sgf, chan, mpos)) {
+                react = true;
+            } else {
+                Stream sp;
+                st_init(sp, rs.seed, step, lcell, rk, PU_PAIR);
+                st_u32(sp);  // the acceptance draw
+                const float u_ster = st_u32(sp);
+                const float u_sel = st_u32(sp);
+                const float u_ch = st_u32(sp);
+                react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan) > 0;
+            }
+        }
+        const uint32_t rslot = queue_slot(A.qsize + 2 * r + 1, react);
+        if (react) {
+            A.qB[rslot] = make_uint4((uint32_t)cidx, e.y, chan, mpos);
+            continue;
+        }
         PairOut o{EV_ACC, 0u};
         Stream s1, s2;
         st_init(s1, rs.seed, step, lcell, rk, PU_LB_A);
