@@ -93,9 +93,8 @@ struct hcao_ctx {
     long long* d_levfix = nullptr;
     double* d_H64 = nullptr;
     float* d_H32 = nullptr;
-    uint2* d_arow = nullptr;
-    float2* d_aw = nullptr;
-    uint8_t* d_ai = nullptr;
+    K5Ent* d_k5e = nullptr;
+    AliasEnt* d_ae = nullptr;
     int amode = -1;
     double omega = 0.75;
 
@@ -122,6 +121,7 @@ struct hcao_ctx {
     long long* d_csum = nullptr;
     uint32_t* d_nbase = nullptr;
     uint32_t* d_chbase = nullptr;
+    uint32_t* d_tsum = nullptr;
     uint32_t* d_chcnt = nullptr;
     // launch shapes (autotuned; results do not depend on them)
     int grid_select = 0, grid_relax = 0, grid_react = 0;
@@ -357,10 +357,14 @@ void build_tables_f32(int amode, int n, const std::vector<float>* lev, const flo
 // w_i(E)/w_i(G_m) (E <= G_m, weights increase with the budget) takes level i
 // with probability w_i(E)/H_k[idx(E)] and rejects with the rest: the K5 mode
 // draw exactly, in constant work instead of a scan of the levels.
+// Output: one K5Ent per (k, m) with H_k[m] and the bucket's slots, appended
+// to ents; the slots appended to ae (offsets are global in ae).
 void build_alias_f32(int amode, int n, const std::vector<float>* lev, const float* base, int shift, int j0,
-                     int MT, const std::vector<float>& H, std::vector<uint2>& rows, std::vector<float2>& aw,
-                     std::vector<uint8_t>& ai) {
-    rows.assign((size_t)n * MT, make_uint2(0u, 0u));
+                     int MT, const std::vector<float>& H, std::vector<K5Ent>& ents, std::vector<AliasEnt>& ae) {
+    const size_t e0 = ents.size();
+    ents.resize(e0 + (size_t)n * MT);
+    for (int k = 0; k < n; ++k)
+        for (int m = 0; m < MT; ++m) ents[e0 + (size_t)k * MT + m] = K5Ent{H[(size_t)k * MT + m], 0u, 0u, 0u};
     std::vector<double> w, q;
     std::vector<int> small, large, alias;
     for (int k = 0; k < n; ++k) {
@@ -383,7 +387,8 @@ void build_alias_f32(int amode, int n, const std::vector<float>* lev, const floa
             double tot = 0.0;
             for (double x : w) tot += x;
             const int L = tot > 0.0 ? (int)w.size() : 0;
-            rows[(size_t)k * MT + m] = make_uint2((uint32_t)aw.size(), (uint32_t)L);
+            ents[e0 + (size_t)k * MT + m].off = (uint32_t)ae.size();
+            ents[e0 + (size_t)k * MT + m].L = (uint32_t)L;
             if (L == 0) continue;
             // Vose: scaled probabilities L w_i / W, split into small and large
             q.assign(L, 0.0);
@@ -405,8 +410,14 @@ void build_alias_f32(int amode, int n, const std::vector<float>* lev, const floa
             for (int i : large) q[i] = 1.0;
             for (int i : small) q[i] = 1.0;  // rounding leftovers
             for (int i = 0; i < L; ++i) {
-                aw.push_back(make_float2((float)q[i], (float)w[i]));
-                ai.push_back((uint8_t)alias[i]);
+                AliasEnt a{};
+                a.prob = (float)q[i];
+                a.wg_j = (float)w[i];
+                a.e_j = lev[k][i];
+                a.alias = (uint32_t)alias[i];
+                a.wg_a = (float)w[alias[i]];
+                a.e_a = lev[k][alias[i]];
+                ae.push_back(a);
             }
         }
     }
@@ -519,6 +530,12 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
     CU(dalloc(ctx, &ctx->d_pbase, (size_t)MAX_ROUNDS * (total + 1)));
     CU(dalloc(ctx, &ctx->d_abase, (size_t)total + 1));
     CU(dalloc(ctx, &ctx->d_nbase, (size_t)total + 1));
+    dfree(ctx, ctx->d_tsum);
+    {
+        const size_t nts = (size_t)SETUP_ARRAYS * (setup_tiles(total) + 1) + 1;
+        CU(dalloc(ctx, &ctx->d_tsum, nts));
+        CU(cudaMemsetAsync(ctx->d_tsum, 0, sizeof(uint32_t) * nts, ctx->stream));
+    }
     CU(dalloc(ctx, &ctx->d_csum, (size_t)5 * cells_alloc));
     if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
         dfree(ctx, ctx->d_cflag);
@@ -690,9 +707,8 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.levfix = ctx->d_levfix;
     a.H64 = ctx->d_H64;
     a.H32 = ctx->d_H32;
-    a.arow = ctx->d_arow;
-    a.aw = ctx->d_aw;
-    a.ai = ctx->d_ai;
+    a.k5e = ctx->d_k5e;
+    a.ae = ctx->d_ae;
     a.cells = ctx->d_cells;
     a.n_cells = ctx->n_cells_total;
     a.res = ctx->d_res;
@@ -713,6 +729,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.Tnode = ctx->d_Tnode;
     a.csum = ctx->d_csum;
     a.nbase = ctx->d_nbase;
+    a.tsum = ctx->d_tsum;
     a.chbase = ctx->d_chbase;
     a.chcnt = ctx->d_chcnt;
     a.work = ctx->d_work;
@@ -795,9 +812,8 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_levfix);
     dfree(ctx, ctx->d_H64);
     dfree(ctx, ctx->d_H32);
-    dfree(ctx, ctx->d_arow);
-    dfree(ctx, ctx->d_aw);
-    dfree(ctx, ctx->d_ai);
+    dfree(ctx, ctx->d_k5e);
+    dfree(ctx, ctx->d_ae);
     dfree(ctx, ctx->d_res);
     dfree(ctx, ctx->d_cells);
     dfree(ctx, ctx->d_cellcnt);
@@ -816,6 +832,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_csum);
     dfree(ctx, ctx->d_nbase);
     dfree(ctx, ctx->d_chbase);
+    dfree(ctx, ctx->d_tsum);
     dfree(ctx, ctx->d_chcnt);
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
@@ -900,9 +917,8 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     const int MT = M + TABLE_PAD;
     std::vector<double> H64;
     std::vector<float> H32;
-    std::vector<uint2> arow;
-    std::vector<float2> aw;
-    std::vector<uint8_t> ai;
+    std::vector<K5Ent> k5e;
+    std::vector<AliasEnt> ae;
     for (int i = 0; i < n; ++i) {
         HostSpecies& s = ctx->sp[i];
         DevSpecies& D = C.sp[i];
@@ -971,11 +987,9 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
                 D.gj0 = (int)(sb >> D.gshift) - M;
                 std::vector<float> t;
                 build_tables_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t);
-                std::vector<uint2> rows;
-                build_alias_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t, rows, aw, ai);
                 D.tab_off = (int)H32.size();
+                build_alias_f32(amode, nm, L, D.base_f, D.gshift, D.gj0, MT, t, k5e, ae);
                 H32.insert(H32.end(), t.begin(), t.end());
-                arow.insert(arow.end(), rows.begin(), rows.end());
                 D.top = (double)bucket_top_f32(D.base_f[0], D.gshift, D.gj0, MT, M);
             }
         }
@@ -1002,19 +1016,15 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     }
     if (!H32.empty()) {
         dfree(ctx, ctx->d_H32);
-        dfree(ctx, ctx->d_arow);
-        dfree(ctx, ctx->d_aw);
-        dfree(ctx, ctx->d_ai);
+        dfree(ctx, ctx->d_k5e);
+        dfree(ctx, ctx->d_ae);
         CU(dalloc(ctx, &ctx->d_H32, H32.size()));
         CU(cudaMemcpyAsync(ctx->d_H32, H32.data(), sizeof(float) * H32.size(), cudaMemcpyHostToDevice, ctx->stream));
-        CU(dalloc(ctx, &ctx->d_arow, arow.size()));
-        CU(cudaMemcpyAsync(ctx->d_arow, arow.data(), sizeof(uint2) * arow.size(), cudaMemcpyHostToDevice, ctx->stream));
-        CU(dalloc(ctx, &ctx->d_aw, std::max<size_t>(aw.size(), 1)));
-        CU(dalloc(ctx, &ctx->d_ai, std::max<size_t>(ai.size(), 1)));
-        if (!aw.empty()) {
-            CU(cudaMemcpyAsync(ctx->d_aw, aw.data(), sizeof(float2) * aw.size(), cudaMemcpyHostToDevice, ctx->stream));
-            CU(cudaMemcpyAsync(ctx->d_ai, ai.data(), ai.size(), cudaMemcpyHostToDevice, ctx->stream));
-        }
+        CU(dalloc(ctx, &ctx->d_k5e, k5e.size()));
+        CU(cudaMemcpyAsync(ctx->d_k5e, k5e.data(), sizeof(K5Ent) * k5e.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CU(dalloc(ctx, &ctx->d_ae, std::max<size_t>(ae.size(), 1)));
+        if (!ae.empty())
+            CU(cudaMemcpyAsync(ctx->d_ae, ae.data(), sizeof(AliasEnt) * ae.size(), cudaMemcpyHostToDevice, ctx->stream));
     }
     return upload_consts(ctx);
 }
@@ -1392,7 +1402,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             CU(e);
             ctx->graph_args = a;
         }
-        const uint64_t per_step = 3 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2) +
+        const uint64_t per_step = setup_launches(a.n_cells) + 2 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2) +
                                   (a.has_recomb ? 2 : 0) + (ctx->hc.creates ? 1 : 0);
         for (int s = 0; s < n_steps; ++s) {
             CU(cudaGraphLaunch(ctx->graph, ctx->stream));
@@ -1428,7 +1438,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             auto& ev = pool[ctx->prof_used[k]++];
             CU(cudaEventRecord(ev.first, ctx->stream));
             if (k == 0) {
-                launch_setup(a, ctx->stream);
+                ctx->launches += launch_setup(a, ctx->stream) - 1;
                 if (a.has_recomb) {
                     if (f64) launch_cellstats<double>(a, ctx->stream);
                     else launch_cellstats<float>(a, ctx->stream);

@@ -20,6 +20,12 @@ constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard ca
 constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)
 constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
 constexpr int FINISH_CHUNK = 1024;  // pair slots per warp of the end-of-step kernels
+constexpr int SETUP_TILE = 256;     // cells per CTA of the step set-up
+// prefix arrays built by the set-up: pairs of rounds 0..MAX_ROUNDS-1, all
+// pairs, FINISH_CHUNK chunks, particles
+enum { SA_ALL = MAX_ROUNDS, SA_CHUNK, SA_PART, SETUP_ARRAYS };
+inline int setup_tiles(int n_cells) { return n_cells <= SETUP_TILE ? 1 : (n_cells + SETUP_TILE - 1) / SETUP_TILE; }
+inline int setup_launches(int n_cells) { return setup_tiles(n_cells) == 1 ? 1 : 2; }
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
@@ -73,6 +79,26 @@ struct DevSpecies {
     long long De_fix[MAXM];
 };
 
+// FP32 K5 table entry of (species, mode k, bucket m), parallel to the float
+// tables: the table value at the bucket's upper edge, and the bucket's alias
+// table (first slot, slots = levels below the edge; 0 if no level fits).
+// Looking up the acceptance weight of mode k's draw also fetches mode k+1's
+// alias table: both index the same bucket.
+struct alignas(16) K5Ent {
+    float H;
+    uint32_t off, L, pad;
+};
+
+// One alias-table slot j of a bucket: threshold, then level j's and its
+// alias's weight at the bucket edge and float energy.  32 bytes on a 32-byte
+// boundary: a proposal reads one sector whichever level it lands on.
+struct alignas(32) AliasEnt {
+    float prob, wg_j, e_j;
+    uint32_t alias;
+    float wg_a, e_a;
+    uint32_t pad[2];
+};
+
 struct DevPair {
     double mr, C, mt, fp, fq;        // reduced mass, VHS constant, total mass, velocity shares
     float mr_f, C_f, fp_f, fq_f, inv2mr_f, pad_f;
@@ -124,9 +150,8 @@ struct StepArgs {
     const long long* levfix;        // level energies in 2^-100 J units (FP32-mode bookkeeping)
     const double* H64;
     const float* H32;
-    const uint2* arow;              // FP32 alias proposals, parallel to H32: (first entry, entries)
-    const float2* aw;               // per entry: alias threshold, weight of the entry's level
-    const uint8_t* ai;              // per entry: alias level
+    const K5Ent* k5e;               // FP32 K5 tables with their alias proposals, parallel to H32
+    const AliasEnt* ae;             // FP32 alias-table slots
     DevCell* cells;
     int n_cells;
     DevRes* res;
@@ -150,6 +175,7 @@ struct StepArgs {
     const double* Tnode;            // [REC_NODES]
     long long* csum;                // [n_cells][5] integer sums: E (2^-96 J), p (2^-104), m (2^-120)
     uint32_t* nbase;                // [n_cells + 1]: particle prefix at step start
+    uint32_t* tsum;                 // [SETUP_ARRAYS][setup tiles + 1] tile totals, then a ticket
     unsigned long long* work;       // [4] K5 level evaluations, mode starts, molecule samples, pairs
     int grid_select, grid_relax, grid_react;  // launch shapes (host-side; results do not depend on them)
     uint64_t pair_cap;              // capacity of cflag / log
@@ -167,7 +193,7 @@ template <> struct RecOf<double> { using T = RecD; };
 
 template <class R> void launch_step(const StepArgs& a, int grid_collide, int block_collide,
                                     cudaStream_t s, uint64_t* launches);
-void launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu)
+int launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu); returns launches
 void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, const int32_t* sp,
                           const uint8_t* qn, int64_t n, uint32_t* flags, cudaStream_t s);
 template <class R> void launch_collide(const StepArgs& a, int r, int grid, int block, cudaStream_t s);

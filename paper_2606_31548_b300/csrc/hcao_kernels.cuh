@@ -742,15 +742,16 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
 // w_i at the bucket's upper edge) and accepted with probability
 // w_i(E)/w_i(edge); a rejection restarts the trial.  That is the K5 mode
 // draw (level i with probability w_i(E)/H_k[idx(E)], restart otherwise) in
-// constant work per mode.  Returns S_OK with the levels in q and their
+// constant work per mode.  Per mode two dependent loads: the proposal's slot
+// (its level, edge weight and energy in one sector) and the table entry of
+// the remaining budget, whose H is the acceptance weight and whose alias
+// table serves the next mode.  Returns S_OK with the levels in q and their
 // fixed-point energy in Esel, S_OVER, S_DEGEN or S_CAP.  Counts mode draws
 // and level evaluations (one per draw).
 static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode, float Ec,
                                        Stream& st, uint32_t (&q)[4], long long& Esel, uint32_t& trials,
                                        uint32_t& wlev, uint32_t& wmode) {
-    const float* __restrict__ Lv = A.lev32;
-    const float* __restrict__ H = A.H32 + S.tab_off;
-    const uint2* __restrict__ rows = A.arow + S.tab_off;
+    const K5Ent* __restrict__ T = A.k5e + S.tab_off;
     const int n = S.n_modes, MT = S.MT, gsh = S.gshift, gj0 = S.gj0;
     q[0] = q[1] = q[2] = q[3] = 0u;
     Esel = S.zpe_fix;
@@ -758,7 +759,9 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
     const float b0 = S.base_f[0];
     const int m0 = grid_idx_f32(b0, gsh, gj0, MT, Ec);
     if (m0 > S.M) return S_OVER;
-    if (m0 == 0 || !(__ldg(H + m0) > 0.f)) return S_DEGEN;
+    if (m0 == 0) return S_DEGEN;
+    const uint4 t0 = __ldg(reinterpret_cast<const uint4*>(T + m0));
+    if (!(__uint_as_float(t0.x) > 0.f)) return S_DEGEN;
     if (__fsub_rn(Ec, b0) < S.eps_min_f) return S_OK;  // only the ground state fits
     for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
         trials++;
@@ -766,25 +769,22 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
         long long es = 0;
         float E = Ec;
         bool ok = true;
+        uint32_t off = t0.y, L = t0.z;
         for (int k = 0; k < n; ++k) {
-            const int m = k == 0 ? m0 : min(grid_idx_f32(S.base_f[k], gsh, gj0, MT, E), MT - 1);
-            const uint2 row = __ldg(rows + k * MT + m);
             wmode++;
-            if (row.y == 0u) { ok = false; break; }
-            // proposal: 24 random bits give the entry (integer part of r L) and the coin
+            if (L == 0u) { ok = false; break; }
+            // proposal: 24 random bits give the slot (integer part of r L) and the coin
             const uint32_t rbits = st_bits24(st);
-            const uint64_t rl = (uint64_t)rbits * row.y;
+            const uint64_t rl = (uint64_t)rbits * L;
             const uint32_t j = (uint32_t)(rl >> 24);
             const float coin = (float)(uint32_t)(rl & 0xFFFFFFu) * 0x1p-24f;
-            const float2 awj = __ldg(A.aw + row.x + j);
-            uint32_t i = j;
-            float wg = awj.y;
-            if (!(coin < awj.x)) {
-                i = __ldg(A.ai + row.x + j);
-                wg = __ldg(A.aw + row.x + i).y;
-            }
+            const float4* slot = reinterpret_cast<const float4*>(A.ae + off + j);
+            const float4 s0 = __ldg(slot), s1 = __ldg(slot + 1);
+            const bool own = coin < s0.x;
+            const uint32_t i = own ? j : __float_as_uint(s0.w);
+            const float wg = own ? s0.y : s1.x;
+            const float e = own ? s0.z : s1.y;
             // acceptance at the actual budget
-            const float e = __ldg(Lv + S.lev_off[k] + i);
             float wE = 0.f;
             if (e < E) {
                 const float x = __fsub_rn(E, e);
@@ -792,7 +792,12 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
                     wE = lb_pow_fast(amode, x);
                 } else {
                     const int mm = grid_idx_f32(S.base_f[k + 1], gsh, gj0, MT, x);
-                    wE = mm == 0 ? 0.f : __ldg(H + (k + 1) * MT + min(mm, MT - 1));
+                    if (mm != 0) {
+                        const uint4 tn = __ldg(reinterpret_cast<const uint4*>(T + (k + 1) * MT + min(mm, MT - 1)));
+                        wE = __uint_as_float(tn.x);
+                        off = tn.y;
+                        L = tn.z;
+                    }
                 }
             }
             wlev++;
@@ -1289,48 +1294,22 @@ __device__ __forceinline__ int cell_of(const uint32_t* pb, int n_cells, uint32_t
 }
 
 // ------------------------------------------------------------- kernels
-constexpr int SETUP_THREADS = 1024;
 #ifdef HCAO_COMMON_KERNELS
 
-// inclusive scan of a[1..n] in place (a[0] = 0 kept), one CTA
-static __device__ void block_scan_inplace(uint32_t* a, int n) {
-    __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) carry = 0;
-    __syncthreads();
-    for (int base = 1; base <= n; base += blockDim.x) {
-        const int i = base + tid;
-        uint32_t v = i <= n ? a[i] : 0u;
+// Per-cell step set-up, one thread per cell, SETUP_TILE cells per CTA: the
+// NTC candidate count N_sel (stochastically rounded), the rounds and their
+// Feistel keys, and the counts behind the step's prefix arrays -- pairs per
+// round, all pairs, FINISH_CHUNK chunks and (with recombination) particles.
+// Each CTA writes the inclusive scans of its tile into the arrays and the
+// tile's totals into tsum; the last CTA to finish (a ticket counter, no
+// waiting) scans the tile totals, which k_setup_fix then adds to the tiles.
+static __global__ void __launch_bounds__(SETUP_TILE) k_setup_cells(StepArgs A) {
+    const int nc = A.n_cells, R = A.max_rounds, nt = (int)gridDim.x;
+    const int c = blockIdx.x * SETUP_TILE + threadIdx.x;
+    uint32_t v[SETUP_ARRAYS];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
-            if (lane >= o) v += t;
-        }
-        if (lane == 31) wsum[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
-                if (lane >= o) w += t;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        const uint32_t add = carry + (wid > 0 ? wsum[wid - 1] : 0u);
-        if (i <= n) a[i] = v + add;
-        __syncthreads();
-        if (tid == 0) carry += wsum[(blockDim.x >> 5) - 1];
-        __syncthreads();
-    }
-}
-
-static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
-    const int nc = A.n_cells;
-    const int R = A.max_rounds;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    for (int q = 0; q < SETUP_ARRAYS; ++q) v[q] = 0u;
+    if (c < nc) {
         DevCell& cl = A.cells[c];
         const DevRes rs = A.res[cl.res];
         const uint32_t N = cl.n;
@@ -1364,42 +1343,119 @@ static __global__ void __launch_bounds__(SETUP_THREADS) k_setup(StepArgs A) {
         cl.ncreated = 0;
         cl.seen = 0ull;
         cl.sgmax_f = (float)cl.sgmax;
-        for (int r = 0; r < R; ++r) {
-            uint32_t cnt = 0;
+        cl.nremoved = 0u;
+#pragma unroll
+        for (int r = 0; r < MAX_ROUNDS; ++r)
             if ((uint32_t)r < rounds) {
                 const uint32_t left = nsel - (uint32_t)r * P;
-                cnt = left < P ? left : P;
+                v[r] = left < P ? left : P;
             }
-            A.pbase[r * (nc + 1) + c + 1] = cnt;
-        }
-        A.abase[c + 1] = nsel;
-        A.chbase[c + 1] = (nsel + (uint32_t)FINISH_CHUNK - 1u) / (uint32_t)FINISH_CHUNK;
-        cl.nremoved = 0u;
+        v[SA_ALL] = nsel;
+        v[SA_CHUNK] = (nsel + (uint32_t)FINISH_CHUNK - 1u) / (uint32_t)FINISH_CHUNK;
         if (A.has_recomb) {
-            A.nbase[c + 1] = N;
+            v[SA_PART] = N;
             for (int q = 0; q < 5; ++q) A.csum[5 * (size_t)c + q] = 0ll;
         }
     }
+    // tile-local inclusive scans of all arrays at once
+    __shared__ uint32_t ws[SETUP_ARRAYS][SETUP_TILE / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < SETUP_ARRAYS; ++q) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v[q], o);
+            if (lane >= o) v[q] += t;
+        }
+        if (lane == 31) ws[q][wid] = v[q];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < SETUP_ARRAYS; ++q) {
+            uint32_t w = lane < SETUP_TILE / 32 ? ws[q][lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < SETUP_TILE / 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < SETUP_TILE / 32) ws[q][lane] = w;
+        }
+    }
+    __syncthreads();
+    if (wid > 0) {
+#pragma unroll
+        for (int q = 0; q < SETUP_ARRAYS; ++q) v[q] += ws[q][wid - 1];
+    }
+    if (c < nc) {
+#pragma unroll
+        for (int r = 0; r < MAX_ROUNDS; ++r)
+            if (r < R) A.pbase[r * (nc + 1) + c + 1] = v[r];
+        A.abase[c + 1] = v[SA_ALL];
+        A.chbase[c + 1] = v[SA_CHUNK];
+        if (A.has_recomb) A.nbase[c + 1] = v[SA_PART];
+    }
+    // tile totals: tsum[q][t + 1]; the exclusive prefix of tile t ends up at tsum[q][t]
+    if (threadIdx.x < SETUP_ARRAYS) A.tsum[threadIdx.x * (nt + 1) + blockIdx.x + 1] = ws[threadIdx.x][SETUP_TILE / 32 - 1];
+    __threadfence();
+    __shared__ uint32_t last;
+    if (threadIdx.x == 0) last = atomicAdd(A.tsum + SETUP_ARRAYS * (nt + 1), 1u) == (uint32_t)(nt - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // warp q scans array q's tile totals in place: tsum[q][t] becomes the
+    // exclusive prefix of tile t, tsum[q][nt] the array's total
+    for (int q = wid; q < SETUP_ARRAYS; q += SETUP_TILE / 32) {
+        uint32_t* ts = A.tsum + q * (nt + 1);
+        uint32_t carry = 0u;
+        for (int b = 0; b < nt; b += 32) {
+            const int t = b + lane;
+            uint32_t x = t < nt ? __ldcg(ts + t + 1) : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (t < nt) ts[t + 1] = carry + x;
+            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        }
+        if (lane == 0) ts[0] = 0u;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1)] = 0;
+        for (int r = 0; r < R; ++r) {
+            A.pbase[r * (nc + 1)] = 0;
+            A.totals[r] = A.tsum[r * (nt + 1) + nt];
+        }
         A.abase[0] = 0;
         A.chbase[0] = 0;
         if (A.has_recomb) A.nbase[0] = 0;
+        A.totals[MAX_ROUNDS] = A.tsum[SA_ALL * (nt + 1) + nt];
+        A.totals[MAX_ROUNDS + 1] = A.tsum[SA_CHUNK * (nt + 1) + nt];
         for (int i = 0; i < 3 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
-    }
-    __syncthreads();
-    for (int r = 0; r < R; ++r) block_scan_inplace(A.pbase + r * (nc + 1), nc);
-    block_scan_inplace(A.abase, nc);
-    block_scan_inplace(A.chbase, nc);
-    if (A.has_recomb) block_scan_inplace(A.nbase, nc);
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < R; ++r) A.totals[r] = A.pbase[r * (nc + 1) + nc];
-        A.totals[MAX_ROUNDS] = A.abase[nc];
-        A.totals[MAX_ROUNDS + 1] = A.chbase[nc];
+        A.tsum[SETUP_ARRAYS * (nt + 1)] = 0u;  // ticket, for the next step
     }
 }
 
-void launch_setup(const StepArgs& a, cudaStream_t s) { k_setup<<<1, SETUP_THREADS, 0, s>>>(a); }
+// adds the scanned tile totals to tiles 1.. (tile 0 is complete)
+static __global__ void __launch_bounds__(SETUP_TILE) k_setup_fix(StepArgs A) {
+    const int nc = A.n_cells, R = A.max_rounds, nt = (int)gridDim.x + 1;
+    const int t = blockIdx.x + 1;
+    const int c = t * SETUP_TILE + threadIdx.x;
+    if (c >= nc) return;
+    for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1) + c + 1] += __ldcg(A.tsum + r * (nt + 1) + t);
+    A.abase[c + 1] += __ldcg(A.tsum + SA_ALL * (nt + 1) + t);
+    A.chbase[c + 1] += __ldcg(A.tsum + SA_CHUNK * (nt + 1) + t);
+    if (A.has_recomb) A.nbase[c + 1] += __ldcg(A.tsum + SA_PART * (nt + 1) + t);
+}
+
+int launch_setup(const StepArgs& a, cudaStream_t s) {
+    const int nt = setup_tiles(a.n_cells);
+    k_setup_cells<<<nt, SETUP_TILE, 0, s>>>(a);
+    if (nt == 1) return 1;
+    k_setup_fix<<<nt - 1, SETUP_TILE, 0, s>>>(a);
+    return 2;
+}
 
 // Load-path validation of staged host arrays: cell and species in range,
 // every quantum number inside its mode's level list (0 beyond the species'
@@ -2282,13 +2338,14 @@ void launch_compact_impl(const StepArgs& a, cudaStream_t s) {
 }
 template <class R>
 void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, uint64_t* launches) {
-    launch_setup(a, s);
+    const int ns = launch_setup(a, s);
     launch_cellstats_impl<R>(a, s);
     for (int r = 0; r < a.max_rounds; ++r) launch_collide_impl<R>(a, r, grid, block, s);
     launch_finish_impl<R>(a, s);
     launch_compact_impl<R>(a, s);
     if (launches)
-        *launches += 3 + a.max_rounds * (a.has_reactions ? 3 : 2) + (a.has_recomb ? 2 : 0) + (a.creates ? 1 : 0);
+        *launches += ns + 2 + a.max_rounds * (a.has_reactions ? 3 : 2) + (a.has_recomb ? 2 : 0) +
+                     (a.creates ? 1 : 0);
 }
 
 // ------------------------------------------------------------- sampler diagnostics
