@@ -34,12 +34,13 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffi
 # least integer/FP32 lane operations each unit needs):
 #   level evaluation (the acceptance weight at the budget): 2 loads, subtract,
 #     bucket index (bit cast, shift, subtract, 2 clamps), table offset, compare = 12
-#   mode draw: two quarters of a Philox4x32-10 block (2 x 10 rounds x 8 ops / 4)
-#     + alias entry (multiply, shift, 2 loads, compare, select) + 8 = 54
+#   mode draw: one quarter of a Philox4x32-10 block (10 rounds x 8 ops / 4)
+#     + alias slot (multiply, shift, 2 loads, compare, 3 selects) + acceptance
+#     on the word's low 8 bits (2 conversions, 2 multiplies, 2 compares) = 34
 #   molecule sample: vibrational energy of up to 9 modes twice + setup = 60
 #   pair: members, two record loads, relative energy, isotropic direction,
 #     scattering, two record stores, event word = 160
-OPS_PER_UNIT = (12, 54, 60, 160)
+OPS_PER_UNIT = (12, 34, 60, 160)
 SMS, LANES_PER_SM = 148, 128
 
 

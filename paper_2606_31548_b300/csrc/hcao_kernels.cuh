@@ -116,19 +116,16 @@ __device__ __forceinline__ double st_u64(Stream& s) {
     uint64_t m = ((uint64_t)(a >> 5) << 26) | (uint64_t)(b >> 6);
     return (double)m * 0x1p-53;
 }
-__device__ __forceinline__ float st_u32(Stream& s) {
+// the next 32-bit word
+__device__ __forceinline__ uint32_t st_word(Stream& s) {
     if (s.pos > 3) { st_block(s); s.pos = 0; }
     const uint32_t w = s.pos == 0 ? s.w0 : (s.pos == 1 ? s.w1 : (s.pos == 2 ? s.w2 : s.w3));
     s.pos++;
-    return (float)(w >> 8) * 0x1p-24f;
+    return w;
 }
+__device__ __forceinline__ float st_u32(Stream& s) { return (float)(st_word(s) >> 8) * 0x1p-24f; }
 // the top 24 bits of the next word (the bits behind st_u32)
-__device__ __forceinline__ uint32_t st_bits24(Stream& s) {
-    if (s.pos > 3) { st_block(s); s.pos = 0; }
-    const uint32_t w = s.pos == 0 ? s.w0 : (s.pos == 1 ? s.w1 : (s.pos == 2 ? s.w2 : s.w3));
-    s.pos++;
-    return w >> 8;
-}
+__device__ __forceinline__ uint32_t st_bits24(Stream& s) { return st_word(s) >> 8; }
 template <class R> __device__ __forceinline__ R st_uni(Stream& s);
 template <> __device__ __forceinline__ double st_uni<double>(Stream& s) { return st_u64(s); }
 template <> __device__ __forceinline__ float st_uni<float>(Stream& s) { return st_u32(s); }
@@ -773,8 +770,10 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
         for (int k = 0; k < n; ++k) {
             wmode++;
             if (L == 0u) { ok = false; break; }
-            // proposal: 24 random bits give the slot (integer part of r L) and the coin
-            const uint32_t rbits = st_bits24(st);
+            // one word: its top 24 bits give the slot (integer part of r L) and
+            // the coin, its low 8 bits the top bits of the acceptance uniform
+            const uint32_t rw = st_word(st);
+            const uint32_t rbits = rw >> 8, u8 = rw & 0xFFu;
             const uint64_t rl = (uint64_t)rbits * L;
             const uint32_t j = (uint32_t)(rl >> 24);
             const float coin = (float)(uint32_t)(rl & 0xFFFFFFu) * 0x1p-24f;
@@ -801,7 +800,15 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
                 }
             }
             wlev++;
-            if (!(st_u32(st) * wg < wE)) { ok = false; break; }
+            // accept if u wg < wE, u = (u8 2^16 + b) 2^-24 with 16 more bits b
+            // drawn only when u8 leaves the test open: rounding is monotone, so
+            // fl(u8 2^-8 wg) >= wE rejects and fl((u8+1) 2^-8 wg) < wE accepts
+            // for every b, the decision of the full 24-bit test either way
+            if (!(__fmul_rn((float)(u8 + 1u) * 0x1p-8f, wg) < wE)) {
+                if (!(__fmul_rn((float)u8 * 0x1p-8f, wg) < wE)) { ok = false; break; }
+                const float u = (float)((u8 << 16) | (st_word(st) >> 16)) * 0x1p-24f;
+                if (!(__fmul_rn(u, wg) < wE)) { ok = false; break; }
+            }
             set_q(nq, k, i);
             E = __fsub_rn(E, e);
             es += __ldg(A.levfix + S.lev_off[k] + i);
@@ -815,53 +822,55 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
     return S_CAP;
 }
 
-// FP32 LB relaxation of up to two molecules (molecule 1, then molecule 2
-// with the updated relative energy, in int64 fixed point); sp < 0 or a
-// species without modes skips a molecule.  Returns the relative energy left
-// for scattering.
-static __device__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C, int spA,
-                                       uint32_t (&qA)[4], long long EvA, Stream stA, int spB,
-                                       uint32_t (&qB)[4], long long EvB, Stream stB, long long Erel,
-                                       PairOut& o, uint32_t* work = nullptr) {
-    uint32_t wl = 0, wm = 0;
-    for (int mol = 0; mol < 2; ++mol) {
-        const int sp = mol ? spB : spA;
-        if (sp < 0 || C->sp[sp].n_modes == 0) continue;
-        const DevSpecies& S = C->sp[sp];
-        const long long Evold = mol ? EvB : EvA;
-        const long long Ecd = Erel + Evold;
-        Stream& st = mol ? stB : stA;
-        o.ev += 1u << EV_SAMP_SHIFT;
-        uint32_t nq[4];
-        long long Esel;
-        uint32_t tr = 0;
-        const int rc = sample_alias_f32(A, S, C->amode, fix2f(Ecd), st, nq, Esel, tr, wl, wm);
-        o.trials += tr;
-        Erel = Ecd - Evold;  // the state is kept unless a new one is drawn
-        if (rc == S_OK) {
-            const long long En = Ecd - Esel;
-            if (En >= 0) {
-                uint32_t (&qd)[4] = mol ? qB : qA;
-                qd[0] = nq[0]; qd[1] = nq[1]; qd[2] = nq[2]; qd[3] = nq[3];
-                Erel = En;
-            } else {
-                o.ev += 1u << EV_DEGEN_SHIFT;
-            }
-        } else if (rc == S_OVER) {
-            o.ev += 1u << EV_OVER_SHIFT;
-        } else if (rc == S_DEGEN) {
-            o.ev += 1u << EV_DEGEN_SHIFT;
-        } else {
-            atomicOr(A.err, (uint32_t)ERR_REJECT);
+// FP32 LB relaxation of one molecule of species sp (levels q, fixed-point
+// E_vib Evold) against the relative energy Erel; returns the relative energy
+// left.  sp < 0 or a species without modes keeps everything.
+static __device__ __forceinline__ long long relax_one(const StepArgs& A, const Consts* __restrict__ C, int sp,
+                                                      uint32_t (&q)[4], long long Evold, Stream& st,
+                                                      long long Erel, PairOut& o, uint32_t& wl, uint32_t& wm) {
+    if (sp < 0 || C->sp[sp].n_modes == 0) return Erel;
+    const DevSpecies& S = C->sp[sp];
+    const long long Ecd = Erel + Evold;
+    o.ev += 1u << EV_SAMP_SHIFT;
+    uint32_t nq[4];
+    long long Esel;
+    uint32_t tr = 0;
+    const int rc = sample_alias_f32(A, S, C->amode, fix2f(Ecd), st, nq, Esel, tr, wl, wm);
+    o.trials += tr;
+    if (rc == S_OK) {
+        const long long En = Ecd - Esel;
+        if (En >= 0) {
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            return En;
         }
+        o.ev += 1u << EV_DEGEN_SHIFT;
+    } else if (rc == S_OVER) {
+        o.ev += 1u << EV_OVER_SHIFT;
+    } else if (rc == S_DEGEN) {
+        o.ev += 1u << EV_DEGEN_SHIFT;
+    } else {
+        atomicOr(A.err, (uint32_t)ERR_REJECT);
     }
+    return Ecd - Evold;  // the state is kept
+}
+
+// FP32 LB relaxation of up to two molecules: molecule 1, then molecule 2
+// with the updated relative energy, in int64 fixed point.  Returns the
+// relative energy left for scattering.
+static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const Consts* __restrict__ C, int spA,
+                                                       uint32_t (&qA)[4], long long EvA, Stream stA, int spB,
+                                                       uint32_t (&qB)[4], long long EvB, Stream stB, long long Erel,
+                                                       PairOut& o, uint32_t* work = nullptr) {
+    uint32_t wl = 0, wm = 0;
+    Erel = relax_one(A, C, spA, qA, EvA, stA, Erel, o, wl, wm);
+    Erel = relax_one(A, C, spB, qB, EvB, stB, Erel, o, wl, wm);
     if (work) { work[0] += wl; work[1] += wm; }
     return Erel;
 }
 
 // FP32 mode: QK reaction test in fixed point (exact thresholds), the same
 // channel order and E_excess-weighted choice as reaction_pick.
-static __device__ int reaction_pick_fix(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
+static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
                                  const uint32_t qP[4], const uint32_t qQ[4], long long Etr,
                                  long long EvP, long long EvQ, float u_ster, float u_sel, float u_ch,
                                  uint32_t& chan) {
@@ -908,7 +917,9 @@ static __device__ int reaction_pick_fix(const StepArgs& A, const Consts* __restr
             else continue;
             if (!(u_ster < (float)rx.steric)) continue;
             const DevSpecies& SA = side ? SQ : SP;
-            const uint32_t* qa = side ? qQ : qP;
+            uint32_t qa[4];  // the words themselves: a pointer chosen at run time puts both arrays in memory
+#pragma unroll
+            for (int w = 0; w < 4; ++w) qa[w] = side ? qQ[w] : qP[w];
             long long s = 0;
             if (rx.alpha_mode == HCAO_ALPHA_ONE_RANDOM_STRETCH) {
                 const int js = min((int)(u_sel * (float)SA.n_stretch), SA.n_stretch - 1);
