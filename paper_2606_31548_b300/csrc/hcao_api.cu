@@ -412,11 +412,9 @@ void build_alias_f32(int amode, int n, const std::vector<float>* lev, const floa
             for (int i = 0; i < L; ++i) {
                 AliasEnt a{};
                 a.prob = (float)q[i];
-                a.wg_j = (float)w[i];
-                a.e_j = lev[k][i];
                 a.alias = (uint32_t)alias[i];
+                a.wg_j = (float)w[i];
                 a.wg_a = (float)w[alias[i]];
-                a.e_a = lev[k][alias[i]];
                 ae.push_back(a);
             }
         }

@@ -89,14 +89,13 @@ struct alignas(16) K5Ent {
     uint32_t off, L, pad;
 };
 
-// One alias-table slot j of a bucket: threshold, then level j's and its
-// alias's weight at the bucket edge and float energy.  32 bytes on a 32-byte
-// boundary: a proposal reads one sector whichever level it lands on.
-struct alignas(32) AliasEnt {
-    float prob, wg_j, e_j;
+// One alias-table slot j of a bucket: threshold, alias, and level j's and
+// its alias's weights at the bucket edge; 16 bytes on a 16-byte boundary.
+// The levels' energies come from the (L1-resident) level lists.
+struct alignas(16) AliasEnt {
+    float prob;
     uint32_t alias;
-    float wg_a, e_a;
-    uint32_t pad[2];
+    float wg_j, wg_a;
 };
 
 struct DevPair {

@@ -739,10 +739,11 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
 // w_i at the bucket's upper edge) and accepted with probability
 // w_i(E)/w_i(edge); a rejection restarts the trial.  That is the K5 mode
 // draw (level i with probability w_i(E)/H_k[idx(E)], restart otherwise) in
-// constant work per mode.  Per mode two dependent loads: the proposal's slot
-// (its level, edge weight and energy in one sector) and the table entry of
-// the remaining budget, whose H is the acceptance weight and whose alias
-// table serves the next mode.  Returns S_OK with the levels in q and their
+// constant work per mode.  Per mode two dependent loads from the larger
+// tables: the proposal's 16-byte slot (threshold, alias, both edge weights)
+// and the table entry of the remaining budget, whose H is the acceptance
+// weight and whose alias table serves the next mode; the level energy comes
+// from the small level list.  Returns S_OK with the levels in q and their
 // fixed-point energy in Esel, S_OVER, S_DEGEN or S_CAP.  Counts mode draws
 // and level evaluations (one per draw).
 static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode, float Ec,
@@ -777,12 +778,13 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
             const uint64_t rl = (uint64_t)rbits * L;
             const uint32_t j = (uint32_t)(rl >> 24);
             const float coin = (float)(uint32_t)(rl & 0xFFFFFFu) * 0x1p-24f;
-            const float4* slot = reinterpret_cast<const float4*>(A.ae + off + j);
-            const float4 s0 = __ldg(slot), s1 = __ldg(slot + 1);
+            const float* lv = A.lev32 + S.lev_off[k];
+            const float4 s0 = __ldg(reinterpret_cast<const float4*>(A.ae + off + j));
+            const float ej = __ldg(lv + j);  // in parallel with the slot
             const bool own = coin < s0.x;
-            const uint32_t i = own ? j : __float_as_uint(s0.w);
-            const float wg = own ? s0.y : s1.x;
-            const float e = own ? s0.z : s1.y;
+            const uint32_t i = own ? j : __float_as_uint(s0.y);
+            const float wg = own ? s0.z : s0.w;
+            const float e = own ? ej : __ldg(lv + i);
             // acceptance at the actual budget
             float wE = 0.f;
             if (e < E) {
