@@ -165,8 +165,9 @@ struct StepArgs {
     void* cscratch;                 // per-pair record of a particle created by a reaction
     uint4* qA;                      // accepted pairs of the current round (cell, pair, ip, iq)
     uint4* qB;                      // reacting pairs (cell, pair, channel)
-    uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax and react queue
-                                    // lengths, then the relax queue's fetch heads
+    uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax-queue entries from
+                                    // the front and react-queue length; then per round
+                                    // FP32 relax-queue entries from the back (qA[pair_cap - 1 - i])
     int has_reactions;
     int has_recomb;
     int creates;                    // a reaction creates particles or removes them (scratch slots)

@@ -826,10 +826,13 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
 
 // FP32 LB relaxation of one molecule of species sp (levels q, fixed-point
 // E_vib Evold) against the relative energy Erel; returns the relative energy
-// left.  sp < 0 or a species without modes keeps everything.
+// left, and took = true when q was replaced by a new state.  sp < 0 or a
+// species without modes keeps everything.
 static __device__ __forceinline__ long long relax_one(const StepArgs& A, const Consts* __restrict__ C, int sp,
                                                       uint32_t (&q)[4], long long Evold, Stream& st,
-                                                      long long Erel, PairOut& o, uint32_t& wl, uint32_t& wm) {
+                                                      long long Erel, PairOut& o, uint32_t& wl, uint32_t& wm,
+                                                      bool& took) {
+    took = false;
     if (sp < 0 || C->sp[sp].n_modes == 0) return Erel;
     const DevSpecies& S = C->sp[sp];
     const long long Ecd = Erel + Evold;
@@ -843,6 +846,7 @@ static __device__ __forceinline__ long long relax_one(const StepArgs& A, const C
         const long long En = Ecd - Esel;
         if (En >= 0) {
             q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            took = true;
             return En;
         }
         o.ev += 1u << EV_DEGEN_SHIFT;
@@ -864,8 +868,9 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
                                                        uint32_t (&qB)[4], long long EvB, Stream stB, long long Erel,
                                                        PairOut& o, uint32_t* work = nullptr) {
     uint32_t wl = 0, wm = 0;
-    Erel = relax_one(A, C, spA, qA, EvA, stA, Erel, o, wl, wm);
-    Erel = relax_one(A, C, spB, qB, EvB, stB, Erel, o, wl, wm);
+    bool took;
+    Erel = relax_one(A, C, spA, qA, EvA, stA, Erel, o, wl, wm, took);
+    Erel = relax_one(A, C, spB, qB, EvB, stB, Erel, o, wl, wm, took);
     if (work) { work[0] += wl; work[1] += wm; }
     return Erel;
 }
@@ -1512,8 +1517,10 @@ void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, con
 
 // Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
 // pairs are finished here; accepted ones go to the relaxation queue.
+constexpr int SELECT_THREADS = 256;
+
 template <class R>
-__global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
+__global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
     using Rec = typename RecOf<R>::T;
     const uint32_t total = A.totals[r];
     const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
@@ -1524,13 +1531,14 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
     if constexpr (std::is_same<R, float>::value) {
         // FP32 mode: no FP64 arithmetic; the second half of a record (the
         // quantum numbers) is read only for accepted pairs when reactions exist
+        __shared__ uint32_t sel_cnt[2][SELECT_THREADS / 32], sel_base[2];
         for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
             const uint32_t g = g0 + threadIdx.x;
             const bool valid = g < total;
             int c = 0;
-            bool accept = false, react = false;
+            bool accept = false, two = false;
             float sgf = 0.f;
-            uint32_t k = 0, ip = 0, iq = 0, chan = 0, mpos = 0;
+            uint32_t k = 0, ip = 0, iq = 0;
             if (valid) {
                 c = cell_of(pb, A.n_cells, g);
                 k = g - __ldg(pb + c);
@@ -1561,16 +1569,42 @@ __global__ void __launch_bounds__(256) k_select(StepArgs A, int r) {
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
                 accept = st_u32(sp) < sgf / cell.sgmax_f;
+                two = C->sp[sP].n_modes > 0 && C->sp[sQ].n_modes > 0;
                 }
                 if (!accept) {
                     A.cflag[ev_idx] = 0u;
                     if (A.log_on) A.log[ev_idx] = hcao_log_rec{rs.step, cell.lcell, rk, ip, iq, -1, 0u};
                 }
             }
-            const uint32_t slot = queue_slot(qsize, accept && !react);
-            if (accept && !react) A.qA[slot] = make_uint4((uint32_t)c, k, ip, iq);
-            const uint32_t rslot = queue_slot(qsize + 1, react);
-            if (react) A.qB[rslot] = make_uint4((uint32_t)c, k, chan, mpos);
+            // pairs with two molecules to relax fill the queue from the front,
+            // the others from the back, so that warps of the relaxation kernel
+            // see mostly one kind (a lane's molecule loop runs once or twice);
+            // one atomic per CTA and end of the queue
+            const bool front = accept && two;
+            {
+                const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+                const unsigned mf = __ballot_sync(0xFFFFFFFFu, front);
+                const unsigned mb = __ballot_sync(0xFFFFFFFFu, accept && !front);
+                if (lane == 0) { sel_cnt[0][wid] = (uint32_t)__popc(mf); sel_cnt[1][wid] = (uint32_t)__popc(mb); }
+                __syncthreads();
+                if (threadIdx.x < 2) {
+                    uint32_t tot = 0u;
+                    for (int w2 = 0; w2 < SELECT_THREADS / 32; ++w2) {
+                        const uint32_t n = sel_cnt[threadIdx.x][w2];
+                        sel_cnt[threadIdx.x][w2] = tot;
+                        tot += n;
+                    }
+                    sel_base[threadIdx.x] =
+                        tot ? atomicAdd(threadIdx.x == 0 ? qsize : A.qsize + 2 * MAX_ROUNDS + r, tot) : 0u;
+                }
+                __syncthreads();
+                const unsigned lt = (1u << lane) - 1u;
+                const uint4 ent = make_uint4((uint32_t)c, k, ip, iq);
+                if (front) A.qA[sel_base[0] + sel_cnt[0][wid] + (uint32_t)__popc(mf & lt)] = ent;
+                else if (accept)
+                    A.qA[A.pair_cap - 1u - (sel_base[1] + sel_cnt[1][wid] + (uint32_t)__popc(mb & lt))] = ent;
+                __syncthreads();  // sel_cnt / sel_base are rewritten in the next pass
+            }
             // per-cell max of sigma_T g: lanes of one cell combine before the atomic
             const unsigned act = __activemask();
             const int lane = threadIdx.x & 31;
@@ -1759,12 +1793,14 @@ template <class R>
 __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
-    const uint32_t total = A.qsize[2 * r];
+    // queue: pairs with two molecules at the front, the others at the back
+    const uint32_t n_front = A.qsize[2 * r];
+    const uint32_t total = n_front + A.qsize[2 * MAX_ROUNDS + r];
     const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t w[2] = {0u, 0u};
     uint32_t w_samp = 0, w_pair = 0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const uint4 e = A.qA[g];
+        const uint4 e = A.qA[g < n_front ? (uint64_t)g : A.pair_cap - 1u - (uint64_t)(g - n_front)];
         const int cidx = (int)e.x;
         const DevCell& cell = A.cells[cidx];
         const DevRes& rs = A.res[cell.res];
@@ -1808,12 +1844,29 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
             A.qB[rslot] = make_uint4((uint32_t)cidx, e.y, chan, mpos);
             continue;
         }
+        // the molecules with modes, P before Q, in one loop: a lane relaxing
+        // its pair's first molecule and a lane relaxing its second (an H-CH3
+        // next to a CH3-H pair) run the same code at the same time
         PairOut o{EV_ACC, 0u};
-        Stream s1, s2;
-        st_init(s1, rs.seed, step, lcell, rk, PU_LB_A);
-        st_init(s2, rs.seed, step, lcell, rk, PU_LB_B);
-        const long long Erel = relax_flat(A, C, sP, qP, EvP, s1, sQ, qQ, EvQ, s2, Etr, o, w);
-        w_samp += (C->sp[sP].n_modes > 0) + (C->sp[sQ].n_modes > 0);
+        long long Erel = Etr;
+        const bool relP = C->sp[sP].n_modes > 0;
+        const int nmol = (int)relP + (int)(C->sp[sQ].n_modes > 0);
+        for (int m = 0; m < nmol; ++m) {
+            const bool isQ = !relP || m == 1;
+            Stream st;
+            st_init(st, rs.seed, step, lcell, rk, isQ ? PU_LB_B : PU_LB_A);
+            uint32_t nq[4];
+            bool took;
+            Erel = relax_one(A, C, isQ ? sQ : sP, nq, isQ ? EvQ : EvP, st, Erel, o, w[0], w[1], took);
+            if (took) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    qP[i] = isQ ? qP[i] : nq[i];
+                    qQ[i] = isQ ? nq[i] : qQ[i];
+                }
+            }
+        }
+        w_samp += (uint32_t)nmol;
         w_pair++;
         Stream ss;
         st_init(ss, rs.seed, step, lcell, rk, PU_SCAT);
@@ -2319,7 +2372,7 @@ void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream
     const int gs = a.grid_select > 0 ? a.grid_select : grid;
     const int gr = a.grid_relax > 0 ? a.grid_relax : grid;
     const int gx = a.grid_react > 0 ? a.grid_react : grid;
-    if (phase == 0) k_select<R><<<gs, 256, 0, s>>>(a, r);
+    if (phase == 0) k_select<R><<<gs, SELECT_THREADS, 0, s>>>(a, r);
     else if (phase == 1) {
         if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<gr, 128, 0, s>>>(a, r);
         else k_relax<R><<<gr, 128, 0, s>>>(a, r);
