@@ -544,7 +544,7 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
         dfree(ctx, ctx->d_qA);
         dfree(ctx, ctx->d_qB);
-        CU(dalloc(ctx, &ctx->d_qA, (size_t)ctx->pair_cap));
+        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)ctx->pair_cap));  // FP32: three regions, see StepArgs::qsize
         CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
     }
@@ -783,7 +783,7 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 2) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_qsize, 3 * MAX_ROUNDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
+        dalloc(ctx, &ctx->d_qsize, QSIZE_WORDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
         delete ctx;
         return HCAO_ENOMEM;
     }

@@ -20,6 +20,7 @@ constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard ca
 constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)
 constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
 constexpr int FINISH_CHUNK = 1024;  // pair slots per warp of the end-of-step kernels
+constexpr int QSIZE_WORDS = 4 * MAX_ROUNDS;  // queue counters (StepArgs::qsize)
 constexpr int SETUP_TILE = 256;     // cells per CTA of the step set-up
 // prefix arrays built by the set-up: pairs of rounds 0..MAX_ROUNDS-1, all
 // pairs, FINISH_CHUNK chunks, particles
@@ -163,11 +164,12 @@ struct StepArgs {
     uint32_t* chcnt;                // [chunks]: particles created in each chunk
     uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
     void* cscratch;                 // per-pair record of a particle created by a reaction
-    uint4* qA;                      // accepted pairs of the current round (cell, pair, ip, iq)
+    uint4* qA;                      // [2 pair_cap] accepted pairs of the current round (cell, pair, ip, iq)
     uint4* qB;                      // reacting pairs (cell, pair, channel)
-    uint32_t* qsize;                // [3 * MAX_ROUNDS]: per round, relax-queue entries from
-                                    // the front and react-queue length; then per round
-                                    // FP32 relax-queue entries from the back (qA[pair_cap - 1 - i])
+    uint32_t* qsize;                // [QSIZE_WORDS]: per round, relax-queue entries at the
+                                    // front and react-queue length; then per round the FP32
+                                    // relax queue's one-molecule entries (qA[2 pair_cap - 1 - i]),
+                                    // then its no-molecule entries (qA[pair_cap + i])
     int has_reactions;
     int has_recomb;
     int creates;                    // a reaction creates particles or removes them (scratch slots)

@@ -1450,7 +1450,7 @@ static __global__ void __launch_bounds__(SETUP_TILE) k_setup_cells(StepArgs A) {
         if (A.has_recomb) A.nbase[0] = 0;
         A.totals[MAX_ROUNDS] = A.tsum[SA_ALL * (nt + 1) + nt];
         A.totals[MAX_ROUNDS + 1] = A.tsum[SA_CHUNK * (nt + 1) + nt];
-        for (int i = 0; i < 3 * MAX_ROUNDS; ++i) A.qsize[i] = 0u;
+        for (int i = 0; i < QSIZE_WORDS; ++i) A.qsize[i] = 0u;
         A.tsum[SETUP_ARRAYS * (nt + 1)] = 0u;  // ticket, for the next step
     }
 }
@@ -1531,12 +1531,13 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
     if constexpr (std::is_same<R, float>::value) {
         // FP32 mode: no FP64 arithmetic; the second half of a record (the
         // quantum numbers) is read only for accepted pairs when reactions exist
-        __shared__ uint32_t sel_cnt[2][SELECT_THREADS / 32], sel_base[2];
+        __shared__ uint32_t sel_cnt[3][SELECT_THREADS / 32], sel_base[3];
         for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
             const uint32_t g = g0 + threadIdx.x;
             const bool valid = g < total;
             int c = 0;
-            bool accept = false, two = false;
+            bool accept = false;
+            int nm = 0;
             float sgf = 0.f;
             uint32_t k = 0, ip = 0, iq = 0;
             if (valid) {
@@ -1569,40 +1570,48 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
                 accept = st_u32(sp) < sgf / cell.sgmax_f;
-                two = C->sp[sP].n_modes > 0 && C->sp[sQ].n_modes > 0;
+                nm = (int)(C->sp[sP].n_modes > 0) + (int)(C->sp[sQ].n_modes > 0);
                 }
                 if (!accept) {
                     A.cflag[ev_idx] = 0u;
                     if (A.log_on) A.log[ev_idx] = hcao_log_rec{rs.step, cell.lcell, rk, ip, iq, -1, 0u};
                 }
             }
-            // pairs with two molecules to relax fill the queue from the front,
-            // the others from the back, so that warps of the relaxation kernel
-            // see mostly one kind (a lane's molecule loop runs once or twice);
-            // one atomic per CTA and end of the queue
-            const bool front = accept && two;
+            // the relaxation queue in three regions by the number of molecules to
+            // relax: two from qA[0] up, one from qA[2 cap - 1] down, none from
+            // qA[cap] up (an accepted pair count never exceeds cap), so that
+            // warps of the relaxation kernel run their molecule loop as their
+            // pairs need; one atomic per CTA and region
             {
                 const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                const unsigned mf = __ballot_sync(0xFFFFFFFFu, front);
-                const unsigned mb = __ballot_sync(0xFFFFFFFFu, accept && !front);
-                if (lane == 0) { sel_cnt[0][wid] = (uint32_t)__popc(mf); sel_cnt[1][wid] = (uint32_t)__popc(mb); }
+                const unsigned m2 = __ballot_sync(0xFFFFFFFFu, accept && nm == 2);
+                const unsigned m1 = __ballot_sync(0xFFFFFFFFu, accept && nm == 1);
+                const unsigned m0 = __ballot_sync(0xFFFFFFFFu, accept && nm == 0);
+                if (lane == 0) {
+                    sel_cnt[0][wid] = (uint32_t)__popc(m2);
+                    sel_cnt[1][wid] = (uint32_t)__popc(m1);
+                    sel_cnt[2][wid] = (uint32_t)__popc(m0);
+                }
                 __syncthreads();
-                if (threadIdx.x < 2) {
+                if (threadIdx.x < 3) {
                     uint32_t tot = 0u;
                     for (int w2 = 0; w2 < SELECT_THREADS / 32; ++w2) {
                         const uint32_t n = sel_cnt[threadIdx.x][w2];
                         sel_cnt[threadIdx.x][w2] = tot;
                         tot += n;
                     }
-                    sel_base[threadIdx.x] =
-                        tot ? atomicAdd(threadIdx.x == 0 ? qsize : A.qsize + 2 * MAX_ROUNDS + r, tot) : 0u;
+                    uint32_t* ctr = threadIdx.x == 0 ? qsize : A.qsize + (threadIdx.x + 1) * MAX_ROUNDS + r;
+                    sel_base[threadIdx.x] = tot ? atomicAdd(ctr, tot) : 0u;
                 }
                 __syncthreads();
                 const unsigned lt = (1u << lane) - 1u;
                 const uint4 ent = make_uint4((uint32_t)c, k, ip, iq);
-                if (front) A.qA[sel_base[0] + sel_cnt[0][wid] + (uint32_t)__popc(mf & lt)] = ent;
-                else if (accept)
-                    A.qA[A.pair_cap - 1u - (sel_base[1] + sel_cnt[1][wid] + (uint32_t)__popc(mb & lt))] = ent;
+                if (accept) {
+                    const int q = 2 - nm;  // region: 0 two molecules, 1 one, 2 none
+                    const unsigned mq = q == 0 ? m2 : (q == 1 ? m1 : m0);
+                    const uint64_t i = sel_base[q] + sel_cnt[q][wid] + (uint32_t)__popc(mq & lt);
+                    A.qA[q == 0 ? i : (q == 1 ? 2u * A.pair_cap - 1u - i : A.pair_cap + i)] = ent;
+                }
                 __syncthreads();  // sel_cnt / sel_base are rewritten in the next pass
             }
             // per-cell max of sigma_T g: lanes of one cell combine before the atomic
@@ -1793,14 +1802,15 @@ template <class R>
 __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
-    // queue: pairs with two molecules at the front, the others at the back
-    const uint32_t n_front = A.qsize[2 * r];
-    const uint32_t total = n_front + A.qsize[2 * MAX_ROUNDS + r];
+    // queue regions: pairs with two molecules to relax, then one, then none
+    const uint32_t n2 = A.qsize[2 * r], n21 = n2 + A.qsize[2 * MAX_ROUNDS + r];
+    const uint32_t total = n21 + A.qsize[3 * MAX_ROUNDS + r];
     const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t w[2] = {0u, 0u};
     uint32_t w_samp = 0, w_pair = 0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const uint4 e = A.qA[g < n_front ? (uint64_t)g : A.pair_cap - 1u - (uint64_t)(g - n_front)];
+        const uint4 e = A.qA[g < n2 ? (uint64_t)g
+                                    : (g < n21 ? 2u * A.pair_cap - 1u - (uint64_t)(g - n2) : A.pair_cap + (g - n21))];
         const int cidx = (int)e.x;
         const DevCell& cell = A.cells[cidx];
         const DevRes& rs = A.res[cell.res];
