@@ -761,16 +761,22 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
     const uint4 t0 = __ldg(reinterpret_cast<const uint4*>(T + m0));
     if (!(__uint_as_float(t0.x) > 0.f)) return S_DEGEN;
     if (__fsub_rn(Ec, b0) < S.eps_min_f) return S_OK;  // only the ground state fits
-    for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
-        trials++;
-        uint32_t nq[4] = {0u, 0u, 0u, 0u};
-        long long es = 0;
-        float E = Ec;
-        bool ok = true;
-        uint32_t off = t0.y, L = t0.z;
-        for (int k = 0; k < n; ++k) {
-            wmode++;
-            if (L == 0u) { ok = false; break; }
+    // One mode draw per pass of a single loop: a rejection starts the next
+    // trial at mode 0 in the next pass.  The draws and their random words are
+    // those of a loop over trials around a loop over modes, but a lane that
+    // restarts does not hold its warp's other lanes for a whole trial.
+    uint32_t nq[4] = {0u, 0u, 0u, 0u};
+    long long es = 0;
+    float E = Ec;
+    uint32_t off = t0.y, L = t0.z, trial = 0;
+    int k = 0;
+    trials++;
+    for (;;) {
+        wmode++;
+        bool acc = false;
+        uint32_t i = 0;
+        float e = 0.f;
+        if (L != 0u) {
             // one word: its top 24 bits give the slot (integer part of r L) and
             // the coin, its low 8 bits the top bits of the acceptance uniform
             const uint32_t rw = st_word(st);
@@ -782,9 +788,9 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
             const float4 s0 = __ldg(reinterpret_cast<const float4*>(A.ae + off + j));
             const float ej = __ldg(lv + j);  // in parallel with the slot
             const bool own = coin < s0.x;
-            const uint32_t i = own ? j : __float_as_uint(s0.y);
+            i = own ? j : __float_as_uint(s0.y);
             const float wg = own ? s0.z : s0.w;
-            const float e = own ? ej : __ldg(lv + i);
+            e = own ? ej : __ldg(lv + i);
             // acceptance at the actual budget
             float wE = 0.f;
             if (e < E) {
@@ -806,22 +812,35 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
             // drawn only when u8 leaves the test open: rounding is monotone, so
             // fl(u8 2^-8 wg) >= wE rejects and fl((u8+1) 2^-8 wg) < wE accepts
             // for every b, the decision of the full 24-bit test either way
+            acc = true;
             if (!(__fmul_rn((float)(u8 + 1u) * 0x1p-8f, wg) < wE)) {
-                if (!(__fmul_rn((float)u8 * 0x1p-8f, wg) < wE)) { ok = false; break; }
-                const float u = (float)((u8 << 16) | (st_word(st) >> 16)) * 0x1p-24f;
-                if (!(__fmul_rn(u, wg) < wE)) { ok = false; break; }
+                if (!(__fmul_rn((float)u8 * 0x1p-8f, wg) < wE)) {
+                    acc = false;
+                } else {
+                    const float u = (float)((u8 << 16) | (st_word(st) >> 16)) * 0x1p-24f;
+                    acc = __fmul_rn(u, wg) < wE;
+                }
             }
+        }
+        if (acc) {
             set_q(nq, k, i);
             E = __fsub_rn(E, e);
             es += __ldg(A.levfix + S.lev_off[k] + i);
-        }
-        if (ok) {
-            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
-            Esel = es;
-            return S_OK;
+            if (++k == n) break;
+        } else {
+            if (++trial >= A.reject_cap) return S_CAP;
+            trials++;
+            nq[0] = nq[1] = nq[2] = nq[3] = 0u;
+            es = 0;
+            E = Ec;
+            off = t0.y;
+            L = t0.z;
+            k = 0;
         }
     }
-    return S_CAP;
+    q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+    Esel = es;
+    return S_OK;
 }
 
 // FP32 LB relaxation of one molecule of species sp (levels q, fixed-point
@@ -1531,7 +1550,10 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
     if constexpr (std::is_same<R, float>::value) {
         // FP32 mode: no FP64 arithmetic; the second half of a record (the
         // quantum numbers) is read only for accepted pairs when reactions exist
-        __shared__ uint32_t sel_cnt[3][SELECT_THREADS / 32], sel_base[3];
+        // region counts, double-buffered by pass: a pass writes the set the
+        // previous pass did not read, so it needs two barriers, not three
+        __shared__ uint32_t sel_cnt[2][3][SELECT_THREADS / 32], sel_base[2][3];
+        int par = 0;
         for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
             const uint32_t g = g0 + threadIdx.x;
             const bool valid = g < total;
@@ -1588,20 +1610,20 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 const unsigned m1 = __ballot_sync(0xFFFFFFFFu, accept && nm == 1);
                 const unsigned m0 = __ballot_sync(0xFFFFFFFFu, accept && nm == 0);
                 if (lane == 0) {
-                    sel_cnt[0][wid] = (uint32_t)__popc(m2);
-                    sel_cnt[1][wid] = (uint32_t)__popc(m1);
-                    sel_cnt[2][wid] = (uint32_t)__popc(m0);
+                    sel_cnt[par][0][wid] = (uint32_t)__popc(m2);
+                    sel_cnt[par][1][wid] = (uint32_t)__popc(m1);
+                    sel_cnt[par][2][wid] = (uint32_t)__popc(m0);
                 }
                 __syncthreads();
                 if (threadIdx.x < 3) {
                     uint32_t tot = 0u;
                     for (int w2 = 0; w2 < SELECT_THREADS / 32; ++w2) {
-                        const uint32_t n = sel_cnt[threadIdx.x][w2];
-                        sel_cnt[threadIdx.x][w2] = tot;
+                        const uint32_t n = sel_cnt[par][threadIdx.x][w2];
+                        sel_cnt[par][threadIdx.x][w2] = tot;
                         tot += n;
                     }
                     uint32_t* ctr = threadIdx.x == 0 ? qsize : A.qsize + (threadIdx.x + 1) * MAX_ROUNDS + r;
-                    sel_base[threadIdx.x] = tot ? atomicAdd(ctr, tot) : 0u;
+                    sel_base[par][threadIdx.x] = tot ? atomicAdd(ctr, tot) : 0u;
                 }
                 __syncthreads();
                 const unsigned lt = (1u << lane) - 1u;
@@ -1609,10 +1631,10 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 if (accept) {
                     const int q = 2 - nm;  // region: 0 two molecules, 1 one, 2 none
                     const unsigned mq = q == 0 ? m2 : (q == 1 ? m1 : m0);
-                    const uint64_t i = sel_base[q] + sel_cnt[q][wid] + (uint32_t)__popc(mq & lt);
+                    const uint64_t i = sel_base[par][q] + sel_cnt[par][q][wid] + (uint32_t)__popc(mq & lt);
                     A.qA[q == 0 ? i : (q == 1 ? 2u * A.pair_cap - 1u - i : A.pair_cap + i)] = ent;
                 }
-                __syncthreads();  // sel_cnt / sel_base are rewritten in the next pass
+                par ^= 1;
             }
             // per-cell max of sigma_T g: lanes of one cell combine before the atomic
             const unsigned act = __activemask();
