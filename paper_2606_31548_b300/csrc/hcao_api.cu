@@ -1770,7 +1770,8 @@ static int64_t job_bytes(const hcao_ctx* ctx, const hcao_job& j) {
     const int64_t cap = (int64_t)std::ceil((double)j.n * f) + (int64_t)ctx->cfg.capacity_extra * j.n_cells +
                         8 * (int64_t)j.n_cells;
     const int64_t rec = ctx->cfg.precision == HCAO_FP64 ? 64 : 32;
-    const int64_t pair = (int64_t)ctx->cfg.max_rounds * (cap / 2 + j.n_cells) * (4 + 16 + 16 + rec);
+    // per pair slot: event word, relaxation queue (two entries: its FP32 regions), reaction queue, scratch record
+    const int64_t pair = (int64_t)ctx->cfg.max_rounds * (cap / 2 + j.n_cells) * (4 + 2 * 16 + 16 + rec);
     return cap * rec + pair + (int64_t)j.n_cells * (int64_t)(sizeof(DevCell) + 8 * NCNT) +
            j.n * 48;  // staging of the host arrays during the load
 }
