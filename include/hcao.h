@@ -57,7 +57,9 @@ typedef struct {
     int precision;          /* HCAO_FP64 (bit-exact parity mode) or HCAO_FP32 */
     int device;             /* CUDA device ordinal */
     void* cuda_stream;      /* borrowed cudaStream_t; NULL = default stream */
-    int table_points;       /* K5 quadratic grid points M, 16..4000 (default 2048) */
+    int table_points;       /* K5 grid, 16..4000 (default 2048): FP64 quadratic grid points M;
+                               FP32 2M geometric buckets (8 mantissa bits) over M/128 octaves
+                               below the span */
     double table_span_J;    /* K5 grid span above the ZPE (default 64 eV) */
     uint32_t reject_cap;    /* trials per LB sample before HCAO_EREJECT_LIMIT (default 2^20) */
     int max_rounds;         /* NTC pairing rounds per cell and step (default 2) */

@@ -911,7 +911,11 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     std::memset(&C, 0, sizeof C);
     C.n_species = n;
     C.amode = amode;
-    const int M = ctx->cfg.table_points;
+    // FP64: table_points quadratic grid points.  FP32: geometric buckets of
+    // F32_BUCKET_BITS mantissa bits over the same table_points / 128 octaves
+    // below the span (finer buckets: fewer rejected draws, larger tables)
+    const int M = ctx->cfg.precision == HCAO_FP32 ? ctx->cfg.table_points << (F32_BUCKET_BITS - 7)
+                                                  : ctx->cfg.table_points;
     const int MT = M + TABLE_PAD;
     std::vector<double> H64;
     std::vector<float> H32;
@@ -977,8 +981,8 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
                     L[j].resize(s.lev[j].size());
                     for (size_t l = 0; l < s.lev[j].size(); ++l) L[j][l] = (float)s.lev[j][l];
                 }
-                // 7 mantissa bits per octave (buckets ~0.8% wide); x = span maps to M
-                D.gshift = 23 - 7;
+                // F32_BUCKET_BITS mantissa bits per octave; x = span maps to M
+                D.gshift = 23 - F32_BUCKET_BITS;
                 const float span = (float)ctx->cfg.table_span_J;
                 uint32_t sb;
                 std::memcpy(&sb, &span, 4);
