@@ -1,23 +1,30 @@
 // hcao_kernels.cuh -- the collision-phase kernels of libhcao (sm_103a).
 //
 // One step of the DSMC collision phase, per reservoir cell:
-//   k_setup   (1 CTA)   NTC candidate count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c
-//                       with stochastic rounding, Feistel keys per pairing round,
-//                       block-wide scans that give every candidate pair a flat index.
-//   per pairing round, three grid kernels over compacted work:
-//   k_select  (grid)    one thread per candidate pair: Feistel pair draw, VHS
-//                       acceptance; accepted pairs appended to a queue.
-//   k_relax   (grid)    one thread per accepted pair: QK reaction test (Eq.
-//                       Ecoll-diss, Eq. Ecoll-exch, competing reactions);
-//                       reacting pairs to a second queue, the rest get the HCAO
-//                       Larsen-Borgnakke relaxation of both molecules (the
-//                       joint acceptance of all modes, sampled exactly with the
-//                       K5 tables) and isotropic VHS scattering.
-//   k_react   (grid)    one thread per reacting pair: dissociation / exchange.
+//   k_setup_cells  one thread per cell, CTAs of SETUP_TILE cells: NTC candidate
+//                  count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c with
+//                  stochastic rounding, Feistel keys per pairing round, tile
+//                  scans of the per-cell counts; the last CTA scans the tiles.
+//   k_setup_fix    adds the tile offsets (flat pair index of every candidate).
+//   k_cellstats    (recombination only) per-cell sums for the cell temperature.
+//   per pairing round:
+//   k_select       one thread per candidate pair: Feistel pair draw, VHS
+//                  acceptance; FP32 mode queues accepted pairs in three regions
+//                  by the number of molecules to relax.
+//   k_relax_fast   (FP32) one thread per accepted pair: recombination and QK
+//                  reaction tests (Eq. Ecoll-diss, Eq. Ecoll-exch, competing
+//                  reactions) -- reacting pairs go to a second queue -- else
+//                  the HCAO Larsen-Borgnakke relaxation of each molecule (the
+//                  joint acceptance of all modes, drawn exactly with the K5
+//                  tables and alias proposals) and isotropic VHS scattering.
+//   k_relax        (FP64) the same with the sequential K5 scan of the oracle.
+//   k_react        one thread per reacting pair: dissociation, exchange,
+//                  recombination.
+//   end of step, one warp per FINISH_CHUNK pair slots of a cell:
+//   k_finish_count per-cell counters; k_finish_append stable append of created
+//   particles; k_cellupd (sigma g)_max, counts, step; k_compact removals.
 // Queue order is irrelevant: pairs of one round are disjoint and every draw is
 // keyed by (step, cell, round, pair), never by a thread or queue position.
-//   k_finish  (warp/cell) (sigma g)_max update, per-cell counters, stable append
-//                       of particles created by dissociation, step counter.
 // Randomness: Philox4x32-10 keyed by the reservoir seed, counter
 // (step, cell, round<<24 | pair, purpose<<24 | block): draws do not depend on
 // launch geometry, so results are identical for any grid or batching.
@@ -25,7 +32,8 @@
 // Template parameter R: double = FP64 parity mode (the translation unit is
 // compiled without FMA contraction; every expression follows the documented
 // operation order), float = FP32 mode (velocities, relative speeds and the
-// sampler in FP32; energies, reaction thresholds and reductions in FP64).
+// sampler in FP32; energies, reaction thresholds and bookkeeping in int64
+// fixed point, 1 unit = 2^-100 J).
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -1535,7 +1543,8 @@ void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, con
 #endif
 
 // Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
-// pairs are finished here; accepted ones go to the relaxation queue.
+// pairs are finished here; accepted ones go to the relaxation queue (in FP32
+// mode into the region of their number of molecules to relax).
 constexpr int SELECT_THREADS = 256;
 
 template <class R>
@@ -1817,9 +1826,10 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
     }
 }
 
-// FP32 phase 2: one thread per accepted pair (grid-stride over the queue).
-// Molecule 1 then molecule 2 with the alias K5 draw (relative energy in int64
-// fixed point), isotropic scattering with the centre-of-mass velocity kept.
+// FP32 phase 2: one thread per accepted pair (grid-stride over the queue's
+// regions: two molecules to relax, then one, then none).  The molecules with
+// modes, P before Q, with the alias K5 draw (relative energy in int64 fixed
+// point), then isotropic scattering with the centre-of-mass velocity kept.
 template <class R>
 __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
