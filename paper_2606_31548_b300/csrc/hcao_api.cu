@@ -79,6 +79,7 @@ double now_s() {
 struct hcao_ctx {
     hcao_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;  // this context's device memory (see hcao_create)
     int sm_count = 148;
     std::string err;
     uint64_t launches = 0;
@@ -185,7 +186,7 @@ template <class T>
 cudaError_t dalloc(hcao_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), ctx->stream);
+    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), count * sizeof(T), ctx->pool, ctx->stream);
 }
 template <class T>
 void dfree(hcao_ctx* ctx, T*& p) {
@@ -552,7 +553,7 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
     dfree(ctx, ctx->d_chcnt);
     CU(dalloc(ctx, &ctx->d_chcnt, (size_t)(ctx->pair_cap / FINISH_CHUNK) + (size_t)total + 1));
     if (ctx->hc.creates && !ctx->d_cscratch)
-        CU(cudaMallocAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->stream));
+        CU(cudaMallocFromPoolAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->pool, ctx->stream));
     // reservoir table
     if ((int)ctx->res.size() > ctx->d_res_cap) {
         DevRes* nr = nullptr;
@@ -782,6 +783,28 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     int dev = ctx->cfg.device;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     ctx->stream = static_cast<cudaStream_t>(ctx->cfg.cuda_stream);
+    // A pool of the context's own: memory it frees stays mapped for its next
+    // allocations (up to POOL_KEEP_BYTES unused), so reloading a reservoir
+    // does not map and unmap its staging buffers and records each time.  The
+    // default pool would return freed memory to the system at every
+    // synchronisation.  Destroyed with the context.
+    {
+        cudaMemPoolProps pp{};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.handleTypes = cudaMemHandleTypeNone;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = dev;
+        uint64_t keep = POOL_KEEP_BYTES;
+        if (cudaMemPoolCreate(&ctx->pool, &pp) != cudaSuccess) {
+            delete ctx;
+            return HCAO_ECUDA;
+        }
+        if (cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaMemPoolDestroy(ctx->pool);
+            delete ctx;
+            return HCAO_ECUDA;
+        }
+    }
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 2) != cudaSuccess ||
         dalloc(ctx, &ctx->d_qsize, QSIZE_WORDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
         delete ctx;
@@ -835,6 +858,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (int k = 0; k < hcao_ctx::NPROF; ++k)
@@ -1257,7 +1281,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     const size_t rs = rec_size(ctx);
     r->total_cap = tot;
     r->rec_bytes = (size_t)tot * rs;
-    CU(cudaMallocAsync(&r->recs, std::max<size_t>(r->rec_bytes, 64), ctx->stream));
+    CU(cudaMallocFromPoolAsync(&r->recs, std::max<size_t>(r->rec_bytes, 64), ctx->pool, ctx->stream));
     CU(cudaMemsetAsync(r->recs, 0, std::max<size_t>(r->rec_bytes, 64), ctx->stream));
     for (int c = 0; c < r->n_cells; ++c)
         cells[c].rec = static_cast<char*>(r->recs) + slot0[c] * rs;

@@ -21,6 +21,7 @@ constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard ca
 constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)
 constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
 constexpr int FINISH_CHUNK = 1024;  // pair slots per warp of the end-of-step kernels
+constexpr uint64_t POOL_KEEP_BYTES = 8ull << 30;  // unused memory a context's pool keeps mapped
 constexpr int QSIZE_WORDS = 4 * MAX_ROUNDS;  // queue counters (StepArgs::qsize)
 constexpr int SETUP_TILE = 256;     // cells per CTA of the step set-up
 // prefix arrays built by the set-up: pairs of rounds 0..MAX_ROUNDS-1, all
