@@ -2596,16 +2596,26 @@ __global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const u
     }
 }
 
-// moments: acc[0..2] momentum, [3] E_tr, [4] E_form, [5 + s] E_vib of species s
+// moments: acc[0..2] momentum, [3] E_tr, [4] E_form, [5 + s] E_vib of species s.
+// Each thread sums its particles in registers (species by an unrolled
+// compare, so no array is indexed at run time); warps then reduce by shuffles
+// and one lane per warp adds into shared memory, once per kernel.  Atomics
+// per particle into a few shared words serialised the block.
 template <class R>
-__global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
-                          const Consts* C, const double* lev64, double* acc, unsigned long long* cnt) {
+__global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                                                 const Consts* C, const double* lev64, double* acc,
+                                                 unsigned long long* cnt) {
     using Rec = typename RecOf<R>::T;
     __shared__ double sacc[5 + MAXS];
     __shared__ unsigned long long scnt[MAXS];
     for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) sacc[i] = 0.0;
     for (int i = threadIdx.x; i < MAXS; i += blockDim.x) scnt[i] = 0ull;
     __syncthreads();
+    double px = 0.0, py = 0.0, pz = 0.0, etr = 0.0, ef = 0.0;
+    double ev[MAXS];
+    uint32_t nc[MAXS];
+#pragma unroll
+    for (int k = 0; k < MAXS; ++k) { ev[k] = 0.0; nc[k] = 0u; }
     const uint64_t total = off[n_cells];
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
          j += (uint64_t)gridDim.x * blockDim.x) {
@@ -2618,13 +2628,36 @@ __global__ void k_moments(const DevCell* cells, int cell0, int n_cells, const ui
         const DevSpecies& S = C->sp[s];
         const double m = S.mass;
         const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
-        atomicAdd(&sacc[0], m * vx);
-        atomicAdd(&sacc[1], m * vy);
-        atomicAdd(&sacc[2], m * vz);
-        atomicAdd(&sacc[3], 0.5 * m * (vx * vx + vy * vy + vz * vz));
-        atomicAdd(&sacc[4], S.E_form);
-        atomicAdd(&sacc[5 + s], evib64(lev64, S, r.q));
-        atomicAdd(&scnt[s], 1ull);
+        px += m * vx;
+        py += m * vy;
+        pz += m * vz;
+        etr += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        ef += S.E_form;
+        const double e = evib64(lev64, S, r.q);
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k)
+            if (s == k) { ev[k] += e; nc[k]++; }
+    }
+    const int lane = threadIdx.x & 31;
+    auto wsum = [](double x) {
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        return x;
+    };
+    px = wsum(px); py = wsum(py); pz = wsum(pz); etr = wsum(etr); ef = wsum(ef);
+    if (lane == 0) {
+        atomicAdd(&sacc[0], px); atomicAdd(&sacc[1], py); atomicAdd(&sacc[2], pz);
+        atomicAdd(&sacc[3], etr); atomicAdd(&sacc[4], ef);
+    }
+#pragma unroll
+    for (int k = 0; k < MAXS; ++k) {
+        const unsigned any = __ballot_sync(0xFFFFFFFFu, nc[k] != 0u);
+        if (any == 0u) continue;  // uniform over the warp
+        const double x = wsum(ev[k]);
+        const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, nc[k]);
+        if (lane == 0) {
+            atomicAdd(&sacc[5 + k], x);
+            atomicAdd(&scnt[k], (unsigned long long)n);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
