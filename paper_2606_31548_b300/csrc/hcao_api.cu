@@ -628,8 +628,12 @@ double tvib_host(const HostSpecies& s, double target) {
     };
     double lo = 1.0, hi = 1.0e6;
     for (int it = 0; it < 200; ++it) {
+        const double plo = lo, phi = hi;
         const double mid = 0.5 * (lo + hi);
         if (mean(mid) < target) lo = mid; else hi = mid;
+        // a pass is a function of (lo, hi) alone: once it changes neither,
+        // the remaining passes would not either (the same result, ~60 passes)
+        if (lo == plo && hi == phi) break;
     }
     return 0.5 * (lo + hi);
 }
