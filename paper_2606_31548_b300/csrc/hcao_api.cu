@@ -147,6 +147,8 @@ struct hcao_ctx {
     uint64_t serve_iterations = 0;
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
+    uint64_t pairs_need = 0;        // pair slots the current layout needs (set by relayout)
+    size_t chcnt_cap = 0;
     uint32_t* d_err = nullptr;
     bool log_on = false;
     uint32_t* d_scratch = nullptr;
@@ -498,23 +500,39 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
     CU(dalloc(ctx, &cells, cells_alloc));
     CU(dalloc(ctx, &cnt, cells_alloc * NCNT));
     CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * cells_alloc * NCNT, ctx->stream));
-    int at = 0;
+    // kept reservoirs' cells and counters move in runs that are contiguous in
+    // the old table: one copy per run, not per reservoir (loading R reservoirs
+    // one by one would otherwise issue O(R^2) copies)
+    int at = 0, run_src = 0, run_dst = 0, run_len = 0;
+    auto flush = [&]() -> cudaError_t {
+        if (run_len == 0) return cudaSuccess;
+        cudaError_t e = cudaMemcpyAsync(cells + run_dst, ctx->d_cells + run_src, sizeof(DevCell) * run_len,
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cnt + (size_t)run_dst * NCNT, ctx->d_cellcnt + (size_t)run_src * NCNT,
+                                sizeof(unsigned long long) * run_len * NCNT, cudaMemcpyDeviceToDevice, ctx->stream);
+        run_len = 0;
+        return e;
+    };
     for (int id = 0; id < (int)ctx->res.size(); ++id) {
         Reservoir& r = ctx->res[id];
         if (!(r.live && r.loaded)) continue;
         if (id == new_res) {
+            CU(flush());
             CU(cudaMemcpyAsync(cells + at, new_cells->data(), sizeof(DevCell) * r.n_cells,
                                cudaMemcpyHostToDevice, ctx->stream));
+        } else if (run_len > 0 && r.cell0 == run_src + run_len) {
+            run_len += r.n_cells;
         } else {
-            CU(cudaMemcpyAsync(cells + at, ctx->d_cells + r.cell0, sizeof(DevCell) * r.n_cells,
-                               cudaMemcpyDeviceToDevice, ctx->stream));
-            CU(cudaMemcpyAsync(cnt + (size_t)at * NCNT, ctx->d_cellcnt + (size_t)r.cell0 * NCNT,
-                               sizeof(unsigned long long) * r.n_cells * NCNT,
-                               cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(flush());
+            run_src = r.cell0;
+            run_dst = at;
+            run_len = r.n_cells;
         }
         r.cell0 = at;
         at += r.n_cells;
     }
+    CU(flush());
     dfree(ctx, ctx->d_cells);
     dfree(ctx, ctx->d_cellcnt);
     ctx->d_cells = cells;
@@ -536,24 +554,9 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         CU(cudaMemsetAsync(ctx->d_tsum, 0, sizeof(uint32_t) * nts, ctx->stream));
     }
     CU(dalloc(ctx, &ctx->d_csum, (size_t)5 * cells_alloc));
-    if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
-        dfree(ctx, ctx->d_cflag);
-        dfree(ctx, ctx->d_log);
-        if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
-        ctx->d_cscratch = nullptr;
-        ctx->pair_cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
-        CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
-        dfree(ctx, ctx->d_qA);
-        dfree(ctx, ctx->d_qB);
-        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)ctx->pair_cap));  // FP32: three regions, see StepArgs::qsize
-        CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
-        if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
-    }
-    // chunk counters: at most pairs / FINISH_CHUNK + one partial chunk per cell
-    dfree(ctx, ctx->d_chcnt);
-    CU(dalloc(ctx, &ctx->d_chcnt, (size_t)(ctx->pair_cap / FINISH_CHUNK) + (size_t)total + 1));
-    if (ctx->hc.creates && !ctx->d_cscratch)
-        CU(cudaMallocFromPoolAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->pool, ctx->stream));
+    // the per-pair buffers are sized at the next step (ensure_pair_buffers):
+    // loading many reservoirs one by one then grows them once, not per load
+    ctx->pairs_need = pairs;
     // reservoir table
     if ((int)ctx->res.size() > ctx->d_res_cap) {
         DevRes* nr = nullptr;
@@ -699,6 +702,36 @@ hcao_status build_recomb_tables(hcao_ctx* ctx) {
     CU(cudaMemcpyAsync(ctx->d_Tnode, ctx->h_Tnode.data(), sizeof(double) * ctx->h_Tnode.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+// Per-pair buffers for the current layout: event words, the relaxation queue
+// (two entries per slot), the reaction queue, the log, the chunk counters and
+// the created-particle scratch; grown (by at least half) only when too small.
+hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
+    const uint64_t pairs = ctx->pairs_need;
+    if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
+        dfree(ctx, ctx->d_cflag);
+        dfree(ctx, ctx->d_log);
+        if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
+        ctx->d_cscratch = nullptr;
+        ctx->pair_cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
+        CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
+        dfree(ctx, ctx->d_qA);
+        dfree(ctx, ctx->d_qB);
+        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)ctx->pair_cap));  // FP32: three regions, see StepArgs::qsize
+        CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
+        if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+    }
+    // chunk counters: at most pairs / FINISH_CHUNK + one partial chunk per cell
+    const size_t nch = (size_t)(ctx->pair_cap / FINISH_CHUNK) + (size_t)ctx->n_cells_total + 1;
+    if (nch > ctx->chcnt_cap) {
+        dfree(ctx, ctx->d_chcnt);
+        CU(dalloc(ctx, &ctx->d_chcnt, nch));
+        ctx->chcnt_cap = nch;
+    }
+    if (ctx->hc.creates && !ctx->d_cscratch)
+        CU(cudaMallocFromPoolAsync(&ctx->d_cscratch, (size_t)ctx->pair_cap * rec_size(ctx), ctx->pool, ctx->stream));
     return HCAO_OK;
 }
 
@@ -1410,7 +1443,10 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
     SERVE_GUARD(ctx);
     if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
     if (ctx->n_cells_total == 0 || n_steps == 0) return HCAO_OK;
-    if (ctx->log_on && !ctx->d_log) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+    {
+        const hcao_status st = ensure_pair_buffers(ctx);
+        if (st != HCAO_OK) return st;
+    }
     StepArgs a = make_args(ctx);
     const int block = 128;
     const int grid = ctx->sm_count * 8;
@@ -1760,7 +1796,8 @@ hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int id, double* out) {
 hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* out, int64_t max, int64_t* n_out) {
     if (!ctx || !n_out) return HCAO_EINVAL;
     *n_out = 0;
-    if (!ctx->log_on || !ctx->d_log) return fail(ctx, HCAO_EINVAL, "read_log: logging is off");
+    if (!ctx->log_on) return fail(ctx, HCAO_EINVAL, "read_log: logging is off");
+    if (!ctx->d_log) return HCAO_OK;  // no step since logging was switched on
     uint32_t tot[MAX_ROUNDS + 2];
     CU(cudaMemcpyAsync(tot, ctx->d_totals, sizeof tot, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
