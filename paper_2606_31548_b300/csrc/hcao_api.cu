@@ -710,22 +710,27 @@ hcao_status build_recomb_tables(hcao_ctx* ctx) {
 // the created-particle scratch; grown (by at least half) only when too small.
 hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
     const uint64_t pairs = ctx->pairs_need;
-    if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log)) {
+    // a capacity is recorded only once its buffers exist, so a failed
+    // allocation leaves the next call to retry, never a null buffer in use
+    if (pairs > ctx->pair_cap || (ctx->log_on && !ctx->d_log) || !ctx->d_cflag) {
+        const uint64_t cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
+        ctx->pair_cap = 0;
         dfree(ctx, ctx->d_cflag);
         dfree(ctx, ctx->d_log);
         if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
         ctx->d_cscratch = nullptr;
-        ctx->pair_cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
-        CU(dalloc(ctx, &ctx->d_cflag, (size_t)ctx->pair_cap));
         dfree(ctx, ctx->d_qA);
         dfree(ctx, ctx->d_qB);
-        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)ctx->pair_cap));  // FP32: three regions, see StepArgs::qsize
-        CU(dalloc(ctx, &ctx->d_qB, (size_t)ctx->pair_cap));
-        if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
+        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)cap));  // FP32: three regions, see StepArgs::qsize
+        CU(dalloc(ctx, &ctx->d_qB, (size_t)cap));
+        if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)cap));
+        CU(dalloc(ctx, &ctx->d_cflag, (size_t)cap));  // last: its presence marks a complete set
+        ctx->pair_cap = cap;
     }
     // chunk counters: at most pairs / FINISH_CHUNK + one partial chunk per cell
     const size_t nch = (size_t)(ctx->pair_cap / FINISH_CHUNK) + (size_t)ctx->n_cells_total + 1;
-    if (nch > ctx->chcnt_cap) {
+    if (nch > ctx->chcnt_cap || !ctx->d_chcnt) {
+        ctx->chcnt_cap = 0;
         dfree(ctx, ctx->d_chcnt);
         CU(dalloc(ctx, &ctx->d_chcnt, nch));
         ctx->chcnt_cap = nch;
