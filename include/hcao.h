@@ -166,7 +166,11 @@ hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int res);
 /* Load n particles into reservoir res (host arrays: v n x 3 doubles, qn
    n x 16 bytes (mode j of particle i at qn[16 i + j]), species and cell
    n int32).  Sorts them into cells with the stable counting sort, keeping
-   input order within a cell.  Replaces any earlier content. */
+   input order within a cell.  Replaces any earlier content.  Input that fails
+   validation (HCAO_EINVAL, HCAO_ELEVEL_OVERFLOW) leaves the reservoir as it
+   was.  A device allocation that fails after the earlier particles were
+   released leaves the context refusing device work (step, init and reads
+   return HCAO_EINVAL) until a load or a removal succeeds. */
 hcao_status hcao_load_particles(hcao_ctx* ctx, int res, int64_t n, const double* host_v,
                                 const uint8_t* host_qn, const int32_t* host_species,
                                 const int32_t* host_cell);

@@ -148,6 +148,7 @@ struct hcao_ctx {
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint64_t pairs_need = 0;        // pair slots the current layout needs (set by relayout)
+    bool layout_ok = true;          // false from a layout change until it completed
     size_t chcnt_cap = 0;
     uint32_t* d_err = nullptr;
     bool log_on = false;
@@ -168,6 +169,14 @@ hcao_status fail(hcao_ctx* c, hcao_status s, const std::string& m) {
     if (c) c->err = m;
     return s;
 }
+
+// device work needs a complete layout: after a load or removal failed part
+// way, the cell table may be stale until a load or removal succeeds
+#define LAYOUT_GUARD(ctx)                                                                     \
+    do {                                                                                      \
+        if ((ctx) && !(ctx)->layout_ok)                                                       \
+            return fail((ctx), HCAO_EINVAL, "the last load or removal failed; load again first"); \
+    } while (0)
 
 // set on the serving engine thread: while a context serves, its state-changing
 // entry points are refused on every other thread
@@ -487,6 +496,7 @@ hcao_status map_err(hcao_ctx* ctx) {
 // loaded reservoirs in reservoir order; per-pair buffers sized for
 // max_rounds * slots / 2 + cells.
 hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new_cells) {
+    ctx->layout_ok = false;  // until every table below exists again
     int total = 0;
     uint64_t pairs = 0;
     for (auto& r : ctx->res)
@@ -570,6 +580,7 @@ hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new
         ctx->d_res_cap = cap;
     }
     CU(cudaStreamSynchronize(ctx->stream));
+    ctx->layout_ok = true;
     return HCAO_OK;
 }
 
@@ -1241,10 +1252,6 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     if (n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!v || !qn || !species || !cell)))
         return fail(ctx, HCAO_EINVAL, "load_particles: bad arguments");
     CU(cudaStreamSynchronize(ctx->stream));
-    if (r->recs) {
-        cudaFreeAsync(r->recs, ctx->stream);
-        r->recs = nullptr;
-    }
     // stage the host arrays; validate and count on the device (a sort by cell
     // gives the per-cell counts); host work stays O(cells)
     double* dv = nullptr;
@@ -1323,6 +1330,13 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     const size_t rs = rec_size(ctx);
     r->total_cap = tot;
     r->rec_bytes = (size_t)tot * rs;
+    // the old records go only now, once the new input has passed its checks;
+    // until relayout completes, the cell table may point at freed records
+    if (r->recs) {
+        ctx->layout_ok = false;
+        cudaFreeAsync(r->recs, ctx->stream);
+        r->recs = nullptr;
+    }
     CU(cudaMallocFromPoolAsync(&r->recs, std::max<size_t>(r->rec_bytes, 64), ctx->pool, ctx->stream));
     CU(cudaMemsetAsync(r->recs, 0, std::max<size_t>(r->rec_bytes, 64), ctx->stream));
     for (int c = 0; c < r->n_cells; ++c)
@@ -1354,6 +1368,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
 }
 
 hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
+    LAYOUT_GUARD(ctx);
     SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1445,6 +1460,7 @@ hcao_status hcao_set_log(hcao_ctx* ctx, int enable) {
 }
 
 hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
+    LAYOUT_GUARD(ctx);
     SERVE_GUARD(ctx);
     if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
     if (ctx->n_cells_total == 0 || n_steps == 0) return HCAO_OK;
@@ -1624,6 +1640,7 @@ hcao_status hcao_sync(hcao_ctx* ctx) {
 }
 
 hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
+    LAYOUT_GUARD(ctx);
     if (!ctx || !n) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "count: no such reservoir");
@@ -1637,6 +1654,7 @@ hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
 }
 
 hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, int32_t* species, int32_t* cell) {
+    LAYOUT_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_particles: no loaded reservoir");
@@ -1677,6 +1695,7 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
 }
 
 hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
+    LAYOUT_GUARD(ctx);
     if (!ctx || !out) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_moments: no loaded reservoir");
@@ -1729,6 +1748,7 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
 }
 
 hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode, uint64_t* counts, int max_levels) {
+    LAYOUT_GUARD(ctx);
     if (!ctx || !counts || max_levels < 1) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_level_populations: no loaded reservoir");
@@ -1757,6 +1777,7 @@ hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode,
 }
 
 hcao_status hcao_read_counters(hcao_ctx* ctx, int id, uint64_t* out, int max, int* n_out) {
+    LAYOUT_GUARD(ctx);
     if (!ctx || !out || max < 1) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_counters: no loaded reservoir");
@@ -1788,6 +1809,7 @@ hcao_status hcao_read_reaction_counts(hcao_ctx* ctx, int id, uint64_t* out, int 
 }
 
 hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int id, double* out) {
+    LAYOUT_GUARD(ctx);
     if (!ctx || !out) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_cell_sgmax: no loaded reservoir");

@@ -97,6 +97,25 @@ def test_load_rejects_bad_levels():
         g.load_particles(rid, w.v, qn, w.species_idx, w.cell)
 
 
+@pytest.mark.parametrize("precision", [hcao.FP64, hcao.FP32])
+def test_rejected_reload_keeps_reservoir(precision):
+    """A reload whose input fails validation leaves the reservoir's particles
+    as they were, and the context keeps stepping."""
+    w = W.relaxation_triatomic(n_particles=2000)
+    g = hcao.from_workload(w, precision=precision)
+    g.step(2)
+    before = g.read_particles(0)
+    qn = np.zeros((w.n, 16), np.uint8)
+    qn[3, 0] = 17  # stretch has 17 levels: 0..16
+    with pytest.raises(hcao.HcaoError):
+        g.load_particles(0, w.v, qn, w.species_idx, w.cell)
+    after = g.read_particles(0)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    g.step(2)
+    assert g.count(0) == w.n
+
+
 # ------------------------------------------------------------- init
 @pytest.mark.parametrize("T", [300.0, 6000.0, 20000.0])
 def test_init_vibration_matches_oracle(T):
