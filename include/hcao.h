@@ -137,7 +137,11 @@ typedef struct {
 
 typedef struct hcao_ctx hcao_ctx;
 
-/* Create a context on config->device.  config may be NULL (defaults). */
+/* Create a context on config->device.  config may be NULL (defaults).  The
+   context allocates its device memory from a stream-ordered memory pool of
+   its own, which keeps up to 8 GiB of memory the context freed mapped for its
+   later allocations (reloading reservoirs reuses it); hcao_destroy releases
+   the pool.  HCAO_ECUDA if the device or the pool cannot be set up. */
 hcao_status hcao_create(const hcao_config* config, hcao_ctx** out);
 /* Free all device memory of the context (synchronises its stream). */
 void hcao_destroy(hcao_ctx* ctx);
