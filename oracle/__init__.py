@@ -87,6 +87,10 @@ def lib():
                                     C.c_void_p, C.POINTER(C.c_uint64)]
         L.ora_sample_init.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_int64,
                                       C.c_void_p]
+        L.ora_sample_products.restype = C.c_int64
+        L.ora_sample_products.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p]
         L.ora_feistel.restype = C.c_uint32
         L.ora_feistel.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]
         L.ora_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
@@ -245,6 +249,30 @@ class Oracle:
         self._chk(self.L.ora_sample_lb(self.ctx, sp, Ec, seed, n, 1 if method == "literal" else 0,
                                        _p(out), C.byref(tr)), "sample_lb")
         return out, int(tr.value)
+
+    def sample_products(self, rx, reactants, seed, n):
+        """n independent executions of reaction rx on one fixed set of
+        reactants, a list of (species, velocity, levels): dissociation [A, M],
+        exchange [A, B], recombination [B, C, M].  Returns (v, q) of the
+        executed events: v (k, 3, 3) and q (k, 2, 16) as ora_sample_products
+        lays them out."""
+        args = []
+        for j in range(3):
+            if j < len(reactants):
+                sp, vv, qq = reactants[j]
+                vv = np.ascontiguousarray(vv, np.float64)
+                qq = np.ascontiguousarray(np.resize(np.asarray(qq, np.uint8), 16))
+            else:
+                sp, vv, qq = -1, np.zeros(3), np.zeros(16, np.uint8)
+            args += [sp, vv, qq]
+        keep = args  # the arrays must outlive the call
+        ov = np.zeros((n, 3, 3), np.float64)
+        oq = np.zeros((n, 2, 16), np.uint8)
+        k = int(self.L.ora_sample_products(self.ctx, rx, keep[0], _p(keep[1]), _p(keep[2]), keep[3], _p(keep[4]),
+                                           _p(keep[5]), keep[6], _p(keep[7]), _p(keep[8]), seed, n,
+                                           _p(ov), _p(oq)))
+        self._chk(min(k, 0), "sample_products")
+        return ov[:k], oq[:k]
 
     def sample_init(self, sp, T, seed, n):
         out = np.zeros((n, 16), np.uint8)

@@ -24,7 +24,10 @@
  *                       equilibrium Boltzmann populations, detailed balance)
  *   dissociation      : pinned (single-step probability vs level-sum quadrature)
  *   exchange          : pinned (single-step probability vs level-sum quadrature)
- *   product split     : parity unpinned beyond conservation (reading A13)
+ *   product split     : pinned (reading A13: each product's levels vs the
+ *                       enumerated LB target at its budget, Beta(3/2,3/2)
+ *                       three-body split, isotropy, conservation; the same
+ *                       for the recombination product, reading A14)
  */
 #include "hcao_oracle.h"
 #include <math.h>
@@ -1358,6 +1361,64 @@ int ora_sample_lb(ora_ctx* c, int sp, double Ec, uint64_t seed, int64_t n, int m
     }
     if (trials) *trials = tr;
     return 0;
+}
+
+int64_t ora_sample_products(ora_ctx* c, int rx, int sp1, const double* v1, const uint8_t* q1, int sp2,
+                            const double* v2, const uint8_t* q2, int sp3, const double* v3, const uint8_t* q3,
+                            uint64_t seed, int64_t n, double* out_v, uint8_t* out_q) {
+    if (rx < 0 || rx >= c->n_reactions || sp1 < 0 || sp1 >= c->n_species || sp2 < 0 || sp2 >= c->n_species ||
+        n < 0)
+        return ORA_EINVAL;
+    const int type = c->rx[rx].type;
+    if (type == ORA_RECOMB && (sp3 < 0 || sp3 >= c->n_species || !v3 || !q3)) return ORA_EINVAL;
+    o_res R;
+    memset(&R, 0, sizeof R);
+    R.seed = seed;
+    int64_t done = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        o_part P1, P2, P3, created[1];
+        memset(&P1, 0, sizeof P1);
+        memset(&P2, 0, sizeof P2);
+        memset(&P3, 0, sizeof P3);
+        P1.sp = sp1;
+        P2.sp = sp2;
+        for (int k = 0; k < 3; ++k) { P1.v[k] = v1[k]; P2.v[k] = v2[k]; }
+        memcpy(P1.qn, q1, 16);
+        memcpy(P2.qn, q2, 16);
+        if (type == ORA_RECOMB) {
+            P3.sp = sp3;
+            for (int k = 0; k < 3; ++k) P3.v[k] = v3[k];
+            memcpy(P3.qn, q3, 16);
+        }
+        const double Ev1 = evib(&c->sp[sp1], P1.qn), Ev2 = evib(&c->sp[sp2], P2.qn);
+        const uint32_t cell = (uint32_t)(i >> 32), rk = (uint32_t)i;
+        int nc = 0, ok;
+        if (type == ORA_DISS)
+            ok = do_diss(c, &R, rx, &P1, &P2, Ev1, cell, rk, NULL, created, &nc);
+        else if (type == ORA_EXCH)
+            ok = do_exch(c, &R, rx, &P1, &P2, Ev1, Ev2, cell, rk);
+        else
+            ok = do_recomb(c, &R, rx, &P1, &P2, &P3, Ev1, Ev2, cell, rk);
+        if (c->error) return c->error;
+        if (!ok) continue;
+        double* v = out_v + 9 * done;
+        uint8_t* q = out_q + 32 * done;
+        memset(v, 0, 9 * sizeof(double));
+        memset(q, 0, 32);
+        for (int k = 0; k < 3; ++k) v[k] = P1.v[k];
+        memcpy(q, P1.qn, 16);
+        if (type == ORA_DISS) {
+            for (int k = 0; k < 3; ++k) { v[3 + k] = created[0].v[k]; v[6 + k] = P2.v[k]; }
+            memcpy(q + 16, created[0].qn, 16);
+        } else if (type == ORA_EXCH) {
+            for (int k = 0; k < 3; ++k) v[3 + k] = P2.v[k];
+            memcpy(q + 16, P2.qn, 16);
+        } else {
+            for (int k = 0; k < 3; ++k) v[6 + k] = P3.v[k];
+        }
+        ++done;
+    }
+    return done;
 }
 
 int ora_sample_init(ora_ctx* c, int sp, double T, uint64_t seed, int64_t n, uint8_t* out_qn) {

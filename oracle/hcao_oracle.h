@@ -101,6 +101,18 @@ double   ora_zpe(ora_ctx*, int sp);
    energy Ec with the chosen sampler; a Philox stream keyed by seed */
 int      ora_sample_lb(ora_ctx*, int sp, double Ec, uint64_t seed, int64_t n, int method,
                        uint8_t* out_qn, uint64_t* trials);
+/* Test diagnostic: n independent executions of reaction rx on one fixed set
+   of reactants, event i with the random streams of pair i.  Reactants 1, 2
+   (species, velocity, levels): dissociation A and its third body M; exchange
+   A and B; recombination B and C, with reactant 3 its third body M (reactant
+   3 is unused otherwise).  Per executed event out_v[9 i ..] receives three
+   velocities and out_q[32 i ..] two level sets: dissociation B, C, M and the
+   levels of B, C; exchange C, D, zeros and the levels of C, D; recombination
+   A, zeros, M and the levels of A.  Returns the number of executed events (0
+   when the reactants cannot react) or a negative error. */
+int64_t  ora_sample_products(ora_ctx*, int rx, int sp1, const double* v1, const uint8_t* q1, int sp2,
+                             const double* v2, const uint8_t* q2, int sp3, const double* v3, const uint8_t* q3,
+                             uint64_t seed, int64_t n, double* out_v, uint8_t* out_q);
 /* draws n initial states of species sp at T_vib (P6/P7) */
 int      ora_sample_init(ora_ctx*, int sp, double T_vib, uint64_t seed, int64_t n,
                          uint8_t* out_qn);
