@@ -1,5 +1,7 @@
 // hcao_api.cu -- host side of libhcao: the C ABI, species level tables and
-// the K5 sampler tables, reservoir layout in HBM, launches.
+// the K5 sampler tables (FP32: alias tables), recombination rate tables,
+// reservoir layout in HBM from a per-context memory pool, launches and the
+// CUDA graph of a step, the continuous-batching serving engine.
 //
 // Host arithmetic that feeds device decisions (level energies, grid bases,
 // K5 tables, VHS pair constants) is evaluated in IEEE double without FMA
@@ -493,8 +495,9 @@ hcao_status map_err(hcao_ctx* ctx) {
 }
 
 // (Re)build the global cell table after reservoirs change: cells of live,
-// loaded reservoirs in reservoir order; per-pair buffers sized for
-// max_rounds * slots / 2 + cells.
+// loaded reservoirs in reservoir order, with the prefix arrays of the step
+// set-up; records the per-pair slots the layout needs (max_rounds * slots / 2
+// + cells), which the next step's ensure_pair_buffers provides.
 hcao_status relayout(hcao_ctx* ctx, int new_res, const std::vector<DevCell>* new_cells) {
     ctx->layout_ok = false;  // until every table below exists again
     int total = 0;
