@@ -534,11 +534,29 @@ def main():
             one()
         torch.cuda.synchronize()
         te = _max_over_ranks(time.perf_counter() - t0)
+        # where an e2e step goes: each call timed alone (host clock, synchronised),
+        # after the timed loop and outside it
+        split = {}
+        for name, f in (("load", lambda: ectx._chk(L.hcao_load_particles(
+                            ectx.h, rid, w.n, C.c_void_p(v_h.data_ptr()), C.c_void_p(q_h.data_ptr()),
+                            C.c_void_p(s_h.data_ptr()), C.c_void_p(c_h.data_ptr())))),
+                        ("step", lambda: ectx._chk(L.hcao_step(ectx.h, 1))),
+                        ("moments", lambda: ectx._chk(L.hcao_read_moments(ectx.h, rid, C.byref(mom))))):
+            ts = []
+            for _ in range(3):
+                ectx.sync()
+                t1 = time.perf_counter()
+                f()
+                ectx.sync()
+                ts.append(time.perf_counter() - t1)
+            split[name] = 1e3 * sorted(ts)[1]
         e2e = {"value": _sum_over_ranks(float(w.n * args.e2e_steps)) / te, "unit": "particle-steps/s",
                "h2d_bytes_per_step": int(w.n * (24 + 16 + 4 + 4)),
                "d2h_bytes_per_step": int(C.sizeof(hcao.Moments)),
+               "split_ms": split,
                "note": "per step: hcao_load_particles from pinned host memory (state of the "
-                       "workload), hcao_step(1), hcao_read_moments"}
+                       "workload), hcao_step(1), hcao_read_moments; split_ms: the median of 3 "
+                       "separate synchronised calls of each, measured after the timed loop"}
         ectx.close()
 
     batched = None
