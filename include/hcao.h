@@ -141,7 +141,10 @@ typedef struct hcao_ctx hcao_ctx;
    context allocates its device memory from a stream-ordered memory pool of
    its own, which keeps up to 8 GiB of memory the context freed mapped for its
    later allocations (reloading reservoirs reuses it); hcao_destroy releases
-   the pool.  HCAO_ECUDA if the device or the pool cannot be set up. */
+   the pool.  HCAO_ECUDA if the device or the pool cannot be set up.  Every
+   call on a context runs on its device and leaves the calling thread's
+   current device as it found it; the serving engine's thread uses the
+   context's device. */
 hcao_status hcao_create(const hcao_config* config, hcao_ctx** out);
 /* Free all device memory of the context (synchronises its stream). */
 void hcao_destroy(hcao_ctx* ctx);

@@ -172,6 +172,16 @@ hcao_status fail(hcao_ctx* c, hcao_status s, const std::string& m) {
     return s;
 }
 
+// Every entry point runs on the context's device and gives the calling
+// thread its previous current device back on return.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(const hcao_ctx* c);
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 // device work needs a complete layout: after a load or removal failed part
 // way, the cell table may be stale until a load or removal succeeds
 #define LAYOUT_GUARD(ctx)                                                                     \
@@ -187,6 +197,12 @@ thread_local bool tl_serve_engine = false;
     do {                                                                  \
         if ((ctx) && (ctx)->serve_running && !tl_serve_engine) return HCAO_EBUSY; \
     } while (0)
+DeviceScope::DeviceScope(const hcao_ctx* c) {
+    int cur = -1;
+    if (c && cudaGetDevice(&cur) == cudaSuccess && cur != c->cfg.device && cudaSetDevice(c->cfg.device) == cudaSuccess)
+        prev = cur;
+}
+
 #define CU(call)                                                                           \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \
@@ -831,6 +847,7 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
         delete ctx;
         return HCAO_EINVAL;
     }
+    DeviceScope ds_(ctx);  // the caller's current device is given back on return
     cudaError_t e = cudaSetDevice(ctx->cfg.device);
     if (e != cudaSuccess) {
         delete ctx;
@@ -878,6 +895,7 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
 }
 
 void hcao_destroy(hcao_ctx* ctx) {
+    DeviceScope ds_(ctx);
     if (!ctx) return;
     hcao_serve_stop(ctx);
     cudaStreamSynchronize(ctx->stream);
@@ -928,6 +946,7 @@ void hcao_destroy(hcao_ctx* ctx) {
 const char* hcao_last_error(const hcao_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
 hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, double* out) {
+    DeviceScope ds_(ctx);
     if (!ctx || !out || reaction < 0 || reaction >= ctx->n_reactions || spM < 0 || spM >= ctx->n_species)
         return fail(ctx, HCAO_EINVAL, "recomb_rate: bad arguments");
     const DevReaction& D = ctx->hc.rx[reaction];
@@ -950,6 +969,7 @@ hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, dou
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) {
+    DeviceScope ds_(ctx);
     if (!ctx || !species || n < 1 || n > MAXS) return fail(ctx, HCAO_EINVAL, "set_species: bad arguments");
     if (ctx->n_species > 0) return fail(ctx, HCAO_EINVAL, "set_species: already set");
     int amode = -1;
@@ -1112,6 +1132,7 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
 }
 
 hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
+    DeviceScope ds_(ctx);
     if (!ctx || n < 0 || n > MAXR || (n > 0 && !rx)) return fail(ctx, HCAO_EINVAL, "set_reactions: bad arguments");
     if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "set_reactions: species first");
     for (auto& r : ctx->res)
@@ -1199,6 +1220,7 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
 
 hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, double weight, double dt,
                                uint64_t seed, double T_sgmax, int* id) {
+    DeviceScope ds_(ctx);
     SERVE_GUARD(ctx);
     if (!ctx || n_cells < 1 || !(cell_volume > 0) || !(weight > 0) || !(dt > 0) || !(T_sgmax > 0) || !id)
         return fail(ctx, HCAO_EINVAL, "add_reservoir: bad arguments");
@@ -1217,6 +1239,7 @@ hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, d
 }
 
 hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int id) {
+    DeviceScope ds_(ctx);
     SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1238,6 +1261,7 @@ hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int id) {
 
 hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_t* perm,
                            uint32_t* offsets) {
+    DeviceScope ds_(ctx);
     if (!ctx || n < 0 || n > 0xFFFFFFFFll || n_cells < 1 || (n > 0 && (!keys || !perm)) || !offsets)
         return fail(ctx, HCAO_EINVAL, "cell_sort: bad arguments");
     hcao_status st = ensure_scratch(ctx, sort_scratch_words(n, n_cells));
@@ -1248,6 +1272,7 @@ hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint3
 
 hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* v, const uint8_t* qn,
                                 const int32_t* species, const int32_t* cell) {
+    DeviceScope ds_(ctx);
     SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1371,6 +1396,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
 }
 
 hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
@@ -1423,6 +1449,7 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
 
 hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int64_t n, uint8_t* host_qn,
                            uint64_t* host_trials) {
+    DeviceScope ds_(ctx);
     if (!ctx || n < 0 || (n > 0 && !host_qn)) return HCAO_EINVAL;
     if (sp < 0 || sp >= ctx->n_species || ctx->sp[sp].n_modes == 0)
         return fail(ctx, HCAO_EINVAL, "sample_lb: species without vibrational modes");
@@ -1456,6 +1483,7 @@ hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int6
 }
 
 hcao_status hcao_set_log(hcao_ctx* ctx, int enable) {
+    DeviceScope ds_(ctx);
     if (!ctx) return HCAO_EINVAL;
     ctx->log_on = enable != 0;
     if (ctx->log_on && !ctx->d_log && ctx->pair_cap > 0) CU(dalloc(ctx, &ctx->d_log, (size_t)ctx->pair_cap));
@@ -1463,6 +1491,7 @@ hcao_status hcao_set_log(hcao_ctx* ctx, int enable) {
 }
 
 hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     SERVE_GUARD(ctx);
     if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
@@ -1556,6 +1585,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
 }
 
 hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable) {
+    DeviceScope ds_(ctx);
     if (!ctx) return HCAO_EINVAL;
     ctx->prof_on = enable != 0;
     for (int k = 0; k < hcao_ctx::NPROF; ++k) {
@@ -1567,6 +1597,7 @@ hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable) {
 }
 
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int max, int* n_out) {
+    DeviceScope ds_(ctx);
     if (!ctx || !ms || !launches || max < 1) return HCAO_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < hcao_ctx::NPROF; ++k) {
@@ -1588,6 +1619,7 @@ hcao_status hcao_read_profile(hcao_ctx* ctx, double* ms, uint64_t* launches, int
 }
 
 hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen) {
+    DeviceScope ds_(ctx);
     if (!ctx || steps_per_candidate < 1) return HCAO_EINVAL;
     if (ctx->n_cells_total == 0) return HCAO_OK;
     const int sm = ctx->sm_count;
@@ -1626,6 +1658,7 @@ hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen) {
 }
 
 hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* out, int max, int* n_out) {
+    DeviceScope ds_(ctx);
     if (!ctx || !out || max < 1) return HCAO_EINVAL;
     unsigned long long w[4];
     CU(cudaMemcpyAsync(w, ctx->d_work, sizeof w, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1637,12 +1670,14 @@ hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* out, int max, int* n_out) {
 }
 
 hcao_status hcao_sync(hcao_ctx* ctx) {
+    DeviceScope ds_(ctx);
     if (!ctx) return HCAO_EINVAL;
     CU(cudaStreamSynchronize(ctx->stream));
     return map_err(ctx);
 }
 
 hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx || !n) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1657,6 +1692,7 @@ hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
 }
 
 hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, int32_t* species, int32_t* cell) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1698,6 +1734,7 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
 }
 
 hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx || !out) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1751,6 +1788,7 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
 }
 
 hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode, uint64_t* counts, int max_levels) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx || !counts || max_levels < 1) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1780,6 +1818,7 @@ hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode,
 }
 
 hcao_status hcao_read_counters(hcao_ctx* ctx, int id, uint64_t* out, int max, int* n_out) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx || !out || max < 1) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1802,6 +1841,7 @@ hcao_status hcao_read_counters(hcao_ctx* ctx, int id, uint64_t* out, int max, in
 }
 
 hcao_status hcao_read_reaction_counts(hcao_ctx* ctx, int id, uint64_t* out, int n) {
+    DeviceScope ds_(ctx);
     if (!ctx || !out || n < 0) return HCAO_EINVAL;
     uint64_t buf[8 + MAXR];
     int got = 0;
@@ -1812,6 +1852,7 @@ hcao_status hcao_read_reaction_counts(hcao_ctx* ctx, int id, uint64_t* out, int 
 }
 
 hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int id, double* out) {
+    DeviceScope ds_(ctx);
     LAYOUT_GUARD(ctx);
     if (!ctx || !out) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
@@ -1824,6 +1865,7 @@ hcao_status hcao_read_cell_sgmax(hcao_ctx* ctx, int id, double* out) {
 }
 
 hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* out, int64_t max, int64_t* n_out) {
+    DeviceScope ds_(ctx);
     if (!ctx || !n_out) return HCAO_EINVAL;
     *n_out = 0;
     if (!ctx->log_on) return fail(ctx, HCAO_EINVAL, "read_log: logging is off");
@@ -1884,6 +1926,7 @@ static void serve_fail(hcao_ctx* ctx, const std::shared_ptr<Job>& jb, int status
 
 static void serve_loop(hcao_ctx* ctx) {
     tl_serve_engine = true;
+    cudaSetDevice(ctx->cfg.device);  // the engine's own thread: the context's device throughout
     for (;;) {
         // ---- admission
         std::vector<std::shared_ptr<Job>> admit;
@@ -1978,6 +2021,7 @@ static void serve_loop(hcao_ctx* ctx) {
 extern "C" {
 
 hcao_status hcao_serve_start(hcao_ctx* ctx, int64_t hbm_budget_bytes, int max_active, int max_batch_steps) {
+    DeviceScope ds_(ctx);
     if (!ctx || max_active < 0 || max_batch_steps < 0) return HCAO_EINVAL;
     if (ctx->n_species == 0) return fail(ctx, HCAO_EINVAL, "serve_start: species first");
     if (ctx->serve_running) return fail(ctx, HCAO_EBUSY, "serve_start: already serving");
@@ -1996,6 +2040,7 @@ hcao_status hcao_serve_start(hcao_ctx* ctx, int64_t hbm_budget_bytes, int max_ac
 }
 
 hcao_status hcao_serve_submit(hcao_ctx* ctx, const hcao_job* job, uint64_t* job_id) {
+    DeviceScope ds_(ctx);
     if (!ctx || !job || !job_id || job->n < 0 || job->n_cells < 1 || job->n_steps < 0 ||
         (job->n > 0 && (!job->v || !job->species || !job->cell)))
         return HCAO_EINVAL;
@@ -2021,6 +2066,7 @@ hcao_status hcao_serve_submit(hcao_ctx* ctx, const hcao_job* job, uint64_t* job_
 }
 
 hcao_status hcao_serve_poll(hcao_ctx* ctx, uint64_t job_id, hcao_job_result* out) {
+    DeviceScope ds_(ctx);
     if (!ctx || !out) return HCAO_EINVAL;
     std::lock_guard<std::mutex> lock(ctx->serve_mu);
     auto it = ctx->serve_jobs.find(job_id);
@@ -2034,6 +2080,7 @@ hcao_status hcao_serve_poll(hcao_ctx* ctx, uint64_t job_id, hcao_job_result* out
 }
 
 hcao_status hcao_serve_stop(hcao_ctx* ctx) {
+    DeviceScope ds_(ctx);
     if (!ctx) return HCAO_EINVAL;
     if (!ctx->serve_running) return HCAO_OK;
     {
@@ -2048,6 +2095,7 @@ hcao_status hcao_serve_stop(hcao_ctx* ctx) {
 
 hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, int64_t* used_bytes,
                              uint64_t* iterations) {
+    DeviceScope ds_(ctx);
     if (!ctx) return HCAO_EINVAL;
     std::lock_guard<std::mutex> lock(ctx->serve_mu);
     if (queued) *queued = (int64_t)ctx->serve_queue.size();
