@@ -880,14 +880,14 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
     }
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 2) != cudaSuccess ||
         dalloc(ctx, &ctx->d_qsize, QSIZE_WORDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
-        delete ctx;
+        hcao_destroy(ctx);  // frees what was allocated and the pool
         return HCAO_ENOMEM;
     }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
     cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 2), ctx->stream);
     cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long) * 4, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        delete ctx;
+        hcao_destroy(ctx);
         return HCAO_ECUDA;
     }
     *out = ctx;
