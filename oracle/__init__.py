@@ -87,6 +87,10 @@ def lib():
                                     C.c_void_p, C.POINTER(C.c_uint64)]
         L.ora_sample_init.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_int64,
                                       C.c_void_p]
+        L.ora_wr_density.restype = C.c_double
+        L.ora_wr_density.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.ora_diss_prob_wr.restype = C.c_double
+        L.ora_diss_prob_wr.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int]
         L.ora_sample_products.restype = C.c_int64
         L.ora_sample_products.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
@@ -250,6 +254,9 @@ class Oracle:
                                        _p(out), C.byref(tr)), "sample_lb")
         return out, int(tr.value)
 
+    def diss_prob_wr(self, rx, T, n_samp=1000) -> float:
+        return float(self.L.ora_diss_prob_wr(self.ctx, rx, T, n_samp))
+
     def sample_products(self, rx, reactants, seed, n):
         """n independent executions of reaction rx on one fixed set of
         reactants, a list of (species, velocity, levels): dissociation [A, M],
@@ -310,6 +317,13 @@ REC_NODES = 225
 
 def rec_node_T(i: int) -> float:
     return float(lib().ora_rec_node_T(i))
+
+
+def wr_density(hnu, E: float) -> float:
+    """Whitten-Rabinovitch density of states (1/J) of oscillators with quanta
+    hnu (J) at energy E (J) above the ground state."""
+    h = np.ascontiguousarray(hnu, np.float64)
+    return float(lib().ora_wr_density(_p(h), len(h), E))
 
 
 def gamma_q(a: float, x: float) -> float:

@@ -582,6 +582,75 @@ double ora_diss_prob(ora_ctx* c, int rx, double T) {
     return P;
 }
 
+/* Whitten-Rabinovitch density of vibrational states (the approximation the
+   paper gives beside Eq. recomb-correct) of l oscillators with quanta hnu[k]
+   (J) at energy E (J) above the ground state:
+     rho(E) = [E + a(E) E_z]^(l-1) / ((l-1)! prod_k hnu_k),  a = 1 - beta Omega,
+     E_z = sum_k hnu_k / 2,  beta = (l-1)^2 sum_k hnu_k^2 / (l (sum_k hnu_k)^2),
+     Omega = 10^(-1.0506 (E/E_z)^(1/4)) for E >= E_z,
+     1/Omega = 5 (E/E_z) + 2.73 (E/E_z)^(1/2) + 3.51 for E < E_z.
+   Readings: the logarithm of the Omega correlation is decadic; E_z is the
+   harmonic zero-point energy of the fundamentals. */
+static double wr_a(const double* hnu, int l, double E) {
+    double Ez = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < l; ++k) {
+        Ez += 0.5 * hnu[k];
+        s1 += hnu[k];
+        s2 += hnu[k] * hnu[k];
+    }
+    const double beta = ((double)(l - 1) * (double)(l - 1)) * s2 / ((double)l * s1 * s1);
+    const double x = E / Ez;
+    const double Om = x >= 1.0 ? pow(10.0, -1.0506 * pow(x, 0.25)) : 1.0 / (5.0 * x + 2.73 * sqrt(x) + 3.51);
+    return 1.0 - beta * Om;
+}
+
+double ora_wr_density(const double* hnu, int l, double E) {
+    double Ez = 0.0, lden = 0.0;
+    for (int k = 0; k < l; ++k) {
+        Ez += 0.5 * hnu[k];
+        lden += log(hnu[k]);
+    }
+    lden += lgamma((double)l);  /* log (l-1)! */
+    return exp((double)(l - 1) * log(E + wr_a(hnu, l, E) * Ez) - lden);
+}
+
+/* The recombination's P by the WR sum: n_samp energies evenly spaced between
+   the ground state and the threshold Dx above it, at the midpoints
+   E_i = (i - 1/2) Dx / n_samp (reading), weighted rho(E_i) exp(-E_i/kT);
+   P = sum_i Q(5/2 - omega, (Dx - E_i)/kT) w_i / sum_i w_i.  The quanta are
+   the fundamentals E_j(1) - E_j(0) of A's modes (harmonic for bends,
+   anharmonic for stretches).  The constant factor of rho cancels. */
+double ora_diss_prob_wr(ora_ctx* c, int rx, double T, int n_samp) {
+    const o_species* s = &c->sp[c->rx[rx].products[0]];
+    const int l = s->n_modes;
+    if (l < 1 || n_samp < 1) return NAN;
+    double hnu[ORA_MAX_MODES], Ez = 0.0;
+    for (int j = 0; j < l; ++j) {
+        hnu[j] = s->E[j][1] - s->E[j][0];
+        Ez += 0.5 * hnu[j];
+    }
+    const double kT = KB * T, a = 2.5 - c->omega;
+    const double Dx = rec_threshold(c, rx) - s->zpe;
+    if (!(Dx > 0.0)) return 1.0;
+    /* log weights first, then the sums relative to their largest */
+    double* lw = (double*)malloc(sizeof(double) * (size_t)n_samp);
+    double mx = -INFINITY;
+    for (int i = 0; i < n_samp; ++i) {
+        const double E = ((double)i + 0.5) * Dx / (double)n_samp;
+        lw[i] = (double)(l - 1) * log(E + wr_a(hnu, l, E) * Ez) - E / kT;
+        if (lw[i] > mx) mx = lw[i];
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n_samp; ++i) {
+        const double E = ((double)i + 0.5) * Dx / (double)n_samp;
+        const double w = exp(lw[i] - mx);
+        num += ora_gamma_q(a, (Dx - E) / kT) * w;
+        den += w;
+    }
+    free(lw);
+    return num / den;
+}
+
 /* vibrational partition sum with energies measured from the ground state */
 static double zvib_x(const o_species* s, double T) {
     double z = 1.0;

@@ -129,6 +129,12 @@ double   ora_rec_node_T(int i);
 double   ora_gamma_q(double a, double x);
 /* thermal dissociation probability per collision of recombination rx's molecule A at T */
 double   ora_diss_prob(ora_ctx*, int rx, double T);
+/* Whitten-Rabinovitch density of states (1/J) of l oscillators with quanta
+   hnu (J) at energy E (J) above the ground state */
+double   ora_wr_density(const double* hnu, int l, double E);
+/* the dissociation probability of recombination rx's molecule A at T by the
+   WR sum over n_samp evenly spaced energies below the threshold */
+double   ora_diss_prob_wr(ora_ctx*, int rx, double T, int n_samp);
 /* equilibrium constant n_B n_C / n_A (m^-3) of recombination rx at T */
 double   ora_keq(ora_ctx*, int rx, double T);
 /* k_r (m^6/s) of recombination rx with a third body of species spM at node i / at T */
