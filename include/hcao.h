@@ -353,6 +353,21 @@ hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, in
    T, interpolated as the collision step does (host copy of the device table). */
 hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, double* out);
 
+/* Whitten-Rabinovitch density of vibrational states (1/J) of n_osc harmonic
+   oscillators with quanta hnu[0..n_osc-1] (J) at energy E (J) above the
+   ground state: the approximation the paper gives beside Eq. recomb-correct
+   for the sampled dissociation probability (decadic logarithm in the Omega
+   correlation, E_z half the sum of the quanta).  Host computation: needs no
+   context or GPU.  NaN for n_osc < 1, a non-positive quantum or E < 0. */
+double hcao_wr_density(const double* hnu, int n_osc, double E);
+/* The sampled form of the dissociation probability with the WR density:
+   n_samp energies at the midpoints of equal intervals between the ground
+   state and the threshold Dx (J above the ground state), weighted
+   rho(E) exp(-E/kT); P = sum Q(5/2 - omega, (Dx - E_i)/kT) w_i / sum w_i, Q
+   the regularised upper incomplete gamma.  Host computation.  NaN for bad
+   arguments; 1 for Dx <= 0.  (The rate tables use the exact level sum.) */
+double hcao_wr_diss_prob(const double* hnu, int n_osc, double Dx, double omega, double T, int n_samp);
+
 /* Number of this library's kernels launched since create (instrumentation). */
 uint64_t hcao_kernel_launches(const hcao_ctx* ctx);
 

@@ -945,6 +945,12 @@ void hcao_destroy(hcao_ctx* ctx) {
 
 const char* hcao_last_error(const hcao_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
 
+double hcao_wr_density(const double* hnu, int n_osc, double E) { return wr_density(hnu, n_osc, E); }
+
+double hcao_wr_diss_prob(const double* hnu, int n_osc, double Dx, double omega, double T, int n_samp) {
+    return wr_diss_prob(hnu, n_osc, Dx, 2.5 - omega, T, n_samp);
+}
+
 hcao_status hcao_recomb_rate(hcao_ctx* ctx, int reaction, int spM, double T, double* out) {
     DeviceScope ds_(ctx);
     if (!ctx || !out || reaction < 0 || reaction >= ctx->n_reactions || spM < 0 || spM >= ctx->n_species)

@@ -181,6 +181,62 @@ double thermal_diss_prob(const std::vector<std::vector<double>>& lev, double D, 
     return walk(c, 0, 0.0, 1.0) / c.zrest[0];
 }
 
+// Whitten-Rabinovitch: l oscillators, quanta hnu, E above the ground state.
+// With x = E/E_z (E_z = half the sum of the quanta), the correction
+// a(x) = 1 - beta w(x), w = 10^(-1.0506 x^(1/4)) for x >= 1 and
+// w = 1/(5 x + 2.73 sqrt(x) + 3.51) below, beta = (l-1)^2 <nu^2> / (l <nu>^2)
+// written with sums: (l-1)^2 S2 / (l S1^2).  The density is
+// (E + a E_z)^(l-1) / ((l-1)! prod hnu); computed through its logarithm.
+static bool wr_setup(const double* hnu, int l, double& Ez, double& beta, double& lden) {
+    if (!hnu || l < 1) return false;
+    double s1 = 0.0, s2 = 0.0;
+    lden = std::lgamma((double)l);
+    for (int k = 0; k < l; ++k) {
+        if (!(hnu[k] > 0.0)) return false;
+        s1 += hnu[k];
+        s2 += hnu[k] * hnu[k];
+        lden += std::log(hnu[k]);
+    }
+    Ez = 0.5 * s1;
+    beta = (double)(l - 1) * (double)(l - 1) * s2 / ((double)l * s1 * s1);
+    return true;
+}
+
+static double wr_log_shape(int l, double Ez, double beta, double E) {
+    const double x = E / Ez;
+    const double w = x < 1.0 ? 1.0 / (5.0 * x + 2.73 * std::sqrt(x) + 3.51)
+                             : std::pow(10.0, -1.0506 * std::sqrt(std::sqrt(x)));
+    return (double)(l - 1) * std::log(E + (1.0 - beta * w) * Ez);
+}
+
+double wr_density(const double* hnu, int l, double E) {
+    double Ez, beta, lden;
+    if (!wr_setup(hnu, l, Ez, beta, lden) || !(E >= 0.0)) return NAN;
+    return std::exp(wr_log_shape(l, Ez, beta, E) - lden);
+}
+
+double wr_diss_prob(const double* hnu, int l, double Dx, double a, double T, int n_samp) {
+    double Ez, beta, lden;
+    if (!wr_setup(hnu, l, Ez, beta, lden) || n_samp < 1 || !(T > 0.0) || !(a > 0.0)) return NAN;
+    if (!(Dx > 0.0)) return 1.0;
+    const double kT = 1.380649e-23 * T, dE = Dx / (double)n_samp;
+    std::vector<double> lw((size_t)n_samp);
+    double top = -INFINITY;
+    for (int i = 0; i < n_samp; ++i) {
+        const double E = ((double)i + 0.5) * dE;
+        lw[(size_t)i] = wr_log_shape(l, Ez, beta, E) - E / kT;
+        top = std::max(top, lw[(size_t)i]);
+    }
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < n_samp; ++i) {
+        const double E = ((double)i + 0.5) * dE;
+        const double w = std::exp(lw[(size_t)i] - top);
+        num += w * inc_gamma_q(a, (Dx - E) / kT);
+        den += w;
+    }
+    return num / den;
+}
+
 double zvib_excited(const std::vector<std::vector<double>>& lev, double T) {
     const double kT = 1.380649e-23 * T;
     double z = 1.0;

@@ -19,6 +19,15 @@ double inc_gamma_q(double a, double x);
 // D: dissociation threshold from the well bottom, a = 5/2 - omega.
 double thermal_diss_prob(const std::vector<std::vector<double>>& lev, double D, double a, double T);
 
+// Whitten-Rabinovitch density of states (1/J) of l oscillators with quanta
+// hnu (J) at E (J) above the ground state; NaN for bad arguments.
+double wr_density(const double* hnu, int l, double E);
+
+// The sampled (WR) dissociation probability: n_samp midpoint energies below
+// the threshold Dx (J above the ground state), weights rho(E) exp(-E/kT),
+// P = sum Q(a, (Dx - E)/kT) w / sum w.  NaN for bad arguments.
+double wr_diss_prob(const double* hnu, int l, double Dx, double a, double T, int n_samp);
+
 // Vibrational partition sum with energies measured from the ground state.
 double zvib_excited(const std::vector<std::vector<double>>& lev, double T);
 

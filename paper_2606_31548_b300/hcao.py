@@ -31,7 +31,7 @@ EXPORTS = [
     "hcao_cell_sort", "hcao_level_energy", "hcao_n_levels", "hcao_kernel_launches",
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
-    "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate",
+    "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -125,6 +125,10 @@ def lib() -> C.CDLL:
         L.hcao_read_reaction_counts.argtypes = [vp, i32, vp, i32]
         L.hcao_read_cell_sgmax.argtypes = [vp, i32, vp]
         L.hcao_set_log.argtypes = [vp, i32]
+        L.hcao_wr_density.argtypes = [vp, i32, dbl]
+        L.hcao_wr_density.restype = dbl
+        L.hcao_wr_diss_prob.argtypes = [vp, i32, dbl, dbl, dbl, i32]
+        L.hcao_wr_diss_prob.restype = dbl
         L.hcao_read_log.argtypes = [vp, vp, i64, C.POINTER(i64)]
         L.hcao_cell_sort.argtypes = [vp, vp, i64, C.c_uint32, vp, vp]
         L.hcao_level_energy.argtypes = [vp, i32, i32, i32, C.POINTER(dbl)]
@@ -156,6 +160,19 @@ def _dptr(ptr) -> C.c_void_p:
     if hasattr(ptr, "data_ptr"):
         return C.c_void_p(ptr.data_ptr())
     return C.c_void_p(int(ptr))
+
+
+def wr_density(hnu, E: float) -> float:
+    """Whitten-Rabinovitch density of states (1/J) of oscillators with quanta
+    hnu (J) at E (J) above the ground state (host computation, no GPU)."""
+    h = np.ascontiguousarray(hnu, np.float64)
+    return float(lib().hcao_wr_density(h.ctypes.data, len(h), E))
+
+
+def wr_diss_prob(hnu, Dx: float, omega: float, T: float, n_samp: int = 1000) -> float:
+    """The WR form of the dissociation probability (host computation)."""
+    h = np.ascontiguousarray(hnu, np.float64)
+    return float(lib().hcao_wr_diss_prob(h.ctypes.data, len(h), Dx, omega, T, n_samp))
 
 
 class Context:
