@@ -1,12 +1,17 @@
-"""Benchmark: the DSMC collision phase (HCAO LB relaxation + QK dissociation)
-on the 4096-cell x 500-particle CH4-like heat bath at 15000 K (2.05M
-particles), one step = one collision phase over all cells.
+"""Benchmark: the DSMC collision phase (HCAO LB relaxation + QK chemistry).
+
+Headline workload: the CH4 + H -> CH3 + H2 exchange mixture, 16384 cells x
+1200 particles (19.7M), 50/50 CH4/H at 4000 K, one stretch coupled to the
+reaction coordinate, FP32 velocities with fixed-point energy bookkeeping.
+One step = one collision phase over all cells.  `--workload heat_bath` times
+the 4096-cell x 500-particle CH4-like heat bath at 15000 K instead.
 
 Prints one JSON line.  `value` = particle-steps/s over the timed steps, device
 time from CUDA events on the library's stream, L2 flushed (a 256 MiB write)
-before every timed step.  `e2e` = the same metric through the C ABI with host
-buffers: every step loads the state from pinned host memory, steps, and reads
-the moments back.  --impl reference times the oracle (CPU) instead.
+before every timed step (the particle state, 630 MB, is larger than L2 too).
+`e2e` = the same metric through the C ABI with host buffers: every step loads
+the state from pinned host memory, steps, and reads the moments back.
+--impl reference times the oracle (CPU) instead.
 """
 from __future__ import annotations
 
@@ -26,9 +31,16 @@ sys.path.insert(0, ROOT)
 from paper_2606_31548_b300 import workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-WORKLOAD = "ch4_heat_bath_4096x500_15000K_dissociation"
+WORKLOADS = {
+    "exchange": "ch4_h_exchange_16384x1200_4000K",
+    "heat_bath": "ch4_heat_bath_4096x500_15000K_dissociation",
+}
 KERNEL_SRC = os.path.join(ROOT, "paper_2606_31548_b300", "csrc", "hcao_kernels.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffic.json")
+FUSED_SRC = os.path.join(ROOT, "paper_2606_31548_b300", "csrc", "hcao_fused.cuh")
+TRAFFIC_FILES = {
+    "queue": os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffic.json"),
+    "fused": os.path.join(ROOT, "profiles", "k_collide_fused_ch4_h_exchange_traffic.json"),
+}
 
 # Algorithmic lane-operations of the relaxation kernel per unit of K5 work (the
 # least integer/FP32 lane operations each unit needs):
@@ -54,16 +66,21 @@ def _peaks():
 
 
 def _kernel_hash():
+    """First 16 hex digits of the sha256 of the collision kernels' source
+    (hcao_kernels.cuh, then hcao_fused.cuh)."""
     import hashlib
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in (KERNEL_SRC, FUSED_SRC):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-def _traffic_per_launch():
-    """DRAM bytes per launch of the relaxation kernel from the committed ncu
+def _traffic_per_launch(path: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, or None if the kernel source changed since it was taken."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(TRAFFIC_FILES[path]) as f:
             t = json.load(f)
         if t.get("kernel_src_sha256_16") != _kernel_hash():
             return None
@@ -104,10 +121,12 @@ def _sum_over_ranks(x: float) -> float:
     return x
 
 
-def replica_workload(rank: int, **kw):
-    """The heat bath each rank steps: the same recipe with a seed of its own
+def headline_workload(kind: str, rank: int = 0, **kw):
+    """The workload each rank steps: the same recipe with a seed of its own
     (ranks are independent replicas; no data-path collective)."""
-    return W.ch4_heat_bath(seed=0x48434132 + rank, **kw)
+    if kind == "heat_bath":
+        return W.ch4_heat_bath(seed=0x48434132 + rank, **kw)
+    return W.ch4_h_exchange(seed=0x48434133 + rank, T0=kw.pop("T0", 4000.0), **kw)
 
 
 def aggregate(units: float, seconds: float):
@@ -126,12 +145,12 @@ class Clocks:
     def __init__(self, device: int):
         self.dev = device
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"hcao_bench_clocks_{os.getpid()}_{device}.csv")
         self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "50"],
@@ -190,11 +209,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples_in_timed_region": len(sm), "samples_total": n_all}
 
 
-def cpu_baseline(budget_s: float = 12.0, cells: int = 48):
+def cpu_baseline(kind: str = "exchange", budget_s: float = 12.0, cells: int = 48):
     """The oracle, as it stands, on a bounded sample of the same workload:
-    `cells` of the 4096 cells (500 particles each), stepped until ~budget_s."""
+    `cells` evenly spaced cells of the headline workload, stepped until
+    ~budget_s (cells are independent and keyed by their index, so a sample of
+    cells steps exactly as those cells do in the whole workload)."""
     import oracle
-    w = W.ch4_heat_bath()
+    w = headline_workload(kind)
     pick = np.arange(cells) * (w.n_cells // cells)
     sel = np.isin(w.cell, pick)
     o = oracle.Oracle()
@@ -215,10 +236,13 @@ def cpu_baseline(budget_s: float = 12.0, cells: int = 48):
         steps += 1
     dt = time.perf_counter() - t0
     acc = int(o.read_counters(0)[1])
+    per_cell = int(np.bincount(w.cell, minlength=w.n_cells).max())
     return {"value": psteps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "host_cores": os.cpu_count(),
             "collisions_per_s": acc / dt,
-            "sample": f"{cells} of the 4096 cells ({int(sel.sum())} particles), {steps} steps, "
-                      f"single-threaded FP64 C oracle, {dt:.1f} s"}
+            "sample": f"{cells} of the {w.n_cells} cells ({int(sel.sum())} particles, "
+                      f"{per_cell} per cell), {steps} steps, single-threaded FP64 C oracle, "
+                      f"{dt:.1f} s, on a host with {os.cpu_count()} cores"}
 
 
 def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> dict:
@@ -230,6 +254,7 @@ def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> 
         ctx.step(1)
     ctx.sync()
     c0 = ctx.read_counters(0)
+    comp0 = composition(ctx, w)
     ms, ps = 0.0, 0
     for _ in range(steps):
         ps += ctx.count(0)
@@ -241,9 +266,12 @@ def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> 
         b.synchronize()
         ms += a.elapsed_time(b)
     c1 = ctx.read_counters(0)
+    comp1 = composition(ctx, w)
     ctx.close()
     t = ms / 1e3
     return {"workload": w.name, "particles": int(w.n), "cells": int(w.n_cells), "T0_K": w.T_tr0,
+            "reactions": [r.type for r in w.reactions],
+            "composition": {"timed_start": comp0, "timed_end": comp1},
             "precision": "fp64" if prec == hcao.FP64 else "fp32", "steps": steps, "warmup": warmup,
             "particle_steps_per_s": ps / t, "collisions_per_s": float(c1[1] - c0[1]) / t,
             "reactions_per_s": float(sum(c1[8:]) - sum(c0[8:])) / t, "ms_per_step": 1e3 * t / steps}
@@ -386,16 +414,28 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
                     "plain loop serves the same arrivals first come first served"}
 
 
+def _config(kind, w, args, ws):
+    per_cell = int(np.bincount(w.cell, minlength=w.n_cells).max())
+    return {"workload": WORKLOADS[kind], "cells": w.n_cells, "particles_per_cell": per_cell,
+            "particles": w.n, "T0_K": w.T_tr0, "precision": args.precision,
+            "species": [s.name for s in w.species],
+            "l2": "flushed (256 MiB write) before every timed step; the particle state is larger than L2",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return 0
-    cb = cpu_baseline(budget_s=max(3.0, min(20.0, 2.0 * args.steps)))
+    cb = cpu_baseline(args.workload, budget_s=max(3.0, min(20.0, 2.0 * args.steps)))
+    w = headline_workload(args.workload)
+    cfg = _config(args.workload, w, args, 1)
+    cfg["precision"] = "fp64"
+    cfg["sample"] = cb["sample"]
     line = {"impl": "reference", "metric": "particle-steps/s", "value": cb["value"],
             "unit": "particle-steps/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": 4096, "particles_per_cell": 500,
-                       "sample": cb["sample"]},
+            "config": cfg,
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
@@ -404,19 +444,26 @@ def run_reference(args):
     return 0
 
 
+def composition(ctx, w):
+    m = ctx.read_moments(0)
+    return {s.name: int(m.n[i]) for i, s in enumerate(w.species)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="exchange", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--batched-res", type=int, default=256, help="reservoirs of the batched run (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=12)
     ap.add_argument("--served-jobs", type=int, default=48, help="jobs of the served run (0: skip)")
-    ap.add_argument("--other-configs", type=int, default=1, help="measure the triatomic and exchange configs too")
+    ap.add_argument("--other-configs", type=int, default=1,
+                    help="measure the exchange temperature sweep, the heat bath and the triatomic too")
     ap.add_argument("--served-rate", type=float, default=50.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -433,7 +480,7 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     prec = hcao.FP32 if args.precision == "fp32" else hcao.FP64
-    w = replica_workload(rank)
+    w = headline_workload(args.workload, rank)
     ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -441,6 +488,7 @@ def main():
         ctx.step(1)
     ctx.sync()
     c0 = ctx.read_counters(0)
+    comp0 = composition(ctx, w)
     work0 = ctx.read_work()
     launches0 = ctx.kernel_launches()
     ctx.set_profiling(True)
@@ -466,19 +514,23 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ctx.sync()
     c1 = ctx.read_counters(0)
+    comp1 = composition(ctx, w)
     work = (ctx.read_work() - work0).astype(np.float64)
     launches = ctx.kernel_launches() - launches0
     kms, kn = ctx.read_profile()
     ctx.set_profiling(False)
     collisions = float(c1[1] - c0[1])
+    reactions = float(sum(c1[8:]) - sum(c0[8:]))
     tot_psteps, t = aggregate(float(psteps), ms / 1e3)
     tot_coll = _sum_over_ranks(collisions)
+    tot_rx = _sum_over_ranks(reactions)
 
-    # roofline of the dominant kernel, the relaxation kernel: it is bound by
-    # plain ALU work (the K5 draws), so achieved = algorithmic lane-operations
-    # (counted K5 work x OPS_PER_UNIT) / its CUDA-event time, against the lane
-    # peak 148 SMs x 128 lanes x the maximum SM clock.  The HBM view (SURVEY's
-    # 2 S bytes per particle-step, S = 26 B FP32 / 38 B FP64) is kept beside it.
+    # roofline.  HBM view (the algorithmic bytes of the collision phase: one
+    # read and one write of each particle's state, 2 S bytes per
+    # particle-step, S = 26 B FP32 / 38 B FP64) over the collide-phase kernels'
+    # CUDA-event time; the ALU view of the relaxation kernel (counted K5 work x
+    # OPS_PER_UNIT lane-operations against 148 SMs x 128 lanes x the maximum
+    # SM clock) beside it.
     names = hcao.Context.PROFILE_KERNELS
     per_step = {k: kms[i] / args.steps for i, k in enumerate(names)}
     hbm_peak, sm_mhz_max, peak_kind = _peaks()
@@ -487,22 +539,35 @@ def main():
     alu_peak = SMS * LANES_PER_SM * sm_mhz_max * 1e6 / 1e9  # Glane-op/s
     alu_ach = lane_ops / relax_s / 1e9 if relax_s > 0 and lane_ops > 0 else None
     S = 26.0 if prec == hcao.FP32 else 38.0
-    collide_s = (kms[1] + kms[2] + kms[3]) / 1e3
+    fused = int(kn[5]) > 0
+    collide_s = (kms[1] + kms[2] + kms[3] + kms[5]) / 1e3
+    step_s = float(np.sum(kms)) / 1e3
+    if fused:  # the relaxation runs inside the fused kernel
+        relax_s = kms[5] / 1e3
+        alu_ach = lane_ops / relax_s / 1e9 if relax_s > 0 and lane_ops > 0 else None
     hbm_ach = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
-    tr = _traffic_per_launch()
-    roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Glane-op/s",
-            "frac": (alu_ach / alu_peak) if alu_ach else None,
+    tr = _traffic_per_launch("fused" if fused else "queue")
+    roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
             "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "peak_kind": f"derived: {SMS} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz ({peak_kind} clock)",
-            "kernel": "k_relax_fast" if prec == hcao.FP32 else "k_relax",
-            "work_per_step": {"level_evals": work[0] / args.steps, "mode_draws": work[1] / args.steps,
-                              "samples": work[2] / args.steps, "pairs": work[3] / args.steps},
-            "ops_per_unit": list(OPS_PER_UNIT),
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+            "kernel": "k_collide_fused (the whole collision phase, one launch per step)" if fused
+                      else "collide phase (select + relax + react kernels)",
+            "path": "fused" if fused else "queue",
+            "bytes_per_particle_step": 2 * S,
+            "step_view": {"achieved_GBps": (2 * S * psteps) / step_s / 1e9 if step_s > 0 else None,
+                          "time": "whole step (set-up and end-of-step kernels included)"},
             "kernel_ms_per_step": per_step,
             "kernel_launches": {k: int(kn[i]) for i, k in enumerate(names)},
-            "hbm_view": {"achieved_GBps": hbm_ach, "peak_GBps": hbm_peak,
-                         "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
-                         "bytes_per_particle_step": 2 * S, "time": "collide phase"}}
+            "alu_view": {"kernel": ("k_collide_fused" if fused else "k_relax_fast") if prec == hcao.FP32
+                         else "k_relax",
+                         "achieved_Glane_op_s": alu_ach, "peak_Glane_op_s": alu_peak,
+                         "frac": (alu_ach / alu_peak) if alu_ach else None,
+                         "peak_kind": f"derived: {SMS} SMs x {LANES_PER_SM} lanes x {sm_mhz_max:.0f} MHz",
+                         "work_per_step": {"level_evals": work[0] / args.steps,
+                                           "mode_draws": work[1] / args.steps,
+                                           "samples": work[2] / args.steps, "pairs": work[3] / args.steps},
+                         "ops_per_unit": list(OPS_PER_UNIT)}}
 
     # e2e through the C ABI with host buffers (pinned): load + step + moments
     e2e = None
@@ -558,48 +623,59 @@ def main():
                        "workload), hcao_step(1), hcao_read_moments; split_ms: the median of 3 "
                        "separate synchronised calls of each, measured after the timed loop"}
         ectx.close()
+        del v_h, q_h, s_h, c_h
 
-    batched = None
-    if args.batched_res > 0 and ws == 1:
-        ctx.close()
-        batched = run_batched(hcao, torch, prec, stream, args.batched_res, args.batched_steps)
     others = None
     if args.other_configs and ws == 1:
-        flush2 = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-        others = {
-            "triatomic_relaxation_20000x1_fp64": run_config(
-                hcao, torch, stream, W.relaxation_triatomic(), hcao.FP64, 50, 5, flush2),
-            "ch4_h_exchange_16384x1200_4000K_fp32": run_config(
-                hcao, torch, stream, W.ch4_h_exchange(T0=4000.0), hcao.FP32, 10, 3, flush2),
-        }
-        del flush2
+        ctx.close()
+        ctx = None
+        others = {}
+        if args.workload != "exchange":
+            others["ch4_h_exchange_16384x1200_4000K_fp32"] = run_config(
+                hcao, torch, stream, W.ch4_h_exchange(T0=4000.0), hcao.FP32, 10, 3, flush)
+        for T in (2000.0, 3000.0, 5000.0, 6000.0):
+            others[f"ch4_h_exchange_16384x1200_{T:.0f}K_fp32"] = run_config(
+                hcao, torch, stream, W.ch4_h_exchange(T0=T), hcao.FP32, 10, 3, flush)
+        if args.workload != "heat_bath":
+            others["ch4_heat_bath_4096x500_15000K_fp32"] = run_config(
+                hcao, torch, stream, W.ch4_heat_bath(), hcao.FP32, 20, 5, flush)
+        others["ch4_heat_bath_4096x500_15000K_no_dissociation_fp32"] = run_config(
+            hcao, torch, stream, W.ch4_heat_bath(dissociation=False), hcao.FP32, 20, 5, flush)
+        others["triatomic_relaxation_20000x1_fp64"] = run_config(
+            hcao, torch, stream, W.relaxation_triatomic(), hcao.FP64, 50, 5, flush)
+    batched = None
+    if args.batched_res > 0 and ws == 1:
+        if ctx is not None:
+            ctx.close()
+            ctx = None
+        batched = run_batched(hcao, torch, prec, stream, args.batched_res, args.batched_steps)
     served = None
     if args.served_jobs > 0 and ws == 1:
         served = run_served(hcao, prec, stream, args.served_jobs, args.served_rate, recombination=True)
     cb = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline()
+        cb = cpu_baseline(args.workload)
     clocks = clk.summary()
     if rank == 0:
         line = {
             "metric": "particle-steps/s", "value": tot_psteps / t, "unit": "particle-steps/s",
-            "collisions_per_s": tot_coll / t,
+            "collisions_per_s": tot_coll / t, "reactions_per_s": tot_rx / t,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == hcao.FP32 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": w.n_cells, "particles_per_cell": 500,
-                       "particles": w.n, "T0_K": w.T_tr0, "precision": args.precision,
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "parallelism": f"replicas x{ws}"},
+            "config": _config(args.workload, w, args, ws),
+            "composition": {"timed_start": comp0, "timed_end": comp1},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served, "other_configs": others,
+            "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served,
+            "other_configs": others,
         }
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     return 0
 
 

@@ -63,7 +63,9 @@ typedef struct {
     double table_span_J;    /* K5 grid span above the ZPE (default 64 eV) */
     uint32_t reject_cap;    /* trials per LB sample before HCAO_EREJECT_LIMIT (default 2^20) */
     int max_rounds;         /* NTC pairing rounds per cell and step (default 2) */
-    double capacity_factor; /* per-cell slots = count*factor + extra (default 2.0) */
+    double capacity_factor; /* per-cell slots = count*factor + extra (default 2.0); a context
+                               whose reactions neither create nor remove particles gives
+                               each cell its count (rounded up to 8) */
     int capacity_extra;     /* (default 64) */
 } hcao_config;
 
@@ -230,8 +232,10 @@ hcao_status hcao_read_log(hcao_ctx* ctx, hcao_log_rec* host_out, int64_t max, in
    their cells): device keys[n] (cell ids < n_cells) -> device perm[n]
    (perm[j] = input index of the j-th particle in cell order, input order kept
    within a cell) and device offsets[n_cells+1] (start of each cell in perm).
-   Keys >= n_cells are sorted but not counted in offsets.  Uses scratch from
-   the context; asynchronous on the context's stream. */
+   Every key must be < n_cells: a larger key is not counted in offsets, and
+   its place in perm is unspecified (the radix passes read only the digits
+   that n_cells needs).  Uses scratch from the context; asynchronous on the
+   context's stream. */
 hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint32_t n_cells,
                            uint32_t* perm, uint32_t* offsets);
 
@@ -256,8 +260,14 @@ hcao_status hcao_sample_lb(hcao_ctx* ctx, int sp, double Ec, uint64_t seed, int6
    - It allocates nothing: its scratch is one file-scope device array sized
      for HCAO_NOALLOC_SORT_MAX_KEYS keys (about 8.7 MB), which every GPU that
      loads the library holds until the process exits.
-   - The first call on a device looks up that array's device address (with
-     the device current); make that first call before any stream capture.
+   - Every call looks up that array's device address with the calling
+     thread's device current (a host-side query, no allocation of its own).
+   - The array belongs to the library's sort module.  Under CUDA's lazy module
+     loading (the default) the first call on each device loads that module,
+     which allocates the array and may synchronise the device and fail for
+     lack of memory (HCAO_ECUDA).  Callers that must never allocate should
+     make one warm-up call on each device at start-up, before any stream
+     capture and before their own allocator takes the device's memory.
    - n > HCAO_NOALLOC_SORT_MAX_KEYS returns HCAO_EINVAL; a failed CUDA call
      returns HCAO_ECUDA.
    - All calls share the one array: calls that may overlap on the GPU (other
@@ -272,11 +282,28 @@ hcao_status hcao_cell_sort_noalloc(const uint32_t* keys, int64_t n, uint32_t n_c
 hcao_status hcao_level_energy(const hcao_ctx* ctx, int sp, int mode, int level, double* out);
 hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out);
 
+/* Collision-phase path.  HCAO_PATH_QUEUE: per pairing round, a selection,
+   a relaxation and a reaction kernel that pass pairs through queues in
+   global memory, then end-of-step kernels (about eleven launches a step; any
+   context).  HCAO_PATH_FUSED: one kernel a step, one CTA per cell, the
+   cell's records staged in shared memory; it needs FP32 mode, no reaction
+   that creates or removes particles (dissociation, recombination), no
+   per-pair log and cells of at most 4096 particle slots, and gives the same
+   bits as the queue path.  HCAO_PATH_AUTO (the default) takes the fused path
+   whenever the context allows it.  hcao_set_step_path(ctx, HCAO_PATH_FUSED)
+   on a context that does not allow it makes the next hcao_step return
+   HCAO_EINVAL.  hcao_get_step_path gives the path the next step takes
+   (HCAO_PATH_QUEUE or HCAO_PATH_FUSED). */
+enum { HCAO_PATH_AUTO = 0, HCAO_PATH_QUEUE = 1, HCAO_PATH_FUSED = 2 };
+hcao_status hcao_set_step_path(hcao_ctx* ctx, int path);
+hcao_status hcao_get_step_path(const hcao_ctx* ctx, int* path);
+
 /* Kernel timing: with profiling on, hcao_step records CUDA events on the
    context's stream around each kernel.  hcao_read_profile accumulates and
    returns, for k = 0 (setup), 1 (select), 2 (relax), 3 (react), 4 (finish),
-   the summed device time in ms (host_ms[k]) and the number of launches
-   (host_launches[k]); *n_out = 5.  hcao_set_profiling resets the sums. */
+   5 (the fused per-cell kernel), the summed device time in ms (host_ms[k])
+   and the number of launches (host_launches[k]); *n_out = min(max, 6).
+   hcao_set_profiling resets the sums. */
 hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
                               int* n_out);

@@ -95,8 +95,8 @@ def lib():
         L.ora_sample_products.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                           C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_uint64, C.c_int64, C.c_void_p, C.c_void_p]
-        L.ora_feistel.restype = C.c_uint32
-        L.ora_feistel.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]
+        L.ora_pair_perm.restype = C.c_uint32
+        L.ora_pair_perm.argtypes = [C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]
         L.ora_philox.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         L.ora_tvib.restype = C.c_double
         L.ora_tvib.argtypes = [C.c_void_p, C.c_int, C.c_int]
@@ -128,9 +128,10 @@ def philox(ctr: Sequence[int], key: Sequence[int]) -> List[int]:
     return list(o)
 
 
-def feistel(x: int, N: int, key: Sequence[int]) -> int:
+def pair_perm(x: int, N: int, key: Sequence[int]) -> int:
+    """The keyed pairing permutation of [0, N)."""
     k = (C.c_uint32 * 4)(*key)
-    return int(lib().ora_feistel(x, N, k))
+    return int(lib().ora_pair_perm(x, N, k))
 
 
 class Oracle:

@@ -18,7 +18,7 @@
  *   K5 table sampler  : pinned (enumerated LB target, chi^2; equals literal P8)
  *   literal P8        : pinned (enumerated LB target, chi^2)
  *   init P6/P7        : pinned (Boltzmann populations, chi^2)
- *   feistel           : pinned (bijection, exhaustive)
+ *   pair_perm         : pinned (bijection, exhaustive; uniform image and partner offsets)
  *   NTC + VHS         : pinned (VHS closed-form collision frequency)
  *   relax + scatter   : pinned (per-collision momentum/energy conservation,
  *                       equilibrium Boltzmann populations, detailed balance)
@@ -42,7 +42,7 @@
 #define PI_D 3.14159265358979323846
 
 /* Philox stream purposes (counter word 3 = purpose << 24 | block). */
-enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
+enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
        PU_INIT = 7, PU_TEST = 8, PU_REC = 9 };
 
 #define MAX_SPECIES 16
@@ -167,26 +167,27 @@ static double st_u01(o_stream* s) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Feistel bijection on [0,N): balanced 4-round Feistel network on the
-   smallest even bit width covering N, cycle-walked into [0,N).  Round
-   function: MurmurHash3's 32-bit finaliser of (R xor round key). */
-static uint32_t fmix32(uint32_t h) {
-    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
-    return h;
-}
-uint32_t ora_feistel(uint32_t x, uint32_t N, const uint32_t key[4]) {
-    int b = 2;
-    while (((uint64_t)1 << b) < (uint64_t)N) b += 2;
-    int half = b / 2;
-    uint32_t mask = (uint32_t)(((uint64_t)1 << half) - 1);
+/* Keyed bijection of [0,N) that forms the disjoint NTC pairs (reading A9:
+   pair k of a round is (pi(2k), pi(2k+1))).  On b-bit words, b the smallest
+   width with 2^b >= N, three rounds of
+       x = ((x xor k_r) * M_r) mod 2^b,   x = x xor (x >> ceil(b/2)),
+   each a bijection of [0, 2^b) (xor with a constant, multiplication by an
+   odd number modulo 2^b, a right xorshift), repeated from the result until it
+   falls in [0,N) (cycle walking keeps a bijection of [0,N)).  Round keys:
+   the round's key words 0..2; multipliers: the odd constants 0x9E3779B1,
+   0x85EBCA6B, 0xC2B2AE35. */
+uint32_t ora_pair_perm(uint32_t x, uint32_t N, const uint32_t key[4]) {
+    static const uint32_t mult[3] = {0x9E3779B1u, 0x85EBCA6Bu, 0xC2B2AE35u};
+    if (N <= 1u) return 0u;
+    int b = 1;
+    while (((uint64_t)1 << b) < (uint64_t)N) b++;
+    uint32_t mask = (uint32_t)(((uint64_t)1 << b) - 1);
+    int h = (b + 1) / 2;
     do {
-        uint32_t L = x >> half, R = x & mask;
-        for (int r = 0; r < 4; ++r) {
-            uint32_t nL = R;
-            uint32_t nR = L ^ (fmix32(R ^ key[r]) & mask);
-            L = nL; R = nR;
+        for (int r = 0; r < 3; ++r) {
+            x = ((x ^ (key[r] & mask)) * mult[r]) & mask;
+            x = x ^ (x >> h);
         }
-        x = (L << half) | R;
     } while (x >= N);
     return x;
 }
@@ -1148,7 +1149,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
         else continue;
         int64_t m = 2 * rd->kmax + (int64_t)k;
         if (m >= (int64_t)rd->N) break;
-        uint32_t iM = ora_feistel((uint32_t)m, rd->N, rd->key);
+        uint32_t iM = ora_pair_perm((uint32_t)m, rd->N, rd->key);
         o_part* M = &rd->cl->p[iM];
         if (M->sp < 0) break;
         double kr = ora_rec_rate(c, r, M->sp, rd->T);
@@ -1315,15 +1316,15 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
         double Tcell = has_rec ? cell_temperature(c, cl) : 0.0;
         for (int64_t r = 0; r < rounds; ++r) {
             o_stream sf;
-            st_init(&sf, R->seed, R->step, (uint32_t)ci, (uint32_t)r << 24, PU_FEISTEL);
+            st_init(&sf, R->seed, R->step, (uint32_t)ci, (uint32_t)r << 24, PU_PERM);
             uint32_t key[4];
             for (int i = 0; i < 4; ++i) key[i] = st_word(&sf);
             int64_t kmax = nsel - r * P;
             if (kmax > P) kmax = P;
             o_round rd = { cl, (uint32_t)N, kmax, key, Tcell };
             for (int64_t k = 0; k < kmax; ++k) {
-                uint32_t ip = ora_feistel((uint32_t)(2 * k), (uint32_t)N, key);
-                uint32_t iq = ora_feistel((uint32_t)(2 * k + 1), (uint32_t)N, key);
+                uint32_t ip = ora_pair_perm((uint32_t)(2 * k), (uint32_t)N, key);
+                uint32_t iq = ora_pair_perm((uint32_t)(2 * k + 1), (uint32_t)N, key);
                 process_pair(c, R, (uint32_t)ci, (uint32_t)r, (uint32_t)k, &cl->p[ip], &cl->p[iq],
                              ip, iq, cl->sgmax, &seen, created, &n_created, &rd);
             }

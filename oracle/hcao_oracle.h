@@ -116,8 +116,8 @@ int64_t  ora_sample_products(ora_ctx*, int rx, int sp1, const double* v1, const 
 /* draws n initial states of species sp at T_vib (P6/P7) */
 int      ora_sample_init(ora_ctx*, int sp, double T_vib, uint64_t seed, int64_t n,
                          uint8_t* out_qn);
-/* Feistel permutation of [0,N) used for the disjoint NTC pairs */
-uint32_t ora_feistel(uint32_t x, uint32_t N, const uint32_t key[4]);
+/* keyed permutation of [0,N) that forms the disjoint NTC pairs */
+uint32_t ora_pair_perm(uint32_t x, uint32_t N, const uint32_t key[4]);
 void     ora_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* T_vib of one species in a reservoir by the zero-point search (P5) */
 double   ora_tvib(ora_ctx*, int res, int sp);

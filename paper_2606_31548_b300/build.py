@@ -24,7 +24,7 @@ UNITS = {
     "hcao_api.cu": [],
     "hcao_rates.cu": [],
 }
-HEADERS = ["hcao_internal.h", "hcao_kernels.cuh", "hcao_sort.h", "hcao_rates.h"]
+HEADERS = ["hcao_internal.h", "hcao_kernels.cuh", "hcao_fused.cuh", "hcao_sort.h", "hcao_rates.h"]
 
 
 def _nvcc() -> str:

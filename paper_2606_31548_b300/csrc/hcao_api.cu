@@ -54,6 +54,7 @@ struct Reservoir {
     void* recs = nullptr;
     size_t rec_bytes = 0;
     uint64_t total_cap = 0;
+    uint32_t max_cap = 0;          // largest cell capacity (slots)
 };
 
 // one served job: its copied inputs, state and result
@@ -153,12 +154,15 @@ struct hcao_ctx {
     bool layout_ok = true;          // false from a layout change until it completed
     size_t chcnt_cap = 0;
     uint32_t* d_err = nullptr;
+    uint32_t* d_ticket = nullptr;   // fused step: CTAs finished
+    int step_path = HCAO_PATH_AUTO; // requested collision-phase path (hcao_set_step_path)
+    int fused_smem_set = -1;        // dynamic shared memory the fused kernel was prepared for (records)
     bool log_on = false;
     uint32_t* d_scratch = nullptr;
     int64_t scratch_words = 0;
     // kernel timing: events recorded on the stream around each kernel class
     bool prof_on = false;
-    static constexpr int NPROF = 5;  // setup, select, relax, react, finish
+    static constexpr int NPROF = 6;  // setup, select, relax, react, finish, fused collide
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[NPROF];
     size_t prof_used[NPROF] = {};
     double prof_ms[NPROF] = {};
@@ -222,6 +226,18 @@ void dfree(hcao_ctx* ctx, T*& p) {
     if (p) cudaFreeAsync(p, ctx->stream);
     p = nullptr;
 }
+
+// A temporary device buffer of one entry point, released on every exit path
+// (stream-ordered, like dfree).
+template <class T>
+struct DevTemp {
+    hcao_ctx* ctx;
+    T* p = nullptr;
+    explicit DevTemp(hcao_ctx* c) : ctx(c) {}
+    ~DevTemp() { dfree(ctx, p); }
+    DevTemp(const DevTemp&) = delete;
+    DevTemp& operator=(const DevTemp&) = delete;
+};
 
 // FP32-mode energy bookkeeping unit: 2^-100 J (int64 range +-7e-12 J,
 // resolution 8e-31 J)
@@ -813,7 +829,26 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.err = ctx->d_err;
     a.max_rounds = ctx->cfg.max_rounds;
     a.reject_cap = ctx->cfg.reject_cap;
+    a.ticket = ctx->d_ticket;
     return a;
+}
+
+// The collision-phase path of the next step: the fused per-cell kernel when
+// the context allows it (FP32, no reaction that creates or removes particles,
+// no per-pair log, every cell within FUSED_MAX_RECS slots), else the
+// per-round queue kernels.  *smem_recs: the records the fused kernel stages.
+bool fused_eligible(const hcao_ctx* ctx, int* smem_recs) {
+    if (ctx->cfg.precision != HCAO_FP32 || ctx->hc.creates || ctx->n_recomb > 0 || ctx->log_on) return false;
+    uint32_t mx = 0;
+    for (const auto& r : ctx->res)
+        if (r.live && r.loaded && r.max_cap > mx) mx = r.max_cap;
+    if (mx > (uint32_t)FUSED_MAX_RECS) return false;
+    if (smem_recs) *smem_recs = (int)mx;
+    return true;
+}
+bool use_fused(const hcao_ctx* ctx, int* smem_recs) {
+    if (ctx->step_path == HCAO_PATH_QUEUE) return false;
+    return fused_eligible(ctx, smem_recs);
 }
 
 }  // namespace
@@ -879,11 +914,13 @@ hcao_status hcao_create(const hcao_config* config, hcao_ctx** out) {
         }
     }
     if (dalloc(ctx, &ctx->d_err, 1) != cudaSuccess || dalloc(ctx, &ctx->d_totals, MAX_ROUNDS + 2) != cudaSuccess ||
-        dalloc(ctx, &ctx->d_qsize, QSIZE_WORDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess) {
+        dalloc(ctx, &ctx->d_qsize, QSIZE_WORDS) != cudaSuccess || dalloc(ctx, &ctx->d_work, 4) != cudaSuccess ||
+        dalloc(ctx, &ctx->d_ticket, 1) != cudaSuccess) {
         hcao_destroy(ctx);  // frees what was allocated and the pool
         return HCAO_ENOMEM;
     }
     cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream);
+    cudaMemsetAsync(ctx->d_ticket, 0, sizeof(uint32_t), ctx->stream);
     cudaMemsetAsync(ctx->d_totals, 0, sizeof(uint32_t) * (MAX_ROUNDS + 2), ctx->stream);
     cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long) * 4, ctx->stream);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -930,6 +967,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_tsum);
     dfree(ctx, ctx->d_chcnt);
     dfree(ctx, ctx->d_err);
+    dfree(ctx, ctx->d_ticket);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -1347,10 +1385,15 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
                 const double m = mean_sigma_g(ctx, a, b, r->T_sgmax);
                 if (m > mx) mx = m;
             }
+    // a context whose reactions neither create nor remove particles keeps
+    // every cell's count for good: its cells need no spare slots
+    const bool grows = ctx->hc.creates != 0;
+    uint32_t max_cap = 0;
     for (int c = 0; c < r->n_cells; ++c) {
         const uint32_t count = off[c + 1] - off[c];
-        uint64_t cap = (uint64_t)std::ceil(count * f) + (uint64_t)ctx->cfg.capacity_extra;
+        uint64_t cap = grows ? (uint64_t)std::ceil(count * f) + (uint64_t)ctx->cfg.capacity_extra : (uint64_t)count;
         cap = (cap + 7) & ~(uint64_t)7;
+        if (cap > max_cap) max_cap = (uint32_t)std::min<uint64_t>(cap, 0xFFFFFFFFull);
         slot0[c] = tot;
         tot += cap;
         DevCell& d = cells[c];
@@ -1363,6 +1406,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     }
     const size_t rs = rec_size(ctx);
     r->total_cap = tot;
+    r->max_cap = max_cap;
     r->rec_bytes = (size_t)tot * rs;
     // the old records go only now, once the new input has passed its checks;
     // until relayout completes, the cell table may point at freed records
@@ -1426,30 +1470,26 @@ hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
             }
         }
     }
-    double *dbt = nullptr, *dsa = nullptr;
-    int* doff = nullptr;
-    CU(dalloc(ctx, &dbt, bt.size()));
-    CU(dalloc(ctx, &dsa, sa.size()));
-    CU(dalloc(ctx, &doff, off.size()));
-    if (!bt.empty()) CU(cudaMemcpyAsync(dbt, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, ctx->stream));
-    if (!sa.empty()) CU(cudaMemcpyAsync(dsa, sa.data(), sizeof(double) * sa.size(), cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(doff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
-    uint64_t* dpo = nullptr;
+    DevTemp<double> dbt(ctx), dsa(ctx);
+    DevTemp<int> doff(ctx);
+    DevTemp<uint64_t> dpo(ctx);
+    CU(dalloc(ctx, &dbt.p, bt.size()));
+    CU(dalloc(ctx, &dsa.p, sa.size()));
+    CU(dalloc(ctx, &doff.p, off.size()));
+    if (!bt.empty()) CU(cudaMemcpyAsync(dbt.p, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, ctx->stream));
+    if (!sa.empty()) CU(cudaMemcpyAsync(dsa.p, sa.data(), sizeof(double) * sa.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(doff.p, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
     uint64_t total = 0;
-    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
     if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_init_vib<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_res, id, ctx->d_consts, dbt,
-                                dsa, doff, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+        launch_init_vib<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_res, id, ctx->d_consts,
+                                dbt.p, dsa.p, doff.p, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
     else
-        launch_init_vib<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_res, id, ctx->d_consts, dbt,
-                               dsa, doff, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
+        launch_init_vib<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_res, id, ctx->d_consts,
+                               dbt.p, dsa.p, doff.p, ctx->cfg.reject_cap, ctx->d_err, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
-    dfree(ctx, dbt);
-    dfree(ctx, dsa);
-    dfree(ctx, doff);
-    dfree(ctx, dpo);
     return map_err(ctx);
 }
 
@@ -1502,14 +1542,65 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
     SERVE_GUARD(ctx);
     if (!ctx || n_steps < 0) return fail(ctx, HCAO_EINVAL, "step: bad arguments");
     if (ctx->n_cells_total == 0 || n_steps == 0) return HCAO_OK;
-    {
+    int smem_recs = 0;
+    const bool fused = use_fused(ctx, &smem_recs);
+    if (ctx->step_path == HCAO_PATH_FUSED && !fused)
+        return fail(ctx, HCAO_EINVAL, "step: the fused path needs FP32, no reaction that creates or removes "
+                                      "particles, no per-pair log and cells of at most 4096 slots");
+    if (!fused) {
         const hcao_status st = ensure_pair_buffers(ctx);
         if (st != HCAO_OK) return st;
+    } else if (ctx->fused_smem_set != smem_recs) {
+        CU(fused_prepare(smem_recs));
+        ctx->fused_smem_set = smem_recs;
     }
     StepArgs a = make_args(ctx);
     const int block = 128;
     const int grid = ctx->sm_count * 8;
     const bool f64 = ctx->cfg.precision == HCAO_FP64;
+    if (fused) {
+        // the whole collision phase of a step as one kernel (one CTA per cell)
+        a.fused_recs = smem_recs;  // part of the graph's key: a new shared-memory size re-captures
+        if (!ctx->prof_on && ctx->use_graph) {
+            if (!ctx->graph || std::memcmp(&a, &ctx->graph_args, sizeof a) != 0) {
+                if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+                ctx->graph = nullptr;
+                if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+                cudaGraph_t g = nullptr;
+                CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+                launch_fused(a, smem_recs, ctx->cap_stream);
+                CU(cudaStreamEndCapture(ctx->cap_stream, &g));
+                cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+                cudaGraphDestroy(g);
+                CU(e);
+                ctx->graph_args = a;
+            }
+            for (int s = 0; s < n_steps; ++s) {
+                CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+                ctx->launches += 1;
+            }
+            return HCAO_OK;
+        }
+        for (int s = 0; s < n_steps; ++s) {
+            std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+            if (ctx->prof_on) {
+                auto& pool = ctx->prof_ev[5];
+                if (ctx->prof_used[5] == pool.size()) {
+                    cudaEvent_t e0, e1;
+                    CU(cudaEventCreate(&e0));
+                    CU(cudaEventCreate(&e1));
+                    pool.emplace_back(e0, e1);
+                }
+                ev = &pool[ctx->prof_used[5]++];
+                CU(cudaEventRecord(ev->first, ctx->stream));
+            }
+            launch_fused(a, smem_recs, ctx->stream);
+            ctx->launches += 1;
+            if (ev) CU(cudaEventRecord(ev->second, ctx->stream));
+        }
+        CU(cudaGetLastError());
+        return HCAO_OK;
+    }
     if (!ctx->prof_on && ctx->use_graph) {
         // one step as a CUDA graph, launched n_steps times on the caller's stream
         if (!ctx->graph || std::memcmp(&a, &ctx->graph_args, sizeof a) != 0) {
@@ -1587,6 +1678,20 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
         }
     }
     CU(cudaGetLastError());
+    return HCAO_OK;
+}
+
+hcao_status hcao_set_step_path(hcao_ctx* ctx, int path) {
+    DeviceScope ds_(ctx);
+    if (!ctx || path < HCAO_PATH_AUTO || path > HCAO_PATH_FUSED) return fail(ctx, HCAO_EINVAL, "set_step_path: bad path");
+    SERVE_GUARD(ctx);
+    ctx->step_path = path;
+    return HCAO_OK;
+}
+
+hcao_status hcao_get_step_path(const hcao_ctx* ctx, int* path) {
+    if (!ctx || !path) return HCAO_EINVAL;
+    *path = use_fused(ctx, nullptr) ? HCAO_PATH_FUSED : HCAO_PATH_QUEUE;
     return HCAO_OK;
 }
 
@@ -1714,27 +1819,26 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
     }
     off[r->n_cells] = n;
     if (n == 0) return map_err(ctx);
-    double* dv = nullptr;
-    uint8_t* dq = nullptr;
-    int32_t *ds = nullptr, *dc = nullptr;
-    uint64_t* doff = nullptr;
-    CU(dalloc(ctx, &dv, (size_t)n * 3));
-    CU(dalloc(ctx, &dq, (size_t)n * 16));
-    CU(dalloc(ctx, &ds, (size_t)n));
-    CU(dalloc(ctx, &dc, (size_t)n));
-    CU(dalloc(ctx, &doff, (size_t)r->n_cells + 1));
-    CU(cudaMemcpyAsync(doff, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
+    DevTemp<double> dv(ctx);
+    DevTemp<uint8_t> dq(ctx);
+    DevTemp<int32_t> ds(ctx), dc(ctx);
+    DevTemp<uint64_t> doff(ctx);
+    CU(dalloc(ctx, &dv.p, (size_t)n * 3));
+    CU(dalloc(ctx, &dq.p, (size_t)n * 16));
+    CU(dalloc(ctx, &ds.p, (size_t)n));
+    CU(dalloc(ctx, &dc.p, (size_t)n));
+    CU(dalloc(ctx, &doff.p, (size_t)r->n_cells + 1));
+    CU(cudaMemcpyAsync(doff.p, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff, n, dv, dq, ds, dc, ctx->stream);
+        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, dv.p, dq.p, ds.p, dc.p, ctx->stream);
     else
-        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff, n, dv, dq, ds, dc, ctx->stream);
+        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, dv.p, dq.p, ds.p, dc.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
-    if (v) CU(cudaMemcpyAsync(v, dv, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
-    if (qn) CU(cudaMemcpyAsync(qn, dq, (size_t)16 * n, cudaMemcpyDeviceToHost, ctx->stream));
-    if (species) CU(cudaMemcpyAsync(species, ds, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    if (cell) CU(cudaMemcpyAsync(cell, dc, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dc); dfree(ctx, doff);
+    if (v) CU(cudaMemcpyAsync(v, dv.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (qn) CU(cudaMemcpyAsync(qn, dq.p, (size_t)16 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (species) CU(cudaMemcpyAsync(species, ds.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cell) CU(cudaMemcpyAsync(cell, dc.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return map_err(ctx);
 }
@@ -1745,32 +1849,29 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     if (!ctx || !out) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_moments: no loaded reservoir");
-    double* dacc = nullptr;
-    unsigned long long* dcnt = nullptr;
-    CU(dalloc(ctx, &dacc, 5 + MAXS));
-    CU(dalloc(ctx, &dcnt, MAXS));
-    CU(cudaMemsetAsync(dacc, 0, sizeof(double) * (5 + MAXS), ctx->stream));
-    CU(cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
-    uint64_t* dpo = nullptr;
+    DevTemp<double> dacc(ctx);
+    DevTemp<unsigned long long> dcnt(ctx);
+    DevTemp<uint64_t> dpo(ctx);
+    CU(dalloc(ctx, &dacc.p, 5 + MAXS));
+    CU(dalloc(ctx, &dcnt.p, MAXS));
+    CU(cudaMemsetAsync(dacc.p, 0, sizeof(double) * (5 + MAXS), ctx->stream));
+    CU(cudaMemsetAsync(dcnt.p, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
     uint64_t total = 0;
-    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
     if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_consts, ctx->d_lev64, dacc,
-                               dcnt, ctx->stream);
+        launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, ctx->d_lev64,
+                               dacc.p, dcnt.p, ctx->stream);
     else
-        launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, ctx->d_consts, ctx->d_lev64, dacc,
-                              dcnt, ctx->stream);
+        launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, ctx->d_lev64,
+                              dacc.p, dcnt.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     double acc[5 + MAXS];
     unsigned long long cnt[MAXS];
-    CU(cudaMemcpyAsync(acc, dacc, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(cnt, dcnt, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(acc, dacc.p, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(cnt, dcnt.p, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    dfree(ctx, dacc);
-    dfree(ctx, dcnt);
-    dfree(ctx, dpo);
     std::memset(out, 0, sizeof *out);
     double M = 0.0;
     int64_t N = 0;
@@ -1801,24 +1902,22 @@ hcao_status hcao_read_level_populations(hcao_ctx* ctx, int id, int sp, int mode,
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_level_populations: no loaded reservoir");
     if (sp < 0 || sp >= ctx->n_species || mode < 0 || mode >= ctx->sp[sp].n_modes)
         return fail(ctx, HCAO_EINVAL, "read_level_populations: bad species or mode");
-    unsigned long long* dh = nullptr;
-    CU(dalloc(ctx, &dh, MAXL));
-    CU(cudaMemsetAsync(dh, 0, sizeof(unsigned long long) * MAXL, ctx->stream));
-    uint64_t* dpo = nullptr;
+    DevTemp<unsigned long long> dh(ctx);
+    DevTemp<uint64_t> dpo(ctx);
+    CU(dalloc(ctx, &dh.p, MAXL));
+    CU(cudaMemsetAsync(dh.p, 0, sizeof(unsigned long long) * MAXL, ctx->stream));
     uint64_t total = 0;
-    hcao_status pst = particle_prefix(ctx, *r, &dpo, &total);
+    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
     if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_levelpop<double>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, sp, mode, dh, ctx->stream);
+        launch_levelpop<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, sp, mode, dh.p, ctx->stream);
     else
-        launch_levelpop<float>(ctx->d_cells, r->cell0, r->n_cells, dpo, total, sp, mode, dh, ctx->stream);
+        launch_levelpop<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, sp, mode, dh.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     unsigned long long h[MAXL];
-    CU(cudaMemcpyAsync(h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(h, dh.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    dfree(ctx, dh);
-    dfree(ctx, dpo);
     for (int i = 0; i < max_levels; ++i) counts[i] = i < MAXL ? (uint64_t)h[i] : 0;
     return map_err(ctx);
 }

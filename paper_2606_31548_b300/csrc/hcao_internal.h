@@ -31,7 +31,7 @@ inline int setup_tiles(int n_cells) { return n_cells <= SETUP_TILE ? 1 : (n_cell
 inline int setup_launches(int n_cells) { return setup_tiles(n_cells) == 1 ? 1 : 2; }
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
-enum { PU_NSEL = 1, PU_FEISTEL = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
+enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
        PU_INIT = 7, PU_REC = 9 };
 
 // per-reservoir counters
@@ -135,7 +135,7 @@ struct DevCell {
     uint32_t nsel, ncreated;
     float sgmax_f;                    // FP32 copy of sgmax for the step
     uint32_t nremoved;                // particles removed this step (recombination)
-    uint32_t fkey[MAX_ROUNDS][4];     // Feistel keys per round of this step
+    uint32_t pkey[MAX_ROUNDS][4];     // pairing-permutation keys per round of this step
 };
 
 struct DevRes {
@@ -188,7 +188,17 @@ struct StepArgs {
     uint32_t* err;
     int max_rounds;
     uint32_t reject_cap;
+    uint32_t* ticket;               // fused step: CTAs finished (the last one advances the reservoirs)
+    int fused_recs;                 // fused step: records staged per CTA (0 on the queue path)
 };
+
+// The FP32 step as one kernel per step, one CTA per cell with its records in
+// shared memory (hcao_fused.cuh, built in hcao_f32.cu).  It serves contexts
+// whose reactions neither create nor remove particles and whose cells all
+// hold at most FUSED_MAX_RECS particle slots.
+constexpr int FUSED_MAX_RECS = 4096;
+void launch_fused(const StepArgs& a, int smem_recs, cudaStream_t s);
+cudaError_t fused_prepare(int smem_recs);  // the kernel's dynamic shared-memory limit
 
 // launchers, one instantiation per precision (hcao_f64.cu / hcao_f32.cu)
 template <class R> struct RecOf;

@@ -3,12 +3,12 @@
 // One step of the DSMC collision phase, per reservoir cell:
 //   k_setup_cells  one thread per cell, CTAs of SETUP_TILE cells: NTC candidate
 //                  count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c with
-//                  stochastic rounding, Feistel keys per pairing round, tile
+//                  stochastic rounding, pairing-permutation keys per round, tile
 //                  scans of the per-cell counts; the last CTA scans the tiles.
 //   k_setup_fix    adds the tile offsets (flat pair index of every candidate).
 //   k_cellstats    (recombination only) per-cell sums for the cell temperature.
 //   per pairing round:
-//   k_select       one thread per candidate pair: Feistel pair draw, VHS
+//   k_select       one thread per candidate pair: permuted pair draw, VHS
 //                  acceptance; FP32 mode queues accepted pairs in three regions
 //                  by the number of molecules to relax.
 //   k_relax_fast   (FP32) one thread per accepted pair: recombination and QK
@@ -138,26 +138,27 @@ template <class R> __device__ __forceinline__ R st_uni(Stream& s);
 template <> __device__ __forceinline__ double st_uni<double>(Stream& s) { return st_u64(s); }
 template <> __device__ __forceinline__ float st_uni<float>(Stream& s) { return st_u32(s); }
 
-// ------------------------------------------------------------- Feistel pairing
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-    h ^= h >> 16; h *= 0x85EBCA6Bu; h ^= h >> 13; h *= 0xC2B2AE35u; h ^= h >> 16;
-    return h;
-}
-// keyed bijection of [0,N): 4-round balanced Feistel on the smallest even bit
-// width covering N, cycle-walked into range
-__device__ __forceinline__ uint32_t feistel(uint32_t x, uint32_t N, const uint32_t key[4]) {
-    int b = 2;
-    while (((uint64_t)1 << b) < (uint64_t)N) b += 2;
-    int half = b >> 1;
-    uint32_t mask = (uint32_t)(((uint64_t)1 << half) - 1);
+// ------------------------------------------------------------- pairing permutation
+// Keyed bijection of [0,N) that forms the disjoint NTC pairs of a round (pair k
+// = (pi(2k), pi(2k+1))).  On b-bit words, b the smallest width with 2^b >= N,
+// three rounds of x = ((x ^ k_r) * M_r) mod 2^b, x ^= x >> ceil(b/2) -- each
+// step a bijection of [0, 2^b) -- repeated from the result until it lands in
+// [0,N) (at most 2 evaluations on average).  Round keys: the round's key
+// words 0..2; multipliers: the odd constants 0x9E3779B1, 0x85EBCA6B,
+// 0xC2B2AE35.
+__device__ __forceinline__ uint32_t pair_perm(uint32_t x, uint32_t N, const uint32_t key[4]) {
+    if (N <= 1u) return 0u;
+    const int b = 32 - __clz(N - 1u);  // smallest b with 2^b >= N
+    const uint32_t mask = (uint32_t)(((uint64_t)1 << b) - 1u);
+    const int h = (b + 1) >> 1;
+    const uint32_t k0 = key[0] & mask, k1 = key[1] & mask, k2 = key[2] & mask;
     for (int walk = 0; walk < (1 << 20); ++walk) {
-        uint32_t L = x >> half, Rr = x & mask;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            uint32_t nR = L ^ (fmix32(Rr ^ key[r]) & mask);
-            L = Rr; Rr = nR;
-        }
-        x = (L << half) | Rr;
+        x = ((x ^ k0) * 0x9E3779B1u) & mask;
+        x ^= x >> h;
+        x = ((x ^ k1) * 0x85EBCA6Bu) & mask;
+        x ^= x >> h;
+        x = ((x ^ k2) * 0xC2B2AE35u) & mask;
+        x ^= x >> h;
         if (x < N) return x;
     }
     return 0;  // unreachable: a cycle through x < N returns to [0,N)
@@ -379,7 +380,11 @@ __device__ __forceinline__ void iso_dir(Stream& st, R d[3]) {
     for (int it = 0; it < 4096; ++it) {
         R x1 = (R)2 * st_uni<R>(st) - (R)1;
         R x2 = (R)2 * st_uni<R>(st) - (R)1;
-        R s = x1 * x1 + x2 * x2;
+        R s;
+        if constexpr (std::is_same<R, float>::value)
+            s = __fadd_rn(__fmul_rn(x1, x1), __fmul_rn(x2, x2));  // no contraction: same bits in every kernel
+        else
+            s = x1 * x1 + x2 * x2;
         if (s < (R)1) {
             const R om = (R)1 - s;
             R r;
@@ -600,7 +605,7 @@ __device__ __forceinline__ uint32_t round_pairs(uint32_t N, int has_recomb) {
     return (has_recomb && N >= 3u) ? N / 3u : N >> 1;
 }
 
-// Where pair k of round r of cell c lives: its Feistel members, its event slot.
+// Where pair k of round r of cell c lives: its permuted members, its event slot.
 struct PairLoc {
     uint32_t N, lcell, rk, ev_idx, ip, iq;
     void* recs;
@@ -613,15 +618,15 @@ __device__ __forceinline__ PairLoc locate(const StepArgs& A, int c, int r, uint3
     L.lcell = cell.lcell;
     L.rk = ((uint32_t)r << 24) | k;
     L.ev_idx = A.abase[c] + (uint32_t)r * round_pairs(L.N, A.has_recomb) + k;
-    const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
-    L.ip = feistel(2u * k, L.N, key);
-    L.iq = feistel(2u * k + 1u, L.N, key);
+    const uint32_t key[4] = {cell.pkey[r][0], cell.pkey[r][1], cell.pkey[r][2], cell.pkey[r][3]};
+    L.ip = pair_perm(2u * k, L.N, key);
+    L.iq = pair_perm(2u * k + 1u, L.N, key);
     L.recs = cell.rec;
     L.sgmax = cell.sgmax;
     return L;
 }
 
-// the same as locate() with the Feistel members already known
+// the same as locate() with the members already known
 __device__ __forceinline__ PairLoc locate_known(const StepArgs& A, int c, int r, uint32_t k, uint32_t ip,
                                                 uint32_t iq) {
     const DevCell& cell = A.cells[c];
@@ -635,6 +640,43 @@ __device__ __forceinline__ PairLoc locate_known(const StepArgs& A, int c, int r,
     L.recs = cell.rec;
     L.sgmax = cell.sgmax;
     return L;
+}
+
+// NTC set-up of one cell for this step: N_sel = 1/2 N (N-1) w (sigma g)_max
+// dt / V_c, rounded stochastically (stream PU_NSEL), the number of pairing
+// rounds of P pairs each, and each round's pairing-permutation key (stream PU_PERM).
+// The FP64 product is written with explicit roundings so that every kernel
+// computing it (compiled with or without FMA contraction) gets the same N_sel.
+// More rounds than max_rounds, or a non-finite (sigma g)_max, leave the cell
+// without pairs and set the error word.
+__device__ __forceinline__ uint32_t ntc_setup(const StepArgs& A, const DevRes& rs, const DevCell& cl, uint32_t N,
+                                              uint32_t P, uint32_t& rounds, uint32_t (*pkey)[4]) {
+    rounds = 0;
+    if (!rs.active || N < 2) return 0u;
+    const double x = __ddiv_rn(
+        __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(0.5, (double)N), (double)(N - 1)), rs.w), cl.sgmax), rs.dt),
+        rs.Vc);
+    long long ns = 0, rr = 0;
+    if (x >= 0.0 && x < 4.0e9) {
+        const double fl = floor(x);
+        ns = (long long)fl;
+        Stream st;
+        st_init(st, rs.seed, rs.step, cl.lcell, 0u, PU_NSEL);
+        if (st_u64(st) < x - fl) ns++;
+        rr = (ns + P - 1) / P;
+        if (rr > A.max_rounds) { atomicOr(A.err, (uint32_t)ERR_ROUNDS); ns = 0; rr = 0; }
+    } else {  // a non-finite or absurd (sigma g)_max: no pairs, report
+        atomicOr(A.err, (uint32_t)ERR_NONFINITE);
+    }
+    for (uint32_t r = 0; r < (uint32_t)rr; ++r) {
+        Stream sf;
+        st_init(sf, rs.seed, rs.step, cl.lcell, r << 24, PU_PERM);
+        st_block(sf);
+        pkey[r][0] = sf.w0; pkey[r][1] = sf.w1;
+        pkey[r][2] = sf.w2; pkey[r][3] = sf.w3;
+    }
+    rounds = (uint32_t)rr;
+    return (uint32_t)ns;
 }
 
 // channel id: reaction (3 bits) | side << 3 | broken stretch << 4
@@ -738,6 +780,37 @@ __device__ __forceinline__ void pair_energy(const DevPair& pc, int amode, const 
         const float g = sqrtf(g2);
         const float gp = amode == 0 ? sqrtf(g) : (amode == 1 ? g : 1.0f);
         sg = (double)(pc.C_f * gp);
+    }
+}
+
+// FP32 pair kinematics with each operation's rounding written out, so that
+// every kernel evaluating them -- the per-round queue kernels and the fused
+// per-cell kernel -- gets the same bits whatever the compiler would contract.
+// Squared relative speed of velocities a and b.
+__device__ __forceinline__ float g2_f32(const float a[3], const float b[3]) {
+    const float gx = __fsub_rn(a[0], b[0]), gy = __fsub_rn(a[1], b[1]), gz = __fsub_rn(a[2], b[2]);
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+// VHS sigma_T g of a pair at squared relative speed g2 (g^(2-2 omega))
+__device__ __forceinline__ float sg_f32(const DevPair& pc, int amode, float g2) {
+    const float gr = __fsqrt_rn(g2);
+    return __fmul_rn(pc.C_f, amode == 0 ? __fsqrt_rn(gr) : (amode == 1 ? gr : 1.0f));
+}
+// relative translational energy 1/2 m_r g^2 in fixed point
+__device__ __forceinline__ long long etr_fix_f32(const DevPair& pc, float g2) {
+    return f2fix(__fmul_rn(__fmul_rn(0.5f, pc.mr_f), g2));
+}
+// isotropic scattering with the centre-of-mass velocity kept: relative speed
+// from the relative energy Erel, direction d
+__device__ __forceinline__ void scatter_f32(const DevPair& pc, long long Erel, const float d[3],
+                                            const float va[3], const float vb[3], float na[3], float nb[3]) {
+    const float gn = __fsqrt_rn(__fmul_rn(fix2f(Erel), pc.inv2mr_f));
+#pragma unroll
+    for (int c3 = 0; c3 < 3; ++c3) {
+        const float V = __fadd_rn(__fmul_rn(pc.fq_f, va[c3]), __fmul_rn(pc.fp_f, vb[c3]));
+        const float G = __fmul_rn(gn, d[c3]);
+        na[c3] = __fadd_rn(V, __fmul_rn(pc.fp_f, G));
+        nb[c3] = __fsub_rn(V, __fmul_rn(pc.fq_f, G));
     }
 }
 
@@ -1053,13 +1126,9 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     const DevSpecies& sD = C->sp[rx.P1];
     const float mA = sA.mass_f, mB = sB.mass_f, mC = sC.mass_f, mD = sD.mass_f;
     const float mAB = mA + mB, mt = mC + mD;
-    float V[3], g[3];
-    for (int i = 0; i < 3; ++i) {
-        V[i] = (mA * vA[i] + mB * vB[i]) / mAB;
-        g[i] = vA[i] - vB[i];
-    }
-    const float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const long long Ein = f2fix(0.5f * C->pair[spA * MAXS + spB].mr_f * g2);
+    float V[3];
+    for (int i = 0; i < 3; ++i) V[i] = __fdiv_rn(__fadd_rn(__fmul_rn(mA, vA[i]), __fmul_rn(mB, vB[i])), mAB);
+    const long long Ein = etr_fix_f32(C->pair[spA * MAXS + spB], g2_f32(vA, vB));
     const long long Eav = Ein + EvA + EvB - rx.dEf_fix;
     if (!(Eav - sC.zpe_fix - sD.zpe_fix > 0) || Eav - sD.zpe_fix > sC.top_fix ||
         Eav - sC.zpe_fix > sD.top_fix)
@@ -1072,14 +1141,14 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     long long Etr = relax_flat(A, C, rx.P0, qC, sC.zpe_fix, sa, rx.P1, qD, sD.zpe_fix, sb,
                                Eav - sC.zpe_fix - sD.zpe_fix, o);
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
-    const float gn = sqrtf(2.0f * fix2f(Etr) / C->pair[rx.P0 * MAXS + rx.P1].mr_f);
+    const float gn = __fsqrt_rn(__fdiv_rn(__fmul_rn(2.0f, fix2f(Etr)), C->pair[rx.P0 * MAXS + rx.P1].mr_f));
     float d[3];
     iso_dir<float>(ss, d);
-    const float fC = mD / mt, fD = mC / mt;
+    const float fC = __fdiv_rn(mD, mt), fD = __fdiv_rn(mC, mt);
     for (int i = 0; i < 3; ++i) {
-        const float G = gn * d[i];
-        vA[i] = V[i] + fC * G;
-        vB[i] = V[i] - fD * G;
+        const float G = __fmul_rn(gn, d[i]);
+        vA[i] = __fadd_rn(V[i], __fmul_rn(fC, G));
+        vB[i] = __fsub_rn(V[i], __fmul_rn(fD, G));
     }
     return true;
 }
@@ -1175,8 +1244,8 @@ __device__ bool recomb_test(const StepArgs& A, const Consts* __restrict__ C, int
     const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
     const uint64_t m = 2ull * (uint64_t)(__ldg(pb + c + 1) - __ldg(pb + c)) + k;
     if (m >= N) return false;
-    const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
-    iM = feistel((uint32_t)m, N, key);
+    const uint32_t key[4] = {cell.pkey[r][0], cell.pkey[r][1], cell.pkey[r][2], cell.pkey[r][3]};
+    iM = pair_perm((uint32_t)m, N, key);
     const Rec* recs = reinterpret_cast<const Rec*>(cell.rec);
     const uint32_t meta = reinterpret_cast<const uint32_t*>(recs + iM)[std::is_same<R, double>::value ? 6 : 3];
     const int sM = (int)(meta & 0xFFu);
@@ -1299,16 +1368,10 @@ __device__ __forceinline__ void relax_scatter_fix(const StepArgs& A, const Const
     const long long E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
     Stream ss;
     st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
-    const float gn = sqrtf(fix2f(E) * pc.inv2mr_f);
     float d[3];
     iso_dir<float>(ss, d);
-    float V[3];
-    for (int i = 0; i < 3; ++i) V[i] = pc.fq_f * Pr.v[i] + pc.fp_f * Qr.v[i];
-    for (int i = 0; i < 3; ++i) {
-        const float G = gn * d[i];
-        Pr.v[i] = V[i] + pc.fp_f * G;
-        Qr.v[i] = V[i] - pc.fq_f * G;
-    }
+    const float va[3] = {Pr.v[0], Pr.v[1], Pr.v[2]}, vb[3] = {Qr.v[0], Qr.v[1], Qr.v[2]};
+    scatter_f32(pc, E, d, va, vb, Pr.v, Qr.v);
 }
 
 __device__ __forceinline__ uint32_t ev_final(const PairOut& o) {
@@ -1343,7 +1406,7 @@ __device__ __forceinline__ int cell_of(const uint32_t* pb, int n_cells, uint32_t
 
 // Per-cell step set-up, one thread per cell, SETUP_TILE cells per CTA: the
 // NTC candidate count N_sel (stochastically rounded), the rounds and their
-// Feistel keys, and the counts behind the step's prefix arrays -- pairs per
+// pairing-permutation keys, and the counts behind the step's prefix arrays -- pairs per
 // round, all pairs, FINISH_CHUNK chunks and (with recombination) particles.
 // Each CTA writes the inclusive scans of its tile into the arrays and the
 // tile's totals into tsum; the last CTA to finish (a ticket counter, no
@@ -1358,32 +1421,9 @@ static __global__ void __launch_bounds__(SETUP_TILE) k_setup_cells(StepArgs A) {
         DevCell& cl = A.cells[c];
         const DevRes rs = A.res[cl.res];
         const uint32_t N = cl.n;
-        uint32_t nsel = 0, rounds = 0, P = round_pairs(N, A.has_recomb);
-        if (rs.active && N >= 2) {
-            // NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically
-            const double x = 0.5 * (double)N * (double)(N - 1) * rs.w * cl.sgmax * rs.dt / rs.Vc;
-            long long ns = 0, rr = 0;
-            if (x >= 0.0 && x < 4.0e9) {
-                const double fl = floor(x);
-                ns = (long long)fl;
-                Stream st;
-                st_init(st, rs.seed, rs.step, cl.lcell, 0u, PU_NSEL);
-                if (st_u64(st) < x - fl) ns++;
-                rr = (ns + P - 1) / P;
-                if (rr > R) { atomicOr(A.err, (uint32_t)ERR_ROUNDS); ns = 0; rr = 0; }
-            } else {  // a non-finite or absurd (sigma g)_max: no pairs, report
-                atomicOr(A.err, (uint32_t)ERR_NONFINITE);
-            }
-            nsel = (uint32_t)ns;
-            rounds = (uint32_t)rr;
-            for (uint32_t r = 0; r < rounds; ++r) {
-                Stream sf;
-                st_init(sf, rs.seed, rs.step, cl.lcell, r << 24, PU_FEISTEL);
-                st_block(sf);
-                cl.fkey[r][0] = sf.w0; cl.fkey[r][1] = sf.w1;
-                cl.fkey[r][2] = sf.w2; cl.fkey[r][3] = sf.w3;
-            }
-        }
+        uint32_t rounds = 0;
+        const uint32_t P = round_pairs(N, A.has_recomb);
+        const uint32_t nsel = ntc_setup(A, rs, cl, N, P, rounds, cl.pkey);
         cl.nsel = nsel;
         cl.ncreated = 0;
         cl.seen = 0ull;
@@ -1577,9 +1617,9 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 const DevCell& cell = A.cells[c];
                 const uint32_t N = cell.n;
                 const uint32_t rk = ((uint32_t)r << 24) | k;
-                const uint32_t key[4] = {cell.fkey[r][0], cell.fkey[r][1], cell.fkey[r][2], cell.fkey[r][3]};
-                ip = feistel(2u * k, N, key);
-                iq = feistel(2u * k + 1u, N, key);
+                const uint32_t key[4] = {cell.pkey[r][0], cell.pkey[r][1], cell.pkey[r][2], cell.pkey[r][3]};
+                ip = pair_perm(2u * k, N, key);
+                iq = pair_perm(2u * k + 1u, N, key);
                 const uint4* recs = reinterpret_cast<const uint4*>(cell.rec);
                 const uint4 a = recs[2 * ip], b = recs[2 * iq];
                 const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
@@ -1587,20 +1627,16 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 const uint32_t ev_idx = A.abase[c] + (uint32_t)r * round_pairs(N, A.has_recomb) + k;
                 // a member removed earlier in this step (recombination): no collision
                 if (sP < MAXS && sQ < MAXS) {
-                const float gx = __uint_as_float(a.x) - __uint_as_float(b.x);
-                const float gy = __uint_as_float(a.y) - __uint_as_float(b.y);
-                const float gz = __uint_as_float(a.z) - __uint_as_float(b.z);
-                const float g2 = gx * gx + gy * gy + gz * gz;
-                const DevPair& pc = C->pair[sP * MAXS + sQ];
-                const float gr = sqrtf(g2);
-                sgf = pc.C_f * (amode == 0 ? sqrtf(gr) : (amode == 1 ? gr : 1.0f));
+                const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+                const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
+                sgf = sg_f32(C->pair[sP * MAXS + sQ], amode, g2_f32(va, vb));
                 if (!(sgf <= 3.0e38f)) {
                     atomicOr(A.err, (uint32_t)ERR_NONFINITE);
                     sgf = 0.f;
                 }
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
-                accept = st_u32(sp) < sgf / cell.sgmax_f;
+                accept = st_u32(sp) < __fdiv_rn(sgf, cell.sgmax_f);
                 nm = (int)(C->sp[sP].n_modes > 0) + (int)(C->sp[sQ].n_modes > 0);
                 }
                 if (!accept) {
@@ -1764,8 +1800,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
         const DevPair& pc = C->pair[sP * MAXS + sQ];
         if constexpr (!std::is_same<R, double>::value) {
             // FP32 mode: fixed-point energies, no FP64 arithmetic
-            const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-            const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+            const long long Etr = etr_fix_f32(pc, g2_f32(Pr.v, Qr.v));
             const long long EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
             const long long EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
             if (C->n_reactions > 0) {
@@ -1857,8 +1892,8 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
         const DevPair& pc = C->pair[sP * MAXS + sQ];
         const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
         const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
-        const float gx = va[0] - vb[0], gy = va[1] - vb[1], gz = va[2] - vb[2];
-        const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+        const float g2 = g2_f32(va, vb);
+        const long long Etr = etr_fix_f32(pc, g2);
         uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
         const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
         const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
@@ -1867,8 +1902,7 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
         bool react = false;
         uint32_t chan = 0u, mpos = 0u;
         if (C->n_reactions > 0) {
-            const float gr = sqrtf(gx * gx + gy * gy + gz * gz);
-            const float sgf = pc.C_f * (C->amode == 0 ? sqrtf(gr) : (C->amode == 1 ? gr : 1.0f));
+            const float sgf = sg_f32(pc, C->amode, g2);
             if (C->has_recomb && recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sgf, chan, mpos)) {
                 react = true;
             } else {
@@ -1912,16 +1946,10 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
         w_pair++;
         Stream ss;
         st_init(ss, rs.seed, step, lcell, rk, PU_SCAT);
-        const float gn = sqrtf(fix2f(Erel) * pc.inv2mr_f);
         float d[3];
         iso_dir<float>(ss, d);
         float na[3], nb[3];
-        for (int c3 = 0; c3 < 3; ++c3) {
-            const float V = pc.fq_f * va[c3] + pc.fp_f * vb[c3];
-            const float G = gn * d[c3];
-            na[c3] = V + pc.fp_f * G;
-            nb[c3] = V - pc.fq_f * G;
-        }
+        scatter_f32(pc, Erel, d, va, vb, na, nb);
         recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
         recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
         recs[2 * ip + 1] = make_uint4(qP[0], qP[1], qP[2], qP[3]);
@@ -1969,8 +1997,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
         const DevPair& pc = C->pair[sP * MAXS + sQ];
         const int rxi = (int)(e.z & 7u), side = (int)((e.z >> 3) & 1u), mode = (int)(e.z >> 4);
         if constexpr (!std::is_same<R, double>::value) {
-            const float gx = Pr.v[0] - Qr.v[0], gy = Pr.v[1] - Qr.v[1], gz = Pr.v[2] - Qr.v[2];
-            const long long Etr = f2fix(0.5f * pc.mr_f * (gx * gx + gy * gy + gz * gz));
+            const long long Etr = etr_fix_f32(pc, g2_f32(Pr.v, Qr.v));
             const long long EvP = evib_fix(A.levfix, C->sp[sP], Pr.q);
             const long long EvQ = evib_fix(A.levfix, C->sp[sQ], Qr.q);
             const DevReaction& rx = C->rx[rxi];

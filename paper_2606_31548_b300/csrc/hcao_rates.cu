@@ -184,8 +184,9 @@ double thermal_diss_prob(const std::vector<std::vector<double>>& lev, double D, 
 // Whitten-Rabinovitch: l oscillators, quanta hnu, E above the ground state.
 // With x = E/E_z (E_z = half the sum of the quanta), the correction
 // a(x) = 1 - beta w(x), w = 10^(-1.0506 x^(1/4)) for x >= 1 and
-// w = 1/(5 x + 2.73 sqrt(x) + 3.51) below, beta = (l-1)^2 <nu^2> / (l <nu>^2)
-// written with sums: (l-1)^2 S2 / (l S1^2).  The density is
+// w = 1/(5 x + 2.73 sqrt(x) + 3.51) below, and the WR beta of the paper,
+// (l-1)^2 S2 / (l S1^2) with S1 the sum of the quanta and S2 the sum of their
+// squares.  The density is
 // (E + a E_z)^(l-1) / ((l-1)! prod hnu); computed through its logarithm.
 static bool wr_setup(const double* hnu, int l, double& Ez, double& beta, double& lden) {
     if (!hnu || l < 1) return false;

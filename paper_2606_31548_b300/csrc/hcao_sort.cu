@@ -197,25 +197,17 @@ constexpr int64_t kNoAllocTiles = (HCAO_NOALLOC_SORT_MAX_KEYS + hcao::SORT_TILE 
 constexpr int64_t kNoAllocWords = 4 * (int64_t)HCAO_NOALLOC_SORT_MAX_KEYS + 256 * kNoAllocTiles;
 __device__ __align__(256) uint32_t g_noalloc_sort_scratch[kNoAllocWords];
 
-// Host-side device addresses of the array, one per device, looked up once with
-// that device current (in host code the array's name is only a stand-in).
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-uint32_t* g_noalloc_ptr[kMaxDevices] = {};
-
+// The array's device address on the current device.  In host code the
+// array's name is only a stand-in, so the address is looked up on every call,
+// with the calling thread's device current: a cached address would outlive a
+// cudaDeviceReset or a re-created primary context, which load the module (and
+// the array) again, possibly elsewhere.  The lookup is a host-side query, not
+// a stream operation.
 cudaError_t noalloc_scratch(uint32_t** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_sort_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_sort_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<uint32_t*>(p);
     return cudaSuccess;
 }
 }  // namespace

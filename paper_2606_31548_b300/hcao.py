@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhcao.so")
 
 FP64, FP32 = 0, 1
+PATH_AUTO, PATH_QUEUE, PATH_FUSED = 0, 1, 2
 DISS, EXCH, RECOMB = 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
           -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND",
@@ -32,6 +33,7 @@ EXPORTS = [
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
     "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
+    "hcao_set_step_path", "hcao_get_step_path",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -145,6 +147,8 @@ def lib() -> C.CDLL:
         L.hcao_serve_stop.argtypes = [vp]
         L.hcao_serve_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(u64)]
         L.hcao_recomb_rate.argtypes = [vp, i32, i32, dbl, C.POINTER(dbl)]
+        L.hcao_set_step_path.argtypes = [vp, i32]
+        L.hcao_get_step_path.argtypes = [vp, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
         L.hcao_kernel_launches.restype = u64
         _lib = L
@@ -352,15 +356,26 @@ class Context:
     def set_profiling(self, on=True) -> None:
         self._chk(self.L.hcao_set_profiling(self.h, 1 if on else 0))
 
-    PROFILE_KERNELS = ("setup", "select", "relax", "react", "finish")
+    PROFILE_KERNELS = ("setup", "select", "relax", "react", "finish", "fused")
 
     def read_profile(self):
-        """(ms, launches) per kernel: setup, select, relax, react, finish."""
-        ms = np.zeros(5)
-        n = np.zeros(5, np.uint64)
+        """(ms, launches) per kernel class: setup, select, relax, react, finish
+        (the queue path) and the fused per-cell kernel."""
+        ms = np.zeros(6)
+        n = np.zeros(6, np.uint64)
         got = C.c_int()
-        self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 5, C.byref(got)))
+        self._chk(self.L.hcao_read_profile(self.h, _p(ms), _p(n), 6, C.byref(got)))
         return ms, n
+
+    def set_step_path(self, path: int) -> None:
+        """PATH_AUTO (default), PATH_QUEUE or PATH_FUSED."""
+        self._chk(self.L.hcao_set_step_path(self.h, path))
+
+    def step_path(self) -> int:
+        """The collision-phase path the next step takes: PATH_QUEUE or PATH_FUSED."""
+        p = C.c_int()
+        self._chk(self.L.hcao_get_step_path(self.h, C.byref(p)))
+        return p.value
 
     def autotune(self, steps_per_candidate=1):
         """Pick launch shapes by timing candidates on live steps; returns (select grid, relax grid)."""

@@ -23,9 +23,11 @@ def test_reference_arm_json_line():
     assert d["metric"] == "particle-steps/s" and d["unit"] == "particle-steps/s"
     assert d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 0
-    assert d["config"]["workload"] == "ch4_heat_bath_4096x500_15000K_dissociation"
+    assert d["config"]["workload"] == "ch4_h_exchange_16384x1200_4000K"
+    assert d["config"]["cells"] == 16384 and d["config"]["particles_per_cell"] == 1200
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host_cores"] == os.cpu_count()
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

@@ -149,7 +149,7 @@ def test_parity_triatomic_multicell():
 
 def test_parity_triatomic_single_cell_20000():
     """The full 20,000-particle single-cell relaxation reservoir (large cell:
-    pairs gathered through the Feistel permutation across many CTAs)."""
+    pairs gathered through the pairing permutation across many CTAs)."""
     g, o = _run_parity(W.relaxation_triatomic(), 25, check_each=False)
     assert g.read_counters(0)[1] > 20000
 

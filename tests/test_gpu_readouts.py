@@ -1,0 +1,128 @@
+"""Readouts of the collision phase's bookkeeping (Sec. "Implementation of the
+polyatomic HCAO model": level populations, vibrational energy and the
+zero-point search for T_vib) against the oracle's particles.
+
+FP64 mode steps bit for bit like the oracle, so the GPU's level populations
+must equal counts taken from the oracle's particles exactly, and its moments
+must equal sums over the oracle's particles up to the summation order of the
+device reduction.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_31548_b300 import hcao
+from paper_2606_31548_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _stepped(w, steps, precision=hcao.FP64):
+    g = hcao.from_workload(w, precision=precision)
+    o = oracle.from_workload(w)
+    g.step(steps)
+    g.sync()
+    o.step(steps)
+    return g, o
+
+
+WORKLOADS = {
+    "triatomic": lambda: W.relaxation_triatomic(n_particles=6000, n_cells=3),
+    "ch4_dissociation": lambda: W.ch4_heat_bath(n_cells=12, per_cell=400),
+    "ch4_h_exchange": lambda: W.ch4_h_exchange(n_cells=6, per_cell=800, T0=6000.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_level_populations_equal_oracle_counts(name):
+    w = WORKLOADS[name]()
+    g, o = _stepped(w, 6)
+    _, qo, so, _ = o.read_particles(0)
+    checked = 0
+    for sp, s in enumerate(w.species):
+        for mode in range(s.n_modes):
+            got = g.read_level_populations(0, sp, mode, 256)
+            exp = np.bincount(qo[so == sp, mode].astype(np.int64), minlength=256).astype(np.uint64)
+            assert np.array_equal(got, exp), (s.name, mode)
+            checked += int(exp.sum())
+    assert checked > 0
+    # fewer slots than levels: the first max_levels counts
+    got = g.read_level_populations(0, 0, 0, 3)
+    assert np.array_equal(got, np.bincount(qo[so == 0, 0], minlength=256)[:3].astype(np.uint64))
+
+
+def test_level_populations_fp32_equal_own_particles():
+    w = W.ch4_heat_bath(n_cells=16, per_cell=300)
+    g = hcao.from_workload(w, precision=hcao.FP32)
+    g.step(4)
+    _, q, s, _ = g.read_particles(0)
+    for sp in (0, 1):
+        for mode in range(w.species[sp].n_modes):
+            got = g.read_level_populations(0, sp, mode, 256)
+            exp = np.bincount(q[s == sp, mode].astype(np.int64), minlength=256).astype(np.uint64)
+            assert np.array_equal(got, exp)
+
+
+def test_level_populations_reject_bad_arguments():
+    w = W.relaxation_triatomic(n_particles=100)
+    g = hcao.from_workload(w)
+    for sp, mode in ((1, 0), (0, 3), (-1, 0), (0, -1)):
+        with pytest.raises(hcao.HcaoError):
+            g.read_level_populations(0, sp, mode, 16)
+    with pytest.raises(hcao.HcaoError):
+        g.read_level_populations(7, 0, 0, 16)  # no such reservoir
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_moments_fp64_equal_oracle_sums(name):
+    w = WORKLOADS[name]()
+    g, o = _stepped(w, 6)
+    m = g.read_moments(0)
+    vo, qo, so, _ = o.read_particles(0)
+    mass = np.array([s.mass for s in w.species])[so]
+    n_sp = np.bincount(so, minlength=16)
+    assert list(m.n) == [int(x) for x in n_sp]
+    # momentum: sums near zero, compared against the scale of sum |m v|
+    for d in range(3):
+        exp = math.fsum(mass * vo[:, d])
+        scale = math.fsum(np.abs(mass * vo[:, d]))
+        assert abs(m.momentum[d] - exp) <= 1e-13 * scale, (d, m.momentum[d], exp)
+    e_tr = math.fsum(0.5 * mass * np.sum(vo * vo, axis=1))
+    assert abs(m.E_tr - e_tr) <= 1e-12 * e_tr
+    e_form = math.fsum(np.array([s.E_form for s in w.species])[so])
+    assert abs(m.E_form - e_form) <= 1e-12 * max(abs(e_form), 1e-30)
+    for sp, s in enumerate(w.species):
+        sel = so == sp
+        if s.n_modes == 0 or not sel.any():
+            assert m.E_vib[sp] == 0.0
+            continue
+        lev = [o.levels(sp, j) for j in range(s.n_modes)]
+        ev = np.zeros(int(sel.sum()))
+        for j in range(s.n_modes):
+            ev += lev[j][qo[sel, j]]
+        exp = math.fsum(ev)
+        assert abs(m.E_vib[sp] - exp) <= 1e-12 * exp, (s.name, m.E_vib[sp], exp)
+        # T_vib: the zero-point search on both sides (root of the mean
+        # vibrational energy above the ZPE), bisection to the same tolerance
+        tv_o = o.tvib(0, sp)
+        assert abs(m.T_vib[sp] - tv_o) <= 1e-9 * tv_o, (s.name, m.T_vib[sp], tv_o)
+    # translational temperature from the peculiar kinetic energy
+    M = float(mass.sum())
+    p2 = sum(math.fsum(mass * vo[:, d]) ** 2 for d in range(3))
+    T_tr = 2.0 / 3.0 * (e_tr - 0.5 * p2 / M) / (len(so) * W.KB)
+    assert abs(m.T_tr - T_tr) <= 1e-11 * T_tr
+
+
+def test_tvib_equals_translational_temperature_at_equilibrium():
+    """Equilibrated triatomic reservoir (FP64, GPU alone): T_vib from the
+    zero-point search meets T_tr (Sec. implementation: T_vib is the
+    temperature whose Boltzmann mean vibrational energy equals the measured
+    one)."""
+    w = W.relaxation_triatomic(n_particles=20000, n_cells=1)
+    w.T_vib0 = w.T_tr0 = 8000.0
+    g = hcao.from_workload(w, precision=hcao.FP64)
+    g.step(200)
+    m = g.read_moments(0)
+    assert abs(m.T_vib[0] - m.T_tr) / m.T_tr < 0.03, (m.T_vib[0], m.T_tr)

@@ -136,3 +136,49 @@ def test_serving_rejects_direct_calls_and_reports_failed_jobs():
     ctx.serve_stop()
     ctx.step(1)  # usable again once the engine has stopped
     ctx.close()
+
+
+def _alone_w(sw, w, n_steps, precision, max_rounds):
+    a = hcao.Context(precision=precision, max_rounds=max_rounds)
+    a.set_species(sw.species)
+    a.set_reactions(sw.reactions)
+    rid = a.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    a.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
+    a.init_vibration(rid, w.T_vib0)
+    a.step(n_steps)
+    out = (a.read_counters(rid), a.count(rid), a.read_moments(rid))
+    a.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [hcao.FP64, hcao.FP32])
+def test_served_jobs_with_chemistry_equal_alone(precision):
+    """The served mix of the benchmark's kinds -- triatomic relaxation, CH4
+    heat bath with dissociation, CH4 <-> CH3 + H with recombination --
+    at small sizes: each job's counters (reaction events included), particle
+    count and moments equal the same job stepped alone."""
+    sw = W.served_jobs(n_jobs=9, rate=1000.0, n_min=1500, n_max=12000, steps_min=2, steps_max=9,
+                       recombination=True, seed=0x5E15)
+    kinds = {j.kind for j in sw.jobs}
+    assert kinds == {"relax", "bath", "equil"}
+    ctx = hcao.Context(precision=precision, max_rounds=4)
+    ctx.set_species(sw.species)
+    ctx.set_reactions(sw.reactions)
+    ctx.serve_start(hbm_budget_bytes=12 << 20, max_active=4, max_batch_steps=3)
+    ids = [ctx.serve_submit(j.workload, j.steps) for j in sw.jobs]
+    res = _wait(ctx, ids)
+    ctx.serve_stop()
+    rx_events = 0
+    for jid, j in zip(ids, sw.jobs):
+        r = res[jid]
+        cnt, n, m = _alone_w(sw, j.workload, j.steps, precision, 4)
+        assert r.status == 0 and r.steps == j.steps
+        assert np.array_equal(np.array(r.counters[: len(cnt)], np.uint64), cnt), (j.kind, list(r.counters), cnt)
+        assert r.n_particles == n
+        assert list(r.moments.n) == list(m.n)
+        for a, b in [(r.moments.E_tr, m.E_tr), (r.moments.E_form, m.E_form)] + \
+                [(r.moments.E_vib[i], m.E_vib[i]) for i in range(4)]:
+            assert abs(a - b) <= 1e-12 * max(abs(b), 1e-30), (j.kind, a, b)
+        rx_events += int(sum(cnt[8:]))
+    assert rx_events > 0
+    ctx.close()

@@ -36,7 +36,7 @@ def _rank_main(rank, world, port, out):
     try:
         ws, r = bench._dist()
         assert (ws, r) == (world, rank)
-        w = bench.replica_workload(rank, n_cells=3, per_cell=200)
+        w = bench.headline_workload("heat_bath", rank, n_cells=3, per_cell=200)
         o = oracle.from_workload(w)
         n0 = o.count(0)
         o.step(2)
@@ -44,7 +44,7 @@ def _rank_main(rank, world, port, out):
         units, secs = bench.aggregate(float(n0 * 2), 1.0 + rank)
         v, q, s, c = o.read_particles(0)
         # the reference arm: ranks other than 0 return at once, printing nothing
-        rc = bench.run_reference(argparse.Namespace(steps=1, warmup=0)) if rank != 0 else 0
+        rc = bench.run_reference(argparse.Namespace(steps=1, warmup=0, workload="exchange")) if rank != 0 else 0
         out.put((rank, n0, units, secs, float(np.sum(v * v)), rc))
     finally:
         dist.destroy_process_group()

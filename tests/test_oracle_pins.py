@@ -33,14 +33,34 @@ def test_philox_known_answers():
         assert oracle.philox(v[0:4], v[4:6]) == v[6:10]
 
 
-@pytest.mark.parametrize("N", [2, 3, 5, 16, 17, 100, 1000, 4096, 20000, 65535])
-def test_feistel_is_bijection(N):
+@pytest.mark.parametrize("N", [2, 3, 5, 16, 17, 100, 1000, 1200, 4096, 4097, 20000, 65535])
+def test_pair_perm_is_bijection(N):
     """The pairing permutation is a bijection of [0,N) (exhaustive)."""
     key = [0x12345678, 0x9ABCDEF0, 0x0F1E2D3C, 0x4B5A6978 ^ N]
-    img = [oracle.feistel(x, N, key) for x in range(N)]
+    img = [oracle.pair_perm(x, N, key) for x in range(N)]
     assert sorted(img) == list(range(N))
     if N >= 100:  # not the identity
         assert sum(i == x for x, i in enumerate(img)) < N // 10
+
+
+def test_pair_perm_pairs_are_uniform():
+    """Over random keys, pair 0's members are uniform over the cell, their
+    offset is uniform over the other particles, and within one key the pairs'
+    members do not follow their index (reading A9: every pair of particles
+    equally likely)."""
+    N = 1200
+    rng = np.random.default_rng(77)
+    keys = rng.integers(0, 2 ** 32, size=(20000, 4))
+    a = np.array([oracle.pair_perm(0, N, list(map(int, k))) for k in keys])
+    b = np.array([oracle.pair_perm(1, N, list(map(int, k))) for k in keys])
+    assert stats.chisquare(np.bincount(a * 40 // N, minlength=40)).pvalue > 1e-4
+    off = (b - a) % N
+    assert off.min() >= 1
+    assert stats.chisquare(np.bincount((off - 1) * 40 // (N - 1), minlength=40)).pvalue > 1e-4
+    key = list(map(int, keys[0]))
+    img = np.array([oracle.pair_perm(x, N, key) for x in range(N)])
+    assert abs(np.corrcoef(np.arange(N // 2), img[0::2])[0, 1]) < 0.15
+    assert abs(np.corrcoef(img[0::2], img[1::2])[0, 1]) < 0.15
 
 
 # ---------------------------------------------------------------- levels
