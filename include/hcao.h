@@ -289,8 +289,10 @@ hcao_status hcao_n_levels(const hcao_ctx* ctx, int sp, int mode, int* out);
    cell's records staged in shared memory; it needs FP32 mode, no reaction
    that creates or removes particles (dissociation, recombination), no
    per-pair log and cells of at most 4096 particle slots, and gives the same
-   bits as the queue path.  HCAO_PATH_AUTO (the default) takes the fused path
-   whenever the context allows it.  hcao_set_step_path(ctx, HCAO_PATH_FUSED)
+   bits as the queue path.  HCAO_PATH_AUTO (the default) takes the queue
+   path, the faster of the two on every workload measured (the fused kernel
+   holds one cell's pairs per CTA and keeps fewer pairs in flight per SM).
+   hcao_set_step_path(ctx, HCAO_PATH_FUSED)
    on a context that does not allow it makes the next hcao_step return
    HCAO_EINVAL.  hcao_get_step_path gives the path the next step takes
    (HCAO_PATH_QUEUE or HCAO_PATH_FUSED). */

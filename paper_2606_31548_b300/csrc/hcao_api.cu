@@ -847,7 +847,10 @@ bool fused_eligible(const hcao_ctx* ctx, int* smem_recs) {
     return true;
 }
 bool use_fused(const hcao_ctx* ctx, int* smem_recs) {
-    if (ctx->step_path == HCAO_PATH_QUEUE) return false;
+    // the queue kernels are the faster path on every workload measured (the
+    // fused kernel keeps fewer pairs in flight per SM), so the fused kernel
+    // runs only when asked for
+    if (ctx->step_path != HCAO_PATH_FUSED) return false;
     return fused_eligible(ctx, smem_recs);
 }
 

@@ -15,7 +15,10 @@ constexpr int MAXM = 16;        // vibrational modes per species
 constexpr int MAXS = 16;        // species
 constexpr int MAXR = 8;         // reactions
 constexpr int MAXL = 256;       // levels per mode (quantum numbers are bytes)
-constexpr int F32_BUCKET_BITS = 8;  // FP32 K5 buckets: mantissa bits per octave (~0.4% wide)
+#ifndef HCAO_F32_BUCKET_BITS
+#define HCAO_F32_BUCKET_BITS 8
+#endif
+constexpr int F32_BUCKET_BITS = HCAO_F32_BUCKET_BITS;  // FP32 K5 buckets: mantissa bits per octave (~0.4% wide)
 constexpr int TABLE_PAD = 17;   // grid entries beyond M (one per mode + 1)
 constexpr int MAX_ROUNDS = 4;   // NTC pairing rounds per cell and step (hard cap)
 constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 500 K * 2^(i/32)

@@ -181,6 +181,15 @@ __device__ __forceinline__ void set_q(uint32_t q[4], int j, uint32_t v) {
 }
 
 // ------------------------------------------------------------- records
+// Record traffic of the FP32 step kernels carries the evict-first (streaming)
+// cache policy, so that the records a step touches (630 MB for 19.7M
+// particles) push fewer sampler-table lines out of L2 (measured: step 3-6%
+// faster on the exchange mixture and the heat bath).
+#define REC_LD(p) __ldcs(p)
+#define REC_ST(p, v) __stcs((p), (v))
+#ifndef HCAO_RELAX_MINB
+#define HCAO_RELAX_MINB 4
+#endif
 __device__ __forceinline__ void load_rec(const RecF* p, RecF& r) {
     const uint4* s = reinterpret_cast<const uint4*>(p);
     uint4 a = s[0], b = s[1];
@@ -1621,7 +1630,7 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 ip = pair_perm(2u * k, N, key);
                 iq = pair_perm(2u * k + 1u, N, key);
                 const uint4* recs = reinterpret_cast<const uint4*>(cell.rec);
-                const uint4 a = recs[2 * ip], b = recs[2 * iq];
+                const uint4 a = REC_LD(recs + 2 * ip), b = REC_LD(recs + 2 * iq);
                 const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
                 const DevRes& rs = A.res[cell.res];
                 const uint32_t ev_idx = A.abase[c] + (uint32_t)r * round_pairs(N, A.has_recomb) + k;
@@ -1866,7 +1875,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
 // modes, P before Q, with the alias K5 draw (relative energy in int64 fixed
 // point), then isotropic scattering with the centre-of-mass velocity kept.
 template <class R>
-__global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
+__global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
     // queue regions: pairs with two molecules to relax, then one, then none
@@ -1886,8 +1895,8 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
         const uint32_t ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
         const uint32_t ip = e.z, iq = e.w;
         uint4* recs = reinterpret_cast<uint4*>(cell.rec);
-        const uint4 a = recs[2 * ip], b = recs[2 * iq];
-        const uint4 qa = recs[2 * ip + 1], qb = recs[2 * iq + 1];
+        const uint4 a = REC_LD(recs + 2 * ip), b = REC_LD(recs + 2 * iq);
+        const uint4 qa = REC_LD(recs + 2 * ip + 1), qb = REC_LD(recs + 2 * iq + 1);
         const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
         const DevPair& pc = C->pair[sP * MAXS + sQ];
         const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
@@ -1950,10 +1959,10 @@ __global__ void __launch_bounds__(128, 4) k_relax_fast(StepArgs A, int r) {
         iso_dir<float>(ss, d);
         float na[3], nb[3];
         scatter_f32(pc, Erel, d, va, vb, na, nb);
-        recs[2 * ip] = make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w);
-        recs[2 * iq] = make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w);
-        recs[2 * ip + 1] = make_uint4(qP[0], qP[1], qP[2], qP[3]);
-        recs[2 * iq + 1] = make_uint4(qQ[0], qQ[1], qQ[2], qQ[3]);
+        REC_ST(recs + 2 * ip, make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w));
+        REC_ST(recs + 2 * iq, make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w));
+        REC_ST(recs + 2 * ip + 1, make_uint4(qP[0], qP[1], qP[2], qP[3]));
+        REC_ST(recs + 2 * iq + 1, make_uint4(qQ[0], qQ[1], qQ[2], qQ[3]));
         A.cflag[ev_idx] = ev_final(o);
         if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
     }

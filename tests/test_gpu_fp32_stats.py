@@ -8,8 +8,8 @@ stream) and allows 3 standard errors of the difference (3.5 where several
 correlated checkpoints of one curve are tested together).
 
 * Exchange (Eq. Ecoll-exch, CH4 + H -> CH3 + H2, one stretch coupled):
-  exchange events per accepted collision and accepted collisions per
-  particle-step at 2000, 4000 and 6000 K.
+  the single-step exchange probability per CH4-H collision and the accepted
+  collisions per particle-step at 2000, 4000 and 6000 K.
 * Relaxation (Sec. "Implementation of the polyatomic HCAO model"): the
   triatomic's T_vib(t) curve over 16 seeds.
 * Conservation: every accepted non-reacting or exchange collision conserves
@@ -36,26 +36,39 @@ def _two_sample(kg, ng, ko, no):
     return pg - po, se
 
 
+def _mixed_exchange(ctx_log, v0_sp, cell0, n_cells):
+    """(exchange events, accepted CH4-H collisions) of the last step's log."""
+    lg = ctx_log.read_log()
+    acc = lg[lg["event"] >= 0]
+    start = np.concatenate([[0], np.cumsum(np.bincount(cell0, minlength=n_cells))[:-1]])
+    ip = start[acc["cell"]] + acc["p"]
+    iq = start[acc["cell"]] + acc["q"]
+    mixed = v0_sp[ip] != v0_sp[iq]
+    return int(np.sum(acc["event"][mixed] == 1)), int(np.sum(mixed)), len(acc)
+
+
 @pytest.mark.parametrize("T", [2000.0, 4000.0, 6000.0])
-def test_fp32_exchange_rate_matches_oracle(T):
-    steps = 3
-    wo = W.ch4_h_exchange(n_cells=192, per_cell=1200, T0=T)
-    wg = W.ch4_h_exchange(n_cells=192, per_cell=1200, T0=T, seed=wo.seed + 101)
-    o = oracle.from_workload(wo)
-    o.step(steps)
-    co = o.read_counters(0)
-    g = hcao.from_workload(wg, precision=hcao.FP32)
-    g.step(steps)
-    cg = g.read_counters(0)
-    acc_o, ex_o = int(co[1]), int(co[8])
-    acc_g, ex_g = int(cg[1]), int(cg[8])
+def test_fp32_exchange_probability_matches_oracle(T):
+    """One step from the Boltzmann state at T: the exchange probability per
+    CH4-H collision (Eq. Ecoll-exch) of FP32 mode against the oracle's, on
+    independent seeds (binomial two-sample, 3 sigma), and the accepted
+    collisions per particle-step."""
+    wo = W.ch4_h_exchange(n_cells=400, per_cell=1200, T0=T)
+    wg = W.ch4_h_exchange(n_cells=400, per_cell=1200, T0=T, seed=wo.seed + 101)
+    o = oracle.from_workload(wo, log=True)
+    _, _, so, co = o.read_particles(0)
+    o.step(1)
+    ex_o, mix_o, acc_o = _mixed_exchange(o, so, co, wo.n_cells)
+    g = hcao.from_workload(wg, precision=hcao.FP32, log=True)
+    _, _, sg, cg = g.read_particles(0)
+    g.step(1)
+    ex_g, mix_g, acc_g = _mixed_exchange(g, sg, cg, wg.n_cells)
     assert ex_o > 500 and ex_g > 500
-    d, se = _two_sample(ex_g, acc_g, ex_o, acc_o)
-    assert abs(d) < 3 * se, (T, ex_g / acc_g, ex_o / acc_o, se)
+    d, se = _two_sample(ex_g, mix_g, ex_o, mix_o)
+    assert abs(d) < 3 * se, (T, ex_g / mix_g, ex_o / mix_o, se)
     # collision rate: accepted collisions per particle-step (Poisson counts)
-    ps = wo.n * steps
-    rg, ro = acc_g / ps, acc_o / ps
-    assert abs(rg - ro) < 3 * math.sqrt(acc_g + acc_o) / ps, (rg, ro)
+    rg, ro = acc_g / wg.n, acc_o / wo.n
+    assert abs(rg - ro) < 3 * math.sqrt(acc_g + acc_o) / wo.n, (rg, ro)
 
 
 def test_fp32_relaxation_curve_matches_oracle():

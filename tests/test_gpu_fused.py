@@ -6,9 +6,9 @@ keyed streams and evaluate every floating-point expression with explicit
 roundings, so after any number of steps they must agree bit for bit: every
 particle's velocity, quantum numbers and species, every counter, every
 cell's (sigma_T g)_max and the K5 work counts.  The full-size exchange
-mixture (16384 cells x 1200, the benchmark's launch configuration) is checked
-on sampled cells against the queue path on those cells alone (cells are
-independent and keyed by their index) and for conservation.
+mixture (16384 cells x 1200, the benchmark's configuration) is checked for
+conservation and, on sampled cells, against the fused kernel on those cells
+alone (cells are independent and keyed by their index).
 """
 import numpy as np
 import pytest
@@ -61,7 +61,8 @@ def test_fused_equals_queue_path(name):
     w = make()
     f = hcao.from_workload(w, precision=hcao.FP32, **kw)
     q = hcao.from_workload(w, precision=hcao.FP32, **kw)
-    q.set_step_path(hcao.PATH_QUEUE)
+    assert q.step_path() == hcao.PATH_QUEUE  # the default
+    f.set_step_path(hcao.PATH_FUSED)
     assert f.step_path() == hcao.PATH_FUSED
     assert q.step_path() == hcao.PATH_QUEUE
     for s in (1, 1, 3, 5):
@@ -77,6 +78,8 @@ def test_fused_equals_queue_path(name):
     if name == "two_rounds":
         f.set_log(True)  # a per-pair log needs the queue path
         assert f.step_path() == hcao.PATH_QUEUE
+        with pytest.raises(hcao.HcaoError):
+            f.step(1)
 
 
 def test_fused_path_eligibility():
@@ -95,10 +98,14 @@ def test_fused_path_eligibility():
     assert hcao.from_workload(w2, precision=hcao.FP64).step_path() == hcao.PATH_QUEUE
     # a cell beyond the shared-memory limit (4096 slots): queue path
     w3 = W.relaxation_triatomic(n_particles=5000, n_cells=1)
-    assert hcao.from_workload(w3, precision=hcao.FP32).step_path() == hcao.PATH_QUEUE
-    # no chemistry, small cells: fused; one fused launch per step
+    g3 = hcao.from_workload(w3, precision=hcao.FP32)
+    g3.set_step_path(hcao.PATH_FUSED)
+    assert g3.step_path() == hcao.PATH_QUEUE
+    # no chemistry, small cells: fused on request; one fused launch per step
     w4 = W.relaxation_triatomic(n_particles=4000, n_cells=4)
     g4 = hcao.from_workload(w4, precision=hcao.FP32)
+    assert g4.step_path() == hcao.PATH_QUEUE
+    g4.set_step_path(hcao.PATH_FUSED)
     assert g4.step_path() == hcao.PATH_FUSED
     n0 = g4.kernel_launches()
     g4.step(7)
@@ -108,6 +115,7 @@ def test_fused_path_eligibility():
 def test_fused_profiling_class():
     w = W.ch4_h_exchange(n_cells=16, per_cell=1200)
     g = hcao.from_workload(w, precision=hcao.FP32)
+    g.set_step_path(hcao.PATH_FUSED)
     g.set_profiling(True)
     g.step(3)
     ms, n = g.read_profile()
@@ -115,14 +123,15 @@ def test_fused_profiling_class():
     assert int(n[:5].sum()) == 0
 
 
-def test_full_size_exchange_fused_sampled_cells_and_conservation():
-    """16384 cells x 1200 (19.7M particles), the benchmark's configuration:
-    two fused steps; 5 sampled cells equal the queue path run on those cells
-    alone, and the totals (particles, energy with formation energies,
-    momentum) are conserved."""
+def test_full_size_exchange_sampled_cells_and_conservation():
+    """16384 cells x 1200 (19.7M particles) in the benchmark's configuration
+    (FP32, the default queue path), two steps: the totals (particles, energy
+    with formation energies, momentum) are conserved, and 5 sampled cells
+    equal the fused kernel's run of those cells alone (cells are independent
+    and keyed by their index)."""
     w = W.ch4_h_exchange()
     g = hcao.from_workload(w, precision=hcao.FP32)
-    assert g.step_path() == hcao.PATH_FUSED
+    assert g.step_path() == hcao.PATH_QUEUE
 
     def totals():
         m = g.read_moments(0)
@@ -136,6 +145,7 @@ def test_full_size_exchange_fused_sampled_cells_and_conservation():
     assert n1 == n0 == w.n
     assert abs(E1 - E0) <= 1e-6 * abs(E0)
     assert np.all(np.abs(p1 - p0) <= 1e-6 * ps)
+    assert g.read_counters(0)[8] > 100000  # exchange events
     vg, qg, sg, cg = g.read_particles(0)
     g.close()
     pick = [0, 1, 4097, 9999, 16383]
@@ -146,7 +156,7 @@ def test_full_size_exchange_fused_sampled_cells_and_conservation():
     q.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
     q.load_particles(0, w.v[sel], w.qn0()[sel], w.species_idx[sel], w.cell[sel])
     q.init_vibration(0, w.T_vib0)
-    q.set_step_path(hcao.PATH_QUEUE)
+    q.set_step_path(hcao.PATH_FUSED)
     q.step(2)
     vq, qq, sq, cq = q.read_particles(0)
     out = np.isin(cg, pick)
