@@ -37,9 +37,9 @@ WORKLOADS = {
 }
 KERNEL_SRC = os.path.join(ROOT, "paper_2606_31548_b300", "csrc", "hcao_kernels.cuh")
 FUSED_SRC = os.path.join(ROOT, "paper_2606_31548_b300", "csrc", "hcao_fused.cuh")
+# DRAM bytes per step of the collide phase (ncu), keyed by (workload, path)
 TRAFFIC_FILES = {
-    "queue": os.path.join(ROOT, "profiles", "k_relax_fast_ch4_heat_bath_traffic.json"),
-    "fused": os.path.join(ROOT, "profiles", "k_collide_fused_ch4_h_exchange_traffic.json"),
+    ("exchange", "queue"): os.path.join(ROOT, "profiles", "collide_ch4_h_exchange_traffic.json"),
 }
 
 # Algorithmic lane-operations of the relaxation kernel per unit of K5 work (the
@@ -76,11 +76,12 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(path: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, or None if the kernel source changed since it was taken."""
+def _traffic_per_step(workload: str, path: str):
+    """DRAM bytes per step of the collide phase from the committed ncu
+    summary, or None if there is none for this workload and path or the
+    kernel source changed since it was taken."""
     try:
-        with open(TRAFFIC_FILES[path]) as f:
+        with open(TRAFFIC_FILES[(workload, path)]) as f:
             t = json.load(f)
         if t.get("kernel_src_sha256_16") != _kernel_hash():
             return None
@@ -546,10 +547,12 @@ def main():
         relax_s = kms[5] / 1e3
         alu_ach = lane_ops / relax_s / 1e9 if relax_s > 0 and lane_ops > 0 else None
     hbm_ach = (2 * S * psteps) / collide_s / 1e9 if collide_s > 0 else None
-    tr = _traffic_per_launch("fused" if fused else "queue")
+    tr = _traffic_per_step(args.workload, "fused" if fused else "queue")
     roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
             "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "traffic": tr["dram_bytes_per_step"] if tr else None,
+            "traffic_unit": "DRAM bytes per step of the collide phase (ncu, cold cache), beside "
+                            f"{2 * S * psteps / args.steps:.4g} algorithmic bytes per step",
             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "kernel": "k_collide_fused (the whole collision phase, one launch per step)" if fused
                       else "collide phase (select + relax + react kernels)",
