@@ -117,7 +117,20 @@ typedef struct {
     double steric;         /* EXCH: steric factor in [0,1] */
     int alpha_mode;        /* EXCH: HCAO_ALPHA_PER_MODE or _ONE_RANDOM_STRETCH */
     const double* alpha;   /* host, n_modes of A, or NULL */
+    int model;             /* DISS, EXCH: HCAO_MODEL_QK (0: the QK test of Eq. Ecoll-diss /
+                              Eq. Ecoll-exch) or HCAO_MODEL_TCE (1: the total-collision-energy
+                              probability of Eq. arrhenius, see below);
+                              RECOMB: HCAO_RPROB_EXACT (0: P of Eq. recomb-correct summed over
+                              every level combination) or HCAO_RPROB_WR (1: P from the sampled
+                              sum with the Whitten-Rabinovitch density of states) */
+    double arrhenius[3];   /* TCE: A (m^3/s K^-b), b, E_a (J) of k(T) = A T^b exp(-E_a/(k T)) */
+    double tce_zeta;       /* TCE: internal degrees of freedom of the pair (half their sum)
+                              whose energy counts in the collision energy; 0 = translational
+                              energy only */
+    int wr_samples;        /* RECOMB with HCAO_RPROB_WR: sample energies (<= 0: 1000) */
 } hcao_reaction;
+enum { HCAO_MODEL_QK = 0, HCAO_MODEL_TCE = 1 };
+enum { HCAO_RPROB_EXACT = 0, HCAO_RPROB_WR = 1 };
 
 /* One candidate pair of the last step (parity inspection). */
 typedef struct {

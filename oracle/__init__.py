@@ -38,7 +38,15 @@ class _Species(C.Structure):
 class _Reaction(C.Structure):
     _fields_ = [("type", C.c_int), ("reactants", C.c_int * 2), ("products", C.c_int * 2),
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
-                ("alpha_mode", C.c_int), ("alpha", C.c_double * MAXM)]
+                ("alpha_mode", C.c_int), ("alpha", C.c_double * MAXM), ("model", C.c_int),
+                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int)]
+
+
+def reaction_model_code(r) -> int:
+    """The C model field of a workload reaction: TCE or QK; WR or exact P."""
+    if r.type == "recomb":
+        return 1 if getattr(r, "recomb_prob", "exact") == "wr" else 0
+    return 1 if getattr(r, "model", "qk") == "tce" else 0
 
 
 class LogRec(C.Structure):
@@ -108,7 +116,8 @@ def lib():
                            ("ora_rec_rate", [C.c_void_p, C.c_int, C.c_int, C.c_double]),
                            ("ora_cell_temperature", [C.c_void_p, C.c_int, C.c_int]),
                            ("ora_rec_node_T", [C.c_int]),
-                           ("ora_gamma_q", [C.c_double, C.c_double])):
+                           ("ora_gamma_q", [C.c_double, C.c_double]),
+                           ("ora_tce_prob", [C.c_void_p, C.c_int, C.c_int, C.c_double])):
             getattr(L, name).restype = C.c_double
             getattr(L, name).argtypes = args
         L.ora_last_error.restype = C.c_char_p
@@ -181,6 +190,11 @@ class Oracle:
         d.alpha_mode = 1 if r.alpha_mode == "one_random_stretch" else 0
         for j, a in enumerate(r.alpha):
             d.alpha[j] = a
+        d.model = reaction_model_code(r)
+        for j, a in enumerate(getattr(r, "arrhenius", None) or []):
+            d.arrhenius[j] = a
+        d.tce_zeta = getattr(r, "tce_zeta", 0.0)
+        d.wr_samples = getattr(r, "wr_samples", 1000)
         self.n_reactions += 1
         return self._chk(self.L.ora_add_reaction(self.ctx, C.byref(d)), "add_reaction")
 
@@ -308,6 +322,10 @@ class Oracle:
 
     def rec_rate_node(self, rx, spM, i) -> float:
         return float(self.L.ora_rec_rate_node(self.ctx, rx, spM, i))
+
+    def tce_prob(self, rx, m, Ec) -> float:
+        """TCE reaction probability of reaction rx with a partner of species m at collision energy Ec."""
+        return float(self.L.ora_tce_prob(self.ctx, rx, m, Ec))
 
     def cell_temperature(self, res, cell) -> float:
         return float(self.L.ora_cell_temperature(self.ctx, res, cell))

@@ -43,7 +43,7 @@
 
 /* Philox stream purposes (counter word 3 = purpose << 24 | block). */
 enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7, PU_TEST = 8, PU_REC = 9 };
+       PU_INIT = 7, PU_TEST = 8, PU_REC = 9, PU_TCE = 10 };
 
 #define MAX_SPECIES 16
 #define MAX_REACTIONS 32
@@ -108,6 +108,9 @@ struct ora_ctx {
        nodes, computed when first needed */
     double rec_P[MAX_REACTIONS][ORA_REC_NODES];
     unsigned char rec_P_done[MAX_REACTIONS][ORA_REC_NODES];
+    /* TCE reactions: the probability tables per partner species (see
+       tce_build), NULL for QK reactions */
+    double* tce[MAX_REACTIONS][MAX_SPECIES];
 };
 
 static void set_err(ora_ctx* c, int code, const char* m) {
@@ -679,7 +682,11 @@ double ora_keq(ora_ctx* c, int rx, double T) {
 double ora_rec_rate_node(ora_ctx* c, int rx, int spM, int i) {
     double T = ora_rec_node_T(i);
     if (!c->rec_P_done[rx][i]) {
-        c->rec_P[rx][i] = ora_diss_prob(c, rx, T);
+        /* P of Eq. recomb-correct: the exact level sum, or its sampled WR form */
+        const ora_reaction_desc* r = &c->rx[rx];
+        c->rec_P[rx][i] = r->model == ORA_RPROB_WR
+                              ? ora_diss_prob_wr(c, rx, T, r->wr_samples > 0 ? r->wr_samples : 1000)
+                              : ora_diss_prob(c, rx, T);
         c->rec_P_done[rx][i] = 1;
     }
     double kf = c->rec_P[rx][i] * ora_mean_sigma_g(c, c->rx[rx].products[0], spM, T);
@@ -702,6 +709,78 @@ double ora_rec_rate(ora_ctx* c, int rx, int spM, double T) {
 }
 
 /* ------------------------------------------------------------------ */
+/* The total-collision-energy (TCE) model, the paper's comparison model
+   (Sec. "Polyatomic QK reaction modeling", Eq. arrhenius): a reaction with
+   the Arrhenius rate coefficient k(T) = A T^b exp(-E_a/kT) occurs in a
+   collision of total energy E_c with probability
+       P(E_c) = C1 (E_c - E_a)^(zeta + b + 1/2) / E_c^(zeta + 3/2 - omega)
+   (0 below E_a), the form whose average over the collision-energy
+   distribution of a VHS gas at equilibrium -- E_c = E_tr + E_int with E_tr
+   ~ Gamma(5/2 - omega) and E_int ~ Gamma(zeta), in units of kT -- is
+   eps k(T) / <sigma_T g>(T).  Integrating gives
+       C1 = eps A k^(1 - omega - b) Gamma(zeta + 5/2 - omega) /
+            (Gamma(zeta + b + 3/2) C_sigma),
+   with <sigma_T g>(T) = C_sigma T^(1 - omega) and eps = 2 for a pair of
+   like species (each collision counted once), 1 otherwise.  Readings:
+     - zeta (tce_zeta) is the number of internal degrees of freedom of the
+       pair, halved, whose energy counts in E_c: 0 takes the relative
+       translational energy alone; otherwise E_c adds both partners'
+       vibrational energy above their zero-point energy;
+     - P above 1 is taken as 1;
+     - P is tabulated per partner species at x_i = X (i/NT)^2 above E_a,
+       i = 0..NT (NT = 4096, X = the sampler span), and interpolated linearly
+       in s = sqrt(x/X) (the table's own variable), constant beyond X;
+     - TCE reactions are tested before the QK channels, in reaction order,
+       with one uniform of their own stream laid against the running sum of
+       their probabilities; a dissociation by TCE breaks the first stretch
+       of its mask (the products do not depend on which). */
+#define TCE_NT 4096
+static int tce_build(ora_ctx* c, int r) {
+    const ora_reaction_desc* d = &c->rx[r];
+    const double A = d->arrhenius[0], b = d->arrhenius[1], Ea = d->arrhenius[2], z = d->tce_zeta;
+    const double w = c->omega;
+    if (!(z >= 0.0) || !(z + b + 1.5 > 0.0) || !(A >= 0.0) || !(Ea >= 0.0)) return ORA_EINVAL;
+    const int a = d->reactants[0];
+    for (int m = 0; m < c->n_species; ++m) {
+        if (d->type == ORA_EXCH && m != d->reactants[1]) continue;
+        const ora_species_desc* SA = &c->sp[a].d;
+        const ora_species_desc* SM = &c->sp[m].d;
+        const double Tr = 0.5 * (SA->T_ref + SM->T_ref);
+        const double Csig = ora_mean_sigma_g(c, a, m, Tr) / pow(Tr, 1.0 - w);
+        const double eps = m == a ? 2.0 : 1.0;
+        const double C1 = eps * A * pow(KB, 1.0 - w - b) * exp(lgamma(z + 2.5 - w) - lgamma(z + b + 1.5)) / Csig;
+        const double beta = z + b + 0.5, gam = z + 1.5 - w;
+        double* t = (double*)malloc(sizeof(double) * (TCE_NT + 1));
+        if (!t) return ORA_ENOMEM;
+        for (int i = 0; i <= TCE_NT; ++i) {
+            const double sv = (double)i / (double)TCE_NT;
+            const double x = c->span * (sv * sv);
+            double P = x > 0.0 ? C1 * pow(x, beta) * pow(Ea + x, -gam) : 0.0;
+            t[i] = P < 1.0 ? P : 1.0;
+        }
+        c->tce[r][m] = t;
+    }
+    return ORA_OK;
+}
+
+/* TCE probability of reaction r for a pair whose partner has species m at
+   collision energy Ec (linear interpolation in s = sqrt(x/X)) */
+static double tce_prob(const ora_ctx* c, int r, int m, double Ec) {
+    const double* t = c->tce[r][m];
+    if (!t) return 0.0;
+    const double x = Ec - c->rx[r].arrhenius[2];
+    if (!(x > 0.0)) return 0.0;
+    const double sv = sqrt(x / c->span);
+    if (!(sv < 1.0)) return t[TCE_NT];
+    const double tt = sv * (double)TCE_NT;
+    const int i = (int)tt;
+    const double f = tt - (double)i;
+    return t[i] + f * (t[i + 1] - t[i]);
+}
+
+double ora_tce_prob(ora_ctx* c, int r, int m, double Ec) { return tce_prob(c, r, m, Ec); }
+
+/* ------------------------------------------------------------------ */
 ora_ctx* ora_create(int table_points, double table_span_J, uint32_t reject_cap) {
     ora_ctx* c = (ora_ctx*)calloc(1, sizeof(ora_ctx));
     if (!c) return NULL;
@@ -713,6 +792,8 @@ ora_ctx* ora_create(int table_points, double table_span_J, uint32_t reject_cap) 
 }
 void ora_destroy(ora_ctx* c) {
     if (!c) return;
+    for (int r = 0; r < MAX_REACTIONS; ++r)
+        for (int m = 0; m < MAX_SPECIES; ++m) free(c->tce[r][m]);
     for (int i = 0; i < c->n_species; ++i)
         for (int k = 0; k < ORA_MAX_MODES; ++k) free(c->sp[i].H[k]);
     for (int r = 0; r < c->n_res; ++r) {
@@ -763,6 +844,10 @@ int ora_add_reaction(ora_ctx* c, const ora_reaction_desc* r) {
         c->rx_zpesum[id] = c->sp[A].zpe + c->sp[B].zpe + c->sp[Cc].zpe;
     } else {
         c->rx_zpesum[id] = 0.0;
+    }
+    if (r->type != ORA_RECOMB && r->model == ORA_MODEL_TCE) {
+        int e = tce_build(c, id);
+        if (e != ORA_OK) return e;
     }
     return c->n_reactions++;
 }
@@ -1171,6 +1256,56 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
         goto relax;
     }
 
+    /* TCE reactions (the comparison model, Eq. arrhenius): tested before
+       the QK channels, in reaction order, against one uniform of their own */
+    {
+        double u_t = -1.0, run = 0.0;
+        for (int r = 0; r < c->n_reactions; ++r) {
+            const ora_reaction_desc* rx = &c->rx[r];
+            if (rx->model != ORA_MODEL_TCE || rx->type == ORA_RECOMB) continue;
+            int side;
+            if (rx->type == ORA_DISS) {
+                if (P->sp == rx->reactants[0]) side = 0;
+                else if (Q->sp == rx->reactants[0]) side = 1;
+                else continue;
+            } else {
+                if (P->sp == rx->reactants[0] && Q->sp == rx->reactants[1]) side = 0;
+                else if (Q->sp == rx->reactants[0] && P->sp == rx->reactants[1]) side = 1;
+                else continue;
+            }
+            double Ec = Etr;
+            if (rx->tce_zeta > 0.0) Ec = (Ec + (EvP - sP->zpe)) + (EvQ - sQ->zpe);
+            run = run + tce_prob(c, r, side ? P->sp : Q->sp, Ec);
+            if (u_t < 0.0) {
+                o_stream st;
+                st_init(&st, R->seed, R->step, cell, rk, PU_TCE);
+                u_t = st_u01(&st);
+            }
+            if (!(u_t < run)) continue;
+            o_part* A = side ? Q : P;
+            o_part* B = side ? P : Q;
+            int done;
+            if (rx->type == ORA_DISS) {
+                int mode = 0;
+                while (mode < 31 && !((rx->diss_mode_mask >> mode) & 1u)) mode++;
+                done = do_diss(c, R, r, A, B, side ? EvQ : EvP, cell, rk, NULL, created, n_created);
+                lr.aux = (uint32_t)mode + (side ? 16u : 0u);
+            } else {
+                done = do_exch(c, R, r, A, B, side ? EvQ : EvP, side ? EvP : EvQ, cell, rk);
+                lr.aux = (uint32_t)side;
+            }
+            if (done) {
+                R->counters[8 + r]++;
+                lr.event = 1 + r;
+                log_push(c, &lr);
+                return;
+            }
+            R->counters[6]++;
+            lr.aux = 0;
+            goto relax;
+        }
+    }
+
     /* QK reaction test: channel list in fixed order (reading A21) */
     o_chan ch[MAX_CHANNELS];
     int nch = 0;
@@ -1180,7 +1315,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
         double EvA = side ? EvQ : EvP;
         for (int r = 0; r < c->n_reactions; ++r) {
             const ora_reaction_desc* rx = &c->rx[r];
-            if (rx->type != ORA_DISS || rx->reactants[0] != A->sp) continue;
+            if (rx->type != ORA_DISS || rx->model == ORA_MODEL_TCE || rx->reactants[0] != A->sp) continue;
             for (int j = 0; j < sA->d.n_stretch; ++j) {
                 if (!((rx->diss_mode_mask >> j) & 1u)) continue;
                 /* Eq. Ecoll-diss */
@@ -1195,7 +1330,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
     }
     for (int r = 0; r < c->n_reactions; ++r) {
         const ora_reaction_desc* rx = &c->rx[r];
-        if (rx->type != ORA_EXCH) continue;
+        if (rx->type != ORA_EXCH || rx->model == ORA_MODEL_TCE) continue;
         int side;
         if (P->sp == rx->reactants[0] && Q->sp == rx->reactants[1]) side = 0;
         else if (Q->sp == rx->reactants[0] && P->sp == rx->reactants[1]) side = 1;

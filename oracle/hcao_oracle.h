@@ -60,7 +60,14 @@ typedef struct {
     double steric;        /* EXCH: steric factor in [0,1] */
     int alpha_mode;       /* EXCH: ORA_ALPHA_PER_MODE or ORA_ALPHA_ONE_RANDOM_STRETCH */
     double alpha[ORA_MAX_MODES];
+    int model;            /* DISS / EXCH: ORA_MODEL_QK or ORA_MODEL_TCE;
+                             RECOMB: ORA_RPROB_EXACT or ORA_RPROB_WR (the probability P) */
+    double arrhenius[3];  /* TCE: A (m^3/s K^-b), b, E_a (J) of Eq. arrhenius */
+    double tce_zeta;      /* TCE: internal degrees of freedom (half the pair's sum) in E_c */
+    int wr_samples;       /* RECOMB, WR: sample energies (<= 0: 1000) */
 } ora_reaction_desc;
+enum { ORA_MODEL_QK = 0, ORA_MODEL_TCE = 1 };
+enum { ORA_RPROB_EXACT = 0, ORA_RPROB_WR = 1 };
 
 typedef struct {
     uint32_t step, cell, round_k, p, q;
@@ -113,6 +120,9 @@ int      ora_sample_lb(ora_ctx*, int sp, double Ec, uint64_t seed, int64_t n, in
 int64_t  ora_sample_products(ora_ctx*, int rx, int sp1, const double* v1, const uint8_t* q1, int sp2,
                              const double* v2, const uint8_t* q2, int sp3, const double* v3, const uint8_t* q3,
                              uint64_t seed, int64_t n, double* out_v, uint8_t* out_q);
+/* TCE probability of reaction rx (model ORA_MODEL_TCE) for a partner of
+   species m at collision energy Ec (J), as the collision step evaluates it */
+double   ora_tce_prob(ora_ctx*, int rx, int m, double Ec);
 /* draws n initial states of species sp at T_vib (P6/P7) */
 int      ora_sample_init(ora_ctx*, int sp, double T_vib, uint64_t seed, int64_t n,
                          uint8_t* out_qn);

@@ -90,6 +90,9 @@ struct hcao_ctx {
     int n_species = 0;
     HostSpecies sp[MAXS];
     int n_reactions = 0;
+    // per reaction: the host-side choices of hcao_reaction (model, TCE
+    // parameters, WR sample count)
+    hcao_reaction rx_host[MAXR] = {};
     Consts hc{};
     Consts* d_consts = nullptr;
     double* d_lev64 = nullptr;
@@ -121,6 +124,9 @@ struct hcao_ctx {
     int n_recomb = 0;
     std::vector<double> h_krec, h_Tnode;
     double* d_krec = nullptr;
+    // TCE reactions: probability tables [slot][MAXS][TCE_NT + 1]
+    std::vector<double> h_tce;
+    double* d_tce = nullptr;
     double* d_Tnode = nullptr;
     long long* d_csum = nullptr;
     uint32_t* d_nbase = nullptr;
@@ -695,6 +701,57 @@ double tvib_host(const HostSpecies& s, double target) {
 // ZPE_C - E_j(0)) and K_eq = n_B n_C / n_A from translational and vibrational
 // partition sums with the formation energies.  Nodes are independent: they are
 // computed on host threads.
+// TCE probability tables (the comparison model, Eq. arrhenius): for a
+// reaction with k(T) = A T^b exp(-E_a/kT), the probability in a collision of
+// total energy E_c is P = C1 (E_c - E_a)^(zeta + b + 1/2) / E_c^(zeta + 3/2 -
+// omega), the form whose average over the equilibrium collision-energy
+// distribution of a VHS gas (E_tr ~ Gamma(5/2 - omega), internal energy ~
+// Gamma(zeta), in units of kT) is eps k(T) / <sigma_T g>(T); integrating,
+//   C1 = eps A k^(1 - omega - b) Gamma(zeta + 5/2 - omega) / (Gamma(zeta + b + 3/2) C_sigma),
+// <sigma_T g>(T) = C_sigma T^(1 - omega), eps = 2 for like partners.  P is
+// capped at 1 and tabulated per partner species at x_i = X (i/NT)^2 above
+// E_a (X the sampler span), i = 0..NT.
+hcao_status build_tce_tables(hcao_ctx* ctx) {
+    Consts& C = ctx->hc;
+    const double w = ctx->omega;
+    int slots = 0;
+    for (int i = 0; i < C.n_reactions; ++i)
+        if (C.rx[i].model == HCAO_MODEL_TCE) C.rx[i].tce_slot = slots++;
+    C.has_tce = slots > 0 ? 1 : 0;
+    ctx->h_tce.assign((size_t)std::max(slots, 1) * MAXS * (TCE_NT + 1), 0.0);
+    const double span = ctx->cfg.table_span_J;
+    for (int i = 0; i < C.n_reactions; ++i) {
+        DevReaction& D = C.rx[i];
+        if (D.model != HCAO_MODEL_TCE) continue;
+        const double A = ctx->rx_host[i].arrhenius[0], b = ctx->rx_host[i].arrhenius[1];
+        const double Ea = ctx->rx_host[i].arrhenius[2], z = ctx->rx_host[i].tce_zeta;
+        for (int m = 0; m < ctx->n_species; ++m) {
+            if (D.type == HCAO_EXCH && m != D.B) continue;
+            const hcao_species& SA = ctx->sp[D.A].d;
+            const hcao_species& SM = ctx->sp[m].d;
+            const double Tr = 0.5 * (SA.T_ref + SM.T_ref);
+            const double Csig = mean_sigma_g(ctx, D.A, m, Tr) / std::pow(Tr, 1.0 - w);
+            const double eps = m == D.A ? 2.0 : 1.0;
+            const double C1 = eps * A * std::pow(KB, 1.0 - w - b) *
+                              std::exp(std::lgamma(z + 2.5 - w) - std::lgamma(z + b + 1.5)) / Csig;
+            const double beta = z + b + 0.5, gam = z + 1.5 - w;
+            double* t = ctx->h_tce.data() + ((size_t)D.tce_slot * MAXS + (size_t)m) * (TCE_NT + 1);
+            for (int k = 0; k <= TCE_NT; ++k) {
+                const double sv = (double)k / (double)TCE_NT;
+                const double x = span * (sv * sv);
+                const double P = x > 0.0 ? C1 * std::pow(x, beta) * std::pow(Ea + x, -gam) : 0.0;
+                t[k] = P < 1.0 ? P : 1.0;
+            }
+        }
+    }
+    dfree(ctx, ctx->d_tce);
+    CU(dalloc(ctx, &ctx->d_tce, ctx->h_tce.size()));
+    CU(cudaMemcpyAsync(ctx->d_tce, ctx->h_tce.data(), sizeof(double) * ctx->h_tce.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
 hcao_status build_recomb_tables(hcao_ctx* ctx) {
     const Consts& C = ctx->hc;
     const int S = ctx->n_species;
@@ -720,7 +777,18 @@ hcao_status build_recomb_tables(hcao_ctx* ctx) {
             double Dthr = INFINITY;
             for (int j = 0; j < sA.d.n_stretch; ++j)
                 if ((D.mask >> j) & 1u) Dthr = std::min(Dthr, (sA.De[j] + D.zpesum) - sA.lev[j][0]);
-            const double P = thermal_diss_prob(levels(D.P0), Dthr, a, T);
+            double P;
+            if (ctx->rx_host[ri].model == HCAO_RPROB_WR) {
+                // the sampled sum with the WR density: the quanta are the
+                // fundamentals E_j(1) - E_j(0) of A's modes, the threshold is
+                // taken above A's ground state
+                double hnu[MAXM];
+                for (int j = 0; j < sA.n_modes; ++j) hnu[j] = sA.lev[j][1] - sA.lev[j][0];
+                const int ns = ctx->rx_host[ri].wr_samples > 0 ? ctx->rx_host[ri].wr_samples : 1000;
+                P = wr_diss_prob(hnu, sA.n_modes, Dthr - sA.zpe, a, T, ns);
+            } else {
+                P = thermal_diss_prob(levels(D.P0), Dthr, a, T);
+            }
             const double f = 2.0 * PI_D * KB * T / (HPLANCK * HPLANCK);
             const double qtr = std::pow(f * sB.d.mass, 1.5) * std::pow(f * sC.d.mass, 1.5) /
                                std::pow(f * sA.d.mass, 1.5);
@@ -830,6 +898,8 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.max_rounds = ctx->cfg.max_rounds;
     a.reject_cap = ctx->cfg.reject_cap;
     a.ticket = ctx->d_ticket;
+    a.tce = ctx->d_tce;
+    a.tce_span = ctx->cfg.table_span_J;
     return a;
 }
 
@@ -838,7 +908,8 @@ StepArgs make_args(hcao_ctx* ctx) {
 // no per-pair log, every cell within FUSED_MAX_RECS slots), else the
 // per-round queue kernels.  *smem_recs: the records the fused kernel stages.
 bool fused_eligible(const hcao_ctx* ctx, int* smem_recs) {
-    if (ctx->cfg.precision != HCAO_FP32 || ctx->hc.creates || ctx->n_recomb > 0 || ctx->log_on) return false;
+    if (ctx->cfg.precision != HCAO_FP32 || ctx->hc.creates || ctx->n_recomb > 0 || ctx->hc.has_tce || ctx->log_on)
+        return false;
     uint32_t mx = 0;
     for (const auto& r : ctx->res)
         if (r.live && r.loaded && r.max_cap > mx) mx = r.max_cap;
@@ -971,6 +1042,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_chcnt);
     dfree(ctx, ctx->d_err);
     dfree(ctx, ctx->d_ticket);
+    dfree(ctx, ctx->d_tce);
     dfree(ctx, ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
@@ -1193,6 +1265,10 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         DevReaction& D = C.rx[i];
         std::memset(&D, 0, sizeof D);
         D.type = r.type;
+        ctx->rx_host[i] = r;
+        ctx->rx_host[i].alpha = nullptr;  // not kept: copied into D.alpha below
+        if (r.model != 0 && r.model != 1)
+            return fail(ctx, HCAO_EINVAL, "set_reactions: bad model");
         if (r.type != HCAO_DISS && r.type != HCAO_EXCH && r.type != HCAO_RECOMB)
             return fail(ctx, HCAO_EINVAL, "set_reactions: bad type");
         if (r.type == HCAO_RECOMB) {
@@ -1234,6 +1310,18 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         D.Ea = r.Ea;
         D.steric = r.steric;
         D.alpha_mode = r.alpha_mode;
+        D.model = r.model;
+        if (r.model == HCAO_MODEL_TCE) {
+            const double b = r.arrhenius[1], z = r.tce_zeta;
+            if (!(r.arrhenius[0] >= 0.0) || !(r.arrhenius[2] >= 0.0) || !(z >= 0.0) || !(z + b + 1.5 > 0.0))
+                return fail(ctx, HCAO_EINVAL, "set_reactions: TCE needs A >= 0, E_a >= 0, zeta >= 0 and "
+                                              "zeta + b + 3/2 > 0");
+            D.tce_Ea = r.arrhenius[2];
+            D.tce_zeta_on = z > 0.0 ? 1 : 0;
+            int mode = 0;
+            while (mode < 31 && !((r.diss_mode_mask >> mode) & 1u)) mode++;
+            D.tce_mode = r.type == HCAO_DISS ? mode : 0;
+        }
         if (r.type == HCAO_DISS) {
             if (A.d.n_stretch == 0 || (r.diss_mode_mask >> A.d.n_stretch) != 0)
                 return fail(ctx, HCAO_EINVAL, "set_reactions: dissociation mask outside the stretches");
@@ -1260,6 +1348,10 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
     ctx->n_recomb = n_rec;
     if (n_rec > 0) {
         hcao_status st = build_recomb_tables(ctx);
+        if (st != HCAO_OK) return st;
+    }
+    {
+        hcao_status st = build_tce_tables(ctx);
         if (st != HCAO_OK) return st;
     }
     return upload_consts(ctx);

@@ -35,7 +35,8 @@ inline int setup_launches(int n_cells) { return setup_tiles(n_cells) == 1 ? 1 : 
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7, PU_REC = 9 };
+       PU_INIT = 7, PU_REC = 9, PU_TCE = 10 };
+constexpr int TCE_NT = 4096;    // TCE probability tables: NT + 1 points per (reaction, partner species)
 
 // per-reservoir counters
 enum { CNT_CAND = 0, CNT_ACC, CNT_SAMPLES, CNT_TRIALS, CNT_OVER, CNT_DEGEN, CNT_NOTEXEC,
@@ -115,6 +116,11 @@ struct DevReaction {
     uint32_t mask;
     int alpha_mode;
     int rslot;                       // RECOMB: slot of its rate table
+    int model;                       // DISS / EXCH: HCAO_MODEL_QK or HCAO_MODEL_TCE
+    int tce_slot;                    // TCE: slot of its probability tables
+    int tce_zeta_on;                 // TCE: the vibrational energies count in E_c
+    int tce_mode;                    // TCE dissociation: the stretch reported as broken
+    double tce_Ea;                   // TCE: E_a (J)
     double Ea, steric, zpesum, dEf;
     double alpha[MAXM];
     long long Ea_fix, zpesum_fix, dEf_fix;   // FP32 mode (2^-100 J units)
@@ -122,7 +128,7 @@ struct DevReaction {
 
 struct Consts {
     int n_species, n_reactions, amode, creates;
-    int has_recomb, pad_c[3];
+    int has_recomb, has_tce, pad_c[2];
     int rec_pair[MAXS * MAXS];       // species pair -> recombination | side << 3, or -1
     DevSpecies sp[MAXS];
     DevPair pair[MAXS * MAXS];
@@ -191,6 +197,8 @@ struct StepArgs {
     uint32_t* err;
     int max_rounds;
     uint32_t reject_cap;
+    const double* tce;              // [slot][MAXS][TCE_NT + 1] TCE probabilities (see tce_prob)
+    double tce_span;                // TCE tables: energy span X above E_a (J)
     uint32_t* ticket;               // fused step: CTAs finished (the last one advances the reservoirs)
     int fused_recs;                 // fused step: records staged per CTA (0 on the queue path)
 };

@@ -693,6 +693,61 @@ __device__ __forceinline__ uint32_t chan_pack(int rx, int side, int mode) {
     return (uint32_t)rx | ((uint32_t)side << 3) | ((uint32_t)mode << 4);
 }
 
+// TCE probability (the comparison model of Eq. arrhenius) of reaction rx for
+// a partner of species m at collision energy Ec: the host table at
+// x_i = X (i/NT)^2 above E_a, linear in s = sqrt(x/X), constant beyond X.
+// Written with explicit roundings (the same bits in every kernel).
+__device__ __forceinline__ double tce_prob(const StepArgs& A, const DevReaction& rx, int m, double Ec) {
+    const double x = __dsub_rn(Ec, rx.tce_Ea);
+    if (!(x > 0.0)) return 0.0;
+    const double* t = A.tce + ((size_t)rx.tce_slot * MAXS + (size_t)m) * (TCE_NT + 1);
+    const double sv = __dsqrt_rn(__ddiv_rn(x, A.tce_span));
+    if (!(sv < 1.0)) return __ldg(t + TCE_NT);
+    const double tt = __dmul_rn(sv, (double)TCE_NT);
+    const int i = (int)tt;
+    const double f = __dsub_rn(tt, (double)i);
+    const double t0 = __ldg(t + i), t1 = __ldg(t + i + 1);
+    return __dadd_rn(t0, __dmul_rn(f, __dsub_rn(t1, t0)));
+}
+
+// TCE reactions, tested before the QK channels in reaction order against one
+// uniform of their own stream (PU_TCE) laid on the running sum of their
+// probabilities.  E_c is the relative translational energy, plus both
+// partners' vibrational energy above their ZPE when the reaction counts
+// internal degrees of freedom.  Returns true with the channel in chan.
+template <class R>
+__device__ bool tce_test(const StepArgs& A, const Consts* __restrict__ C, const DevRes& rs, uint32_t lcell,
+                         uint32_t rk, int sP, int sQ, double Etr, double EvP, double EvQ, uint32_t& chan) {
+    double run = 0.0, u = -1.0;
+    for (int ri = 0; ri < C->n_reactions; ++ri) {
+        const DevReaction& rx = C->rx[ri];
+        if (rx.model != HCAO_MODEL_TCE || rx.type == HCAO_RECOMB) continue;
+        int side;
+        if (rx.type == HCAO_DISS) {
+            if (sP == rx.A) side = 0;
+            else if (sQ == rx.A) side = 1;
+            else continue;
+        } else {
+            if (sP == rx.A && sQ == rx.B) side = 0;
+            else if (sQ == rx.A && sP == rx.B) side = 1;
+            else continue;
+        }
+        double Ec = Etr;
+        if (rx.tce_zeta_on)
+            Ec = __dadd_rn(__dadd_rn(Ec, __dsub_rn(EvP, C->sp[sP].zpe)), __dsub_rn(EvQ, C->sp[sQ].zpe));
+        run = __dadd_rn(run, tce_prob(A, rx, side ? sP : sQ, Ec));
+        if (u < 0.0) {
+            Stream st;
+            st_init(st, rs.seed, rs.step, lcell, rk, PU_TCE);
+            u = (double)st_uni<R>(st);
+        }
+        if (!(u < run)) continue;
+        chan = (uint32_t)ri | ((uint32_t)side << 3) | ((uint32_t)(rx.type == HCAO_DISS ? rx.tce_mode : 0) << 4);
+        return true;
+    }
+    return false;
+}
+
 // QK reaction test: channels in fixed order (partner 1 stretches, partner 2
 // stretches, exchange); one with E_excess > 0 is taken, several are chosen
 // with probability proportional to E_excess ("Competing reactions").  Two
@@ -719,7 +774,7 @@ __device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, in
             const double EvA = side ? EvQ : EvP;
             for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
                 const DevReaction& rx = C->rx[ri];
-                if (rx.type != HCAO_DISS || rx.A != spA) continue;
+                if (rx.type != HCAO_DISS || rx.model == HCAO_MODEL_TCE || rx.A != spA) continue;
                 for (int j = 0; j < SA.n_stretch; ++j) {
                     if (!((rx.mask >> j) & 1u)) continue;
                     // Eq. Ecoll-diss: ZPEs of A, B, C removed, the breaking mode's restored
@@ -738,7 +793,7 @@ __device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, in
         }
         for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
             const DevReaction& rx = C->rx[ri];
-            if (rx.type != HCAO_EXCH) continue;
+            if (rx.type != HCAO_EXCH || rx.model == HCAO_MODEL_TCE) continue;
             int side;
             if (sP == rx.A && sQ == rx.B) side = 0;
             else if (sQ == rx.A && sP == rx.B) side = 1;
@@ -1009,7 +1064,7 @@ static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const
             const long long EvA = side ? EvQ : EvP;
             for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
                 const DevReaction& rx = C->rx[ri];
-                if (rx.type != HCAO_DISS || rx.A != spA) continue;
+                if (rx.type != HCAO_DISS || rx.model == HCAO_MODEL_TCE || rx.A != spA) continue;
                 const long long base = Etr + EvA - rx.zpesum_fix;
                 for (int j = 0; j < SA.n_stretch; ++j) {
                     if (!((rx.mask >> j) & 1u)) continue;
@@ -1026,7 +1081,7 @@ static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const
         }
         for (int ri = 0; ri < C->n_reactions && !picked; ++ri) {
             const DevReaction& rx = C->rx[ri];
-            if (rx.type != HCAO_EXCH) continue;
+            if (rx.type != HCAO_EXCH || rx.model == HCAO_MODEL_TCE) continue;
             int side;
             if (sP == rx.A && sQ == rx.B) side = 0;
             else if (sQ == rx.A && sP == rx.B) side = 1;
@@ -1846,6 +1901,11 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
                 A.qB[slot] = make_uint4((uint32_t)c, e.y, rchan, mpos);
                 continue;
             }
+            if (C->has_tce && tce_test<R>(A, C, rs, L.lcell, L.rk, sP, sQ, Etr, EvP, EvQ, rchan)) {
+                const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
+                A.qB[slot] = make_uint4((uint32_t)c, e.y, rchan, 0u);
+                continue;
+            }
             Stream sp;
             st_init(sp, rs.seed, rs.step, L.lcell, L.rk, PU_PAIR);
             st_u64(sp);
@@ -1913,6 +1973,9 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         if (C->n_reactions > 0) {
             const float sgf = sg_f32(pc, C->amode, g2);
             if (C->has_recomb && recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sgf, chan, mpos)) {
+                react = true;
+            } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
+                                                     fix2d(EvQ), chan)) {
                 react = true;
             } else {
                 Stream sp;

@@ -62,7 +62,8 @@ class _Species(C.Structure):
 class _Reaction(C.Structure):
     _fields_ = [("type", C.c_int), ("reactants", C.c_int * 2), ("products", C.c_int * 2),
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
-                ("alpha_mode", C.c_int), ("alpha", C.POINTER(C.c_double))]
+                ("alpha_mode", C.c_int), ("alpha", C.POINTER(C.c_double)), ("model", C.c_int),
+                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int)]
 
 
 class LogRec(C.Structure):
@@ -252,6 +253,14 @@ class Context:
                 buf = (C.c_double * len(r.alpha))(*r.alpha)
                 keep.append(buf)
                 d.alpha = C.cast(buf, C.POINTER(C.c_double))
+            if r.type == "recomb":
+                d.model = 1 if getattr(r, "recomb_prob", "exact") == "wr" else 0
+            else:
+                d.model = 1 if getattr(r, "model", "qk") == "tce" else 0
+            for j, a in enumerate(getattr(r, "arrhenius", None) or []):
+                d.arrhenius[j] = a
+            d.tce_zeta = getattr(r, "tce_zeta", 0.0)
+            d.wr_samples = getattr(r, "wr_samples", 1000)
         self._chk(self.L.hcao_set_reactions(self.h, arr, len(reactions)))
         self.n_reactions = len(reactions)
 

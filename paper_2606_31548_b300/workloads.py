@@ -46,7 +46,7 @@ class Species:
 
 @dataclasses.dataclass
 class Reaction:
-    type: str                       # "diss" or "exch"
+    type: str                       # "diss", "exch" or "recomb"
     reactants: List[int]
     products: List[int]
     diss_mode_mask: int = 0
@@ -54,6 +54,11 @@ class Reaction:
     steric: float = 1.0
     alpha_mode: str = "per_mode"    # or "one_random_stretch" (reading A18)
     alpha: List[float] = dataclasses.field(default_factory=list)
+    model: str = "qk"               # diss / exch: "qk" or "tce" (Arrhenius via TCE)
+    arrhenius: Optional[List[float]] = None   # TCE: A (m^3/s K^-b), b, E_a (J)
+    tce_zeta: float = 0.0           # TCE: internal DOF (half the pair's sum) in the collision energy
+    recomb_prob: str = "exact"      # recomb: "exact" level sum or "wr" (Whitten-Rabinovitch)
+    wr_samples: int = 1000
 
 
 def triatomic() -> Species:

@@ -46,6 +46,43 @@ def test_rate_tables_match_oracle():
         g.recomb_rate(0, 0, 3000.0)  # reaction 0 is the dissociation
 
 
+def _wr(w):
+    for r in w.reactions:
+        if r.type == "recomb":
+            r.recomb_prob = "wr"
+    return w
+
+
+def test_wr_rate_tables_match_oracle():
+    """The recombination rate tables built from the WR form of P (the sampled
+    sum with the Whitten-Rabinovitch density, Sec. "Recombination
+    reactions"): library against oracle at nodes and between them, and below
+    the exact-sum tables as the WR form runs low for CH4."""
+    w = _wr(W.ch4_recombination(n_cells=1, per_cell=10))
+    g = hcao.from_workload(w, precision=hcao.FP64)
+    o = oracle.from_workload(w)
+    ge = hcao.from_workload(W.ch4_recombination(n_cells=1, per_cell=10), precision=hcao.FP64)
+    for T in (2000.0, 2031.7, 4000.0, 9000.0):
+        for m in range(3):
+            kg, ko = g.recomb_rate(1, m, T), o.rec_rate(1, m, T)
+            assert abs(kg - ko) <= 1e-10 * ko, (T, m, kg, ko)
+        ratio = g.recomb_rate(1, 2, T) / ge.recomb_rate(1, 2, T)
+        assert 0.4 < ratio < 0.95, (T, ratio)
+
+
+def test_parity_recombination_wr_fp64():
+    """A recombination run with the WR rate tables: bit-exact with the
+    oracle's run with its own WR tables (FP64 mode)."""
+    w = _wr(W.ch4_recombination(n_cells=6, per_cell=800, T0=3000.0, n_density=1e26))
+    g = hcao.from_workload(w, precision=hcao.FP64, log=True)
+    o = oracle.from_workload(w, log=True)
+    for _ in range(4):
+        g.step(1)
+        o.step(1)
+        _assert_same(g, o)
+    assert g.read_reaction_counts(0, 2)[1] > 20  # recombinations happened
+
+
 @pytest.mark.parametrize("case", ["one_round", "four_rounds"])
 def test_parity_recombination_fp64(case):
     w = W.ch4_recombination(n_cells=6, per_cell=800, T0=2000.0, n_density=1e26)
