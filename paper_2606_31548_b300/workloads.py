@@ -322,3 +322,152 @@ def served_jobs(n_jobs: int = 48, rate: float = 50.0, n_min: int = 10_000, n_max
                        dt, T, T, js, steps, shuffle=False)
         jobs.append(ServedJob(t, kind, w, steps))
     return ServedWorkload("served_jobs", species, rx, jobs)
+
+
+# ----------------------------------------------------------------- paper presets
+# The species and reaction tables of the paper's verification cases (Sec.
+# "Verification": tab:h2o, tab:hcn, tab:ch4, tab:ch3 and the Arrhenius
+# tables).  The tables give omega_e (m^-1) and chi_e of each Morse stretch and
+# Theta (K) of each bend.  Readings (the tables leave these open):
+#   - a stretch's dissociation energy is the Morse value
+#     D_e = h c omega_e / (4 chi_e) (Eq. energy-AHO with chi_e = h c omega_e /
+#     (4 D_e)); its levels are kept below it;
+#   - masses are the molecular masses, VHS d_ref 4e-10 m for polyatomic
+#     molecules, 3.5e-10 m for diatomics, 3.0e-10 m for N and 2.5e-10 m for
+#     H, T_ref = 273 K and omega = 0.75 for all;
+#   - formation energies from the well bottoms: the fragment that keeps a
+#     bond's partner carries that bond's D_e, so that breaking it costs
+#     exactly D_e (reading A13);
+#   - the paper's particle weights and number densities would give 1e14 to
+#     1e17 particles for its reservoir volume; the presets keep the number
+#     densities and temperatures and choose the particle count, w = n V / N;
+#   - Arrhenius E_a values are given in K and converted with k.
+HC_JM = 6.62607015e-34 * 299792458.0   # h c, J m
+
+
+def morse(we_m1: float, chi_e: float):
+    """(omega_e, omega_e chi_e, D_e) of a Morse stretch from omega_e (m^-1)
+    and chi_e (the paper's table form)."""
+    return we_m1, we_m1 * chi_e, HC_JM * we_m1 / (4.0 * chi_e)
+
+
+def _morse_species(name, mass_u, d_ref, stretches, thetas, E_form=0.0) -> Species:
+    we, wexe, De = [], [], []
+    for w_, c_ in stretches:
+        a, b, d = morse(w_, c_)
+        we.append(a); wexe.append(b); De.append(d)
+    return Species(name, mass_u * AMU, d_ref, E_form=E_form, we=we, wexe=wexe, De=De, theta=list(thetas))
+
+
+def paper_species(name: str) -> Species:
+    """Species of the paper's verification tables (tab:h2o, tab:hcn, tab:ch4,
+    tab:ch3 and the diatomics named beside them)."""
+    oh = (387620.0, 0.021774)
+    hc = (342040.0, 0.0146)
+    cn_in_hcn = (211920.0, 0.00368)
+    ch = (312350.0, 0.0190)
+    h2 = (439524.0, 0.0287)
+    if name == "H2O":
+        return _morse_species("H2O", 18.015, 4.0e-10, [oh, oh], [2294.3])
+    if name == "OH":  # the water molecule's O-H stretch parameters
+        return _morse_species("OH", 17.007, 3.5e-10, [oh], [], E_form=morse(*oh)[2])
+    if name == "N2":
+        return _morse_species("N2", 28.014, 3.5e-10, [(234599.0, 0.007439)], [])
+    if name == "HCN":  # modes: HC stretch, CN stretch, two bends
+        return _morse_species("HCN", 27.025, 4.0e-10, [hc, cn_in_hcn], [1023.9, 1023.9])
+    if name == "CN":  # the paper's CN constants (chi_e as printed beside the table)
+        return _morse_species("CN", 26.017, 3.5e-10, [(211920.0, 0.0146)], [], E_form=morse(*hc)[2])
+    if name == "HC":
+        return _morse_species("HC", 13.019, 3.5e-10, [hc], [], E_form=morse(*cn_in_hcn)[2])
+    if name == "CH4":
+        return _morse_species("CH4", 16.043, 4.0e-10, [ch] * 4, [1565.2, 1565.2, 1360.3, 1360.3, 1360.3])
+    if name == "CH3":
+        return _morse_species("CH3", 15.035, 4.0e-10, [ch] * 3, [872.1, 2016.2, 2016.2], E_form=morse(*ch)[2])
+    if name == "H2":
+        return _morse_species("H2", 2.016, 2.9e-10, [h2], [], E_form=-morse(*h2)[2])
+    if name == "H":
+        return Species("H", 1.008 * AMU, 2.5e-10)
+    if name == "N":
+        return Species("N", 14.007 * AMU, 3.0e-10)
+    raise ValueError(name)
+
+
+# Arrhenius parameters of the paper's TCE reference runs: A (m^3/s K^-b), b,
+# E_a (K), and the internal degrees of freedom (half the pair's sum) that the
+# TCE collision energy counts (reading: 0, translation only, except for HCN,
+# whose b = -2.6 needs zeta > 1.1 for the probability to stay finite at the
+# threshold; zeta = 2, HCN's two bends and two stretches halved)
+PAPER_ARRHENIUS = {
+    "H2O+M->H+OH+M": ([8e-15, 0.0, 52920.0], 0.0),
+    "HCN+M->H+CN+M": ([5.9283e-4, -2.6, 62845.0], 2.0),
+    "CH4+H->CH3+H2": ([1.03e-24, 2.5, 4825.0], 0.0),
+    "CH4+M->CH3+H+M": ([5.26e-12, 0.0, 51488.0], 0.0),
+}
+
+
+def _tce(key):
+    (A, b, Ea_K), zeta = PAPER_ARRHENIUS[key]
+    return dict(model="tce", arrhenius=[A, b, Ea_K * KB], tce_zeta=zeta)
+
+
+def paper_water(model: str = "qk", n_per_species: int = 200_000, n_cells: int = 1,
+                seed: int = 0x48434140) -> Workload:
+    """H2O + N2 -> H + OH + N2 (Sec. "Verification", water case): T0 = 6000 K,
+    n = 1e23 m^-3 of H2O and of N2, dt = 2e-9 s; QK (either O-H stretch may
+    break) or TCE with the paper's Arrhenius parameters."""
+    sp = [paper_species(s) for s in ("H2O", "N2", "H", "OH")]
+    kw = _tce("H2O+M->H+OH+M") if model == "tce" else {}
+    rx = [Reaction("diss", [0], [3, 2], diss_mode_mask=0b11, **kw)]
+    counts = np.full(n_cells, 2 * n_per_species // n_cells)
+    return _build(f"paper_water_{model}", sp, rx, n_cells, counts, [1.0, 1.0, 0.0, 0.0], 4.64e-6, 2e23,
+                  2e-9, 6000.0, 6000.0, seed, 2000)
+
+
+def paper_hcn(T0: float = 5000.0, model: str = "qk", n_per_species: int = 200_000, n_cells: int = 1,
+              seed: int = 0x48434141) -> Workload:
+    """HCN + N, the two dissociation channels H + CN and HC + N (Sec.
+    "Verification", hydrogen cyanide case): n = 3e24 m^-3 of HCN and of N at
+    T0 = 5000 or 12000 K; QK (both channels) or TCE (the H + CN channel
+    only, the paper's Arrhenius parameters).  dt = 0.2 / nu(T0)."""
+    sp = [paper_species(s) for s in ("HCN", "N", "H", "CN", "HC")]
+    if model == "tce":
+        rx = [Reaction("diss", [0], [3, 2], diss_mode_mask=0b01, **_tce("HCN+M->H+CN+M"))]
+    else:
+        rx = [Reaction("diss", [0], [3, 2], diss_mode_mask=0b01),
+              Reaction("diss", [0], [4, 1], diss_mode_mask=0b10)]
+    dt = 0.2 / vhs_collision_frequency(sp[0], 6e24, T0)
+    counts = np.full(n_cells, 2 * n_per_species // n_cells)
+    return _build(f"paper_hcn_{model}_{T0:.0f}K", sp, rx, n_cells, counts, [1.0, 1.0, 0.0, 0.0, 0.0], 4.64e-6,
+                  6e24, dt, T0, T0, seed, 2000)
+
+
+def paper_methane_exchange(model: str = "qk", n_per_species: int = 100_000, n_cells: int = 1,
+                           seed: int = 0x48434142) -> Workload:
+    """CH4 + H -> CH3 + H2 (Sec. "Verification", methane case): CH4, H, CH3
+    and H2 at n = 1e22 m^-3 each, T0 = 5000 K, dt = 5e-9 s; QK with 21% of
+    every mode's energy coupled (alpha_j = 0.21) and E_a = 1.03e-19 J, or TCE
+    with the paper's Arrhenius parameters."""
+    sp = [paper_species(s) for s in ("CH4", "H", "CH3", "H2")]
+    if model == "tce":
+        rx = [Reaction("exch", [0, 1], [2, 3], **_tce("CH4+H->CH3+H2"))]
+    else:
+        rx = [Reaction("exch", [0, 1], [2, 3], Ea=1.03e-19, steric=1.0, alpha_mode="per_mode", alpha=[0.21] * 9)]
+    counts = np.full(n_cells, 4 * n_per_species // n_cells)
+    return _build(f"paper_methane_exchange_{model}", sp, rx, n_cells, counts, [1.0, 1.0, 1.0, 1.0], 4.64e-6,
+                  4e22, 5e-9, 5000.0, 5000.0, seed, 2000)
+
+
+def paper_methane_dissociation(model: str = "qk", n_per_species: int = 100_000, n_cells: int = 1,
+                               seed: int = 0x48434143) -> Workload:
+    """CH4 + M <-> CH3 + H + M (Sec. "Verification", methane case): CH4, CH3
+    and H at n = 1e23 m^-3 each, T0 = 9000 K; the forward dissociation by QK
+    or TCE (the paper's Arrhenius parameters), the backward recombination
+    from the equilibrium constant in both.  dt = 0.2 / nu(T0)."""
+    sp = [paper_species(s) for s in ("CH4", "CH3", "H")]
+    kw = _tce("CH4+M->CH3+H+M") if model == "tce" else {}
+    rx = [Reaction("diss", [0], [1, 2], diss_mode_mask=0xF, **kw),
+          Reaction("recomb", [1, 2], [0, -1], diss_mode_mask=0xF)]
+    dt = 0.2 / vhs_collision_frequency(sp[0], 3e23, 9000.0)
+    counts = np.full(n_cells, 3 * n_per_species // n_cells)
+    return _build(f"paper_methane_dissociation_{model}", sp, rx, n_cells, counts, [1.0, 1.0, 1.0], 4.64e-6,
+                  3e23, dt, 9000.0, 9000.0, seed, 2000)
