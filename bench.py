@@ -122,12 +122,17 @@ def _sum_over_ranks(x: float) -> float:
     return x
 
 
-def headline_workload(kind: str, rank: int = 0, **kw):
-    """The workload each rank steps: the same recipe with a seed of its own
-    (ranks are independent replicas; no data-path collective)."""
-    if kind == "heat_bath":
-        return W.ch4_heat_bath(seed=0x48434132 + rank, **kw)
-    return W.ch4_h_exchange(seed=0x48434133 + rank, T0=kw.pop("T0", 4000.0), **kw)
+CELLS_PER_RANK = {"exchange": 16384, "heat_bath": 4096}
+
+
+def headline_workload(kind: str, rank: int = 0, world: int = 1, **kw):
+    """The cells rank `rank` steps: the contiguous range [rank C, (rank + 1) C)
+    of one workload of world x C cells (C = 16384 for the exchange mixture,
+    4096 for the heat bath), drawn cell by cell so that the split does not
+    change the particles, and keyed by the global cell index: each rank steps
+    its range exactly as the whole workload would (no data-path collective)."""
+    C = kw.pop("cells_per_rank", CELLS_PER_RANK[kind])
+    return W.cell_range(kind, rank * C, (rank + 1) * C, world * C, **kw)
 
 
 def aggregate(units: float, seconds: float):
@@ -417,11 +422,12 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
 
 def _config(kind, w, args, ws):
     per_cell = int(np.bincount(w.cell, minlength=w.n_cells).max())
-    return {"workload": WORKLOADS[kind], "cells": w.n_cells, "particles_per_cell": per_cell,
-            "particles": w.n, "T0_K": w.T_tr0, "precision": args.precision,
+    return {"workload": WORKLOADS[kind], "cells": w.n_cells * ws, "cells_per_rank": w.n_cells,
+            "particles_per_cell": per_cell, "particles": w.n * ws, "T0_K": w.T_tr0, "precision": args.precision,
             "species": [s.name for s in w.species],
             "l2": "flushed (256 MiB write) before every timed step; the particle state is larger than L2",
-            "parallelism": f"replicas x{ws}"}
+            "parallelism": f"contiguous cell ranges x{ws} (one workload of {ws} x {w.n_cells} cells, "
+                           "keyed by global cell index; no data-path collective)"}
 
 
 def run_reference(args):
@@ -481,7 +487,7 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     prec = hcao.FP32 if args.precision == "fp32" else hcao.FP64
-    w = headline_workload(args.workload, rank)
+    w = headline_workload(args.workload, rank, ws)
     ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 

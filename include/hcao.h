@@ -182,6 +182,16 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* reactions, in
    reservoir index. */
 hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, double weight,
                                double dt, uint64_t seed, double T_sgmax, int* id);
+/* The index of reservoir res's first cell in the random-number keys
+   (default 0).  Every draw of a cell is keyed by (reservoir seed, step, cell
+   index, round, pair), so a reservoir that holds cells [base, base +
+   n_cells) of a larger workload -- same seed, same cell volume, weight and
+   time step -- steps those cells exactly as the whole workload would: one
+   workload split across GPUs or processes by contiguous cell ranges gives
+   the same particles as the unsplit run (Multi-GPU split, no exchange between
+   the ranges).  Call before hcao_load_particles (HCAO_EINVAL after it);
+   base + n_cells must fit 32 bits. */
+hcao_status hcao_set_cell_base(hcao_ctx* ctx, int res, uint32_t base);
 /* Remove a reservoir and free its device memory. */
 hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int res);
 

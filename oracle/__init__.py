@@ -72,6 +72,7 @@ def lib():
         L.ora_load.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]
         L.ora_init_vibration.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.ora_set_cell_base.argtypes = [C.c_void_p, C.c_int, C.c_uint32]
         L.ora_step.argtypes = [C.c_void_p, C.c_int]
         L.ora_set_log.argtypes = [C.c_void_p, C.c_int]
         L.ora_log_count.restype = C.c_int64
@@ -209,6 +210,9 @@ class Oracle:
         cell = np.ascontiguousarray(cell, dtype=np.int32)
         self._chk(self.L.ora_load(self.ctx, res, v.shape[0], _p(v), _p(qn), _p(species), _p(cell)),
                   "load")
+
+    def set_cell_base(self, res, base):
+        self._chk(self.L.ora_set_cell_base(self.ctx, res, base), "set_cell_base")
 
     def init_vibration(self, res, T_vib):
         self._chk(self.L.ora_init_vibration(self.ctx, res, T_vib), "init_vibration")
@@ -358,6 +362,8 @@ def from_workload(w, table_points=2048, table_span_J=64 * 1.602176634e-19, log=F
     for r in w.reactions:
         o.add_reaction(r)
     res = o.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    if getattr(w, "cell_base", 0):
+        o.set_cell_base(res, w.cell_base)
     o.load(res, w.v, w.qn0(), w.species_idx, w.cell)
     if init_vib:
         o.init_vibration(res, w.T_vib0)

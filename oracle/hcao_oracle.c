@@ -84,6 +84,7 @@ typedef struct {
     double Vc, w, dt, T_sgmax;
     uint64_t seed;
     uint32_t step;
+    uint32_t cell_base;  /* index of the first cell in the random-number keys */
     o_cell* cells;
     uint64_t counters[8 + MAX_REACTIONS];
 } o_res;
@@ -900,13 +901,19 @@ int ora_load(ora_ctx* c, int res, int64_t n, const double* v, const uint8_t* qn,
     return 0;
 }
 
+int ora_set_cell_base(ora_ctx* c, int res, uint32_t base) {
+    if (res < 0 || res >= c->n_res) return ORA_EINVAL;
+    c->res[res]->cell_base = base;
+    return 0;
+}
+
 int ora_init_vibration(ora_ctx* c, int res, double T_vib) {
     o_res* R = c->res[res];
     for (int j = 0; j < R->n_cells; ++j) {
         o_cell* cl = &R->cells[j];
         for (int i = 0; i < cl->n; ++i) {
             o_stream st;
-            st_init(&st, R->seed, 0xFFFFFFFFu, (uint32_t)j, (uint32_t)i, PU_INIT);
+            st_init(&st, R->seed, 0xFFFFFFFFu, R->cell_base + (uint32_t)j, (uint32_t)i, PU_INIT);
             const o_species* s = &c->sp[cl->p[i].sp];
             memset(cl->p[i].qn, 0, 16);
             if (sample_init(c, s, T_vib, &st, cl->p[i].qn) != S_OK) {
@@ -1429,6 +1436,9 @@ relax:;
 static int step_reservoir(ora_ctx* c, o_res* R) {
     for (int ci = 0; ci < R->n_cells; ++ci) {
         o_cell* cl = &R->cells[ci];
+        /* the cell's index in every random-number key: a reservoir may hold a
+           contiguous range of a larger workload's cells */
+        const uint32_t gc = R->cell_base + (uint32_t)ci;
         int N = cl->n;
         if (N < 2) continue;
         /* NTC: N_sel = 1/2 N (N-1) w (sigma g)_max dt / V_c, rounded stochastically */
@@ -1436,7 +1446,7 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
         double fl = floor(x);
         int64_t nsel = (int64_t)fl;
         o_stream sn;
-        st_init(&sn, R->seed, R->step, (uint32_t)ci, 0u, PU_NSEL);
+        st_init(&sn, R->seed, R->step, gc, 0u, PU_NSEL);
         if (st_u01(&sn) < x - fl) nsel++;
         int has_rec = 0;
         for (int r = 0; r < c->n_reactions; ++r) has_rec |= c->rx[r].type == ORA_RECOMB;
@@ -1451,7 +1461,7 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
         double Tcell = has_rec ? cell_temperature(c, cl) : 0.0;
         for (int64_t r = 0; r < rounds; ++r) {
             o_stream sf;
-            st_init(&sf, R->seed, R->step, (uint32_t)ci, (uint32_t)r << 24, PU_PERM);
+            st_init(&sf, R->seed, R->step, gc, (uint32_t)r << 24, PU_PERM);
             uint32_t key[4];
             for (int i = 0; i < 4; ++i) key[i] = st_word(&sf);
             int64_t kmax = nsel - r * P;
@@ -1460,7 +1470,7 @@ static int step_reservoir(ora_ctx* c, o_res* R) {
             for (int64_t k = 0; k < kmax; ++k) {
                 uint32_t ip = ora_pair_perm((uint32_t)(2 * k), (uint32_t)N, key);
                 uint32_t iq = ora_pair_perm((uint32_t)(2 * k + 1), (uint32_t)N, key);
-                process_pair(c, R, (uint32_t)ci, (uint32_t)r, (uint32_t)k, &cl->p[ip], &cl->p[iq],
+                process_pair(c, R, gc, (uint32_t)r, (uint32_t)k, &cl->p[ip], &cl->p[iq],
                              ip, iq, cl->sgmax, &seen, created, &n_created, &rd);
             }
         }

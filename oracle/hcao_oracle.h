@@ -87,6 +87,10 @@ int      ora_add_reservoir(ora_ctx*, int n_cells, double cell_volume, double wei
 int      ora_load(ora_ctx*, int res, int64_t n, const double* v, const uint8_t* qn,
                   const int32_t* species, const int32_t* cell);
 int      ora_init_vibration(ora_ctx*, int res, double T_vib);
+/* index of the reservoir's first cell in the random-number keys (default 0):
+   a reservoir holding cells [base, base + n_cells) of a larger workload steps
+   those cells exactly as the whole workload would */
+int      ora_set_cell_base(ora_ctx*, int res, uint32_t base);
 int      ora_step(ora_ctx*, int n_steps);
 int      ora_set_log(ora_ctx*, int enable);
 int64_t  ora_log_count(ora_ctx*);

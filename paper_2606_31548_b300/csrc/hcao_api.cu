@@ -55,6 +55,7 @@ struct Reservoir {
     size_t rec_bytes = 0;
     uint64_t total_cap = 0;
     uint32_t max_cap = 0;          // largest cell capacity (slots)
+    uint32_t cell_base = 0;        // index of the first cell in the random-number keys
 };
 
 // one served job: its copied inputs, state and result
@@ -1377,6 +1378,19 @@ hcao_status hcao_add_reservoir(hcao_ctx* ctx, int n_cells, double cell_volume, d
     return HCAO_OK;
 }
 
+hcao_status hcao_set_cell_base(hcao_ctx* ctx, int id, uint32_t base) {
+    DeviceScope ds_(ctx);
+    SERVE_GUARD(ctx);
+    if (!ctx) return HCAO_EINVAL;
+    Reservoir* r = get_res(ctx, id);
+    if (!r) return fail(ctx, HCAO_ENOTFOUND, "set_cell_base: no such reservoir");
+    if (r->loaded) return fail(ctx, HCAO_EINVAL, "set_cell_base: before the reservoir is loaded");
+    if ((uint64_t)base + (uint64_t)r->n_cells > 0x100000000ull)
+        return fail(ctx, HCAO_EINVAL, "set_cell_base: cell indices beyond 32 bits");
+    r->cell_base = base;
+    return HCAO_OK;
+}
+
 hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int id) {
     DeviceScope ds_(ctx);
     SERVE_GUARD(ctx);
@@ -1496,7 +1510,7 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
         d.n = count;
         d.cap = (uint32_t)cap;
         d.res = (uint32_t)id;
-        d.lcell = (uint32_t)c;
+        d.lcell = r->cell_base + (uint32_t)c;  // the cell's index in every random-number key
         d.sgmax = 2.0 * mx;  // reading A10: 2 <sigma_T g>(T_sgmax), largest pair present
     }
     const size_t rs = rec_size(ctx);

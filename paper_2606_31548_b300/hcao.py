@@ -33,7 +33,7 @@ EXPORTS = [
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
     "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
-    "hcao_set_step_path", "hcao_get_step_path",
+    "hcao_set_step_path", "hcao_get_step_path", "hcao_set_cell_base",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -149,6 +149,7 @@ def lib() -> C.CDLL:
         L.hcao_serve_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(u64)]
         L.hcao_recomb_rate.argtypes = [vp, i32, i32, dbl, C.POINTER(dbl)]
         L.hcao_set_step_path.argtypes = [vp, i32]
+        L.hcao_set_cell_base.argtypes = [vp, i32, C.c_uint32]
         L.hcao_get_step_path.argtypes = [vp, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
         L.hcao_kernel_launches.restype = u64
@@ -269,6 +270,10 @@ class Context:
         self._chk(self.L.hcao_add_reservoir(self.h, n_cells, cell_volume, weight, dt, seed, T_sgmax,
                                             C.byref(rid)))
         return rid.value
+
+    def set_cell_base(self, res: int, base: int) -> None:
+        """Key reservoir res's cells as cells base, base + 1, ... of a larger workload."""
+        self._chk(self.L.hcao_set_cell_base(self.h, res, base))
 
     def remove_reservoir(self, res: int) -> None:
         self._chk(self.L.hcao_remove_reservoir(self.h, res))
@@ -475,6 +480,8 @@ def from_workload(w, precision=FP64, log=False, init_vib=True, **kw) -> Context:
     c.set_species(w.species)
     c.set_reactions(w.reactions)
     rid = c.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    if getattr(w, "cell_base", 0):
+        c.set_cell_base(rid, w.cell_base)
     c.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
     if init_vib:
         c.init_vibration(rid, w.T_vib0)

@@ -120,6 +120,7 @@ class Workload:
     species_idx: np.ndarray
     cell: np.ndarray
     steps: int
+    cell_base: int = 0              # index of the first cell in the random-number keys
 
     @property
     def n(self) -> int:
@@ -200,6 +201,47 @@ def ch4_recombination(n_cells: int = 8, per_cell: int = 2000, steps: int = 500,
     dt = 0.2 / vhs_collision_frequency(sp[0], n_density, T0)
     return _build("ch4_recombination", sp, rx, n_cells, np.full(n_cells, per_cell), list(fractions),
                   4.64e-6, n_density, dt, T0, T0, seed, steps)
+
+
+def cell_range(kind: str, c0: int, c1: int, total_cells: int, per_cell: Optional[int] = None,
+               T0: Optional[float] = None, seed: Optional[int] = None) -> Workload:
+    """Cells [c0, c1) of a workload of total_cells cells whose initial state
+    is drawn cell by cell, from a generator seeded by (seed, cell), so that
+    any split of the cells into contiguous ranges holds exactly the
+    particles of the whole: the unit of the multi-GPU split (each rank one
+    range; cell_base = c0 keys the range's cells by their global index).
+    kind "exchange": the CH4 + H mixture of ch4_h_exchange (50/50, 1200 per
+    cell, 4000 K); kind "heat_bath": the CH4 bath of ch4_heat_bath (500 per
+    cell, 15000 K).  Weight and cell volume are those of the whole."""
+    if kind == "exchange":
+        T = 4000.0 if T0 is None else T0
+        ref = ch4_h_exchange(n_cells=1, per_cell=2, T0=T)
+        pc = 1200 if per_cell is None else per_cell
+        fractions, n_density, sd = np.array([0.5, 0.5]), 2e22, 0x48434133
+    elif kind == "heat_bath":
+        T = 15000.0 if T0 is None else T0
+        ref = ch4_heat_bath(n_cells=1, per_cell=2, T0=T)
+        pc = 500 if per_cell is None else per_cell
+        fractions, n_density, sd = np.array([1.0]), 1e23, 0x48434132
+    else:
+        raise ValueError(kind)
+    sd = sd if seed is None else seed
+    V_total = 4.64e-6
+    n_loc = (c1 - c0) * pc
+    sp = np.zeros(n_loc, np.int32)
+    v = np.zeros((n_loc, 3))
+    masses = np.array([s.mass for s in ref.species])
+    for i, c in enumerate(range(c0, c1)):
+        rng = np.random.default_rng((sd, c))
+        s_c = rng.choice(len(fractions), size=pc, p=fractions / fractions.sum()).astype(np.int32) \
+            if len(fractions) > 1 else np.zeros(pc, np.int32)
+        sp[i * pc:(i + 1) * pc] = s_c
+        v[i * pc:(i + 1) * pc] = maxwellian(rng, pc, masses[s_c], T)
+    cell = np.repeat(np.arange(c1 - c0, dtype=np.int32), pc)
+    weight = n_density * V_total / (total_cells * pc)
+    return Workload(f"{ref.name}_cells_{c0}_{c1}_of_{total_cells}", ref.species, ref.reactions, c1 - c0,
+                    V_total / total_cells, weight, ref.dt, T, T, sd, np.ascontiguousarray(v), sp, cell, ref.steps,
+                    cell_base=c0)
 
 
 def random_levels(rng: np.random.Generator, n: int, n_levels: List[int], n_modes: int) -> np.ndarray:
