@@ -32,14 +32,15 @@ class _Species(C.Structure):
     _fields_ = [("mass", C.c_double), ("d_ref", C.c_double), ("T_ref", C.c_double),
                 ("omega", C.c_double), ("E_form", C.c_double), ("n_stretch", C.c_int),
                 ("we", C.c_double * MAXM), ("wexe", C.c_double * MAXM), ("De", C.c_double * MAXM),
-                ("n_bend", C.c_int), ("theta", C.c_double * MAXM)]
+                ("n_bend", C.c_int), ("theta", C.c_double * MAXM), ("rot_dof", C.c_int)]
 
 
 class _Reaction(C.Structure):
     _fields_ = [("type", C.c_int), ("reactants", C.c_int * 2), ("products", C.c_int * 2),
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
                 ("alpha_mode", C.c_int), ("alpha", C.c_double * MAXM), ("model", C.c_int),
-                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int)]
+                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int),
+                ("gamma", C.c_double)]
 
 
 def reaction_model_code(r) -> int:
@@ -73,6 +74,12 @@ def lib():
                                C.c_void_p]
         L.ora_init_vibration.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.ora_set_cell_base.argtypes = [C.c_void_p, C.c_int, C.c_uint32]
+        L.ora_init_rotation.argtypes = [C.c_void_p, C.c_int, C.c_double]
+        L.ora_load_erot.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.ora_read_erot.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+        L.ora_ln.restype = C.c_double
+        L.ora_ln.argtypes = [C.c_double]
+        L.ora_sample_rot_fraction.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_void_p]
         L.ora_step.argtypes = [C.c_void_p, C.c_int]
         L.ora_set_log.argtypes = [C.c_void_p, C.c_int]
         L.ora_log_count.restype = C.c_int64
@@ -178,6 +185,7 @@ class Oracle:
         d.n_bend = len(s.theta)
         for j, t in enumerate(s.theta):
             d.theta[j] = t
+        d.rot_dof = getattr(s, "rot_dof", 0)
         return self._chk(self.L.ora_add_species(self.ctx, C.byref(d)), "add_species")
 
     def add_reaction(self, r) -> int:
@@ -196,6 +204,7 @@ class Oracle:
             d.arrhenius[j] = a
         d.tce_zeta = getattr(r, "tce_zeta", 0.0)
         d.wr_samples = getattr(r, "wr_samples", 1000)
+        d.gamma = getattr(r, "gamma", 0.0)
         self.n_reactions += 1
         return self._chk(self.L.ora_add_reaction(self.ctx, C.byref(d)), "add_reaction")
 
@@ -210,6 +219,23 @@ class Oracle:
         cell = np.ascontiguousarray(cell, dtype=np.int32)
         self._chk(self.L.ora_load(self.ctx, res, v.shape[0], _p(v), _p(qn), _p(species), _p(cell)),
                   "load")
+
+    def init_rotation(self, res, T_rot):
+        self._chk(self.L.ora_init_rotation(self.ctx, res, T_rot), "init_rotation")
+
+    def load_erot(self, res, erot):
+        e = np.ascontiguousarray(erot, np.float64)
+        self._chk(self.L.ora_load_erot(self.ctx, res, _p(e)), "load_erot")
+
+    def read_erot(self, res) -> np.ndarray:
+        out = np.zeros(self.count(res))
+        self._chk(self.L.ora_read_erot(self.ctx, res, _p(out)), "read_erot")
+        return out
+
+    def sample_rot_fraction(self, sp, seed, n) -> np.ndarray:
+        out = np.zeros(n)
+        self._chk(self.L.ora_sample_rot_fraction(self.ctx, sp, seed, n, _p(out)), "sample_rot_fraction")
+        return out
 
     def set_cell_base(self, res, base):
         self._chk(self.L.ora_set_cell_base(self.ctx, res, base), "set_cell_base")
@@ -349,6 +375,11 @@ def wr_density(hnu, E: float) -> float:
     return float(lib().ora_wr_density(_p(h), len(h), E))
 
 
+def ln(x: float) -> float:
+    """The oracle's own natural logarithm (rotation draws)."""
+    return float(lib().ora_ln(x))
+
+
 def gamma_q(a: float, x: float) -> float:
     return float(lib().ora_gamma_q(a, x))
 
@@ -367,6 +398,8 @@ def from_workload(w, table_points=2048, table_span_J=64 * 1.602176634e-19, log=F
     o.load(res, w.v, w.qn0(), w.species_idx, w.cell)
     if init_vib:
         o.init_vibration(res, w.T_vib0)
+        if any(getattr(s, "rot_dof", 0) for s in w.species):
+            o.init_rotation(res, getattr(w, "T_rot0", w.T_tr0))
     o.set_log(log)
     return o
 

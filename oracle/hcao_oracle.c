@@ -43,7 +43,7 @@
 
 /* Philox stream purposes (counter word 3 = purpose << 24 | block). */
 enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7, PU_TEST = 8, PU_REC = 9, PU_TCE = 10 };
+       PU_INIT = 7, PU_TEST = 8, PU_REC = 9, PU_TCE = 10, PU_ROT = 11, PU_ROTINIT = 12 };
 
 #define MAX_SPECIES 16
 #define MAX_REACTIONS 32
@@ -65,12 +65,14 @@ typedef struct {
     double eps_min;     /* smallest single-quantum excitation of any mode */
     int MT;
     double* H[ORA_MAX_MODES];
+    double rot_fmax;    /* rotation: the maximum of the LB fraction's density shape */
 } o_species;
 
 typedef struct {
     double v[3];
     int32_t sp;
     uint8_t qn[ORA_MAX_MODES];
+    double erot;    /* classical rotational energy, J */
 } o_part;
 
 typedef struct {
@@ -824,6 +826,15 @@ int ora_add_species(ora_ctx* c, const ora_species_desc* d) {
     for (int j = 0; j < s->n_modes; ++j)
         if (s->n_levels[j] < 1) return ORA_EINVAL;
     if (build_tables(c, s)) return ORA_ENOMEM;
+    if (d->rot_dof != 0 && d->rot_dof != 2 && d->rot_dof != 3) return ORA_EINVAL;
+    if (d->rot_dof == 2) {
+        s->rot_fmax = 1.0;  /* (1 - x)^(3/2 - omega) is largest at x = 0 */
+    } else if (d->rot_dof == 3) {
+        /* x^(1/2) (1 - x)^(3/2 - omega) peaks at x = 1/2 / (1/2 + 3/2 - omega) */
+        const double bb = 1.5 - c->omega;
+        const double xs = 0.5 / (0.5 + bb);
+        s->rot_fmax = sqrt(xs) * pow(1.0 - xs, bb);
+    }
     return c->n_species++;
 }
 
@@ -901,6 +912,55 @@ int ora_load(ora_ctx* c, int res, int64_t n, const double* v, const uint8_t* qn,
     return 0;
 }
 
+static double rot_fraction(const ora_ctx* c, const o_species* s, o_stream* st);
+static double rot_init_energy(const o_species* s, double kT, o_stream* st);
+
+int ora_init_rotation(ora_ctx* c, int res, double T_rot) {
+    if (res < 0 || res >= c->n_res || !(T_rot >= 0.0)) return ORA_EINVAL;
+    o_res* R = c->res[res];
+    for (int j = 0; j < R->n_cells; ++j) {
+        o_cell* cl = &R->cells[j];
+        for (int i = 0; i < cl->n; ++i) {
+            const o_species* s = &c->sp[cl->p[i].sp];
+            cl->p[i].erot = 0.0;
+            if (s->d.rot_dof == 0 || T_rot == 0.0) continue;
+            o_stream st;
+            st_init(&st, R->seed, 0xFFFFFFFEu, R->cell_base + (uint32_t)j, (uint32_t)i, PU_ROTINIT);
+            cl->p[i].erot = rot_init_energy(s, KB * T_rot, &st);
+        }
+    }
+    return 0;
+}
+
+int ora_load_erot(ora_ctx* c, int res, const double* erot) {
+    if (res < 0 || res >= c->n_res) return ORA_EINVAL;
+    o_res* R = c->res[res];
+    int64_t o = 0;
+    for (int j = 0; j < R->n_cells; ++j)
+        for (int i = 0; i < R->cells[j].n; ++i, ++o)
+            R->cells[j].p[i].erot = c->sp[R->cells[j].p[i].sp].d.rot_dof ? erot[o] : 0.0;
+    return 0;
+}
+
+int ora_read_erot(ora_ctx* c, int res, double* erot) {
+    if (res < 0 || res >= c->n_res) return ORA_EINVAL;
+    o_res* R = c->res[res];
+    int64_t o = 0;
+    for (int j = 0; j < R->n_cells; ++j)
+        for (int i = 0; i < R->cells[j].n; ++i, ++o) erot[o] = R->cells[j].p[i].erot;
+    return 0;
+}
+
+int ora_sample_rot_fraction(ora_ctx* c, int sp, uint64_t seed, int64_t n, double* out) {
+    if (sp < 0 || sp >= c->n_species || c->sp[sp].d.rot_dof == 0) return ORA_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+        o_stream st;
+        st_init(&st, seed, (uint32_t)i, (uint32_t)(i >> 32), 0u, PU_ROT);
+        out[i] = rot_fraction(c, &c->sp[sp], &st);
+    }
+    return 0;
+}
+
 int ora_set_cell_base(ora_ctx* c, int res, uint32_t base) {
     if (res < 0 || res >= c->n_res) return ORA_EINVAL;
     c->res[res]->cell_base = base;
@@ -938,6 +998,78 @@ static void iso_dir(o_stream* st, double d[3]) {
             return;
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Rotation (Sec. "Rotation coupling"; the paper drops rotation in its
+   verification runs).  Readings:
+     - a molecule's rotation is one classical energy E_rot with rot_dof
+       degrees of freedom (2 linear, 3 non-linear);
+     - every accepted collision that relaxes (reading A8) also relaxes the
+       rotation of each rotating partner, after the vibrational draws, P
+       before Q: with E_c = E_rel + E_rot the classical LB draw gives
+       E_rot' = x E_c, x ~ Beta(rot_dof/2, (5 - 2 omega)/2), and E_rel' =
+       E_c - E_rot' (one stream PU_ROT per pair);
+     - x is drawn by rejection under the maximum of its density shape
+       x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega), written with square roots only;
+     - the QK collision energies add gamma E_rot,A (the paper's extended
+       Eq. Ecoll-diss and Eq. Ecoll-exch), gamma per reaction;
+     - a reaction puts the reactants' rotational energy into the energy it
+       redistributes; products start with E_rot = 0 and take rotation in
+       their next collisions; a third body keeps its rotation;
+     - TCE with internal degrees of freedom counts E_rot of both partners;
+     - initial rotation at T_rot: E_rot = kT Gamma(rot_dof/2), from
+       -ln(u) (rot_dof 2) plus Marsaglia's polar normal squared over two
+       (rot_dof 3), with the logarithm ora_ln. */
+
+/* natural logarithm for x > 0 (normal doubles): x = m 2^e with m in
+   [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m - 1)/(m + 1), |s| < 0.172,
+   by the atanh series to s^25 (remainder below 1e-19), plus e ln 2 */
+double ora_ln(double x) {
+    union { double d; uint64_t u; } b;
+    b.d = x;
+    int e = (int)((b.u >> 52) & 0x7FF) - 1022;
+    b.u = (b.u & 0x000FFFFFFFFFFFFFull) | 0x3FE0000000000000ull;  /* m in [0.5, 1) */
+    double m = b.d;
+    if (m < 0.70710678118654752440) { m = m * 2.0; e = e - 1; }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double s2 = s * s;
+    double t = 1.0 / 25.0;
+    for (int k = 23; k >= 1; k -= 2) t = 1.0 / (double)k + s2 * t;
+    return 2.0 * s * t + (double)e * 0.69314718055994530942;
+}
+
+/* the LB fraction's density shape (1 - x)^(3/2 - omega) times x^(1/2) for
+   three rotational degrees of freedom */
+static double rot_shape(const ora_ctx* c, int rot_dof, double x) {
+    double f = pw(c, 1.0 - x);
+    if (rot_dof == 3) f = f * sqrt(x);
+    return f;
+}
+
+static double rot_fraction(const ora_ctx* c, const o_species* s, o_stream* st) {
+    for (uint32_t it = 0; it < c->reject_cap; ++it) {
+        const double x = st_u01(st);
+        const double y = st_u01(st);
+        if (y * s->rot_fmax < rot_shape(c, s->d.rot_dof, x)) return x;
+    }
+    return 0.5;
+}
+
+static double rot_init_energy(const o_species* s, double kT, o_stream* st) {
+    double E = -ora_ln(1.0 - st_u01(st));
+    if (s->d.rot_dof == 3) {
+        for (;;) {
+            const double x1 = 2.0 * st_u01(st) - 1.0;
+            const double x2 = 2.0 * st_u01(st) - 1.0;
+            const double q = x1 * x1 + x2 * x2;
+            if (q > 0.0 && q < 1.0) {
+                E = E + x1 * x1 * (-ora_ln(q) / q);
+                break;
+            }
+        }
+    }
+    return E * kT;
 }
 
 typedef struct { int rx, side, mode; double ex; } o_chan;
@@ -991,7 +1123,7 @@ static int do_diss(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* M, double Ev
     double KEin = 0.5 * mA * vA2 + 0.5 * mM * vM2;
     double KEcm = 0.5 * mt * V2;
     double dEf = (sB->d.E_form + sC->d.E_form) - sA->d.E_form;
-    double Eav = KEin - KEcm + EvibA - dEf;
+    double Eav = KEin - KEcm + EvibA - dEf + A->erot;  /* A's rotation joins the pool */
     if (!(Eav - sB->zpe - sC->zpe > 0.0) || Eav - sC->zpe > table_top(sB, c) ||
         Eav - sB->zpe > table_top(sC, c))
         return 0;
@@ -1034,6 +1166,7 @@ static int do_diss(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* M, double Ev
     }
     A->sp = r->products[0];
     memcpy(A->qn, qB, 16);
+    A->erot = 0.0;  /* products start without rotation; M keeps its own */
     for (int i = 0; i < 3; ++i) { A->v[i] = vB[i]; M->v[i] = vM[i]; }
     o_part nc;
     memset(&nc, 0, sizeof nc);
@@ -1064,7 +1197,7 @@ static int do_exch(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* B, double Ev
     double KEin = 0.5 * mA * vA2 + 0.5 * mB * vB2;
     double KEcm = 0.5 * mt * V2;
     double dEf = (sC->d.E_form + sD->d.E_form) - (sA->d.E_form + sB->d.E_form);
-    double Eav = KEin - KEcm + EvA + EvB - dEf;
+    double Eav = (KEin - KEcm + EvA + EvB - dEf + A->erot) + B->erot;  /* rotation joins the pool */
     if (!(Eav - sC->zpe - sD->zpe > 0.0) || Eav - sD->zpe > table_top(sC, c) ||
         Eav - sC->zpe > table_top(sD, c))
         return 0;
@@ -1092,6 +1225,8 @@ static int do_exch(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* B, double Ev
     B->sp = r->products[1];
     memcpy(A->qn, qC, 16);
     memcpy(B->qn, qD, 16);
+    A->erot = 0.0;
+    B->erot = 0.0;
     return 1;
 }
 
@@ -1122,7 +1257,7 @@ static int do_recomb(ora_ctx* c, o_res* R, int rx, o_part* B, o_part* Cp, o_part
     double KEin = (0.5 * mB * vB2 + 0.5 * mC * vC2) + 0.5 * mM * vM2;
     double KEcm = 0.5 * mt * V2;
     double dEf = sA->d.E_form - (sB->d.E_form + sC->d.E_form);
-    double Eav = KEin - KEcm + EvB + EvC - dEf;
+    double Eav = (KEin - KEcm + EvB + EvC - dEf + B->erot) + Cp->erot;  /* rotation joins the pool */
     if (!(Eav - sA->zpe > 0.0) || Eav > table_top(sA, c)) return 0;
     o_stream sa, ss;
     st_init(&sa, R->seed, R->step, cell, rk, PU_LB_A);
@@ -1142,7 +1277,9 @@ static int do_recomb(ora_ctx* c, o_res* R, int rx, o_part* B, o_part* Cp, o_part
     }
     B->sp = r->products[0];
     memcpy(B->qn, qA, 16);
+    B->erot = 0.0;
     Cp->sp = -1;
+    Cp->erot = 0.0;
     return 1;
 }
 
@@ -1281,7 +1418,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
                 else continue;
             }
             double Ec = Etr;
-            if (rx->tce_zeta > 0.0) Ec = (Ec + (EvP - sP->zpe)) + (EvQ - sQ->zpe);
+            if (rx->tce_zeta > 0.0) Ec = (((Ec + (EvP - sP->zpe)) + (EvQ - sQ->zpe)) + P->erot) + Q->erot;
             run = run + tce_prob(c, r, side ? P->sp : Q->sp, Ec);
             if (u_t < 0.0) {
                 o_stream st;
@@ -1325,8 +1462,9 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
             if (rx->type != ORA_DISS || rx->model == ORA_MODEL_TCE || rx->reactants[0] != A->sp) continue;
             for (int j = 0; j < sA->d.n_stretch; ++j) {
                 if (!((rx->diss_mode_mask >> j) & 1u)) continue;
-                /* Eq. Ecoll-diss */
+                /* Eq. Ecoll-diss (with gamma E_rot,A, Sec. "Rotation coupling") */
                 double Ecoll = Etr + EvA - c->rx_zpesum[r] + sA->E[j][0];
+                if (rx->gamma != 0.0) Ecoll = Ecoll + rx->gamma * A->erot;
                 double Eex = Ecoll - sA->d.De[j];
                 if (Eex > 0.0 && nch < MAX_CHANNELS) {
                     o_chan cc = { r, side, j, Eex };
@@ -1354,6 +1492,7 @@ static void process_pair(ora_ctx* c, o_res* R, uint32_t cell, uint32_t round, ui
             for (int j = 0; j < sA->n_modes; ++j) s = s + rx->alpha[j] * sA->E[j][A->qn[j]];
         }
         double Ecoll = Etr + s;
+        if (rx->gamma != 0.0) Ecoll = Ecoll + rx->gamma * A->erot;  /* Sec. "Rotation coupling" */
         double Eex = Ecoll - rx->Ea;
         if (Eex > 0.0 && nch < MAX_CHANNELS) {
             o_chan cc = { r, side, 0, Eex };
@@ -1414,6 +1553,19 @@ relax:;
         double Ec = E + EvQ;
         relax_one(c, R, sQ, Ec, &s2, Q->qn);
         E = Ec - evib(sQ, Q->qn);
+    }
+    /* classical LB rotational relaxation, P then Q (one stream) */
+    if (sP->d.rot_dof > 0 || sQ->d.rot_dof > 0) {
+        o_stream sr;
+        st_init(&sr, R->seed, R->step, cell, rk, PU_ROT);
+        for (int m = 0; m < 2; ++m) {
+            o_part* X = m ? Q : P;
+            const o_species* sX = m ? sQ : sP;
+            if (sX->d.rot_dof == 0) continue;
+            const double Ec = E + X->erot;
+            X->erot = rot_fraction(c, sX, &sr) * Ec;
+            E = Ec - X->erot;
+        }
     }
     /* isotropic VHS scattering; centre-of-mass velocity kept */
     o_stream ss;

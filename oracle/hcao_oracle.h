@@ -48,6 +48,7 @@ typedef struct {
     double De[ORA_MAX_MODES];    /* J, from the well bottom */
     int n_bend;      /* harmonic bends, modes n_stretch..n_stretch+n_bend-1 */
     double theta[ORA_MAX_MODES]; /* K */
+    int rot_dof;     /* classical rotational degrees of freedom: 0, 2 (linear) or 3 */
 } ora_species_desc;
 
 typedef struct {
@@ -65,6 +66,7 @@ typedef struct {
     double arrhenius[3];  /* TCE: A (m^3/s K^-b), b, E_a (J) of Eq. arrhenius */
     double tce_zeta;      /* TCE: internal degrees of freedom (half the pair's sum) in E_c */
     int wr_samples;       /* RECOMB, WR: sample energies (<= 0: 1000) */
+    double gamma;         /* DISS / EXCH (QK): rotation-vibration coupling, gamma E_rot,A in E_coll */
 } ora_reaction_desc;
 enum { ORA_MODEL_QK = 0, ORA_MODEL_TCE = 1 };
 enum { ORA_RPROB_EXACT = 0, ORA_RPROB_WR = 1 };
@@ -87,6 +89,19 @@ int      ora_add_reservoir(ora_ctx*, int n_cells, double cell_volume, double wei
 int      ora_load(ora_ctx*, int res, int64_t n, const double* v, const uint8_t* qn,
                   const int32_t* species, const int32_t* cell);
 int      ora_init_vibration(ora_ctx*, int res, double T_vib);
+/* Rotation (Sec. "Rotation coupling"): per particle a classical rotational
+   energy (0 after ora_load).  ora_init_rotation draws it at T_rot from the
+   equilibrium distribution Gamma(rot_dof/2) kT; ora_load_erot and
+   ora_read_erot copy it in and out in the order of ora_read_particles. */
+int      ora_init_rotation(ora_ctx*, int res, double T_rot);
+int      ora_load_erot(ora_ctx*, int res, const double* erot);
+int      ora_read_erot(ora_ctx*, int res, double* erot);
+/* the natural logarithm the oracle's rotation draws use (own series, see
+   ora_ln in the source) */
+double   ora_ln(double x);
+/* n classical LB rotational fractions of species sp (Beta(rot_dof/2,
+   (5 - 2 omega)/2)) from a Philox stream keyed by seed (test diagnostic) */
+int      ora_sample_rot_fraction(ora_ctx*, int sp, uint64_t seed, int64_t n, double* out);
 /* index of the reservoir's first cell in the random-number keys (default 0):
    a reservoir holding cells [base, base + n_cells) of a larger workload steps
    those cells exactly as the whole workload would */

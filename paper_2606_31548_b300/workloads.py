@@ -38,6 +38,7 @@ class Species:
     De: List[float] = dataclasses.field(default_factory=list)     # J per stretch
     theta: List[float] = dataclasses.field(default_factory=list)  # K per bend
     coupling_m1: float = 0.0        # stretch-bend coupling, stored, unused (reading A1)
+    rot_dof: int = 0                # classical rotational degrees of freedom (0, 2 or 3)
 
     @property
     def n_modes(self) -> int:
@@ -59,6 +60,7 @@ class Reaction:
     tce_zeta: float = 0.0           # TCE: internal DOF (half the pair's sum) in the collision energy
     recomb_prob: str = "exact"      # recomb: "exact" level sum or "wr" (Whitten-Rabinovitch)
     wr_samples: int = 1000
+    gamma: float = 0.0              # rotation-vibration coupling: gamma E_rot,A in the QK collision energy
 
 
 def triatomic() -> Species:
