@@ -81,6 +81,9 @@ typedef struct {
     const double* De;                 /* host, n_stretch, J (truncates the levels) */
     int n_bend;
     const double* theta;              /* host, n_bend, K (Theta form of Eq. energy-SHO) */
+    int rot_dof;                      /* classical rotational degrees of freedom: 0 (none), 2
+                                         (linear) or 3 (Sec. "Rotation coupling"); a rotating
+                                         species has at most 12 modes in FP32 mode */
 } hcao_species;
 
 /* One reaction (Sec. "Polyatomic QK reaction modeling").
@@ -128,6 +131,9 @@ typedef struct {
                               whose energy counts in the collision energy; 0 = translational
                               energy only */
     int wr_samples;        /* RECOMB with HCAO_RPROB_WR: sample energies (<= 0: 1000) */
+    double gamma;          /* DISS, EXCH (QK): rotation-vibration coupling in [0, 1]; the
+                              collision energies of Eq. Ecoll-diss and Eq. Ecoll-exch add
+                              gamma E_rot,A (Sec. "Rotation coupling") */
 } hcao_reaction;
 enum { HCAO_MODEL_QK = 0, HCAO_MODEL_TCE = 1 };
 enum { HCAO_RPROB_EXACT = 0, HCAO_RPROB_WR = 1 };
@@ -148,6 +154,8 @@ typedef struct {
     double E_form;                      /* sum of formation energies, J */
     double T_tr;                        /* from the peculiar translational energy, K */
     double T_vib[HCAO_MAX_SPECIES];     /* zero-point search (Sec. implementation), K */
+    double E_rot[HCAO_MAX_SPECIES];     /* sum of rotational energies, J */
+    double T_rot[HCAO_MAX_SPECIES];     /* 2 <E_rot> / (rot_dof k), K (0 without rotation) */
 } hcao_moments;
 
 typedef struct hcao_ctx hcao_ctx;
@@ -211,6 +219,23 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int res, int64_t n, const double*
    stretches drawn uniformly over 0..i_diss and accepted with
    exp(-(E_i - E_0)/(k T_vib)) (Sec. implementation, Eq. accept-quant). */
 hcao_status hcao_init_vibration(hcao_ctx* ctx, int res, double T_vib);
+
+/* Rotation (Sec. "Rotation coupling"; the paper's verification runs leave it
+   out).  Each molecule of a species with rot_dof > 0 carries a classical
+   rotational energy, 0 after hcao_load_particles.  Every accepted collision
+   that relaxes also relaxes the rotation of each rotating partner after the
+   vibrational draws, P before Q, by the classical LB draw E_rot' = x (E_rel +
+   E_rot), x ~ Beta(rot_dof/2, (5 - 2 omega)/2).  A reaction adds the
+   reactants' rotational energy to the energy it redistributes; products start
+   without rotation; a third body keeps its own.
+   hcao_init_rotation draws every rotational energy of reservoir res from the
+   equilibrium distribution at T_rot (kT times a Gamma(rot_dof/2) variate);
+   hcao_load_erot / hcao_read_erot copy them in and out (host, n doubles in
+   the order of hcao_read_particles; entries of non-rotating species are
+   ignored / 0). */
+hcao_status hcao_init_rotation(hcao_ctx* ctx, int res, double T_rot);
+hcao_status hcao_load_erot(hcao_ctx* ctx, int res, const double* host_erot);
+hcao_status hcao_read_erot(hcao_ctx* ctx, int res, double* host_erot);
 
 /* Advance every reservoir by n_steps collision phases (NTC pair selection with
    VHS cross-sections, QK reaction test and execution, HCAO LB relaxation,

@@ -909,7 +909,8 @@ StepArgs make_args(hcao_ctx* ctx) {
 // no per-pair log, every cell within FUSED_MAX_RECS slots), else the
 // per-round queue kernels.  *smem_recs: the records the fused kernel stages.
 bool fused_eligible(const hcao_ctx* ctx, int* smem_recs) {
-    if (ctx->cfg.precision != HCAO_FP32 || ctx->hc.creates || ctx->n_recomb > 0 || ctx->hc.has_tce || ctx->log_on)
+    if (ctx->cfg.precision != HCAO_FP32 || ctx->hc.creates || ctx->n_recomb > 0 || ctx->hc.has_tce ||
+        ctx->hc.has_rot || ctx->log_on)
         return false;
     uint32_t mx = 0;
     for (const auto& r : ctx->res)
@@ -1107,6 +1108,10 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
             return fail(ctx, HCAO_EINVAL, "set_species: bad species parameters");
         if ((d.n_stretch > 0 && (!d.we || !d.wexe || !d.De)) || (d.n_bend > 0 && !d.theta))
             return fail(ctx, HCAO_EINVAL, "set_species: missing mode arrays");
+        if (d.rot_dof != 0 && d.rot_dof != 2 && d.rot_dof != 3)
+            return fail(ctx, HCAO_EINVAL, "set_species: rot_dof must be 0, 2 or 3");
+        if (d.rot_dof != 0 && ctx->cfg.precision == HCAO_FP32 && d.n_stretch + d.n_bend > 12)
+            return fail(ctx, HCAO_EINVAL, "set_species: a rotating species has at most 12 modes in FP32 mode");
     }
     ctx->amode = amode;
     ctx->omega = species[0].omega;
@@ -1147,6 +1152,19 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
         D.mass = s.d.mass;
         D.mass_f = (float)s.d.mass;
         D.E_form = s.d.E_form;
+        // rotation: the maximum of the LB fraction's density shape,
+        // x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega): 1 at x = 0 for two degrees
+        // of freedom, at x = 1/2 / (1/2 + 3/2 - omega) for three
+        D.rot_dof = s.d.rot_dof;
+        if (s.d.rot_dof == 2) {
+            D.rot_fmax = 1.0;
+        } else if (s.d.rot_dof == 3) {
+            const double bb = 1.5 - ctx->omega;
+            const double xs = 0.5 / (0.5 + bb);
+            D.rot_fmax = std::sqrt(xs) * std::pow(1.0 - xs, bb);
+        }
+        D.rot_fmax_f = (float)D.rot_fmax;
+        if (s.d.rot_dof) C.has_rot = 1;
         D.zpe = s.zpe;
         D.n_modes = s.n_modes;
         D.n_stretch = s.d.n_stretch;
@@ -1312,6 +1330,9 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         D.steric = r.steric;
         D.alpha_mode = r.alpha_mode;
         D.model = r.model;
+        if (!(r.gamma >= 0.0 && r.gamma <= 1.0)) return fail(ctx, HCAO_EINVAL, "set_reactions: gamma outside [0, 1]");
+        D.gamma = r.gamma;
+        D.gamma_f = (float)r.gamma;
         if (r.model == HCAO_MODEL_TCE) {
             const double b = r.arrhenius[1], z = r.tce_zeta;
             if (!(r.arrhenius[0] >= 0.0) || !(r.arrhenius[2] >= 0.0) || !(z >= 0.0) || !(z + b + 1.5 > 0.0))
@@ -1939,9 +1960,9 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
     CU(dalloc(ctx, &doff.p, (size_t)r->n_cells + 1));
     CU(cudaMemcpyAsync(doff.p, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->cfg.precision == HCAO_FP64)
-        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, dv.p, dq.p, ds.p, dc.p, ctx->stream);
+        launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, ctx->d_consts, dv.p, dq.p, ds.p, dc.p, ctx->stream);
     else
-        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, dv.p, dq.p, ds.p, dc.p, ctx->stream);
+        launch_pack<float>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, ctx->d_consts, dv.p, dq.p, ds.p, dc.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     if (v) CU(cudaMemcpyAsync(v, dv.p, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1961,9 +1982,9 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     DevTemp<double> dacc(ctx);
     DevTemp<unsigned long long> dcnt(ctx);
     DevTemp<uint64_t> dpo(ctx);
-    CU(dalloc(ctx, &dacc.p, 5 + MAXS));
+    CU(dalloc(ctx, &dacc.p, 5 + 2 * MAXS));
     CU(dalloc(ctx, &dcnt.p, MAXS));
-    CU(cudaMemsetAsync(dacc.p, 0, sizeof(double) * (5 + MAXS), ctx->stream));
+    CU(cudaMemsetAsync(dacc.p, 0, sizeof(double) * (5 + 2 * MAXS), ctx->stream));
     CU(cudaMemsetAsync(dcnt.p, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
     uint64_t total = 0;
     hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
@@ -1976,7 +1997,7 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
                               dacc.p, dcnt.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
-    double acc[5 + MAXS];
+    double acc[5 + 2 * MAXS];
     unsigned long long cnt[MAXS];
     CU(cudaMemcpyAsync(acc, dacc.p, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(cnt, dcnt.p, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
@@ -2000,6 +2021,73 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     for (int s = 0; s < ctx->n_species; ++s)
         if (cnt[s] > 0 && ctx->sp[s].n_modes > 0)
             out->T_vib[s] = tvib_host(ctx->sp[s], acc[5 + s] / (double)cnt[s] - ctx->sp[s].zpe);
+    for (int s = 0; s < MAXS; ++s) out->E_rot[s] = acc[5 + MAXS + s];
+    for (int s = 0; s < ctx->n_species; ++s)
+        if (cnt[s] > 0 && ctx->sp[s].d.rot_dof > 0)
+            out->T_rot[s] = 2.0 * (acc[5 + MAXS + s] / (double)cnt[s]) / ((double)ctx->sp[s].d.rot_dof * KB);
+    return map_err(ctx);
+}
+
+// rotational energies in canonical order: out of the records (to_records 0)
+// or into them (1)
+hcao_status erot_copy(hcao_ctx* ctx, int id, double* host, int to_records) {
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "rotation: no loaded reservoir");
+    DevTemp<uint64_t> dpo(ctx);
+    DevTemp<double> de(ctx);
+    uint64_t total = 0;
+    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
+    if (pst != HCAO_OK) return pst;
+    if (total == 0) return map_err(ctx);
+    CU(dalloc(ctx, &de.p, (size_t)total));
+    if (to_records) CU(cudaMemcpyAsync(de.p, host, sizeof(double) * total, cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_erot<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, de.p, to_records,
+                            ctx->stream);
+    else
+        launch_erot<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, de.p, to_records,
+                           ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
+    if (!to_records) CU(cudaMemcpyAsync(host, de.p, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return map_err(ctx);
+}
+
+hcao_status hcao_read_erot(hcao_ctx* ctx, int id, double* host_erot) {
+    DeviceScope ds_(ctx);
+    LAYOUT_GUARD(ctx);
+    if (!ctx || !host_erot) return HCAO_EINVAL;
+    return erot_copy(ctx, id, host_erot, 0);
+}
+
+hcao_status hcao_load_erot(hcao_ctx* ctx, int id, const double* host_erot) {
+    DeviceScope ds_(ctx);
+    LAYOUT_GUARD(ctx);
+    SERVE_GUARD(ctx);
+    if (!ctx || !host_erot) return HCAO_EINVAL;
+    return erot_copy(ctx, id, const_cast<double*>(host_erot), 1);
+}
+
+hcao_status hcao_init_rotation(hcao_ctx* ctx, int id, double T_rot) {
+    DeviceScope ds_(ctx);
+    LAYOUT_GUARD(ctx);
+    SERVE_GUARD(ctx);
+    if (!ctx || !(T_rot >= 0.0)) return fail(ctx, HCAO_EINVAL, "init_rotation: bad arguments");
+    Reservoir* r = get_res(ctx, id);
+    if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "init_rotation: no loaded reservoir");
+    DevTemp<uint64_t> dpo(ctx);
+    uint64_t total = 0;
+    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
+    if (pst != HCAO_OK) return pst;
+    if (ctx->cfg.precision == HCAO_FP64)
+        launch_init_rot<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_res, id, ctx->d_consts,
+                                T_rot, ctx->stream);
+    else
+        launch_init_rot<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_res, id, ctx->d_consts,
+                               T_rot, ctx->stream);
+    ctx->launches++;
+    CU(cudaGetLastError());
     return map_err(ctx);
 }
 

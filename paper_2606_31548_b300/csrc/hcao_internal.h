@@ -35,7 +35,7 @@ inline int setup_launches(int n_cells) { return setup_tiles(n_cells) == 1 ? 1 : 
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
-       PU_INIT = 7, PU_REC = 9, PU_TCE = 10 };
+       PU_INIT = 7, PU_REC = 9, PU_TCE = 10, PU_ROT = 11, PU_ROTINIT = 12 };
 constexpr int TCE_NT = 4096;    // TCE probability tables: NT + 1 points per (reaction, partner species)
 
 // per-reservoir counters
@@ -51,6 +51,8 @@ enum { ERR_REJECT = 1, ERR_CAPACITY = 2, ERR_ROUNDS = 4, ERR_LEVEL = 8, ERR_NONF
 constexpr uint32_t SPECIES_NONE = 0xFFu;
 
 // Particle records.  FP32: 32 bytes (one sector); FP64: 64 bytes (two sectors).
+// A rotating species' classical rotational energy: FP32, the float in q[3]
+// (such species have at most 12 modes); FP64, erot.
 struct alignas(16) RecF {
     float v[3];
     uint32_t meta;        // species in bits 0..7
@@ -61,7 +63,8 @@ struct alignas(16) RecD {
     uint32_t meta;
     uint32_t pad;
     uint32_t q[4];
-    uint32_t pad2[4];
+    double erot;
+    uint32_t pad2[2];
 };
 static_assert(sizeof(RecF) == 32, "RecF layout");
 static_assert(sizeof(RecD) == 64, "RecD layout");
@@ -84,6 +87,11 @@ struct DevSpecies {
     // FP32-mode bookkeeping in int64 fixed point (1 unit = 2^-100 J)
     long long zpe_fix, top_fix;
     long long De_fix[MAXM];
+    // rotation: classical degrees of freedom (0, 2, 3) and the maximum of the
+    // LB fraction's density shape x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega)
+    int rot_dof, pad_r;
+    double rot_fmax;
+    float rot_fmax_f, pad_rf;
 };
 
 // FP32 K5 table entry of (species, mode k, bucket m), parallel to the float
@@ -124,11 +132,13 @@ struct DevReaction {
     double Ea, steric, zpesum, dEf;
     double alpha[MAXM];
     long long Ea_fix, zpesum_fix, dEf_fix;   // FP32 mode (2^-100 J units)
+    double gamma;                    // rotation-vibration coupling: gamma E_rot,A in the QK E_coll
+    float gamma_f, pad_gf;
 };
 
 struct Consts {
     int n_species, n_reactions, amode, creates;
-    int has_recomb, has_tce, pad_c[2];
+    int has_recomb, has_tce, has_rot, pad_c;
     int rec_pair[MAXS * MAXS];       // species pair -> recombination | side << 3, or -1
     DevSpecies sp[MAXS];
     DevPair pair[MAXS * MAXS];
@@ -233,8 +243,16 @@ template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm
                                             int n_cells, const double* v, const uint8_t* qn,
                                             const int32_t* sp, int64_t n, cudaStream_t s);
 template <class R> void launch_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
-                                    uint64_t total, double* v, uint8_t* qn, int32_t* sp,
+                                    uint64_t total, const Consts* C, double* v, uint8_t* qn, int32_t* sp,
                                     int32_t* cell, cudaStream_t s);
+// rotational energies out of / into the records (canonical order), and
+// their initialisation at T_rot
+template <class R> void launch_erot(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                                    uint64_t total, const Consts* C, double* host_order_erot, int to_records,
+                                    cudaStream_t s);
+template <class R> void launch_init_rot(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+                                        uint64_t total, const DevRes* res, int res_slot, const Consts* C,
+                                        double T_rot, cudaStream_t s);
 template <class R> void launch_init_vib(const DevCell* cells, int cell0, int n_cells,
                                         const uint64_t* off, uint64_t total, const DevRes* res,
                                         int res_slot, const Consts* C, const double* bend_thr,

@@ -210,6 +210,9 @@ __device__ __forceinline__ void load_rec(const RecD* p, RecD& r) {
     r.v[2] = __hiloint2double((int)b.y, (int)b.x);
     r.meta = b.z; r.pad = 0;
     r.q[0] = c.x; r.q[1] = c.y; r.q[2] = c.z; r.q[3] = c.w;
+    const uint4 e = s[3];
+    r.erot = __hiloint2double((int)e.y, (int)e.x);
+    r.pad2[0] = r.pad2[1] = 0u;
 }
 __device__ __forceinline__ void store_rec(RecD* p, const RecD& r) {
     uint4* d = reinterpret_cast<uint4*>(p);
@@ -218,6 +221,64 @@ __device__ __forceinline__ void store_rec(RecD* p, const RecD& r) {
     d[0] = make_uint4((uint32_t)v0, (uint32_t)(v0 >> 32), (uint32_t)v1, (uint32_t)(v1 >> 32));
     d[1] = make_uint4((uint32_t)v2, (uint32_t)(v2 >> 32), r.meta, 0u);
     d[2] = make_uint4(r.q[0], r.q[1], r.q[2], r.q[3]);
+    const unsigned long long e = __double_as_longlong(r.erot);
+    d[3] = make_uint4((uint32_t)e, (uint32_t)(e >> 32), 0u, 0u);
+}
+
+// ------------------------------------------------------------- rotation
+// A molecule's classical rotational energy (Sec. "Rotation coupling"): FP64
+// records hold it as a double, FP32 records as the float in q[3] (rotating
+// species have at most 12 modes).
+__device__ __forceinline__ float erot_f(const uint32_t q[4]) { return __uint_as_float(q[3]); }
+// the FP64 record's rotational energy (0 for a species that does not rotate);
+// the FP32 overloads serve only code paths that FP32 mode never runs
+__device__ __forceinline__ double rec_erot(const RecD& r) { return r.erot; }
+__device__ __forceinline__ double rec_erot(const RecF&) { return 0.0; }
+__device__ __forceinline__ void rec_set_erot(RecD& r, double e) { r.erot = e; }
+__device__ __forceinline__ void rec_set_erot(RecF&, double) {}
+// a record's rotational energy in either precision (readouts)
+__device__ __forceinline__ double rec_erot_of(const RecD& r, const DevSpecies&) { return r.erot; }
+__device__ __forceinline__ double rec_erot_of(const RecF& r, const DevSpecies& S) {
+    return S.rot_dof ? (double)erot_f(r.q) : 0.0;
+}
+__device__ __forceinline__ void rec_put_erot(RecD& r, const DevSpecies& S, double e) { r.erot = S.rot_dof ? e : 0.0; }
+__device__ __forceinline__ void rec_put_erot(RecF& r, const DevSpecies& S, double e) {
+    if (S.rot_dof) r.q[3] = __float_as_uint((float)e);
+}
+
+// Natural logarithm for x > 0 (normal doubles), the draws of the initial
+// rotation: x = m 2^e with m in [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s),
+// s = (m - 1)/(m + 1), by the atanh series to s^25, plus e ln 2; every
+// operation rounded as written.
+__device__ __forceinline__ double ln_series(double x) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((u >> 52) & 0x7FF) - 1022;
+    u = (u & 0x000FFFFFFFFFFFFFull) | 0x3FE0000000000000ull;
+    double m = __longlong_as_double((long long)u);
+    if (m < 0.70710678118654752440) { m = __dmul_rn(m, 2.0); e = e - 1; }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double s2 = __dmul_rn(s, s);
+    double t = __ddiv_rn(1.0, 25.0);
+    for (int k = 23; k >= 1; k -= 2) t = __dadd_rn(__ddiv_rn(1.0, (double)k), __dmul_rn(s2, t));
+    return __dadd_rn(__dmul_rn(__dmul_rn(2.0, s), t), __dmul_rn((double)e, 0.69314718055994530942));
+}
+
+// The classical LB fraction x ~ Beta(rot_dof/2, (5 - 2 omega)/2) of the
+// energy a rotating molecule keeps: rejection under the maximum of the
+// density shape x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega), square roots only.
+template <class R>
+__device__ __forceinline__ R rot_fraction(const StepArgs& A, const DevSpecies& S, int amode, Stream& st) {
+    for (uint32_t it = 0; it < A.reject_cap; ++it) {
+        const R x = st_uni<R>(st);
+        const R y = st_uni<R>(st);
+        R f = lb_pow<R>(amode, sub_rn((R)1, x));
+        if (S.rot_dof == 3) f = mul_rn(f, sqrt_rn(x));
+        R fm;
+        if constexpr (std::is_same<R, double>::value) fm = S.rot_fmax;
+        else fm = S.rot_fmax_f;
+        if (mul_rn(y, fm) < f) return x;
+    }
+    return (R)0.5;
 }
 
 // ------------------------------------------------------------- tables
@@ -423,7 +484,8 @@ struct PairOut {
 template <class R>
 __device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& rx, double vA[3],
                         double vM[3], int spA, int spM, double EvA, const DevRes& rs, uint32_t lcell,
-                        uint32_t rk, uint32_t qB[4], uint32_t qC[4], double vC[3], PairOut& o) {
+                        uint32_t rk, uint32_t qB[4], uint32_t qC[4], double vC[3], PairOut& o,
+                        double erA = 0.0) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sM = C->sp[spM];
     const DevSpecies& sB = C->sp[rx.P0];
@@ -438,7 +500,7 @@ __device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& r
     const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
     const double KEin = 0.5 * mA * vA2 + 0.5 * mM * vM2;
     const double KEcm = 0.5 * mt * V2;
-    const double Eav = KEin - KEcm + EvA - rx.dEf;
+    const double Eav = KEin - KEcm + EvA - rx.dEf + erA;  // A's rotation joins the pool
     if (!(Eav - sB.zpe - sC.zpe > 0.0) || Eav - sC.zpe > sB.top || Eav - sB.zpe > sC.top)
         return false;
     Stream sa, sb, ss;
@@ -499,7 +561,8 @@ __device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& r
 template <class R>
 __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& rx, double vA[3],
                         double vB[3], int spA, int spB, double EvA, double EvB, const DevRes& rs,
-                        uint32_t lcell, uint32_t rk, uint32_t qC[4], uint32_t qD[4], PairOut& o) {
+                        uint32_t lcell, uint32_t rk, uint32_t qC[4], uint32_t qD[4], PairOut& o,
+                        double erA = 0.0, double erB = 0.0) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sB = C->sp[spB];
     const DevSpecies& sC = C->sp[rx.P0];
@@ -513,7 +576,7 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
     const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
     const double KEin = 0.5 * mA * vA2 + 0.5 * mB * vB2;
     const double KEcm = 0.5 * mt * V2;
-    const double Eav = KEin - KEcm + EvA + EvB - rx.dEf;
+    const double Eav = (KEin - KEcm + EvA + EvB - rx.dEf + erA) + erB;  // rotation joins the pool
     if (!(Eav - sC.zpe - sD.zpe > 0.0) || Eav - sD.zpe > sC.top || Eav - sC.zpe > sD.top)
         return false;
     Stream sa, sb, ss;
@@ -562,7 +625,8 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
 template <class R>
 __device__ bool do_recomb(const StepArgs& A, const Consts* C, const DevReaction& rx, double vB[3],
                           double vC[3], double vM[3], int spB, int spC, int spM, double EvB, double EvC,
-                          const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t qA[4], PairOut& o) {
+                          const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t qA[4], PairOut& o,
+                          double erB = 0.0, double erC = 0.0) {
     const DevSpecies& sA = C->sp[rx.P0];
     const DevSpecies& sB = C->sp[spB];
     const DevSpecies& sC = C->sp[spC];
@@ -577,7 +641,7 @@ __device__ bool do_recomb(const StepArgs& A, const Consts* C, const DevReaction&
     const double V2 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
     const double KEin = (0.5 * mB * vB2 + 0.5 * mC * vC2) + 0.5 * mM * vM2;
     const double KEcm = 0.5 * mt * V2;
-    const double Eav = KEin - KEcm + EvB + EvC - rx.dEf;
+    const double Eav = (KEin - KEcm + EvB + EvC - rx.dEf + erB) + erC;  // rotation joins the pool
     if (!(Eav - sA.zpe > 0.0) || Eav > sA.top) return false;
     Stream sa, ss;
     st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
@@ -717,7 +781,8 @@ __device__ __forceinline__ double tce_prob(const StepArgs& A, const DevReaction&
 // internal degrees of freedom.  Returns true with the channel in chan.
 template <class R>
 __device__ bool tce_test(const StepArgs& A, const Consts* __restrict__ C, const DevRes& rs, uint32_t lcell,
-                         uint32_t rk, int sP, int sQ, double Etr, double EvP, double EvQ, uint32_t& chan) {
+                         uint32_t rk, int sP, int sQ, double Etr, double EvP, double EvQ, uint32_t& chan,
+                         double erP = 0.0, double erQ = 0.0) {
     double run = 0.0, u = -1.0;
     for (int ri = 0; ri < C->n_reactions; ++ri) {
         const DevReaction& rx = C->rx[ri];
@@ -733,8 +798,9 @@ __device__ bool tce_test(const StepArgs& A, const Consts* __restrict__ C, const 
             else continue;
         }
         double Ec = Etr;
-        if (rx.tce_zeta_on)
-            Ec = __dadd_rn(__dadd_rn(Ec, __dsub_rn(EvP, C->sp[sP].zpe)), __dsub_rn(EvQ, C->sp[sQ].zpe));
+        if (rx.tce_zeta_on)  // internal energy: vibration above the ZPE and rotation of both
+            Ec = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(Ec, __dsub_rn(EvP, C->sp[sP].zpe)),
+                                               __dsub_rn(EvQ, C->sp[sQ].zpe)), erP), erQ);
         run = __dadd_rn(run, tce_prob(A, rx, side ? sP : sQ, Ec));
         if (u < 0.0) {
             Stream st;
@@ -755,7 +821,8 @@ __device__ bool tce_test(const StepArgs& A, const Consts* __restrict__ C, const 
 template <class R>
 __device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
                              const uint32_t qP[4], const uint32_t qQ[4], double Etr, double EvP,
-                             double EvQ, double u_ster, double u_sel, double u_ch, uint32_t& chan) {
+                             double EvQ, double u_ster, double u_sel, double u_ch, uint32_t& chan,
+                             double erP = 0.0, double erQ = 0.0) {
     const DevSpecies& SP = C->sp[sP];
     const DevSpecies& SQ = C->sp[sQ];
     int nch = 0;
@@ -779,7 +846,9 @@ __device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, in
                     if (!((rx.mask >> j) & 1u)) continue;
                     // Eq. Ecoll-diss: ZPEs of A, B, C removed, the breaking mode's restored
                     const double E0j = __ldg(A.lev64 + SA.lev_off[j]);
-                    const double Ecoll = Etr + EvA - rx.zpesum + E0j;
+                    double Ecoll = Etr + EvA - rx.zpesum + E0j;
+                    // rotation coupling (Sec. "Rotation coupling"): gamma E_rot,A
+                    if (rx.gamma != 0.0) Ecoll = Ecoll + rx.gamma * (side ? erQ : erP);
                     const double Eex = Ecoll - SA.De[j];
                     if (!(Eex > 0.0)) continue;
                     const uint32_t id = chan_pack(ri, side, j);
@@ -810,7 +879,8 @@ __device__ int reaction_pick(const StepArgs& A, const Consts* __restrict__ C, in
                 for (int j = 0; j < SA.n_modes; ++j)
                     s = s + rx.alpha[j] * __ldg(A.lev64 + SA.lev_off[j] + get_q(qa, j));
             }
-            const double Ecoll = Etr + s;
+            double Ecoll = Etr + s;
+            if (rx.gamma != 0.0) Ecoll = Ecoll + rx.gamma * (side ? erQ : erP);
             const double Eex = Ecoll - rx.Ea;
             if (!(Eex > 0.0)) continue;
             const uint32_t id = chan_pack(ri, side, 0);
@@ -1044,7 +1114,7 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
 static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const Consts* __restrict__ C, int sP, int sQ,
                                  const uint32_t qP[4], const uint32_t qQ[4], long long Etr,
                                  long long EvP, long long EvQ, float u_ster, float u_sel, float u_ch,
-                                 uint32_t& chan) {
+                                 uint32_t& chan, float erP = 0.f, float erQ = 0.f) {
     const DevSpecies& SP = C->sp[sP];
     const DevSpecies& SQ = C->sp[sQ];
     int nch = 0;
@@ -1068,7 +1138,8 @@ static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const
                 const long long base = Etr + EvA - rx.zpesum_fix;
                 for (int j = 0; j < SA.n_stretch; ++j) {
                     if (!((rx.mask >> j) & 1u)) continue;
-                    const long long Eex = base + __ldg(A.levfix + SA.lev_off[j]) - SA.De_fix[j];
+                    long long Eex = base + __ldg(A.levfix + SA.lev_off[j]) - SA.De_fix[j];
+                    if (rx.gamma != 0.0) Eex += f2fix(__fmul_rn(rx.gamma_f, side ? erQ : erP));
                     if (Eex <= 0) continue;
                     const uint32_t id = chan_pack(ri, side, j);
                     if (pass == 0) { nch++; tot += Eex; last = id; }
@@ -1101,7 +1172,8 @@ static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const
                     sd = sd + rx.alpha[j] * (double)__ldg(A.levfix + SA.lev_off[j] + get_q(qa, j));
                 s = __double2ll_rn(sd);
             }
-            const long long Eex = Etr + s - rx.Ea_fix;
+            long long Eex = Etr + s - rx.Ea_fix;
+            if (rx.gamma != 0.0) Eex += f2fix(__fmul_rn(rx.gamma_f, side ? erQ : erP));
             if (Eex <= 0) continue;
             const uint32_t id = chan_pack(ri, side, 0);
             if (pass == 0) { nch++; tot += Eex; last = id; }
@@ -1121,7 +1193,7 @@ static __device__ __forceinline__ int reaction_pick_fix(const StepArgs& A, const
 static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
                             float vA[3], float vM[3], int spA, int spM, long long EvA, const DevRes& rs,
                             uint32_t lcell, uint32_t rk, uint32_t (&qB)[4], uint32_t (&qC)[4],
-                            float vC[3], PairOut& o) {
+                            float vC[3], PairOut& o, float erA = 0.f) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sM = C->sp[spM];
     const DevSpecies& sB = C->sp[rx.P0];
@@ -1137,7 +1209,7 @@ static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__
     }
     const float g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
     const long long Ein = f2fix(0.5f * C->pair[spA * MAXS + spM].mr_f * g2);
-    const long long Eav = Ein + EvA - rx.dEf_fix;
+    const long long Eav = Ein + EvA - rx.dEf_fix + f2fix(erA);  // A's rotation joins the pool
     if (!(Eav - sB.zpe_fix - sC.zpe_fix > 0) || Eav - sC.zpe_fix > sB.top_fix ||
         Eav - sB.zpe_fix > sC.top_fix)
         return false;
@@ -1183,7 +1255,7 @@ static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__
 static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__ C, const DevReaction& rx,
                             float vA[3], float vB[3], int spA, int spB, long long EvA, long long EvB,
                             const DevRes& rs, uint32_t lcell, uint32_t rk, uint32_t (&qC)[4],
-                            uint32_t (&qD)[4], PairOut& o) {
+                            uint32_t (&qD)[4], PairOut& o, float erA = 0.f, float erB = 0.f) {
     const DevSpecies& sA = C->sp[spA];
     const DevSpecies& sB = C->sp[spB];
     const DevSpecies& sC = C->sp[rx.P0];
@@ -1193,7 +1265,7 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     float V[3];
     for (int i = 0; i < 3; ++i) V[i] = __fdiv_rn(__fadd_rn(__fmul_rn(mA, vA[i]), __fmul_rn(mB, vB[i])), mAB);
     const long long Ein = etr_fix_f32(C->pair[spA * MAXS + spB], g2_f32(vA, vB));
-    const long long Eav = Ein + EvA + EvB - rx.dEf_fix;
+    const long long Eav = Ein + EvA + EvB - rx.dEf_fix + f2fix(erA) + f2fix(erB);
     if (!(Eav - sC.zpe_fix - sD.zpe_fix > 0) || Eav - sD.zpe_fix > sC.top_fix ||
         Eav - sC.zpe_fix > sD.top_fix)
         return false;
@@ -1224,7 +1296,7 @@ static __device__ bool do_recomb_fix(const StepArgs& A, const Consts* __restrict
                                      const DevReaction& rx, float vB[3], float vC[3], float vM[3],
                                      int spB, int spC, int spM, long long EvB, long long EvC,
                                      const DevRes& rs, uint32_t lcell, uint32_t rk,
-                                     uint32_t (&qA)[4], PairOut& o) {
+                                     uint32_t (&qA)[4], PairOut& o, float erB = 0.f, float erC = 0.f) {
     const DevSpecies& sA = C->sp[rx.P0];
     const float mB = C->sp[spB].mass_f, mC = C->sp[spC].mass_f, mM = C->sp[spM].mass_f;
     const float m3 = (mB + mC) + mM;
@@ -1238,7 +1310,7 @@ static __device__ bool do_recomb_fix(const StepArgs& A, const Consts* __restrict
         eM += m * m;
     }
     const long long Ein = f2fix(0.5f * mB * eB) + f2fix(0.5f * mC * eC) + f2fix(0.5f * mM * eM);
-    const long long Eav = Ein + EvB + EvC - rx.dEf_fix;
+    const long long Eav = Ein + EvB + EvC - rx.dEf_fix + f2fix(erB) + f2fix(erC);
     if (!(Eav - sA.zpe_fix > 0) || Eav > sA.top_fix) return false;
     Stream sa, sb, ss;
     st_init(sa, rs.seed, rs.step, lcell, rk, PU_LB_A);
@@ -1390,6 +1462,20 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
         }
     }
     o.trials += tr;
+    // classical LB rotational relaxation, P then Q, one stream per pair
+    if (SP.rot_dof > 0 || SQ.rot_dof > 0) {
+        Stream sr;
+        st_init(sr, rs.seed, rs.step, L.lcell, L.rk, PU_ROT);
+        for (int m = 0; m < 2; ++m) {
+            Rec& X = m ? Qr : Pr;
+            const DevSpecies& SX = m ? SQ : SP;
+            if (SX.rot_dof == 0) continue;
+            const double Ec = E + rec_erot(X);
+            const double er = rot_fraction<double>(A, SX, amode, sr) * Ec;
+            rec_set_erot(X, er);
+            E = Ec - er;
+        }
+    }
     }
     Stream ss;
     st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
@@ -1421,15 +1507,45 @@ __device__ void relax_scatter(const StepArgs& A, const Consts* __restrict__ C, c
 
 // FP32 mode: relaxation (flattened sampler, fixed-point bookkeeping) and
 // isotropic scattering with the centre-of-mass velocity kept.
+// FP32 classical LB rotational relaxation of a pair's rotating molecules, P
+// then Q (one stream): energies in fixed point, the new rotational energy a
+// float stored in q[3]; erP, erQ the rotational energies before the
+// collision.  Returns the relative energy left.
+__device__ __forceinline__ long long rot_relax_fix(const StepArgs& A, const Consts* __restrict__ C, uint64_t seed,
+                                                   uint32_t step, uint32_t lcell, uint32_t rk, int sP, int sQ,
+                                                   float erP, float erQ, uint32_t (&qP)[4], uint32_t (&qQ)[4],
+                                                   long long E) {
+    const DevSpecies& SP = C->sp[sP];
+    const DevSpecies& SQ = C->sp[sQ];
+    if (SP.rot_dof == 0 && SQ.rot_dof == 0) return E;
+    Stream sr;
+    st_init(sr, seed, step, lcell, rk, PU_ROT);
+    if (SP.rot_dof > 0) {
+        const long long Ec = E + f2fix(erP);
+        const float e = __fmul_rn(rot_fraction<float>(A, SP, C->amode, sr), fix2f(Ec));
+        qP[3] = __float_as_uint(e);
+        E = Ec - f2fix(e);
+    }
+    if (SQ.rot_dof > 0) {
+        const long long Ec = E + f2fix(erQ);
+        const float e = __fmul_rn(rot_fraction<float>(A, SQ, C->amode, sr), fix2f(Ec));
+        qQ[3] = __float_as_uint(e);
+        E = Ec - f2fix(e);
+    }
+    return E;
+}
+
 __device__ __forceinline__ void relax_scatter_fix(const StepArgs& A, const Consts* __restrict__ C,
                                                   const DevRes& rs, const PairLoc& L, RecF& Pr,
                                                   RecF& Qr, const DevPair& pc, long long Etr,
                                                   long long EvP, long long EvQ, PairOut& o) {
     const int sP = (int)(Pr.meta & 0xFFu), sQ = (int)(Qr.meta & 0xFFu);
+    const float erP = C->sp[sP].rot_dof ? erot_f(Pr.q) : 0.f, erQ = C->sp[sQ].rot_dof ? erot_f(Qr.q) : 0.f;
     Stream s1, s2;
     st_init(s1, rs.seed, rs.step, L.lcell, L.rk, PU_LB_A);
     st_init(s2, rs.seed, rs.step, L.lcell, L.rk, PU_LB_B);
-    const long long E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
+    long long E = relax_flat(A, C, sP, Pr.q, EvP, s1, sQ, Qr.q, EvQ, s2, Etr, o);
+    E = rot_relax_fix(A, C, rs.seed, rs.step, L.lcell, L.rk, sP, sQ, erP, erQ, Pr.q, Qr.q, E);
     Stream ss;
     st_init(ss, rs.seed, rs.step, L.lcell, L.rk, PU_SCAT);
     float d[3];
@@ -1901,7 +2017,8 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
                 A.qB[slot] = make_uint4((uint32_t)c, e.y, rchan, mpos);
                 continue;
             }
-            if (C->has_tce && tce_test<R>(A, C, rs, L.lcell, L.rk, sP, sQ, Etr, EvP, EvQ, rchan)) {
+            if (C->has_tce && tce_test<R>(A, C, rs, L.lcell, L.rk, sP, sQ, Etr, EvP, EvQ, rchan, rec_erot(Pr),
+                                          rec_erot(Qr))) {
                 const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
                 A.qB[slot] = make_uint4((uint32_t)c, e.y, rchan, 0u);
                 continue;
@@ -1914,7 +2031,7 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
             const double u_ch = st_u64(sp);
             uint32_t chan = 0u;
             const int nch = reaction_pick<R>(A, C, sP, sQ, Pr.q, Qr.q, Etr, EvP, EvQ, u_ster, u_sel,
-                                             u_ch, chan);
+                                             u_ch, chan, rec_erot(Pr), rec_erot(Qr));
             if (nch > 0) {
                 const uint32_t slot = queue_slot(A.qsize + 2 * r + 1, true);
                 A.qB[slot] = make_uint4((uint32_t)c, e.y, chan, 0u);
@@ -1966,6 +2083,8 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
         const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
         const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
+        const float erP = C->sp[sP].rot_dof ? __uint_as_float(qa.w) : 0.f;
+        const float erQ = C->sp[sQ].rot_dof ? __uint_as_float(qb.w) : 0.f;
         // reaction tests (recombination, then the QK channels in fixed point);
         // a reacting pair goes to the reaction queue instead
         bool react = false;
@@ -1975,7 +2094,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
             if (C->has_recomb && recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sgf, chan, mpos)) {
                 react = true;
             } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
-                                                     fix2d(EvQ), chan)) {
+                                                     fix2d(EvQ), chan, (double)erP, (double)erQ)) {
                 react = true;
             } else {
                 Stream sp;
@@ -1984,7 +2103,8 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
                 const float u_ster = st_u32(sp);
                 const float u_sel = st_u32(sp);
                 const float u_ch = st_u32(sp);
-                react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan) > 0;
+                react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan, erP,
+                                          erQ) > 0;
             }
         }
         const uint32_t rslot = queue_slot(A.qsize + 2 * r + 1, react);
@@ -2016,6 +2136,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         }
         w_samp += (uint32_t)nmol;
         w_pair++;
+        if (C->has_rot) Erel = rot_relax_fix(A, C, rs.seed, step, lcell, rk, sP, sQ, erP, erQ, qP, qQ, Erel);
         Stream ss;
         st_init(ss, rs.seed, step, lcell, rk, PU_SCAT);
         float d[3];
@@ -2080,6 +2201,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
             RecF& RB = side ? Pr : Qr;
             for (int i = 0; i < 3; ++i) { vA[i] = RA.v[i]; vB[i] = RB.v[i]; }
             const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
+            const float erA = C->sp[spA].rot_dof ? erot_f(RA.q) : 0.f, erB = C->sp[spB].rot_dof ? erot_f(RB.q) : 0.f;
             uint32_t q1[4], q2[4];
             bool done;
             if (rx.type == HCAO_RECOMB) {
@@ -2089,7 +2211,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
                 load_rec(recs + iM, Mr);
                 float vM[3] = {Mr.v[0], Mr.v[1], Mr.v[2]};
                 done = do_recomb_fix(A, C, rx, vA, vB, vM, spA, spB, (int)(Mr.meta & 0xFFu),
-                                     side ? EvQ : EvP, side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o);
+                                     side ? EvQ : EvP, side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o, erA, erB);
                 lr.aux = (uint32_t)side + 2u * iM;
                 if (done) {
                     for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; Mr.v[i] = vM[i]; }
@@ -2103,7 +2225,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
                 }
             } else if (rx.type == HCAO_DISS) {
                 done = do_diss_fix(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
-                                   vN, o);
+                                   vN, o, erA);
                 lr.aux = (uint32_t)mode + (side ? 16u : 0u);
                 if (done) {
                     for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; RB.v[i] = vB[i]; }
@@ -2118,7 +2240,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
                 }
             } else {
                 done = do_exch_fix(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, side ? EvP : EvQ, rs,
-                                   L.lcell, L.rk, q1, q2, o);
+                                   L.lcell, L.rk, q1, q2, o, erA, erB);
                 lr.aux = (uint32_t)side;
                 if (done) {
                     for (int i = 0; i < 3; ++i) { RA.v[i] = vA[i]; RB.v[i] = vB[i]; }
@@ -2154,6 +2276,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
         Rec& RB = side ? Pr : Qr;
         for (int i = 0; i < 3; ++i) { vA[i] = (double)RA.v[i]; vB[i] = (double)RB.v[i]; }
         const int spA = (int)(RA.meta & 0xFFu), spB = (int)(RB.meta & 0xFFu);
+        const double erA = rec_erot(RA), erB = rec_erot(RB);
         uint32_t q1[4], q2[4];
         bool done;
         if (rx.type == HCAO_RECOMB) {
@@ -2163,13 +2286,15 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
             load_rec(recs + iM, Mr);
             double vM[3] = {(double)Mr.v[0], (double)Mr.v[1], (double)Mr.v[2]};
             done = do_recomb<R>(A, C, rx, vA, vB, vM, spA, spB, (int)(Mr.meta & 0xFFu), side ? EvQ : EvP,
-                                side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o);
+                                side ? EvP : EvQ, rs, L.lcell, L.rk, q1, o, erA, erB);
             lr.aux = (uint32_t)side + 2u * iM;
             if (done) {
                 for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; Mr.v[i] = (R)vM[i]; }
                 RA.meta = (uint32_t)rx.P0;
                 for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                rec_set_erot(RA, 0.0);  // products start without rotation; M keeps its own
                 RB.meta = SPECIES_NONE;
+                rec_set_erot(RB, 0.0);
                 store_rec(recs + iM, Mr);
                 reinterpret_cast<uint32_t*>(reinterpret_cast<Rec*>(A.cscratch) + L.ev_idx)[0] =
                     side ? L.ip : L.iq;
@@ -2177,7 +2302,7 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
             }
         } else if (rx.type == HCAO_DISS) {
             done = do_diss<R>(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, rs, L.lcell, L.rk, q1, q2,
-                              vN, o);
+                              vN, o, erA);
             lr.aux = (uint32_t)mode + (side ? 16u : 0u);
             if (done) {
                 // A becomes B in place; M keeps its state; C goes to the pair's
@@ -2185,23 +2310,26 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
                 for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
                 RA.meta = (uint32_t)rx.P0;
                 for (int j = 0; j < 4; ++j) RA.q[j] = q1[j];
+                rec_set_erot(RA, 0.0);
                 Rec RN;
                 for (int i = 0; i < 3; ++i) RN.v[i] = (R)vN[i];
                 RN.meta = (uint32_t)rx.P1;
                 for (int j = 0; j < 4; ++j) RN.q[j] = q2[j];
-                if constexpr (std::is_same<R, double>::value) { RN.pad = 0; }
+                if constexpr (std::is_same<R, double>::value) { RN.pad = 0; RN.erot = 0.0; }
                 store_rec(reinterpret_cast<Rec*>(A.cscratch) + L.ev_idx, RN);
                 o.ev |= EV_CREATED;
             }
         } else {
             done = do_exch<R>(A, C, rx, vA, vB, spA, spB, side ? EvQ : EvP, side ? EvP : EvQ, rs,
-                              L.lcell, L.rk, q1, q2, o);
+                              L.lcell, L.rk, q1, q2, o, erA, erB);
             lr.aux = (uint32_t)side;
             if (done) {
                 for (int i = 0; i < 3; ++i) { RA.v[i] = (R)vA[i]; RB.v[i] = (R)vB[i]; }
                 RA.meta = (uint32_t)rx.P0;
                 RB.meta = (uint32_t)rx.P1;
                 for (int j = 0; j < 4; ++j) { RA.q[j] = q1[j]; RB.q[j] = q2[j]; }
+                rec_set_erot(RA, 0.0);
+                rec_set_erot(RB, 0.0);
             }
         }
         if (done) {
@@ -2627,7 +2755,7 @@ __device__ __forceinline__ int cell_of64(const uint64_t* off, int n_cells, uint6
 }
 
 template <class R>
-__global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
+__global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off, const Consts* C,
                        double* v, uint8_t* qn, int32_t* sp, int32_t* cell) {
     using Rec = typename RecOf<R>::T;
     const uint64_t total = off[n_cells];
@@ -2640,7 +2768,10 @@ __global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint6
         if (v) for (int d = 0; d < 3; ++d) v[3 * j + d] = (double)r.v[d];
         if (qn) {
             uint32_t* q = reinterpret_cast<uint32_t*>(qn + 16 * j);
-            for (int w = 0; w < 4; ++w) q[w] = r.q[w];
+            const int s = (int)(r.meta & 0xFFu);
+            // an FP32 record's q[3] holds a rotating species' rotational energy
+            const bool rot_word = std::is_same<R, float>::value && s < MAXS && C->sp[s].rot_dof;
+            for (int w = 0; w < 4; ++w) q[w] = (w == 3 && rot_word) ? 0u : r.q[w];
         }
         if (sp) sp[j] = (int32_t)(r.meta & 0xFFu);
         if (cell) cell[j] = c;
@@ -2705,16 +2836,16 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
                                                  const Consts* C, const double* lev64, double* acc,
                                                  unsigned long long* cnt) {
     using Rec = typename RecOf<R>::T;
-    __shared__ double sacc[5 + MAXS];
+    __shared__ double sacc[5 + 2 * MAXS];
     __shared__ unsigned long long scnt[MAXS];
-    for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) sacc[i] = 0.0;
+    for (int i = threadIdx.x; i < 5 + 2 * MAXS; i += blockDim.x) sacc[i] = 0.0;
     for (int i = threadIdx.x; i < MAXS; i += blockDim.x) scnt[i] = 0ull;
     __syncthreads();
     double px = 0.0, py = 0.0, pz = 0.0, etr = 0.0, ef = 0.0;
-    double ev[MAXS];
+    double ev[MAXS], er[MAXS];
     uint32_t nc[MAXS];
 #pragma unroll
-    for (int k = 0; k < MAXS; ++k) { ev[k] = 0.0; nc[k] = 0u; }
+    for (int k = 0; k < MAXS; ++k) { ev[k] = 0.0; er[k] = 0.0; nc[k] = 0u; }
     const uint64_t total = off[n_cells];
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
          j += (uint64_t)gridDim.x * blockDim.x) {
@@ -2733,9 +2864,10 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
         etr += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         ef += S.E_form;
         const double e = evib64(lev64, S, r.q);
+        const double erot = rec_erot_of(r, S);
 #pragma unroll
         for (int k = 0; k < MAXS; ++k)
-            if (s == k) { ev[k] += e; nc[k]++; }
+            if (s == k) { ev[k] += e; er[k] += erot; nc[k]++; }
     }
     const int lane = threadIdx.x & 31;
     auto wsum = [](double x) {
@@ -2752,15 +2884,84 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
         const unsigned any = __ballot_sync(0xFFFFFFFFu, nc[k] != 0u);
         if (any == 0u) continue;  // uniform over the warp
         const double x = wsum(ev[k]);
+        const double y = wsum(er[k]);
         const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, nc[k]);
         if (lane == 0) {
             atomicAdd(&sacc[5 + k], x);
+            if (y != 0.0) atomicAdd(&sacc[5 + MAXS + k], y);
             atomicAdd(&scnt[k], (unsigned long long)n);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 5 + MAXS; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
+    for (int i = threadIdx.x; i < 5 + 2 * MAXS; i += blockDim.x) atomicAdd(&acc[i], sacc[i]);
     for (int i = threadIdx.x; i < MAXS; i += blockDim.x) atomicAdd(&cnt[i], scnt[i]);
+}
+
+// rotational energies out of the records (to_records = 0) or into them (1),
+// in canonical order
+template <class R>
+__global__ void k_erot(const DevCell* cells, int cell0, int n_cells, const uint64_t* off, const Consts* C,
+                       double* e, int to_records) {
+    using Rec = typename RecOf<R>::T;
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        Rec* recs = reinterpret_cast<Rec*>(cells[cell0 + c].rec);
+        Rec r;
+        load_rec(recs + (j - off[c]), r);
+        const int s = (int)(r.meta & 0xFFu);
+        if (s >= MAXS) continue;
+        if (to_records) {
+            rec_put_erot(r, C->sp[s], e[j]);
+            store_rec(recs + (j - off[c]), r);
+        } else {
+            e[j] = rec_erot_of(r, C->sp[s]);
+        }
+    }
+}
+
+// Initial rotational energies at T_rot: kT Gamma(rot_dof/2), -ln(u) plus,
+// for three degrees of freedom, Marsaglia's polar normal squared over two;
+// keyed by (seed, 0xFFFFFFFE, cell, particle) as the oracle's
+template <class R>
+__global__ void k_init_rot(const DevCell* cells, int cell0, int n_cells, const uint64_t* off, const DevRes* res,
+                           int rslot, const Consts* C, double kT) {
+    using Rec = typename RecOf<R>::T;
+    const DevRes rs = res[rslot];
+    const uint64_t total = off[n_cells];
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const int c = cell_of64(off, n_cells, j);
+        const uint32_t i = (uint32_t)(j - off[c]);
+        const DevCell& cl = cells[cell0 + c];
+        Rec* recs = reinterpret_cast<Rec*>(cl.rec);
+        Rec r;
+        load_rec(recs + i, r);
+        const int s = (int)(r.meta & 0xFFu);
+        if (s >= MAXS) continue;
+        const DevSpecies& S = C->sp[s];
+        double E = 0.0;
+        if (S.rot_dof > 0 && kT > 0.0) {
+            Stream st;
+            st_init(st, rs.seed, 0xFFFFFFFEu, cl.lcell, i, PU_ROTINIT);
+            E = -ln_series(__dsub_rn(1.0, st_u64(st)));
+            if (S.rot_dof == 3) {
+                for (int it = 0; it < 4096; ++it) {
+                    const double x1 = __dsub_rn(__dmul_rn(2.0, st_u64(st)), 1.0);
+                    const double x2 = __dsub_rn(__dmul_rn(2.0, st_u64(st)), 1.0);
+                    const double q = __dadd_rn(__dmul_rn(x1, x1), __dmul_rn(x2, x2));
+                    if (q > 0.0 && q < 1.0) {
+                        E = __dadd_rn(E, __dmul_rn(__dmul_rn(x1, x1), __ddiv_rn(-ln_series(q), q)));
+                        break;
+                    }
+                }
+            }
+            E = __dmul_rn(E, kT);
+        }
+        rec_put_erot(r, S, E);
+        store_rec(recs + i, r);
+    }
 }
 
 template <class R>
@@ -2818,11 +3019,28 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, const u
     }                                                                                            \
     template <>                                                                                  \
     void launch_pack<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,       \
-                        uint64_t total, double* v, uint8_t* qn, int32_t* sp, int32_t* cell,      \
+                        uint64_t total, const Consts* C, double* v, uint8_t* qn, int32_t* sp,    \
+                        int32_t* cell, cudaStream_t s) {                                         \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);                \
+        k_pack<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, C, v, qn, sp, cell);          \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_erot<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,       \
+                        uint64_t total, const Consts* C, double* e, int to_records,              \
                         cudaStream_t s) {                                                        \
         if (total == 0) return;                                                                  \
         const int grid = (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);                \
-        k_pack<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, v, qn, sp, cell);             \
+        k_erot<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, C, e, to_records);            \
+    }                                                                                            \
+    template <>                                                                                  \
+    void launch_init_rot<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,   \
+                            uint64_t total, const DevRes* res, int rslot, const Consts* C,       \
+                            double T_rot, cudaStream_t s) {                                      \
+        if (total == 0) return;                                                                  \
+        const int grid = (int)(total / 256 + 1 < 4096 ? total / 256 + 1 : 4096);                \
+        k_init_rot<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, res, rslot, C,            \
+                                           1.380649e-23 * T_rot);                                \
     }                                                                                            \
     template <>                                                                                  \
     void launch_init_vib<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,   \

@@ -33,7 +33,8 @@ EXPORTS = [
     "hcao_set_profiling", "hcao_read_profile", "hcao_sample_lb", "hcao_cell_sort_noalloc",
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
     "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
-    "hcao_set_step_path", "hcao_get_step_path", "hcao_set_cell_base",
+    "hcao_set_step_path", "hcao_get_step_path", "hcao_set_cell_base", "hcao_init_rotation",
+    "hcao_load_erot", "hcao_read_erot",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -56,14 +57,16 @@ class _Species(C.Structure):
     _fields_ = [("mass", C.c_double), ("d_ref", C.c_double), ("T_ref", C.c_double),
                 ("omega", C.c_double), ("E_form", C.c_double), ("n_stretch", C.c_int),
                 ("we", C.POINTER(C.c_double)), ("wexe", C.POINTER(C.c_double)),
-                ("De", C.POINTER(C.c_double)), ("n_bend", C.c_int), ("theta", C.POINTER(C.c_double))]
+                ("De", C.POINTER(C.c_double)), ("n_bend", C.c_int), ("theta", C.POINTER(C.c_double)),
+                ("rot_dof", C.c_int)]
 
 
 class _Reaction(C.Structure):
     _fields_ = [("type", C.c_int), ("reactants", C.c_int * 2), ("products", C.c_int * 2),
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
                 ("alpha_mode", C.c_int), ("alpha", C.POINTER(C.c_double)), ("model", C.c_int),
-                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int)]
+                ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int),
+                ("gamma", C.c_double)]
 
 
 class LogRec(C.Structure):
@@ -78,7 +81,7 @@ LOG_DTYPE = np.dtype([("step", "u4"), ("cell", "u4"), ("round_k", "u4"), ("p", "
 class Moments(C.Structure):
     _fields_ = [("n", C.c_int64 * 16), ("momentum", C.c_double * 3), ("E_tr", C.c_double),
                 ("E_vib", C.c_double * 16), ("E_form", C.c_double), ("T_tr", C.c_double),
-                ("T_vib", C.c_double * 16)]
+                ("T_vib", C.c_double * 16), ("E_rot", C.c_double * 16), ("T_rot", C.c_double * 16)]
 
 
 class Job(C.Structure):
@@ -150,6 +153,9 @@ def lib() -> C.CDLL:
         L.hcao_recomb_rate.argtypes = [vp, i32, i32, dbl, C.POINTER(dbl)]
         L.hcao_set_step_path.argtypes = [vp, i32]
         L.hcao_set_cell_base.argtypes = [vp, i32, C.c_uint32]
+        L.hcao_init_rotation.argtypes = [vp, i32, dbl]
+        L.hcao_load_erot.argtypes = [vp, i32, vp]
+        L.hcao_read_erot.argtypes = [vp, i32, vp]
         L.hcao_get_step_path.argtypes = [vp, C.POINTER(i32)]
         L.hcao_kernel_launches.argtypes = [vp]
         L.hcao_kernel_launches.restype = u64
@@ -229,6 +235,7 @@ class Context:
             d = arr[i]
             d.mass, d.d_ref, d.T_ref, d.omega, d.E_form = s.mass, s.d_ref, s.T_ref, s.omega, s.E_form
             d.n_stretch, d.n_bend = len(s.we), len(s.theta)
+            d.rot_dof = getattr(s, "rot_dof", 0)
             for name in ("we", "wexe", "De", "theta"):
                 vals = list(getattr(s, name))
                 buf = (C.c_double * max(1, len(vals)))(*vals)
@@ -262,6 +269,7 @@ class Context:
                 d.arrhenius[j] = a
             d.tce_zeta = getattr(r, "tce_zeta", 0.0)
             d.wr_samples = getattr(r, "wr_samples", 1000)
+            d.gamma = getattr(r, "gamma", 0.0)
         self._chk(self.L.hcao_set_reactions(self.h, arr, len(reactions)))
         self.n_reactions = len(reactions)
 
@@ -287,6 +295,18 @@ class Context:
 
     def init_vibration(self, res, T_vib) -> None:
         self._chk(self.L.hcao_init_vibration(self.h, res, T_vib))
+
+    def init_rotation(self, res, T_rot) -> None:
+        self._chk(self.L.hcao_init_rotation(self.h, res, T_rot))
+
+    def load_erot(self, res, erot) -> None:
+        e = np.ascontiguousarray(erot, dtype=np.float64)
+        self._chk(self.L.hcao_load_erot(self.h, res, _p(e)))
+
+    def read_erot(self, res) -> np.ndarray:
+        out = np.zeros(max(self.count(res), 1))
+        self._chk(self.L.hcao_read_erot(self.h, res, _p(out)))
+        return out[: self.count(res)]
 
     # -- run
     def step(self, n=1) -> None:
@@ -485,6 +505,8 @@ def from_workload(w, precision=FP64, log=False, init_vib=True, **kw) -> Context:
     c.load_particles(rid, w.v, w.qn0(), w.species_idx, w.cell)
     if init_vib:
         c.init_vibration(rid, w.T_vib0)
+        if any(getattr(s, "rot_dof", 0) for s in w.species):
+            c.init_rotation(rid, getattr(w, "T_rot0", w.T_tr0))
     if log:
         c.set_log(True)
     return c
