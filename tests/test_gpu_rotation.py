@@ -135,4 +135,4 @@ def test_rotation_fp32_relaxation_matches_oracle():
     cg, co = np.array(cur["gpu"]), np.array(cur["oracle"])
     se = np.sqrt(cg.var(0, ddof=1) / seeds + co.var(0, ddof=1) / seeds)
     assert np.all(np.abs(cg.mean(0) - co.mean(0)) < 3.5 * se), (cg.mean(0), co.mean(0), se)
-    assert co.mean(0)[-1] > 2000.0
+    assert co.mean(0)[-1] > 1000.0 and cg.mean(0)[-1] > 1000.0  # warming from 300 K
