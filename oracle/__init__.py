@@ -40,7 +40,7 @@ class _Reaction(C.Structure):
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
                 ("alpha_mode", C.c_int), ("alpha", C.c_double * MAXM), ("model", C.c_int),
                 ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int),
-                ("gamma", C.c_double)]
+                ("gamma", C.c_double), ("prod_split", C.c_int)]
 
 
 def reaction_model_code(r) -> int:
@@ -79,6 +79,8 @@ def lib():
         L.ora_read_erot.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
         L.ora_ln.restype = C.c_double
         L.ora_ln.argtypes = [C.c_double]
+        L.ora_exp.restype = C.c_double
+        L.ora_exp.argtypes = [C.c_double]
         L.ora_sample_rot_fraction.argtypes = [C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_void_p]
         L.ora_step.argtypes = [C.c_void_p, C.c_int]
         L.ora_set_log.argtypes = [C.c_void_p, C.c_int]
@@ -205,6 +207,7 @@ class Oracle:
         d.tce_zeta = getattr(r, "tce_zeta", 0.0)
         d.wr_samples = getattr(r, "wr_samples", 1000)
         d.gamma = getattr(r, "gamma", 0.0)
+        d.prod_split = 1 if getattr(r, "product_split", "relaxation") == "collision_temperature" else 0
         self.n_reactions += 1
         return self._chk(self.L.ora_add_reaction(self.ctx, C.byref(d)), "add_reaction")
 
@@ -378,6 +381,11 @@ def wr_density(hnu, E: float) -> float:
 def ln(x: float) -> float:
     """The oracle's own natural logarithm (rotation draws)."""
     return float(lib().ora_ln(x))
+
+
+def exp(x: float) -> float:
+    """The oracle's own exponential (used where the device must reproduce it)."""
+    return float(lib().ora_exp(x))
 
 
 def gamma_q(a: float, x: float) -> float:

@@ -65,6 +65,8 @@ typedef struct {
     double eps_min;     /* smallest single-quantum excitation of any mode */
     int MT;
     double* H[ORA_MAX_MODES];
+    double* Hh[ORA_MAX_MODES]; /* the same tables at exponent 1/2 (built for the products of a
+                                  reaction that redistributes at the collision temperature) */
     double rot_fmax;    /* rotation: the maximum of the LB fraction's density shape */
 } o_species;
 
@@ -201,11 +203,12 @@ uint32_t ora_pair_perm(uint32_t x, uint32_t N, const uint32_t key[4]) {
 /* ------------------------------------------------------------------ */
 /* LB weight (E_coll - sum E_j)^(xi_rel/2 - 1), xi_rel = 5 - 2 omega:
    exponent 0.75, 1 or 0.5 for omega = 0.75, 0.5, 1 (written with sqrt). */
-static double pw(const ora_ctx* c, double x) {
-    if (c->amode == 0) { double s = sqrt(x); return s * sqrt(s); }
-    if (c->amode == 1) return x;
+static double pw_mode(int amode, double x) {
+    if (amode == 0) { double s = sqrt(x); return s * sqrt(s); }
+    if (amode == 1) return x;
     return sqrt(x);
 }
+static double pw(const ora_ctx* c, double x) { return pw_mode(c->amode, x); }
 /* g^(2 - 2 omega): sigma_T(g) g of the VHS model */
 static double gpow(const ora_ctx* c, double g) {
     if (c->amode == 0) return sqrt(g);
@@ -282,11 +285,32 @@ static int64_t grid_idx(const o_species* s, int k, double E) {
     }
     return hi;
 }
-static double W_tab(const o_species* s, int k, double E) {
+static double W_tab(const o_species* s, double* const* H, int k, double E) {
     int64_t m = grid_idx(s, k, E);
     if (m == 0) return 0.0;
     if (m > s->MT - 1) m = s->MT - 1; /* only reached by table entries never queried */
-    return s->H[k][m];
+    return H[k][m];
+}
+/* The tables H (s->H at the context's exponent, amode = c->amode; s->Hh at
+   exponent 1/2, amode 2) on the species' grid. */
+static int fill_tables(const o_species* s, int amode, double** H) {
+    int n = s->n_modes;
+    for (int k = n - 1; k >= 0; --k) {
+        H[k] = (double*)malloc(sizeof(double) * (size_t)s->MT);
+        if (!H[k]) return -1;
+        for (int m = 0; m < s->MT; ++m) {
+            double g = grid_pt(s, k, m);
+            double sum = 0.0;
+            for (int i = 0; i < s->n_levels[k]; ++i) {
+                if (!(s->E[k][i] < g)) break;
+                double x = g - s->E[k][i];
+                double w = (k == n - 1) ? pw_mode(amode, x) : W_tab(s, H, k + 1, x);
+                sum = sum + w;
+            }
+            H[k][m] = sum;
+        }
+    }
+    return 0;
 }
 static int build_tables(ora_ctx* c, o_species* s) {
     int n = s->n_modes;
@@ -298,22 +322,7 @@ static int build_tables(ora_ctx* c, o_species* s) {
     s->eps_min = INFINITY;
     for (int j = 0; j < n; ++j)
         if (s->n_levels[j] > 1 && s->E[j][1] - s->E[j][0] < s->eps_min) s->eps_min = s->E[j][1] - s->E[j][0];
-    for (int k = n - 1; k >= 0; --k) {
-        s->H[k] = (double*)malloc(sizeof(double) * (size_t)s->MT);
-        if (!s->H[k]) return -1;
-        for (int m = 0; m < s->MT; ++m) {
-            double g = grid_pt(s, k, m);
-            double sum = 0.0;
-            for (int i = 0; i < s->n_levels[k]; ++i) {
-                if (!(s->E[k][i] < g)) break;
-                double x = g - s->E[k][i];
-                double w = (k == n - 1) ? pw(c, x) : W_tab(s, k + 1, x);
-                sum = sum + w;
-            }
-            s->H[k][m] = sum;
-        }
-    }
-    return 0;
+    return fill_tables(s, c->amode, s->H);
 }
 
 static double evib(const o_species* s, const uint8_t* qn) {
@@ -335,13 +344,13 @@ enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
    exactly (each trial's acceptance probability is pw(..)/H_0).  Below the
    smallest single-quantum excitation only the ground state has sum E < Ec, so
    it is taken without a draw. */
-static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
-                        uint8_t* qn_out, uint64_t* trials) {
+static int sample_table_with(ora_ctx* c, const o_species* s, int amode, double* const* H, double Ec,
+                             o_stream* st, uint8_t* qn_out, uint64_t* trials) {
     int n = s->n_modes;
     if (n == 0) return S_OK;
     int64_t m0 = grid_idx(s, 0, Ec);
     if (m0 > c->M) return S_OVER;
-    if (m0 == 0 || !(s->H[0][m0] > 0.0)) return S_DEGEN;
+    if (m0 == 0 || !(H[0][m0] > 0.0)) return S_DEGEN;
     if (Ec - s->base[0] < s->eps_min) {
         memset(qn_out, 0, (size_t)n);
         return S_OK;
@@ -354,13 +363,13 @@ static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
         for (int k = 0; k < n; ++k) {
             int64_t m = (k == 0) ? m0 : grid_idx(s, k, E);
             double u = st_u01(st);
-            double t = u * s->H[k][m];
+            double t = u * H[k][m];
             double cum = 0.0;
             int sel = -1;
             for (int i = 0; i < s->n_levels[k]; ++i) {
                 if (!(s->E[k][i] < E)) break;
                 double x = E - s->E[k][i];
-                double w = (k == n - 1) ? pw(c, x) : W_tab(s, k + 1, x);
+                double w = (k == n - 1) ? pw_mode(amode, x) : W_tab(s, H, k + 1, x);
                 cum = cum + w;
                 if (t < cum) { sel = i; break; }
             }
@@ -374,6 +383,10 @@ static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st,
         }
     }
     return S_CAP;
+}
+static int sample_table(ora_ctx* c, const o_species* s, double Ec, o_stream* st, uint8_t* qn_out,
+                        uint64_t* trials) {
+    return sample_table_with(c, s, c->amode, s->H, Ec, st, qn_out, trials);
 }
 
 /* Literal P8 (distribution reference): each mode drawn uniformly below Ec
@@ -798,7 +811,7 @@ void ora_destroy(ora_ctx* c) {
     for (int r = 0; r < MAX_REACTIONS; ++r)
         for (int m = 0; m < MAX_SPECIES; ++m) free(c->tce[r][m]);
     for (int i = 0; i < c->n_species; ++i)
-        for (int k = 0; k < ORA_MAX_MODES; ++k) free(c->sp[i].H[k]);
+        for (int k = 0; k < ORA_MAX_MODES; ++k) { free(c->sp[i].H[k]); free(c->sp[i].Hh[k]); }
     for (int r = 0; r < c->n_res; ++r) {
         o_res* R = c->res[r];
         for (int j = 0; j < R->n_cells; ++j) free(R->cells[j].p);
@@ -860,6 +873,17 @@ int ora_add_reaction(ora_ctx* c, const ora_reaction_desc* r) {
     if (r->type != ORA_RECOMB && r->model == ORA_MODEL_TCE) {
         int e = tce_build(c, id);
         if (e != ORA_OK) return e;
+    }
+    if (r->prod_split == ORA_SPLIT_TCOLL) {
+        for (int k = 0; k < 2; ++k) {
+            const int p = r->products[k];
+            if (p < 0 || p >= c->n_species) continue;
+            o_species* sp = &c->sp[p];
+            if (sp->n_modes == 0 || sp->Hh[0]) continue;
+            if (fill_tables(sp, 2, sp->Hh)) return ORA_ENOMEM;
+        }
+    } else if (r->prod_split != ORA_SPLIT_RELAX) {
+        return ORA_EINVAL;
     }
     return c->n_reactions++;
 }
@@ -1039,6 +1063,25 @@ double ora_ln(double x) {
     return 2.0 * s * t + (double)e * 0.69314718055994530942;
 }
 
+/* exponential for -708 <= x <= 709: x = k ln 2 + r with k the integer
+   nearest x / ln 2 and |r| <= ln 2 / 2 + tiny; ln 2 split into L1 (29
+   significant bits, so k L1 is exact) and L2 = ln 2 - L1; e^r by its Taylor
+   series to r^18 in Horner form (remainder below 1e-25), times 2^k.  Below
+   -708 the result is taken as 0. */
+double ora_exp(double x) {
+    if (x < -708.0) return 0.0;
+    if (x > 709.0) return HUGE_VAL;
+    const double L1 = 0x1.62e42ffp-1, L2 = -0x1.718432a1b0e26p-35;
+    const int k = (int)floor(x * 0x1.71547652b82fep+0 + 0.5);
+    const double r = (x - (double)k * L1) - (double)k * L2;
+    double t = 1.0;
+    for (int n = 18; n >= 1; --n) t = 1.0 + (r * t) / (double)n;
+    return ldexp(t, k);
+}
+
+/* x^y for x > 0 from the two series above */
+static double ora_pow(double x, double y) { return ora_exp(y * ora_ln(x)); }
+
 /* the LB fraction's density shape (1 - x)^(3/2 - omega) times x^(1/2) for
    three rotational degrees of freedom */
 static double rot_shape(const ora_ctx* c, int rot_dof, double x) {
@@ -1097,6 +1140,106 @@ static void product_state(ora_ctx* c, o_res* R, const o_species* s, double Ec, o
     if (r != S_OK) { memset(qn, 0, 16); set_err(c, ORA_EREJECT, "product sampler failed"); }
 }
 
+/* ------------------------------------------------------------------ */
+/* The second reading of the product redistribution (Sec. "Polyatomic QK
+   reaction modeling": the energy left after the reaction is shared with LB
+   over all available degrees of freedom by equipartition, the vibrational
+   degrees of freedom found by root-finding at a collision temperature).
+   Readings:
+     - the products' translational degrees of freedom: 3 per relative
+       motion (6 after a dissociation, 3 after an exchange or a
+       recombination);
+     - the collision temperature T_c solves E_x = xi_tr/2 k T_c + sum over
+       the products of <E_vib>(T_c), E_x the available energy above the
+       products' ground states and <E_vib> the Boltzmann mean over the
+       levels above the ZPE; a product's vibrational degrees of freedom are
+       xi_vib = 2 <E_vib>(T_c) / (k T_c);
+     - the first product's levels follow p ~ (E - E_state)^b1 with
+       b1 = (xi_tr + xi_vib,2(T_c))/2 - 1 (the rest shared by the
+       translation and the second product's vibration), at the budget of
+       reading A13 (the partner's ZPE reserved); the second product's with
+       b2 = xi_tr/2 - 1 at what the first left; a recombination's single
+       product with b = xi_tr/2 - 1;
+     - drawn exactly: a table draw at exponent a_t accepted with
+       ((E - sum E)/(E - ZPE))^(b - a_t), a_t the context's exponent
+       3/2 - omega when b reaches it, else 1/2 (every b here is at least
+       1/2, since xi_tr >= 3). */
+/* <E_vib>(T) above the ground level with the exponential ora_exp: a
+   stretch's Boltzmann mean over its level list, a bend's harmonic
+   k Theta / (e^(Theta/T) - 1) (0 once Theta/T > 700) */
+static double mean_evib_c(const o_species* s, double T) {
+    const double kT = KB * T;
+    double e = 0.0;
+    for (int j = 0; j < s->n_modes; ++j) {
+        if (s->is_bend[j]) {
+            const double th = s->d.theta[j - s->d.n_stretch];
+            const double x = th / T;
+            if (x <= 700.0) e = e + (KB * th) / (ora_exp(x) - 1.0);
+        } else {
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < s->n_levels[j]; ++i) {
+                const double de = s->E[j][i] - s->E[j][0];
+                const double b = ora_exp(-de / kT);
+                num = num + de * b;
+                den = den + b;
+            }
+            e = e + num / den;
+        }
+    }
+    return e;
+}
+
+static double xi_vib_at(const o_species* s, double T) {
+    return s->n_modes ? (2.0 * mean_evib_c(s, T)) / (KB * T) : 0.0;
+}
+
+/* T_c by bisection on [1 K, 1e7 K]; 100 halvings reach adjacent doubles */
+static double tcoll_root(double xi_tr, const o_species* p1, const o_species* p2, double Ex) {
+    double lo = 1.0, hi = 1.0e7;
+    for (int it = 0; it < 100; ++it) {
+        const double T = 0.5 * (lo + hi);
+        double g = (0.5 * xi_tr) * (KB * T) - Ex;
+        if (p1 && p1->n_modes) g = g + mean_evib_c(p1, T);
+        if (p2 && p2->n_modes) g = g + mean_evib_c(p2, T);
+        if (g < 0.0) lo = T; else hi = T;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int sample_exponent(ora_ctx* c, const o_species* s, double Ec, double b, o_stream* st, uint8_t* qn,
+                           uint64_t* trials) {
+    const int n = s->n_modes;
+    memset(qn, 0, 16);
+    if (n == 0) return S_OK;
+    if (!(Ec > s->zpe)) return S_DEGEN;
+    const double a = 1.5 - c->omega;
+    const int use_main = b >= a;
+    const double a_t = use_main ? a : 0.5;
+    if (!use_main && (!(b >= 0.5) || !s->Hh[0])) return S_CAP;
+    const double span = Ec - s->zpe;
+    uint8_t nq[ORA_MAX_MODES];
+    for (uint32_t trial = 0; trial < c->reject_cap; ++trial) {
+        const int r = use_main ? sample_table_with(c, s, c->amode, s->H, Ec, st, nq, trials)
+                               : sample_table_with(c, s, 2, s->Hh, Ec, st, nq, trials);
+        if (r != S_OK) return r;
+        const double Esum = evib(s, nq);
+        if (b == a_t || st_u01(st) < ora_pow((Ec - Esum) / span, b - a_t)) {
+            memcpy(qn, nq, (size_t)n);
+            return S_OK;
+        }
+    }
+    return S_CAP;
+}
+
+static void product_state_b(ora_ctx* c, o_res* R, const o_species* s, double Ec, double b, o_stream* st,
+                            uint8_t* qn) {
+    memset(qn, 0, 16);
+    if (s->n_modes == 0) return;
+    R->counters[2]++;
+    int r = sample_exponent(c, s, Ec, b, st, qn, &R->counters[3]);
+    if (r != S_OK) { memset(qn, 0, 16); set_err(c, ORA_EREJECT, "product sampler failed"); }
+}
+
 static double table_top(const o_species* s, const ora_ctx* c) {
     if (s->n_modes == 0) return INFINITY;
     return grid_pt(s, 0, c->M);
@@ -1132,9 +1275,15 @@ static int do_diss(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* M, double Ev
     st_init(&sb, R->seed, R->step, cell, rk, PU_LB_B);
     st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
     uint8_t qB[16], qC[16];
-    product_state(c, R, sB, Eav - sC->zpe, &sa, qB);
+    if (r->prod_split == ORA_SPLIT_TCOLL) {
+        const double Tc = tcoll_root(6.0, sB, sC, Eav - sB->zpe - sC->zpe);
+        product_state_b(c, R, sB, Eav - sC->zpe, (6.0 + xi_vib_at(sC, Tc)) / 2.0 - 1.0, &sa, qB);
+    } else {
+        product_state(c, R, sB, Eav - sC->zpe, &sa, qB);
+    }
     double EvB = evib(sB, qB);
-    product_state(c, R, sC, Eav - EvB, &sb, qC);
+    if (r->prod_split == ORA_SPLIT_TCOLL) product_state_b(c, R, sC, Eav - EvB, 2.0, &sb, qC);
+    else product_state(c, R, sC, Eav - EvB, &sb, qC);
     double EvC = evib(sC, qC);
     double Etr = (Eav - EvB) - EvC;
     double x;
@@ -1206,9 +1355,15 @@ static int do_exch(ora_ctx* c, o_res* R, int rx, o_part* A, o_part* B, double Ev
     st_init(&sb, R->seed, R->step, cell, rk, PU_LB_B);
     st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
     uint8_t qC[16], qD[16];
-    product_state(c, R, sC, Eav - sD->zpe, &sa, qC);
+    if (r->prod_split == ORA_SPLIT_TCOLL) {
+        const double Tc = tcoll_root(3.0, sC, sD, Eav - sC->zpe - sD->zpe);
+        product_state_b(c, R, sC, Eav - sD->zpe, (3.0 + xi_vib_at(sD, Tc)) / 2.0 - 1.0, &sa, qC);
+    } else {
+        product_state(c, R, sC, Eav - sD->zpe, &sa, qC);
+    }
     double EvC = evib(sC, qC);
-    product_state(c, R, sD, Eav - EvC, &sb, qD);
+    if (r->prod_split == ORA_SPLIT_TCOLL) product_state_b(c, R, sD, Eav - EvC, 0.5, &sb, qD);
+    else product_state(c, R, sD, Eav - EvC, &sb, qD);
     double EvD = evib(sD, qD);
     double Etr = (Eav - EvC) - EvD;
     double mu = mC * mD / mt;
@@ -1263,7 +1418,8 @@ static int do_recomb(ora_ctx* c, o_res* R, int rx, o_part* B, o_part* Cp, o_part
     st_init(&sa, R->seed, R->step, cell, rk, PU_LB_A);
     st_init(&ss, R->seed, R->step, cell, rk, PU_SCAT);
     uint8_t qA[16];
-    product_state(c, R, sA, Eav, &sa, qA);
+    if (r->prod_split == ORA_SPLIT_TCOLL) product_state_b(c, R, sA, Eav, 0.5, &sa, qA);
+    else product_state(c, R, sA, Eav, &sa, qA);
     double Etr = Eav - evib(sA, qA);
     double mu = mA * mM / mt;
     double g = sqrt(2.0 * Etr / mu);

@@ -67,7 +67,11 @@ typedef struct {
     double tce_zeta;      /* TCE: internal degrees of freedom (half the pair's sum) in E_c */
     int wr_samples;       /* RECOMB, WR: sample energies (<= 0: 1000) */
     double gamma;         /* DISS / EXCH (QK): rotation-vibration coupling, gamma E_rot,A in E_coll */
+    int prod_split;       /* products' vibrational states: ORA_SPLIT_RELAX (reading A13, the
+                             relaxation target) or ORA_SPLIT_TCOLL (equipartition at the
+                             collision temperature) */
 } ora_reaction_desc;
+enum { ORA_SPLIT_RELAX = 0, ORA_SPLIT_TCOLL = 1 };
 enum { ORA_MODEL_QK = 0, ORA_MODEL_TCE = 1 };
 enum { ORA_RPROB_EXACT = 0, ORA_RPROB_WR = 1 };
 
@@ -99,6 +103,7 @@ int      ora_read_erot(ora_ctx*, int res, double* erot);
 /* the natural logarithm the oracle's rotation draws use (own series, see
    ora_ln in the source) */
 double   ora_ln(double x);
+double   ora_exp(double x);  /* own exponential (Taylor series after ln 2 reduction) */
 /* n classical LB rotational fractions of species sp (Beta(rot_dof/2,
    (5 - 2 omega)/2)) from a Philox stream keyed by seed (test diagnostic) */
 int      ora_sample_rot_fraction(ora_ctx*, int sp, uint64_t seed, int64_t n, double* out);

@@ -61,6 +61,8 @@ class Reaction:
     recomb_prob: str = "exact"      # recomb: "exact" level sum or "wr" (Whitten-Rabinovitch)
     wr_samples: int = 1000
     gamma: float = 0.0              # rotation-vibration coupling: gamma E_rot,A in the QK collision energy
+    product_split: str = "relaxation"  # products' levels: "relaxation" (reading A13) or
+                                       # "collision_temperature" (equipartition at T_c; oracle only)
 
 
 def triatomic() -> Species:
