@@ -134,8 +134,29 @@ typedef struct {
     double gamma;          /* DISS, EXCH (QK): rotation-vibration coupling in [0, 1]; the
                               collision energies of Eq. Ecoll-diss and Eq. Ecoll-exch add
                               gamma E_rot,A (Sec. "Rotation coupling") */
+    int prod_split;        /* how the products' levels share the energy left (Sec. "Polyatomic
+                              QK reaction modeling"), see below: HCAO_SPLIT_RELAX (0) or
+                              HCAO_SPLIT_TCOLL (1) */
 } hcao_reaction;
 enum { HCAO_MODEL_QK = 0, HCAO_MODEL_TCE = 1 };
+/* Product levels.  HCAO_SPLIT_RELAX: each product's levels follow the
+   relaxation step's LB target (exponent 3/2 - omega), the first product at
+   the available energy less the second's ZPE, the second at what the first
+   left.  HCAO_SPLIT_TCOLL: equipartition at a collision temperature T_c,
+   the root of xi_tr/2 k T_c + sum over the products of <E_vib>(T_c) = the
+   energy above the products' ground states (xi_tr = 6 after a dissociation,
+   3 after an exchange or a recombination; <E_vib> the Boltzmann mean of a
+   stretch's levels, k Theta / (e^(Theta/T) - 1) for a bend); the first
+   product's levels follow (E - E_state)^b1, b1 = (xi_tr + xi_vib,2(T_c))/2 - 1
+   with xi_vib = 2 <E_vib> / (k T_c), the second's (E - E_state)^(xi_tr/2 - 1),
+   a recombination's product (E - E_state)^(1/2).  Drawn exactly: a table
+   draw at exponent 3/2 - omega (or 1/2, tables built for the products when
+   the exponent is below 3/2 - omega) accepted with ((E - sum E)/(E - ZPE))
+   to the power of the difference.  FP64 mode evaluates T_c by bisection
+   with its own exponential; FP32 mode interpolates b1 from a per-reaction
+   table over the energy above the ground states (4096 points per reaction,
+   log-spaced). */
+enum { HCAO_SPLIT_RELAX = 0, HCAO_SPLIT_TCOLL = 1 };
 enum { HCAO_RPROB_EXACT = 0, HCAO_RPROB_WR = 1 };
 
 /* One candidate pair of the last step (parity inspection). */

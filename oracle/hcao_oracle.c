@@ -28,6 +28,22 @@
  *                       enumerated LB target at its budget, Beta(3/2,3/2)
  *                       three-body split, isotropy, conservation; the same
  *                       for the recombination product, reading A14)
+ *   T_c product split : pinned (each product's levels vs the enumerated
+ *                       target at the exponent the collision temperature
+ *                       gives, found independently with scipy; the
+ *                       relaxation-table exponent rejected)
+ *   recombination     : pinned (Q(a,x) vs scipy, P(T) vs binned convolution
+ *                       and level sums, K_eq closed form, rate law)
+ *   WR density / P    : pinned (exact harmonic state counts, quadrature for
+ *                       one oscillator, convergence)
+ *   TCE               : pinned (P(E_c) closed form, the Arrhenius rate from
+ *                       the probability's thermal average by quadrature)
+ *   competing choice  : pinned (channel frequencies vs E_excess shares)
+ *   rotation          : pinned (own log vs libm, Beta fraction, Gamma
+ *                       initialisation, equipartition, gamma-coupled
+ *                       dissociation probability closed form)
+ *   own exp           : pinned (vs libm within 2 ulp)
+ *   cell_base split   : pinned (two cell ranges reproduce the whole run)
  */
 #include "hcao_oracle.h"
 #include <math.h>

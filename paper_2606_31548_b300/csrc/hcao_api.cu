@@ -103,6 +103,11 @@ struct hcao_ctx {
     float* d_H32 = nullptr;
     K5Ent* d_k5e = nullptr;
     AliasEnt* d_ae = nullptr;
+    // collision-temperature product split: exponent-1/2 tables, FP32 b1 tables
+    double* d_H64h = nullptr;
+    K5Ent* d_k5eh = nullptr;
+    AliasEnt* d_aeh = nullptr;
+    float* d_tcb = nullptr;
     int amode = -1;
     double omega = 0.75;
 
@@ -865,6 +870,10 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.H32 = ctx->d_H32;
     a.k5e = ctx->d_k5e;
     a.ae = ctx->d_ae;
+    a.H64h = ctx->d_H64h;
+    a.k5eh = ctx->d_k5eh;
+    a.aeh = ctx->d_aeh;
+    a.tcb = ctx->d_tcb;
     a.cells = ctx->d_cells;
     a.n_cells = ctx->n_cells_total;
     a.res = ctx->d_res;
@@ -1022,6 +1031,10 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_H32);
     dfree(ctx, ctx->d_k5e);
     dfree(ctx, ctx->d_ae);
+    dfree(ctx, ctx->d_H64h);
+    dfree(ctx, ctx->d_k5eh);
+    dfree(ctx, ctx->d_aeh);
+    dfree(ctx, ctx->d_tcb);
     dfree(ctx, ctx->d_res);
     dfree(ctx, ctx->d_cells);
     dfree(ctx, ctx->d_cellcnt);
@@ -1168,6 +1181,8 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
         D.zpe = s.zpe;
         D.n_modes = s.n_modes;
         D.n_stretch = s.d.n_stretch;
+        D.tab_off_h = -1;
+        for (int b = 0; b < s.d.n_bend; ++b) D.theta[s.d.n_stretch + b] = s.theta[b];
         D.M = M;
         D.MT = MT;
         for (int j = 0; j < s.d.n_stretch; ++j) {
@@ -1269,6 +1284,122 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
     return upload_consts(ctx);
 }
 
+// Collision-temperature product split (host side).  <E_vib>(T) of species i
+// above its ground level: Boltzmann mean of each stretch's levels, k Theta /
+// (e^(Theta/T) - 1) for a bend; T_c by bisection; b1 of the first product.
+static double mean_evib_host(const HostSpecies& s, double T) {
+    const double kT = KB * T;
+    double e = 0.0;
+    for (int j = 0; j < s.n_modes; ++j) {
+        if (j >= s.d.n_stretch) {
+            const double x = s.theta[j - s.d.n_stretch] / T;
+            if (x <= 700.0) e += KB * s.theta[j - s.d.n_stretch] / std::expm1(x);
+        } else {
+            double num = 0.0, den = 0.0;
+            for (double l : s.lev[j]) {
+                const double de = l - s.lev[j][0];
+                const double b = std::exp(-de / kT);
+                num += de * b;
+                den += b;
+            }
+            e += num / den;
+        }
+    }
+    return e;
+}
+static double b1_host(const HostSpecies& p1, const HostSpecies& p2, double xi_tr, double Ex) {
+    double lo = 1.0, hi = 1.0e7;
+    for (int it = 0; it < 100; ++it) {
+        const double T = 0.5 * (lo + hi);
+        const double g = 0.5 * xi_tr * KB * T + mean_evib_host(p1, T) + mean_evib_host(p2, T) - Ex;
+        if (g < 0.0) lo = T; else hi = T;
+    }
+    const double Tc = 0.5 * (lo + hi);
+    const double xi2 = p2.n_modes ? 2.0 * mean_evib_host(p2, Tc) / (KB * Tc) : 0.0;
+    return (xi_tr + xi2) / 2.0 - 1.0;
+}
+
+// Tables of the reactions with the collision-temperature split: the
+// products' K5 tables at exponent 1/2 (a product's exponent falls below the
+// context's 3/2 - omega after an exchange or a recombination; not needed
+// when that exponent is 1/2 already), and in FP32 mode each dissociation's
+// and exchange's b1 over E_x = 2^(TCB_L0 + i / TCB_PER_OCTAVE) J.
+hcao_status build_split_tables(hcao_ctx* ctx) {
+    Consts& C = ctx->hc;
+    dfree(ctx, ctx->d_H64h);
+    dfree(ctx, ctx->d_k5eh);
+    dfree(ctx, ctx->d_aeh);
+    dfree(ctx, ctx->d_tcb);
+    for (int i = 0; i < ctx->n_species; ++i) C.sp[i].tab_off_h = -1;
+    bool any = false;
+    for (int r = 0; r < C.n_reactions; ++r)
+        if (C.rx[r].prod_split == HCAO_SPLIT_TCOLL) any = true;
+    if (!any) return HCAO_OK;
+    const bool fp32 = ctx->cfg.precision == HCAO_FP32;
+    std::vector<double> H64;
+    std::vector<K5Ent> k5e;
+    std::vector<AliasEnt> ae;
+    std::vector<float> tcb;
+    for (int r = 0; r < C.n_reactions; ++r) {
+        DevReaction& R = C.rx[r];
+        if (R.prod_split != HCAO_SPLIT_TCOLL) continue;
+        for (int k = 0; k < 2 && C.amode != 2; ++k) {
+            const int p = k ? R.P1 : R.P0;
+            if (p < 0) continue;
+            DevSpecies& D = C.sp[p];
+            const HostSpecies& s = ctx->sp[p];
+            const int nm = s.n_modes;
+            if (nm == 0 || D.tab_off_h >= 0) continue;
+            if (!fp32) {
+                std::vector<double> L[MAXM];
+                for (int j = 0; j < nm; ++j) L[j] = s.lev[j];
+                std::vector<double> t;
+                build_tables<double>(2, nm, L, D.base, D.cq, D.MT, t);
+                D.tab_off_h = (int)H64.size();
+                H64.insert(H64.end(), t.begin(), t.end());
+            } else {
+                std::vector<float> L[MAXM];
+                for (int j = 0; j < nm; ++j) {
+                    L[j].resize(s.lev[j].size());
+                    for (size_t l = 0; l < s.lev[j].size(); ++l) L[j][l] = (float)s.lev[j][l];
+                }
+                std::vector<float> t;
+                build_tables_f32(2, nm, L, D.base_f, D.gshift, D.gj0, D.MT, t);
+                D.tab_off_h = (int)k5e.size();
+                build_alias_f32(2, nm, L, D.base_f, D.gshift, D.gj0, D.MT, t, k5e, ae);
+            }
+        }
+        if (fp32 && R.type != HCAO_RECOMB) {
+            R.tcb_off = (int)tcb.size();
+            const double xi_tr = R.type == HCAO_DISS ? 6.0 : 3.0;
+            for (int i = 0; i < TCB_N; ++i) {
+                const double Ex = std::exp2(TCB_L0 + (double)i / TCB_PER_OCTAVE);
+                tcb.push_back((float)b1_host(ctx->sp[R.P0], ctx->sp[R.P1], xi_tr, Ex));
+            }
+        }
+    }
+    if (!H64.empty()) {
+        CU(dalloc(ctx, &ctx->d_H64h, H64.size()));
+        CU(cudaMemcpyAsync(ctx->d_H64h, H64.data(), sizeof(double) * H64.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    }
+    if (!k5e.empty()) {
+        CU(dalloc(ctx, &ctx->d_k5eh, k5e.size()));
+        CU(cudaMemcpyAsync(ctx->d_k5eh, k5e.data(), sizeof(K5Ent) * k5e.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CU(dalloc(ctx, &ctx->d_aeh, std::max<size_t>(ae.size(), 1)));
+        if (!ae.empty())
+            CU(cudaMemcpyAsync(ctx->d_aeh, ae.data(), sizeof(AliasEnt) * ae.size(), cudaMemcpyHostToDevice,
+                               ctx->stream));
+    }
+    if (!tcb.empty()) {
+        CU(dalloc(ctx, &ctx->d_tcb, tcb.size()));
+        CU(cudaMemcpyAsync(ctx->d_tcb, tcb.data(), sizeof(float) * tcb.size(), cudaMemcpyHostToDevice,
+                           ctx->stream));
+    }
+    return HCAO_OK;
+}
+
 hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
     DeviceScope ds_(ctx);
     if (!ctx || n < 0 || n > MAXR || (n > 0 && !rx)) return fail(ctx, HCAO_EINVAL, "set_reactions: bad arguments");
@@ -1288,6 +1419,8 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         ctx->rx_host[i].alpha = nullptr;  // not kept: copied into D.alpha below
         if (r.model != 0 && r.model != 1)
             return fail(ctx, HCAO_EINVAL, "set_reactions: bad model");
+        if (r.prod_split != HCAO_SPLIT_RELAX && r.prod_split != HCAO_SPLIT_TCOLL)
+            return fail(ctx, HCAO_EINVAL, "set_reactions: bad prod_split");
         if (r.type != HCAO_DISS && r.type != HCAO_EXCH && r.type != HCAO_RECOMB)
             return fail(ctx, HCAO_EINVAL, "set_reactions: bad type");
         if (r.type == HCAO_RECOMB) {
@@ -1307,6 +1440,7 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
                     return fail(ctx, HCAO_EINVAL, "set_reactions: two recombinations of one species pair");
             }
             D.mask = r.diss_mode_mask;
+            D.prod_split = r.prod_split;
             // the reverse dissociation's threshold terms (Eq. Ecoll-diss) and the released energy
             D.zpesum = P.zpe + ctx->sp[D.A].zpe + ctx->sp[D.B].zpe;
             D.dEf = P.d.E_form - (ctx->sp[D.A].d.E_form + ctx->sp[D.B].d.E_form);
@@ -1333,6 +1467,7 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         if (!(r.gamma >= 0.0 && r.gamma <= 1.0)) return fail(ctx, HCAO_EINVAL, "set_reactions: gamma outside [0, 1]");
         D.gamma = r.gamma;
         D.gamma_f = (float)r.gamma;
+        D.prod_split = r.prod_split;
         if (r.model == HCAO_MODEL_TCE) {
             const double b = r.arrhenius[1], z = r.tce_zeta;
             if (!(r.arrhenius[0] >= 0.0) || !(r.arrhenius[2] >= 0.0) || !(z >= 0.0) || !(z + b + 1.5 > 0.0))
@@ -1374,6 +1509,10 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
     }
     {
         hcao_status st = build_tce_tables(ctx);
+        if (st != HCAO_OK) return st;
+    }
+    {
+        hcao_status st = build_split_tables(ctx);
         if (st != HCAO_OK) return st;
     }
     return upload_consts(ctx);

@@ -92,6 +92,11 @@ struct DevSpecies {
     int rot_dof, pad_r;
     double rot_fmax;
     float rot_fmax_f, pad_rf;
+    // products of a reaction with the collision-temperature split: bend
+    // temperatures (K) by mode index (0 for stretches) and the offset of the
+    // exponent-1/2 tables (-1 if none)
+    double theta[MAXM];
+    int tab_off_h, pad_h;
 };
 
 // FP32 K5 table entry of (species, mode k, bucket m), parallel to the float
@@ -134,7 +139,14 @@ struct DevReaction {
     long long Ea_fix, zpesum_fix, dEf_fix;   // FP32 mode (2^-100 J units)
     double gamma;                    // rotation-vibration coupling: gamma E_rot,A in the QK E_coll
     float gamma_f, pad_gf;
+    int prod_split;                  // HCAO_SPLIT_RELAX or HCAO_SPLIT_TCOLL
+    int tcb_off;                     // FP32, DISS / EXCH with TCOLL: offset of its b1 table
 };
+// FP32 b1 tables of the collision-temperature split: b1 at E_x = 2^(TCB_L0 +
+// i / TCB_PER_OCTAVE) J, i = 0..TCB_N-1, linear in log2 E_x (clamped)
+#define TCB_N 4096
+#define TCB_L0 (-80.0)
+#define TCB_PER_OCTAVE 128.0
 
 struct Consts {
     int n_species, n_reactions, amode, creates;
@@ -173,6 +185,10 @@ struct StepArgs {
     const float* H32;
     const K5Ent* k5e;               // FP32 K5 tables with their alias proposals, parallel to H32
     const AliasEnt* ae;             // FP32 alias-table slots
+    const double* H64h;             // exponent-1/2 tables of the collision-temperature split:
+    const K5Ent* k5eh;              //   FP64 tables, FP32 tables + alias slots (offsets DevSpecies
+    const AliasEnt* aeh;            //   tab_off_h), FP32 b1 tables (DevReaction tcb_off)
+    const float* tcb;
     DevCell* cells;
     int n_cells;
     DevRes* res;

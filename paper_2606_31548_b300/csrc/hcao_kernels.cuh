@@ -263,6 +263,24 @@ __device__ __forceinline__ double ln_series(double x) {
     return __dadd_rn(__dmul_rn(__dmul_rn(2.0, s), t), __dmul_rn((double)e, 0.69314718055994530942));
 }
 
+// Exponential for -708 <= x <= 709 (0 below), every operation rounded as
+// written: x = k ln 2 + r with k the integer nearest x / ln 2, ln 2 split into
+// L1 (29 significant bits: k L1 is exact) and L2 = ln 2 - L1, e^r by its
+// Taylor series to r^18 in Horner form, times 2^k built from its exponent bits.
+__device__ __forceinline__ double exp_series(double x) {
+    if (x < -708.0) return 0.0;
+    if (x > 709.0) return __longlong_as_double(0x7FF0000000000000ll);
+    const double L1 = 0x1.62e42ffp-1, L2 = -0x1.718432a1b0e26p-35;
+    const int k = (int)floor(__dadd_rn(__dmul_rn(x, 0x1.71547652b82fep+0), 0.5));
+    const double kd = (double)k;
+    const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(kd, L1)), __dmul_rn(kd, L2));
+    double t = 1.0;
+    for (int n = 18; n >= 1; --n) t = __dadd_rn(1.0, __ddiv_rn(__dmul_rn(r, t), (double)n));
+    return __dmul_rn(t, __longlong_as_double((long long)(k + 1023) << 52));
+}
+// x^y = e^(y ln x) for x > 0 from the two series
+__device__ __forceinline__ double pow_series(double x, double y) { return exp_series(__dmul_rn(y, ln_series(x))); }
+
 // The classical LB fraction x ~ Beta(rot_dof/2, (5 - 2 omega)/2) of the
 // energy a rotating molecule keeps: rejection under the maximum of the
 // density shape x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega), square roots only.
@@ -376,12 +394,11 @@ enum { S_OK = 0, S_OVER = 1, S_DEGEN = 2, S_CAP = -1 };
 // tables; a draw running past the end of a mode's levels restarts the trial.
 // Every accepted state has probability lb_pow(..)/H_0: the target, exactly.
 template <class R>
-__device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, double Ec_d,
-                         Stream& st, uint32_t q[4], uint32_t& trials) {
+__device__ int sample_lb_tab(const StepArgs& A, const DevSpecies& S, int amode, const R* H, double Ec_d,
+                             Stream& st, uint32_t q[4], uint32_t& trials) {
     const int n = S.n_modes;
     if (n == 0) return S_OK;
     const R* L = lev_tab<R>(A);
-    const R* H = h_tab<R>(A) + S.tab_off;
     const R cq = sp_cq<R>(S), inv = sp_inv<R>(S);
     const int MT = S.MT;
     const R Ec = (R)Ec_d;
@@ -436,6 +453,85 @@ __device__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, doub
             E = sub_rn(E, __ldg(Lk + sel));
         }
         if (ok) {
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            return S_OK;
+        }
+    }
+    return S_CAP;
+}
+template <class R>
+__device__ __forceinline__ int sample_lb(const StepArgs& A, const DevSpecies& S, int amode, double Ec_d,
+                                         Stream& st, uint32_t q[4], uint32_t& trials) {
+    return sample_lb_tab<R>(A, S, amode, h_tab<R>(A) + S.tab_off, Ec_d, st, q, trials);
+}
+
+// ------------------------------------------------- collision-temperature split
+// The second reading of the product redistribution (Sec. "Polyatomic QK
+// reaction modeling"): equipartition at a collision temperature T_c, the root
+// of xi_tr/2 k T_c + sum over the products of <E_vib>(T_c) = E_x (E_x the
+// energy above the products' ground states); a product's levels then follow
+// (E - sum E)^b with b = (the degrees of freedom left to share with)/2 - 1.
+// FP64 mode, every operation rounded as written.
+__device__ __forceinline__ double mean_evib_tc(const StepArgs& A, const DevSpecies& S, double T) {
+    const double kT = __dmul_rn(1.380649e-23, T);
+    double e = 0.0;
+    for (int j = 0; j < S.n_modes; ++j) {
+        if (j >= S.n_stretch) {  // bend: k Theta / (e^(Theta/T) - 1)
+            const double th = S.theta[j];
+            const double x = __ddiv_rn(th, T);
+            if (x <= 700.0) e = __dadd_rn(e, __ddiv_rn(__dmul_rn(1.380649e-23, th), __dsub_rn(exp_series(x), 1.0)));
+        } else {  // stretch: Boltzmann mean over its levels above the ground level
+            const double* L = A.lev64 + S.lev_off[j];
+            const double e0 = __ldg(L);
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < S.n_lev[j]; ++i) {
+                const double de = __dsub_rn(__ldg(L + i), e0);
+                const double b = exp_series(__ddiv_rn(-de, kT));
+                num = __dadd_rn(num, __dmul_rn(de, b));
+                den = __dadd_rn(den, b);
+            }
+            e = __dadd_rn(e, __ddiv_rn(num, den));
+        }
+    }
+    return e;
+}
+__device__ __forceinline__ double xi_vib_tc(const StepArgs& A, const DevSpecies& S, double T) {
+    return S.n_modes ? __ddiv_rn(__dmul_rn(2.0, mean_evib_tc(A, S, T)), __dmul_rn(1.380649e-23, T)) : 0.0;
+}
+// T_c by bisection on [1 K, 1e7 K]; 100 halvings reach adjacent doubles
+static __device__ double tcoll_root(const StepArgs& A, double xi_tr, const DevSpecies& P1, const DevSpecies& P2,
+                             double Ex) {
+    double lo = 1.0, hi = 1.0e7;
+    for (int it = 0; it < 100; ++it) {
+        const double T = __dmul_rn(0.5, __dadd_rn(lo, hi));
+        double g = __dsub_rn(__dmul_rn(__dmul_rn(0.5, xi_tr), __dmul_rn(1.380649e-23, T)), Ex);
+        if (P1.n_modes) g = __dadd_rn(g, mean_evib_tc(A, P1, T));
+        if (P2.n_modes) g = __dadd_rn(g, mean_evib_tc(A, P2, T));
+        if (g < 0.0) lo = T; else hi = T;
+    }
+    return __dmul_rn(0.5, __dadd_rn(lo, hi));
+}
+// One product's levels with p ~ (Ec - sum E)^b, exactly: a table draw at
+// exponent a_t (the context's 3/2 - omega when b reaches it, else 1/2 from
+// the exponent-1/2 tables) accepted with ((Ec - sum E)/(Ec - ZPE))^(b - a_t)
+static __device__ int sample_exponent(const StepArgs& A, const DevSpecies& S, int amode, double Ec, double b,
+                               Stream& st, uint32_t q[4], uint32_t& trials) {
+    q[0] = q[1] = q[2] = q[3] = 0u;
+    if (S.n_modes == 0) return S_OK;
+    if (!(Ec > S.zpe)) return S_DEGEN;
+    const double a = amode == 0 ? 0.75 : (amode == 1 ? 1.0 : 0.5);
+    const bool use_main = b >= a;
+    const double a_t = use_main ? a : 0.5;
+    if (!use_main && (!(b >= 0.5) || S.tab_off_h < 0)) return S_CAP;
+    const double* H = use_main ? A.H64 + S.tab_off : A.H64h + S.tab_off_h;
+    const int am = use_main ? amode : 2;
+    const double span = __dsub_rn(Ec, S.zpe);
+    for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
+        uint32_t nq[4];
+        const int r = sample_lb_tab<double>(A, S, am, H, Ec, st, nq, trials);
+        if (r != S_OK) return r;
+        const double Esum = evib64(A.lev64, S, nq);
+        if (b == a_t || st_uni<double>(st) < pow_series(__ddiv_rn(__dsub_rn(Ec, Esum), span), __dsub_rn(b, a_t))) {
             q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
             return S_OK;
         }
@@ -509,9 +605,17 @@ __device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& r
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) { qB[j] = 0u; qC[j] = 0u; }
     uint32_t tr = 0;
+    const bool tc = rx.prod_split == HCAO_SPLIT_TCOLL;
     if (sB.n_modes > 0) {
         o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<R>(A, sB, C->amode, Eav - sC.zpe, sa, qB, tr) != S_OK) {
+        int rc;
+        if (tc) {  // xi_tr = 6: B shares with the two relative motions and C's vibration
+            const double Tc = tcoll_root(A, 6.0, sB, sC, Eav - sB.zpe - sC.zpe);
+            rc = sample_exponent(A, sB, C->amode, Eav - sC.zpe, (6.0 + xi_vib_tc(A, sC, Tc)) / 2.0 - 1.0, sa, qB, tr);
+        } else {
+            rc = sample_lb<R>(A, sB, C->amode, Eav - sC.zpe, sa, qB, tr);
+        }
+        if (rc != S_OK) {
             for (int j = 0; j < 4; ++j) qB[j] = 0u;
             atomicOr(A.err, (uint32_t)ERR_REJECT);
         }
@@ -519,7 +623,9 @@ __device__ bool do_diss(const StepArgs& A, const Consts* C, const DevReaction& r
     const double EvB = evib64(A.lev64, sB, qB);
     if (sC.n_modes > 0) {
         o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<R>(A, sC, C->amode, Eav - EvB, sb, qC, tr) != S_OK) {
+        const int rc = tc ? sample_exponent(A, sC, C->amode, Eav - EvB, 2.0, sb, qC, tr)
+                          : sample_lb<R>(A, sC, C->amode, Eav - EvB, sb, qC, tr);
+        if (rc != S_OK) {
             for (int j = 0; j < 4; ++j) qC[j] = 0u;
             atomicOr(A.err, (uint32_t)ERR_REJECT);
         }
@@ -585,9 +691,17 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) { qC[j] = 0u; qD[j] = 0u; }
     uint32_t tr = 0;
+    const bool tc = rx.prod_split == HCAO_SPLIT_TCOLL;
     if (sC.n_modes > 0) {
         o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<R>(A, sC, C->amode, Eav - sD.zpe, sa, qC, tr) != S_OK) {
+        int rc;
+        if (tc) {  // xi_tr = 3: C shares with the relative motion and D's vibration
+            const double Tc = tcoll_root(A, 3.0, sC, sD, Eav - sC.zpe - sD.zpe);
+            rc = sample_exponent(A, sC, C->amode, Eav - sD.zpe, (3.0 + xi_vib_tc(A, sD, Tc)) / 2.0 - 1.0, sa, qC, tr);
+        } else {
+            rc = sample_lb<R>(A, sC, C->amode, Eav - sD.zpe, sa, qC, tr);
+        }
+        if (rc != S_OK) {
             for (int j = 0; j < 4; ++j) qC[j] = 0u;
             atomicOr(A.err, (uint32_t)ERR_REJECT);
         }
@@ -595,7 +709,9 @@ __device__ bool do_exch(const StepArgs& A, const Consts* C, const DevReaction& r
     const double EvC = evib64(A.lev64, sC, qC);
     if (sD.n_modes > 0) {
         o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<R>(A, sD, C->amode, Eav - EvC, sb, qD, tr) != S_OK) {
+        const int rc = tc ? sample_exponent(A, sD, C->amode, Eav - EvC, 0.5, sb, qD, tr)
+                          : sample_lb<R>(A, sD, C->amode, Eav - EvC, sb, qD, tr);
+        if (rc != S_OK) {
             for (int j = 0; j < 4; ++j) qD[j] = 0u;
             atomicOr(A.err, (uint32_t)ERR_REJECT);
         }
@@ -650,7 +766,9 @@ __device__ bool do_recomb(const StepArgs& A, const Consts* C, const DevReaction&
     uint32_t tr = 0;
     if (sA.n_modes > 0) {
         o.ev += 1u << EV_SAMP_SHIFT;
-        if (sample_lb<R>(A, sA, C->amode, Eav, sa, qA, tr) != S_OK) {
+        const int rc = rx.prod_split == HCAO_SPLIT_TCOLL ? sample_exponent(A, sA, C->amode, Eav, 0.5, sa, qA, tr)
+                                                        : sample_lb<R>(A, sA, C->amode, Eav, sa, qA, tr);
+        if (rc != S_OK) {
             for (int j = 0; j < 4; ++j) qA[j] = 0u;
             atomicOr(A.err, (uint32_t)ERR_REJECT);
         }
@@ -961,10 +1079,10 @@ __device__ __forceinline__ void scatter_f32(const DevPair& pc, long long Erel, c
 // from the small level list.  Returns S_OK with the levels in q and their
 // fixed-point energy in Esel, S_OVER, S_DEGEN or S_CAP.  Counts mode draws
 // and level evaluations (one per draw).
-static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode, float Ec,
-                                       Stream& st, uint32_t (&q)[4], long long& Esel, uint32_t& trials,
-                                       uint32_t& wlev, uint32_t& wmode) {
-    const K5Ent* __restrict__ T = A.k5e + S.tab_off;
+static __device__ int sample_alias_tab(const StepArgs& A, const K5Ent* __restrict__ T,
+                                       const AliasEnt* __restrict__ AE, const DevSpecies& S, int amode,
+                                       float Ec, Stream& st, uint32_t (&q)[4], long long& Esel,
+                                       uint32_t& trials, uint32_t& wlev, uint32_t& wmode) {
     const int n = S.n_modes, MT = S.MT, gsh = S.gshift, gj0 = S.gj0;
     q[0] = q[1] = q[2] = q[3] = 0u;
     Esel = S.zpe_fix;
@@ -1000,7 +1118,7 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
             const uint32_t j = (uint32_t)(rl >> 24);
             const float coin = (float)(uint32_t)(rl & 0xFFFFFFu) * 0x1p-24f;
             const float* lv = A.lev32 + S.lev_off[k];
-            const float4 s0 = __ldg(reinterpret_cast<const float4*>(A.ae + off + j));
+            const float4 s0 = __ldg(reinterpret_cast<const float4*>(AE + off + j));
             const float ej = __ldg(lv + j);  // in parallel with the slot
             const bool own = coin < s0.x;
             i = own ? j : __float_as_uint(s0.y);
@@ -1057,6 +1175,11 @@ static __device__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, i
     Esel = es;
     return S_OK;
 }
+static __device__ __forceinline__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode,
+                                                       float Ec, Stream& st, uint32_t (&q)[4], long long& Esel,
+                                                       uint32_t& trials, uint32_t& wlev, uint32_t& wmode) {
+    return sample_alias_tab(A, A.k5e + S.tab_off, A.ae, S, amode, Ec, st, q, Esel, trials, wlev, wmode);
+}
 
 // FP32 LB relaxation of one molecule of species sp (levels q, fixed-point
 // E_vib Evold) against the relative energy Erel; returns the relative energy
@@ -1107,6 +1230,68 @@ static __device__ __forceinline__ long long relax_flat(const StepArgs& A, const 
     Erel = relax_one(A, C, spB, qB, EvB, stB, Erel, o, wl, wm, took);
     if (work) { work[0] += wl; work[1] += wm; }
     return Erel;
+}
+
+// FP32 mode, the collision-temperature split: one product's levels with
+// p ~ (E - sum E)^b (E = Erel + Evold, Evold its ground state): alias draws at
+// exponent a_t (the context's 3/2 - omega when b reaches it, else 1/2 from
+// the exponent-1/2 tables) accepted with ((E - sum E)/(E - ZPE))^(b - a_t).
+// Returns the relative energy left; a failed draw keeps the ground state.
+static __device__ long long relax_one_b(const StepArgs& A, const Consts* __restrict__ C, int sp,
+                                        uint32_t (&q)[4], long long Evold, Stream& st, long long Erel,
+                                        float b, PairOut& o) {
+    if (sp < 0 || C->sp[sp].n_modes == 0) return Erel;
+    const DevSpecies& S = C->sp[sp];
+    const long long Ecd = Erel + Evold;
+    o.ev += 1u << EV_SAMP_SHIFT;
+    const float a = C->amode == 0 ? 0.75f : (C->amode == 1 ? 1.0f : 0.5f);
+    const bool use_main = b >= a;
+    const float a_t = use_main ? a : 0.5f;
+    if (!use_main && S.tab_off_h < 0) {
+        atomicOr(A.err, (uint32_t)ERR_REJECT);
+        return Erel;
+    }
+    const K5Ent* T = use_main ? A.k5e + S.tab_off : A.k5eh + S.tab_off_h;
+    const AliasEnt* AE = use_main ? A.ae : A.aeh;
+    const int am = use_main ? C->amode : 2;
+    const double span = (double)(Ecd - S.zpe_fix);
+    uint32_t tr = 0, wl = 0, wm = 0;
+    for (uint32_t trial = 0; trial < A.reject_cap; ++trial) {
+        uint32_t nq[4];
+        long long Esel;
+        const int rc = sample_alias_tab(A, T, AE, S, am, fix2f(Ecd), st, nq, Esel, tr, wl, wm);
+        if (rc != S_OK) {
+            o.trials += tr;
+            if (rc == S_OVER) o.ev += 1u << EV_OVER_SHIFT;
+            else if (rc == S_DEGEN) o.ev += 1u << EV_DEGEN_SHIFT;
+            else atomicOr(A.err, (uint32_t)ERR_REJECT);
+            return Erel;
+        }
+        const long long En = Ecd - Esel;
+        if (En < 0) {
+            o.trials += tr;
+            o.ev += 1u << EV_DEGEN_SHIFT;
+            return Erel;
+        }
+        if (b == a_t || st_u32(st) < powf((float)((double)En / span), b - a_t)) {
+            o.trials += tr;
+            q[0] = nq[0]; q[1] = nq[1]; q[2] = nq[2]; q[3] = nq[3];
+            return En;
+        }
+    }
+    o.trials += tr;
+    atomicOr(A.err, (uint32_t)ERR_REJECT);
+    return Erel;
+}
+// FP32 mode: b1 of the collision-temperature split at E_x (J) from the
+// reaction's table, linear in log2 E_x and clamped at the ends
+static __device__ __forceinline__ float tcb_b1(const StepArgs& A, const DevReaction& rx, double Ex) {
+    const float* t = A.tcb + rx.tcb_off;
+    float u = (log2f((float)Ex) - (float)TCB_L0) * (float)TCB_PER_OCTAVE;
+    u = fminf(fmaxf(u, 0.0f), (float)(TCB_N - 1));
+    const int i = min((int)u, TCB_N - 2);
+    const float f = u - (float)i;
+    return t[i] + f * (t[i + 1] - t[i]);
 }
 
 // FP32 mode: QK reaction test in fixed point (exact thresholds), the same
@@ -1220,8 +1405,15 @@ static __device__ bool do_diss_fix(const StepArgs& A, const Consts* __restrict__
     for (int j = 0; j < 4; ++j) { qB[j] = 0u; qC[j] = 0u; }
     // products start in their ground states: B is drawn at Eav - ZPE_C, then C
     // at Eav - E_vib,B; what is left is translational
-    long long Etr = relax_flat(A, C, rx.P0, qB, sB.zpe_fix, sa, rx.P1, qC, sC.zpe_fix, sb,
-                               Eav - sB.zpe_fix - sC.zpe_fix, o);
+    long long Etr;
+    if (rx.prod_split == HCAO_SPLIT_TCOLL) {
+        const long long Ex = Eav - sB.zpe_fix - sC.zpe_fix;
+        Etr = relax_one_b(A, C, rx.P0, qB, sB.zpe_fix, sa, Ex, tcb_b1(A, rx, fix2d(Ex)), o);
+        Etr = relax_one_b(A, C, rx.P1, qC, sC.zpe_fix, sb, Etr, 2.0f, o);
+    } else {
+        Etr = relax_flat(A, C, rx.P0, qB, sB.zpe_fix, sa, rx.P1, qC, sC.zpe_fix, sb,
+                         Eav - sB.zpe_fix - sC.zpe_fix, o);
+    }
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
     float x = 0.5f;
     for (int it = 0; it < 4096; ++it) {  // Beta(3/2,3/2) by rejection under 1/2
@@ -1274,8 +1466,15 @@ static __device__ bool do_exch_fix(const StepArgs& A, const Consts* __restrict__
     st_init(sb, rs.seed, rs.step, lcell, rk, PU_LB_B);
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) { qC[j] = 0u; qD[j] = 0u; }
-    long long Etr = relax_flat(A, C, rx.P0, qC, sC.zpe_fix, sa, rx.P1, qD, sD.zpe_fix, sb,
-                               Eav - sC.zpe_fix - sD.zpe_fix, o);
+    long long Etr;
+    if (rx.prod_split == HCAO_SPLIT_TCOLL) {
+        const long long Ex = Eav - sC.zpe_fix - sD.zpe_fix;
+        Etr = relax_one_b(A, C, rx.P0, qC, sC.zpe_fix, sa, Ex, tcb_b1(A, rx, fix2d(Ex)), o);
+        Etr = relax_one_b(A, C, rx.P1, qD, sD.zpe_fix, sb, Etr, 0.5f, o);
+    } else {
+        Etr = relax_flat(A, C, rx.P0, qC, sC.zpe_fix, sa, rx.P1, qD, sD.zpe_fix, sb,
+                         Eav - sC.zpe_fix - sD.zpe_fix, o);
+    }
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
     const float gn = __fsqrt_rn(__fdiv_rn(__fmul_rn(2.0f, fix2f(Etr)), C->pair[rx.P0 * MAXS + rx.P1].mr_f));
     float d[3];
@@ -1318,7 +1517,9 @@ static __device__ bool do_recomb_fix(const StepArgs& A, const Consts* __restrict
     st_init(ss, rs.seed, rs.step, lcell, rk, PU_SCAT);
     for (int j = 0; j < 4; ++j) qA[j] = 0u;
     uint32_t qn[4] = {0u, 0u, 0u, 0u};
-    long long Etr = relax_flat(A, C, rx.P0, qA, sA.zpe_fix, sa, -1, qn, 0, sb, Eav - sA.zpe_fix, o);
+    long long Etr = rx.prod_split == HCAO_SPLIT_TCOLL
+                        ? relax_one_b(A, C, rx.P0, qA, sA.zpe_fix, sa, Eav - sA.zpe_fix, 0.5f, o)
+                        : relax_flat(A, C, rx.P0, qA, sA.zpe_fix, sa, -1, qn, 0, sb, Eav - sA.zpe_fix, o);
     if (Etr < 0) { Etr = 0; o.ev += 1u << EV_DEGEN_SHIFT; }
     const DevPair& pam = C->pair[rx.P0 * MAXS + spM];
     const float gn = sqrtf(fix2f(Etr) * pam.inv2mr_f);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhcao.so")
 
 FP64, FP32 = 0, 1
 PATH_AUTO, PATH_QUEUE, PATH_FUSED = 0, 1, 2
+SPLIT_RELAX, SPLIT_TCOLL = 0, 1
 DISS, EXCH, RECOMB = 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
           -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND",
@@ -66,7 +67,7 @@ class _Reaction(C.Structure):
                 ("diss_mode_mask", C.c_uint32), ("Ea", C.c_double), ("steric", C.c_double),
                 ("alpha_mode", C.c_int), ("alpha", C.POINTER(C.c_double)), ("model", C.c_int),
                 ("arrhenius", C.c_double * 3), ("tce_zeta", C.c_double), ("wr_samples", C.c_int),
-                ("gamma", C.c_double)]
+                ("gamma", C.c_double), ("prod_split", C.c_int)]
 
 
 class LogRec(C.Structure):
@@ -270,6 +271,8 @@ class Context:
             d.tce_zeta = getattr(r, "tce_zeta", 0.0)
             d.wr_samples = getattr(r, "wr_samples", 1000)
             d.gamma = getattr(r, "gamma", 0.0)
+            split = getattr(r, "product_split", "relaxation")
+            d.prod_split = {"relaxation": SPLIT_RELAX, "collision_temperature": SPLIT_TCOLL}[split]
         self._chk(self.L.hcao_set_reactions(self.h, arr, len(reactions)))
         self.n_reactions = len(reactions)
 

@@ -62,7 +62,7 @@ class Reaction:
     wr_samples: int = 1000
     gamma: float = 0.0              # rotation-vibration coupling: gamma E_rot,A in the QK collision energy
     product_split: str = "relaxation"  # products' levels: "relaxation" (reading A13) or
-                                       # "collision_temperature" (equipartition at T_c; oracle only)
+                                       # "collision_temperature" (equipartition at T_c)
 
 
 def triatomic() -> Species:
