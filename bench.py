@@ -7,8 +7,12 @@ One step = one collision phase over all cells.  `--workload heat_bath` times
 the 4096-cell x 500-particle CH4-like heat bath at 15000 K instead.
 
 Prints one JSON line.  `value` = particle-steps/s over the timed steps, device
-time from CUDA events on the library's stream, L2 flushed (a 256 MiB write)
-before every timed step (the particle state, 630 MB, is larger than L2 too).
+time from CUDA events on the library's stream around every step.  The
+exchange mixture's particle state (630 MB of records) is 5x the L2, so its
+steps run back to back without a flush; a state below twice the L2 (the heat
+bath, the triatomic) is flushed (a 256 MiB write) before every timed step.
+For the headline the same steps with a flush before each are reported
+beside it (`l2_flushed`).
 `e2e` = the same metric through the C ABI with host buffers: every step loads
 the state from pinned host memory, steps, and reads the moments back.
 --impl reference times the oracle (CPU) instead.
@@ -251,10 +255,31 @@ def cpu_baseline(kind: str = "exchange", budget_s: float = 12.0, cells: int = 48
                       f"{dt:.1f} s, on a host with {os.cpu_count()} cores"}
 
 
+L2_BYTES = 126 * 1024 * 1024
+
+
+def needs_flush(w, prec) -> bool:
+    """Timing rule: between timed steps either L2 is flushed or the state is
+    larger than L2.  A state below twice L2 (after the growth of a
+    dissociating workload) is flushed before every timed step."""
+    rec = 32 if prec == 1 else 64  # FP32 / FP64 record bytes
+    return w.n * rec < 2 * L2_BYTES
+
+
+def l2_note(w, prec) -> str:
+    rec = 32 if prec == 1 else 64
+    if needs_flush(w, prec):
+        return "flushed (256 MiB write) before every timed step"
+    return (f"not flushed: the particle state ({w.n * rec / 2**20:.0f} MiB of records) is "
+            f"{w.n * rec / L2_BYTES:.1f}x the 126 MB L2; steps run back to back as in a long run")
+
+
 def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> dict:
     """Device throughput of one more configuration: `warmup` untimed steps,
     then `steps` steps timed one by one with CUDA events (L2 flushed before
-    each); particle-steps counted from the particles entering each step."""
+    each unless the state is well above L2); particle-steps counted from the
+    particles entering each step."""
+    do_flush = needs_flush(w, prec)
     ctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream)
     for _ in range(warmup):
         ctx.step(1)
@@ -264,7 +289,8 @@ def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> 
     ms, ps = 0.0, 0
     for _ in range(steps):
         ps += ctx.count(0)
-        flush.zero_()
+        if do_flush:
+            flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         ctx.step(1)
@@ -279,7 +305,7 @@ def run_config(hcao, torch, stream, w, prec, steps: int, warmup: int, flush) -> 
             "reactions": [r.type for r in w.reactions],
             "composition": {"timed_start": comp0, "timed_end": comp1},
             "precision": "fp64" if prec == hcao.FP64 else "fp32", "steps": steps, "warmup": warmup,
-            "particle_steps_per_s": ps / t, "collisions_per_s": float(c1[1] - c0[1]) / t,
+            "l2": l2_note(w, prec), "particle_steps_per_s": ps / t, "collisions_per_s": float(c1[1] - c0[1]) / t,
             "reactions_per_s": float(sum(c1[8:]) - sum(c0[8:])) / t, "ms_per_step": 1e3 * t / steps}
 
 
@@ -380,6 +406,7 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
                     res[jid] = r
         time.sleep(0.001)
     _, _, _, iters = ctx.serve_stats()
+    timing = ctx.serve_timing()
     ctx.serve_stop()
     ctx.close()
     lat_s = [res[jid].t_done - (t0 + j.arrival) for jid, j in zip(ids, jobs)]
@@ -416,6 +443,10 @@ def run_served(hcao, prec, stream, n_jobs: int, rate: float, recombination: bool
             "served_particle_steps_per_s": sw.particle_steps / span_s,
             "plain_particle_steps_per_s": sw.particle_steps / span_p,
             "engine_iterations": int(iters),
+            "engine_time_s": timing,
+            "engine_note": "engine thread's host time by activity: admit (reservoir set-up and load "
+                           "from the job's host copy), step (step launches + synchronisation: the "
+                           "device busy with the resident jobs), retire (read-back, release), wait",
             "note": "jobs/s over the span from the first arrival to the last completion; the "
                     "plain loop serves the same arrivals first come first served"}
 
@@ -425,7 +456,7 @@ def _config(kind, w, args, ws):
     return {"workload": WORKLOADS[kind], "cells": w.n_cells * ws, "cells_per_rank": w.n_cells,
             "particles_per_cell": per_cell, "particles": w.n * ws, "T0_K": w.T_tr0, "precision": args.precision,
             "species": [s.name for s in w.species],
-            "l2": "flushed (256 MiB write) before every timed step; the particle state is larger than L2",
+            "l2": l2_note(w, 1 if args.precision == "fp32" else 0),
             "parallelism": f"contiguous cell ranges x{ws} (one workload of {ws} x {w.n_cells} cells, "
                            "keyed by global cell index; no data-path collective)"}
 
@@ -467,7 +498,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--batched-res", type=int, default=256, help="reservoirs of the batched run (0: skip)")
-    ap.add_argument("--batched-steps", type=int, default=12)
+    ap.add_argument("--batched-steps", type=int, default=1000)
     ap.add_argument("--served-jobs", type=int, default=48, help="jobs of the served run (0: skip)")
     ap.add_argument("--other-configs", type=int, default=1,
                     help="measure the exchange temperature sweep, the heat bath and the triatomic too")
@@ -502,13 +533,15 @@ def main():
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     psteps = 0
+    do_flush = needs_flush(w, prec)
     with Clocks(local) as clk:
         clk.start()
         t_wall0 = time.perf_counter()
         for i in range(args.steps):
             n = ctx.count(0)  # particles entering this step (host sync, outside the events)
             psteps += n
-            flush.zero_()
+            if do_flush:
+                flush.zero_()
             ev[i][0].record(stream)
             ctx.step(1)
             ev[i][1].record(stream)
@@ -521,19 +554,50 @@ def main():
     c1 = ctx.read_counters(0)
     comp1 = composition(ctx, w)
     launches = ctx.kernel_launches() - launches0
-    # the per-kernel split of the roofline: as many further steps, after the
-    # timed ones, with CUDA events around every kernel (launched one by one,
-    # not as the step's graph; outside the timed region)
-    work0 = ctx.read_work()
-    ctx.set_profiling(True)
+    ctx.close()
+    ctx = None
+    # The per-kernel split of the roofline: the same steps of the same
+    # workload (a fresh context from the same state, the same warm-up, so the
+    # same composition at every step), with CUDA events around every kernel
+    # (launched one by one, not as the step's graph); outside the timed region.
+    pctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
+    for _ in range(args.warmup):
+        pctx.step(1)
+    work0 = pctx.read_work()
+    pctx.set_profiling(True)
     psteps_prof = 0
     for i in range(args.steps):
-        psteps_prof += ctx.count(0)
-        flush.zero_()
-        ctx.step(1)
-    kms, kn = ctx.read_profile()
-    ctx.set_profiling(False)
-    work = (ctx.read_work() - work0).astype(np.float64)
+        psteps_prof += pctx.count(0)
+        if do_flush:
+            flush.zero_()
+        pctx.step(1)
+    kms, kn = pctx.read_profile()
+    pctx.set_profiling(False)
+    work_end = pctx.read_work()
+    pctx.close()
+    # The same steps again, with L2 flushed before each (cold tables at every
+    # step start), beside the headline when it runs without flushing.
+    l2_flushed = None
+    if not do_flush:
+        fctx = hcao.from_workload(w, precision=prec, stream=stream.cuda_stream, device=local)
+        for _ in range(args.warmup):
+            fctx.step(1)
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        psf = 0
+        for i in range(args.steps):
+            psf += fctx.count(0)
+            flush.zero_()
+            evf[i][0].record(stream)
+            fctx.step(1)
+            evf[i][1].record(stream)
+        torch.cuda.synchronize()
+        fctx.close()
+        msf = sum(a.elapsed_time(b) for a, b in evf)
+        l2_flushed = {"ms_per_step": msf / args.steps, "particle_steps_per_s": psf / (msf / 1e3),
+                      "note": "the timed steps again (fresh context, same warm-up), a 256 MiB write "
+                              "before each"}
+    work = (work_end - work0).astype(np.float64)
     collisions = float(c1[1] - c0[1])
     reactions = float(sum(c1[8:]) - sum(c0[8:]))
     tot_psteps, t = aggregate(float(psteps), ms / 1e3)
@@ -593,7 +657,8 @@ def main():
     # e2e through the C ABI with host buffers (pinned): load + step + moments
     e2e = None
     if args.e2e_steps > 0:
-        v_h = torch.from_numpy(w.v).pin_memory()
+        vdt = np.float32 if prec == hcao.FP32 else np.float64
+        v_h = torch.from_numpy(np.ascontiguousarray(w.v, dtype=vdt)).pin_memory()
         q_h = torch.from_numpy(w.qn0()).pin_memory()
         s_h = torch.from_numpy(w.species_idx).pin_memory()
         c_h = torch.from_numpy(w.cell).pin_memory()
@@ -603,12 +668,12 @@ def main():
         rid = ectx.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
         L = ectx.L
         import ctypes as C
+        load = L.hcao_load_particles_f32 if prec == hcao.FP32 else L.hcao_load_particles
         mom = hcao.Moments()
 
         def one():
-            ectx._chk(L.hcao_load_particles(ectx.h, rid, w.n, C.c_void_p(v_h.data_ptr()),
-                                            C.c_void_p(q_h.data_ptr()), C.c_void_p(s_h.data_ptr()),
-                                            C.c_void_p(c_h.data_ptr())))
+            ectx._chk(load(ectx.h, rid, w.n, C.c_void_p(v_h.data_ptr()), C.c_void_p(q_h.data_ptr()),
+                           C.c_void_p(s_h.data_ptr()), C.c_void_p(c_h.data_ptr())))
             ectx._chk(L.hcao_step(ectx.h, 1))
             ectx._chk(L.hcao_read_moments(ectx.h, rid, C.byref(mom)))
 
@@ -623,7 +688,7 @@ def main():
         # where an e2e step goes: each call timed alone (host clock, synchronised),
         # after the timed loop and outside it
         split = {}
-        for name, f in (("load", lambda: ectx._chk(L.hcao_load_particles(
+        for name, f in (("load", lambda: ectx._chk(load(
                             ectx.h, rid, w.n, C.c_void_p(v_h.data_ptr()), C.c_void_p(q_h.data_ptr()),
                             C.c_void_p(s_h.data_ptr()), C.c_void_p(c_h.data_ptr())))),
                         ("step", lambda: ectx._chk(L.hcao_step(ectx.h, 1))),
@@ -637,10 +702,11 @@ def main():
                 ts.append(time.perf_counter() - t1)
             split[name] = 1e3 * sorted(ts)[1]
         e2e = {"value": _sum_over_ranks(float(w.n * args.e2e_steps)) / te, "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(w.n * (24 + 16 + 4 + 4)),
+               "h2d_bytes_per_step": int(w.n * (3 * v_h.element_size() + 16 + 4 + 4)),
                "d2h_bytes_per_step": int(C.sizeof(hcao.Moments)),
                "split_ms": split,
-               "note": "per step: hcao_load_particles from pinned host memory (state of the "
+               "note": "per step: hcao_load_particles (FP32 velocities through hcao_load_particles_f32 "
+                       "in FP32 mode) from pinned host memory (state of the "
                        "workload), hcao_step(1), hcao_read_moments; split_ms: the median of 3 "
                        "separate synchronised calls of each, measured after the timed loop"}
         ectx.close()
@@ -648,8 +714,6 @@ def main():
 
     others = None
     if args.other_configs and ws == 1:
-        ctx.close()
-        ctx = None
         others = {}
         if args.workload != "exchange":
             others["ch4_h_exchange_16384x1200_4000K_fp32"] = run_config(
@@ -688,6 +752,7 @@ def main():
             "config": _config(args.workload, w, args, ws),
             "composition": {"timed_start": comp0, "timed_end": comp1},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "gpu_launches": int(launches),
+            "l2_flushed": l2_flushed,
             "clocks": clocks, "wall_s_timed_loop": t_wall, "batched": batched, "served": served,
             "other_configs": others,
         }

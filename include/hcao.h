@@ -235,6 +235,13 @@ hcao_status hcao_remove_reservoir(hcao_ctx* ctx, int res);
 hcao_status hcao_load_particles(hcao_ctx* ctx, int res, int64_t n, const double* host_v,
                                 const uint8_t* host_qn, const int32_t* host_species,
                                 const int32_t* host_cell);
+/* hcao_load_particles with FP32 host velocities (n x 3 floats): 12 instead of
+   24 bytes per particle cross the host-device link.  In FP32 mode the records
+   equal those of hcao_load_particles with the same values rounded to float;
+   in FP64 mode the floats are widened exactly. */
+hcao_status hcao_load_particles_f32(hcao_ctx* ctx, int res, int64_t n, const float* host_v,
+                                    const uint8_t* host_qn, const int32_t* host_species,
+                                    const int32_t* host_cell);
 /* Initial quantum numbers of all particles of res at T_vib on the device:
    bends i = floor(-ln(r) T_vib / Theta) (redrawn beyond the level list),
    stretches drawn uniformly over 0..i_diss and accepted with
@@ -445,6 +452,13 @@ hcao_status hcao_serve_stop(hcao_ctx* ctx);
 /* Queue length, resident jobs, budgeted bytes in use, engine iterations. */
 hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, int64_t* used_bytes,
                              uint64_t* iterations);
+/* The engine thread's time since hcao_serve_start by activity, host clock in
+   seconds, into seconds4[4]: [0] admission (reservoir set-up, the load from
+   the job's host copy, initial levels), [1] stepping (the iterations' step
+   launches and their synchronisation: the device busy with resident jobs),
+   [2] retirement (moments, counters, release), [3] waiting for work.
+   Thread-safe; HCAO_EINVAL for a null argument. */
+hcao_status hcao_serve_timing(hcao_ctx* ctx, double* seconds4);
 
 /* The tabulated recombination rate coefficient k_r (m^6/s) of reaction
    `reaction` (an HCAO_RECOMB) with a third body of species spM at temperature

@@ -160,6 +160,10 @@ struct hcao_ctx {
     int64_t serve_budget = 0, serve_used = 0;
     int serve_max_active = 256, serve_max_batch_steps = 64;
     uint64_t serve_iterations = 0;
+    // engine time by activity (host clock, s): admission (reservoir set-up,
+    // load, initial levels), stepping (the iterations' graph launches and
+    // their synchronisation), retirement (read-back, release), waiting
+    double serve_t[4] = {0.0, 0.0, 0.0, 0.0};
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint64_t pairs_need = 0;        // pair slots the current layout needs (set by relayout)
@@ -1583,31 +1587,34 @@ hcao_status hcao_cell_sort(hcao_ctx* ctx, const uint32_t* keys, int64_t n, uint3
     return HCAO_OK;
 }
 
-hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* v, const uint8_t* qn,
-                                const int32_t* species, const int32_t* cell) {
+// One load path for FP64 (v) or FP32 (vf) host velocities, exactly one given.
+static hcao_status load_impl(hcao_ctx* ctx, int id, int64_t n, const double* v, const float* vf,
+                             const uint8_t* qn, const int32_t* species, const int32_t* cell) {
     DeviceScope ds_(ctx);
     SERVE_GUARD(ctx);
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "load_particles: no such reservoir");
-    if (n < 0 || n > 0x7FFFFFFFll || (n > 0 && (!v || !qn || !species || !cell)))
+    if (n < 0 || n > 0x7FFFFFFFll || (n > 0 && ((!v && !vf) || !qn || !species || !cell)))
         return fail(ctx, HCAO_EINVAL, "load_particles: bad arguments");
     CU(cudaStreamSynchronize(ctx->stream));
     // stage the host arrays; validate and count on the device (a sort by cell
     // gives the per-cell counts); host work stays O(cells)
     double* dv = nullptr;
+    float* dvf = nullptr;
     uint8_t* dq = nullptr;
     int32_t* ds = nullptr;
     uint32_t *dk = nullptr, *dperm = nullptr, *doff = nullptr, *dflags = nullptr;
     uint64_t* dslot = nullptr;
     auto release = [&]() {
-        dfree(ctx, dv); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dk);
+        dfree(ctx, dv); dfree(ctx, dvf); dfree(ctx, dq); dfree(ctx, ds); dfree(ctx, dk);
         dfree(ctx, dperm); dfree(ctx, doff); dfree(ctx, dslot); dfree(ctx, dflags);
     };
     std::vector<uint32_t> off((size_t)r->n_cells + 1, 0u);
     uint32_t flags[2] = {0u, 0u};
     if (n > 0) {
-        CU(dalloc(ctx, &dv, (size_t)n * 3));
+        if (vf) CU(dalloc(ctx, &dvf, (size_t)n * 3));
+        else CU(dalloc(ctx, &dv, (size_t)n * 3));
         CU(dalloc(ctx, &dq, (size_t)n * 16));
         CU(dalloc(ctx, &ds, (size_t)n));
         CU(dalloc(ctx, &dk, (size_t)n));
@@ -1616,7 +1623,8 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
         CU(dalloc(ctx, &dslot, (size_t)r->n_cells));
         CU(dalloc(ctx, &dflags, 2));
         CU(cudaMemsetAsync(dflags, 0, 2 * sizeof(uint32_t), ctx->stream));
-        CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        if (vf) CU(cudaMemcpyAsync(dvf, vf, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        else CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -1692,9 +1700,9 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
         // scatter the staged particles into their cells' slots in sorted order
         CU(cudaMemcpyAsync(dslot, slot0.data(), sizeof(uint64_t) * r->n_cells, cudaMemcpyHostToDevice, ctx->stream));
         if (ctx->cfg.precision == HCAO_FP64)
-            launch_scatter_load<double>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
+            launch_scatter_load<double>(r->recs, dperm, doff, dslot, r->n_cells, dv, dvf, dq, ds, n, ctx->stream);
         else
-            launch_scatter_load<float>(r->recs, dperm, doff, dslot, r->n_cells, dv, dq, ds, n, ctx->stream);
+            launch_scatter_load<float>(r->recs, dperm, doff, dslot, r->n_cells, dv, dvf, dq, ds, n, ctx->stream);
         ctx->launches++;
         CU(cudaGetLastError());
         release();
@@ -1712,6 +1720,16 @@ hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* 
     CU(cudaMemcpyAsync(ctx->d_res + id, &dr, sizeof dr, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return HCAO_OK;
+}
+
+hcao_status hcao_load_particles(hcao_ctx* ctx, int id, int64_t n, const double* v, const uint8_t* qn,
+                                const int32_t* species, const int32_t* cell) {
+    return load_impl(ctx, id, n, v, nullptr, qn, species, cell);
+}
+
+hcao_status hcao_load_particles_f32(hcao_ctx* ctx, int id, int64_t n, const float* v, const uint8_t* qn,
+                                    const int32_t* species, const int32_t* cell) {
+    return load_impl(ctx, id, n, nullptr, v, qn, species, cell);
 }
 
 hcao_status hcao_init_vibration(hcao_ctx* ctx, int id, double T) {
@@ -2371,11 +2389,13 @@ static void serve_loop(hcao_ctx* ctx) {
     for (;;) {
         // ---- admission
         std::vector<std::shared_ptr<Job>> admit;
+        double t0 = now_s();
         {
             std::unique_lock<std::mutex> lock(ctx->serve_mu);
             if (ctx->serve_active.empty() && ctx->serve_queue.empty()) {
                 if (ctx->serve_stop) return;
                 ctx->serve_cv.wait_for(lock, std::chrono::milliseconds(20));
+                ctx->serve_t[3] += now_s() - t0;
                 continue;
             }
             while (!ctx->serve_queue.empty() && (int)ctx->serve_active.size() + (int)admit.size() < ctx->serve_max_active) {
@@ -2414,6 +2434,11 @@ static void serve_loop(hcao_ctx* ctx) {
             jb->result.t_admit = now_s();
             ctx->serve_active.push_back(jb);
         }
+        {
+            const double t1 = now_s();
+            ctx->serve_t[0] += t1 - t0;
+            t0 = t1;
+        }
         if (ctx->serve_active.empty()) continue;
         // ---- one engine iteration: every resident job advances K steps
         int K = ctx->serve_max_batch_steps;
@@ -2437,6 +2462,11 @@ static void serve_loop(hcao_ctx* ctx) {
             for (auto& jb : ctx->serve_active) jb->steps_left -= K;
             ctx->serve_iterations++;
         }
+        {
+            const double t1 = now_s();
+            ctx->serve_t[1] += t1 - t0;
+            t0 = t1;
+        }
         // ---- retirement
         std::vector<std::shared_ptr<Job>> keep;
         for (auto& jb : ctx->serve_active) {
@@ -2456,6 +2486,7 @@ static void serve_loop(hcao_ctx* ctx) {
             jb->state = st == HCAO_OK ? 2 : 3;
         }
         ctx->serve_active.swap(keep);
+        ctx->serve_t[2] += now_s() - t0;
     }
 }
 
@@ -2474,6 +2505,7 @@ hcao_status hcao_serve_start(hcao_ctx* ctx, int64_t hbm_budget_bytes, int max_ac
     ctx->serve_max_active = max_active > 0 ? max_active : 256;
     ctx->serve_max_batch_steps = max_batch_steps > 0 ? max_batch_steps : 8;
     ctx->serve_used = 0;
+    for (double& t : ctx->serve_t) t = 0.0;
     ctx->serve_stop = false;
     ctx->serve_running = true;
     ctx->serve_thread = std::thread(serve_loop, ctx);
@@ -2543,6 +2575,13 @@ hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, in
     if (active) *active = (int64_t)ctx->serve_active.size();
     if (used_bytes) *used_bytes = ctx->serve_used;
     if (iterations) *iterations = ctx->serve_iterations;
+    return HCAO_OK;
+}
+
+hcao_status hcao_serve_timing(hcao_ctx* ctx, double* seconds4) {
+    if (!ctx || !seconds4) return HCAO_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    for (int i = 0; i < 4; ++i) seconds4[i] = ctx->serve_t[i];
     return HCAO_OK;
 }
 

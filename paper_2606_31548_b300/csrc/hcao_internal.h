@@ -256,8 +256,9 @@ template <class R> void launch_cellstats(const StepArgs& a, cudaStream_t s);
 template <class R> void launch_compact(const StepArgs& a, cudaStream_t s);
 template <class R> void launch_scatter_load(void* rec_base, const uint32_t* perm,
                                             const uint32_t* offsets, const uint64_t* cell_slot0,
-                                            int n_cells, const double* v, const uint8_t* qn,
-                                            const int32_t* sp, int64_t n, cudaStream_t s);
+                                            int n_cells, const double* v, const float* vf,
+                                            const uint8_t* qn, const int32_t* sp, int64_t n,
+                                            cudaStream_t s);
 template <class R> void launch_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
                                     uint64_t total, const Consts* C, double* v, uint8_t* qn, int32_t* sp,
                                     int32_t* cell, cudaStream_t s);

@@ -188,7 +188,7 @@ __device__ __forceinline__ void set_q(uint32_t q[4], int j, uint32_t v) {
 #define REC_LD(p) __ldcs(p)
 #define REC_ST(p, v) __stcs((p), (v))
 #ifndef HCAO_RELAX_MINB
-#define HCAO_RELAX_MINB 4
+#define HCAO_RELAX_MINB 8
 #endif
 __device__ __forceinline__ void load_rec(const RecF* p, RecF& r) {
     const uint4* s = reinterpret_cast<const uint4*>(p);
@@ -2922,7 +2922,8 @@ __global__ void k_sample_diag(StepArgs A, int sp, double Ec, uint64_t seed, int6
 template <class R>
 __global__ void k_scatter_load(typename RecOf<R>::T* recs, const uint32_t* perm,
                                const uint32_t* offsets, const uint64_t* slot0, int n_cells,
-                               const double* v, const uint8_t* qn, const int32_t* sp, int64_t n) {
+                               const double* v, const float* vf, const uint8_t* qn, const int32_t* sp,
+                               int64_t n) {
     using Rec = typename RecOf<R>::T;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -2934,7 +2935,7 @@ __global__ void k_scatter_load(typename RecOf<R>::T* recs, const uint32_t* perm,
         }
         const uint32_t i = perm[j];
         Rec r;
-        for (int d = 0; d < 3; ++d) r.v[d] = (R)v[3 * (int64_t)i + d];
+        for (int d = 0; d < 3; ++d) r.v[d] = vf ? (R)vf[3 * (int64_t)i + d] : (R)v[3 * (int64_t)i + d];
         r.meta = (uint32_t)sp[i];
         const uint32_t* q = reinterpret_cast<const uint32_t*>(qn + 16 * (int64_t)i);
         for (int w = 0; w < 4; ++w) r.q[w] = q[w];
@@ -3210,13 +3211,13 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, const u
     template <>                                                                                  \
     void launch_scatter_load<R>(void* rec_base, const uint32_t* perm, const uint32_t* offsets,   \
                                 const uint64_t* slot0, int n_cells, const double* v,             \
-                                const uint8_t* qn, const int32_t* sp, int64_t n,                 \
+                                const float* vf, const uint8_t* qn, const int32_t* sp, int64_t n, \
                                 cudaStream_t s) {                                                \
         if (n <= 0) return;                                                                      \
         int grid = (int)((n + 255) / 256);                                                       \
         if (grid > 4096) grid = 4096;                                                            \
         k_scatter_load<R><<<grid, 256, 0, s>>>(reinterpret_cast<typename RecOf<R>::T*>(rec_base), \
-                                               perm, offsets, slot0, n_cells, v, qn, sp, n);     \
+                                               perm, offsets, slot0, n_cells, v, vf, qn, sp, n); \
     }                                                                                            \
     template <>                                                                                  \
     void launch_pack<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,       \

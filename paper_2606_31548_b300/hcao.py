@@ -35,7 +35,7 @@ EXPORTS = [
     "hcao_read_work", "hcao_autotune", "hcao_serve_start", "hcao_serve_submit", "hcao_serve_poll",
     "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
     "hcao_set_step_path", "hcao_get_step_path", "hcao_set_cell_base", "hcao_init_rotation",
-    "hcao_load_erot", "hcao_read_erot",
+    "hcao_load_erot", "hcao_read_erot", "hcao_load_particles_f32", "hcao_serve_timing",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -121,6 +121,8 @@ def lib() -> C.CDLL:
         L.hcao_add_reservoir.argtypes = [vp, i32, dbl, dbl, dbl, u64, dbl, C.POINTER(i32)]
         L.hcao_remove_reservoir.argtypes = [vp, i32]
         L.hcao_load_particles.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+        L.hcao_load_particles_f32.argtypes = [vp, i32, i64, vp, vp, vp, vp]
+        L.hcao_serve_timing.argtypes = [vp, vp]
         L.hcao_init_vibration.argtypes = [vp, i32, dbl]
         L.hcao_step.argtypes = [vp, i32]
         L.hcao_sync.argtypes = [vp]
@@ -290,11 +292,15 @@ class Context:
         self._chk(self.L.hcao_remove_reservoir(self.h, res))
 
     def load_particles(self, res, v, qn, species, cell) -> None:
-        v = np.ascontiguousarray(v, dtype=np.float64)
+        """FP32 velocity arrays go through hcao_load_particles_f32 (half the
+        bytes over the host-device link), anything else as FP64."""
+        f32 = isinstance(v, np.ndarray) and v.dtype == np.float32
+        v = np.ascontiguousarray(v, dtype=np.float32 if f32 else np.float64)
         qn = np.ascontiguousarray(qn, dtype=np.uint8)
         species = np.ascontiguousarray(species, dtype=np.int32)
         cell = np.ascontiguousarray(cell, dtype=np.int32)
-        self._chk(self.L.hcao_load_particles(self.h, res, v.shape[0], _p(v), _p(qn), _p(species), _p(cell)))
+        fn = self.L.hcao_load_particles_f32 if f32 else self.L.hcao_load_particles
+        self._chk(fn(self.h, res, v.shape[0], _p(v), _p(qn), _p(species), _p(cell)))
 
     def init_vibration(self, res, T_vib) -> None:
         self._chk(self.L.hcao_init_vibration(self.h, res, T_vib))
@@ -473,6 +479,12 @@ class Context:
         q, a, b, it = C.c_int64(), C.c_int64(), C.c_int64(), C.c_uint64()
         self._chk(self.L.hcao_serve_stats(self.h, C.byref(q), C.byref(a), C.byref(b), C.byref(it)))
         return q.value, a.value, b.value, it.value
+
+    def serve_timing(self) -> dict:
+        """The engine thread's seconds by activity since serve_start."""
+        t = np.zeros(4)
+        self._chk(self.L.hcao_serve_timing(self.h, _p(t)))
+        return {"admit_s": float(t[0]), "step_s": float(t[1]), "retire_s": float(t[2]), "wait_s": float(t[3])}
 
 
 def from_batched(bw, precision=FP64, init_vib=True, **kw) -> Context:

@@ -126,3 +126,28 @@ def test_tvib_equals_translational_temperature_at_equilibrium():
     g.step(200)
     m = g.read_moments(0)
     assert abs(m.T_vib[0] - m.T_tr) / m.T_tr < 0.03, (m.T_vib[0], m.T_tr)
+
+
+@pytest.mark.parametrize("precision", [hcao.FP32, hcao.FP64])
+def test_load_with_fp32_velocities(precision):
+    """hcao_load_particles_f32 (12 bytes of velocity per particle over the
+    link) gives the records of hcao_load_particles with the same values, and
+    the same run after three steps."""
+    w = W.ch4_heat_bath(n_cells=37, per_cell=123)
+    vf = w.v.astype(np.float32)
+    ctxs = []
+    for v in (vf.astype(np.float64), vf):
+        g = hcao.Context(precision=precision)
+        g.set_species(w.species)
+        g.set_reactions(w.reactions)
+        rid = g.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+        g.load_particles(rid, v, w.qn0(), w.species_idx, w.cell)
+        g.init_vibration(rid, w.T_vib0)
+        ctxs.append(g)
+    for steps in (0, 3):
+        if steps:
+            for g in ctxs:
+                g.step(steps)
+        a, b = ctxs[0].read_particles(0), ctxs[1].read_particles(0)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)

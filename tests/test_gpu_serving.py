@@ -78,9 +78,12 @@ def test_served_jobs_equal_alone(precision):
             time.sleep(0.05)  # the first wave is already running
     res = _wait(ctx, ids)
     q, a, used, iters = ctx.serve_stats()
+    t = ctx.serve_timing()
     ctx.serve_stop()
     assert q == 0 and a == 0 and used == 0
     assert iters >= max(steps) // 4
+    # the engine's time by activity: every job was admitted, stepped and retired
+    assert t["admit_s"] > 0 and t["step_s"] > 0 and t["retire_s"] > 0 and t["wait_s"] >= 0
     for i, w in enumerate(bw.reservoirs):
         _same(res[ids[i]], _alone(bw, w, steps[i], precision))
         assert res[ids[i]].steps == steps[i]
