@@ -121,6 +121,7 @@ struct hcao_ctx {
     uint32_t* d_abase = nullptr;
     uint32_t* d_totals = nullptr;
     uint32_t* d_cflag = nullptr;
+    uint32_t* d_rmpos = nullptr;
     void* d_cscratch = nullptr;
     uint4* d_qA = nullptr;
     uint4* d_qB = nullptr;
@@ -840,6 +841,7 @@ hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
         const uint64_t cap = std::max<uint64_t>({pairs, (uint64_t)1024, ctx->pair_cap + ctx->pair_cap / 2});
         ctx->pair_cap = 0;
         dfree(ctx, ctx->d_cflag);
+        dfree(ctx, ctx->d_rmpos);
         dfree(ctx, ctx->d_log);
         if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
         ctx->d_cscratch = nullptr;
@@ -848,6 +850,7 @@ hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
         CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)cap));  // FP32: three regions, see StepArgs::qsize
         CU(dalloc(ctx, &ctx->d_qB, (size_t)cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)cap));
+        CU(dalloc(ctx, &ctx->d_rmpos, (size_t)cap));
         CU(dalloc(ctx, &ctx->d_cflag, (size_t)cap));  // last: its presence marks a complete set
         ctx->pair_cap = cap;
     }
@@ -887,6 +890,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.abase = ctx->d_abase;
     a.totals = ctx->d_totals;
     a.cflag = ctx->d_cflag;
+    a.rmpos = ctx->d_rmpos;
     a.cscratch = ctx->d_cscratch;
     a.qA = ctx->d_qA;
     a.qB = ctx->d_qB;
@@ -1046,6 +1050,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_abase);
     dfree(ctx, ctx->d_totals);
     dfree(ctx, ctx->d_cflag);
+    dfree(ctx, ctx->d_rmpos);
     if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
     dfree(ctx, ctx->d_log);
     dfree(ctx, ctx->d_qA);

@@ -166,6 +166,7 @@ struct DevCell {
     uint32_t nsel, ncreated;
     float sgmax_f;                    // FP32 copy of sgmax for the step
     uint32_t nremoved;                // particles removed this step (recombination)
+    uint32_t rmfill;                  // removed positions gathered into rmpos this step
     uint32_t pkey[MAX_ROUNDS][4];     // pairing-permutation keys per round of this step
 };
 
@@ -200,6 +201,8 @@ struct StepArgs {
     uint32_t* chbase;               // [n_cells + 1]: prefix of FINISH_CHUNK chunks of each cell's pairs
     uint32_t* chcnt;                // [chunks]: particles created in each chunk
     uint32_t* cflag;                // per-pair event word (acceptance, reaction, creation, trials)
+    uint32_t* rmpos;                // recombination: a cell's removed positions at its event
+                                    // slots [abase, abase + nremoved), gathered by k_finish_count
     void* cscratch;                 // per-pair record of a particle created by a reaction
     uint4* qA;                      // [2 pair_cap] accepted pairs of the current round (cell, pair, ip, iq)
     uint4* qB;                      // reacting pairs (cell, pair, channel)

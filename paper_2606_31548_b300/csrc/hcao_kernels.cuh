@@ -2553,9 +2553,12 @@ __global__ void __launch_bounds__(128) k_react(StepArgs A, int r) {
 // chunks (prefix chbase, built by k_setup); one warp takes one chunk, so a
 // cell of 500 particles costs one warp and a cell of 4M about a thousand.
 // k_finish_count: per chunk, the event words reduced into the cell's
-// counters, and the number of particles the chunk's reactions created.
+// counters, and the number of particles the chunk's reactions created; the
+// positions of particles removed by recombination gathered into the cell's
+// list (rmpos at the cell's event slots, in no particular order).
 template <class R>
 __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
+    using Rec = typename RecOf<R>::T;
     const int lane = threadIdx.x & 31;
     const uint32_t nch = A.totals[MAX_ROUNDS + 1];
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -2576,7 +2579,12 @@ __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
             over += (ev >> EV_OVER_SHIFT) & 3u;
             degen += (ev >> EV_DEGEN_SHIFT) & 3u;
             notex += (ev & EV_NOTEXEC) ? 1u : 0u;
-            removed += (ev & EV_REMOVED) ? 1u : 0u;
+            if (ev & EV_REMOVED) {
+                removed++;
+                const uint32_t slot = atomicAdd(&cl.rmfill, 1u);
+                A.rmpos[base + slot] =
+                    reinterpret_cast<const uint32_t*>(reinterpret_cast<const Rec*>(A.cscratch) + base + j)[0];
+            }
             created += (ev & EV_CREATED) ? 1u : 0u;
             trials += ev >> EV_TRIAL_SHIFT;
             const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
@@ -2767,32 +2775,26 @@ __global__ void __launch_bounds__(256) k_cellstats(StepArgs A) {
 // d removed among a cell's n records, the surviving records at positions
 // >= n - d move, in increasing position order, into the removed positions
 // below n - d, taken in increasing order.  One CTA per cell with removals:
-// the removed positions (kept in the pairs' scratch slots) are gathered and
-// sorted in shared memory.
+// the removed positions (gathered by k_finish_count, over all the cell's
+// chunks) are sorted in shared memory.
 template <class R>
 __global__ void __launch_bounds__(256) k_compact(StepArgs A) {
     using Rec = typename RecOf<R>::T;
     __shared__ uint32_t pos[MAX_REMOVALS];
-    __shared__ uint32_t cnt;
     for (int c = blockIdx.x; c < A.n_cells; c += gridDim.x) {
         DevCell& cl = A.cells[c];
         const uint32_t d = cl.nremoved;
         if (d == 0u) continue;
         __syncthreads();
         if (d > (uint32_t)MAX_REMOVALS) {
-            if (threadIdx.x == 0) atomicOr(A.err, (uint32_t)ERR_CAPACITY);
+            if (threadIdx.x == 0) {
+                atomicOr(A.err, (uint32_t)ERR_CAPACITY);
+                cl.rmfill = 0u;
+            }
             continue;
         }
-        const uint32_t nsel = cl.nsel, base = A.abase[c];
-        if (threadIdx.x == 0) cnt = 0u;
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < nsel; j += blockDim.x)
-            if (A.cflag[base + j] & EV_REMOVED) {
-                const uint32_t slot = atomicAdd(&cnt, 1u);
-                if (slot < (uint32_t)MAX_REMOVALS)
-                    pos[slot] = reinterpret_cast<const uint32_t*>(reinterpret_cast<const Rec*>(A.cscratch) +
-                                                                  base + j)[0];
-            }
+        const uint32_t base = A.abase[c];
+        for (uint32_t j = threadIdx.x; j < d; j += blockDim.x) pos[j] = A.rmpos[base + j];
         __syncthreads();
         uint32_t P = 1;
         while (P < d) P <<= 1;
@@ -2833,6 +2835,7 @@ __global__ void __launch_bounds__(256) k_compact(StepArgs A) {
         if (threadIdx.x == 0) {
             cl.n = t0;
             cl.nremoved = 0u;
+            cl.rmfill = 0u;
         }
     }
 }
