@@ -1507,6 +1507,19 @@ hcao_status hcao_set_reactions(hcao_ctx* ctx, const hcao_reaction* rx, int n) {
         D.dEf_fix = to_fix(D.dEf);
         D.Ea_fix = to_fix(D.Ea);
     }
+    // species pairs that some QK dissociation or exchange can take (the
+    // FP32 relaxation kernel skips the QK test for all others)
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            uint32_t qk = 0u;
+            for (int i = 0; i < n; ++i) {
+                const DevReaction& D = C.rx[i];
+                if (D.model == HCAO_MODEL_TCE) continue;
+                if (D.type == HCAO_DISS && (D.A == a || D.A == b)) qk = 1u;
+                if (D.type == HCAO_EXCH && ((D.A == a && D.B == b) || (D.A == b && D.B == a))) qk = 1u;
+            }
+            C.pair[a * MAXS + b].qk = qk;
+        }
     C.n_reactions = n;
     C.creates = creates;
     C.has_recomb = n_rec > 0 ? 1 : 0;

@@ -120,7 +120,8 @@ struct alignas(16) AliasEnt {
 
 struct DevPair {
     double mr, C, mt, fp, fq;        // reduced mass, VHS constant, total mass, velocity shares
-    float mr_f, C_f, fp_f, fq_f, inv2mr_f, pad_f;
+    float mr_f, C_f, fp_f, fq_f, inv2mr_f;
+    uint32_t qk;                     // a QK dissociation or exchange exists for this species pair
 };
 
 // DISS: A + M -> P0 + P1; EXCH: A + B -> P0 + P1; RECOMB: A + B (+ M) -> P0

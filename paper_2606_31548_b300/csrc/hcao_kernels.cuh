@@ -2291,13 +2291,13 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         bool react = false;
         uint32_t chan = 0u, mpos = 0u;
         if (C->n_reactions > 0) {
-            const float sgf = sg_f32(pc, C->amode, g2);
-            if (C->has_recomb && recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sgf, chan, mpos)) {
+            if (C->has_recomb &&
+                recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sg_f32(pc, C->amode, g2), chan, mpos)) {
                 react = true;
             } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
                                                      fix2d(EvQ), chan, (double)erP, (double)erQ)) {
                 react = true;
-            } else {
+            } else if (pc.qk) {  // a pair no QK reaction can take draws nothing from this stream
                 Stream sp;
                 st_init(sp, rs.seed, step, lcell, rk, PU_PAIR);
                 st_u32(sp);  // the acceptance draw
@@ -2351,20 +2351,22 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         A.cflag[ev_idx] = ev_final(o);
         if (A.log_on) A.log[ev_idx] = hcao_log_rec{step, lcell, rk, ip, iq, 0, 0u};
     }
-    // work counters: one atomic per warp and counter
-    const unsigned act = __activemask();
-    unsigned long long wl = w[0], wm = w[1], ws = w_samp, wp = w_pair;
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        wl += __shfl_xor_sync(act, wl, o2);
-        wm += __shfl_xor_sync(act, wm, o2);
-        ws += __shfl_xor_sync(act, ws, o2);
-        wp += __shfl_xor_sync(act, wp, o2);
+    // work counters: reduced over the CTA, one atomic per CTA and counter
+    // (none for a CTA without work: an empty round's launch stays cheap)
+    __shared__ unsigned long long wred[4][4];
+    unsigned long long wv[4] = {w[0], w[1], w_samp, w_pair};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        for (int o2 = 16; o2 > 0; o2 >>= 1) wv[i] += __shfl_xor_sync(0xFFFFFFFFu, wv[i], o2);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) wred[threadIdx.x >> 5][i] = wv[i];
     }
-    if ((threadIdx.x & 31) == 0 && A.work) {
-        atomicAdd(A.work + 0, wl);
-        atomicAdd(A.work + 1, wm);
-        atomicAdd(A.work + 2, ws);
-        atomicAdd(A.work + 3, wp);
+    __syncthreads();
+    if (threadIdx.x < 4 && A.work) {
+        const unsigned long long t = wred[0][threadIdx.x] + wred[1][threadIdx.x] + wred[2][threadIdx.x] +
+                                     wred[3][threadIdx.x];
+        if (t) atomicAdd(A.work + threadIdx.x, t);
     }
 }
 
