@@ -104,6 +104,21 @@ def test_parity_recombination_fp64(case):
         assert np.any((lg["round_k"] >> 24) >= 1)
 
 
+def test_parity_recombination_single_large_cell_fp64():
+    """One cell of 12,000 particles (its event slots span several 1024-slot
+    chunks, so the removed positions are gathered by several warps in no
+    fixed order before the compaction sorts them): bit-exact with the
+    oracle."""
+    w = W.ch4_recombination(n_cells=1, per_cell=12000, T0=2500.0, n_density=1e26)
+    g = hcao.from_workload(w, precision=hcao.FP64, log=True)
+    o = oracle.from_workload(w, log=True)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        _assert_same(g, o)
+    assert g.read_counters(0)[9] > 50  # recombinations happened
+
+
 def _totals(g, species):
     m = g.read_moments(0)
     E = m.E_tr + sum(m.E_vib[i] for i in range(16)) + m.E_form
