@@ -42,7 +42,8 @@ typedef enum {
     HCAO_ECAPACITY = -7,       /* a cell ran out of particle slots */
     HCAO_EROUNDS = -8,         /* NTC needed more pairing rounds than configured */
     HCAO_ENOTFOUND = -9,
-    HCAO_ENONFINITE = -10      /* a non-finite velocity or (sigma_T g)_max was met */
+    HCAO_ENONFINITE = -10,     /* a non-finite velocity or (sigma_T g)_max was met */
+    HCAO_ECANCELLED = -11      /* a served job cancelled before it finished */
 } hcao_status;
 
 enum { HCAO_FP64 = 0, HCAO_FP32 = 1 };
@@ -447,6 +448,12 @@ hcao_status hcao_serve_submit(hcao_ctx* ctx, const hcao_job* job, uint64_t* job_
    and returns its status (HCAO_ENOTFOUND for an unknown or released id).
    Thread-safe. */
 hcao_status hcao_serve_poll(hcao_ctx* ctx, uint64_t job_id, hcao_job_result* out);
+/* Cancel a served job: a queued job is dropped at once; a resident job is
+   retired at the end of the engine's current iteration (its reservoir
+   removed, its steps so far discarded).  Either way the job's result reports
+   HCAO_ECANCELLED with t_done set.  HCAO_ENOTFOUND for an unknown, finished
+   or released id.  Thread-safe. */
+hcao_status hcao_serve_cancel(hcao_ctx* ctx, uint64_t job_id);
 /* Finishes the queued and resident jobs, then stops the engine thread. */
 hcao_status hcao_serve_stop(hcao_ctx* ctx);
 /* Queue length, resident jobs, budgeted bytes in use, engine iterations. */
@@ -459,6 +466,18 @@ hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, in
    [2] retirement (moments, counters, release), [3] waiting for work.
    Thread-safe; HCAO_EINVAL for a null argument. */
 hcao_status hcao_serve_timing(hcao_ctx* ctx, double* seconds4);
+/* Clear the context's device error word.  Device-side conditions (a
+   rejection loop at its cap, a cell out of slots, more rounds needed, a
+   non-finite value) set a sticky word that every synchronising call reports
+   until it is cleared; the particle state stays consistent (a failed draw
+   keeps the molecule's state), so a caller may clear it and carry on. */
+hcao_status hcao_clear_error(hcao_ctx* ctx);
+/* Fault injection for tests (a host-side fault: no device fault, trap or
+   hang): the context's next n device allocations of per-call buffers
+   (staging, scratch, per-pair buffers, tables) fail as out of memory, so the
+   calls that make them return HCAO_ENOMEM as a real shortage would.  n <= 0
+   disarms it.  Thread-safe. */
+hcao_status hcao_debug_fail_allocs(hcao_ctx* ctx, int n);
 
 /* The tabulated recombination rate coefficient k_r (m^6/s) of reaction
    `reaction` (an HCAO_RECOMB) with a third body of species spM at temperature

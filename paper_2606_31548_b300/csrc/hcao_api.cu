@@ -17,6 +17,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -69,6 +70,7 @@ struct Job {
     int steps_left = 0;
     int64_t est_bytes = 0;
     int state = 0;         // 0 queued, 1 resident, 2 done, 3 failed
+    bool cancel = false;   // resident and cancelled: retired at the iteration's end
     hcao_job_result result{};
 };
 
@@ -165,6 +167,7 @@ struct hcao_ctx {
     // load, initial levels), stepping (the iterations' graph launches and
     // their synchronisation), retirement (read-back, release), waiting
     double serve_t[4] = {0.0, 0.0, 0.0, 0.0};
+    std::atomic<int> fail_allocs{0};  // test fault injection: device allocations left to fail
     hcao_log_rec* d_log = nullptr;
     uint64_t pair_cap = 0;
     uint64_t pairs_need = 0;        // pair slots the current layout needs (set by relayout)
@@ -236,6 +239,8 @@ template <class T>
 cudaError_t dalloc(hcao_ctx* ctx, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (ctx->fail_allocs.load() > 0 && ctx->fail_allocs.fetch_sub(1) > 0)  // test fault injection
+        return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), count * sizeof(T), ctx->pool, ctx->stream);
 }
 template <class T>
@@ -2488,6 +2493,20 @@ static void serve_loop(hcao_ctx* ctx) {
         // ---- retirement
         std::vector<std::shared_ptr<Job>> keep;
         for (auto& jb : ctx->serve_active) {
+            bool cancelled;
+            {
+                std::lock_guard<std::mutex> lock(ctx->serve_mu);
+                cancelled = jb->cancel;
+            }
+            if (cancelled) {
+                hcao_remove_reservoir(ctx, jb->res);
+                std::lock_guard<std::mutex> lock(ctx->serve_mu);
+                ctx->serve_used -= jb->est_bytes;
+                jb->result.status = HCAO_ECANCELLED;
+                jb->result.t_done = now_s();
+                jb->state = 3;
+                continue;
+            }
             if (jb->steps_left > 0) { keep.push_back(jb); continue; }
             hcao_job_result r = jb->result;
             hcao_status st = hcao_read_moments(ctx, jb->res, &r.moments);
@@ -2593,6 +2612,44 @@ hcao_status hcao_serve_stats(hcao_ctx* ctx, int64_t* queued, int64_t* active, in
     if (active) *active = (int64_t)ctx->serve_active.size();
     if (used_bytes) *used_bytes = ctx->serve_used;
     if (iterations) *iterations = ctx->serve_iterations;
+    return HCAO_OK;
+}
+
+hcao_status hcao_serve_cancel(hcao_ctx* ctx, uint64_t job_id) {
+    if (!ctx) return HCAO_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->serve_mu);
+    auto it = ctx->serve_jobs.find(job_id);
+    if (it == ctx->serve_jobs.end()) return HCAO_ENOTFOUND;
+    const std::shared_ptr<Job>& jb = it->second;
+    if (jb->state == 0) {
+        for (auto q = ctx->serve_queue.begin(); q != ctx->serve_queue.end(); ++q)
+            if ((*q)->id == job_id) {
+                ctx->serve_queue.erase(q);
+                jb->state = 3;
+                jb->result.status = HCAO_ECANCELLED;
+                jb->result.t_done = now_s();
+                return HCAO_OK;
+            }
+    }
+    if (jb->state <= 1) {  // resident, or being admitted by the engine right now
+        jb->cancel = true;
+        return HCAO_OK;
+    }
+    return HCAO_ENOTFOUND;  // finished or failed
+}
+
+hcao_status hcao_clear_error(hcao_ctx* ctx) {
+    DeviceScope ds_(ctx);
+    SERVE_GUARD(ctx);
+    if (!ctx) return HCAO_EINVAL;
+    CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(uint32_t), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return HCAO_OK;
+}
+
+hcao_status hcao_debug_fail_allocs(hcao_ctx* ctx, int n) {
+    if (!ctx) return HCAO_EINVAL;
+    ctx->fail_allocs.store(n > 0 ? n : 0);
     return HCAO_OK;
 }
 

@@ -22,7 +22,7 @@ SPLIT_RELAX, SPLIT_TCOLL = 0, 1
 DISS, EXCH, RECOMB = 1, 2, 3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EREJECT_LIMIT",
           -5: "ELEVEL_OVERFLOW", -6: "EBUSY", -7: "ECAPACITY", -8: "EROUNDS", -9: "ENOTFOUND",
-          -10: "ENONFINITE"}
+          -10: "ENONFINITE", -11: "ECANCELLED"}
 
 EXPORTS = [
     "hcao_create", "hcao_destroy", "hcao_last_error", "hcao_default_config", "hcao_set_species",
@@ -36,6 +36,7 @@ EXPORTS = [
     "hcao_serve_stop", "hcao_serve_stats", "hcao_recomb_rate", "hcao_wr_density", "hcao_wr_diss_prob",
     "hcao_set_step_path", "hcao_get_step_path", "hcao_set_cell_base", "hcao_init_rotation",
     "hcao_load_erot", "hcao_read_erot", "hcao_load_particles_f32", "hcao_serve_timing",
+    "hcao_serve_cancel", "hcao_debug_fail_allocs", "hcao_clear_error",
 ]
 REC_NODES = 225
 MAX_REMOVALS_PER_CELL = 4096
@@ -123,6 +124,9 @@ def lib() -> C.CDLL:
         L.hcao_load_particles.argtypes = [vp, i32, i64, vp, vp, vp, vp]
         L.hcao_load_particles_f32.argtypes = [vp, i32, i64, vp, vp, vp, vp]
         L.hcao_serve_timing.argtypes = [vp, vp]
+        L.hcao_serve_cancel.argtypes = [vp, u64]
+        L.hcao_debug_fail_allocs.argtypes = [vp, i32]
+        L.hcao_clear_error.argtypes = [vp]
         L.hcao_init_vibration.argtypes = [vp, i32, dbl]
         L.hcao_step.argtypes = [vp, i32]
         L.hcao_sync.argtypes = [vp]
@@ -479,6 +483,17 @@ class Context:
         q, a, b, it = C.c_int64(), C.c_int64(), C.c_int64(), C.c_uint64()
         self._chk(self.L.hcao_serve_stats(self.h, C.byref(q), C.byref(a), C.byref(b), C.byref(it)))
         return q.value, a.value, b.value, it.value
+
+    def serve_cancel(self, job_id) -> None:
+        self._chk(self.L.hcao_serve_cancel(self.h, job_id))
+
+    def clear_error(self) -> None:
+        """Clear the sticky device error word (see hcao_clear_error)."""
+        self._chk(self.L.hcao_clear_error(self.h))
+
+    def debug_fail_allocs(self, n) -> None:
+        """Test fault injection: the next n device allocations fail as out of memory."""
+        self._chk(self.L.hcao_debug_fail_allocs(self.h, n))
 
     def serve_timing(self) -> dict:
         """The engine thread's seconds by activity since serve_start."""

@@ -151,3 +151,40 @@ def test_load_with_fp32_velocities(precision):
         a, b = ctxs[0].read_particles(0), ctxs[1].read_particles(0)
         for x, y in zip(a, b):
             assert np.array_equal(x, y)
+
+
+def test_rejection_cap_reports_and_keeps_state_fp64():
+    """A rejection loop that hits its cap (reject_cap = 1: a K5 trial that
+    would restart fails the draw instead) keeps the molecule's state and
+    reports HCAO_EREJECT_LIMIT from the next synchronising call, without any
+    device fault; after hcao_clear_error the context reads out and steps on.
+    The particles equal the oracle's run with the same cap, which also
+    reports the cap."""
+    # ground-state molecules (the initialiser's own rejection loop would hit
+    # the cap of 1 too)
+    w = W.ch4_heat_bath(n_cells=8, per_cell=400, dissociation=False)
+    g = hcao.from_workload(w, precision=hcao.FP64, reject_cap=1, init_vib=False)
+    o = oracle.Oracle(reject_cap=1)
+    for s in w.species:
+        o.add_species(s)
+    res = o.add_reservoir(w.n_cells, w.cell_volume, w.weight, w.dt, w.seed, w.T_tr0)
+    o.load(res, w.v, w.qn0(), w.species_idx, w.cell)
+    o_failed = False
+    for _ in range(3):
+        g.step(1)
+        try:
+            o.step(1)
+        except RuntimeError:
+            o_failed = True
+    with pytest.raises(hcao.HcaoError) as e:
+        g.sync()
+    assert e.value.code == -4 and o_failed
+    g.clear_error()
+    g.sync()
+    vg, qg, sg, cg = g.read_particles(0)
+    vo, qo, so, co = o.read_particles(0)
+    assert np.array_equal(cg, co) and np.array_equal(sg, so) and np.array_equal(qg, qo)
+    assert np.array_equal(vg, vo)
+    g.step(1)
+    g.clear_error()
+    g.sync()

@@ -185,3 +185,68 @@ def test_served_jobs_with_chemistry_equal_alone(precision):
         rx_events += int(sum(cnt[8:]))
     assert rx_events > 0
     ctx.close()
+
+
+def _poll_status(ctx, jid, timeout=60.0):
+    """The final status of a job: 0, or the error code its poll raises."""
+    t0 = time.time()
+    while True:
+        try:
+            r = ctx.serve_poll(jid)
+        except hcao.HcaoError as e:
+            return e.code
+        if r is not None:
+            return r.status
+        assert time.time() - t0 < timeout, "served job did not finish"
+        time.sleep(0.002)
+
+
+def test_serving_cancel_queued_and_resident_jobs():
+    """A resident job cancelled mid-run is retired at the end of the engine's
+    iteration and reports HCAO_ECANCELLED; a queued job is dropped at once;
+    the job that runs beside them is unaffected (equal to itself alone);
+    cancelling a finished job is HCAO_ENOTFOUND."""
+    bw, _ = _jobs(n_res=3)
+    ctx = hcao.Context(precision=hcao.FP32)
+    ctx.set_species(bw.species)
+    # one resident job at a time; 4 steps per iteration
+    ctx.serve_start(max_active=1, max_batch_steps=4)
+    w_long, w_queued, w_short = bw.reservoirs
+    long_id = ctx.serve_submit(w_long, 200000)
+    queued_id = ctx.serve_submit(w_queued, 5)
+    time.sleep(0.2)  # the long job is resident and stepping, the other queued
+    ctx.serve_cancel(queued_id)
+    ctx.serve_cancel(long_id)
+    assert _poll_status(ctx, queued_id) == -11
+    assert _poll_status(ctx, long_id) == -11
+    short_id = ctx.serve_submit(w_short, 6)
+    res = _wait(ctx, [short_id])
+    with pytest.raises(hcao.HcaoError) as e:
+        ctx.serve_cancel(short_id)  # finished and released
+    assert e.value.code == -9
+    q, a, used, _ = ctx.serve_stats()
+    ctx.serve_stop()
+    assert q == 0 and a == 0 and used == 0
+    _same(res[short_id], _alone(bw, w_short, 6, hcao.FP32))
+    ctx.close()
+
+
+def test_serving_admission_allocation_failure():
+    """A device allocation that fails while a job is admitted (injected on
+    the host) fails that job with HCAO_ENOMEM; the engine goes on, and the
+    next job's result equals its run alone."""
+    bw, _ = _jobs(n_res=2)
+    ctx = hcao.Context(precision=hcao.FP64)
+    ctx.set_species(bw.species)
+    ctx.serve_start(max_active=4, max_batch_steps=4)
+    ctx.debug_fail_allocs(1)
+    bad = ctx.serve_submit(bw.reservoirs[0], 5)
+    assert _poll_status(ctx, bad) == -2
+    ctx.debug_fail_allocs(0)
+    good = ctx.serve_submit(bw.reservoirs[1], 7)
+    res = _wait(ctx, [good])
+    q, a, used, _ = ctx.serve_stats()
+    ctx.serve_stop()
+    assert q == 0 and a == 0 and used == 0
+    _same(res[good], _alone(bw, bw.reservoirs[1], 7, hcao.FP64))
+    ctx.close()

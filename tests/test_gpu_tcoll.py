@@ -101,6 +101,50 @@ def test_fp32_tcoll_exchange_products_match_oracle():
         assert abs(mg[s][0] - mr[s][0]) > 8 * se_r, (s, mg[s], mr[s])
 
 
+def _mean_evib_of(run, sp_id, levels):
+    v, q, sp, c = run.read_particles(0)
+    idx = np.where(sp == sp_id)[0]
+    ev = np.zeros(len(idx))
+    for j, L in enumerate(levels):
+        ev += L[q[idx, j]] - L[0]
+    return ev.mean(), ev.var(ddof=1) / len(ev), len(ev)
+
+
+@pytest.mark.parametrize("name", ["dissociation", "recombination"])
+def test_fp32_tcoll_products_match_oracle(name):
+    """One step from a state without the product species: the products' mean
+    vibrational energy in FP32 mode against the oracle's (independent seeds,
+    4 sigma).  Dissociation CH4 + M -> CH3 + H + M at 15000 K (CH3 exponent
+    2: H has no modes); recombination CH3 + H + M -> CH4 + M at 3000 K
+    (exponent 1/2, through the exponent-1/2 tables).  For the dissociation the
+    relaxation-table reading is also run and must differ by > 8 sigma."""
+    def make(seed_off, split):
+        if name == "dissociation":
+            w = W.ch4_heat_bath(n_cells=200, per_cell=500, seed=0x7C0D0 + seed_off)
+        else:
+            w = W.ch4_recombination(n_cells=4, per_cell=50000, T0=3000.0, n_density=1e26,
+                                    fractions=(0.0, 1.0, 1.0), seed=0x7C0E0 + seed_off)
+        return _split(w, split)
+
+    prod = 1 if name == "dissociation" else 0
+    wg, wo = make(1, TC), make(2, TC)
+    o = oracle.from_workload(wo)
+    levels = [np.array(o.levels(prod, j)) for j in range(wo.species[prod].n_modes)]
+    o.step(1)
+    mo = _mean_evib_of(o, prod, levels)
+    g = hcao.from_workload(wg, precision=hcao.FP32)
+    g.step(1)
+    mg = _mean_evib_of(g, prod, levels)
+    assert mg[2] > 1000 and mo[2] > 1000
+    se = math.sqrt(mg[1] + mo[1])
+    assert abs(mg[0] - mo[0]) < 4 * se, (mg, mo)
+    if name == "dissociation":
+        r = hcao.from_workload(make(1, "relaxation"), precision=hcao.FP32)
+        r.step(1)
+        mr = _mean_evib_of(r, prod, levels)
+        assert abs(mg[0] - mr[0]) > 8 * math.sqrt(mg[1] + mr[1]), (mg, mr)
+
+
 @pytest.mark.parametrize("name", ["dissociation", "recombination"])
 def test_fp32_tcoll_conserves(name):
     if name == "dissociation":
