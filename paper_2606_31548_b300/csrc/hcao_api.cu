@@ -124,6 +124,8 @@ struct hcao_ctx {
     uint32_t* d_totals = nullptr;
     uint32_t* d_cflag = nullptr;
     uint32_t* d_rmpos = nullptr;
+    uint32_t* d_blkcell = nullptr;  // per round, the cell of every 256th candidate pair
+    uint32_t blk_stride = 0;
     void* d_cscratch = nullptr;
     uint4* d_qA = nullptr;
     uint4* d_qB = nullptr;
@@ -856,6 +858,9 @@ hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
         CU(dalloc(ctx, &ctx->d_qB, (size_t)cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)cap));
         CU(dalloc(ctx, &ctx->d_rmpos, (size_t)cap));
+        dfree(ctx, ctx->d_blkcell);
+        CU(dalloc(ctx, &ctx->d_blkcell, (size_t)MAX_ROUNDS * (size_t)(cap / 256 + 2)));
+        ctx->blk_stride = (uint32_t)(cap / 256 + 2);
         CU(dalloc(ctx, &ctx->d_cflag, (size_t)cap));  // last: its presence marks a complete set
         ctx->pair_cap = cap;
     }
@@ -896,6 +901,8 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.totals = ctx->d_totals;
     a.cflag = ctx->d_cflag;
     a.rmpos = ctx->d_rmpos;
+    a.blkcell = ctx->d_blkcell;
+    a.blk_stride = ctx->blk_stride;
     a.cscratch = ctx->d_cscratch;
     a.qA = ctx->d_qA;
     a.qB = ctx->d_qB;
@@ -1056,6 +1063,7 @@ void hcao_destroy(hcao_ctx* ctx) {
     dfree(ctx, ctx->d_totals);
     dfree(ctx, ctx->d_cflag);
     dfree(ctx, ctx->d_rmpos);
+    dfree(ctx, ctx->d_blkcell);
     if (ctx->d_cscratch) cudaFreeAsync(ctx->d_cscratch, ctx->stream);
     dfree(ctx, ctx->d_log);
     dfree(ctx, ctx->d_qA);

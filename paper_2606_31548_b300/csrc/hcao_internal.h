@@ -197,6 +197,8 @@ struct StepArgs {
     int n_res;
     unsigned long long* counters;   // [n_res][NCNT]
     uint32_t* pbase;                // [MAX_ROUNDS][n_cells + 1]: round-r pair prefix
+    uint32_t* blkcell;              // [MAX_ROUNDS][blk_stride]: cell of round r's pair 256 b
+    uint32_t blk_stride;
     uint32_t* abase;                // [n_cells + 1]: all-round pair prefix
     uint32_t* totals;               // [MAX_ROUNDS + 2]: pairs per round, all pairs, chunks
     uint32_t* chbase;               // [n_cells + 1]: prefix of FINISH_CHUNK chunks of each cell's pairs

@@ -6,6 +6,7 @@
 //                  stochastic rounding, pairing-permutation keys per round, tile
 //                  scans of the per-cell counts; the last CTA scans the tiles.
 //   k_setup_fix    adds the tile offsets (flat pair index of every candidate).
+//   k_blockcells   the cell of every 256th candidate of each round.
 //   k_cellstats    (recombination only) per-cell sums for the cell temperature.
 //   per pairing round:
 //   k_select       one thread per candidate pair: permuted pair draw, VHS
@@ -1915,12 +1916,28 @@ static __global__ void __launch_bounds__(SETUP_TILE) k_setup_fix(StepArgs A) {
     if (A.has_recomb) A.nbase[c + 1] += __ldcg(A.tsum + SA_PART * (nt + 1) + t);
 }
 
+// The cell of every 256th candidate pair of each round (b = 0 .. ceil(total /
+// 256)): the selection then searches only the cells between two entries
+// (one or two for cells of hundreds of pairs) instead of all cells.
+static __global__ void __launch_bounds__(256) k_blockcells(StepArgs A) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (int r = 0; r < A.max_rounds; ++r) {
+        const uint32_t total = A.totals[r];
+        const uint32_t nb = (total + 255u) / 256u + 1u;
+        const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
+        for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb && b < A.blk_stride; b += stride)
+            A.blkcell[(size_t)r * A.blk_stride + b] = (uint32_t)cell_of(pb, A.n_cells, b * 256u);
+    }
+}
+
 int launch_setup(const StepArgs& a, cudaStream_t s) {
     const int nt = setup_tiles(a.n_cells);
     k_setup_cells<<<nt, SETUP_TILE, 0, s>>>(a);
-    if (nt == 1) return 1;
-    k_setup_fix<<<nt - 1, SETUP_TILE, 0, s>>>(a);
-    return 2;
+    if (nt > 1) k_setup_fix<<<nt - 1, SETUP_TILE, 0, s>>>(a);
+    const uint32_t nbl = a.blk_stride;
+    const int g = (int)((nbl + 255u) / 256u) < 592 ? (int)((nbl + 255u) / 256u) : 592;
+    k_blockcells<<<g < 1 ? 1 : g, 256, 0, s>>>(a);
+    return nt == 1 ? 2 : 3;
 }
 
 // Load-path validation of staged host arrays: cell and species in range,
@@ -1993,7 +2010,16 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
             float sgf = 0.f;
             uint32_t k = 0, ip = 0, iq = 0;
             if (valid) {
-                c = cell_of(pb, A.n_cells, g);
+                {  // the cell of g: bisection between the cells of g's 256-pair block and the next
+                    const uint32_t* bc = A.blkcell + (size_t)r * A.blk_stride + (g >> 8);
+                    int lo = (int)__ldg(bc), hi = (int)__ldg(bc + 1) + 1;
+                    if (hi > A.n_cells) hi = A.n_cells;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (__ldg(pb + mid) <= g) lo = mid; else hi = mid;
+                    }
+                    c = lo;
+                }
                 k = g - __ldg(pb + c);
                 const DevCell& cell = A.cells[c];
                 const uint32_t N = cell.n;
