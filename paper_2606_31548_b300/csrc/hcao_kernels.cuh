@@ -1782,6 +1782,23 @@ __device__ __forceinline__ int cell_of(const uint32_t* pb, int n_cells, uint32_t
     }
     return lo;
 }
+// The same for a whole warp with one g (all 32 lanes active, g < pb[n_cells]):
+// a 32-way search, each round's lanes probing evenly spaced cells, so a few
+// dependent loads replace the bisection's log2(n_cells).
+__device__ __forceinline__ int cell_of_warp(const uint32_t* pb, int n_cells, uint32_t g) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n_cells;  // pb[lo] <= g < pb[hi]
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + (lane + 1) * step;
+        const bool le = idx < hi && __ldg(pb + idx) <= g;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int nlo = lo + c * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    return lo;
+}
 
 // ------------------------------------------------------------- kernels
 #ifdef HCAO_COMMON_KERNELS
@@ -2592,7 +2609,7 @@ __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long* cellcnt = reinterpret_cast<unsigned long long*>(A.counters);
     for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
-        const int c = cell_of(A.chbase, A.n_cells, ch);
+        const int c = cell_of_warp(A.chbase, A.n_cells, ch);
         DevCell& cl = A.cells[c];
         const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
         const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
@@ -2663,7 +2680,7 @@ __global__ void __launch_bounds__(256) k_finish_append(StepArgs A) {
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < nch; ch += warps) {
         if (A.chcnt[ch] == 0u) continue;  // uniform over the warp
-        const int c = cell_of(A.chbase, A.n_cells, ch);
+        const int c = cell_of_warp(A.chbase, A.n_cells, ch);
         const DevCell& cl = A.cells[c];
         const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
         const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
