@@ -2179,10 +2179,10 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     if (pst != HCAO_OK) return pst;
     if (ctx->cfg.precision == HCAO_FP64)
         launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, ctx->d_lev64,
-                               dacc.p, dcnt.p, ctx->stream);
+                               ctx->d_levfix, dacc.p, dcnt.p, ctx->stream);
     else
         launch_moments<float>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, ctx->d_lev64,
-                              dacc.p, dcnt.p, ctx->stream);
+                              ctx->d_levfix, dacc.p, dcnt.p, ctx->stream);
     ctx->launches++;
     CU(cudaGetLastError());
     double acc[5 + 2 * MAXS];

@@ -283,8 +283,8 @@ template <class R> void launch_init_vib(const DevCell* cells, int cell0, int n_c
                                         uint32_t reject_cap, uint32_t* err, cudaStream_t s);
 template <class R> void launch_moments(const DevCell* cells, int cell0, int n_cells,
                                        const uint64_t* off, uint64_t total, const Consts* C,
-                                       const double* lev64, double* acc, unsigned long long* cnt,
-                                       cudaStream_t s);
+                                       const double* lev64, const long long* levfix, double* acc,
+                                       unsigned long long* cnt, cudaStream_t s);
 template <class R> void launch_sample_diag(const StepArgs& a, int sp, double Ec, uint64_t seed,
                                            int64_t n, uint8_t* out, unsigned long long* trials,
                                            int* status, cudaStream_t s);

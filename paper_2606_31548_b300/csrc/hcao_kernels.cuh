@@ -3003,6 +3003,22 @@ __device__ __forceinline__ int cell_of64(const uint64_t* off, int n_cells, uint6
     }
     return lo;
 }
+// the same for a whole warp with one j (all lanes active, j < off[n_cells]): a
+// 32-way search, each round's lanes probing evenly spaced cells
+__device__ __forceinline__ int cell_of64_warp(const uint64_t* off, int n_cells, uint64_t j) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n_cells;  // off[lo] <= j < off[hi]
+    while (hi - lo > 1) {
+        const int step = (hi - lo + 31) >> 5;
+        const int idx = lo + (lane + 1) * step;
+        const bool le = idx < hi && off[idx] <= j;
+        const int c = __popc(__ballot_sync(0xFFFFFFFFu, le));
+        const int nlo = lo + c * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
+    }
+    return lo;
+}
 
 template <class R>
 __global__ void k_pack(const DevCell* cells, int cell0, int n_cells, const uint64_t* off, const Consts* C,
@@ -3080,26 +3096,37 @@ __global__ void k_init_vib(const DevCell* cells, int cell0, int n_cells, const u
 // Each thread sums its particles in registers (species by an unrolled
 // compare, so no array is indexed at run time); warps then reduce by shuffles
 // and one lane per warp adds into shared memory, once per kernel.  Atomics
-// per particle into a few shared words serialised the block.
+// per particle into a few shared words serialised the block.  A warp finds
+// the cell of its 32 consecutive particles once (warp search, then each lane
+// steps forward).  FP32 mode sums each species' vibrational energy in the
+// fixed point of its bookkeeping (exact integer sums per thread; B300's FP64
+// rate made the per-species FP64 sums most of the kernel's time).
 template <class R>
 __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,
-                                                 const Consts* C, const double* lev64, double* acc,
-                                                 unsigned long long* cnt) {
+                                                 const Consts* C, const double* lev64, const long long* levfix,
+                                                 double* acc, unsigned long long* cnt) {
     using Rec = typename RecOf<R>::T;
     __shared__ double sacc[5 + 2 * MAXS];
     __shared__ unsigned long long scnt[MAXS];
     for (int i = threadIdx.x; i < 5 + 2 * MAXS; i += blockDim.x) sacc[i] = 0.0;
     for (int i = threadIdx.x; i < MAXS; i += blockDim.x) scnt[i] = 0ull;
     __syncthreads();
+    constexpr bool f32 = std::is_same<R, float>::value;
     double px = 0.0, py = 0.0, pz = 0.0, etr = 0.0, ef = 0.0;
     double ev[MAXS], er[MAXS];
+    long long evx[MAXS];
     uint32_t nc[MAXS];
 #pragma unroll
-    for (int k = 0; k < MAXS; ++k) { ev[k] = 0.0; er[k] = 0.0; nc[k] = 0u; }
+    for (int k = 0; k < MAXS; ++k) { ev[k] = 0.0; er[k] = 0.0; evx[k] = 0ll; nc[k] = 0u; }
+    const bool rot = C->has_rot != 0;
+    const int lane = threadIdx.x & 31;
     const uint64_t total = off[n_cells];
-    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total;
-         j += (uint64_t)gridDim.x * blockDim.x) {
-        const int c = cell_of64(off, n_cells, j);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); j0 < total; j0 += stride) {
+        int c = cell_of64_warp(off, n_cells, j0);  // j0 is the same for the warp's lanes
+        const uint64_t j = j0 + (uint64_t)lane;
+        if (j >= total) continue;
+        while (off[c + 1] <= j) ++c;
         const Rec* recs = reinterpret_cast<const Rec*>(cells[cell0 + c].rec);
         Rec r;
         load_rec(recs + (j - off[c]), r);
@@ -3113,13 +3140,30 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
         pz += m * vz;
         etr += 0.5 * m * (vx * vx + vy * vy + vz * vz);
         ef += S.E_form;
-        const double e = evib64(lev64, S, r.q);
-        const double erot = rec_erot_of(r, S);
+        if constexpr (f32) {
+            const long long e = evib_fix(levfix, S, r.q);
 #pragma unroll
-        for (int k = 0; k < MAXS; ++k)
-            if (s == k) { ev[k] += e; er[k] += erot; nc[k]++; }
+            for (int k = 0; k < MAXS; ++k)
+                if (s == k) { evx[k] += e; nc[k]++; }
+        } else {
+            const double e = evib64(lev64, S, r.q);
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k)
+                if (s == k) { ev[k] += e; nc[k]++; }
+        }
+        if (rot) {
+            const double erot = rec_erot_of(r, S);
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k)
+                if (s == k) er[k] += erot;
+        }
     }
-    const int lane = threadIdx.x & 31;
+    if constexpr (f32) {
+        // per thread below 2^53 units (its particles' vibrational energies),
+        // so the conversion is exact
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) ev[k] = (double)evx[k] * 0x1p-100;
+    }
     auto wsum = [](double x) {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
         return x;
@@ -3304,11 +3348,12 @@ __global__ void k_levelpop(const DevCell* cells, int cell0, int n_cells, const u
     }                                                                                            \
     template <>                                                                                  \
     void launch_moments<R>(const DevCell* cells, int cell0, int n_cells, const uint64_t* off,    \
-                           uint64_t total, const Consts* C, const double* lev64, double* acc,    \
-                           unsigned long long* cnt, cudaStream_t s) {                            \
+                           uint64_t total, const Consts* C, const double* lev64,                 \
+                           const long long* levfix, double* acc, unsigned long long* cnt,        \
+                           cudaStream_t s) {                                                     \
         if (total == 0) return;                                                                  \
         const int grid = (int)(total / 256 + 1 < 1184 ? total / 256 + 1 : 1184);                \
-        k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, C, lev64, acc, cnt);       \
+        k_moments<R><<<grid, 256, 0, s>>>(cells, cell0, n_cells, off, C, lev64, levfix, acc, cnt); \
     }                                                                                            \
     template <>                                                                                  \
     void launch_sample_diag<R>(const StepArgs& a, int sp, double Ec, uint64_t seed, int64_t n,   \

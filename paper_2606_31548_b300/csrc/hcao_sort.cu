@@ -73,6 +73,81 @@ static __global__ void __launch_bounds__(1024) k_scan_excl(uint32_t* a, int64_t 
     }
 }
 
+// Exclusive scan of a long array in three steps: per-chunk sums, one CTA's
+// scan of the sums, and per-chunk scans offset by them (the result equals the
+// single-CTA scan: integer sums in any grouping).  SCAN_CHUNK elements per CTA,
+// four per thread.
+constexpr int SCAN_CHUNK = 4096;
+constexpr int64_t SCAN_SINGLE_MAX = 65536;  // shorter arrays: the single-CTA scan
+
+static __global__ void __launch_bounds__(1024) k_chunk_sums(const uint32_t* __restrict__ a, int64_t n,
+                                                            uint32_t* sums) {
+    __shared__ uint32_t ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+    uint32_t v = 0u;
+    for (int i = tid; i < SCAN_CHUNK; i += 1024) {
+        const int64_t j = base + i;
+        if (j < n) v += a[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = ws[lane];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xFFFFFFFFu, w, o);
+        if (lane == 0) sums[blockIdx.x] = w;
+    }
+}
+
+static __global__ void __launch_bounds__(1024) k_chunk_scan(uint32_t* a, int64_t n,
+                                                            const uint32_t* __restrict__ sums_excl) {
+    __shared__ uint32_t ws[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t j0 = (int64_t)blockIdx.x * SCAN_CHUNK + 4 * tid;
+    uint32_t x[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = j0 + i < n ? a[j0 + i] : 0u;
+    const uint32_t t = x[0] + x[1] + x[2] + x[3];
+    uint32_t v = t;  // inclusive scan of the threads' totals
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) ws[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        ws[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = sums_excl[blockIdx.x] + (wid > 0 ? ws[wid - 1] : 0u) + v - t;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (j0 + i < n) {
+            a[j0 + i] = run;
+            run += x[i];
+        }
+}
+
+// a[0..n) exclusive scan in place on stream s; tmp holds scan_tmp_words(n)
+static int64_t scan_tmp_words(int64_t n) { return n > SCAN_SINGLE_MAX ? (n + SCAN_CHUNK - 1) / SCAN_CHUNK : 0; }
+static int scan_excl(uint32_t* a, int64_t n, uint32_t* tmp, cudaStream_t s) {
+    if (n <= SCAN_SINGLE_MAX) {
+        k_scan_excl<<<1, 1024, 0, s>>>(a, n);
+        return 1;
+    }
+    const int64_t nc = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    k_chunk_sums<<<(unsigned)nc, 1024, 0, s>>>(a, n, tmp);
+    k_scan_excl<<<1, 1024, 0, s>>>(tmp, nc);
+    k_chunk_scan<<<(unsigned)nc, 1024, 0, s>>>(a, n, tmp);
+    return 3;
+}
+
 static __global__ void __launch_bounds__(SORT_THREADS)
 k_digit_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ iin, int64_t n,
                 int shift, const uint32_t* __restrict__ hist, int nblocks, uint32_t* kout,
@@ -130,8 +205,9 @@ static __global__ void k_zero(uint32_t* a, int64_t n) {
 
 int64_t sort_scratch_words(int64_t n, uint32_t n_cells) {
     const int64_t nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    const int64_t nh = 256 * (nblocks > 0 ? nblocks : 1);
     (void)n_cells;
-    return 4 * n + 256 * (nblocks > 0 ? nblocks : 1);
+    return 4 * n + nh + scan_tmp_words(nh) + 1;
 }
 
 int sort_passes(uint32_t n_cells) {
@@ -149,6 +225,7 @@ cudaError_t cell_sort(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_
     uint32_t* kB = scratch + 2 * n;
     uint32_t* iB = scratch + 3 * n;
     uint32_t* hist = scratch + 4 * n;
+    uint32_t* stmp = hist + 256 * (nblocks > 0 ? nblocks : 1);  // chunk sums of the long scans
     uint64_t L = 0;
     // offsets[c] = count of cell c, then one exclusive scan over n_cells + 1
     // entries: offsets[c] = start of cell c, offsets[n_cells] = n
@@ -174,10 +251,10 @@ cudaError_t cell_sort(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_
         uint32_t* kout = (p % 2 == 0) ? kA : kB;
         uint32_t* iout = (p == passes - 1) ? perm : ((p % 2 == 0) ? iA : iB);
         k_digit_hist<<<(unsigned)nblocks, SORT_THREADS, 0, s>>>(kin, n, shift, hist, (int)nblocks);
-        k_scan_excl<<<1, 1024, 0, s>>>(hist, 256 * nblocks);
+        L += (uint64_t)scan_excl(hist, 256 * nblocks, stmp, s);
         k_digit_scatter<<<(unsigned)nblocks, SORT_THREADS, 0, s>>>(kin, iin, n, shift, hist,
                                                                    (int)nblocks, kout, iout);
-        L += 3;
+        L += 2;
         kin = kout;
         iin = iout;
     }
@@ -194,7 +271,8 @@ cudaError_t cell_sort(const uint32_t* keys, int64_t n, uint32_t n_cells, uint32_
 // GPU that loads this library holds that array until the process exits.
 namespace {
 constexpr int64_t kNoAllocTiles = (HCAO_NOALLOC_SORT_MAX_KEYS + hcao::SORT_TILE - 1) / hcao::SORT_TILE;
-constexpr int64_t kNoAllocWords = 4 * (int64_t)HCAO_NOALLOC_SORT_MAX_KEYS + 256 * kNoAllocTiles;
+constexpr int64_t kNoAllocWords = 4 * (int64_t)HCAO_NOALLOC_SORT_MAX_KEYS + 256 * kNoAllocTiles +
+                                  (256 * kNoAllocTiles + 4095) / 4096 + 1;
 __device__ __align__(256) uint32_t g_noalloc_sort_scratch[kNoAllocWords];
 
 // The array's device address on the current device.  In host code the
