@@ -149,6 +149,9 @@ struct hcao_ctx {
     // CUDA graph of one step, captured on a private stream, re-captured when
     // the kernel arguments change
     cudaStream_t cap_stream = nullptr;
+    // the load path's second stream (copies overlapping the cell sort) and its events
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_aux0 = nullptr, ev_aux1 = nullptr;
     cudaGraphExec_t graph = nullptr;
     StepArgs graph_args{};
     bool use_graph = true;
@@ -1085,6 +1088,9 @@ void hcao_destroy(hcao_ctx* ctx) {
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    if (ctx->ev_aux0) cudaEventDestroy(ctx->ev_aux0);
+    if (ctx->ev_aux1) cudaEventDestroy(ctx->ev_aux1);
     for (int k = 0; k < hcao_ctx::NPROF; ++k)
         for (auto& e : ctx->prof_ev[k]) {
             cudaEventDestroy(e.first);
@@ -1654,15 +1660,34 @@ static hcao_status load_impl(hcao_ctx* ctx, int id, int64_t n, const double* v, 
         CU(dalloc(ctx, &dslot, (size_t)r->n_cells));
         CU(dalloc(ctx, &dflags, 2));
         CU(cudaMemsetAsync(dflags, 0, 2 * sizeof(uint32_t), ctx->stream));
-        if (vf) CU(cudaMemcpyAsync(dvf, vf, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        else CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        // The cell keys first, and their sort (safe for any key: a key out of
+        // range is only misplaced, and the input is rejected below) on the
+        // context's stream, while the other arrays copy on a second stream.
+        if (!ctx->aux_stream) {
+            CU(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+            CU(cudaEventCreateWithFlags(&ctx->ev_aux0, cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&ctx->ev_aux1, cudaEventDisableTiming));
+        }
+        CU(cudaEventRecord(ctx->ev_aux0, ctx->stream));  // the staging buffers exist
+        CU(cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_aux0, 0));
         CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
+        if (vf) CU(cudaMemcpyAsync(dvf, vf, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->aux_stream));
+        else CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->aux_stream));
+        CU(cudaMemcpyAsync(dq, qn, (size_t)16 * n, cudaMemcpyHostToDevice, ctx->aux_stream));
+        CU(cudaMemcpyAsync(ds, species, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->aux_stream));
+        CU(cudaEventRecord(ctx->ev_aux1, ctx->aux_stream));
+        hcao_status st = hcao_cell_sort(ctx, dk, n, (uint32_t)r->n_cells, dperm, doff);
+        CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_aux1, 0));  // every array is on the device
+        if (st != HCAO_OK) {
+            CU(cudaStreamSynchronize(ctx->stream));
+            release();
+            return st;
+        }
         launch_validate_load(ctx->d_consts, r->n_cells, reinterpret_cast<const int32_t*>(dk), ds, dq, n, dflags,
                              ctx->stream);
         ctx->launches++;
         CU(cudaMemcpyAsync(flags, dflags, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaMemcpyAsync(off.data(), doff, sizeof(uint32_t) * off.size(), cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
         if (flags[0] & (LOAD_BAD_CELL | LOAD_BAD_SPECIES)) {
             release();
@@ -1673,13 +1698,6 @@ static hcao_status load_impl(hcao_ctx* ctx, int id, int64_t n, const double* v, 
             release();
             return fail(ctx, HCAO_ELEVEL_OVERFLOW, "load_particles: quantum number outside the level list");
         }
-        hcao_status st = hcao_cell_sort(ctx, dk, n, (uint32_t)r->n_cells, dperm, doff);
-        if (st != HCAO_OK) {
-            release();
-            return st;
-        }
-        CU(cudaMemcpyAsync(off.data(), doff, sizeof(uint32_t) * off.size(), cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
     }
     // capacities and slot bases
     const double f = ctx->cfg.capacity_factor;
