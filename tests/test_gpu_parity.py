@@ -154,6 +154,23 @@ def test_parity_triatomic_single_cell_20000():
     assert g.read_counters(0)[1] > 20000
 
 
+def test_parity_triatomic_c1_all_1000_steps():
+    """The triatomic relaxation reservoir (20,000 particles, one cell, FP64)
+    over its whole run of 1000 steps: every particle, counter and
+    (sigma g)_max equal to the oracle's at steps 250, 500 and 1000."""
+    w = W.relaxation_triatomic()
+    g, o = _pair(w, log=False)
+    done = 0
+    for mark in (250, 500, 1000):
+        g.step(mark - done)
+        o.step(mark - done)
+        done = mark
+        _assert_same_state(g, o)
+        assert np.array_equal(g.read_counters(0), o.read_counters(0)[: len(g.read_counters(0))])
+        assert np.array_equal(g.read_cell_sgmax(0, 1), o.read_cell_sgmax(0, 1))
+    assert g.read_counters(0)[1] > 1_000_000  # accepted collisions over the run
+
+
 def test_parity_ch4_dissociation():
     g, o = _run_parity(W.ch4_heat_bath(n_cells=24, per_cell=250), 8)
     assert g.read_reaction_counts(0, 1)[0] > 100
