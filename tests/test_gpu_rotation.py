@@ -57,7 +57,17 @@ CASES = {
     "ch4_h_exchange_gamma": lambda: _gamma(_rotating(W.ch4_h_exchange(n_cells=8, per_cell=500, T0=5000.0)), 1.0),
     "ch4_recombination": lambda: _wr(_rotating(W.ch4_recombination(n_cells=5, per_cell=800, T0=3000.0,
                                                                      n_density=1e26))),
+    # rotation pooled into the products' energy under the collision-temperature split
+    "ch4_dissociation_gamma_tcoll": lambda: _tc(_gamma(_rotating(W.ch4_heat_bath(n_cells=10, per_cell=300)), 0.5)),
+    "ch4_recombination_tcoll": lambda: _tc(_rotating(W.ch4_recombination(n_cells=5, per_cell=800, T0=3000.0,
+                                                                         n_density=1e26))),
 }
+
+
+def _tc(w):
+    for r in w.reactions:
+        r.product_split = "collision_temperature"
+    return w
 
 
 def _gamma(w, g):
@@ -77,7 +87,7 @@ def _wr(w):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_rotation_parity_fp64(name):
     w = CASES[name]()
-    kw = {"max_rounds": 4} if name == "ch4_recombination" else {}
+    kw = {"max_rounds": 4} if name.startswith("ch4_recombination") else {}
     g = hcao.from_workload(w, precision=hcao.FP64, log=True, **kw)
     o = oracle.from_workload(w, log=True)
     for _ in range(5):
