@@ -171,6 +171,41 @@ def test_parity_triatomic_c1_all_1000_steps():
     assert g.read_counters(0)[1] > 1_000_000  # accepted collisions over the run
 
 
+@pytest.mark.parametrize("T", [40.0, 400000.0])
+def test_parity_degenerate_energies(T):
+    """The sampler's edge cases, in both precisions: a 40 K gas, where most
+    collision energies lie below the smallest single-quantum excitation (the
+    ground state is taken without a draw), and a 400,000 K gas, where some
+    collision energies pass the top of the level tables (the state is kept
+    and the overflow counted).  FP64 equals the oracle bit for bit; FP32
+    keeps every particle's energy and momentum to 1e-6 and counts the same
+    kinds of events."""
+    w = W.relaxation_triatomic(n_particles=6000, n_cells=3)
+    w.v = w.v * np.sqrt(T / w.T_tr0)
+    w.T_tr0 = T
+    w.T_vib0 = T
+    g, o = _pair(w)
+    for _ in range(3):
+        g.step(1)
+        o.step(1)
+        _assert_same_log(g, o)
+        _assert_same_state(g, o)
+    cg, co = g.read_counters(0), o.read_counters(0)
+    assert np.array_equal(cg, co[: len(cg)])
+    assert cg[1] > 100  # collisions happened
+    if T > 1e5:
+        assert cg[4] > 0  # table overflows counted
+    f = hcao.from_workload(w, precision=hcao.FP32)
+    m0 = f.read_moments(0)
+    f.step(3)
+    m1 = f.read_moments(0)
+    E0 = m0.E_tr + m0.E_vib[0]
+    E1 = m1.E_tr + m1.E_vib[0]
+    assert abs(E1 - E0) <= 1e-6 * E0
+    if T > 1e5:
+        assert f.read_counters(0)[4] > 0
+
+
 def test_parity_ch4_dissociation():
     g, o = _run_parity(W.ch4_heat_bath(n_cells=24, per_cell=250), 8)
     assert g.read_reaction_counts(0, 1)[0] > 100
