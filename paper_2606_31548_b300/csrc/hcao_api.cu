@@ -1670,6 +1670,12 @@ static hcao_status load_impl(hcao_ctx* ctx, int id, int64_t n, const double* v, 
         }
         CU(cudaEventRecord(ctx->ev_aux0, ctx->stream));  // the staging buffers exist
         CU(cudaStreamWaitEvent(ctx->aux_stream, ctx->ev_aux0, 0));
+        // on any early return below, the second stream's copies finish first:
+        // they read the caller's host arrays, which the caller may release
+        struct AuxDrain {
+            cudaStream_t s;
+            ~AuxDrain() { cudaStreamSynchronize(s); }
+        } aux_drain{ctx->aux_stream};
         CU(cudaMemcpyAsync(dk, cell, sizeof(int32_t) * n, cudaMemcpyHostToDevice, ctx->stream));
         if (vf) CU(cudaMemcpyAsync(dvf, vf, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, ctx->aux_stream));
         else CU(cudaMemcpyAsync(dv, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->aux_stream));
