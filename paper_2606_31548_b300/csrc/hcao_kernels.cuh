@@ -381,9 +381,14 @@ __device__ __forceinline__ double evib64(const double* lev, const DevSpecies& S,
 __device__ __forceinline__ long long f2fix(float x) { return __float2ll_rn(__fmul_rn(x, 0x1p100f)); }
 __device__ __forceinline__ float fix2f(long long a) { return __fmul_rn(__ll2float_rn(a), 0x1p-100f); }
 __device__ __forceinline__ double fix2d(long long a) { return __ll2double_rn(a) * 0x1p-100; }
+// (unrolled over the 16 mode slots: each quantum number is a fixed byte of
+// its word, and the integer sum does not depend on the order)
 __device__ __forceinline__ long long evib_fix(const long long* lf, const DevSpecies& S, const uint32_t q[4]) {
+    const int n = S.n_modes;
     long long e = 0;
-    for (int j = 0; j < S.n_modes; ++j) e += __ldg(lf + S.lev_off[j] + get_q(q, j));
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+        if (j < n) e += __ldg(lf + S.lev_off[j] + ((q[j >> 2] >> ((j & 3) * 8)) & 0xFFu));
     return e;
 }
 
