@@ -22,9 +22,8 @@
 //   k_react        one thread per reacting pair: dissociation, exchange,
 //                  recombination.
 //   end of step, one warp per FINISH_CHUNK pair slots of a cell:
-//   k_finish_count per-cell counters and removed positions; k_finish_append
-//   stable append of created particles; k_cellupd (sigma g)_max, counts,
-//   step; k_compact removals.
+//   k_finish_count per-cell counters; k_finish_append stable append of created
+//   particles; k_cellupd (sigma g)_max, counts, step; k_compact removals.
 // Queue order is irrelevant: pairs of one round are disjoint and every draw is
 // keyed by (step, cell, round, pair), never by a thread or queue position.
 // Randomness: Philox4x32-10 keyed by the reservoir seed, counter
