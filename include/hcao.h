@@ -39,7 +39,8 @@ typedef enum {
     HCAO_EREJECT_LIMIT = -4,   /* an LB/init rejection loop hit its cap */
     HCAO_ELEVEL_OVERFLOW = -5, /* a quantum number outside a mode's level list */
     HCAO_EBUSY = -6,           /* job still running (serving) */
-    HCAO_ECAPACITY = -7,       /* a cell ran out of particle slots */
+    HCAO_ECAPACITY = -7,       /* a cell ran out of particle slots, or would pair over 2^24
+                                  pairs in one NTC round (N/2, N/3 with recombination) */
     HCAO_EROUNDS = -8,         /* NTC needed more pairing rounds than configured */
     HCAO_ENOTFOUND = -9,
     HCAO_ENONFINITE = -10,     /* a non-finite velocity or (sigma_T g)_max was met */

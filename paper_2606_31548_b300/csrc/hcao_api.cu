@@ -154,6 +154,7 @@ struct hcao_ctx {
     cudaEvent_t ev_aux0 = nullptr, ev_aux1 = nullptr;
     cudaGraphExec_t graph = nullptr;
     StepArgs graph_args{};
+    uint64_t graph_launches = 0;     // kernels launched by one replay of the step graph
     bool use_graph = true;
     // serving engine: thread-safe queue in, results out; the engine thread is
     // the only caller of the context's other functions while it runs
@@ -526,7 +527,47 @@ double mean_sigma_g(const hcao_ctx* ctx, int a, int b, double T) {
     return 2.0 * d * d * std::sqrt(2.0 * PI_D * KB * Tr / mr) * std::pow(T / Tr, 1.0 - ctx->omega);
 }
 
+// Work classes of the FP32 relaxation queue.  A species pair's work key is
+// the mode counts of the molecules it relaxes, in order (P first when it has
+// modes), and whether it takes the QK test; its class is the rank of its key
+// among the distinct keys of the species present, heaviest work (most modes)
+// first, the keys past the NCLS - 1 heaviest sharing the last class.  Pairs of
+// one class run mode-draw loops of like length, so the lanes of a warp that
+// holds them stay busy together.
+static void assign_work_classes(Consts& C) {
+    const int S = C.n_species;
+    struct Key { int first, second, qk; };
+    std::vector<Key> keys;
+    auto key_of = [&](int a, int b) {
+        const int ma = C.sp[a].n_modes, mb = C.sp[b].n_modes;
+        return Key{ma > 0 ? ma : mb, ma > 0 ? mb : 0, (int)C.pair[a * MAXS + b].qk};
+    };
+    auto same = [](const Key& x, const Key& y) { return x.first == y.first && x.second == y.second && x.qk == y.qk; };
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            const Key k = key_of(a, b);
+            bool seen = false;
+            for (const Key& x : keys) seen = seen || same(x, k);
+            if (!seen) keys.push_back(k);
+        }
+    std::sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+        if (x.first + x.second != y.first + y.second) return x.first + x.second > y.first + y.second;
+        if (x.first != y.first) return x.first > y.first;
+        return x.qk > y.qk;
+    });
+    for (int i = 0; i < MAXS * MAXS; ++i) C.pair[i].cls = NCLS - 1;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            const Key k = key_of(a, b);
+            int rank = 0;
+            while (!same(keys[rank], k)) ++rank;
+            C.pair[a * MAXS + b].cls = (uint32_t)std::min(rank, NCLS - 1);
+        }
+    C.n_cls = std::min((int)keys.size(), NCLS);
+}
+
 hcao_status upload_consts(hcao_ctx* ctx) {
+    assign_work_classes(ctx->hc);
     if (!ctx->d_consts) CU(dalloc(ctx, &ctx->d_consts, 1));
     CU(cudaMemcpyAsync(ctx->d_consts, &ctx->hc, sizeof(Consts), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -857,7 +898,7 @@ hcao_status ensure_pair_buffers(hcao_ctx* ctx) {
         ctx->d_cscratch = nullptr;
         dfree(ctx, ctx->d_qA);
         dfree(ctx, ctx->d_qB);
-        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)cap));  // FP32: three regions, see StepArgs::qsize
+        CU(dalloc(ctx, &ctx->d_qA, 2 * (size_t)cap));  // FP32: class-ordered half + staging half
         CU(dalloc(ctx, &ctx->d_qB, (size_t)cap));
         if (ctx->log_on) CU(dalloc(ctx, &ctx->d_log, (size_t)cap));
         CU(dalloc(ctx, &ctx->d_rmpos, (size_t)cap));
@@ -924,6 +965,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.grid_select = ctx->grid_select;
     a.grid_relax = ctx->grid_relax;
     a.grid_react = ctx->grid_react;
+    a.qorder = ctx->hc.n_cls > 1 ? 1 : 0;
     a.pair_cap = ctx->pair_cap;
     a.log = ctx->d_log;
     a.log_on = ctx->log_on ? 1 : 0;
@@ -1951,20 +1993,19 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
             cudaGraph_t g = nullptr;
             CU(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
-            uint64_t dummy = 0;
-            if (f64) launch_step<double>(a, grid, block, ctx->cap_stream, &dummy);
-            else launch_step<float>(a, grid, block, ctx->cap_stream, &dummy);
+            uint64_t in_graph = 0;
+            if (f64) launch_step<double>(a, grid, block, ctx->cap_stream, &in_graph);
+            else launch_step<float>(a, grid, block, ctx->cap_stream, &in_graph);
             CU(cudaStreamEndCapture(ctx->cap_stream, &g));
+            ctx->graph_launches = in_graph;
             cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
             cudaGraphDestroy(g);
             CU(e);
             ctx->graph_args = a;
         }
-        const uint64_t per_step = setup_launches(a.n_cells) + 2 + (uint64_t)a.max_rounds * (a.has_reactions ? 3 : 2) +
-                                  (a.has_recomb ? 2 : 0) + (ctx->hc.creates ? 1 : 0);
         for (int s = 0; s < n_steps; ++s) {
             CU(cudaGraphLaunch(ctx->graph, ctx->stream));
-            ctx->launches += per_step;
+            ctx->launches += ctx->graph_launches;  // the kernels captured in the graph
         }
         return HCAO_OK;
     }
@@ -2014,6 +2055,7 @@ hcao_status hcao_step(hcao_ctx* ctx, int n_steps) {
             } else {
                 if (f64) launch_phase<double>(a, r, k - 1, grid, ctx->stream);
                 else launch_phase<float>(a, r, k - 1, grid, ctx->stream);
+                if (k == 1 && !f64 && a.qorder) ctx->launches++;  // the FP32 queue placement after the selection
             }
             CU(cudaEventRecord(ev.second, ctx->stream));
             ctx->launches++;

@@ -14,8 +14,9 @@
 //      coalesced 128-bit loads;
 //   3. per round and per batch of candidate pairs: the permuted pair draw and
 //      the VHS acceptance from shared memory; accepted pairs queued in shared
-//      memory in three regions by the number of molecules to relax (the same
-//      SIMT grouping as the queue kernels);
+//      memory in three regions by the number of molecules to relax (coarser
+//      than the queue path's work classes: a cell has only a few hundred
+//      pairs a round, too few to fill warps class by class);
 //   4. per accepted pair: the QK reaction test (Eq. Ecoll-diss, Eq.
 //      Ecoll-exch, competing reactions), then the exchange or the HCAO LB
 //      relaxation (the K5 alias draw) and isotropic scattering; the new

@@ -25,13 +25,15 @@ constexpr int REC_NODES = HCAO_REC_NODES;  // recombination rate table: T_i = 50
 constexpr int MAX_REMOVALS = HCAO_MAX_REMOVALS_PER_CELL;
 constexpr int FINISH_CHUNK = 1024;  // pair slots per warp of the end-of-step kernels
 constexpr uint64_t POOL_KEEP_BYTES = 8ull << 30;  // unused memory a context's pool keeps mapped
-constexpr int QSIZE_WORDS = 4 * MAX_ROUNDS;  // queue counters (StepArgs::qsize)
+constexpr int NCLS = 16;        // work classes of the FP32 relaxation queue
+constexpr int QCNT_OFF = 2 * MAX_ROUNDS;               // StepArgs::qsize: per-class counts
+constexpr int QCUR_OFF = QCNT_OFF + MAX_ROUNDS * NCLS;  // StepArgs::qsize: per-class placement cursors
+constexpr int QSIZE_WORDS = QCUR_OFF + MAX_ROUNDS * NCLS;  // queue counters (StepArgs::qsize)
 constexpr int SETUP_TILE = 256;     // cells per CTA of the step set-up
 // prefix arrays built by the set-up: pairs of rounds 0..MAX_ROUNDS-1, all
 // pairs, FINISH_CHUNK chunks, particles
 enum { SA_ALL = MAX_ROUNDS, SA_CHUNK, SA_PART, SETUP_ARRAYS };
 inline int setup_tiles(int n_cells) { return n_cells <= SETUP_TILE ? 1 : (n_cells + SETUP_TILE - 1) / SETUP_TILE; }
-inline int setup_launches(int n_cells) { return setup_tiles(n_cells) == 1 ? 1 : 2; }
 
 // Philox stream purposes: counter word 3 = purpose << 24 | block index.
 enum { PU_NSEL = 1, PU_PERM = 2, PU_PAIR = 3, PU_LB_A = 4, PU_LB_B = 5, PU_SCAT = 6,
@@ -122,6 +124,7 @@ struct DevPair {
     double mr, C, mt, fp, fq;        // reduced mass, VHS constant, total mass, velocity shares
     float mr_f, C_f, fp_f, fq_f, inv2mr_f;
     uint32_t qk;                     // a QK dissociation or exchange exists for this species pair
+    uint32_t cls;                    // FP32 relaxation-queue work class (assign_work_classes)
 };
 
 // DISS: A + M -> P0 + P1; EXCH: A + B -> P0 + P1; RECOMB: A + B (+ M) -> P0
@@ -151,7 +154,7 @@ struct DevReaction {
 
 struct Consts {
     int n_species, n_reactions, amode, creates;
-    int has_recomb, has_tce, has_rot, pad_c;
+    int has_recomb, has_tce, has_rot, n_cls;  // n_cls: FP32 relaxation-queue work classes in use
     int rec_pair[MAXS * MAXS];       // species pair -> recombination | side << 3, or -1
     DevSpecies sp[MAXS];
     DevPair pair[MAXS * MAXS];
@@ -207,12 +210,15 @@ struct StepArgs {
     uint32_t* rmpos;                // recombination: a cell's removed positions at its event
                                     // slots [abase, abase + nremoved), gathered by k_finish_count
     void* cscratch;                 // per-pair record of a particle created by a reaction
-    uint4* qA;                      // [2 pair_cap] accepted pairs of the current round (cell, pair, ip, iq)
+    uint4* qA;                      // [2 pair_cap] accepted pairs of the current round (cell, pair, ip, iq);
+                                    // FP32: k_select stages them at qA[pair_cap + i] with the work
+                                    // class in the pair word's top byte, k_qorder places them
+                                    // class by class at qA[0 ..)
     uint4* qB;                      // reacting pairs (cell, pair, channel)
-    uint32_t* qsize;                // [QSIZE_WORDS]: per round, relax-queue entries at the
-                                    // front and react-queue length; then per round the FP32
-                                    // relax queue's one-molecule entries (qA[2 pair_cap - 1 - i]),
-                                    // then its no-molecule entries (qA[pair_cap + i])
+    uint32_t* qsize;                // [QSIZE_WORDS]: per round, relax-queue entries and
+                                    // react-queue length; then per round and class the FP32
+                                    // relax queue's counts (QCNT_OFF), then the placement
+                                    // cursors (QCUR_OFF)
     int has_reactions;
     int has_recomb;
     int creates;                    // a reaction creates particles or removes them (scratch slots)
@@ -223,6 +229,7 @@ struct StepArgs {
     uint32_t* tsum;                 // [SETUP_ARRAYS][setup tiles + 1] tile totals, then a ticket
     unsigned long long* work;       // [4] K5 level evaluations, mode starts, molecule samples, pairs
     int grid_select, grid_relax, grid_react;  // launch shapes (host-side; results do not depend on them)
+    int qorder;                     // FP32: the relaxation queue is staged and placed by work class
     uint64_t pair_cap;              // capacity of cflag / log
     hcao_log_rec* log;
     int log_on;

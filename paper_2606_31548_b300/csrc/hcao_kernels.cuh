@@ -5,13 +5,15 @@
 //                  count N_sel = 1/2 N(N-1) w (sigma g)_max dt / V_c with
 //                  stochastic rounding, pairing-permutation keys per round, tile
 //                  scans of the per-cell counts; the last CTA scans the tiles.
-//   k_setup_fix    adds the tile offsets (flat pair index of every candidate).
-//   k_blockcells   the cell of every 256th candidate of each round.
+//   k_setup_fix    adds the tile offsets (flat pair index of every candidate)
+//                  and tabulates the cell of every 256th candidate of each round.
 //   k_cellstats    (recombination only) per-cell sums for the cell temperature.
 //   per pairing round:
 //   k_select       one thread per candidate pair: permuted pair draw, VHS
-//                  acceptance; FP32 mode queues accepted pairs in three regions
-//                  by the number of molecules to relax.
+//                  acceptance; FP32 mode stages accepted pairs with their
+//                  species pair's work class and counts them per class.
+//   k_qorder       (FP32, more than one work class) places the staged queue
+//                  class by class, so a warp's pairs run like mode-draw loops.
 //   k_relax_fast   (FP32) one thread per accepted pair: recombination and QK
 //                  reaction tests (Eq. Ecoll-diss, Eq. Ecoll-exch, competing
 //                  reactions) -- reacting pairs go to a second queue -- else
@@ -1827,6 +1829,9 @@ static __global__ void __launch_bounds__(SETUP_TILE) k_setup_cells(StepArgs A) {
         const uint32_t N = cl.n;
         uint32_t rounds = 0;
         const uint32_t P = round_pairs(N, A.has_recomb);
+        // a round's pair index is a 24-bit field of the pair's Philox key (and
+        // of the FP32 queue's pair word): at most 2^24 pairs a round
+        if (P > (1u << 24)) atomicOr(A.err, (uint32_t)ERR_CAPACITY);
         const uint32_t nsel = ntc_setup(A, rs, cl, N, P, rounds, cl.pkey);
         cl.nsel = nsel;
         cl.ncreated = 0;
@@ -1921,45 +1926,56 @@ static __global__ void __launch_bounds__(SETUP_TILE) k_setup_cells(StepArgs A) {
         if (A.has_recomb) A.nbase[0] = 0;
         A.totals[MAX_ROUNDS] = A.tsum[SA_ALL * (nt + 1) + nt];
         A.totals[MAX_ROUNDS + 1] = A.tsum[SA_CHUNK * (nt + 1) + nt];
-        for (int i = 0; i < QSIZE_WORDS; ++i) A.qsize[i] = 0u;
         A.tsum[SETUP_ARRAYS * (nt + 1)] = 0u;  // ticket, for the next step
     }
+    for (int i = threadIdx.x; i < QSIZE_WORDS; i += SETUP_TILE) A.qsize[i] = 0u;
 }
 
-// adds the scanned tile totals to tiles 1.. (tile 0 is complete)
+// Adds the scanned tile totals to every tile (tile 0's are zero) and
+// tabulates the cell of every 256th candidate pair of each round, entries b =
+// 0 .. ceil(total / 256): cell c writes the entries with pb[c] <= 256 b <
+// pb[c + 1], the last cell also the entry past the end (the largest c with
+// pb[c] <= 256 b, as a bisection would find it).  The selection then searches
+// only the cells between two entries (one or two for cells of hundreds of
+// pairs) instead of all cells.
 static __global__ void __launch_bounds__(SETUP_TILE) k_setup_fix(StepArgs A) {
-    const int nc = A.n_cells, R = A.max_rounds, nt = (int)gridDim.x + 1;
-    const int t = blockIdx.x + 1;
+    const int nc = A.n_cells, R = A.max_rounds, nt = (int)gridDim.x;
+    const int t = blockIdx.x;
     const int c = t * SETUP_TILE + threadIdx.x;
-    if (c >= nc) return;
-    for (int r = 0; r < R; ++r) A.pbase[r * (nc + 1) + c + 1] += __ldcg(A.tsum + r * (nt + 1) + t);
+    const bool in = c < nc;
+    uint32_t lo[MAX_ROUNDS], hi[MAX_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < MAX_ROUNDS; ++r) {
+        lo[r] = hi[r] = 0u;
+        if (in && r < R) {
+            const uint32_t off = __ldcg(A.tsum + r * (nt + 1) + t);
+            const uint32_t* pb = A.pbase + r * (nc + 1);
+            hi[r] = pb[c + 1] + off;
+            // the tile's first cell starts at the tile's offset; the others
+            // at their left neighbour's end, read before it is offset
+            lo[r] = threadIdx.x == 0 ? off : pb[c] + off;
+        }
+    }
+    __syncthreads();
+    if (!in) return;
+#pragma unroll
+    for (int r = 0; r < MAX_ROUNDS; ++r) {
+        if (r >= R) break;
+        A.pbase[r * (nc + 1) + c + 1] = hi[r];
+        uint32_t* bc = A.blkcell + (size_t)r * A.blk_stride;
+        const uint32_t bend = (hi[r] + 255u) / 256u + (c == nc - 1 ? 1u : 0u);
+        for (uint32_t b = (lo[r] + 255u) / 256u; b < bend && b < A.blk_stride; ++b) bc[b] = (uint32_t)c;
+    }
     A.abase[c + 1] += __ldcg(A.tsum + SA_ALL * (nt + 1) + t);
     A.chbase[c + 1] += __ldcg(A.tsum + SA_CHUNK * (nt + 1) + t);
     if (A.has_recomb) A.nbase[c + 1] += __ldcg(A.tsum + SA_PART * (nt + 1) + t);
 }
 
-// The cell of every 256th candidate pair of each round (b = 0 .. ceil(total /
-// 256)): the selection then searches only the cells between two entries
-// (one or two for cells of hundreds of pairs) instead of all cells.
-static __global__ void __launch_bounds__(256) k_blockcells(StepArgs A) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (int r = 0; r < A.max_rounds; ++r) {
-        const uint32_t total = A.totals[r];
-        const uint32_t nb = (total + 255u) / 256u + 1u;
-        const uint32_t* pb = A.pbase + r * (A.n_cells + 1);
-        for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb && b < A.blk_stride; b += stride)
-            A.blkcell[(size_t)r * A.blk_stride + b] = (uint32_t)cell_of(pb, A.n_cells, b * 256u);
-    }
-}
-
 int launch_setup(const StepArgs& a, cudaStream_t s) {
     const int nt = setup_tiles(a.n_cells);
     k_setup_cells<<<nt, SETUP_TILE, 0, s>>>(a);
-    if (nt > 1) k_setup_fix<<<nt - 1, SETUP_TILE, 0, s>>>(a);
-    const uint32_t nbl = a.blk_stride;
-    const int g = (int)((nbl + 255u) / 256u) < 592 ? (int)((nbl + 255u) / 256u) : 592;
-    k_blockcells<<<g < 1 ? 1 : g, 256, 0, s>>>(a);
-    return nt == 1 ? 2 : 3;
+    k_setup_fix<<<nt, SETUP_TILE, 0, s>>>(a);
+    return 2;
 }
 
 // Load-path validation of staged host arrays: cell and species in range,
@@ -2004,7 +2020,7 @@ void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, con
 
 // Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
 // pairs are finished here; accepted ones go to the relaxation queue (in FP32
-// mode into the region of their number of molecules to relax).
+// mode staged with their work class, for k_qorder).
 constexpr int SELECT_THREADS = 256;
 
 template <class R>
@@ -2019,16 +2035,18 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
     if constexpr (std::is_same<R, float>::value) {
         // FP32 mode: no FP64 arithmetic; the second half of a record (the
         // quantum numbers) is read only for accepted pairs when reactions exist
-        // region counts, double-buffered by pass: a pass writes the set the
+        // staging counts, double-buffered by pass: a pass writes the set the
         // previous pass did not read, so it needs two barriers, not three
-        __shared__ uint32_t sel_cnt[2][3][SELECT_THREADS / 32], sel_base[2][3];
+        __shared__ uint32_t sel_cnt[2][SELECT_THREADS / 32], sel_base[2], cls_cnt[2][NCLS];
+        if (threadIdx.x < 2 * NCLS) cls_cnt[threadIdx.x / NCLS][threadIdx.x % NCLS] = 0u;
+        __syncthreads();
         int par = 0;
         for (uint32_t g0 = blockIdx.x * blockDim.x; g0 < total; g0 += stride) {
             const uint32_t g = g0 + threadIdx.x;
             const bool valid = g < total;
             int c = 0;
             bool accept = false;
-            int nm = 0;
+            uint32_t cls = 0u;
             float sgf = 0.f;
             uint32_t k = 0, ip = 0, iq = 0;
             if (valid) {
@@ -2066,47 +2084,46 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 Stream sp;
                 st_init(sp, rs.seed, rs.step, cell.lcell, rk, PU_PAIR);
                 accept = st_u32(sp) < __fdiv_rn(sgf, cell.sgmax_f);
-                nm = (int)(C->sp[sP].n_modes > 0) + (int)(C->sp[sQ].n_modes > 0);
+                cls = C->pair[sP * MAXS + sQ].cls;
                 }
                 if (!accept) {
                     A.cflag[ev_idx] = 0u;
                     if (A.log_on) A.log[ev_idx] = hcao_log_rec{rs.step, cell.lcell, rk, ip, iq, -1, 0u};
                 }
             }
-            // the relaxation queue in three regions by the number of molecules to
-            // relax: two from qA[0] up, one from qA[2 cap - 1] down, none from
-            // qA[cap] up (an accepted pair count never exceeds cap), so that
-            // warps of the relaxation kernel run their molecule loop as their
-            // pairs need; one atomic per CTA and region
+            // the relaxation queue, staged at qA[cap + i] in arrival order with
+            // the pair's work class in the top byte of the pair word (k < 2^24,
+            // as in the pair's Philox key); k_qorder then places the entries
+            // class by class, so that the lanes of a warp of the relaxation
+            // kernel run mode-draw loops of like length (with a single class in
+            // use: straight to qA[i], no placement).  One atomic per CTA for
+            // the staging slots, one per CTA and present class for the counts.
             {
                 const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-                const unsigned m2 = __ballot_sync(0xFFFFFFFFu, accept && nm == 2);
-                const unsigned m1 = __ballot_sync(0xFFFFFFFFu, accept && nm == 1);
-                const unsigned m0 = __ballot_sync(0xFFFFFFFFu, accept && nm == 0);
-                if (lane == 0) {
-                    sel_cnt[par][0][wid] = (uint32_t)__popc(m2);
-                    sel_cnt[par][1][wid] = (uint32_t)__popc(m1);
-                    sel_cnt[par][2][wid] = (uint32_t)__popc(m0);
-                }
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, accept);
+                if (lane == 0) sel_cnt[par][wid] = (uint32_t)__popc(m);
+                if (accept && A.qorder) atomicAdd(&cls_cnt[par][cls], 1u);
                 __syncthreads();
-                if (threadIdx.x < 3) {
+                if (threadIdx.x == 0) {
                     uint32_t tot = 0u;
                     for (int w2 = 0; w2 < SELECT_THREADS / 32; ++w2) {
-                        const uint32_t n = sel_cnt[par][threadIdx.x][w2];
-                        sel_cnt[par][threadIdx.x][w2] = tot;
+                        const uint32_t n = sel_cnt[par][w2];
+                        sel_cnt[par][w2] = tot;
                         tot += n;
                     }
-                    uint32_t* ctr = threadIdx.x == 0 ? qsize : A.qsize + (threadIdx.x + 1) * MAX_ROUNDS + r;
-                    sel_base[par][threadIdx.x] = tot ? atomicAdd(ctr, tot) : 0u;
+                    sel_base[par] = tot ? atomicAdd(qsize, tot) : 0u;
+                }
+                if (threadIdx.x < NCLS) {
+                    const uint32_t n = cls_cnt[par][threadIdx.x];
+                    if (n) {
+                        atomicAdd(A.qsize + QCNT_OFF + r * NCLS + threadIdx.x, n);
+                        cls_cnt[par][threadIdx.x] = 0u;
+                    }
                 }
                 __syncthreads();
-                const unsigned lt = (1u << lane) - 1u;
-                const uint4 ent = make_uint4((uint32_t)c, k, ip, iq);
                 if (accept) {
-                    const int q = 2 - nm;  // region: 0 two molecules, 1 one, 2 none
-                    const unsigned mq = q == 0 ? m2 : (q == 1 ? m1 : m0);
-                    const uint64_t i = sel_base[par][q] + sel_cnt[par][q][wid] + (uint32_t)__popc(mq & lt);
-                    A.qA[q == 0 ? i : (q == 1 ? 2u * A.pair_cap - 1u - i : A.pair_cap + i)] = ent;
+                    const uint64_t i = sel_base[par] + sel_cnt[par][wid] + (uint32_t)__popc(m & ((1u << lane) - 1u));
+                    A.qA[(A.qorder ? A.pair_cap : 0u) + i] = make_uint4((uint32_t)c, (k & 0xFFFFFFu) | (cls << 24), ip, iq);
                 }
                 par ^= 1;
             }
@@ -2207,6 +2224,60 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
     }
 }
 
+// FP32: the staged relaxation queue (qA[cap + i], arrival order) placed class
+// by class at qA[0 ..): class c starts at the sum of the counts of classes
+// below c (heaviest work first).  A CTA takes a chunk of 2048 staged entries,
+// ranks them per class in shared memory, reserves each class's share of the
+// chunk with one atomic on the class cursor and writes them out, so a class
+// keeps the chunks' order.  The order within a class is free: every draw of a
+// pair is keyed by the pair, not by its queue slot.
+constexpr int QORDER_GRID = 592;  // 148 SMs x 4 CTAs of 256 threads, grid-stride over chunks
+constexpr int QORDER_PER = 8;     // entries per thread and chunk
+static __global__ void __launch_bounds__(256) k_qorder(StepArgs A, int r) {
+    __shared__ uint32_t start[NCLS], cnt[NCLS], base[NCLS];
+    const uint32_t total = A.qsize[2 * r];
+    if (threadIdx.x < NCLS) {
+        uint32_t s0 = 0u;
+        for (int c = 0; c < (int)threadIdx.x; ++c) s0 += A.qsize[QCNT_OFF + r * NCLS + c];
+        start[threadIdx.x] = s0;
+    }
+    uint32_t* cur = A.qsize + QCUR_OFF + r * NCLS;
+    const uint4* stage = A.qA + A.pair_cap;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    constexpr uint32_t CH = 256u * QORDER_PER;
+    for (uint32_t c0 = blockIdx.x * CH; c0 < total; c0 += gridDim.x * CH) {
+        if (threadIdx.x < NCLS) cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        uint4 e[QORDER_PER];
+        uint32_t rank[QORDER_PER];
+#pragma unroll
+        for (int j = 0; j < QORDER_PER; ++j) {
+            const uint32_t i = c0 + (uint32_t)j * 256u + threadIdx.x;
+            const bool v = i < total;
+            e[j] = v ? stage[i] : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t cls = v ? e[j].y >> 24 : 0xFFFFFFFFu;  // no class: lanes past the end
+            const unsigned grp = __match_any_sync(0xFFFFFFFFu, cls);
+            const int leader = __ffs(grp) - 1;
+            uint32_t b0 = 0u;
+            if (v && lane == leader) b0 = atomicAdd(&cnt[cls], (uint32_t)__popc(grp));
+            rank[j] = __shfl_sync(0xFFFFFFFFu, b0, leader) + (uint32_t)__popc(grp & lt);
+        }
+        __syncthreads();
+        if (threadIdx.x < NCLS) {
+            const uint32_t n = cnt[threadIdx.x];
+            base[threadIdx.x] = n ? start[threadIdx.x] + atomicAdd(cur + threadIdx.x, n) : 0u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < QORDER_PER; ++j) {
+            const uint32_t i = c0 + (uint32_t)j * 256u + threadIdx.x;
+            if (i < total) A.qA[base[e[j].y >> 24] + rank[j]] = e[j];
+        }
+        __syncthreads();  // base and cnt are rewritten for the next chunk
+    }
+}
+
 // Phase 2: accepted pairs.  QK reaction test; reacting pairs go to the
 // reaction queue, the others are relaxed and scattered here.
 template <class R>
@@ -2296,29 +2367,28 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
     }
 }
 
-// FP32 phase 2: one thread per accepted pair (grid-stride over the queue's
-// regions: two molecules to relax, then one, then none).  The molecules with
+// FP32 phase 2: one thread per accepted pair (grid-stride over the queue in
+// work-class order, heaviest class first).  The molecules with
 // modes, P before Q, with the alias K5 draw (relative energy in int64 fixed
 // point), then isotropic scattering with the centre-of-mass velocity kept.
 template <class R>
 __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
-    // queue regions: pairs with two molecules to relax, then one, then none
-    const uint32_t n2 = A.qsize[2 * r], n21 = n2 + A.qsize[2 * MAX_ROUNDS + r];
-    const uint32_t total = n21 + A.qsize[3 * MAX_ROUNDS + r];
+    // the queue in work classes (k_qorder); the pair word's top byte is the class
+    const uint32_t total = A.qsize[2 * r];
     const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t w[2] = {0u, 0u};
     uint32_t w_samp = 0, w_pair = 0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
-        const uint4 e = A.qA[g < n2 ? (uint64_t)g
-                                    : (g < n21 ? 2u * A.pair_cap - 1u - (uint64_t)(g - n2) : A.pair_cap + (g - n21))];
+        const uint4 e = A.qA[g];
+        const uint32_t kp = e.y & 0xFFFFFFu;
         const int cidx = (int)e.x;
         const DevCell& cell = A.cells[cidx];
         const DevRes& rs = A.res[cell.res];
         const uint32_t step = rs.step, lcell = cell.lcell;
-        const uint32_t rk = ((uint32_t)r << 24) | e.y;
-        const uint32_t ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + e.y;
+        const uint32_t rk = ((uint32_t)r << 24) | kp;
+        const uint32_t ev_idx = A.abase[cidx] + (uint32_t)r * round_pairs(cell.n, A.has_recomb) + kp;
         const uint32_t ip = e.z, iq = e.w;
         uint4* recs = reinterpret_cast<uint4*>(cell.rec);
         const uint4 a = REC_LD(recs + 2 * ip), b = REC_LD(recs + 2 * iq);
@@ -2340,7 +2410,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         uint32_t chan = 0u, mpos = 0u;
         if (C->n_reactions > 0) {
             if (C->has_recomb &&
-                recomb_test<float>(A, C, cidx, r, e.y, sP, sQ, (double)sg_f32(pc, C->amode, g2), chan, mpos)) {
+                recomb_test<float>(A, C, cidx, r, kp, sP, sQ, (double)sg_f32(pc, C->amode, g2), chan, mpos)) {
                 react = true;
             } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
                                                      fix2d(EvQ), chan, (double)erP, (double)erQ)) {
@@ -2358,7 +2428,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         }
         const uint32_t rslot = queue_slot(A.qsize + 2 * r + 1, react);
         if (react) {
-            A.qB[rslot] = make_uint4((uint32_t)cidx, e.y, chan, mpos);
+            A.qB[rslot] = make_uint4((uint32_t)cidx, kp, chan, mpos);
             continue;
         }
         // the molecules with modes, P before Q, in one loop: a lane relaxing
@@ -2619,39 +2689,48 @@ __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
         const uint32_t j0 = (ch - A.chbase[c]) * (uint32_t)FINISH_CHUNK;
         const uint32_t j1 = min(j0 + (uint32_t)FINISH_CHUNK, cl.nsel);
         const uint32_t base = A.abase[c];
-        uint32_t acc = 0, samp = 0, over = 0, degen = 0, notex = 0, removed = 0, created = 0;
+        uint32_t acc = 0, samp = 0, over = 0, degen = 0, notex = 0, removed = 0, created = 0, trials = 0;
         uint32_t rxc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        unsigned long long trials = 0;
-        for (uint32_t j = j0 + lane; j < j1; j += 32) {
-            const uint32_t ev = A.cflag[base + j];
-            acc += ev & EV_ACC;
-            samp += (ev >> EV_SAMP_SHIFT) & 3u;
-            over += (ev >> EV_OVER_SHIFT) & 3u;
-            degen += (ev >> EV_DEGEN_SHIFT) & 3u;
-            notex += (ev & EV_NOTEXEC) ? 1u : 0u;
-            if (ev & EV_REMOVED) {
-                removed++;
-                const uint32_t slot = atomicAdd(&cl.rmfill, 1u);
-                A.rmpos[base + slot] =
-                    reinterpret_cast<const uint32_t*>(reinterpret_cast<const Rec*>(A.cscratch) + base + j)[0];
-            }
-            created += (ev & EV_CREATED) ? 1u : 0u;
-            trials += ev >> EV_TRIAL_SHIFT;
-            const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
-            if (rxid > 0 && rxid <= 8) rxc[rxid - 1]++;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-            samp += __shfl_xor_sync(0xFFFFFFFFu, samp, o);
-            over += __shfl_xor_sync(0xFFFFFFFFu, over, o);
-            degen += __shfl_xor_sync(0xFFFFFFFFu, degen, o);
-            notex += __shfl_xor_sync(0xFFFFFFFFu, notex, o);
-            removed += __shfl_xor_sync(0xFFFFFFFFu, removed, o);
-            created += __shfl_xor_sync(0xFFFFFFFFu, created, o);
-            trials += __shfl_xor_sync(0xFFFFFFFFu, trials, o);
+        // four event words a lane in flight at once (the words are read-only
+        // here); a slot past the chunk reads as 0, which counts nothing.  A
+        // chunk's trials fit 32 bits (at most 1024 x 65535)
+        for (uint32_t j = j0 + lane; j < j1; j += 128) {
+            uint32_t evs[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) rxc[i] += __shfl_xor_sync(0xFFFFFFFFu, rxc[i], o);
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t jj = j + 32u * (uint32_t)u;
+                evs[u] = jj < j1 ? __ldg(A.cflag + base + jj) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t ev = evs[u];
+                acc += ev & EV_ACC;
+                samp += (ev >> EV_SAMP_SHIFT) & 3u;
+                over += (ev >> EV_OVER_SHIFT) & 3u;
+                degen += (ev >> EV_DEGEN_SHIFT) & 3u;
+                notex += (ev & EV_NOTEXEC) ? 1u : 0u;
+                if (ev & EV_REMOVED) {
+                    removed++;
+                    const uint32_t slot = atomicAdd(&cl.rmfill, 1u);
+                    A.rmpos[base + slot] = reinterpret_cast<const uint32_t*>(
+                        reinterpret_cast<const Rec*>(A.cscratch) + base + j + 32u * (uint32_t)u)[0];
+                }
+                created += (ev & EV_CREATED) ? 1u : 0u;
+                trials += ev >> EV_TRIAL_SHIFT;
+                const uint32_t rxid = (ev >> EV_RX_SHIFT) & 63u;
+                if (rxid > 0 && rxid <= 8) rxc[rxid - 1]++;
+            }
         }
+        acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+        samp = __reduce_add_sync(0xFFFFFFFFu, samp);
+        over = __reduce_add_sync(0xFFFFFFFFu, over);
+        degen = __reduce_add_sync(0xFFFFFFFFu, degen);
+        notex = __reduce_add_sync(0xFFFFFFFFu, notex);
+        removed = __reduce_add_sync(0xFFFFFFFFu, removed);
+        created = __reduce_add_sync(0xFFFFFFFFu, created);
+        trials = __reduce_add_sync(0xFFFFFFFFu, trials);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) rxc[i] = __reduce_add_sync(0xFFFFFFFFu, rxc[i]);
         unsigned long long* cc = cellcnt + (size_t)c * NCNT;
         // one lane per counter; a cell of one chunk needs no atomics, but its
         // counters may also receive other chunks' atomics, so all use them
@@ -2666,7 +2745,7 @@ __global__ void __launch_bounds__(256) k_finish_count(StepArgs A) {
                 A.chcnt[ch] = created;
                 if (created) atomicAdd(&cl.ncreated, created);
                 break;
-            case 7: if (trials) atomicAdd(cc + CNT_TRIALS, trials); break;
+            case 7: if (trials) atomicAdd(cc + CNT_TRIALS, (unsigned long long)trials); break;
             default:
                 if (lane < 16 && rxc[lane - 8] && lane - 8 < NCNT - CNT_RX0)
                     atomicAdd(cc + CNT_RX0 + (lane - 8), (unsigned long long)rxc[lane - 8]);
@@ -2895,8 +2974,11 @@ void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream
     const int gs = a.grid_select > 0 ? a.grid_select : grid;
     const int gr = a.grid_relax > 0 ? a.grid_relax : grid;
     const int gx = a.grid_react > 0 ? a.grid_react : grid;
-    if (phase == 0) k_select<R><<<gs, SELECT_THREADS, 0, s>>>(a, r);
-    else if (phase == 1) {
+    if (phase == 0) {
+        k_select<R><<<gs, SELECT_THREADS, 0, s>>>(a, r);
+        if constexpr (std::is_same<R, float>::value)
+            if (a.qorder) k_qorder<<<QORDER_GRID, 256, 0, s>>>(a, r);
+    } else if (phase == 1) {
         if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<gr, 128, 0, s>>>(a, r);
         else k_relax<R><<<gr, 128, 0, s>>>(a, r);
     } else if (a.has_reactions) k_react<R><<<gx, 128, 0, s>>>(a, r);
@@ -2933,8 +3015,8 @@ void launch_step_impl(const StepArgs& a, int grid, int block, cudaStream_t s, ui
     launch_finish_impl<R>(a, s);
     launch_compact_impl<R>(a, s);
     if (launches)
-        *launches += ns + 2 + a.max_rounds * (a.has_reactions ? 3 : 2) + (a.has_recomb ? 2 : 0) +
-                     (a.creates ? 1 : 0);
+        *launches += ns + 2 + a.max_rounds * ((a.has_reactions ? 3 : 2) + (std::is_same<R, float>::value && a.qorder ? 1 : 0)) +
+                     (a.has_recomb ? 2 : 0) + (a.creates ? 1 : 0);
 }
 
 // ------------------------------------------------------------- sampler diagnostics

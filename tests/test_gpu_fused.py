@@ -34,6 +34,23 @@ def _ragged():
     return base
 
 
+def _ragged_multitile():
+    """1000 cells (four set-up tiles of 256) of 0..299 particles, a fifth of
+    them empty: tile offsets and the block-cell table across tiles."""
+    base = W.relaxation_triatomic(n_particles=10, n_cells=1)
+    rng = np.random.default_rng(23)
+    counts = rng.integers(0, 300, 1000)
+    counts[rng.random(1000) < 0.2] = 0
+    n = int(counts.sum())
+    cell = np.repeat(np.arange(len(counts), dtype=np.int32), counts)
+    base.cell = cell[rng.permutation(n)]
+    base.n_cells = len(counts)
+    base.species_idx = np.zeros(n, np.int32)
+    base.v = W.maxwellian(rng, n, np.full(n, base.species[0].mass), 20000.0)
+    base.weight = 1e23 * base.cell_volume / counts.max()
+    return base
+
+
 def _two_rounds():
     w = W.relaxation_triatomic(n_particles=4000, n_cells=4)
     w.dt *= 3.0  # N_sel > N/2: two pairing rounds per step
@@ -46,6 +63,7 @@ CASES = {
     "ch4_bath_no_dissociation": (lambda: W.ch4_heat_bath(n_cells=40, per_cell=500, dissociation=False), {}),
     "triatomic_multicell": (lambda: W.relaxation_triatomic(n_particles=12000, n_cells=6), {}),
     "ragged_cells": (_ragged, {}),
+    "ragged_multitile": (_ragged_multitile, {}),
     "two_rounds": (_two_rounds, {"max_rounds": 4}),
 }
 
@@ -110,6 +128,23 @@ def test_fused_path_eligibility():
     n0 = g4.kernel_launches()
     g4.step(7)
     assert g4.kernel_launches() - n0 == 7
+
+
+def test_queue_path_launch_count():
+    """The launches a step's CUDA graph replays are counted from its capture:
+    the same count as the profiled step, which launches kernel by kernel.
+    Exchange mixture, two rounds: set-up 2, per round select, work-class
+    placement, relax and react, then the finish count and the cell update."""
+    w = W.ch4_h_exchange(n_cells=16, per_cell=600)
+    g = hcao.from_workload(w, precision=hcao.FP32)
+    p = hcao.from_workload(w, precision=hcao.FP32)
+    p.set_profiling(True)
+    n0, m0 = g.kernel_launches(), p.kernel_launches()
+    g.step(3)
+    p.step(3)
+    assert g.kernel_launches() - n0 == p.kernel_launches() - m0 == 3 * 12
+    for x, y in zip(_state(g, w), _state(p, w)):
+        assert np.array_equal(x, y)
 
 
 def test_fused_profiling_class():
