@@ -1780,6 +1780,19 @@ __device__ __forceinline__ uint32_t queue_slot(uint32_t* size, bool want) {
     return base + (uint32_t)__popc(m & ((1u << lane) - 1u));
 }
 
+// A cell's max sigma_T g of the step (bits of a double >= 0, which order as
+// integers).  In a large cell (a single-cell reservoir of millions) the
+// atomic only when the value could raise the max: the max only grows during
+// the step, so a value not above one already read changes nothing, and a
+// stale read merely costs an atomic; without the test the cell's warps queue
+// on one word.  A small cell takes the atomic without the read (few warps
+// share its word, and the read would add its latency).
+constexpr uint32_t SEEN_READ_MIN_N = 8192;
+__device__ __forceinline__ void seen_max(unsigned long long* seen, double v, uint32_t N) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (N < SEEN_READ_MIN_N || b > __ldcg(seen)) atomicMax(seen, b);
+}
+
 // cell of flat pair index g in a prefix array (largest c with pb[c] <= g)
 __device__ __forceinline__ int cell_of(const uint32_t* pb, int n_cells, uint32_t g) {
     int lo = 0, hi = n_cells;
@@ -2048,7 +2061,7 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
             bool accept = false;
             uint32_t cls = 0u;
             float sgf = 0.f;
-            uint32_t k = 0, ip = 0, iq = 0;
+            uint32_t k = 0, ip = 0, iq = 0, N = 0;
             if (valid) {
                 {  // the cell of g: bisection between the cells of g's 256-pair block and the next
                     const uint32_t* bc = A.blkcell + (size_t)r * A.blk_stride + (g >> 8);
@@ -2062,7 +2075,7 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 }
                 k = g - __ldg(pb + c);
                 const DevCell& cell = A.cells[c];
-                const uint32_t N = cell.n;
+                N = cell.n;
                 const uint32_t rk = ((uint32_t)r << 24) | k;
                 const uint32_t key[4] = {cell.pkey[r][0], cell.pkey[r][1], cell.pkey[r][2], cell.pkey[r][3]};
                 ip = pair_perm(2u * k, N, key);
@@ -2138,8 +2151,7 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 const unsigned grp = __ballot_sync(act, key == cl);
                 float mx = key == cl ? sgf : 0.f;
                 for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(act, mx, o));
-                if (lane == leader)
-                    atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong((double)mx));
+                if (lane == leader) seen_max(&A.cells[cl].seen, (double)mx, N);  // the leader's cell is cl
                 left &= ~grp;
             }
         }
@@ -2150,12 +2162,13 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
         int c = 0;
         bool accept = false, react = false;
         double sg = 0.0;
-        uint32_t k = 0, ip = 0, iq = 0, chan = 0;
+        uint32_t k = 0, ip = 0, iq = 0, chan = 0, N = 0;
         if (valid) {
             c = cell_of(pb, A.n_cells, g);
             k = g - __ldg(pb + c);
             const PairLoc L = locate(A, c, r, k);
             ip = L.ip;
+            N = L.N;
             iq = L.iq;
             const DevRes& rs = A.res[A.cells[c].res];
             const Rec* recs = reinterpret_cast<const Rec*>(L.recs);
@@ -2216,8 +2229,7 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
                 if (v > mx) mx = v;
                 g2 &= g2 - 1;
             }
-            if (lane == leader)
-                atomicMax(&A.cells[cl].seen, (unsigned long long)__double_as_longlong(mx));
+            if (lane == leader) seen_max(&A.cells[cl].seen, mx, N);  // the leader's cell is cl
             left &= ~grp;
         }
     }
