@@ -551,9 +551,9 @@ def main():
     _barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ctx.sync()
+    launches = ctx.kernel_launches() - launches0  # the timed steps' kernels only (the read-outs below launch too)
     c1 = ctx.read_counters(0)
     comp1 = composition(ctx, w)
-    launches = ctx.kernel_launches() - launches0
     ctx.close()
     ctx = None
     # The per-kernel split of the roofline: the same steps of the same

@@ -283,8 +283,12 @@ hcao_status hcao_count(hcao_ctx* ctx, int res, int64_t* n);
    host arrays sized by hcao_count; any of them may be NULL. */
 hcao_status hcao_read_particles(hcao_ctx* ctx, int res, double* host_v, uint8_t* host_qn,
                                 int32_t* host_species, int32_t* host_cell);
-/* Moments of reservoir res, reduced on the device in FP64; T_vib by the
-   zero-point search on the host. */
+/* Moments of reservoir res, reduced on the device; T_vib by the zero-point
+   search on the host.  FP64 mode sums in FP64.  FP32 mode sums exact int64
+   fixed point: E_vib from the level tables, momentum and E_tr from float
+   products of each particle's velocity and its mass (the mass as a float
+   pair, so unrounded): a few float roundings per particle (<= 3e-7
+   relative), unbiased.  Synchronises. */
 hcao_status hcao_read_moments(hcao_ctx* ctx, int res, hcao_moments* out);
 /* Level populations of one mode of one species in reservoir res:
    counts[i] = particles with quantum number i (i < max_levels). */

@@ -1234,6 +1234,7 @@ hcao_status hcao_set_species(hcao_ctx* ctx, const hcao_species* species, int n) 
         DevSpecies& D = C.sp[i];
         D.mass = s.d.mass;
         D.mass_f = (float)s.d.mass;
+        D.mass_lo_f = (float)(s.d.mass - (double)D.mass_f);
         D.E_form = s.d.E_form;
         // rotation: the maximum of the LB fraction's density shape,
         // x^(rot_dof/2 - 1) (1 - x)^(3/2 - omega): 1 at x = 0 for two degrees
@@ -2240,9 +2241,12 @@ hcao_status hcao_read_moments(hcao_ctx* ctx, int id, hcao_moments* out) {
     CU(dalloc(ctx, &dcnt.p, MAXS));
     CU(cudaMemsetAsync(dacc.p, 0, sizeof(double) * (5 + 2 * MAXS), ctx->stream));
     CU(cudaMemsetAsync(dcnt.p, 0, sizeof(unsigned long long) * MAXS, ctx->stream));
-    uint64_t total = 0;
-    hcao_status pst = particle_prefix(ctx, *r, &dpo.p, &total);
-    if (pst != HCAO_OK) return pst;
+    // the particle prefix on the device: no copy of the cell table, and the
+    // total stays there too (the kernel reads it; the grid is the full one)
+    CU(dalloc(ctx, &dpo.p, (size_t)r->n_cells + 1));
+    launch_cell_prefix(ctx->d_cells, r->cell0, r->n_cells, dpo.p, ctx->stream);
+    ctx->launches++;
+    const uint64_t total = ~0ull;
     if (ctx->cfg.precision == HCAO_FP64)
         launch_moments<double>(ctx->d_cells, r->cell0, r->n_cells, dpo.p, total, ctx->d_consts, ctx->d_lev64,
                                ctx->d_levfix, dacc.p, dcnt.p, ctx->stream);
@@ -2379,18 +2383,20 @@ hcao_status hcao_read_counters(hcao_ctx* ctx, int id, uint64_t* out, int max, in
     if (!ctx || !out || max < 1) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_counters: no loaded reservoir");
-    std::vector<unsigned long long> h((size_t)r->n_cells * NCNT);
-    CU(cudaMemcpyAsync(h.data(), ctx->d_cellcnt + (size_t)r->cell0 * NCNT, sizeof(unsigned long long) * h.size(),
-                       cudaMemcpyDeviceToHost, ctx->stream));
+    // summed over the reservoir's cells on the device; NCNT words come back
+    DevTemp<unsigned long long> dsum(ctx);
+    CU(dalloc(ctx, &dsum.p, NCNT));
+    CU(cudaMemsetAsync(dsum.p, 0, sizeof(unsigned long long) * NCNT, ctx->stream));
+    launch_sum_counters(ctx->d_cellcnt, r->cell0, r->n_cells, NCNT,
+                        dsum.p, ctx->stream);
+    ctx->launches++;
+    unsigned long long h[NCNT];
+    CU(cudaMemcpyAsync(h, dsum.p, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
     DevRes dr{};
     CU(cudaMemcpyAsync(&dr, ctx->d_res + id, sizeof dr, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     const int n = std::min(max, 8 + ctx->n_reactions);
-    for (int i = 0; i < n; ++i) {
-        uint64_t s = 0;
-        for (int c = 0; c < r->n_cells; ++c) s += h[(size_t)c * NCNT + i];
-        out[i] = s;
-    }
+    for (int i = 0; i < n; ++i) out[i] = h[i];
     if (n > CNT_STEPS) out[CNT_STEPS] = dr.step;
     if (n_out) *n_out = n;
     return map_err(ctx);

@@ -85,7 +85,8 @@ struct DevSpecies {
     int n_lev[MAXM];
     int tab_off;                     // offset of table 0; table k at tab_off + k * MT
     float mass_f;
-    int pad[2];
+    float mass_lo_f;                 // mass - mass_f rounded to float: mass_f + mass_lo_f carries ~48 bits
+    int pad;
     // FP32-mode bookkeeping in int64 fixed point (1 unit = 2^-100 J)
     long long zpe_fix, top_fix;
     long long De_fix[MAXM];
@@ -260,6 +261,12 @@ template <class R> void launch_step(const StepArgs& a, int grid_collide, int blo
 int launch_setup(const StepArgs& a, cudaStream_t s);  // precision-independent (hcao_f64.cu); returns launches
 void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, const int32_t* sp,
                           const uint8_t* qn, int64_t n, uint32_t* flags, cudaStream_t s);
+// precision-independent read-outs on the device: a reservoir's particle prefix
+// over its cells (n_cells + 1 entries), and its counters summed over its cells
+// into out (zeroed by the caller)
+void launch_cell_prefix(const DevCell* cells, int cell0, int n_cells, uint64_t* off, cudaStream_t s);
+void launch_sum_counters(const unsigned long long* cnt, int cell0, int n_cells, int n_cnt, unsigned long long* out,
+                         cudaStream_t s);
 template <class R> void launch_collide(const StepArgs& a, int r, int grid, int block, cudaStream_t s);
 // phase k of round r: 0 select, 1 relax, 2 react (for per-kernel timing)
 template <class R> void launch_phase(const StepArgs& a, int r, int phase, int grid, cudaStream_t s);

@@ -2029,6 +2029,68 @@ void launch_validate_load(const Consts* C, int n_cells, const int32_t* cell, con
     if (g > 2368) g = 2368;
     k_validate_load<<<(int)g, 256, 0, s>>>(C, n_cells, cell, sp, qn, n, flags);
 }
+
+// off[c] = the particles of cells cell0 .. cell0 + c - 1 (c = 0 .. n_cells),
+// the canonical-order prefix of a reservoir, on the device (no copy of the
+// cell table to the host): one CTA, each thread a contiguous run of cells.
+static __global__ void __launch_bounds__(1024) k_cell_prefix(const DevCell* cells, int cell0, int n_cells,
+                                                             uint64_t* off) {
+    __shared__ uint64_t wtot[32];
+    const int per = (n_cells + 1023) / 1024;
+    const int c0 = min((int)threadIdx.x * per, n_cells), c1 = min(c0 + per, n_cells);
+    uint64_t s = 0;
+    for (int c = c0; c < c1; ++c) s += cells[cell0 + c].n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t x = s;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t t = wtot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= o) t += y;
+        }
+        wtot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    uint64_t run = (wid ? wtot[wid - 1] : 0ull) + x - s;  // exclusive prefix of this thread's run
+    for (int c = c0; c < c1; ++c) {
+        off[c] = run;
+        run += cells[cell0 + c].n;
+    }
+    if (threadIdx.x == 0) off[n_cells] = wtot[31];
+}
+
+void launch_cell_prefix(const DevCell* cells, int cell0, int n_cells, uint64_t* off, cudaStream_t s) {
+    k_cell_prefix<<<1, 1024, 0, s>>>(cells, cell0, n_cells, off);
+}
+
+// out[i] = the sum over cells cell0 .. cell0 + n_cells - 1 of counter i
+// (n_cnt counters a cell): a warp per counter and CTA, one atomic each.
+static __global__ void __launch_bounds__(256) k_sum_counters(const unsigned long long* cnt, int cell0, int n_cells,
+                                                              int n_cnt, unsigned long long* out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < n_cnt; i += 8) {
+        unsigned long long s = 0;
+        for (int c = blockIdx.x * 32 + lane; c < n_cells; c += gridDim.x * 32)
+            s += cnt[(size_t)(cell0 + c) * n_cnt + i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0 && s) atomicAdd(out + i, s);
+    }
+}
+
+void launch_sum_counters(const unsigned long long* cnt, int cell0, int n_cells, int n_cnt, unsigned long long* out,
+                         cudaStream_t s) {
+    const int g = (n_cells + 31) / 32 < 148 ? (n_cells + 31) / 32 : 148;
+    k_sum_counters<<<g < 1 ? 1 : g, 256, 0, s>>>(cnt, cell0, n_cells, n_cnt, out);
+}
 #endif
 
 // Phase 1 of a round: every candidate pair's VHS acceptance (NTC).  Rejected
@@ -3212,6 +3274,12 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
     __syncthreads();
     constexpr bool f32 = std::is_same<R, float>::value;
     double px = 0.0, py = 0.0, pz = 0.0, etr = 0.0, ef = 0.0;
+    // FP32 mode: momentum (2^-110 kg m/s) and translational energy (2^-100
+    // J) in int64 fixed point from float products, exact integer sums (no
+    // FP64 work per particle); the mass as the float pair mass_f + mass_lo_f,
+    // so that only the float rounding of each particle's v and v^2 products
+    // remains (unbiased), not that of the mass; E_form from the species counts
+    long long pxx = 0, pyx = 0, pzx = 0, etx = 0;
     double ev[MAXS], er[MAXS];
     long long evx[MAXS];
     uint32_t nc[MAXS];
@@ -3232,13 +3300,26 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
         const int s = (int)(r.meta & 0xFFu);
         if (s >= MAXS) continue;  // a removed particle left by a failed compaction (error reported)
         const DevSpecies& S = C->sp[s];
-        const double m = S.mass;
-        const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
-        px += m * vx;
-        py += m * vy;
-        pz += m * vz;
-        etr += 0.5 * m * (vx * vx + vy * vy + vz * vz);
-        ef += S.E_form;
+        if constexpr (f32) {
+            const float mf = S.mass_f, ml = S.mass_lo_f;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const long long p = __float2ll_rn(__fmul_rn(__fmul_rn(mf, r.v[d]), 0x1p110f)) +
+                                    __float2ll_rn(__fmul_rn(__fmul_rn(ml, r.v[d]), 0x1p110f));
+                if (d == 0) pxx += p; else if (d == 1) pyx += p; else pzx += p;
+            }
+            const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(r.v[0], r.v[0]), __fmul_rn(r.v[1], r.v[1])),
+                                       __fmul_rn(r.v[2], r.v[2]));
+            etx += f2fix(__fmul_rn(__fmul_rn(0.5f, mf), v2)) + f2fix(__fmul_rn(__fmul_rn(0.5f, ml), v2));
+        } else {
+            const double m = S.mass;
+            const double vx = r.v[0], vy = r.v[1], vz = r.v[2];
+            px += m * vx;
+            py += m * vy;
+            pz += m * vz;
+            etr += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+            ef += S.E_form;
+        }
         if constexpr (f32) {
             const long long e = evib_fix(levfix, S, r.q);
 #pragma unroll
@@ -3258,10 +3339,17 @@ __global__ void __launch_bounds__(256) k_moments(const DevCell* cells, int cell0
         }
     }
     if constexpr (f32) {
-        // per thread below 2^53 units (its particles' vibrational energies),
-        // so the conversion is exact
+        // a thread's sums stay below 2^53 units up to ~1e9 particles a
+        // launch, where the conversions are exact
 #pragma unroll
-        for (int k = 0; k < MAXS; ++k) ev[k] = (double)evx[k] * 0x1p-100;
+        for (int k = 0; k < MAXS; ++k) {
+            ev[k] = (double)evx[k] * 0x1p-100;
+            if (nc[k]) ef += (double)nc[k] * C->sp[k].E_form;
+        }
+        px = (double)pxx * 0x1p-110;
+        py = (double)pyx * 0x1p-110;
+        pz = (double)pzx * 0x1p-110;
+        etr = (double)etx * 0x1p-100;
     }
     auto wsum = [](double x) {
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
