@@ -696,21 +696,14 @@ hcao_status read_cells(hcao_ctx* ctx, const Reservoir& r, std::vector<DevCell>& 
 }
 
 // off[c] = first particle of cell c in canonical order, off[n_cells] = total,
-// uploaded to a fresh device buffer the caller frees
+// in a fresh device buffer the caller frees: scanned on the device, only the
+// total comes back (synchronises)
 hcao_status particle_prefix(hcao_ctx* ctx, const Reservoir& r, uint64_t** d_off, uint64_t* total) {
-    std::vector<DevCell> cells;
-    hcao_status st = read_cells(ctx, r, cells);
-    if (st != HCAO_OK) return st;
-    std::vector<uint64_t> off((size_t)r.n_cells + 1);
-    uint64_t n = 0;
-    for (int c = 0; c < r.n_cells; ++c) {
-        off[c] = n;
-        n += cells[c].n;
-    }
-    off[r.n_cells] = n;
-    CU(dalloc(ctx, d_off, off.size()));
-    CU(cudaMemcpyAsync(*d_off, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
-    *total = n;
+    CU(dalloc(ctx, d_off, (size_t)r.n_cells + 1));
+    launch_cell_prefix(ctx->d_cells, r.cell0, r.n_cells, *d_off, ctx->stream);
+    ctx->launches++;
+    CU(cudaMemcpyAsync(total, *d_off + r.n_cells, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return HCAO_OK;
 }
 
@@ -2180,10 +2173,11 @@ hcao_status hcao_count(hcao_ctx* ctx, int id, int64_t* n) {
     if (!r) return fail(ctx, HCAO_ENOTFOUND, "count: no such reservoir");
     *n = 0;
     if (!r->loaded) return HCAO_OK;
-    std::vector<DevCell> cells;
-    hcao_status st = read_cells(ctx, *r, cells);
+    DevTemp<uint64_t> dpo(ctx);
+    uint64_t total = 0;
+    hcao_status st = particle_prefix(ctx, *r, &dpo.p, &total);
     if (st != HCAO_OK) return st;
-    for (auto& c : cells) *n += c.n;
+    *n = (int64_t)total;
     return map_err(ctx);
 }
 
@@ -2193,27 +2187,18 @@ hcao_status hcao_read_particles(hcao_ctx* ctx, int id, double* v, uint8_t* qn, i
     if (!ctx) return HCAO_EINVAL;
     Reservoir* r = get_res(ctx, id);
     if (!r || !r->loaded) return fail(ctx, HCAO_ENOTFOUND, "read_particles: no loaded reservoir");
-    std::vector<DevCell> cells;
-    hcao_status st = read_cells(ctx, *r, cells);
-    if (st != HCAO_OK) return st;
-    std::vector<uint64_t> off((size_t)r->n_cells + 1);
+    DevTemp<uint64_t> doff(ctx);
     uint64_t n = 0;
-    for (int c = 0; c < r->n_cells; ++c) {
-        off[c] = n;
-        n += cells[c].n;
-    }
-    off[r->n_cells] = n;
+    hcao_status st = particle_prefix(ctx, *r, &doff.p, &n);
+    if (st != HCAO_OK) return st;
     if (n == 0) return map_err(ctx);
     DevTemp<double> dv(ctx);
     DevTemp<uint8_t> dq(ctx);
     DevTemp<int32_t> ds(ctx), dc(ctx);
-    DevTemp<uint64_t> doff(ctx);
     CU(dalloc(ctx, &dv.p, (size_t)n * 3));
     CU(dalloc(ctx, &dq.p, (size_t)n * 16));
     CU(dalloc(ctx, &ds.p, (size_t)n));
     CU(dalloc(ctx, &dc.p, (size_t)n));
-    CU(dalloc(ctx, &doff.p, (size_t)r->n_cells + 1));
-    CU(cudaMemcpyAsync(doff.p, off.data(), sizeof(uint64_t) * off.size(), cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->cfg.precision == HCAO_FP64)
         launch_pack<double>(ctx->d_cells, r->cell0, r->n_cells, doff.p, n, ctx->d_consts, dv.p, dq.p, ds.p, dc.p, ctx->stream);
     else
