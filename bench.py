@@ -726,6 +726,9 @@ def main():
                 hcao, torch, stream, W.ch4_heat_bath(), hcao.FP32, 20, 5, flush)
         others["ch4_heat_bath_4096x500_15000K_no_dissociation_fp32"] = run_config(
             hcao, torch, stream, W.ch4_heat_bath(dissociation=False), hcao.FP32, 20, 5, flush)
+        # the heat bath in the FP64 parity mode too (its configuration names both)
+        others["ch4_heat_bath_4096x500_15000K_fp64"] = run_config(
+            hcao, torch, stream, W.ch4_heat_bath(), hcao.FP64, 10, 3, flush)
         others["triatomic_relaxation_20000x1_fp64"] = run_config(
             hcao, torch, stream, W.relaxation_triatomic(), hcao.FP64, 50, 5, flush)
     batched = None

@@ -51,6 +51,16 @@ def _ragged_multitile():
     return base
 
 
+def _many_species():
+    """Nine species of 0, 1, 3, 4, 6 and 9 modes: 31 distinct work keys
+    (the mode counts of the molecules a pair relaxes, in order), more than the
+    queue path's 16 work classes, so the lightest keys share the last class."""
+    names = ["H2O", "OH", "N2", "HCN", "CH4", "CH3", "H2", "H", "N"]
+    species = [W.paper_species(n) for n in names]
+    return W._build("many_species", species, [], 40, np.full(40, 300), [1.0] * len(names), 4.64e-6, 1e23,
+                    2.0e-9, 8000.0, 8000.0, 0x4D535053, 10)
+
+
 def _two_rounds():
     w = W.relaxation_triatomic(n_particles=4000, n_cells=4)
     w.dt *= 3.0  # N_sel > N/2: two pairing rounds per step
@@ -64,6 +74,7 @@ CASES = {
     "triatomic_multicell": (lambda: W.relaxation_triatomic(n_particles=12000, n_cells=6), {}),
     "ragged_cells": (_ragged, {}),
     "ragged_multitile": (_ragged_multitile, {}),
+    "many_species": (_many_species, {}),
     "two_rounds": (_two_rounds, {"max_rounds": 4}),
 }
 
