@@ -392,12 +392,15 @@ hcao_status hcao_set_profiling(hcao_ctx* ctx, int enable);
 hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_launches, int max,
                               int* n_out);
 
-/* Launch-shape autotuner: steps the reservoirs by 7 x steps_per_candidate
+/* Launch-schedule autotuner: steps the reservoirs by 7 x steps_per_candidate
    steps while timing candidate grid sizes of the pair-acceptance and
-   relaxation kernels (CUDA events), then keeps the fastest.  The simulation
-   advances normally: results do not depend on launch shapes (every draw is
-   keyed by step, cell and pair).  chosen (may be NULL) receives the two grid
-   sizes. */
+   relaxation kernels (CUDA events), then keeps the fastest; in FP32 mode with
+   more than one work class (species pairs whose molecules differ in mode
+   counts) 2 x steps_per_candidate more, timing the relaxation queue with and
+   without its placement by work class.  The simulation advances normally:
+   results do not depend on the schedule (every draw is keyed by step, cell
+   and pair).  chosen (may be NULL, else 3 ints) receives the two grid sizes
+   and 1 if the queue is placed by work class. */
 hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen);
 
 /* Algorithmic work of the FP32 relaxation kernel since create: host_out[0]

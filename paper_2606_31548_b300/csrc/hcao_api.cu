@@ -146,6 +146,7 @@ struct hcao_ctx {
     uint32_t* d_chcnt = nullptr;
     // launch shapes (autotuned; results do not depend on them)
     int grid_select = 0, grid_relax = 0, grid_react = 0;
+    bool qorder_off = false;  // the autotuner found the FP32 work-class placement not paying
     // CUDA graph of one step, captured on a private stream, re-captured when
     // the kernel arguments change
     cudaStream_t cap_stream = nullptr;
@@ -958,7 +959,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.grid_select = ctx->grid_select;
     a.grid_relax = ctx->grid_relax;
     a.grid_react = ctx->grid_react;
-    a.qorder = ctx->hc.n_cls > 1 ? 1 : 0;
+    a.qorder = (ctx->hc.n_cls > 1 && !ctx->qorder_off) ? 1 : 0;
     a.pair_cap = ctx->pair_cap;
     a.log = ctx->d_log;
     a.log_on = ctx->log_on ? 1 : 0;
@@ -2116,14 +2117,15 @@ hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen) {
     const int rel_cand[3] = {4 * sm, 5 * sm, 8 * sm};
     const bool was_prof = ctx->prof_on;
     ctx->prof_on = true;
-    auto time_phase = [&](int k) -> double {  // mean ms of profile class k over the candidate's steps
+    // ms of profile classes k (and k2, when >= 0) over one candidate's steps
+    auto time_phase = [&](int k, int k2 = -1) -> double {
         for (int j = 0; j < hcao_ctx::NPROF; ++j) { ctx->prof_used[j] = 0; ctx->prof_ms[j] = 0; ctx->prof_n[j] = 0; }
         if (hcao_step(ctx, steps_per_candidate) != HCAO_OK) return 1e30;
         double ms[hcao_ctx::NPROF];
         uint64_t n[hcao_ctx::NPROF];
         int got = 0;
         if (hcao_read_profile(ctx, ms, n, hcao_ctx::NPROF, &got) != HCAO_OK) return 1e30;
-        return ms[k];
+        return ms[k] + (k2 >= 0 ? ms[k2] : 0.0);
     };
     double best = 1e30;
     int bs = ctx->grid_select, br = ctx->grid_relax;
@@ -2140,9 +2142,22 @@ hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen) {
         if (t < best) { best = t; br = c; }
     }
     ctx->grid_relax = br;
+    // the FP32 relaxation queue's placement by work class: kept where it pays
+    // (selection with the placement + relaxation, against both without it)
+    if (ctx->cfg.precision == HCAO_FP32 && ctx->hc.n_cls > 1 && !use_fused(ctx, nullptr)) {
+        ctx->qorder_off = false;
+        const double t_on = time_phase(1, 2);
+        ctx->qorder_off = true;
+        const double t_off = time_phase(1, 2);
+        ctx->qorder_off = t_off < t_on;
+    }
     ctx->prof_on = was_prof;
     for (int j = 0; j < hcao_ctx::NPROF; ++j) { ctx->prof_used[j] = 0; ctx->prof_ms[j] = 0; ctx->prof_n[j] = 0; }
-    if (chosen) { chosen[0] = bs; chosen[1] = br; }
+    if (chosen) {
+        chosen[0] = bs;
+        chosen[1] = br;
+        chosen[2] = (ctx->hc.n_cls > 1 && !ctx->qorder_off) ? 1 : 0;
+    }
     return map_err(ctx);
 }
 

@@ -425,10 +425,11 @@ class Context:
         return p.value
 
     def autotune(self, steps_per_candidate=1):
-        """Pick launch shapes by timing candidates on live steps; returns (select grid, relax grid)."""
-        out = np.zeros(2, np.int32)
+        """Pick the launch schedule by timing candidates on live steps; returns
+        (select grid, relax grid, queue placed by work class: 0 or 1)."""
+        out = np.zeros(3, np.int32)
         self._chk(self.L.hcao_autotune(self.h, steps_per_candidate, _p(out)))
-        return int(out[0]), int(out[1])
+        return int(out[0]), int(out[1]), int(out[2])
 
     def read_work(self) -> np.ndarray:
         """[level evaluations, mode draws, molecule samples, relaxed pairs] (FP32 relax kernel)."""
