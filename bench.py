@@ -529,7 +529,6 @@ def main():
     ctx.sync()
     c0 = ctx.read_counters(0)
     comp0 = composition(ctx, w)
-    launches0 = ctx.kernel_launches()
     torch.cuda.synchronize()
     _barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -539,21 +538,23 @@ def main():
     with Clocks(local) as clk:
         clk.start()
         t_wall0 = time.perf_counter()
+        launches = 0
         for i in range(args.steps):
             n = ctx.count(0)  # particles entering this step (host sync, outside the events)
             psteps += n
             if do_flush:
                 flush.zero_()
+            l0 = ctx.kernel_launches()
             ev[i][0].record(stream)
             ctx.step(1)
             ev[i][1].record(stream)
+            launches += ctx.kernel_launches() - l0  # the step's kernels (not the count's read-out)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
         clk.stop()
     _barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ctx.sync()
-    launches = ctx.kernel_launches() - launches0  # the timed steps' kernels only (the read-outs below launch too)
     c1 = ctx.read_counters(0)
     comp1 = composition(ctx, w)
     ctx.close()

@@ -403,10 +403,13 @@ hcao_status hcao_read_profile(hcao_ctx* ctx, double* host_ms, uint64_t* host_lau
    and 1 if the queue is placed by work class. */
 hcao_status hcao_autotune(hcao_ctx* ctx, int steps_per_candidate, int* chosen);
 
-/* Algorithmic work of the FP32 relaxation kernel since create: host_out[0]
-   LB level evaluations (one weight of one level of one mode), [1] mode draws
-   (one Philox uniform each), [2] molecule samples, [3] relaxed pairs; *n_out
-   = 4.  Zero in FP64 mode.  (Instrumentation for the ALU roofline.) */
+/* Algorithmic work of the FP32 relaxation kernel since create, counted on
+   the steps taken with profiling on (hcao_set_profiling, and the autotuner's
+   steps; other steps skip the counting, which costs the kernel ~4%):
+   host_out[0] LB level evaluations (one weight of one level of one mode), [1]
+   mode draws (one Philox uniform each), [2] molecule samples, [3] relaxed
+   pairs; *n_out = 4.  Zero in FP64 mode.  (Instrumentation for the ALU
+   roofline.) */
 hcao_status hcao_read_work(hcao_ctx* ctx, uint64_t* host_out, int max, int* n_out);
 
 /* ---------------------------------------------------------------- serving

@@ -955,7 +955,7 @@ StepArgs make_args(hcao_ctx* ctx) {
     a.tsum = ctx->d_tsum;
     a.chbase = ctx->d_chbase;
     a.chcnt = ctx->d_chcnt;
-    a.work = ctx->d_work;
+    a.work = ctx->prof_on ? ctx->d_work : nullptr;  // the K5 work is counted on profiled steps
     a.grid_select = ctx->grid_select;
     a.grid_relax = ctx->grid_relax;
     a.grid_react = ctx->grid_react;

@@ -1062,16 +1062,25 @@ __device__ __forceinline__ long long etr_fix_f32(const DevPair& pc, float g2) {
 }
 // isotropic scattering with the centre-of-mass velocity kept: relative speed
 // from the relative energy Erel, direction d
-__device__ __forceinline__ void scatter_f32(const DevPair& pc, long long Erel, const float d[3],
-                                            const float va[3], const float vb[3], float na[3], float nb[3]) {
+__device__ __forceinline__ float cm_velocity_f32(const DevPair& pc, float va, float vb) {
+    return __fadd_rn(__fmul_rn(pc.fq_f, va), __fmul_rn(pc.fp_f, vb));
+}
+// the same from the centre-of-mass velocity V (cm_velocity_f32)
+__device__ __forceinline__ void scatter_cm_f32(const DevPair& pc, long long Erel, const float d[3],
+                                               const float V[3], float na[3], float nb[3]) {
     const float gn = __fsqrt_rn(__fmul_rn(fix2f(Erel), pc.inv2mr_f));
 #pragma unroll
     for (int c3 = 0; c3 < 3; ++c3) {
-        const float V = __fadd_rn(__fmul_rn(pc.fq_f, va[c3]), __fmul_rn(pc.fp_f, vb[c3]));
         const float G = __fmul_rn(gn, d[c3]);
-        na[c3] = __fadd_rn(V, __fmul_rn(pc.fp_f, G));
-        nb[c3] = __fsub_rn(V, __fmul_rn(pc.fq_f, G));
+        na[c3] = __fadd_rn(V[c3], __fmul_rn(pc.fp_f, G));
+        nb[c3] = __fsub_rn(V[c3], __fmul_rn(pc.fq_f, G));
     }
+}
+__device__ __forceinline__ void scatter_f32(const DevPair& pc, long long Erel, const float d[3],
+                                            const float va[3], const float vb[3], float na[3], float nb[3]) {
+    const float V[3] = {cm_velocity_f32(pc, va[0], vb[0]), cm_velocity_f32(pc, va[1], vb[1]),
+                        cm_velocity_f32(pc, va[2], vb[2])};
+    scatter_cm_f32(pc, Erel, d, V, na, nb);
 }
 
 // FP32 K5 draw of one molecule's levels at collision energy Ec (float, from
@@ -2445,7 +2454,9 @@ __global__ void __launch_bounds__(128) k_relax(StepArgs A, int r) {
 // work-class order, heaviest class first).  The molecules with
 // modes, P before Q, with the alias K5 draw (relative energy in int64 fixed
 // point), then isotropic scattering with the centre-of-mass velocity kept.
-template <class R>
+// COUNT: the K5 work counters (profiled steps only: four more live registers
+// under the 64-register bound cost the kernel ~4%).
+template <class R, bool COUNT>
 __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A, int r) {
     static_assert(std::is_same<R, float>::value, "FP32 mode only");
     const Consts* __restrict__ C = A.C;
@@ -2469,41 +2480,56 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         const uint4 qa = REC_LD(recs + 2 * ip + 1), qb = REC_LD(recs + 2 * iq + 1);
         const int sP = (int)(a.w & 0xFFu), sQ = (int)(b.w & 0xFFu);
         const DevPair& pc = C->pair[sP * MAXS + sQ];
-        const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
-        const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
-        const float g2 = g2_f32(va, vb);
-        const long long Etr = etr_fix_f32(pc, g2);
-        uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
-        const long long EvP = evib_fix(A.levfix, C->sp[sP], qP);
-        const long long EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
-        const float erP = C->sp[sP].rot_dof ? __uint_as_float(qa.w) : 0.f;
-        const float erQ = C->sp[sQ].rot_dof ? __uint_as_float(qb.w) : 0.f;
-        // reaction tests (recombination, then the QK channels in fixed point);
-        // a reacting pair goes to the reaction queue instead
-        bool react = false;
-        uint32_t chan = 0u, mpos = 0u;
-        if (C->n_reactions > 0) {
-            if (C->has_recomb &&
-                recomb_test<float>(A, C, cidx, r, kp, sP, sQ, (double)sg_f32(pc, C->amode, g2), chan, mpos)) {
-                react = true;
-            } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
-                                                     fix2d(EvQ), chan, (double)erP, (double)erQ)) {
-                react = true;
-            } else if (pc.qk) {  // a pair no QK reaction can take draws nothing from this stream
-                Stream sp;
-                st_init(sp, rs.seed, step, lcell, rk, PU_PAIR);
-                st_u32(sp);  // the acceptance draw
-                const float u_ster = st_u32(sp);
-                const float u_sel = st_u32(sp);
-                const float u_ch = st_u32(sp);
-                react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan, erP,
-                                          erQ) > 0;
-            }
+        // what the pair keeps across its draws is held small (the sampler's
+        // own state needs the registers): the centre-of-mass velocity instead
+        // of both velocities, and the species as the records' meta words.
+        // (Storing a relaxed molecule's levels as soon as they are drawn, to
+        // drop the pair's level words too, measured slower.)
+        float V[3];
+        float g2;
+        {
+            const float va[3] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z)};
+            const float vb[3] = {__uint_as_float(b.x), __uint_as_float(b.y), __uint_as_float(b.z)};
+            g2 = g2_f32(va, vb);
+#pragma unroll
+            for (int c3 = 0; c3 < 3; ++c3) V[c3] = cm_velocity_f32(pc, va[c3], vb[c3]);
         }
-        const uint32_t rslot = queue_slot(A.qsize + 2 * r + 1, react);
-        if (react) {
-            A.qB[rslot] = make_uint4((uint32_t)cidx, kp, chan, mpos);
-            continue;
+        const long long Etr = etr_fix_f32(pc, g2);
+        long long EvP, EvQ;
+        float erP, erQ;
+        uint32_t qP[4] = {qa.x, qa.y, qa.z, qa.w}, qQ[4] = {qb.x, qb.y, qb.z, qb.w};
+        {
+            EvP = evib_fix(A.levfix, C->sp[sP], qP);
+            EvQ = evib_fix(A.levfix, C->sp[sQ], qQ);
+            erP = C->sp[sP].rot_dof ? __uint_as_float(qa.w) : 0.f;
+            erQ = C->sp[sQ].rot_dof ? __uint_as_float(qb.w) : 0.f;
+            // reaction tests (recombination, then the QK channels in fixed
+            // point); a reacting pair goes to the reaction queue instead
+            bool react = false;
+            uint32_t chan = 0u, mpos = 0u;
+            if (C->n_reactions > 0) {
+                if (C->has_recomb &&
+                    recomb_test<float>(A, C, cidx, r, kp, sP, sQ, (double)sg_f32(pc, C->amode, g2), chan, mpos)) {
+                    react = true;
+                } else if (C->has_tce && tce_test<float>(A, C, rs, lcell, rk, sP, sQ, fix2d(Etr), fix2d(EvP),
+                                                         fix2d(EvQ), chan, (double)erP, (double)erQ)) {
+                    react = true;
+                } else if (pc.qk) {  // a pair no QK reaction can take draws nothing from this stream
+                    Stream sp;
+                    st_init(sp, rs.seed, step, lcell, rk, PU_PAIR);
+                    st_u32(sp);  // the acceptance draw
+                    const float u_ster = st_u32(sp);
+                    const float u_sel = st_u32(sp);
+                    const float u_ch = st_u32(sp);
+                    react = reaction_pick_fix(A, C, sP, sQ, qP, qQ, Etr, EvP, EvQ, u_ster, u_sel, u_ch, chan, erP,
+                                              erQ) > 0;
+                }
+            }
+            const uint32_t rslot = queue_slot(A.qsize + 2 * r + 1, react);
+            if (react) {
+                A.qB[rslot] = make_uint4((uint32_t)cidx, kp, chan, mpos);
+                continue;
+            }
         }
         // the molecules with modes, P before Q, in one loop: a lane relaxing
         // its pair's first molecule and a lane relaxing its second (an H-CH3
@@ -2518,7 +2544,9 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
             st_init(st, rs.seed, step, lcell, rk, isQ ? PU_LB_B : PU_LB_A);
             uint32_t nq[4];
             bool took;
-            Erel = relax_one(A, C, isQ ? sQ : sP, nq, isQ ? EvQ : EvP, st, Erel, o, w[0], w[1], took);
+            uint32_t wl_ = 0, wm_ = 0;  // unread (and dropped) without COUNT
+            Erel = relax_one(A, C, isQ ? sQ : sP, nq, isQ ? EvQ : EvP, st, Erel, o, COUNT ? w[0] : wl_,
+                             COUNT ? w[1] : wm_, took);
             if (took) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -2527,17 +2555,22 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
                 }
             }
         }
-        w_samp += (uint32_t)nmol;
-        w_pair++;
+        if (COUNT) {
+            w_samp += (uint32_t)nmol;
+            w_pair++;
+        }
         if (C->has_rot) Erel = rot_relax_fix(A, C, rs.seed, step, lcell, rk, sP, sQ, erP, erQ, qP, qQ, Erel);
         Stream ss;
         st_init(ss, rs.seed, step, lcell, rk, PU_SCAT);
         float d[3];
         iso_dir<float>(ss, d);
         float na[3], nb[3];
-        scatter_f32(pc, Erel, d, va, vb, na, nb);
-        REC_ST(recs + 2 * ip, make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]), a.w));
-        REC_ST(recs + 2 * iq, make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]), b.w));
+        scatter_cm_f32(pc, Erel, d, V, na, nb);
+        // the meta word is the species (the selection admits no removed member)
+        REC_ST(recs + 2 * ip, make_uint4(__float_as_uint(na[0]), __float_as_uint(na[1]), __float_as_uint(na[2]),
+                                         (uint32_t)sP));
+        REC_ST(recs + 2 * iq, make_uint4(__float_as_uint(nb[0]), __float_as_uint(nb[1]), __float_as_uint(nb[2]),
+                                         (uint32_t)sQ));
         REC_ST(recs + 2 * ip + 1, make_uint4(qP[0], qP[1], qP[2], qP[3]));
         REC_ST(recs + 2 * iq + 1, make_uint4(qQ[0], qQ[1], qQ[2], qQ[3]));
         A.cflag[ev_idx] = ev_final(o);
@@ -2545,6 +2578,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
     }
     // work counters: reduced over the CTA, one atomic per CTA and counter
     // (none for a CTA without work: an empty round's launch stays cheap)
+    if (!COUNT) return;
     __shared__ unsigned long long wred[4][4];
     unsigned long long wv[4] = {w[0], w[1], w_samp, w_pair};
 #pragma unroll
@@ -3053,7 +3087,10 @@ void launch_phase_impl(const StepArgs& a, int r, int phase, int grid, cudaStream
         if constexpr (std::is_same<R, float>::value)
             if (a.qorder) k_qorder<<<QORDER_GRID, 256, 0, s>>>(a, r);
     } else if (phase == 1) {
-        if constexpr (std::is_same<R, float>::value) k_relax_fast<R><<<gr, 128, 0, s>>>(a, r);
+        if constexpr (std::is_same<R, float>::value) {
+            if (a.work) k_relax_fast<R, true><<<gr, 128, 0, s>>>(a, r);
+            else k_relax_fast<R, false><<<gr, 128, 0, s>>>(a, r);
+        }
         else k_relax<R><<<gr, 128, 0, s>>>(a, r);
     } else if (a.has_reactions) k_react<R><<<gx, 128, 0, s>>>(a, r);
 }

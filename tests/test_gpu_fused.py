@@ -100,8 +100,17 @@ def test_fused_equals_queue_path(name):
         a, b = _state(f, w), _state(q, w)
         for x, y, what in zip(a, b, ("v", "qn", "species", "cell", "counters", "sgmax", "work")):
             assert np.array_equal(x, y), (name, what)
+    # one more step each with profiling on: the K5 work is counted then
+    f.set_profiling(True)
+    q.set_profiling(True)
+    f.step(1)
+    q.step(1)
+    a, b = _state(f, w), _state(q, w)
+    for x, y, what in zip(a, b, ("v", "qn", "species", "cell", "counters", "sgmax", "work")):
+        assert np.array_equal(x, y), (name, what)
+    assert a[6][3] > 0  # relaxed pairs counted
     c = f.read_counters(0)
-    assert c[1] > 0 and c[7] == 10  # collisions happened; ten steps
+    assert c[1] > 0 and c[7] == 11  # collisions happened; eleven steps
     if name.startswith("exchange"):
         assert c[8] > 0  # exchange events
     if name == "two_rounds":
@@ -154,8 +163,11 @@ def test_queue_path_launch_count():
     g.step(3)
     p.step(3)
     assert g.kernel_launches() - n0 == p.kernel_launches() - m0 == 3 * 12
-    for x, y in zip(_state(g, w), _state(p, w)):
+    a, b = _state(g, w), _state(p, w)
+    for x, y in zip(a[:6], b[:6]):
         assert np.array_equal(x, y)
+    # the K5 work is counted on profiled steps only
+    assert int(a[6].sum()) == 0 and b[6][3] > 0
 
 
 def test_fused_profiling_class():
