@@ -135,6 +135,37 @@ __device__ __forceinline__ uint32_t st_word(Stream& s) {
     return w;
 }
 __device__ __forceinline__ float st_u32(Stream& s) { return (float)(st_word(s) >> 8) * 0x1p-24f; }
+// The same stream with its key and fixed counter words in shared memory (one
+// column per thread of a CTA of at most 128 threads: k_relax_fast, launched
+// with 128), so that a long loop of draws holds only the block counter and
+// the buffered block in registers: the FP32 relaxation kernel's LB draws
+// (the kernel spills under its 64-register bound; 6 fewer live registers in
+// the draw loop made it 3% faster).  The words drawn are those of Stream.
+static __shared__ uint32_t s_lbkey[6][128];
+struct LbStream {
+    uint32_t blk;
+    uint32_t w0, w1, w2, w3;
+    int pos;
+};
+__device__ __forceinline__ void st_init(LbStream& s, uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                                        uint32_t purpose) {
+    const int t = threadIdx.x;
+    s_lbkey[0][t] = (uint32_t)seed; s_lbkey[1][t] = (uint32_t)(seed >> 32);
+    s_lbkey[2][t] = c0; s_lbkey[3][t] = c1; s_lbkey[4][t] = c2; s_lbkey[5][t] = purpose << 24;
+    s.blk = 0; s.pos = 4;
+}
+__device__ __forceinline__ uint32_t st_word(LbStream& s) {
+    if (s.pos > 3) {
+        const int t = threadIdx.x;
+        s.w0 = s_lbkey[2][t]; s.w1 = s_lbkey[3][t]; s.w2 = s_lbkey[4][t]; s.w3 = s_lbkey[5][t] | (s.blk & 0xFFFFFFu);
+        philox10(s.w0, s.w1, s.w2, s.w3, s_lbkey[0][t], s_lbkey[1][t]);
+        s.blk++;
+        s.pos = 0;
+    }
+    const uint32_t w = s.pos == 0 ? s.w0 : (s.pos == 1 ? s.w1 : (s.pos == 2 ? s.w2 : s.w3));
+    s.pos++;
+    return w;
+}
 // the top 24 bits of the next word (the bits behind st_u32)
 __device__ __forceinline__ uint32_t st_bits24(Stream& s) { return st_word(s) >> 8; }
 template <class R> __device__ __forceinline__ R st_uni(Stream& s);
@@ -1096,9 +1127,10 @@ __device__ __forceinline__ void scatter_f32(const DevPair& pc, long long Erel, c
 // from the small level list.  Returns S_OK with the levels in q and their
 // fixed-point energy in Esel, S_OVER, S_DEGEN or S_CAP.  Counts mode draws
 // and level evaluations (one per draw).
+template <class ST>
 static __device__ int sample_alias_tab(const StepArgs& A, const K5Ent* __restrict__ T,
                                        const AliasEnt* __restrict__ AE, const DevSpecies& S, int amode,
-                                       float Ec, Stream& st, uint32_t (&q)[4], long long& Esel,
+                                       float Ec, ST& st, uint32_t (&q)[4], long long& Esel,
                                        uint32_t& trials, uint32_t& wlev, uint32_t& wmode) {
     const int n = S.n_modes, MT = S.MT, gsh = S.gshift, gj0 = S.gj0;
     q[0] = q[1] = q[2] = q[3] = 0u;
@@ -1192,8 +1224,9 @@ static __device__ int sample_alias_tab(const StepArgs& A, const K5Ent* __restric
     Esel = es;
     return S_OK;
 }
+template <class ST>
 static __device__ __forceinline__ int sample_alias_f32(const StepArgs& A, const DevSpecies& S, int amode,
-                                                       float Ec, Stream& st, uint32_t (&q)[4], long long& Esel,
+                                                       float Ec, ST& st, uint32_t (&q)[4], long long& Esel,
                                                        uint32_t& trials, uint32_t& wlev, uint32_t& wmode) {
     return sample_alias_tab(A, A.k5e + S.tab_off, A.ae, S, amode, Ec, st, q, Esel, trials, wlev, wmode);
 }
@@ -1202,8 +1235,9 @@ static __device__ __forceinline__ int sample_alias_f32(const StepArgs& A, const 
 // E_vib Evold) against the relative energy Erel; returns the relative energy
 // left, and took = true when q was replaced by a new state.  sp < 0 or a
 // species without modes keeps everything.
+template <class ST>
 static __device__ __forceinline__ long long relax_one(const StepArgs& A, const Consts* __restrict__ C, int sp,
-                                                      uint32_t (&q)[4], long long Evold, Stream& st,
+                                                      uint32_t (&q)[4], long long Evold, ST& st,
                                                       long long Erel, PairOut& o, uint32_t& wl, uint32_t& wm,
                                                       bool& took) {
     took = false;
@@ -2540,7 +2574,7 @@ __global__ void __launch_bounds__(128, HCAO_RELAX_MINB) k_relax_fast(StepArgs A,
         const int nmol = (int)relP + (int)(C->sp[sQ].n_modes > 0);
         for (int m = 0; m < nmol; ++m) {
             const bool isQ = !relP || m == 1;
-            Stream st;
+            LbStream st;
             st_init(st, rs.seed, step, lcell, rk, isQ ? PU_LB_B : PU_LB_A);
             uint32_t nq[4];
             bool took;
