@@ -140,7 +140,8 @@ __device__ __forceinline__ float st_u32(Stream& s) { return (float)(st_word(s) >
 // with 128), so that a long loop of draws holds only the block counter and
 // the buffered block in registers: the FP32 relaxation kernel's LB draws
 // (the kernel spills under its 64-register bound; 6 fewer live registers in
-// the draw loop made it 3% faster).  The words drawn are those of Stream.
+// the draw loop made the exchange step 2% faster).  The words drawn are those
+// of Stream.
 static __shared__ uint32_t s_lbkey[6][128];
 struct LbStream {
     uint32_t blk;
