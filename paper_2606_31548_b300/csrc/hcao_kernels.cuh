@@ -26,6 +26,10 @@
 //   end of step, one warp per FINISH_CHUNK pair slots of a cell:
 //   k_finish_count per-cell counters; k_finish_append stable append of created
 //   particles; k_cellupd (sigma g)_max, counts, step; k_compact removals.
+// Read-outs run flat over a reservoir's particles in canonical order, on a
+// particle prefix the device scans (k_cell_prefix): k_moments (momentum and
+// energies; FP32 in int64 fixed point), k_levelpop, k_pack, k_erot; the
+// counters are summed over the cells on the device (k_sum_counters).
 // Queue order is irrelevant: pairs of one round are disjoint and every draw is
 // keyed by (step, cell, round, pair), never by a thread or queue position.
 // Randomness: Philox4x32-10 keyed by the reservoir seed, counter
@@ -2346,9 +2350,10 @@ __global__ void __launch_bounds__(SELECT_THREADS) k_select(StepArgs A, int r) {
 // by class at qA[0 ..): class c starts at the sum of the counts of classes
 // below c (heaviest work first).  A CTA takes a chunk of 2048 staged entries,
 // ranks them per class in shared memory, reserves each class's share of the
-// chunk with one atomic on the class cursor and writes them out, so a class
-// keeps the chunks' order.  The order within a class is free: every draw of a
-// pair is keyed by the pair, not by its queue slot.
+// chunk with one atomic on the class cursor and writes them out, so a chunk's
+// entries of one class stay together (and near the cells they came from).
+// The order within a class is free: every draw of a pair is keyed by the
+// pair, not by its queue slot.
 constexpr int QORDER_GRID = 592;  // 148 SMs x 4 CTAs of 256 threads, grid-stride over chunks
 constexpr int QORDER_PER = 8;     // entries per thread and chunk
 static __global__ void __launch_bounds__(256) k_qorder(StepArgs A, int r) {
