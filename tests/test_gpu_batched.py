@@ -69,6 +69,18 @@ def test_autotune_does_not_change_results():
     assert chosen[0] > 0 and chosen[1] > 0 and chosen[2] in (0, 1)
 
 
+def test_autotune_single_work_class():
+    """One species: a single work class, so the queue goes straight to its
+    place (no placement kernel) and the autotuner times only the grids."""
+    w = W.relaxation_triatomic(n_particles=20000, n_cells=8)
+    g = hcao.from_workload(w, precision=hcao.FP32)
+    n0 = g.kernel_launches()
+    g.step(1)
+    assert g.kernel_launches() - n0 == 2 + 2 * 2 + 2  # set-up, (select, relax) x 2 rounds, finish
+    chosen = g.autotune(1)
+    assert int(g.read_counters(0)[7]) == 8 and chosen[2] == 0
+
+
 def test_remove_all_then_add_again():
     """Reservoirs come and go (the serving pattern): removing the last one and
     adding another keeps the context usable and the results unchanged."""
