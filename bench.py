@@ -636,7 +636,7 @@ def main():
                             f"{2 * S * psteps / args.steps:.4g} algorithmic bytes per step",
             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
             "kernel": "k_collide_fused (the whole collision phase, one launch per step)" if fused
-                      else "collide phase (select + relax + react kernels)",
+                      else "collide phase (select + work-class placement + relax + react kernels)",
             "path": "fused" if fused else "queue",
             "bytes_per_particle_step": 2 * S,
             "step_view": {"achieved_GBps": (2 * S * psteps) / (ms / 1e3) / 1e9 if ms > 0 else None,
